@@ -1,0 +1,358 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each test checks one oracle function against something other than itself: an
+exact algebraic identity of the paper (Sec. 5.1 two-level exactness), a dense
+triple product, a brute-force enumeration of a definition on a tiny input, a
+textbook invariant, a published test vector, or a library direct solver.
+"""
+import os
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+import scipy.sparse.linalg as sla
+
+import oracle
+from oracle import Q_AMG_A, Q_AMG_P, Q_AMG_R, Q_AMG_S, Q_MGR_COR, Q_MGR_CORKEPT, Q_MGR_S, Q_MGR_W
+from paper_1904_05960_gb300 import synth
+from tests.helpers import labeled_system, poisson3d, scalar_problem
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def dense(p):
+    return p.to_scipy().toarray()
+
+
+# ---------------------------------------------------------------- splitmix64
+def test_splitmix64_published_vectors():
+    """The PMIS weight hash equals the published SplitMix64 outputs."""
+    with open(os.path.join(GOLDEN, "splitmix64.txt")) as f:
+        rows = [l.split() for l in f if l.strip() and not l.startswith("#")]
+    assert rows
+    for x, out in rows:
+        assert oracle.splitmix64(int(x, 16)) == int(out, 16)
+
+
+# ------------------------------------------------- reduction operators (5.1)
+@pytest.mark.parametrize("two_phase", [False, True])
+def test_wp_and_coarse_grid_equal_dense_triple_product(two_phase):
+    """With no dropping, S_1 = R~ A P~ = A_CC - A_CF D_FF^-1 A_FC (Sec. 5.2),
+    with R~ = [0 I] and P~ = [W_p; I], W_p = -D_FF^-1 A_FC (Eq. injective_rp)."""
+    p = labeled_system(seed=3, two_phase=two_phase)
+    o = oracle.Oracle(p, nmax_drop=[-1, -1])
+    A = dense(p)
+    F = np.nonzero(p.dof_label == 0)[0]
+    Cc = np.nonzero(p.dof_label != 0)[0]
+    D = np.diag(A[np.ix_(F, F)])
+    Wp = -A[np.ix_(F, Cc)] / D[:, None]
+    assert np.allclose(o.scipy(Q_MGR_W, 0).toarray(), Wp, rtol=1e-13, atol=1e-14)
+    Pt = np.zeros((len(p.rhs), len(Cc)))
+    Pt[F] = Wp
+    Pt[Cc, np.arange(len(Cc))] = 1.0
+    Rt = np.zeros((len(Cc), len(p.rhs)))
+    Rt[np.arange(len(Cc)), Cc] = 1.0
+    S_dense = Rt @ A @ Pt
+    S = o.scipy(Q_MGR_S, 0).toarray()
+    assert np.abs(S - S_dense).max() <= 1e-12 * np.abs(S_dense).max()
+
+
+def test_second_reduction_is_pressure_schur_complement():
+    """S_2 = A~_pp - A~_ps D_ss^-1 A~_sp with no dropping (Eq. coarse_grid_pressure)."""
+    p = labeled_system(seed=5, two_phase=True)
+    o = oracle.Oracle(p)
+    S1 = o.scipy(Q_MGR_S, 0).toarray()
+    s_idx = np.arange(0, S1.shape[0], 2)
+    p_idx = np.arange(1, S1.shape[0], 2)
+    Dss = np.diag(S1[np.ix_(s_idx, s_idx)])
+    S2_dense = S1[np.ix_(p_idx, p_idx)] - S1[np.ix_(p_idx, s_idx)] @ (S1[np.ix_(s_idx, p_idx)] / Dss[:, None])
+    S2 = o.scipy(Q_MGR_S, 1).toarray()
+    assert np.abs(S2 - S2_dense).max() <= 1e-12 * np.abs(S2_dense).max()
+
+
+def test_drop_nmax_zero_keeps_only_point_diagonal_blocks():
+    """N_max = 0 leaves A_cor with diagonal field sub-blocks only (Sec. 5.2)."""
+    p = labeled_system(seed=7, two_phase=True, density=0.3)
+    o = oracle.Oracle(p, nmax_drop=[0, -1])
+    kept = o.scipy(Q_MGR_CORKEPT, 0).tocoo()
+    cnode = p.dof_node[p.dof_label != 0]
+    assert kept.nnz > 0
+    assert np.all(cnode[kept.row] == cnode[kept.col])
+    full = o.scipy(Q_MGR_COR, 0).tocoo()
+    same = cnode[full.row] == cnode[full.col]
+    assert same.sum() == kept.nnz
+
+
+@pytest.mark.parametrize("nmax", [1, 4])
+def test_drop_rule_brute_force(nmax):
+    """G keeps the own-point entries plus the nmax others of largest |value|."""
+    p = labeled_system(seed=11, two_phase=True, density=0.35)
+    o = oracle.Oracle(p, nmax_drop=[nmax, -1])
+    A = dense(p)
+    F = np.nonzero(p.dof_label == 0)[0]
+    Cc = np.nonzero(p.dof_label != 0)[0]
+    D = np.diag(A[np.ix_(F, F)])
+    cor_dense = A[np.ix_(Cc, F)] @ (A[np.ix_(F, Cc)] / D[:, None])
+    cor = o.scipy(Q_MGR_COR, 0)
+    kept = o.scipy(Q_MGR_CORKEPT, 0)
+    assert np.allclose(cor.toarray(), cor_dense, rtol=1e-12, atol=1e-13)
+    cnode = p.dof_node[Cc]
+    for i in range(len(Cc)):
+        cols = cor.indices[cor.indptr[i]:cor.indptr[i + 1]]
+        own = [c for c in cols if cnode[c] == cnode[i]]
+        rest = [c for c in cols if cnode[c] != cnode[i]]
+        rest.sort(key=lambda c: (-abs(cor_dense[i, c]), c))
+        want = sorted(own + rest[:nmax])
+        got = sorted(kept.indices[kept.indptr[i]:kept.indptr[i + 1]].tolist())
+        assert got == want
+
+
+# ---------------------------------------- MGR exactness identities (Sec. 5.1)
+def test_two_level_mgr_is_exact_with_ideal_components():
+    """A_FF diagonal makes Jacobi interpolation ideal; with exact F-relaxation
+    and an exact coarse solve, I - M^-1 A = 0 (Eqs. MGR-mul1 / MGR-pre)."""
+    p = labeled_system(seed=13, two_phase=False, diag_uu=True, n_nodes=30, n_cells=40)
+    o = oracle.Oracle(p, nmax_drop=[-1], amg_max_coarse=1000)
+    A = dense(p)
+    rng = np.random.default_rng(0)
+    for _ in range(3):
+        x = rng.standard_normal(p.n)
+        z = o.apply(A @ x)
+        assert np.linalg.norm(z - x) <= 1e-10 * np.linalg.norm(x)
+
+
+def test_three_level_mgr_is_exact_with_ideal_components():
+    """Same identity applied recursively (Algorithm 2): A_uu and A_ss diagonal,
+    no dropping, no global smoother, exact coarsest solve."""
+    p = labeled_system(seed=17, two_phase=True, diag_uu=True, diag_ss=True, n_nodes=25,
+                       n_cells=30)
+    o = oracle.Oracle(p, nmax_drop=[-1, -1], global_sweeps=[0, 0], amg_max_coarse=1000)
+    A = dense(p)
+    x = np.random.default_rng(1).standard_normal(p.n)
+    z = o.apply(A @ x)
+    assert np.linalg.norm(z - x) <= 1e-10 * np.linalg.norm(x)
+
+
+def test_dropping_breaks_exactness():
+    """The same setting with N_max = 0 is no longer exact (a control for the
+    exactness tests: G does change the coarse grid)."""
+    p = labeled_system(seed=13, two_phase=False, diag_uu=True, n_nodes=30, n_cells=40,
+                       density=0.3)
+    o = oracle.Oracle(p, nmax_drop=[0], amg_max_coarse=1000)
+    A = dense(p)
+    x = np.random.default_rng(0).standard_normal(p.n)
+    z = o.apply(A @ x)
+    assert np.linalg.norm(z - x) > 1e-6 * np.linalg.norm(x)
+
+
+def test_block_jacobi_global_smoother_exact_on_block_diagonal():
+    """One sweep of cell-block Jacobi solves a block-diagonal flow system
+    exactly, so the whole level returns A^-1 v (global relaxation of Alg. 2)."""
+    p0 = labeled_system(seed=19, two_phase=True, block_diag_flow=True, n_nodes=1, n_cells=50)
+    keep = np.nonzero(p0.dof_label != 0)[0]
+    A = p0.to_scipy()[keep][:, keep]
+    from tests.helpers import to_problem
+    p = to_problem(A, p0.dof_label[keep], p0.dof_node[keep], p0.dof_comp[keep])
+    o = oracle.Oracle(p, num_levels=1, f_label_mask=[1 << 1], frelax=[oracle.FRELAX_JACOBI],
+                      frelax_sweeps=[1], nmax_drop=[-1], global_sweeps=[1])
+    x = np.random.default_rng(2).standard_normal(p.n)
+    z = o.apply(A @ x)
+    assert np.linalg.norm(z - x) <= 1e-12 * np.linalg.norm(x)
+
+
+def test_fgmres_one_iteration_with_exact_preconditioner():
+    p = labeled_system(seed=13, two_phase=False, diag_uu=True, n_nodes=30, n_cells=40)
+    o = oracle.Oracle(p, nmax_drop=[-1], amg_max_coarse=1000)
+    r = o.fgmres(p.rhs)
+    assert r["status"] == 0 and r["iters"] == 1
+
+
+# ----------------------------------------------------------------- AMG (Sec. 6)
+def _amg_only(A, **kw):
+    return oracle.Oracle(scalar_problem(A), num_levels=0, **kw)
+
+
+def test_strength_brute_force():
+    rng = np.random.default_rng(4)
+    A = sp.random(60, 60, density=0.2, random_state=rng, format="csr",
+                  data_rvs=lambda k: rng.uniform(-1, 1, k)) + sp.eye(60) * 3
+    A = sp.csr_matrix(A)
+    A.sort_indices()
+    o = _amg_only(A, amg_max_coarse=4)
+    S = o.scipy(Q_AMG_S, 0, 0)
+    Ad = A.toarray()
+    for i in range(60):
+        cols = [j for j in A.indices[A.indptr[i]:A.indptr[i + 1]] if j != i]
+        negs = [-Ad[i, j] for j in cols]
+        m = max(negs) if negs else 0.0
+        want = sorted(j for j in cols if m > 0 and -Ad[i, j] >= 0.25 * m)
+        got = sorted(S.indices[S.indptr[i]:S.indptr[i + 1]].tolist())
+        assert got == want
+
+
+def test_strength_unknown_approach_ignores_other_components():
+    """The A_uu AMG (F-relaxation of the first reduction) sees only couplings
+    between equal displacement components (unknown approach, Sec. 6); brute
+    force over the definition restricted to equal components."""
+    p = synth.single_phase(3, 3, 3)
+    o = oracle.Oracle(p, amg_max_coarse=8)
+    nu = p.meta["n_u"]
+    Auu = p.to_scipy()[:nu, :nu].tocsr()
+    comp = p.dof_comp[:nu]
+    S = o.scipy(Q_AMG_S, 0, 0)
+    Sc = S.tocoo()
+    assert Sc.nnz > 0 and np.all(comp[Sc.row] == comp[Sc.col])
+    for i in range(nu):
+        cols = [j for j in Auu.indices[Auu.indptr[i]:Auu.indptr[i + 1]]
+                if j != i and comp[j] == comp[i]]
+        vals = {j: Auu[i, j] for j in cols}
+        m = max([-v for v in vals.values()], default=0.0)
+        want = sorted(j for j in cols if m > 0 and -vals[j] >= 0.25 * m)
+        assert sorted(S.indices[S.indptr[i]:S.indptr[i + 1]].tolist()) == want
+
+
+def _pmis_invariants(S, cf):
+    """What the synchronous PMIS rounds guarantee: every point decided; no two
+    C points depend strongly on each other (the later one would have been made
+    F); isolated points are F; every other F point has a C point in S_i; where
+    S is symmetric, C is an independent set."""
+    St = S.T.tocsr()
+    C = cf == 1
+    assert np.all((cf == 1) | (cf == -1))
+    M = S.multiply(St).tocoo()            # mutual strong dependence
+    assert not np.any(C[M.row] & C[M.col]), "two C points depend on each other"
+    if (S != St).nnz == 0:
+        Sc = S.tocoo()
+        assert not np.any(C[Sc.row] & C[Sc.col]), "C points must be independent"
+    for i in range(S.shape[0]):
+        row = S.indices[S.indptr[i]:S.indptr[i + 1]]
+        trow = St.indices[St.indptr[i]:St.indptr[i + 1]]
+        if len(row) == 0 and len(trow) == 0:
+            assert not C[i], f"isolated point {i} must be F"
+            continue
+        if not C[i]:
+            assert np.any(C[row]), f"F point {i} has no C point in S_i"
+
+
+def test_pmis_invariants_poisson():
+    A = poisson3d(10, 9, 8)
+    o = _amg_only(A, amg_max_coarse=10)
+    for k in range(o.amg_levels(0) - 1):
+        _pmis_invariants(o.scipy(Q_AMG_S, 0, k), o.cf(0, k))
+
+
+def test_pmis_invariants_elasticity_hierarchy():
+    p = synth.config(1)
+    o = oracle.Oracle(p)
+    for k in range(o.amg_levels(0) - 1):
+        _pmis_invariants(o.scipy(Q_AMG_S, 0, k), o.cf(0, k))
+
+
+def test_interpolation_structure_and_constant_preservation():
+    """Direct interpolation: C rows are unit rows, F rows use strong C
+    neighbours only, at most P_max entries, and rows whose matrix row sums to
+    zero interpolate constants exactly (also after truncation with row-sum
+    rescaling)."""
+    A = poisson3d(9, 9, 9)
+    o = _amg_only(A, amg_max_coarse=10, amg_pmax=4)
+    S = o.scipy(Q_AMG_S, 0, 0)
+    P = o.scipy(Q_AMG_P, 0, 0)
+    cf = o.cf(0, 0)
+    cidx = np.cumsum(cf == 1) - 1
+    rowsum = np.asarray(A.sum(axis=1)).ravel()
+    Pone = P @ np.ones(P.shape[1])
+    for i in range(A.shape[0]):
+        cols = P.indices[P.indptr[i]:P.indptr[i + 1]]
+        vals = P.data[P.indptr[i]:P.indptr[i + 1]]
+        if cf[i] == 1:
+            assert cols.tolist() == [cidx[i]] and vals.tolist() == [1.0]
+            continue
+        assert len(cols) <= 4
+        strongC = set(cidx[j] for j in S.indices[S.indptr[i]:S.indptr[i + 1]] if cf[j] == 1)
+        assert set(cols.tolist()) <= strongC
+        if rowsum[i] == 0 and len(cols):
+            assert abs(Pone[i] - 1.0) <= 1e-14
+
+
+def test_interpolation_without_truncation_keeps_all_strong_c():
+    A = poisson3d(7, 7, 7)
+    o = _amg_only(A, amg_max_coarse=10, amg_pmax=0)
+    S = o.scipy(Q_AMG_S, 0, 0)
+    P = o.scipy(Q_AMG_P, 0, 0)
+    cf = o.cf(0, 0)
+    for i in np.nonzero(cf == -1)[0]:
+        nC = sum(cf[j] == 1 for j in S.indices[S.indptr[i]:S.indptr[i + 1]])
+        assert P.indptr[i + 1] - P.indptr[i] == nC
+
+
+def test_galerkin_coarse_operator_is_dense_triple_product():
+    p = synth.config(1)
+    o = oracle.Oracle(p)
+    for slot in (0, 1):
+        for k in range(o.amg_levels(slot) - 1):
+            A = o.scipy(Q_AMG_A, slot, k).toarray()
+            P = o.scipy(Q_AMG_P, slot, k).toarray()
+            R = o.scipy(Q_AMG_R, slot, k).toarray()
+            assert np.array_equal(R, P.T)
+            Ac = o.scipy(Q_AMG_A, slot, k + 1).toarray()
+            ref = P.T @ A @ P
+            assert np.abs(Ac - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+def test_l1_diagonal():
+    A = poisson3d(5, 4, 3)
+    o = _amg_only(A, amg_max_coarse=5)
+    Ad = A.toarray()
+    want = np.diag(Ad) + (np.abs(Ad).sum(axis=1) - np.abs(np.diag(Ad)))
+    assert np.allclose(o.l1(0, 0), want, rtol=1e-15)
+
+
+def test_coarsest_level_is_exact_solve():
+    A = poisson3d(6, 5, 4)
+    o = _amg_only(A, amg_max_coarse=1000)
+    b = np.random.default_rng(3).standard_normal(A.shape[0])
+    x = o.vcycle(0, b)
+    assert np.allclose(x, np.linalg.solve(A.toarray(), b), rtol=1e-12, atol=1e-12)
+
+
+def test_vcycle_symmetric_and_contracting_on_poisson():
+    """With R = P^T and one l1-Jacobi sweep before and after, the V-cycle is a
+    symmetric operator B, and the error propagator I - BA contracts."""
+    A = poisson3d(8, 8, 8)
+    o = _amg_only(A, amg_max_coarse=20)
+    assert o.amg_levels(0) >= 3
+    n = A.shape[0]
+    B = np.column_stack([o.vcycle(0, e) for e in np.eye(n)])
+    assert np.abs(B - B.T).max() <= 1e-12 * np.abs(B).max()
+    assert np.linalg.eigvalsh((B + B.T) / 2).min() > 0
+    E = np.eye(n) - B @ A.toarray()
+    rho = np.abs(np.linalg.eigvals(E)).max()
+    assert rho < 0.9
+
+
+# --------------------------------------------------------------- full solves
+def test_single_phase_solve_matches_direct_solver():
+    p = synth.config(1)
+    o = oracle.Oracle(p)
+    r = o.fgmres(p.rhs, restart=50, maxit=500, rtol=1e-8)
+    assert r["status"] == 0 and r["relres"] <= 1e-8
+    x = sla.spsolve(p.to_scipy().tocsc(), p.rhs)
+    assert np.linalg.norm(r["x"] - x) <= 1e-6 * np.linalg.norm(x)
+
+
+def test_two_phase_solve_matches_direct_solver():
+    p = synth.two_phase(10, 9, 6)
+    o = oracle.Oracle(p)
+    r = o.fgmres(p.rhs, restart=50, maxit=500, rtol=1e-8)
+    assert r["status"] == 0 and r["relres"] <= 1e-8
+    x = sla.spsolve(p.to_scipy().tocsc(), p.rhs)
+    assert np.linalg.norm(r["x"] - x) <= 1e-6 * np.linalg.norm(x)
+    A = p.to_scipy()
+    assert np.linalg.norm(p.rhs - A @ r["x"]) <= 1e-8 * np.linalg.norm(p.rhs) * 1.0001
+
+
+def test_restarted_fgmres_converges():
+    p = synth.two_phase(8, 8, 4)
+    o = oracle.Oracle(p)
+    r = o.fgmres(p.rhs, restart=5, maxit=500, rtol=1e-8)
+    assert r["status"] == 0 and r["relres"] <= 1e-8
