@@ -1,0 +1,201 @@
+/*
+ * mgr_gb300.h -- C ABI of the GB300 (sm_103a) multigrid-reduction solver.
+ *
+ * The library applies the multigrid reduction (MGR) preconditioner of Bui,
+ * Osei-Kuffuor, Castelletto and White ("A Scalable Multigrid Reduction
+ * Framework for Multiphase Poromechanics of Heterogeneous Media") inside a
+ * right-preconditioned flexible GMRES solve (Sec. 4) of the fully implicit
+ * multiphase-poromechanics Jacobian (Eq. "block_linear_system").  Setup and
+ * solve run entirely in CUDA kernels on the device.
+ *
+ * Conventions shared by every entry point
+ *   - Return value: 0 on success, MGR_NOT_CONVERGED (+1) when FGMRES stopped
+ *     at max_iter (x then holds the last iterate and info is filled), and a
+ *     negative MGR_ERR_* code on failure; mgr_error_string() names it.
+ *   - Pointers documented as "device" must point to memory of the current
+ *     CUDA device; "host" pointers to ordinary host memory.
+ *   - All device work is enqueued on `stream` (a cudaStream_t; NULL = the
+ *     legacy default stream).  mgr_setup and fgmres_solve synchronise the
+ *     stream before returning; mgr_apply and mgr_vcycle do not.
+ *   - Ownership: the caller owns the matrix arrays and all vectors.  mgr_setup
+ *     copies what it needs, so the matrix may be freed after it returns, except
+ *     that fgmres_solve reads the matrix passed to it.  A handle owns its
+ *     hierarchy and workspace (device memory from cudaMallocAsync on the setup
+ *     stream) until mgr_destroy.
+ *   - A handle is not thread-safe: do not use one handle from two host threads
+ *     or two streams at once.
+ */
+#ifndef MGR_GB300_H
+#define MGR_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MGR_MAX_LEVELS 8
+
+/* status codes */
+#define MGR_SUCCESS 0
+#define MGR_NOT_CONVERGED 1
+#define MGR_ERR_INVALID_ARG (-1)
+#define MGR_ERR_CUDA (-2)
+#define MGR_ERR_OOM (-3)
+#define MGR_ERR_ZERO_DIAG (-4)   /* zero pivot: D_FF, a smoother block, the coarsest LU */
+#define MGR_ERR_BREAKDOWN (-5)   /* NaN/Inf in the Arnoldi process */
+#define MGR_ERR_TIMEOUT (-6)     /* a bounded device wait expired */
+#define MGR_ERR_COARSE (-7)      /* coarsest AMG level larger than the dense-LU cap */
+
+/* F-relaxation kinds (per MGR level) */
+#define MGR_FRELAX_AMG_VCYCLE 0  /* one AMG V-cycle on A_FF per sweep (Sec. 5.3) */
+#define MGR_FRELAX_JACOBI 1      /* z_F += D_FF^-1 (v - A z)_F per sweep (Sec. 5.3) */
+
+/* preconditioner precision */
+#define MGR_FP64 0
+#define MGR_MIXED 1              /* FP32 hierarchy and MGR/AMG apply; FP64 Krylov */
+
+/*
+ * One square sparse matrix in CSR with per-dof grouping (the 3x3 field-block
+ * system of Eq. "block_linear_system": three displacement dofs per vertex and
+ * saturation/pressure dofs per cell).  All arrays are DEVICE pointers.
+ *   row_ptr  [n+1] int64, row_ptr[0] = 0, row_ptr[n] = nnz
+ *   col_idx  [nnz] int32, strictly ascending within each row (no duplicates)
+ *   val      [nnz] FP64
+ *   dof_label[n]   field of each dof (0 = u, 1 = s, 2 = p); the C/F split of
+ *                  each MGR level is a set of labels (Sec. 5.1: the user
+ *                  chooses the C/F partition)
+ *   dof_node [n]   point (vertex or cell) of each dof; the dofs of one point are
+ *                  consecutive and at most 4 (the interleaved ordering of the
+ *                  Remark in Sec. 5.3), giving the blocks of the global smoother
+ *                  and the "diagonals of the sub-blocks" kept by the dropping
+ *                  operator G (Eq. "drop_operator")
+ *   dof_comp [n]   component within the point (x/y/z or s/p); the AMG of the
+ *                  first F-relaxation couples only equal components (the
+ *                  "unknown approach" of Sec. 6).  May be NULL (all 0).
+ */
+typedef struct {
+  int64_t n;
+  int64_t nnz;
+  const int64_t* row_ptr;
+  const int32_t* col_idx;
+  const double* val;
+  const int32_t* dof_label;
+  const int32_t* dof_node;
+  const int32_t* dof_comp;
+} mgr_matrix_t;
+
+/*
+ * Solver configuration.  mgr_options_default() fills the configuration of
+ * Sec. 5.3 / Sec. 6: two reductions (F = {u}, then F = {s}), N_max = 4 at the
+ * first and no dropping at the second, one AMG V-cycle as the first
+ * F-relaxation, one Jacobi sweep as the second, three cell-block Jacobi sweeps
+ * as the second-level global smoother, AMG (theta 0.25, P_max 4, coarsest
+ * <= 256 rows, <= 25 levels) on the final pressure system.
+ */
+typedef struct {
+  int32_t num_levels;                       /* number of reductions (0..8) */
+  uint32_t f_label_mask[MGR_MAX_LEVELS];    /* bit b set: label b is F at level l */
+  int32_t frelax[MGR_MAX_LEVELS];           /* MGR_FRELAX_* */
+  int32_t frelax_sweeps[MGR_MAX_LEVELS];
+  int32_t nmax_drop[MGR_MAX_LEVELS];        /* N_max of G; < 0: no dropping */
+  int32_t global_sweeps[MGR_MAX_LEVELS];    /* point-block Jacobi sweeps; 0 = none */
+  double amg_theta;                         /* strength threshold */
+  int32_t amg_pmax;                         /* interpolation truncation; 0 = none */
+  int32_t amg_max_coarse;                   /* stop coarsening at <= this many rows */
+  int32_t amg_max_levels;
+  int32_t precision;                        /* MGR_FP64 or MGR_MIXED */
+  uint64_t seed;                            /* PMIS weight hash seed */
+} mgr_options_t;
+
+typedef struct {
+  int32_t restart;   /* Krylov subspace size m (default 50) */
+  int32_t max_iter;  /* total preconditioner applications (default 1000) */
+  double rtol;       /* stop when ||b - A x||_2 <= rtol ||b||_2 (default 1e-8) */
+} fgmres_options_t;
+
+typedef struct {
+  int32_t iters;         /* preconditioner applications performed */
+  int32_t restarts;
+  int32_t converged;     /* 1 if the true relative residual met rtol */
+  double rel_res_true;   /* ||b - A x|| / ||b|| recomputed in FP64 at the end */
+  double setup_s;        /* device time of mgr_setup for this handle */
+  double solve_s;        /* device time of this fgmres_solve */
+  double* res_hist;      /* host array or NULL: estimated relative residual
+                            after each iteration (entry 0 = 1.0) */
+  int32_t res_hist_cap;
+} fgmres_info_t;
+
+typedef struct mgr_handle_s* mgr_handle_t;
+
+/* Fill `o` with the defaults described above; two_phase = 0 gives the
+ * single-reduction u | p configuration. */
+void mgr_options_default(mgr_options_t* o, int two_phase);
+void fgmres_options_default(fgmres_options_t* o);
+
+/*
+ * Build the MGR hierarchy of A (Sec. 5.2-5.3, Eqs. "injective_rp",
+ * "drop_operator", "coarse_grid_flow_sparse", "coarse_grid_pressure") and the
+ * inner AMG hierarchies (Sec. 6) on the device.  On success *out holds a new
+ * handle.  Errors: INVALID_ARG (bad sizes/options, more than 4 dofs per point,
+ * an empty F or C set), ZERO_DIAG, COARSE, OOM, CUDA.
+ */
+int mgr_setup(const mgr_matrix_t* A, const mgr_options_t* o, void* stream, mgr_handle_t* out);
+
+/*
+ * z = M^-1 v: one application of the multilevel MGR preconditioner with
+ * pre-smoothing F-relaxation (Algorithm 2, Eq. "MGR-pre").  v and z are device
+ * FP64 arrays of length n; they must not overlap.  Under MGR_MIXED, v is
+ * rounded to FP32 on entry and z computed in FP32, then widened.
+ */
+int mgr_apply(mgr_handle_t h, const double* v, double* z, void* stream);
+
+/*
+ * Solve A x = b by right-preconditioned flexible GMRES(m) with the handle's
+ * MGR preconditioner (Sec. 4), x0 = 0, FP64 Arnoldi with classical
+ * Gram-Schmidt applied twice, Givens rotations, and the true residual
+ * recomputed in FP64 at every restart.  A must be the matrix the handle was set
+ * up from; b and x are device FP64 arrays of length n.  info (host) may be
+ * NULL.  Returns 0, MGR_NOT_CONVERGED, or an error (BREAKDOWN on NaN/Inf).
+ */
+int fgmres_solve(mgr_handle_t h, const mgr_matrix_t* A, const double* b, double* x,
+                 const fgmres_options_t* o, fgmres_info_t* info, void* stream);
+
+/* Release every device allocation of the handle (synchronises the device). */
+int mgr_destroy(mgr_handle_t h);
+
+const char* mgr_error_string(int code);
+
+/* ---- inspection (parity checks against an independent implementation) ---- */
+
+/* Hierarchy matrices, copied to HOST buffers.  kind:
+ *   0 A_l of MGR level `slot`;   1 W_p of level slot (nF x nC);
+ *   2 A_cor = A_CF D_FF^-1 A_FC before dropping;  3 G(A_cor);
+ *   4 the next-level operator S_{slot+1};
+ *   10 AMG operator, 11 strength pattern, 12 interpolation P, 13 R = P^T of
+ *   AMG slot `slot` (0..L-1: F-relaxation AMG of MGR level slot; L: the AMG
+ *   of the coarsest MGR level), level `lvl`.
+ * dims[0..2] receive rows, cols, nnz; row_ptr/col_idx/val are filled when
+ * non-NULL (sizes n+1, nnz, nnz).  Synchronises the device. */
+int mgr_get_csr(mgr_handle_t h, int kind, int slot, int lvl, int64_t* dims,
+                int64_t* row_ptr, int32_t* col_idx, double* val);
+
+/* Number of AMG levels in slot `slot` (0 if that slot has no AMG). */
+int mgr_amg_levels(mgr_handle_t h, int slot);
+
+/* C/F marks (+1 C, -1 F, int8, HOST buffer of length n or NULL) of AMG slot
+ * `slot`, level `lvl`; returns n, or a negative error. */
+int64_t mgr_get_cf(mgr_handle_t h, int slot, int lvl, int8_t* out);
+
+/* One V-cycle of AMG slot `slot` from a zero guess: x = B b (device FP64
+ * arrays of that AMG's size).  Asynchronous on `stream`. */
+int mgr_vcycle(mgr_handle_t h, int slot, const double* b, double* x, void* stream);
+
+/* Splitmix64 (Steele, Lea, Flood 2014) as evaluated on the device, for tests
+ * of the PMIS weight hash: out[i] = splitmix64(in[i]) for n values (device). */
+int mgr_splitmix64_device(const uint64_t* in, uint64_t* out, int64_t n, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MGR_GB300_H */

@@ -696,8 +696,9 @@ static int mgr_level_setup(oracle_t *h, int l, ocsr *Snext) {
     int64_t nb = 0;
     for (int64_t i = 0; i < n;) {
       int64_t j = i + 1;
-      while (j < n && L->node[j] == L->node[i] && j - i < 4) j++;
-      L->bstart[nb] = i; L->bsize[nb] = (int32_t)(j - i); nb++;
+      while (j < n && L->node[j] == L->node[i]) j++;
+      if (j - i > 4) st = ORC_ERR_ARG;   /* at most 4 dofs per point */
+      L->bstart[nb] = i; L->bsize[nb] = (int32_t)(j - i > 4 ? 4 : j - i); nb++;
       i = j;
     }
     L->nblk = nb;

@@ -1,0 +1,424 @@
+// Device application of the MGR preconditioner (Algorithm 2 of Bui et al.,
+// pre-smoothing F-relaxation, Eq. "MGR-pre") and of the inner AMG V-cycles
+// (Sec. 6), in FP64 or FP32.
+//
+// Every kernel here streams a sparse matrix once and gathers vector entries
+// through the read-only cache; the work is HBM-bound, so the kernels fuse the
+// element-wise smoother / residual / correction arithmetic into the sparse
+// product that produces it instead of running separate vector passes.
+#include <cuda_runtime.h>
+
+#include "mgr_internal.cuh"
+
+namespace mgr {
+
+static constexpr unsigned FULL = 0xffffffffu;
+
+template <class T>
+__device__ __forceinline__ T ldg(const T* p) {
+  return __ldg(p);
+}
+
+// ----------------------------------------------------------------------------
+// CSR sparse products, G lanes per row (G in 2..32), fused epilogues.
+//   MODE_AX     y = A x
+//   MODE_RES    y = b - A x
+//   MODE_SMOOTH y = xin + dinv .* (b - A xin)          (x = xin)
+//   MODE_ADD    y = y + A x
+//   MODE_GRES   y[t] = b[rows[t]] - (A x)[t]           (A has one row per t)
+//   MODE_RROWS  y[t] = b[rows[t]] - (A x)[rows[t]]     (a subset of A's rows)
+// ----------------------------------------------------------------------------
+enum { MODE_AX = 0, MODE_RES = 1, MODE_SMOOTH = 2, MODE_ADD = 3, MODE_GRES = 4, MODE_RROWS = 5 };
+
+template <class T, class X, class Y, int G, int MODE>
+__global__ void __launch_bounds__(256)
+k_spmv(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci, const T* __restrict__ val,
+       int64_t nr, const X* __restrict__ x, Y* __restrict__ y, const Y* __restrict__ b,
+       const T* __restrict__ dinv, const int64_t* __restrict__ rows) {
+  const int64_t gid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+  const int lane = threadIdx.x & (G - 1);
+  const int64_t stride = ((int64_t)gridDim.x * blockDim.x) / G;
+  for (int64_t i = gid / G; i < nr; i += stride) {
+    const int64_t row = (MODE == MODE_RROWS) ? rows[i] : i;
+    const int64_t e0 = rp[row], e1 = rp[row + 1];
+    Y acc = 0;
+    for (int64_t k = e0 + lane; k < e1; k += G)
+      acc += (Y)val[k] * (Y)ldg(x + ci[k]);
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o, G);
+    if (lane == 0) {
+      if (MODE == MODE_AX) y[i] = acc;
+      else if (MODE == MODE_RES) y[i] = b[i] - acc;
+      else if (MODE == MODE_SMOOTH) y[i] = (Y)x[i] + (Y)dinv[i] * (b[i] - acc);
+      else if (MODE == MODE_ADD) y[i] += acc;
+      else if (MODE == MODE_GRES) y[i] = b[rows[i]] - acc;
+      else if (MODE == MODE_RROWS) y[i] = b[row] - acc;
+    }
+  }
+}
+
+static int pick_group(int64_t nnz, int64_t nr) {
+  double avg = nr > 0 ? (double)nnz / (double)nr : 1.0;
+  int g = 2;
+  while (g < 32 && g * 2 <= avg) g *= 2;
+  return g;
+}
+
+template <class T, class X, class Y, int MODE>
+static void spmv_launch(const int64_t* rp, const int32_t* ci, const T* val, int64_t nr, int64_t nnz,
+                        const X* x, Y* y, const Y* b, const T* dinv, const int64_t* rows,
+                        cudaStream_t s) {
+  if (nr <= 0) return;
+  const int G = pick_group(nnz, nr);
+  const int tpb = 256;
+  int64_t threads = nr * G;
+  unsigned grid = (unsigned)std::min<int64_t>((threads + tpb - 1) / tpb, 152LL * 64);
+#define MGR_SPMV_CASE(g)                                                                \
+  case g:                                                                               \
+    k_spmv<T, X, Y, g, MODE><<<grid, tpb, 0, s>>>(rp, ci, val, nr, x, y, b, dinv, rows); \
+    break;
+  switch (G) {
+    MGR_SPMV_CASE(2)
+    MGR_SPMV_CASE(4)
+    MGR_SPMV_CASE(8)
+    MGR_SPMV_CASE(16)
+    MGR_SPMV_CASE(32)
+  }
+#undef MGR_SPMV_CASE
+}
+
+template <class T>
+static inline const T* vals(const Csr& a);
+template <>
+inline const double* vals<double>(const Csr& a) { return a.v; }
+template <>
+inline const float* vals<float>(const Csr& a) { return a.vf; }
+
+template <class T>
+static inline const T* pick(const double* d, const float* f);
+template <>
+inline const double* pick<double>(const double* d, const float*) { return d; }
+template <>
+inline const float* pick<float>(const double*, const float* f) { return f; }
+
+template <class T, int MODE>
+static void spmv(const Csr& A, const T* x, T* y, const T* b, const T* dinv, const int64_t* rows,
+                 cudaStream_t s) {
+  spmv_launch<T, T, T, MODE>(A.rp, A.ci, vals<T>(A), A.nr, A.nnz, x, y, b, dinv, rows, s);
+}
+
+void spmv64(const int64_t* rp, const int32_t* ci, const double* v, int64_t nr, int64_t nnz,
+            const double* x, double* y, cudaStream_t s) {
+  spmv_launch<double, double, double, MODE_AX>(rp, ci, v, nr, nnz, x, y, nullptr, nullptr, nullptr, s);
+}
+
+void spmv64_x32(const int64_t* rp, const int32_t* ci, const double* v, int64_t nr, int64_t nnz,
+                const float* x, double* y, cudaStream_t s) {
+  spmv_launch<double, float, double, MODE_AX>(rp, ci, v, nr, nnz, x, y, nullptr, nullptr, nullptr, s);
+}
+
+void residual64(const int64_t* rp, const int32_t* ci, const double* v, int64_t nr, int64_t nnz,
+                const double* b, const double* x, double* r, cudaStream_t s) {
+  spmv_launch<double, double, double, MODE_RES>(rp, ci, v, nr, nnz, x, r, b, nullptr, nullptr, s);
+}
+
+// ----------------------------------------------------------------------------
+// Vector kernels
+// ----------------------------------------------------------------------------
+template <class T>
+__global__ void k_scale(const T* __restrict__ d, const T* __restrict__ b, T* __restrict__ x, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    x[i] = d[i] * b[i];
+}
+
+template <class T>
+__global__ void k_gather(const T* __restrict__ src, const int64_t* __restrict__ idx, int64_t n,
+                         T* __restrict__ dst) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+    dst[t] = src[idx[t]];
+}
+
+// z[idx[t]] += d[t] * e[t]   (d may be null: plain add)
+template <class T>
+__global__ void k_scatter_add(T* __restrict__ z, const int64_t* __restrict__ idx,
+                              const T* __restrict__ e, const T* __restrict__ d, int64_t n) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+    z[idx[t]] += d ? d[t] * e[t] : e[t];
+}
+
+// x = Ainv b for the dense coarsest inverse: one warp per row.
+template <class T>
+__global__ void k_dense_gemv(const T* __restrict__ a, int64_t n, const T* __restrict__ b, T* __restrict__ x) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32; i < n;
+       i += ((int64_t)gridDim.x * blockDim.x) / 32) {
+    T acc = 0;
+    for (int64_t j = lane; j < n; j += 32) acc += a[i * n + j] * b[j];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
+    if (lane == 0) x[i] = acc;
+  }
+}
+
+template <class A, class B>
+__global__ void k_cast(const A* __restrict__ a, B* __restrict__ b, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = (B)a[i];
+}
+
+// Point-block Jacobi (global smoother, Sec. 5.3 Remarks): one thread per block.
+//   first sweep from zero: z = B^-1 v
+//   later sweeps        : zout = zin + B^-1 (v - A zin)
+template <class T, bool FIRST>
+__global__ void k_block_jacobi(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                               const T* __restrict__ val, const int64_t* __restrict__ bstart,
+                               const T* __restrict__ binv, int64_t nblk, const T* __restrict__ v,
+                               const T* __restrict__ zin, T* __restrict__ zout) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nblk; k += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s0 = bstart[k];
+    const int b = (int)(bstart[k + 1] - s0);
+    T r[4];
+    for (int i = 0; i < b; i++) {
+      T acc = v[s0 + i];
+      if (!FIRST)
+        for (int64_t q = rp[s0 + i]; q < rp[s0 + i + 1]; q++) acc -= val[q] * ldg(zin + ci[q]);
+      r[i] = acc;
+    }
+    const T* M = binv + 16 * k;
+    for (int i = 0; i < b; i++) {
+      T d = 0;
+      for (int j = 0; j < b; j++) d += M[i * 4 + j] * r[j];
+      zout[s0 + i] = FIRST ? d : zin[s0 + i] + d;
+    }
+  }
+}
+
+// Interpolation and correction of Algorithm 2: z_F += W_p e_C, z_C += e_C.
+// With base != null the F part of z is zero except base (= e_F of the
+// F-relaxation) and C is zero, so z is written instead: z_F = base + W_p e_C,
+// z_C = e_C.
+template <class T, int G>
+__global__ void __launch_bounds__(256)
+k_interp_correct(const int64_t* __restrict__ wrp, const int32_t* __restrict__ wci,
+                 const T* __restrict__ wv, const int64_t* __restrict__ Fidx,
+                 const int64_t* __restrict__ Cidx, int64_t nF, int64_t nC,
+                 const T* __restrict__ eC, const T* __restrict__ base, T* __restrict__ z) {
+  const int64_t gid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+  const int lane = threadIdx.x & (G - 1);
+  const int64_t stride = ((int64_t)gridDim.x * blockDim.x) / G;
+  for (int64_t t = gid / G; t < nF + nC; t += stride) {
+    if (t < nF) {
+      T acc = 0;
+      for (int64_t k = wrp[t] + lane; k < wrp[t + 1]; k += G) acc += wv[k] * ldg(eC + wci[k]);
+#pragma unroll
+      for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o, G);
+      if (lane == 0) {
+        const int64_t d = Fidx ? Fidx[t] : t;
+        if (base) z[d] = base[t] + acc;
+        else z[d] += acc;
+      }
+    } else if (lane == 0) {
+      const int64_t c = t - nF;
+      const int64_t d = Cidx ? Cidx[c] : nF + c;
+      if (base) z[d] = eC[c];
+      else z[d] += eC[c];
+    }
+  }
+}
+
+static unsigned vgrid(int64_t n) { return grid_for(n, 256, 152 * 16); }
+
+// ----------------------------------------------------------------------------
+// Workspace
+// ----------------------------------------------------------------------------
+template <class T>
+static int alloc_amg_ws(Pool& P, Amg* g) {
+  if (!g) return MGR_SUCCESS;
+  for (size_t k = 0; k < g->lev.size(); k++) {
+    AmgLevel& L = g->lev[k];
+    int64_t n = L.A.nr;
+    if (k > 0) {
+      L.x = P.get<T>(n);
+      L.b = P.get<T>(n);
+    }
+    L.r = P.get<T>(n);
+    L.t = P.get<T>(n);
+  }
+  return P.err;
+}
+
+template <class T>
+static int alloc_ws(Handle* h) {
+  Pool& P = h->pool;
+  for (auto& L : h->lev) {
+    L.z2 = P.get<T>(L.n);
+    L.rF = P.get<T>(L.nF);
+    L.eF = P.get<T>(L.nF);
+    L.rC = P.get<T>(L.nC);
+    L.eC = P.get<T>(L.nC);
+    MGR_TRY(alloc_amg_ws<T>(P, L.famg));
+  }
+  MGR_TRY(alloc_amg_ws<T>(P, h->camg));
+  return P.err;
+}
+
+int alloc_apply_workspace(Handle* h, cudaStream_t s) {
+  (void)s;
+  if (h->opt.precision == MGR_MIXED) {
+    MGR_TRY(alloc_ws<float>(h));
+    h->vin32 = h->pool.get<float>(h->n);
+    h->zout32 = h->pool.get<float>(h->n);
+    return h->pool.err;
+  }
+  return alloc_ws<double>(h);
+}
+
+// ----------------------------------------------------------------------------
+// AMG V-cycle from a zero guess (one l1-Jacobi sweep down, one up)
+// ----------------------------------------------------------------------------
+template <class T>
+static void vcycle(Amg* g, int k, const T* b, T* x, cudaStream_t s) {
+  AmgLevel& L = g->lev[k];
+  const int64_t n = L.A.nr;
+  if (k == (int)g->lev.size() - 1) {
+    const T* inv = pick<T>(g->inv, g->invf);
+    k_dense_gemv<T><<<grid_for(n * 32, 256), 256, 0, s>>>(inv, n, b, x);
+    return;
+  }
+  AmgLevel& C = g->lev[k + 1];
+  const T* dinv = pick<T>(L.dinv, L.dinvf);
+  T* t = (T*)L.t;
+  T* r = (T*)L.r;
+  k_scale<T><<<vgrid(n), 256, 0, s>>>(dinv, b, t, n);
+  spmv<T, MODE_RES>(L.A, t, r, b, nullptr, nullptr, s);
+  spmv<T, MODE_AX>(L.R, r, (T*)C.b, nullptr, nullptr, nullptr, s);
+  vcycle<T>(g, k + 1, (const T*)C.b, (T*)C.x, s);
+  spmv<T, MODE_ADD>(L.P, (const T*)C.x, t, nullptr, nullptr, nullptr, s);
+  spmv<T, MODE_SMOOTH>(L.A, t, x, b, dinv, nullptr, s);
+}
+
+// ----------------------------------------------------------------------------
+// Algorithm 2 at level l
+// ----------------------------------------------------------------------------
+template <class T>
+static void mgr_level(Handle* h, int l, const T* v, T* z, cudaStream_t s) {
+  if (l == h->L) {
+    vcycle<T>(h->camg, 0, v, z, s);
+    return;
+  }
+  MgrLevel& L = h->lev[l];
+  const int64_t n = L.n, nF = L.nF, nC = L.nC;
+  const T* Av = vals<T>(L.A);
+  const int64_t* Fi = L.F_is_prefix ? nullptr : L.Fidx;
+  const int64_t* Ci = L.F_is_prefix ? nullptr : L.Cidx;
+  bool zero = true;             // z == 0 (not materialised)
+  // global relaxation z = M_glo^-1 v (point-block Jacobi sweeps from zero)
+  if (L.global_sweeps > 0) {
+    const T* binv = pick<T>(L.binv, L.binvf);
+    T* buf[2] = {((L.global_sweeps - 1) % 2 == 0) ? z : (T*)L.z2,
+                 ((L.global_sweeps - 1) % 2 == 0) ? (T*)L.z2 : z};
+    k_block_jacobi<T, true><<<vgrid(L.nblk), 256, 0, s>>>(L.A.rp, L.A.ci, Av, L.bstart, binv,
+                                                          L.nblk, v, nullptr, buf[0]);
+    for (int sw = 1; sw < L.global_sweeps; sw++)
+      k_block_jacobi<T, false><<<vgrid(L.nblk), 256, 0, s>>>(L.A.rp, L.A.ci, Av, L.bstart, binv,
+                                                             L.nblk, v, buf[(sw - 1) % 2],
+                                                             buf[sw % 2]);
+    zero = false;
+  }
+  // F-relaxation z <- z + Q M_FF^-1 Q^T (v - A z)
+  T* rF = (T*)L.rF;
+  T* eF = (T*)L.eF;
+  const T* zF_only = nullptr;   // z = [e_F at F, 0 at C], not materialised
+  for (int sw = 0; sw < L.frelax_sweeps; sw++) {
+    if (zF_only) {
+      cudaMemsetAsync(z, 0, sizeof(T) * n, s);
+      k_scatter_add<T><<<vgrid(nF), 256, 0, s>>>(z, L.Fidx, eF, nullptr, nF);
+      zF_only = nullptr;
+      zero = false;
+    }
+    const T* rhs;
+    if (zero) {
+      if (L.F_is_prefix) {
+        rhs = v;
+      } else {
+        k_gather<T><<<vgrid(nF), 256, 0, s>>>(v, L.Fidx, nF, rF);
+        rhs = rF;
+      }
+    } else {
+      spmv_launch<T, T, T, MODE_RROWS>(L.A.rp, L.A.ci, Av, nF, L.A.nnz * nF / (n > 0 ? n : 1), z,
+                                       rF, v, nullptr, L.Fidx, s);
+      rhs = rF;
+    }
+    if (L.frelax == MGR_FRELAX_AMG_VCYCLE) vcycle<T>(L.famg, 0, rhs, eF, s);
+    else k_scale<T><<<vgrid(nF), 256, 0, s>>>(pick<T>(L.dFinv, L.dFinvf), rhs, eF, nF);
+    if (zero) zF_only = eF;
+    else k_scatter_add<T><<<vgrid(nF), 256, 0, s>>>(z, L.Fidx, eF, nullptr, nF);
+  }
+  // restrict r_C = (v - A z)_C (injection restriction, W_r = 0)
+  T* rC = (T*)L.rC;
+  T* eC = (T*)L.eC;
+  if (zF_only) {
+    // z is zero outside F, so (A z)_C = A_CF z_F
+    spmv_launch<T, T, T, MODE_GRES>(L.Acf.rp, L.Acf.ci, vals<T>(L.Acf), nC, L.Acf.nnz, zF_only,
+                                    rC, v, nullptr, L.Cidx, s);
+  } else if (zero) {
+    k_gather<T><<<vgrid(nC), 256, 0, s>>>(v, L.Cidx, nC, rC);
+    cudaMemsetAsync(z, 0, sizeof(T) * n, s);
+  } else {
+    spmv_launch<T, T, T, MODE_RROWS>(L.A.rp, L.A.ci, Av, nC, L.A.nnz * nC / (n > 0 ? n : 1), z,
+                                     rC, v, nullptr, L.Cidx, s);
+  }
+  // coarse-grid correction by recursion
+  mgr_level<T>(h, l + 1, rC, eC, s);
+  // interpolate e = P~ e_C = [W_p e_C; e_C] and correct
+  const int G = pick_group(L.W.nnz, nF);
+  unsigned grid = (unsigned)std::min<int64_t>(((nF + nC) * G + 255) / 256, 152LL * 64);
+  const T* wv = vals<T>(L.W);
+  switch (G) {
+    case 2: k_interp_correct<T, 2><<<grid, 256, 0, s>>>(L.W.rp, L.W.ci, wv, Fi, Ci, nF, nC, eC, zF_only, z); break;
+    case 4: k_interp_correct<T, 4><<<grid, 256, 0, s>>>(L.W.rp, L.W.ci, wv, Fi, Ci, nF, nC, eC, zF_only, z); break;
+    case 8: k_interp_correct<T, 8><<<grid, 256, 0, s>>>(L.W.rp, L.W.ci, wv, Fi, Ci, nF, nC, eC, zF_only, z); break;
+    case 16: k_interp_correct<T, 16><<<grid, 256, 0, s>>>(L.W.rp, L.W.ci, wv, Fi, Ci, nF, nC, eC, zF_only, z); break;
+    default: k_interp_correct<T, 32><<<grid, 256, 0, s>>>(L.W.rp, L.W.ci, wv, Fi, Ci, nF, nC, eC, zF_only, z); break;
+  }
+}
+
+int apply_mgr(Handle* h, const double* v, double* z, cudaStream_t s) {
+  if (h->opt.precision == MGR_MIXED) {
+    k_cast<double, float><<<vgrid(h->n), 256, 0, s>>>(v, h->vin32, h->n);
+    mgr_level<float>(h, 0, h->vin32, h->zout32, s);
+    k_cast<float, double><<<vgrid(h->n), 256, 0, s>>>(h->zout32, z, h->n);
+  } else {
+    mgr_level<double>(h, 0, v, z, s);
+  }
+  MGR_TRY_CUDA(cudaGetLastError());
+  return MGR_SUCCESS;
+}
+
+int apply_mgr32(Handle* h, const float* v, float* z, cudaStream_t s) {
+  mgr_level<float>(h, 0, v, z, s);
+  MGR_TRY_CUDA(cudaGetLastError());
+  return MGR_SUCCESS;
+}
+
+int apply_mgr_mixed_into(Handle* h, const double* v, float* z, cudaStream_t s) {
+  k_cast<double, float><<<vgrid(h->n), 256, 0, s>>>(v, h->vin32, h->n);
+  mgr_level<float>(h, 0, h->vin32, z, s);
+  MGR_TRY_CUDA(cudaGetLastError());
+  return MGR_SUCCESS;
+}
+
+int apply_vcycle64(Handle* h, Amg* g, const double* b, double* x, cudaStream_t s) {
+  if (h->opt.precision == MGR_MIXED) {
+    int64_t n = g->lev[0].A.nr;
+    k_cast<double, float><<<vgrid(n), 256, 0, s>>>(b, h->vin32, n);
+    vcycle<float>(g, 0, h->vin32, h->zout32, s);
+    k_cast<float, double><<<vgrid(n), 256, 0, s>>>(h->zout32, x, n);
+  } else {
+    vcycle<double>(g, 0, b, x, s);
+  }
+  MGR_TRY_CUDA(cudaGetLastError());
+  return MGR_SUCCESS;
+}
+
+}  // namespace mgr

@@ -1,0 +1,221 @@
+// C ABI of the GB300 MGR library (declared in include/mgr_gb300.h).
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cstring>
+#include <new>
+
+#include "mgr_internal.cuh"
+
+namespace mgr {
+int fgmres_run(Handle* h, const mgr_matrix_t* A, const double* b, double* x,
+               const fgmres_options_t* o, fgmres_info_t* info, cudaStream_t s);
+
+__global__ void k_splitmix(const uint64_t* __restrict__ in, uint64_t* __restrict__ out, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = splitmix64(in[i]);
+}
+
+static void destroy_amg(Amg* g) { delete g; }
+
+static const Csr* find_csr(Handle* h, int kind, int slot, int lvl) {
+  if (kind < 10) {
+    if (slot < 0 || slot >= h->L) return nullptr;
+    MgrLevel& L = h->lev[slot];
+    switch (kind) {
+      case 0: return &L.A;
+      case 1: return &L.W;
+      case 2: return &L.cor;
+      case 3: return &L.corkept;
+      case 4: return (slot + 1 < h->L) ? &h->lev[slot + 1].A : &h->Acoarse;
+    }
+    return nullptr;
+  }
+  Amg* g = (slot == h->L) ? h->camg : (slot >= 0 && slot < h->L ? h->lev[slot].famg : nullptr);
+  if (!g || lvl < 0 || lvl >= (int)g->lev.size()) return nullptr;
+  AmgLevel& A = g->lev[lvl];
+  const bool coarsened = lvl + 1 < (int)g->lev.size();
+  switch (kind) {
+    case 10: return &A.A;
+    case 11: return coarsened ? &A.S : nullptr;
+    case 12: return coarsened ? &A.P : nullptr;
+    case 13: return coarsened ? &A.R : nullptr;
+  }
+  return nullptr;
+}
+
+static Amg* find_amg(Handle* h, int slot) {
+  if (slot == h->L) return h->camg;
+  if (slot >= 0 && slot < h->L) return h->lev[slot].famg;
+  return nullptr;
+}
+
+}  // namespace mgr
+
+using namespace mgr;
+
+extern "C" {
+
+void mgr_options_default(mgr_options_t* o, int two_phase) {
+  std::memset(o, 0, sizeof(*o));
+  o->num_levels = two_phase ? 2 : 1;
+  o->f_label_mask[0] = 1u << 0;
+  o->f_label_mask[1] = 1u << 1;
+  o->frelax[0] = MGR_FRELAX_AMG_VCYCLE;
+  o->frelax[1] = MGR_FRELAX_JACOBI;
+  for (int l = 0; l < MGR_MAX_LEVELS; l++) o->frelax_sweeps[l] = 1;
+  o->nmax_drop[0] = 4;
+  for (int l = 1; l < MGR_MAX_LEVELS; l++) o->nmax_drop[l] = -1;
+  o->global_sweeps[0] = 0;
+  o->global_sweeps[1] = two_phase ? 3 : 0;
+  o->amg_theta = 0.25;
+  o->amg_pmax = 4;
+  o->amg_max_coarse = 256;
+  o->amg_max_levels = 25;
+  o->precision = MGR_FP64;
+  o->seed = 0;
+}
+
+void fgmres_options_default(fgmres_options_t* o) {
+  o->restart = 50;
+  o->max_iter = 1000;
+  o->rtol = 1e-8;
+}
+
+const char* mgr_error_string(int code) {
+  switch (code) {
+    case MGR_SUCCESS: return "success";
+    case MGR_NOT_CONVERGED: return "not converged within max_iter";
+    case MGR_ERR_INVALID_ARG: return "invalid argument";
+    case MGR_ERR_CUDA: return "CUDA error";
+    case MGR_ERR_OOM: return "out of device memory";
+    case MGR_ERR_ZERO_DIAG: return "zero pivot (D_FF, smoother block or coarsest LU)";
+    case MGR_ERR_BREAKDOWN: return "NaN/Inf in the Arnoldi process";
+    case MGR_ERR_TIMEOUT: return "bounded device wait expired";
+    case MGR_ERR_COARSE: return "coarsest AMG level exceeds the dense-LU cap";
+  }
+  return "unknown status";
+}
+
+int mgr_setup(const mgr_matrix_t* A, const mgr_options_t* o, void* stream, mgr_handle_t* out) {
+  if (!A || !o || !out || A->n <= 0 || A->nnz < 0 || !A->row_ptr || !A->col_idx || !A->val ||
+      !A->dof_label || !A->dof_node)
+    return MGR_ERR_INVALID_ARG;
+  if (o->num_levels < 0 || o->num_levels > MGR_MAX_LEVELS || o->amg_max_levels < 1 ||
+      o->amg_pmax < 0 || (o->precision != MGR_FP64 && o->precision != MGR_MIXED))
+    return MGR_ERR_INVALID_ARG;
+  if (A->n > INT32_MAX) return MGR_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  Handle* h = new (std::nothrow) Handle();
+  if (!h) return MGR_ERR_OOM;
+  h->opt = *o;
+  h->L = o->num_levels;
+  h->n = A->n;
+  h->pool.s = s;
+  *out = nullptr;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaEventRecord(e0, s);
+  int rc = MGR_SUCCESS;
+  h->derr = h->pool.get<int>(1);
+  if (!h->derr) rc = h->pool.err;
+  if (!rc && cudaMemsetAsync(h->derr, 0, sizeof(int), s) != cudaSuccess) rc = MGR_ERR_CUDA;
+  if (!rc) rc = build_mgr_hierarchy(h, A, s);
+  if (!rc && o->precision == MGR_MIXED) rc = to_fp32(h, s);
+  if (!rc) rc = alloc_apply_workspace(h, s);
+  cudaEventRecord(e1, s);
+  if (cudaStreamSynchronize(s) != cudaSuccess && !rc) rc = MGR_ERR_CUDA;
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  h->setup_s = ms * 1e-3;
+  if (rc) {
+    mgr_destroy(reinterpret_cast<mgr_handle_t>(h));
+    return rc;
+  }
+  *out = reinterpret_cast<mgr_handle_t>(h);
+  return MGR_SUCCESS;
+}
+
+int mgr_apply(mgr_handle_t hh, const double* v, double* z, void* stream) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (!h || !v || !z) return MGR_ERR_INVALID_ARG;
+  return apply_mgr(h, v, z, (cudaStream_t)stream);
+}
+
+int fgmres_solve(mgr_handle_t hh, const mgr_matrix_t* A, const double* b, double* x,
+                 const fgmres_options_t* o, fgmres_info_t* info, void* stream) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (!h || !A || !b || !x || A->n != h->n) return MGR_ERR_INVALID_ARG;
+  fgmres_options_t d;
+  fgmres_options_default(&d);
+  return fgmres_run(h, A, b, x, o ? o : &d, info, (cudaStream_t)stream);
+}
+
+int mgr_destroy(mgr_handle_t hh) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (!h) return MGR_SUCCESS;
+  cudaDeviceSynchronize();
+  for (auto& L : h->lev) delete L.famg;
+  delete h->camg;
+  h->pool.free_all();
+  if (h->hpinned) cudaFreeHost(h->hpinned);
+  delete h;
+  return MGR_SUCCESS;
+}
+
+int mgr_get_csr(mgr_handle_t hh, int kind, int slot, int lvl, int64_t* dims, int64_t* row_ptr,
+                int32_t* col_idx, double* val) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (!h || !dims) return MGR_ERR_INVALID_ARG;
+  const Csr* a = find_csr(h, kind, slot, lvl);
+  if (!a || !a->rp) return MGR_ERR_INVALID_ARG;
+  MGR_TRY_CUDA(cudaDeviceSynchronize());
+  dims[0] = a->nr;
+  dims[1] = a->nc;
+  dims[2] = a->nnz;
+  if (row_ptr) MGR_TRY_CUDA(cudaMemcpy(row_ptr, a->rp, sizeof(int64_t) * (a->nr + 1), cudaMemcpyDeviceToHost));
+  if (col_idx && a->nnz) MGR_TRY_CUDA(cudaMemcpy(col_idx, a->ci, sizeof(int32_t) * a->nnz, cudaMemcpyDeviceToHost));
+  if (val && a->nnz) MGR_TRY_CUDA(cudaMemcpy(val, a->v, sizeof(double) * a->nnz, cudaMemcpyDeviceToHost));
+  return MGR_SUCCESS;
+}
+
+int mgr_amg_levels(mgr_handle_t hh, int slot) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (!h) return 0;
+  Amg* g = find_amg(h, slot);
+  return g ? (int)g->lev.size() : 0;
+}
+
+int64_t mgr_get_cf(mgr_handle_t hh, int slot, int lvl, int8_t* out) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (!h) return MGR_ERR_INVALID_ARG;
+  Amg* g = find_amg(h, slot);
+  if (!g || lvl < 0 || lvl + 1 >= (int)g->lev.size()) return MGR_ERR_INVALID_ARG;
+  const AmgLevel& L = g->lev[lvl];
+  if (out) {
+    MGR_TRY_CUDA(cudaDeviceSynchronize());
+    MGR_TRY_CUDA(cudaMemcpy(out, L.cf, L.A.nr, cudaMemcpyDeviceToHost));
+  }
+  return L.A.nr;
+}
+
+int mgr_vcycle(mgr_handle_t hh, int slot, const double* b, double* x, void* stream) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (!h || !b || !x) return MGR_ERR_INVALID_ARG;
+  Amg* g = find_amg(h, slot);
+  if (!g) return MGR_ERR_INVALID_ARG;
+  return apply_vcycle64(h, g, b, x, (cudaStream_t)stream);
+}
+
+int mgr_splitmix64_device(const uint64_t* in, uint64_t* out, int64_t n, void* stream) {
+  if (n < 0 || (n > 0 && (!in || !out))) return MGR_ERR_INVALID_ARG;
+  if (n == 0) return MGR_SUCCESS;
+  k_splitmix<<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(in, out, n);
+  MGR_TRY_CUDA(cudaGetLastError());
+  return MGR_SUCCESS;
+}
+
+}  // extern "C"

@@ -1,0 +1,206 @@
+// Internal declarations of the GB300 MGR library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <vector>
+
+#include "../../include/mgr_gb300.h"
+
+namespace mgr {
+
+// ----------------------------------------------------------------------------
+// Errors
+// ----------------------------------------------------------------------------
+struct Status {
+  int code = MGR_SUCCESS;
+};
+
+#define MGR_TRY_CUDA(expr)                                                       \
+  do {                                                                           \
+    cudaError_t _e = (expr);                                                     \
+    if (_e != cudaSuccess) {                                                     \
+      fprintf(stderr, "mgr_gb300: %s failed: %s (%s:%d)\n", #expr,               \
+              cudaGetErrorString(_e), __FILE__, __LINE__);                       \
+      return _e == cudaErrorMemoryAllocation ? MGR_ERR_OOM : MGR_ERR_CUDA;       \
+    }                                                                            \
+  } while (0)
+
+#define MGR_TRY(expr)            \
+  do {                           \
+    int _s = (expr);             \
+    if (_s != MGR_SUCCESS) return _s; \
+  } while (0)
+
+// device-side error word values (first error wins)
+enum DevErr : int { DEV_OK = 0, DEV_ZERO_DIAG = 1, DEV_BAD_ARG = 2, DEV_OVERFLOW = 3 };
+
+// ----------------------------------------------------------------------------
+// Device memory owned by a handle (stream-ordered allocations)
+// ----------------------------------------------------------------------------
+struct Pool {
+  std::vector<void*> ptrs;
+  cudaStream_t s = nullptr;
+  int err = MGR_SUCCESS;
+  template <class T>
+  T* get(size_t n) {
+    void* p = nullptr;
+    size_t bytes = (n ? n : 1) * sizeof(T);
+    cudaError_t e = cudaMallocAsync(&p, bytes, s);
+    if (e != cudaSuccess) {
+      err = (e == cudaErrorMemoryAllocation) ? MGR_ERR_OOM : MGR_ERR_CUDA;
+      (void)cudaGetLastError();
+      return nullptr;
+    }
+    ptrs.push_back(p);
+    return static_cast<T*>(p);
+  }
+  void release(void* p) {
+    for (auto& q : ptrs)
+      if (q == p) {
+        cudaFreeAsync(q, s);
+        q = nullptr;
+      }
+  }
+  void free_all() {
+    for (void* p : ptrs)
+      if (p) cudaFree(p);
+    ptrs.clear();
+  }
+};
+
+// ----------------------------------------------------------------------------
+// Sparse matrix in CSR on the device
+// ----------------------------------------------------------------------------
+struct Csr {
+  int64_t nr = 0, nc = 0, nnz = 0;
+  int64_t* rp = nullptr;
+  int32_t* ci = nullptr;
+  double* v = nullptr;   // FP64 values (setup, FP64 apply)
+  float* vf = nullptr;   // FP32 copy (mixed-precision apply), may be null
+};
+
+// ----------------------------------------------------------------------------
+// Hierarchy
+// ----------------------------------------------------------------------------
+struct AmgLevel {
+  Csr A, S, P, R;
+  int8_t* cf = nullptr;      // +1 C, -1 F (levels that were coarsened)
+  int32_t* comp = nullptr;
+  double* dinv = nullptr;    // 1 / l1-diagonal
+  float* dinvf = nullptr;
+  // apply workspace (value type chosen by the handle precision)
+  void* x = nullptr;
+  void* b = nullptr;
+  void* r = nullptr;
+  void* t = nullptr;
+};
+
+struct Amg {
+  std::vector<AmgLevel> lev;
+  int64_t ncoarse = 0;
+  double* inv = nullptr;     // dense inverse of the coarsest operator (row-major)
+  float* invf = nullptr;
+};
+
+struct MgrLevel {
+  Csr A;                         // A_l
+  int64_t n = 0, nF = 0, nC = 0;
+  int32_t *label = nullptr, *node = nullptr, *comp = nullptr;
+  int64_t *Fidx = nullptr, *Cidx = nullptr;   // ascending dof lists
+  bool F_is_prefix = false;                  // F = [0, nF), C = [nF, n)
+  double* dFinv = nullptr;       // 1 / diag(A_FF)
+  float* dFinvf = nullptr;
+  Csr W;                         // W_p = -D_FF^-1 A_FC (nF x nC)
+  Csr Acf;                       // A_CF (nC x nF)
+  Csr cor, corkept;              // A_cor before / after G (inspection)
+  Amg* famg = nullptr;           // F-relaxation AMG on A_FF
+  int frelax = MGR_FRELAX_AMG_VCYCLE, frelax_sweeps = 1, global_sweeps = 0;
+  int64_t nblk = 0;
+  int64_t* bstart = nullptr;     // block starts (nblk + 1 entries)
+  double* binv = nullptr;        // 16 values per block, row-major b x b
+  float* binvf = nullptr;
+  // apply workspace (precision of the handle), sized n / nF / nC
+  void *z = nullptr, *z2 = nullptr, *r = nullptr, *rF = nullptr, *eF = nullptr,
+       *rC = nullptr, *eC = nullptr;
+};
+
+struct Handle {
+  mgr_options_t opt;
+  int L = 0;
+  int64_t n = 0;
+  std::vector<MgrLevel> lev;     // L levels
+  Csr Acoarse;                   // operator of the coarsest MGR level
+  Amg* camg = nullptr;
+  Pool pool;
+  double setup_s = 0.0;
+  // mixed-precision entry/exit buffers
+  float* vin32 = nullptr;
+  float* zout32 = nullptr;
+  // FGMRES workspace (lazily sized)
+  int64_t kry_n = 0;
+  int kry_m = 0;
+  double* V = nullptr;           // (m+1) x n
+  void* Z = nullptr;             // m x n (FP64, or FP32 under MGR_MIXED)
+  double* w = nullptr;
+  double* r = nullptr;
+  double* part = nullptr;        // partial dot products
+  double* hcol = nullptr;        // device Hessenberg column scratch
+  double* hred = nullptr;
+  double* yv = nullptr;
+  double* hpinned = nullptr;     // pinned host mirror for small readbacks
+  int* derr = nullptr;           // device error word
+};
+
+// ----------------------------------------------------------------------------
+// Setup entry points (setup.cu)
+// ----------------------------------------------------------------------------
+int scan_exclusive(const int64_t* in, int64_t* out, int64_t n, cudaStream_t s, Pool& tmp);
+int build_mgr_hierarchy(Handle* h, const mgr_matrix_t* A, cudaStream_t s);
+int build_amg(Handle* h, const Csr& A, const int32_t* comp, int slot, Amg** out, cudaStream_t s);
+int to_fp32(Handle* h, cudaStream_t s);
+
+// ----------------------------------------------------------------------------
+// Apply entry points (apply.cu)
+// ----------------------------------------------------------------------------
+int alloc_apply_workspace(Handle* h, cudaStream_t s);
+int apply_mgr(Handle* h, const double* v, double* z, cudaStream_t s);
+int apply_mgr32(Handle* h, const float* v, float* z, cudaStream_t s);
+int apply_mgr_mixed_into(Handle* h, const double* v, float* z, cudaStream_t s);
+int apply_vcycle64(Handle* h, Amg* g, const double* b, double* x, cudaStream_t s);
+// generic CSR SpMV (FP64): y = A x
+void spmv64(const int64_t* rp, const int32_t* ci, const double* v, int64_t nr,
+            int64_t nnz, const double* x, double* y, cudaStream_t s);
+void spmv64_x32(const int64_t* rp, const int32_t* ci, const double* v, int64_t nr,
+                int64_t nnz, const float* x, double* y, cudaStream_t s);
+void residual64(const int64_t* rp, const int32_t* ci, const double* v, int64_t nr,
+                int64_t nnz, const double* b, const double* x, double* r, cudaStream_t s);
+
+// ----------------------------------------------------------------------------
+// Small device helpers
+// ----------------------------------------------------------------------------
+__host__ __device__ inline uint64_t splitmix64(uint64_t x) {
+  // SplitMix64 (Steele, Lea, Flood 2014): one step from state x.
+  uint64_t z = x + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+inline unsigned grid_for(int64_t work, int per_block, int cap = 152 * 32) {
+  int64_t g = (work + per_block - 1) / per_block;
+  if (g < 1) g = 1;
+  if (g > cap) g = cap;
+  return (unsigned)g;
+}
+
+template <class T>
+inline int read_back(T* host, const T* dev, cudaStream_t s) {
+  MGR_TRY_CUDA(cudaMemcpyAsync(host, dev, sizeof(T), cudaMemcpyDeviceToHost, s));
+  MGR_TRY_CUDA(cudaStreamSynchronize(s));
+  return MGR_SUCCESS;
+}
+
+}  // namespace mgr

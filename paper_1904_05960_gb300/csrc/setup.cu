@@ -1,0 +1,1325 @@
+// Device setup of the MGR and AMG hierarchies.
+//
+// Compiled with -fmad=false, and every product / sum that feeds a later
+// integer decision (strength, PMIS, truncation, dropping, sparsity patterns) is
+// written with explicit round-to-nearest intrinsics, one rounding per multiply
+// and per add, in ascending inner-index order.  With that rule the integer
+// outputs of the setup (C/F marks, strength graphs, CSR patterns of P, R, RAP,
+// W_p, S_l) are a deterministic function of the input, independent of the
+// thread schedule.
+//
+// Paper map (Bui et al., Sec. 5-6):
+//   C/F split per level from field labels ........ Sec. 5.1, Sec. 5.3
+//   W_p = -D_FF^-1 A_FC, W_r = 0 .................. Eq. "injective_rp"
+//   S = A_CC - G(A_CF D_FF^-1 A_FC) ............... Eq. "drop_operator",
+//                                                   Eqs. "coarse_grid_flow_sparse",
+//                                                   "coarse_grid_pressure"
+//   point-block global smoother blocks ............ Sec. 5.3 Remarks
+//   AMG: unknown-approach strength, PMIS, direct
+//   interpolation, Galerkin RAP, dense coarsest ... Sec. 6 solver settings
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cmath>
+
+#include "mgr_internal.cuh"
+
+namespace mgr {
+
+static constexpr unsigned FULL = 0xffffffffu;
+static constexpr int LU_CAP = 4096;
+
+// ============================================================================
+// Exclusive scan (int64): out[i] = sum_{j<i} in[j] for i <= n (out[n] = total)
+// ============================================================================
+static constexpr int SCAN_TPB = 1024;
+static constexpr int SCAN_TILE = 2 * SCAN_TPB;
+
+__device__ int64_t block_excl_scan(int64_t v, int64_t* total) {
+  __shared__ int64_t wsum[32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nw = blockDim.x >> 5;
+  int64_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int64_t y = __shfl_up_sync(FULL, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) wsum[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    int64_t s = (lane < nw) ? wsum[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int64_t y = __shfl_up_sync(FULL, s, o);
+      if (lane >= o) s += y;
+    }
+    wsum[lane] = s;
+  }
+  __syncthreads();
+  int64_t pre = (wid > 0 ? wsum[wid - 1] : 0) + x - v;
+  *total = wsum[nw - 1];
+  __syncthreads();
+  return pre;
+}
+
+__global__ void k_scan_tile(const int64_t* __restrict__ in, int64_t n, int64_t* __restrict__ out,
+                            int64_t* __restrict__ bsum) {
+  int64_t base = (int64_t)blockIdx.x * SCAN_TILE + 2 * threadIdx.x;
+  int64_t a = (base < n) ? in[base] : 0;
+  int64_t b = (base + 1 < n) ? in[base + 1] : 0;
+  int64_t tot;
+  int64_t pre = block_excl_scan(a + b, &tot);
+  if (base <= n) out[base] = pre;
+  if (base + 1 <= n) out[base + 1] = pre + a;
+  if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
+}
+
+__global__ void k_scan_add(int64_t* __restrict__ out, int64_t n, const int64_t* __restrict__ off) {
+  int64_t base = (int64_t)blockIdx.x * SCAN_TILE + 2 * threadIdx.x;
+  int64_t o = off[blockIdx.x];
+  if (base <= n) out[base] += o;
+  if (base + 1 <= n) out[base + 1] += o;
+}
+
+int scan_exclusive(const int64_t* in, int64_t* out, int64_t n, cudaStream_t s, Pool& tmp) {
+  int64_t m = n + 1;
+  int64_t nb = (m + SCAN_TILE - 1) / SCAN_TILE;
+  int64_t* bsum = tmp.get<int64_t>(nb);
+  if (!bsum) return tmp.err;
+  k_scan_tile<<<(unsigned)nb, SCAN_TPB, 0, s>>>(in, n, out, bsum);
+  if (nb > 1) {
+    int64_t* boff = tmp.get<int64_t>(nb + 1);
+    if (!boff) return tmp.err;
+    MGR_TRY(scan_exclusive(bsum, boff, nb, s, tmp));
+    k_scan_add<<<(unsigned)nb, SCAN_TPB, 0, s>>>(out, n, boff);
+  }
+  MGR_TRY_CUDA(cudaGetLastError());
+  return MGR_SUCCESS;
+}
+
+// scan counts -> row pointer, return total on the host
+static int rowptr_from_counts(const int64_t* cnt, int64_t* rp, int64_t n, int64_t* total,
+                              cudaStream_t s, Pool& tmp) {
+  MGR_TRY(scan_exclusive(cnt, rp, n, s, tmp));
+  return read_back(total, rp + n, s);
+}
+
+__device__ inline void dev_fail(int* err, int code) { atomicCAS(err, DEV_OK, code); }
+
+static int check_dev_err(int* derr, cudaStream_t s) {
+  int e = 0;
+  MGR_TRY(read_back(&e, derr, s));
+  if (e == DEV_ZERO_DIAG) return MGR_ERR_ZERO_DIAG;
+  if (e == DEV_BAD_ARG) return MGR_ERR_INVALID_ARG;
+  if (e != DEV_OK) return MGR_ERR_CUDA;
+  return MGR_SUCCESS;
+}
+
+// ============================================================================
+// Generic CSR kernels
+// ============================================================================
+static inline unsigned nblocks(int64_t n, int tpb) {
+  int64_t g = (n + tpb - 1) / tpb;
+  return (unsigned)(g < 1 ? 1 : g);
+}
+
+// Row subset and column relabelling: out = A[rows, cols] with colmap[j] the new
+// index of column j (monotone in j) or -1.
+__global__ void k_extract_count(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                const int64_t* __restrict__ rows, int64_t nrows,
+                                const int32_t* __restrict__ colmap, int64_t* __restrict__ cnt) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nrows) return;
+  int64_t r = rows ? rows[t] : t;
+  int64_t c = 0;
+  for (int64_t k = rp[r]; k < rp[r + 1]; k++) c += (colmap[ci[k]] >= 0);
+  cnt[t] = c;
+}
+
+__global__ void k_extract_fill(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                               const double* __restrict__ v, const int64_t* __restrict__ rows,
+                               int64_t nrows, const int32_t* __restrict__ colmap,
+                               const int64_t* __restrict__ orp, int32_t* __restrict__ oci,
+                               double* __restrict__ ov) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nrows) return;
+  int64_t r = rows ? rows[t] : t;
+  int64_t o = orp[t];
+  for (int64_t k = rp[r]; k < rp[r + 1]; k++) {
+    int32_t c = colmap[ci[k]];
+    if (c >= 0) {
+      oci[o] = c;
+      ov[o] = v[k];
+      o++;
+    }
+  }
+}
+
+static int csr_alloc(Pool& P, Csr& a, int64_t nr, int64_t nc, int64_t nnz) {
+  a.nr = nr;
+  a.nc = nc;
+  a.nnz = nnz;
+  a.rp = P.get<int64_t>(nr + 1);
+  a.ci = P.get<int32_t>(nnz);
+  a.v = P.get<double>(nnz);
+  return P.err;
+}
+
+static int extract(Pool& P, Pool& tmp, const Csr& A, const int64_t* rows, int64_t nrows,
+                   const int32_t* colmap, int64_t ncols, Csr& out, cudaStream_t s) {
+  int64_t* cnt = tmp.get<int64_t>(nrows + 1);
+  if (!cnt) return tmp.err;
+  out.nr = nrows;
+  out.nc = ncols;
+  out.rp = P.get<int64_t>(nrows + 1);
+  if (!out.rp) return P.err;
+  k_extract_count<<<nblocks(nrows, 256), 256, 0, s>>>(A.rp, A.ci, rows, nrows, colmap, cnt);
+  MGR_TRY(rowptr_from_counts(cnt, out.rp, nrows, &out.nnz, s, tmp));
+  out.ci = P.get<int32_t>(out.nnz);
+  out.v = P.get<double>(out.nnz);
+  if (P.err) return P.err;
+  k_extract_fill<<<nblocks(nrows, 256), 256, 0, s>>>(A.rp, A.ci, A.v, rows, nrows, colmap,
+                                                      out.rp, out.ci, out.v);
+  MGR_TRY_CUDA(cudaGetLastError());
+  return MGR_SUCCESS;
+}
+
+static int copy_csr(Pool& P, const Csr& a, Csr& b, cudaStream_t s) {
+  MGR_TRY(csr_alloc(P, b, a.nr, a.nc, a.nnz));
+  MGR_TRY_CUDA(cudaMemcpyAsync(b.rp, a.rp, sizeof(int64_t) * (a.nr + 1), cudaMemcpyDeviceToDevice, s));
+  MGR_TRY_CUDA(cudaMemcpyAsync(b.ci, a.ci, sizeof(int32_t) * a.nnz, cudaMemcpyDeviceToDevice, s));
+  MGR_TRY_CUDA(cudaMemcpyAsync(b.v, a.v, sizeof(double) * a.nnz, cudaMemcpyDeviceToDevice, s));
+  return MGR_SUCCESS;
+}
+
+// ============================================================================
+// Deterministic sparse matrix product C = A * B
+//   symbolic: one warp per output row; the candidate columns (union of the B
+//   rows selected by the A row) are marked in a shared-memory bitmap window of
+//   SPG_WBITS columns and extracted in ascending order.
+//   numeric : one warp per output row; the A entries are taken one at a time in
+//   ascending order and the lanes add a_ik * b_kj into distinct output slots,
+//   so every entry is summed over ascending k from 0.0 exactly as a sequential
+//   Gustavson product would.
+// ============================================================================
+static constexpr int SPG_WARPS = 8;
+static constexpr int SPG_WORDS = 1024;                 // 32768 columns per window
+static constexpr int64_t SPG_WBITS = 32LL * SPG_WORDS;
+
+template <bool FILL>
+__global__ void __launch_bounds__(SPG_WARPS * 32)
+k_spgemm_symbolic(const int64_t* __restrict__ arp, const int32_t* __restrict__ aci, int64_t nr,
+                  const int64_t* __restrict__ brp, const int32_t* __restrict__ bci,
+                  int64_t* __restrict__ cnt_or_rp, int32_t* __restrict__ cci) {
+  extern __shared__ uint32_t smem[];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint32_t* bm = smem + wid * SPG_WORDS;
+  for (int64_t i = (int64_t)blockIdx.x * SPG_WARPS + wid; i < nr; i += (int64_t)gridDim.x * SPG_WARPS) {
+    const int64_t a0 = arp[i], a1 = arp[i + 1];
+    int32_t lo = INT32_MAX, hi = -1;
+    for (int64_t t = a0 + lane; t < a1; t += 32) {
+      int32_t k = aci[t];
+      int64_t b0 = brp[k], b1 = brp[k + 1];
+      if (b1 > b0) {
+        lo = min(lo, bci[b0]);
+        hi = max(hi, bci[b1 - 1]);
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      lo = min(lo, __shfl_xor_sync(FULL, lo, o));
+      hi = max(hi, __shfl_xor_sync(FULL, hi, o));
+    }
+    int64_t running = 0;
+    const int64_t out0 = FILL ? cnt_or_rp[i] : 0;
+    for (int64_t w0 = lo; hi >= 0 && w0 <= hi; w0 += SPG_WBITS) {
+      for (int q = lane; q < SPG_WORDS; q += 32) bm[q] = 0u;
+      __syncwarp();
+      const int64_t w1 = w0 + SPG_WBITS;
+      for (int64_t t = a0 + lane; t < a1; t += 32) {
+        int32_t k = aci[t];
+        for (int64_t e = brp[k]; e < brp[k + 1]; e++) {
+          int64_t j = bci[e];
+          if (j >= w0 && j < w1) {
+            int64_t off = j - w0;
+            atomicOr(&bm[off >> 5], 1u << (off & 31));
+          }
+        }
+      }
+      __syncwarp();
+      int64_t wend = (hi - w0) / 32 + 1;           // words that can hold bits
+      if (wend > SPG_WORDS) wend = SPG_WORDS;
+      for (int64_t q0 = 0; q0 < wend; q0 += 32) {
+        int64_t q = q0 + lane;
+        uint32_t word = (q < wend) ? bm[q] : 0u;
+        int c = __popc(word);
+        int x = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          int y = __shfl_up_sync(FULL, x, o);
+          if (lane >= o) x += y;
+        }
+        int tot = __shfl_sync(FULL, x, 31);
+        if (FILL) {
+          int64_t pos = out0 + running + (x - c);
+          while (word) {
+            int b = __ffs(word) - 1;
+            word &= word - 1;
+            cci[pos++] = (int32_t)(w0 + 32 * q + b);
+          }
+        }
+        running += tot;
+      }
+      __syncwarp();
+    }
+    if (!FILL && lane == 0) cnt_or_rp[i] = running;
+  }
+}
+
+__device__ inline int64_t lower_bound_i32(const int32_t* a, int64_t n, int32_t key) {
+  int64_t lo = 0, hi = n;
+  while (lo < hi) {
+    int64_t mid = (lo + hi) >> 1;
+    if (a[mid] < key) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(256)
+k_spgemm_numeric(const int64_t* __restrict__ arp, const int32_t* __restrict__ aci,
+                 const double* __restrict__ av, int64_t nr, const int64_t* __restrict__ brp,
+                 const int32_t* __restrict__ bci, const double* __restrict__ bv,
+                 const int64_t* __restrict__ crp, const int32_t* __restrict__ cci,
+                 double* __restrict__ cv) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+  for (int64_t i = (int64_t)blockIdx.x * wpb + wid; i < nr; i += (int64_t)gridDim.x * wpb) {
+    const int64_t c0 = crp[i], m = crp[i + 1] - c0;
+    for (int64_t q = lane; q < m; q += 32) cv[c0 + q] = 0.0;
+    __syncwarp();
+    for (int64_t t = arp[i]; t < arp[i + 1]; t++) {
+      const int32_t k = aci[t];
+      const double a = av[t];
+      for (int64_t e = brp[k] + lane; e < brp[k + 1]; e += 32) {
+        int64_t pos = c0 + lower_bound_i32(cci + c0, m, bci[e]);
+        cv[pos] = __dadd_rn(cv[pos], __dmul_rn(a, bv[e]));
+      }
+      __syncwarp();
+    }
+  }
+}
+
+static int spgemm(Pool& P, Pool& tmp, const Csr& A, const Csr& B, Csr& C, cudaStream_t s) {
+  C.nr = A.nr;
+  C.nc = B.nc;
+  C.rp = P.get<int64_t>(A.nr + 1);
+  int64_t* cnt = tmp.get<int64_t>(A.nr + 1);
+  if (P.err || tmp.err) return P.err ? P.err : tmp.err;
+  const size_t sm = sizeof(uint32_t) * SPG_WORDS * SPG_WARPS;
+  static bool attr = false;
+  if (!attr) {
+    MGR_TRY_CUDA(cudaFuncSetAttribute(k_spgemm_symbolic<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    MGR_TRY_CUDA(cudaFuncSetAttribute(k_spgemm_symbolic<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    attr = true;
+  }
+  unsigned g = grid_for(A.nr, SPG_WARPS, 152 * 16);
+  k_spgemm_symbolic<false><<<g, SPG_WARPS * 32, sm, s>>>(A.rp, A.ci, A.nr, B.rp, B.ci, cnt, nullptr);
+  MGR_TRY(rowptr_from_counts(cnt, C.rp, A.nr, &C.nnz, s, tmp));
+  C.ci = P.get<int32_t>(C.nnz);
+  C.v = P.get<double>(C.nnz);
+  if (P.err) return P.err;
+  k_spgemm_symbolic<true><<<g, SPG_WARPS * 32, sm, s>>>(A.rp, A.ci, A.nr, B.rp, B.ci, C.rp, C.ci);
+  k_spgemm_numeric<<<grid_for(A.nr, 8, 152 * 16), 256, 0, s>>>(A.rp, A.ci, A.v, A.nr, B.rp, B.ci,
+                                                                B.v, C.rp, C.ci, C.v);
+  MGR_TRY_CUDA(cudaGetLastError());
+  return MGR_SUCCESS;
+}
+
+// ============================================================================
+// Transpose with rows ordered by ascending original row index
+// ============================================================================
+__global__ void k_count_cols(const int32_t* __restrict__ ci, int64_t nnz, int64_t* __restrict__ cnt) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nnz; k += (int64_t)gridDim.x * blockDim.x)
+    atomicAdd((unsigned long long*)&cnt[ci[k]], 1ull);
+}
+
+__global__ void k_transpose_fill(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                 const double* __restrict__ v, int64_t nr,
+                                 const int64_t* __restrict__ trp, int64_t* __restrict__ cursor,
+                                 int32_t* __restrict__ tci, double* __restrict__ tv) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nr) return;
+  for (int64_t k = rp[i]; k < rp[i + 1]; k++) {
+    int32_t c = ci[k];
+    int64_t d = trp[c] + (int64_t)atomicAdd((unsigned long long*)&cursor[c], 1ull);
+    tci[d] = (int32_t)i;
+    if (tv) tv[d] = v[k];
+  }
+}
+
+__global__ void k_sort_rows(const int64_t* __restrict__ rp, int64_t nr, int32_t* __restrict__ ci,
+                            double* __restrict__ v) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nr) return;
+  int64_t b = rp[i], e = rp[i + 1];
+  for (int64_t k = b + 1; k < e; k++) {
+    int32_t c = ci[k];
+    double x = v ? v[k] : 0.0;
+    int64_t q = k - 1;
+    while (q >= b && ci[q] > c) {
+      ci[q + 1] = ci[q];
+      if (v) v[q + 1] = v[q];
+      q--;
+    }
+    ci[q + 1] = c;
+    if (v) v[q + 1] = x;
+  }
+}
+
+static int transpose(Pool& P, Pool& tmp, const Csr& A, Csr& T, bool values, bool sorted,
+                     cudaStream_t s) {
+  T.nr = A.nc;
+  T.nc = A.nr;
+  T.nnz = A.nnz;
+  T.rp = P.get<int64_t>(A.nc + 1);
+  T.ci = P.get<int32_t>(A.nnz);
+  T.v = values ? P.get<double>(A.nnz) : nullptr;
+  int64_t* cnt = tmp.get<int64_t>(A.nc + 1);
+  int64_t* cur = tmp.get<int64_t>(A.nc + 1);
+  if (P.err || tmp.err) return P.err ? P.err : tmp.err;
+  MGR_TRY_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int64_t) * (A.nc + 1), s));
+  MGR_TRY_CUDA(cudaMemsetAsync(cur, 0, sizeof(int64_t) * (A.nc + 1), s));
+  k_count_cols<<<grid_for(A.nnz, 256), 256, 0, s>>>(A.ci, A.nnz, cnt);
+  int64_t tot = 0;
+  MGR_TRY(rowptr_from_counts(cnt, T.rp, A.nc, &tot, s, tmp));
+  k_transpose_fill<<<nblocks(A.nr, 256), 256, 0, s>>>(A.rp, A.ci, A.v, A.nr, T.rp, cur, T.ci, T.v);
+  if (sorted) k_sort_rows<<<nblocks(T.nr, 128), 128, 0, s>>>(T.rp, T.nr, T.ci, T.v);
+  MGR_TRY_CUDA(cudaGetLastError());
+  return MGR_SUCCESS;
+}
+
+// ============================================================================
+// MGR reduction level (Sec. 5.1-5.3)
+// ============================================================================
+__global__ void k_flag_f(const int32_t* __restrict__ label, int64_t n, uint32_t mask,
+                         int64_t* __restrict__ flag, int* err) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int32_t l = label[i];
+  if (l < 0 || l > 31) {
+    dev_fail(err, DEV_BAD_ARG);
+    flag[i] = 0;
+    return;
+  }
+  flag[i] = (mask >> l) & 1u;
+}
+
+__global__ void k_split(const int64_t* __restrict__ fpos, int64_t n, int64_t* __restrict__ Fidx,
+                        int64_t* __restrict__ Cidx, int32_t* __restrict__ colF,
+                        int32_t* __restrict__ colC) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int64_t f = fpos[i];
+  if (fpos[i + 1] != f) {
+    Fidx[f] = i;
+    colF[i] = (int32_t)f;
+    colC[i] = -1;
+  } else {
+    int64_t c = i - f;
+    Cidx[c] = i;
+    colC[i] = (int32_t)c;
+    colF[i] = -1;
+  }
+}
+
+// D_FF entries; T = D_FF^-1 A_FC (t = a / d) and W_p = -T on the A_FC pattern.
+__global__ void k_dff_and_w(const int64_t* __restrict__ arp, const int32_t* __restrict__ aci,
+                            const double* __restrict__ av, const int64_t* __restrict__ Fidx,
+                            int64_t nF, const int64_t* __restrict__ frp,
+                            const double* __restrict__ fv, double* __restrict__ tv,
+                            double* __restrict__ wv, double* __restrict__ dinv, int* err) {
+  int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= nF) return;
+  int64_t r = Fidx[f];
+  double d = 0.0;
+  for (int64_t k = arp[r]; k < arp[r + 1]; k++)
+    if (aci[k] == r) d = av[k];
+  if (d == 0.0) {
+    dev_fail(err, DEV_ZERO_DIAG);
+    d = 1.0;
+  }
+  dinv[f] = 1.0 / d;
+  for (int64_t k = frp[f]; k < frp[f + 1]; k++) {
+    double t = __ddiv_rn(fv[k], d);
+    tv[k] = t;
+    wv[k] = -t;
+  }
+}
+
+// G: keep the own-point columns plus the nmax others of largest |value|
+// (ties: smaller column); nmax < 0 keeps everything.
+__global__ void k_drop_mark(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                            const double* __restrict__ v, int64_t nr,
+                            const int32_t* __restrict__ cnode, int nmax,
+                            int8_t* __restrict__ keep, int64_t* __restrict__ cnt) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nr) return;
+  int64_t b = rp[i], e = rp[i + 1];
+  int64_t kept = 0;
+  if (nmax < 0) {
+    for (int64_t k = b; k < e; k++) keep[k] = 1;
+    kept = e - b;
+  } else {
+    int32_t own = cnode[i];
+    for (int64_t k = b; k < e; k++) {
+      int8_t o = (cnode[ci[k]] == own);
+      keep[k] = o;
+      kept += o;
+    }
+    for (int r = 0; r < nmax; r++) {
+      int64_t best = -1;
+      for (int64_t k = b; k < e; k++) {
+        if (keep[k]) continue;
+        if (best < 0 || fabs(v[k]) > fabs(v[best]) ||
+            (fabs(v[k]) == fabs(v[best]) && ci[k] < ci[best]))
+          best = k;
+      }
+      if (best < 0) break;
+      keep[best] = 2;     // selected (not own-point)
+      kept++;
+    }
+  }
+  cnt[i] = kept;
+}
+
+__global__ void k_drop_fill(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                            const double* __restrict__ v, int64_t nr,
+                            const int8_t* __restrict__ keep, const int64_t* __restrict__ krp,
+                            int32_t* __restrict__ kci, double* __restrict__ kv) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nr) return;
+  int64_t o = krp[i];
+  for (int64_t k = rp[i]; k < rp[i + 1]; k++)
+    if (keep[k]) {
+      kci[o] = ci[k];
+      kv[o] = v[k];
+      o++;
+    }
+}
+
+// S = A_CC - K on the union pattern, s = (a or 0) - (k or 0).
+template <bool FILL>
+__global__ void k_union_sub(const int64_t* __restrict__ arp, const int32_t* __restrict__ aci,
+                            const double* __restrict__ av, const int64_t* __restrict__ krp,
+                            const int32_t* __restrict__ kci, const double* __restrict__ kv,
+                            int64_t nr, int64_t* __restrict__ cnt_or_rp,
+                            int32_t* __restrict__ sci, double* __restrict__ sv) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nr) return;
+  int64_t p = arp[i], pe = arp[i + 1], q = krp[i], qe = krp[i + 1];
+  int64_t o = FILL ? cnt_or_rp[i] : 0;
+  while (p < pe || q < qe) {
+    int64_t cp = (p < pe) ? aci[p] : INT64_MAX;
+    int64_t cq = (q < qe) ? kci[q] : INT64_MAX;
+    double a = 0.0, c = 0.0;
+    int64_t col;
+    if (cp == cq) {
+      col = cp;
+      a = av[p++];
+      c = kv[q++];
+    } else if (cp < cq) {
+      col = cp;
+      a = av[p++];
+    } else {
+      col = cq;
+      c = kv[q++];
+    }
+    if (FILL) {
+      sci[o] = (int32_t)col;
+      sv[o] = __dsub_rn(a, c);
+    }
+    o++;
+  }
+  if (!FILL) cnt_or_rp[i] = o;
+}
+
+__global__ void k_gather3(const int32_t* __restrict__ a, const int32_t* __restrict__ b,
+                          const int32_t* __restrict__ c, const int64_t* __restrict__ idx,
+                          int64_t n, int32_t* __restrict__ oa, int32_t* __restrict__ ob,
+                          int32_t* __restrict__ oc) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  int64_t i = idx[t];
+  oa[t] = a[i];
+  ob[t] = b[i];
+  oc[t] = c[i];
+}
+
+// point blocks: maximal runs of equal dof_node (at most 4 dofs)
+__global__ void k_block_heads(const int32_t* __restrict__ node, int64_t n, int64_t* __restrict__ head) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  head[i] = (i == 0 || node[i] != node[i - 1]) ? 1 : 0;
+}
+
+__global__ void k_block_starts(const int64_t* __restrict__ hpos, int64_t n,
+                               int64_t* __restrict__ bstart, int64_t nblk) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i > n) return;
+  if (i == n) {
+    bstart[nblk] = n;
+    return;
+  }
+  if (hpos[i + 1] != hpos[i]) bstart[hpos[i]] = i;
+}
+
+// Inverse of each diagonal point block by Gauss-Jordan with partial pivoting.
+__global__ void k_block_inv(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                            const double* __restrict__ v, const int64_t* __restrict__ bstart,
+                            int64_t nblk, double* __restrict__ binv, int* err) {
+  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nblk) return;
+  int64_t s0 = bstart[k];
+  int b = (int)(bstart[k + 1] - s0);
+  if (b > 4) {
+    dev_fail(err, DEV_BAD_ARG);
+    return;
+  }
+  double m[4][8];
+  for (int i = 0; i < b; i++)
+    for (int j = 0; j < 2 * b; j++) m[i][j] = (j >= b && j - b == i) ? 1.0 : 0.0;
+  for (int i = 0; i < b; i++) {
+    int64_t r = s0 + i;
+    for (int64_t q = rp[r]; q < rp[r + 1]; q++) {
+      int64_t c = ci[q] - s0;
+      if (c >= 0 && c < b) m[i][c] = v[q];
+    }
+  }
+  for (int c = 0; c < b; c++) {
+    int p = c;
+    for (int i = c + 1; i < b; i++)
+      if (fabs(m[i][c]) > fabs(m[p][c])) p = i;
+    if (m[p][c] == 0.0) {
+      dev_fail(err, DEV_ZERO_DIAG);
+      return;
+    }
+    if (p != c)
+      for (int j = 0; j < 2 * b; j++) {
+        double t = m[c][j];
+        m[c][j] = m[p][j];
+        m[p][j] = t;
+      }
+    double piv = m[c][c];
+    for (int j = 0; j < 2 * b; j++) m[c][j] /= piv;
+    for (int i = 0; i < b; i++) {
+      if (i == c) continue;
+      double f = m[i][c];
+      for (int j = 0; j < 2 * b; j++) m[i][j] -= f * m[c][j];
+    }
+  }
+  for (int i = 0; i < 4; i++)
+    for (int j = 0; j < 4; j++) binv[k * 16 + i * 4 + j] = (i < b && j < b) ? m[i][b + j] : 0.0;
+}
+
+// ============================================================================
+// AMG setup (Sec. 6 solver settings)
+// ============================================================================
+// l1-Jacobi diagonal d_i = a_ii + sum_{j != i} |a_ij| (Baker et al. 2011).
+__global__ void k_l1_inv(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                         const double* __restrict__ v, int64_t n, double* __restrict__ dinv, int* err) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double off = 0.0, aii = 0.0;
+  for (int64_t k = rp[i]; k < rp[i + 1]; k++) {
+    if (ci[k] == i) aii = v[k];
+    else off = __dadd_rn(off, fabs(v[k]));
+  }
+  double d = __dadd_rn(aii, off);
+  if (d == 0.0) {
+    dev_fail(err, DEV_ZERO_DIAG);
+    d = 1.0;
+  }
+  dinv[i] = 1.0 / d;
+}
+
+// Strength of connection on negative couplings between equal components.
+template <bool FILL>
+__global__ void k_strength(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                           const double* __restrict__ v, const int32_t* __restrict__ comp,
+                           int64_t n, double theta, int64_t* __restrict__ cnt_or_rp,
+                           int32_t* __restrict__ sci) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int32_t ci_ = comp[i];
+  double m = 0.0;
+  bool any = false;
+  for (int64_t k = rp[i]; k < rp[i + 1]; k++) {
+    int32_t j = ci[k];
+    if (j == i || comp[j] != ci_) continue;
+    double neg = -v[k];
+    if (!any || neg > m) {
+      m = neg;
+      any = true;
+    }
+  }
+  int64_t o = FILL ? cnt_or_rp[i] : 0;
+  if (any && m > 0.0) {
+    double thr = __dmul_rn(theta, m);
+    for (int64_t k = rp[i]; k < rp[i + 1]; k++) {
+      int32_t j = ci[k];
+      if (j == i || comp[j] != ci_) continue;
+      if (-v[k] >= thr) {
+        if (FILL) sci[o] = j;
+        o++;
+      }
+    }
+  }
+  if (!FILL) cnt_or_rp[i] = o;
+}
+
+__global__ void k_pmis_init(const int64_t* __restrict__ srp, const int64_t* __restrict__ strp,
+                            int64_t n, uint64_t seed, int slot, int level, double* __restrict__ w,
+                            int8_t* __restrict__ cf) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  uint64_t key = seed ^ ((uint64_t)slot << 48) ^ ((uint64_t)level << 40) ^ (uint64_t)i;
+  double u = (double)(splitmix64(key) >> 11) * (1.0 / 9007199254740992.0);
+  int64_t nt = strp[i + 1] - strp[i];
+  w[i] = __dadd_rn((double)nt, u);
+  cf[i] = (srp[i + 1] == srp[i] && nt == 0) ? (int8_t)-1 : (int8_t)0;
+}
+
+__global__ void k_pmis_select(const int64_t* __restrict__ srp, const int32_t* __restrict__ sci,
+                              const int64_t* __restrict__ strp, const int32_t* __restrict__ stci,
+                              const double* __restrict__ w, const int8_t* __restrict__ cf,
+                              int64_t n, int8_t* __restrict__ newc) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (cf[i] != 0) {
+    newc[i] = 0;
+    return;
+  }
+  const double wi = w[i];
+  bool best = true;
+  for (int64_t k = srp[i]; k < srp[i + 1] && best; k++) {
+    int32_t j = sci[k];
+    if (cf[j] != 0) continue;
+    double wj = w[j];
+    if (!(wi > wj || (wi == wj && i > j))) best = false;
+  }
+  for (int64_t k = strp[i]; k < strp[i + 1] && best; k++) {
+    int32_t j = stci[k];
+    if (cf[j] != 0) continue;
+    double wj = w[j];
+    if (!(wi > wj || (wi == wj && i > j))) best = false;
+  }
+  newc[i] = best ? 1 : 0;
+}
+
+__global__ void k_pmis_apply_c(const int8_t* __restrict__ newc, int64_t n, int8_t* __restrict__ cf) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && newc[i]) cf[i] = 1;
+}
+
+__global__ void k_pmis_mark_f(const int64_t* __restrict__ srp, const int32_t* __restrict__ sci,
+                              int64_t n, int8_t* __restrict__ cf, unsigned long long* undecided) {
+  int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n || cf[j] != 0) return;
+  for (int64_t k = srp[j]; k < srp[j + 1]; k++)
+    if (cf[sci[k]] == 1) {
+      cf[j] = -1;
+      return;
+    }
+  atomicAdd(undecided, 1ull);
+}
+
+__global__ void k_flag_c(const int8_t* __restrict__ cf, int64_t n, int64_t* __restrict__ flag) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) flag[i] = (cf[i] == 1);
+}
+
+// Direct interpolation restricted to equal components with positive couplings
+// lumped into the diagonal when no positive strong C neighbour exists, then
+// truncation to the pmax entries of largest |w| (ties: smaller column) with the
+// row sum kept.  The weights are recomputed where needed instead of stored, so
+// a thread needs no per-row scratch.
+struct InterpRow {
+  double alpha, beta, dd;
+  int64_t nsc;   // number of strong C neighbours
+};
+
+__device__ inline InterpRow interp_row(const int64_t* rp, const int32_t* ci, const double* v,
+                                       const int64_t* srp, const int32_t* sci,
+                                       const int32_t* comp, const int8_t* cf, int64_t i) {
+  double sn = 0.0, sp = 0.0, cn = 0.0, cp = 0.0, aii = 0.0;
+  int64_t nsc = 0;
+  int64_t sb = srp[i], se = srp[i + 1], sq = sb;
+  for (int64_t k = rp[i]; k < rp[i + 1]; k++) {
+    int32_t j = ci[k];
+    double a = v[k];
+    if (j == i) {
+      aii = a;
+      continue;
+    }
+    while (sq < se && sci[sq] < j) sq++;
+    bool strong = (sq < se && sci[sq] == j);
+    if (comp[j] != comp[i]) continue;
+    bool sc = strong && cf[j] == 1;
+    if (a < 0.0) {
+      sn = __dadd_rn(sn, a);
+      if (sc) cn = __dadd_rn(cn, a);
+    } else if (a > 0.0) {
+      sp = __dadd_rn(sp, a);
+      if (sc) cp = __dadd_rn(cp, a);
+    }
+    if (sc) nsc++;
+  }
+  InterpRow r;
+  r.nsc = (cn != 0.0 || cp != 0.0) ? nsc : 0;
+  r.dd = (cp == 0.0) ? __dadd_rn(aii, sp) : aii;
+  r.alpha = (cn != 0.0) ? __ddiv_rn(sn, cn) : 0.0;
+  r.beta = (cp != 0.0) ? __ddiv_rn(sp, cp) : 0.0;
+  return r;
+}
+
+// Iterates the strong-C entries of row i in ascending column order, calling
+// f(col j, weight w) for each.
+template <class Fn>
+__device__ inline void for_strong_c(const int64_t* rp, const int32_t* ci, const double* v,
+                                    const int64_t* srp, const int32_t* sci, const int8_t* cf,
+                                    int64_t i, const InterpRow& r, Fn f) {
+  int64_t sb = srp[i], se = srp[i + 1], sq = sb;
+  for (int64_t k = rp[i]; k < rp[i + 1]; k++) {
+    int32_t j = ci[k];
+    if (j == i) continue;
+    while (sq < se && sci[sq] < j) sq++;
+    if (!(sq < se && sci[sq] == j) || cf[j] != 1) continue;
+    double a = v[k];
+    double coef = (a < 0.0) ? r.alpha : r.beta;
+    double w = __ddiv_rn(-__dmul_rn(coef, a), r.dd);
+    f(j, w);
+  }
+}
+
+static constexpr int PMAX_CAP = 16;
+
+template <bool FILL>
+__global__ void k_interp(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                         const double* __restrict__ v, const int64_t* __restrict__ srp,
+                         const int32_t* __restrict__ sci, const int32_t* __restrict__ comp,
+                         const int8_t* __restrict__ cf, const int64_t* __restrict__ cmap,
+                         int64_t n, int pmax, int64_t* __restrict__ cnt_or_rp,
+                         int32_t* __restrict__ pci, double* __restrict__ pv) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (cf[i] == 1) {
+    if (FILL) {
+      int64_t o = cnt_or_rp[i];
+      pci[o] = (int32_t)cmap[i];
+      pv[o] = 1.0;
+    } else {
+      cnt_or_rp[i] = 1;
+    }
+    return;
+  }
+  InterpRow r = interp_row(rp, ci, v, srp, sci, comp, cf, i);
+  const bool trunc = pmax > 0 && r.nsc > pmax;
+  if (!FILL) {
+    cnt_or_rp[i] = trunc ? pmax : r.nsc;
+    return;
+  }
+  if (r.nsc == 0) return;
+  int64_t o = cnt_or_rp[i];
+  const int64_t oend = cnt_or_rp[i + 1];
+  if (!trunc) {
+    for_strong_c(rp, ci, v, srp, sci, cf, i, r, [&](int32_t j, double w) {
+      if (o < oend) {
+        pci[o] = (int32_t)cmap[j];
+        pv[o] = w;
+      }
+      o++;
+    });
+    return;
+  }
+  // select pmax largest |w| (ties: smaller column), repeated max search
+  int32_t sel[PMAX_CAP];
+  int ns = 0;
+  for (int q = 0; q < pmax; q++) {
+    int32_t bj = -1;
+    double bw = 0.0;
+    for_strong_c(rp, ci, v, srp, sci, cf, i, r, [&](int32_t j, double w) {
+      for (int t = 0; t < ns; t++)
+        if (sel[t] == j) return;
+      if (bj < 0 || fabs(w) > fabs(bw) || (fabs(w) == fabs(bw) && j < bj)) {
+        bj = j;
+        bw = w;
+      }
+    });
+    if (bj >= 0) sel[ns++] = bj;
+  }
+  double sall = 0.0, skept = 0.0;
+  for_strong_c(rp, ci, v, srp, sci, cf, i, r, [&](int32_t j, double w) {
+    sall = __dadd_rn(sall, w);
+    for (int t = 0; t < ns; t++)
+      if (sel[t] == j) {
+        skept = __dadd_rn(skept, w);
+        break;
+      }
+  });
+  for_strong_c(rp, ci, v, srp, sci, cf, i, r, [&](int32_t j, double w) {
+    for (int t = 0; t < ns; t++)
+      if (sel[t] == j) {
+        if (o < oend) {
+          pci[o] = (int32_t)cmap[j];
+          pv[o] = (skept != 0.0) ? __dmul_rn(w, __ddiv_rn(sall, skept)) : w;
+        }
+        o++;
+        break;
+      }
+  });
+}
+
+__global__ void k_coarse_comp(const int8_t* __restrict__ cf, const int64_t* __restrict__ cmap,
+                              const int32_t* __restrict__ comp, int64_t n, int32_t* __restrict__ cc) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && cf[i] == 1) cc[cmap[i]] = comp[i];
+}
+
+// Coarsest level: dense LU with partial pivoting (ties: smaller row), then the
+// explicit inverse (one column per thread), in a single thread block.
+__global__ void k_csr_to_dense(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                               const double* __restrict__ v, int64_t n, double* __restrict__ d) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  for (int64_t k = rp[i]; k < rp[i + 1]; k++) d[i * n + ci[k]] = v[k];
+}
+
+__global__ void __launch_bounds__(1024) k_dense_lu_inverse(double* __restrict__ a, int n,
+                                                           int32_t* __restrict__ piv,
+                                                           double* __restrict__ inv, int* err) {
+  __shared__ double sval[1024];
+  __shared__ int sidx[1024];
+  __shared__ int fail;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  if (tid == 0) fail = 0;
+  __syncthreads();
+  for (int k = 0; k < n; k++) {
+    double best = -1.0;
+    int bi = n;
+    for (int i = k + tid; i < n; i += nt) {
+      double x = fabs(a[(int64_t)i * n + k]);
+      if (x > best || (x == best && i < bi)) {
+        best = x;
+        bi = i;
+      }
+    }
+    sval[tid] = best;
+    sidx[tid] = bi;
+    __syncthreads();
+    for (int s = nt / 2; s > 0; s >>= 1) {
+      if (tid < s) {
+        double x = sval[tid + s];
+        int xi = sidx[tid + s];
+        if (x > sval[tid] || (x == sval[tid] && xi < sidx[tid])) {
+          sval[tid] = x;
+          sidx[tid] = xi;
+        }
+      }
+      __syncthreads();
+    }
+    int p = sidx[0];
+    if (tid == 0) {
+      piv[k] = p;
+      if (sval[0] == 0.0) fail = 1;
+    }
+    __syncthreads();
+    if (fail) break;
+    if (p != k)
+      for (int j = tid; j < n; j += nt) {
+        double t = a[(int64_t)k * n + j];
+        a[(int64_t)k * n + j] = a[(int64_t)p * n + j];
+        a[(int64_t)p * n + j] = t;
+      }
+    __syncthreads();
+    double akk = a[(int64_t)k * n + k];
+    for (int i = k + 1 + tid; i < n; i += nt) a[(int64_t)i * n + k] /= akk;
+    __syncthreads();
+    int m = n - k - 1;
+    for (int64_t e = tid; e < (int64_t)m * m; e += nt) {
+      int i = k + 1 + (int)(e / m), j = k + 1 + (int)(e % m);
+      a[(int64_t)i * n + j] -= a[(int64_t)i * n + k] * a[(int64_t)k * n + j];
+    }
+    __syncthreads();
+  }
+  if (fail) {
+    if (tid == 0) dev_fail(err, DEV_ZERO_DIAG);
+    return;
+  }
+  for (int c = tid; c < n; c += nt) {
+    // column c of the inverse: x = e_c, permute, L solve, U solve
+    for (int i = 0; i < n; i++) inv[(int64_t)i * n + c] = (i == c) ? 1.0 : 0.0;
+    for (int k = 0; k < n; k++) {
+      int p = piv[k];
+      if (p != k) {
+        double t = inv[(int64_t)k * n + c];
+        inv[(int64_t)k * n + c] = inv[(int64_t)p * n + c];
+        inv[(int64_t)p * n + c] = t;
+      }
+    }
+    for (int i = 0; i < n; i++) {
+      double s = inv[(int64_t)i * n + c];
+      for (int j = 0; j < i; j++) s -= a[(int64_t)i * n + j] * inv[(int64_t)j * n + c];
+      inv[(int64_t)i * n + c] = s;
+    }
+    for (int i = n - 1; i >= 0; i--) {
+      double s = inv[(int64_t)i * n + c];
+      for (int j = i + 1; j < n; j++) s -= a[(int64_t)i * n + j] * inv[(int64_t)j * n + c];
+      inv[(int64_t)i * n + c] = s / a[(int64_t)i * n + i];
+    }
+  }
+}
+
+static int dense_coarsest(Handle* h, Amg* g, Pool& tmp, cudaStream_t s) {
+  Pool& P = h->pool;
+  const Csr& A = g->lev.back().A;
+  int64_t n = A.nr;
+  g->ncoarse = n;
+  if (n == 0) return MGR_SUCCESS;
+  if (n > LU_CAP) return MGR_ERR_COARSE;
+  double* d = tmp.get<double>(n * n);
+  int32_t* piv = tmp.get<int32_t>(n);
+  g->inv = P.get<double>(n * n);
+  if (P.err || tmp.err) return P.err ? P.err : tmp.err;
+  MGR_TRY_CUDA(cudaMemsetAsync(d, 0, sizeof(double) * n * n, s));
+  k_csr_to_dense<<<nblocks(n, 256), 256, 0, s>>>(A.rp, A.ci, A.v, n, d);
+  k_dense_lu_inverse<<<1, 1024, 0, s>>>(d, (int)n, piv, g->inv, h->derr);
+  MGR_TRY_CUDA(cudaGetLastError());
+  return check_dev_err(h->derr, s);
+}
+
+int build_amg(Handle* h, const Csr& A0, const int32_t* comp0, int slot, Amg** out,
+              cudaStream_t s) {
+  Pool& P = h->pool;
+  Pool tmp;
+  tmp.s = s;
+  Amg* g = new Amg();
+  *out = g;
+  const mgr_options_t& o = h->opt;
+  g->lev.emplace_back();
+  {
+    AmgLevel& L0 = g->lev[0];
+    int rc = copy_csr(P, A0, L0.A, s);
+    if (rc) return rc;
+    L0.comp = P.get<int32_t>(A0.nr);
+    if (!L0.comp) return P.err;
+    if (comp0)
+      MGR_TRY_CUDA(cudaMemcpyAsync(L0.comp, comp0, sizeof(int32_t) * A0.nr, cudaMemcpyDeviceToDevice, s));
+    else
+      MGR_TRY_CUDA(cudaMemsetAsync(L0.comp, 0, sizeof(int32_t) * A0.nr, s));
+  }
+  int rc = MGR_SUCCESS;
+  for (int k = 0;; k++) {
+    AmgLevel* L = &g->lev[k];
+    const int64_t n = L->A.nr;
+    L->dinv = P.get<double>(n);
+    if (!L->dinv) { rc = P.err; break; }
+    k_l1_inv<<<nblocks(n, 256), 256, 0, s>>>(L->A.rp, L->A.ci, L->A.v, n, L->dinv, h->derr);
+    if (n <= o.amg_max_coarse || k + 1 >= o.amg_max_levels || k + 1 >= 32) break;
+    // strength graph
+    int64_t* cnt = tmp.get<int64_t>(n + 1);
+    L->S.nr = L->S.nc = n;
+    L->S.rp = P.get<int64_t>(n + 1);
+    if (tmp.err || P.err) { rc = tmp.err ? tmp.err : P.err; break; }
+    k_strength<false><<<nblocks(n, 128), 128, 0, s>>>(L->A.rp, L->A.ci, L->A.v, L->comp, n,
+                                                     o.amg_theta, cnt, nullptr);
+    if ((rc = rowptr_from_counts(cnt, L->S.rp, n, &L->S.nnz, s, tmp))) break;
+    L->S.ci = P.get<int32_t>(L->S.nnz);
+    if (P.err) { rc = P.err; break; }
+    k_strength<true><<<nblocks(n, 128), 128, 0, s>>>(L->A.rp, L->A.ci, L->A.v, L->comp, n,
+                                                    o.amg_theta, L->S.rp, L->S.ci);
+    Csr ST;
+    if ((rc = transpose(tmp, tmp, L->S, ST, false, false, s))) break;
+    // PMIS
+    double* w = tmp.get<double>(n);
+    int8_t* newc = tmp.get<int8_t>(n);
+    L->cf = P.get<int8_t>(n);
+    unsigned long long* und = tmp.get<unsigned long long>(1);
+    if (tmp.err || P.err) { rc = tmp.err ? tmp.err : P.err; break; }
+    k_pmis_init<<<nblocks(n, 256), 256, 0, s>>>(L->S.rp, ST.rp, n, o.seed, slot, k, w, L->cf);
+    for (int round = 0; round < 100000; round++) {
+      k_pmis_select<<<nblocks(n, 256), 256, 0, s>>>(L->S.rp, L->S.ci, ST.rp, ST.ci, w, L->cf, n, newc);
+      k_pmis_apply_c<<<nblocks(n, 256), 256, 0, s>>>(newc, n, L->cf);
+      cudaMemsetAsync(und, 0, sizeof(unsigned long long), s);
+      k_pmis_mark_f<<<nblocks(n, 256), 256, 0, s>>>(L->S.rp, L->S.ci, n, L->cf, und);
+      unsigned long long left = 0;
+      if ((rc = read_back(&left, und, s))) break;
+      if (left == 0) break;
+    }
+    if (rc) break;
+    // coarse numbering
+    int64_t* flag = tmp.get<int64_t>(n + 1);
+    int64_t* cmap = tmp.get<int64_t>(n + 1);
+    if (tmp.err) { rc = tmp.err; break; }
+    k_flag_c<<<nblocks(n, 256), 256, 0, s>>>(L->cf, n, flag);
+    int64_t nc = 0;
+    if ((rc = rowptr_from_counts(flag, cmap, n, &nc, s, tmp))) break;
+    if (nc == 0 || nc == n) break;
+    // interpolation
+    if (o.amg_pmax > PMAX_CAP) { rc = MGR_ERR_INVALID_ARG; break; }
+    L->P.nr = n;
+    L->P.nc = nc;
+    L->P.rp = P.get<int64_t>(n + 1);
+    if (P.err) { rc = P.err; break; }
+    k_interp<false><<<nblocks(n, 128), 128, 0, s>>>(L->A.rp, L->A.ci, L->A.v, L->S.rp, L->S.ci,
+                                                   L->comp, L->cf, cmap, n, o.amg_pmax, cnt,
+                                                   nullptr, nullptr);
+    if ((rc = rowptr_from_counts(cnt, L->P.rp, n, &L->P.nnz, s, tmp))) break;
+    L->P.ci = P.get<int32_t>(L->P.nnz);
+    L->P.v = P.get<double>(L->P.nnz);
+    if (P.err) { rc = P.err; break; }
+    k_interp<true><<<nblocks(n, 128), 128, 0, s>>>(L->A.rp, L->A.ci, L->A.v, L->S.rp, L->S.ci,
+                                                  L->comp, L->cf, cmap, n, o.amg_pmax, L->P.rp,
+                                                  L->P.ci, L->P.v);
+    if ((rc = transpose(P, tmp, L->P, L->R, true, true, s))) break;
+    Csr AP;
+    if ((rc = spgemm(tmp, tmp, L->A, L->P, AP, s))) break;
+    g->lev.emplace_back();
+    L = &g->lev[k];
+    AmgLevel& C = g->lev[k + 1];
+    if ((rc = spgemm(P, tmp, L->R, AP, C.A, s))) break;
+    C.comp = P.get<int32_t>(nc);
+    if (P.err) { rc = P.err; break; }
+    k_coarse_comp<<<nblocks(n, 256), 256, 0, s>>>(L->cf, cmap, L->comp, n, C.comp);
+    MGR_TRY_CUDA(cudaGetLastError());
+  }
+  if (rc == MGR_SUCCESS) rc = check_dev_err(h->derr, s);
+  if (rc == MGR_SUCCESS) rc = dense_coarsest(h, g, tmp, s);
+  cudaStreamSynchronize(s);
+  tmp.free_all();
+  return rc;
+}
+
+// ============================================================================
+// MGR hierarchy
+// ============================================================================
+static int setup_level(Handle* h, int l, const int32_t* label, const int32_t* node,
+                       const int32_t* comp, Pool& tmp, cudaStream_t s, Csr& Snext,
+                       int32_t** nlabel, int32_t** nnode, int32_t** ncomp) {
+  Pool& P = h->pool;
+  MgrLevel& L = h->lev[l];
+  const mgr_options_t& o = h->opt;
+  const int64_t n = L.A.nr;
+  L.n = n;
+  L.label = const_cast<int32_t*>(label);
+  L.node = const_cast<int32_t*>(node);
+  L.comp = const_cast<int32_t*>(comp);
+  L.frelax = o.frelax[l];
+  L.frelax_sweeps = o.frelax_sweeps[l];
+  L.global_sweeps = o.global_sweeps[l];
+  if (L.frelax != MGR_FRELAX_AMG_VCYCLE && L.frelax != MGR_FRELAX_JACOBI) return MGR_ERR_INVALID_ARG;
+  if (L.frelax_sweeps < 0 || L.global_sweeps < 0) return MGR_ERR_INVALID_ARG;
+
+  int64_t* flag = tmp.get<int64_t>(n + 1);
+  int64_t* fpos = tmp.get<int64_t>(n + 1);
+  int32_t* colF = tmp.get<int32_t>(n);
+  int32_t* colC = tmp.get<int32_t>(n);
+  if (tmp.err) return tmp.err;
+  k_flag_f<<<nblocks(n, 256), 256, 0, s>>>(label, n, o.f_label_mask[l], flag, h->derr);
+  MGR_TRY(rowptr_from_counts(flag, fpos, n, &L.nF, s, tmp));
+  MGR_TRY(check_dev_err(h->derr, s));
+  L.nC = n - L.nF;
+  if (L.nF == 0 || L.nC == 0) return MGR_ERR_INVALID_ARG;
+  L.Fidx = P.get<int64_t>(L.nF);
+  L.Cidx = P.get<int64_t>(L.nC);
+  if (P.err) return P.err;
+  k_split<<<nblocks(n, 256), 256, 0, s>>>(fpos, n, L.Fidx, L.Cidx, colF, colC);
+  {
+    int64_t last_f = -1;
+    MGR_TRY(read_back(&last_f, L.Fidx + (L.nF - 1), s));
+    L.F_is_prefix = (last_f == L.nF - 1);
+  }
+  // blocks of A: A_FF (tmp), A_FC (tmp), A_CF, A_CC (tmp)
+  Csr Aff, Afc, Acc;
+  MGR_TRY(extract(tmp, tmp, L.A, L.Fidx, L.nF, colF, L.nF, Aff, s));
+  MGR_TRY(extract(tmp, tmp, L.A, L.Fidx, L.nF, colC, L.nC, Afc, s));
+  MGR_TRY(extract(P, tmp, L.A, L.Cidx, L.nC, colF, L.nF, L.Acf, s));
+  MGR_TRY(extract(tmp, tmp, L.A, L.Cidx, L.nC, colC, L.nC, Acc, s));
+  // D_FF, T = D^-1 A_FC, W_p = -T
+  L.dFinv = P.get<double>(L.nF);
+  L.W = Afc;
+  L.W.rp = P.get<int64_t>(L.nF + 1);
+  L.W.ci = P.get<int32_t>(Afc.nnz);
+  L.W.v = P.get<double>(Afc.nnz);
+  Csr T = Afc;
+  T.v = tmp.get<double>(Afc.nnz);
+  if (P.err || tmp.err) return P.err ? P.err : tmp.err;
+  MGR_TRY_CUDA(cudaMemcpyAsync(L.W.rp, Afc.rp, sizeof(int64_t) * (L.nF + 1), cudaMemcpyDeviceToDevice, s));
+  MGR_TRY_CUDA(cudaMemcpyAsync(L.W.ci, Afc.ci, sizeof(int32_t) * Afc.nnz, cudaMemcpyDeviceToDevice, s));
+  k_dff_and_w<<<nblocks(L.nF, 256), 256, 0, s>>>(L.A.rp, L.A.ci, L.A.v, L.Fidx, L.nF, Afc.rp, Afc.v,
+                                                  T.v, L.W.v, L.dFinv, h->derr);
+  MGR_TRY(check_dev_err(h->derr, s));
+  // A_cor = A_CF T
+  MGR_TRY(spgemm(P, tmp, L.Acf, T, L.cor, s));
+  // next-level labels (needed for G's own-point rule)
+  *nlabel = P.get<int32_t>(L.nC);
+  *nnode = P.get<int32_t>(L.nC);
+  *ncomp = P.get<int32_t>(L.nC);
+  if (P.err) return P.err;
+  k_gather3<<<nblocks(L.nC, 256), 256, 0, s>>>(label, node, comp, L.Cidx, L.nC, *nlabel, *nnode, *ncomp);
+  // G
+  int8_t* keep = tmp.get<int8_t>(L.cor.nnz);
+  int64_t* cnt = tmp.get<int64_t>(L.nC + 1);
+  if (tmp.err) return tmp.err;
+  k_drop_mark<<<nblocks(L.nC, 128), 128, 0, s>>>(L.cor.rp, L.cor.ci, L.cor.v, L.nC, *nnode,
+                                                  o.nmax_drop[l], keep, cnt);
+  L.corkept.nr = L.corkept.nc = L.nC;
+  L.corkept.rp = P.get<int64_t>(L.nC + 1);
+  if (P.err) return P.err;
+  MGR_TRY(rowptr_from_counts(cnt, L.corkept.rp, L.nC, &L.corkept.nnz, s, tmp));
+  L.corkept.ci = P.get<int32_t>(L.corkept.nnz);
+  L.corkept.v = P.get<double>(L.corkept.nnz);
+  if (P.err) return P.err;
+  k_drop_fill<<<nblocks(L.nC, 256), 256, 0, s>>>(L.cor.rp, L.cor.ci, L.cor.v, L.nC, keep,
+                                                  L.corkept.rp, L.corkept.ci, L.corkept.v);
+  // S = A_CC - G(A_cor)
+  Snext.nr = Snext.nc = L.nC;
+  Snext.rp = P.get<int64_t>(L.nC + 1);
+  if (P.err) return P.err;
+  k_union_sub<false><<<nblocks(L.nC, 256), 256, 0, s>>>(Acc.rp, Acc.ci, Acc.v, L.corkept.rp,
+                                                       L.corkept.ci, L.corkept.v, L.nC, cnt,
+                                                       nullptr, nullptr);
+  MGR_TRY(rowptr_from_counts(cnt, Snext.rp, L.nC, &Snext.nnz, s, tmp));
+  Snext.ci = P.get<int32_t>(Snext.nnz);
+  Snext.v = P.get<double>(Snext.nnz);
+  if (P.err) return P.err;
+  k_union_sub<true><<<nblocks(L.nC, 256), 256, 0, s>>>(Acc.rp, Acc.ci, Acc.v, L.corkept.rp,
+                                                      L.corkept.ci, L.corkept.v, L.nC, Snext.rp,
+                                                      Snext.ci, Snext.v);
+  MGR_TRY_CUDA(cudaGetLastError());
+  // F-relaxation AMG on A_FF
+  if (L.frelax == MGR_FRELAX_AMG_VCYCLE && L.frelax_sweeps > 0) {
+    int32_t* fcomp = tmp.get<int32_t>(L.nF);
+    int32_t* dummy1 = tmp.get<int32_t>(L.nF);
+    int32_t* dummy2 = tmp.get<int32_t>(L.nF);
+    if (tmp.err) return tmp.err;
+    k_gather3<<<nblocks(L.nF, 256), 256, 0, s>>>(comp, label, node, L.Fidx, L.nF, fcomp, dummy1, dummy2);
+    MGR_TRY(build_amg(h, Aff, fcomp, l, &L.famg, s));
+  }
+  // point-block global smoother
+  if (L.global_sweeps > 0) {
+    int64_t* head = tmp.get<int64_t>(n + 1);
+    int64_t* hpos = tmp.get<int64_t>(n + 1);
+    if (tmp.err) return tmp.err;
+    k_block_heads<<<nblocks(n, 256), 256, 0, s>>>(node, n, head);
+    MGR_TRY(rowptr_from_counts(head, hpos, n, &L.nblk, s, tmp));
+    L.bstart = P.get<int64_t>(L.nblk + 1);
+    L.binv = P.get<double>(16 * L.nblk);
+    if (P.err) return P.err;
+    k_block_starts<<<nblocks(n + 1, 256), 256, 0, s>>>(hpos, n, L.bstart, L.nblk);
+    k_block_inv<<<nblocks(L.nblk, 128), 128, 0, s>>>(L.A.rp, L.A.ci, L.A.v, L.bstart, L.nblk,
+                                                      L.binv, h->derr);
+    MGR_TRY(check_dev_err(h->derr, s));
+  }
+  return MGR_SUCCESS;
+}
+
+int build_mgr_hierarchy(Handle* h, const mgr_matrix_t* A, cudaStream_t s) {
+  Pool& P = h->pool;
+  const int L = h->L;
+  h->lev.resize(L);
+  const int64_t n = A->n;
+  // own copies of the input
+  Csr A0;
+  A0.nr = A0.nc = n;
+  A0.nnz = A->nnz;
+  A0.rp = const_cast<int64_t*>(A->row_ptr);
+  A0.ci = const_cast<int32_t*>(A->col_idx);
+  A0.v = const_cast<double*>(A->val);
+  int32_t* label = P.get<int32_t>(n);
+  int32_t* node = P.get<int32_t>(n);
+  int32_t* comp = P.get<int32_t>(n);
+  if (P.err) return P.err;
+  MGR_TRY_CUDA(cudaMemcpyAsync(label, A->dof_label, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
+  MGR_TRY_CUDA(cudaMemcpyAsync(node, A->dof_node, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
+  if (A->dof_comp)
+    MGR_TRY_CUDA(cudaMemcpyAsync(comp, A->dof_comp, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
+  else
+    MGR_TRY_CUDA(cudaMemsetAsync(comp, 0, sizeof(int32_t) * n, s));
+  Csr cur;
+  MGR_TRY(copy_csr(P, A0, cur, s));
+  int rc = MGR_SUCCESS;
+  for (int l = 0; l < L && rc == MGR_SUCCESS; l++) {
+    Pool tmp;
+    tmp.s = s;
+    h->lev[l].A = cur;
+    Csr S;
+    int32_t *nl = nullptr, *nn = nullptr, *nc = nullptr;
+    rc = setup_level(h, l, label, node, comp, tmp, s, S, &nl, &nn, &nc);
+    cudaStreamSynchronize(s);
+    tmp.free_all();
+    if (rc) break;
+    cur = S;
+    label = nl;
+    node = nn;
+    comp = nc;
+  }
+  if (rc) return rc;
+  h->Acoarse = cur;
+  // the coarsest MGR level is a scalar problem: one component
+  Pool tmp;
+  tmp.s = s;
+  int32_t* zero = tmp.get<int32_t>(cur.nr);
+  if (!zero) return tmp.err;
+  MGR_TRY_CUDA(cudaMemsetAsync(zero, 0, sizeof(int32_t) * cur.nr, s));
+  rc = build_amg(h, cur, zero, L, &h->camg, s);
+  cudaStreamSynchronize(s);
+  tmp.free_all();
+  return rc;
+}
+
+// ============================================================================
+// FP32 copies of everything the mixed-precision apply reads
+// ============================================================================
+__global__ void k_d2f(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = (float)a[i];
+}
+
+static int f32(Pool& P, const double* a, float** b, int64_t n, cudaStream_t s) {
+  if (!a || n == 0) return MGR_SUCCESS;
+  *b = P.get<float>(n);
+  if (!*b) return P.err;
+  k_d2f<<<grid_for(n, 256), 256, 0, s>>>(a, *b, n);
+  return MGR_SUCCESS;
+}
+
+static int amg_to_fp32(Handle* h, Amg* g, cudaStream_t s) {
+  if (!g) return MGR_SUCCESS;
+  Pool& P = h->pool;
+  for (auto& L : g->lev) {
+    MGR_TRY(f32(P, L.A.v, &L.A.vf, L.A.nnz, s));
+    MGR_TRY(f32(P, L.P.v, &L.P.vf, L.P.nnz, s));
+    MGR_TRY(f32(P, L.R.v, &L.R.vf, L.R.nnz, s));
+    MGR_TRY(f32(P, L.dinv, &L.dinvf, L.A.nr, s));
+  }
+  MGR_TRY(f32(P, g->inv, &g->invf, g->ncoarse * g->ncoarse, s));
+  return MGR_SUCCESS;
+}
+
+int to_fp32(Handle* h, cudaStream_t s) {
+  Pool& P = h->pool;
+  for (auto& L : h->lev) {
+    MGR_TRY(f32(P, L.A.v, &L.A.vf, L.A.nnz, s));
+    MGR_TRY(f32(P, L.W.v, &L.W.vf, L.W.nnz, s));
+    MGR_TRY(f32(P, L.Acf.v, &L.Acf.vf, L.Acf.nnz, s));
+    MGR_TRY(f32(P, L.dFinv, &L.dFinvf, L.nF, s));
+    MGR_TRY(f32(P, L.binv, &L.binvf, 16 * L.nblk, s));
+    MGR_TRY(amg_to_fp32(h, L.famg, s));
+  }
+  MGR_TRY(amg_to_fp32(h, h->camg, s));
+  MGR_TRY_CUDA(cudaGetLastError());
+  return MGR_SUCCESS;
+}
+
+}  // namespace mgr

@@ -1,0 +1,285 @@
+"""Python binding of the GB300 MGR library (include/mgr_gb300.h).
+
+Argument marshalling only: every step of setup, preconditioner application and
+the Krylov solve runs in the CUDA kernels of ``libmgr_gb300.so``.  PyTorch
+provides the device buffers and the stream handle.  There is no fallback: if
+the compiled library is missing, loading it raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+MGR_MAX_LEVELS = 8
+MGR_SUCCESS, MGR_NOT_CONVERGED = 0, 1
+MGR_FRELAX_AMG_VCYCLE, MGR_FRELAX_JACOBI = 0, 1
+MGR_FP64, MGR_MIXED = 0, 1
+
+# hierarchy inspection kinds (mgr_get_csr)
+Q_MGR_A, Q_MGR_W, Q_MGR_COR, Q_MGR_CORKEPT, Q_MGR_S = 0, 1, 2, 3, 4
+Q_AMG_A, Q_AMG_S, Q_AMG_P, Q_AMG_R = 10, 11, 12, 13
+
+EXPORTED = ["mgr_options_default", "fgmres_options_default", "mgr_setup", "mgr_apply",
+            "fgmres_solve", "mgr_destroy", "mgr_error_string", "mgr_get_csr",
+            "mgr_amg_levels", "mgr_get_cf", "mgr_vcycle", "mgr_splitmix64_device"]
+
+
+class MgrMatrix(C.Structure):
+    _fields_ = [("n", C.c_int64), ("nnz", C.c_int64), ("row_ptr", C.c_void_p),
+                ("col_idx", C.c_void_p), ("val", C.c_void_p), ("dof_label", C.c_void_p),
+                ("dof_node", C.c_void_p), ("dof_comp", C.c_void_p)]
+
+
+class MgrOptions(C.Structure):
+    _fields_ = [("num_levels", C.c_int32),
+                ("f_label_mask", C.c_uint32 * MGR_MAX_LEVELS),
+                ("frelax", C.c_int32 * MGR_MAX_LEVELS),
+                ("frelax_sweeps", C.c_int32 * MGR_MAX_LEVELS),
+                ("nmax_drop", C.c_int32 * MGR_MAX_LEVELS),
+                ("global_sweeps", C.c_int32 * MGR_MAX_LEVELS),
+                ("amg_theta", C.c_double), ("amg_pmax", C.c_int32),
+                ("amg_max_coarse", C.c_int32), ("amg_max_levels", C.c_int32),
+                ("precision", C.c_int32), ("seed", C.c_uint64)]
+
+
+class FgmresOptions(C.Structure):
+    _fields_ = [("restart", C.c_int32), ("max_iter", C.c_int32), ("rtol", C.c_double)]
+
+
+class FgmresInfo(C.Structure):
+    _fields_ = [("iters", C.c_int32), ("restarts", C.c_int32), ("converged", C.c_int32),
+                ("rel_res_true", C.c_double), ("setup_s", C.c_double), ("solve_s", C.c_double),
+                ("res_hist", C.c_void_p), ("res_hist_cap", C.c_int32)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib_path():
+    return _build.LIB
+
+
+def lib():
+    """Load libmgr_gb300.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = lib_path()
+            if not os.path.exists(path):
+                raise RuntimeError(
+                    f"{path} is missing: build the CUDA library first "
+                    "(python -m paper_1904_05960_gb300.build); there is no CPU fallback")
+            L = C.CDLL(path)
+            P, I64 = C.c_void_p, C.c_int64
+            L.mgr_options_default.argtypes = [C.POINTER(MgrOptions), C.c_int]
+            L.mgr_options_default.restype = None
+            L.fgmres_options_default.argtypes = [C.POINTER(FgmresOptions)]
+            L.fgmres_options_default.restype = None
+            L.mgr_setup.argtypes = [C.POINTER(MgrMatrix), C.POINTER(MgrOptions), P, C.POINTER(P)]
+            L.mgr_apply.argtypes = [P, P, P, P]
+            L.fgmres_solve.argtypes = [P, C.POINTER(MgrMatrix), P, P, C.POINTER(FgmresOptions),
+                                       C.POINTER(FgmresInfo), P]
+            L.mgr_destroy.argtypes = [P]
+            L.mgr_error_string.argtypes = [C.c_int]
+            L.mgr_error_string.restype = C.c_char_p
+            L.mgr_get_csr.argtypes = [P, C.c_int, C.c_int, C.c_int, P, P, P, P]
+            L.mgr_amg_levels.argtypes = [P, C.c_int]
+            L.mgr_get_cf.argtypes = [P, C.c_int, C.c_int, P]
+            L.mgr_get_cf.restype = I64
+            L.mgr_vcycle.argtypes = [P, C.c_int, P, P, P]
+            L.mgr_splitmix64_device.argtypes = [P, P, I64, P]
+            _lib = L
+    return _lib
+
+
+class MgrError(RuntimeError):
+    def __init__(self, code, what):
+        msg = lib().mgr_error_string(code).decode()
+        super().__init__(f"{what} failed: {msg} ({code})")
+        self.code = code
+
+
+def _check(code, what):
+    if code < 0:
+        raise MgrError(code, what)
+    return code
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+# ---------------------------------------------------------------------------
+def mgr_options_default(two_phase=True, **overrides):
+    """The paper's configuration (Sec. 5.3 / Sec. 6); keyword overrides take
+    lists for the per-level fields."""
+    o = MgrOptions()
+    lib().mgr_options_default(C.byref(o), 1 if two_phase else 0)
+    for k, v in overrides.items():
+        if isinstance(v, (list, tuple)):
+            arr = getattr(o, k)
+            for i, x in enumerate(v):
+                arr[i] = x
+        else:
+            setattr(o, k, v)
+    return o
+
+
+def fgmres_options_default(**overrides):
+    o = FgmresOptions()
+    lib().fgmres_options_default(C.byref(o))
+    for k, v in overrides.items():
+        setattr(o, k, v)
+    return o
+
+
+class DeviceMatrix:
+    """A synth.Problem (or any CSR with labels) copied into device tensors."""
+
+    def __init__(self, prob, device="cuda"):
+        import torch
+        self.n = int(prob.n)
+        self.nnz = int(prob.row_ptr[-1])
+        t = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a, dtype=dt)).to(device)
+        self.row_ptr = t(prob.row_ptr, np.int64)
+        self.col_idx = t(prob.col, np.int32)
+        self.val = t(prob.val, np.float64)
+        self.dof_label = t(prob.dof_label, np.int32)
+        self.dof_node = t(prob.dof_node, np.int32)
+        self.dof_comp = t(prob.dof_comp, np.int32) if prob.dof_comp is not None else None
+        self._s = MgrMatrix(self.n, self.nnz, self.row_ptr.data_ptr(), self.col_idx.data_ptr(),
+                            self.val.data_ptr(), self.dof_label.data_ptr(),
+                            self.dof_node.data_ptr(),
+                            self.dof_comp.data_ptr() if self.dof_comp is not None else None)
+
+    @property
+    def c(self):
+        return self._s
+
+
+def mgr_setup(A: DeviceMatrix, opts: MgrOptions, stream=None):
+    h = C.c_void_p()
+    _check(lib().mgr_setup(C.byref(A.c), C.byref(opts), _stream_ptr(stream), C.byref(h)),
+           "mgr_setup")
+    return h
+
+
+def mgr_apply(h, v, z, stream=None):
+    """z = M^-1 v (device FP64 tensors)."""
+    return _check(lib().mgr_apply(h, _ptr(v), _ptr(z), _stream_ptr(stream)), "mgr_apply")
+
+
+def fgmres_solve(h, A: DeviceMatrix, b, x, opts: FgmresOptions | None = None, stream=None,
+                 hist_cap=0):
+    info = FgmresInfo()
+    hist = np.zeros(max(hist_cap, 1))
+    if hist_cap:
+        info.res_hist = hist.ctypes.data
+        info.res_hist_cap = hist_cap
+    o = opts if opts is not None else fgmres_options_default()
+    st = _check(lib().fgmres_solve(h, C.byref(A.c), _ptr(b), _ptr(x), C.byref(o),
+                                   C.byref(info), _stream_ptr(stream)), "fgmres_solve")
+    return dict(status=st, iters=info.iters, restarts=info.restarts,
+                converged=bool(info.converged), relres=info.rel_res_true,
+                setup_s=info.setup_s, solve_s=info.solve_s,
+                hist=hist[:min(hist_cap, info.iters + 1)] if hist_cap else None)
+
+
+def mgr_destroy(h):
+    if h:
+        lib().mgr_destroy(h)
+
+
+def mgr_get_csr(h, kind, slot=0, lvl=0):
+    """(rows, cols, row_ptr, col, val) of a hierarchy matrix (host numpy), or None."""
+    dims = np.zeros(3, dtype=np.int64)
+    if lib().mgr_get_csr(h, kind, slot, lvl, dims.ctypes.data, None, None, None) != 0:
+        return None
+    nr, nc, nnz = (int(x) for x in dims)
+    rp = np.zeros(nr + 1, dtype=np.int64)
+    ci = np.zeros(max(nnz, 1), dtype=np.int32)
+    v = np.zeros(max(nnz, 1))
+    _check(lib().mgr_get_csr(h, kind, slot, lvl, dims.ctypes.data, rp.ctypes.data,
+                             ci.ctypes.data, v.ctypes.data), "mgr_get_csr")
+    return nr, nc, rp, ci[:nnz], v[:nnz]
+
+
+def mgr_get_scipy(h, kind, slot=0, lvl=0):
+    import scipy.sparse as sp
+    r = mgr_get_csr(h, kind, slot, lvl)
+    if r is None:
+        return None
+    nr, nc, rp, ci, v = r
+    return sp.csr_matrix((v, ci, rp), shape=(nr, nc))
+
+
+def mgr_amg_levels(h, slot):
+    return int(lib().mgr_amg_levels(h, slot))
+
+
+def mgr_get_cf(h, slot, lvl):
+    n = lib().mgr_get_cf(h, slot, lvl, None)
+    if n < 0:
+        return None
+    out = np.zeros(n, dtype=np.int8)
+    lib().mgr_get_cf(h, slot, lvl, out.ctypes.data)
+    return out
+
+
+def mgr_vcycle(h, slot, b, x, stream=None):
+    return _check(lib().mgr_vcycle(h, slot, _ptr(b), _ptr(x), _stream_ptr(stream)), "mgr_vcycle")
+
+
+def mgr_splitmix64_device(inp, out, stream=None):
+    return _check(lib().mgr_splitmix64_device(_ptr(inp), _ptr(out), inp.numel(),
+                                              _stream_ptr(stream)), "mgr_splitmix64_device")
+
+
+class Solver:
+    """Convenience wrapper: device copy of a problem + MGR handle."""
+
+    def __init__(self, prob, precision=MGR_FP64, stream=None, **opt_overrides):
+        two_phase = bool(prob.meta.get("two_phase", True))
+        self.A = DeviceMatrix(prob)
+        self.opts = mgr_options_default(two_phase, precision=precision, **opt_overrides)
+        self.stream = stream
+        self.h = mgr_setup(self.A, self.opts, stream)
+
+    def solve(self, b, restart=50, max_iter=1000, rtol=1e-8, hist_cap=0):
+        import torch
+        x = torch.zeros_like(b)
+        r = fgmres_solve(self.h, self.A, b, x,
+                         fgmres_options_default(restart=restart, max_iter=max_iter, rtol=rtol),
+                         self.stream, hist_cap=hist_cap)
+        r["x"] = x
+        return r
+
+    def apply(self, v):
+        import torch
+        z = torch.empty_like(v)
+        mgr_apply(self.h, v, z, self.stream)
+        return z
+
+    def close(self):
+        if getattr(self, "h", None):
+            mgr_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

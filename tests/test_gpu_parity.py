@@ -1,0 +1,217 @@
+"""Parity of the CUDA path (through the C ABI) against the CPU oracle.
+
+Bars (written here, derived in the design notes):
+  * integer work -- C/F marks, strength graphs, CSR patterns of W_p, A_cor,
+    G(A_cor), S_l, P, R and every Galerkin operator: bit-exact;
+  * FP64 setup values (W_p, A_cor, S_l, P, RAP): <= 1e-12 relative to the
+    largest magnitude of the matrix (both sides use the same rounded
+    operations in the same order, so in practice they are equal);
+  * one FP64 preconditioner application / V-cycle: <= 1e-10 relative (same
+    operator, different summation order inside the sparse products and an
+    explicit coarsest inverse instead of an LU solve);
+  * FGMRES to 1e-8: iteration counts within +-2 and the solution within 1e-6
+    relative of the oracle's.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1904_05960_gb300 import synth
+from tests.helpers import labeled_system
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_1904_05960_gb300 import mgr  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def _same_pattern(a, b, what):
+    assert a.shape == b.shape, f"{what}: shape {a.shape} vs {b.shape}"
+    assert np.array_equal(a.indptr, b.indptr), f"{what}: row pointers differ"
+    assert np.array_equal(a.indices, b.indices), f"{what}: column indices differ"
+
+
+def _close_values(a, b, what, rtol=1e-12):
+    scale = max(np.abs(a.data).max() if a.nnz else 0.0, 1e-300)
+    d = np.abs(a.data - b.data).max() if a.nnz else 0.0
+    assert d <= rtol * scale, f"{what}: max diff {d:.3e} vs scale {scale:.3e}"
+
+
+def compare_hierarchy(o, h, L):
+    for l in range(L):
+        for kind, name in ((mgr.Q_MGR_W, "W_p"), (mgr.Q_MGR_COR, "A_cor"),
+                           (mgr.Q_MGR_CORKEPT, "G(A_cor)"), (mgr.Q_MGR_S, "S")):
+            a = o.scipy(kind, l)
+            b = mgr.mgr_get_scipy(h, kind, l)
+            _same_pattern(a, b, f"level {l} {name}")
+            _close_values(a, b, f"level {l} {name}")
+    for slot in range(L + 1):
+        no = o.amg_levels(slot)
+        assert mgr.mgr_amg_levels(h, slot) == no, f"AMG slot {slot} depth"
+        for k in range(no):
+            a = o.scipy(oracle.Q_AMG_A, slot, k)
+            b = mgr.mgr_get_scipy(h, mgr.Q_AMG_A, slot, k)
+            _same_pattern(a, b, f"AMG {slot}/{k} A")
+            _close_values(a, b, f"AMG {slot}/{k} A")
+            if k + 1 < no:
+                cf_o, cf_g = o.cf(slot, k), mgr.mgr_get_cf(h, slot, k)
+                assert np.array_equal(cf_o, cf_g), f"AMG {slot}/{k} C/F marks"
+                for kind, name in ((mgr.Q_AMG_S, "S"), (mgr.Q_AMG_P, "P"), (mgr.Q_AMG_R, "R")):
+                    a = o.scipy(kind, slot, k)
+                    b = mgr.mgr_get_scipy(h, kind, slot, k)
+                    if name == "S":
+                        a.sort_indices()
+                        b.sort_indices()
+                        _same_pattern(a, b, f"AMG {slot}/{k} strength")
+                    else:
+                        _same_pattern(a, b, f"AMG {slot}/{k} {name}")
+                        _close_values(a, b, f"AMG {slot}/{k} {name}")
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+SMALL = [
+    ("single_phase_8", lambda: synth.config(1)),
+    ("two_phase_10x9x6", lambda: synth.two_phase(10, 9, 6)),
+    ("two_phase_13x11x7_ragged", lambda: synth.two_phase(13, 11, 7, seed=3, sigma=1.5)),
+    ("two_phase_24x20x12", lambda: synth.two_phase(24, 20, 12, seed=5, corr=(6.0, 6.0, 2.0))),
+]
+
+
+@pytest.mark.parametrize("name,make", SMALL, ids=[s[0] for s in SMALL])
+def test_hierarchy_bit_exact_small(name, make):
+    p = make()
+    o = oracle.Oracle(p)
+    s = mgr.Solver(p)
+    compare_hierarchy(o, s.h, o.num_levels)
+    s.close()
+
+
+@pytest.mark.parametrize("name,make", SMALL, ids=[s[0] for s in SMALL])
+def test_apply_and_vcycles_match_oracle(name, make):
+    p = make()
+    o = oracle.Oracle(p)
+    s = mgr.Solver(p)
+    rng = np.random.default_rng(7)
+    v = rng.standard_normal(p.n)
+    z = s.apply(torch.from_numpy(v).cuda()).cpu().numpy()
+    assert _rel(z, o.apply(v)) <= 1e-10
+    for slot in range(o.num_levels + 1):
+        if o.amg_levels(slot) == 0:
+            continue
+        nA = o.scipy(oracle.Q_AMG_A, slot, 0).shape[0]
+        b = rng.standard_normal(nA)
+        x = torch.zeros(nA, dtype=torch.float64, device="cuda")
+        mgr.mgr_vcycle(s.h, slot, torch.from_numpy(b).cuda(), x)
+        torch.cuda.synchronize()
+        assert _rel(x.cpu().numpy(), o.vcycle(slot, b)) <= 1e-10
+    s.close()
+
+
+@pytest.mark.parametrize("name,make", SMALL, ids=[s[0] for s in SMALL])
+def test_fgmres_matches_oracle(name, make):
+    p = make()
+    ref = oracle.Oracle(p).fgmres(p.rhs)
+    s = mgr.Solver(p)
+    r = s.solve(torch.from_numpy(p.rhs).cuda())
+    assert r["converged"] and r["relres"] <= 1e-8
+    assert abs(r["iters"] - ref["iters"]) <= 2, (r["iters"], ref["iters"])
+    assert _rel(r["x"].cpu().numpy(), ref["x"]) <= 1e-6
+    s.close()
+
+
+def test_restart_path_matches_oracle():
+    p = synth.two_phase(8, 8, 4)
+    ref = oracle.Oracle(p).fgmres(p.rhs, restart=5)
+    s = mgr.Solver(p)
+    r = s.solve(torch.from_numpy(p.rhs).cuda(), restart=5)
+    assert r["converged"] and r["restarts"] >= 1
+    assert abs(r["iters"] - ref["iters"]) <= 2
+    assert _rel(r["x"].cpu().numpy(), ref["x"]) <= 1e-6
+    s.close()
+
+
+def test_exact_two_level_identity_on_gpu():
+    """With ideal components the GPU preconditioner is A^-1 (Sec. 5.1)."""
+    p = labeled_system(seed=13, two_phase=False, diag_uu=True, n_nodes=30, n_cells=40)
+    s = mgr.Solver(p, nmax_drop=[-1], amg_max_coarse=1000)
+    A = p.to_scipy()
+    x = np.random.default_rng(0).standard_normal(p.n)
+    z = s.apply(torch.from_numpy(A @ x).cuda()).cpu().numpy()
+    assert _rel(z, x) <= 1e-10
+    s.close()
+
+
+def test_nmax_variants_bit_exact():
+    p = synth.two_phase(9, 8, 5, seed=2)
+    for nmax in (0, 1, 7):
+        o = oracle.Oracle(p, nmax_drop=[nmax, -1])
+        s = mgr.Solver(p, nmax_drop=[nmax, -1])
+        compare_hierarchy(o, s.h, 2)
+        s.close()
+
+
+def test_splitmix64_device_matches_published_vectors():
+    xs = np.array([0, 0x9E3779B97F4A7C15, 0x3C6EF372FE94F82A, 12345], dtype=np.uint64)
+    out = torch.zeros(4, dtype=torch.int64, device="cuda")
+    mgr.mgr_splitmix64_device(torch.from_numpy(xs.view(np.int64)).cuda(), out)
+    got = out.cpu().numpy().view(np.uint64)
+    assert [int(g) for g in got] == [oracle.splitmix64(int(x)) for x in xs]
+    assert int(got[0]) == 0xE220A8397B1DCDAF
+
+
+def test_mixed_precision_solution_within_1e6():
+    p = synth.two_phase(16, 16, 8)
+    ref = oracle.Oracle(p).fgmres(p.rhs)
+    s = mgr.Solver(p, precision=mgr.MGR_MIXED)
+    r = s.solve(torch.from_numpy(p.rhs).cuda())
+    assert r["converged"] and r["relres"] <= 1e-8
+    assert _rel(r["x"].cpu().numpy(), ref["x"]) <= 1e-6
+    s.close()
+
+
+def test_invalid_arguments_are_rejected():
+    p = synth.two_phase(4, 4, 3)
+    A = mgr.DeviceMatrix(p)
+    with pytest.raises(mgr.MgrError) as e:
+        mgr.mgr_setup(A, mgr.mgr_options_default(True, num_levels=9))
+    assert e.value.code == -1
+    with pytest.raises(mgr.MgrError) as e:   # F = every label: empty C set
+        mgr.mgr_setup(A, mgr.mgr_options_default(True, f_label_mask=[0b111, 0b10]))
+    assert e.value.code == -1
+
+
+def test_zero_diagonal_reported():
+    p = synth.two_phase(4, 4, 3)
+    v = p.val.copy()
+    r0, r1 = p.row_ptr[5], p.row_ptr[6]
+    cols = p.col[r0:r1]
+    v[r0 + int(np.nonzero(cols == 5)[0][0])] = 0.0
+    p.val = v
+    with pytest.raises(mgr.MgrError) as e:
+        mgr.Solver(p)
+    assert e.value.code == -4
+
+
+def test_full_size_workload_hierarchy_and_solve():
+    """The 64x64x32 two-phase workload (680,419 unknowns): the whole integer
+    hierarchy bit-exact and the FP64 solve within the bars."""
+    p = synth.config(2)
+    o = oracle.Oracle(p)
+    s = mgr.Solver(p)
+    compare_hierarchy(o, s.h, 2)
+    ref = o.fgmres(p.rhs)
+    r = s.solve(torch.from_numpy(p.rhs).cuda())
+    assert r["converged"] and abs(r["iters"] - ref["iters"]) <= 2
+    assert _rel(r["x"].cpu().numpy(), ref["x"]) <= 1e-6
+    s.close()
