@@ -98,6 +98,7 @@ const char* mgr_error_string(int code) {
 }
 
 int mgr_setup(const mgr_matrix_t* A, const mgr_options_t* o, void* stream, mgr_handle_t* out) {
+  (void)cudaGetLastError();  // errors of earlier calls are not this call's
   if (!A || !o || !out || A->n <= 0 || A->nnz < 0 || !A->row_ptr || !A->col_idx || !A->val ||
       !A->dof_label || !A->dof_node)
     return MGR_ERR_INVALID_ARG;
@@ -140,6 +141,7 @@ int mgr_setup(const mgr_matrix_t* A, const mgr_options_t* o, void* stream, mgr_h
 }
 
 int mgr_apply(mgr_handle_t hh, const double* v, double* z, void* stream) {
+  (void)cudaGetLastError();  // errors of earlier calls are not this call's
   Handle* h = reinterpret_cast<Handle*>(hh);
   if (!h || !v || !z) return MGR_ERR_INVALID_ARG;
   return apply_mgr(h, v, z, (cudaStream_t)stream);
@@ -147,6 +149,7 @@ int mgr_apply(mgr_handle_t hh, const double* v, double* z, void* stream) {
 
 int fgmres_solve(mgr_handle_t hh, const mgr_matrix_t* A, const double* b, double* x,
                  const fgmres_options_t* o, fgmres_info_t* info, void* stream) {
+  (void)cudaGetLastError();  // errors of earlier calls are not this call's
   Handle* h = reinterpret_cast<Handle*>(hh);
   if (!h || !A || !b || !x || A->n != h->n) return MGR_ERR_INVALID_ARG;
   fgmres_options_t d;
@@ -168,6 +171,7 @@ int mgr_destroy(mgr_handle_t hh) {
 
 int mgr_get_csr(mgr_handle_t hh, int kind, int slot, int lvl, int64_t* dims, int64_t* row_ptr,
                 int32_t* col_idx, double* val) {
+  (void)cudaGetLastError();  // errors of earlier calls are not this call's
   Handle* h = reinterpret_cast<Handle*>(hh);
   if (!h || !dims) return MGR_ERR_INVALID_ARG;
   const Csr* a = find_csr(h, kind, slot, lvl);
@@ -178,7 +182,10 @@ int mgr_get_csr(mgr_handle_t hh, int kind, int slot, int lvl, int64_t* dims, int
   dims[2] = a->nnz;
   if (row_ptr) MGR_TRY_CUDA(cudaMemcpy(row_ptr, a->rp, sizeof(int64_t) * (a->nr + 1), cudaMemcpyDeviceToHost));
   if (col_idx && a->nnz) MGR_TRY_CUDA(cudaMemcpy(col_idx, a->ci, sizeof(int32_t) * a->nnz, cudaMemcpyDeviceToHost));
-  if (val && a->nnz) MGR_TRY_CUDA(cudaMemcpy(val, a->v, sizeof(double) * a->nnz, cudaMemcpyDeviceToHost));
+  if (val && a->nnz) {
+    if (a->v) MGR_TRY_CUDA(cudaMemcpy(val, a->v, sizeof(double) * a->nnz, cudaMemcpyDeviceToHost));
+    else for (int64_t k = 0; k < a->nnz; k++) val[k] = 1.0;   // pattern-only matrix
+  }
   return MGR_SUCCESS;
 }
 
@@ -203,6 +210,7 @@ int64_t mgr_get_cf(mgr_handle_t hh, int slot, int lvl, int8_t* out) {
 }
 
 int mgr_vcycle(mgr_handle_t hh, int slot, const double* b, double* x, void* stream) {
+  (void)cudaGetLastError();  // errors of earlier calls are not this call's
   Handle* h = reinterpret_cast<Handle*>(hh);
   if (!h || !b || !x) return MGR_ERR_INVALID_ARG;
   Amg* g = find_amg(h, slot);
@@ -211,6 +219,7 @@ int mgr_vcycle(mgr_handle_t hh, int slot, const double* b, double* x, void* stre
 }
 
 int mgr_splitmix64_device(const uint64_t* in, uint64_t* out, int64_t n, void* stream) {
+  (void)cudaGetLastError();  // errors of earlier calls are not this call's
   if (n < 0 || (n > 0 && (!in || !out))) return MGR_ERR_INVALID_ARG;
   if (n == 0) return MGR_SUCCESS;
   k_splitmix<<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(in, out, n);
