@@ -195,6 +195,10 @@ int mgr_vcycle(mgr_handle_t h, int slot, const double* b, double* x, void* strea
  * of the PMIS weight hash: out[i] = splitmix64(in[i]) for n values (device). */
 int mgr_splitmix64_device(const uint64_t* in, uint64_t* out, int64_t n, void* stream);
 
+/* Number of CUDA kernel launches this library has issued in this process
+ * (all handles, all threads).  Lets a caller count the kernels of a region. */
+int64_t mgr_launch_count(void);
+
 #ifdef __cplusplus
 }
 #endif

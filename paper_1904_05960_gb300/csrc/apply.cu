@@ -75,7 +75,7 @@ static void spmv_launch(const int64_t* rp, const int32_t* ci, const T* val, int6
   unsigned grid = (unsigned)std::min<int64_t>((threads + tpb - 1) / tpb, 152LL * 64);
 #define MGR_SPMV_CASE(g)                                                                \
   case g:                                                                               \
-    k_spmv<T, X, Y, g, MODE><<<grid, tpb, 0, s>>>(rp, ci, val, nr, x, y, b, dinv, rows); \
+    MGR_LAUNCH k_spmv<T, X, Y, g, MODE><<<grid, tpb, 0, s>>>(rp, ci, val, nr, x, y, b, dinv, rows); \
     break;
   switch (G) {
     MGR_SPMV_CASE(2)
@@ -282,14 +282,14 @@ static void vcycle(Amg* g, int k, const T* b, T* x, cudaStream_t s) {
   const int64_t n = L.A.nr;
   if (k == (int)g->lev.size() - 1) {
     const T* inv = pick<T>(g->inv, g->invf);
-    k_dense_gemv<T><<<grid_for(n * 32, 256), 256, 0, s>>>(inv, n, b, x);
+    MGR_LAUNCH k_dense_gemv<T><<<grid_for(n * 32, 256), 256, 0, s>>>(inv, n, b, x);
     return;
   }
   AmgLevel& C = g->lev[k + 1];
   const T* dinv = pick<T>(L.dinv, L.dinvf);
   T* t = (T*)L.t;
   T* r = (T*)L.r;
-  k_scale<T><<<vgrid(n), 256, 0, s>>>(dinv, b, t, n);
+  MGR_LAUNCH k_scale<T><<<vgrid(n), 256, 0, s>>>(dinv, b, t, n);
   spmv<T, MODE_RES>(L.A, t, r, b, nullptr, nullptr, s);
   spmv<T, MODE_AX>(L.R, r, (T*)C.b, nullptr, nullptr, nullptr, s);
   vcycle<T>(g, k + 1, (const T*)C.b, (T*)C.x, s);
@@ -317,10 +317,10 @@ static void mgr_level(Handle* h, int l, const T* v, T* z, cudaStream_t s) {
     const T* binv = pick<T>(L.binv, L.binvf);
     T* buf[2] = {((L.global_sweeps - 1) % 2 == 0) ? z : (T*)L.z2,
                  ((L.global_sweeps - 1) % 2 == 0) ? (T*)L.z2 : z};
-    k_block_jacobi<T, true><<<vgrid(L.nblk), 256, 0, s>>>(L.A.rp, L.A.ci, Av, L.bstart, binv,
+    MGR_LAUNCH k_block_jacobi<T, true><<<vgrid(L.nblk), 256, 0, s>>>(L.A.rp, L.A.ci, Av, L.bstart, binv,
                                                           L.nblk, v, nullptr, buf[0]);
     for (int sw = 1; sw < L.global_sweeps; sw++)
-      k_block_jacobi<T, false><<<vgrid(L.nblk), 256, 0, s>>>(L.A.rp, L.A.ci, Av, L.bstart, binv,
+      MGR_LAUNCH k_block_jacobi<T, false><<<vgrid(L.nblk), 256, 0, s>>>(L.A.rp, L.A.ci, Av, L.bstart, binv,
                                                              L.nblk, v, buf[(sw - 1) % 2],
                                                              buf[sw % 2]);
     zero = false;
@@ -332,7 +332,7 @@ static void mgr_level(Handle* h, int l, const T* v, T* z, cudaStream_t s) {
   for (int sw = 0; sw < L.frelax_sweeps; sw++) {
     if (zF_only) {
       cudaMemsetAsync(z, 0, sizeof(T) * n, s);
-      k_scatter_add<T><<<vgrid(nF), 256, 0, s>>>(z, L.Fidx, eF, nullptr, nF);
+      MGR_LAUNCH k_scatter_add<T><<<vgrid(nF), 256, 0, s>>>(z, L.Fidx, eF, nullptr, nF);
       zF_only = nullptr;
       zero = false;
     }
@@ -341,7 +341,7 @@ static void mgr_level(Handle* h, int l, const T* v, T* z, cudaStream_t s) {
       if (L.F_is_prefix) {
         rhs = v;
       } else {
-        k_gather<T><<<vgrid(nF), 256, 0, s>>>(v, L.Fidx, nF, rF);
+        MGR_LAUNCH k_gather<T><<<vgrid(nF), 256, 0, s>>>(v, L.Fidx, nF, rF);
         rhs = rF;
       }
     } else {
@@ -350,9 +350,9 @@ static void mgr_level(Handle* h, int l, const T* v, T* z, cudaStream_t s) {
       rhs = rF;
     }
     if (L.frelax == MGR_FRELAX_AMG_VCYCLE) vcycle<T>(L.famg, 0, rhs, eF, s);
-    else k_scale<T><<<vgrid(nF), 256, 0, s>>>(pick<T>(L.dFinv, L.dFinvf), rhs, eF, nF);
+    else MGR_LAUNCH k_scale<T><<<vgrid(nF), 256, 0, s>>>(pick<T>(L.dFinv, L.dFinvf), rhs, eF, nF);
     if (zero) zF_only = eF;
-    else k_scatter_add<T><<<vgrid(nF), 256, 0, s>>>(z, L.Fidx, eF, nullptr, nF);
+    else MGR_LAUNCH k_scatter_add<T><<<vgrid(nF), 256, 0, s>>>(z, L.Fidx, eF, nullptr, nF);
   }
   // restrict r_C = (v - A z)_C (injection restriction, W_r = 0)
   T* rC = (T*)L.rC;
@@ -362,7 +362,7 @@ static void mgr_level(Handle* h, int l, const T* v, T* z, cudaStream_t s) {
     spmv_launch<T, T, T, MODE_GRES>(L.Acf.rp, L.Acf.ci, vals<T>(L.Acf), nC, L.Acf.nnz, zF_only,
                                     rC, v, nullptr, L.Cidx, s);
   } else if (zero) {
-    k_gather<T><<<vgrid(nC), 256, 0, s>>>(v, L.Cidx, nC, rC);
+    MGR_LAUNCH k_gather<T><<<vgrid(nC), 256, 0, s>>>(v, L.Cidx, nC, rC);
     cudaMemsetAsync(z, 0, sizeof(T) * n, s);
   } else {
     spmv_launch<T, T, T, MODE_RROWS>(L.A.rp, L.A.ci, Av, nC, L.A.nnz * nC / (n > 0 ? n : 1), z,
@@ -375,19 +375,19 @@ static void mgr_level(Handle* h, int l, const T* v, T* z, cudaStream_t s) {
   unsigned grid = (unsigned)std::min<int64_t>(((nF + nC) * G + 255) / 256, 152LL * 64);
   const T* wv = vals<T>(L.W);
   switch (G) {
-    case 2: k_interp_correct<T, 2><<<grid, 256, 0, s>>>(L.W.rp, L.W.ci, wv, Fi, Ci, nF, nC, eC, zF_only, z); break;
-    case 4: k_interp_correct<T, 4><<<grid, 256, 0, s>>>(L.W.rp, L.W.ci, wv, Fi, Ci, nF, nC, eC, zF_only, z); break;
-    case 8: k_interp_correct<T, 8><<<grid, 256, 0, s>>>(L.W.rp, L.W.ci, wv, Fi, Ci, nF, nC, eC, zF_only, z); break;
-    case 16: k_interp_correct<T, 16><<<grid, 256, 0, s>>>(L.W.rp, L.W.ci, wv, Fi, Ci, nF, nC, eC, zF_only, z); break;
-    default: k_interp_correct<T, 32><<<grid, 256, 0, s>>>(L.W.rp, L.W.ci, wv, Fi, Ci, nF, nC, eC, zF_only, z); break;
+    case 2: MGR_LAUNCH k_interp_correct<T, 2><<<grid, 256, 0, s>>>(L.W.rp, L.W.ci, wv, Fi, Ci, nF, nC, eC, zF_only, z); break;
+    case 4: MGR_LAUNCH k_interp_correct<T, 4><<<grid, 256, 0, s>>>(L.W.rp, L.W.ci, wv, Fi, Ci, nF, nC, eC, zF_only, z); break;
+    case 8: MGR_LAUNCH k_interp_correct<T, 8><<<grid, 256, 0, s>>>(L.W.rp, L.W.ci, wv, Fi, Ci, nF, nC, eC, zF_only, z); break;
+    case 16: MGR_LAUNCH k_interp_correct<T, 16><<<grid, 256, 0, s>>>(L.W.rp, L.W.ci, wv, Fi, Ci, nF, nC, eC, zF_only, z); break;
+    default: MGR_LAUNCH k_interp_correct<T, 32><<<grid, 256, 0, s>>>(L.W.rp, L.W.ci, wv, Fi, Ci, nF, nC, eC, zF_only, z); break;
   }
 }
 
 int apply_mgr(Handle* h, const double* v, double* z, cudaStream_t s) {
   if (h->opt.precision == MGR_MIXED) {
-    k_cast<double, float><<<vgrid(h->n), 256, 0, s>>>(v, h->vin32, h->n);
+    MGR_LAUNCH k_cast<double, float><<<vgrid(h->n), 256, 0, s>>>(v, h->vin32, h->n);
     mgr_level<float>(h, 0, h->vin32, h->zout32, s);
-    k_cast<float, double><<<vgrid(h->n), 256, 0, s>>>(h->zout32, z, h->n);
+    MGR_LAUNCH k_cast<float, double><<<vgrid(h->n), 256, 0, s>>>(h->zout32, z, h->n);
   } else {
     mgr_level<double>(h, 0, v, z, s);
   }
@@ -402,7 +402,7 @@ int apply_mgr32(Handle* h, const float* v, float* z, cudaStream_t s) {
 }
 
 int apply_mgr_mixed_into(Handle* h, const double* v, float* z, cudaStream_t s) {
-  k_cast<double, float><<<vgrid(h->n), 256, 0, s>>>(v, h->vin32, h->n);
+  MGR_LAUNCH k_cast<double, float><<<vgrid(h->n), 256, 0, s>>>(v, h->vin32, h->n);
   mgr_level<float>(h, 0, h->vin32, z, s);
   MGR_TRY_CUDA(cudaGetLastError());
   return MGR_SUCCESS;
@@ -411,9 +411,9 @@ int apply_mgr_mixed_into(Handle* h, const double* v, float* z, cudaStream_t s) {
 int apply_vcycle64(Handle* h, Amg* g, const double* b, double* x, cudaStream_t s) {
   if (h->opt.precision == MGR_MIXED) {
     int64_t n = g->lev[0].A.nr;
-    k_cast<double, float><<<vgrid(n), 256, 0, s>>>(b, h->vin32, n);
+    MGR_LAUNCH k_cast<double, float><<<vgrid(n), 256, 0, s>>>(b, h->vin32, n);
     vcycle<float>(g, 0, h->vin32, h->zout32, s);
-    k_cast<float, double><<<vgrid(n), 256, 0, s>>>(h->zout32, x, n);
+    MGR_LAUNCH k_cast<float, double><<<vgrid(n), 256, 0, s>>>(h->zout32, x, n);
   } else {
     vcycle<double>(g, 0, b, x, s);
   }

@@ -8,6 +8,8 @@
 #include "mgr_internal.cuh"
 
 namespace mgr {
+std::atomic<long long> g_launches{0};
+
 int fgmres_run(Handle* h, const mgr_matrix_t* A, const double* b, double* x,
                const fgmres_options_t* o, fgmres_info_t* info, cudaStream_t s);
 
@@ -222,9 +224,11 @@ int mgr_splitmix64_device(const uint64_t* in, uint64_t* out, int64_t n, void* st
   (void)cudaGetLastError();  // errors of earlier calls are not this call's
   if (n < 0 || (n > 0 && (!in || !out))) return MGR_ERR_INVALID_ARG;
   if (n == 0) return MGR_SUCCESS;
-  k_splitmix<<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(in, out, n);
+  MGR_LAUNCH k_splitmix<<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(in, out, n);
   MGR_TRY_CUDA(cudaGetLastError());
   return MGR_SUCCESS;
 }
+
+int64_t mgr_launch_count(void) { return (int64_t)g_launches.load(); }
 
 }  // extern "C"

@@ -133,8 +133,8 @@ static int ensure_krylov(Handle* h, int m, cudaStream_t s) {
 // dst[0..nv) = V[0..nv)^T w, computed twice-reduced (fixed order)
 static void mdot(Handle* h, const double* V, int64_t ld, int nv, const double* w, int64_t n,
                  double* dst, int accumulate, cudaStream_t s) {
-  k_mdot<<<KGRID, KB, 0, s>>>(V, ld, nv, w, n, h->part);
-  k_mdot_final<<<1, KB, 0, s>>>(h->part, KGRID, nv, dst, accumulate);
+  MGR_LAUNCH k_mdot<<<KGRID, KB, 0, s>>>(V, ld, nv, w, n, h->part);
+  MGR_LAUNCH k_mdot_final<<<1, KB, 0, s>>>(h->part, KGRID, nv, dst, accumulate);
 }
 
 int fgmres_run(Handle* h, const mgr_matrix_t* A, const double* b, double* x,
@@ -153,7 +153,7 @@ int fgmres_run(Handle* h, const mgr_matrix_t* A, const double* b, double* x,
   MGR_TRY_CUDA(cudaEventRecord(e0, s));
 
   std::vector<double> H((size_t)(m + 1) * m, 0.0), cs(m), sn(m), g(m + 1), y(m);
-  k_fill0<<<grid_for(n, KB), KB, 0, s>>>(x, n);
+  MGR_LAUNCH k_fill0<<<grid_for(n, KB), KB, 0, s>>>(x, n);
   // ||b||
   mdot(h, b, n, 1, b, n, h->hred, 0, s);
   MGR_TRY(read_back(hp, h->hred, s));
@@ -171,7 +171,7 @@ int fgmres_run(Handle* h, const mgr_matrix_t* A, const double* b, double* x,
     while (iters < maxit) {
       // v_0 = r / beta
       mdot(h, h->r, n, 1, h->r, n, h->hred, 0, s);
-      k_scale_by_norm<<<grid_for(n, KB), KB, 0, s>>>(h->r, h->hred, h->V, n);
+      MGR_LAUNCH k_scale_by_norm<<<grid_for(n, KB), KB, 0, s>>>(h->r, h->hred, h->V, n);
       std::fill(g.begin(), g.end(), 0.0);
       g[0] = beta;
       int jend = 0;
@@ -191,13 +191,13 @@ int fgmres_run(Handle* h, const mgr_matrix_t* A, const double* b, double* x,
         }
         // classical Gram-Schmidt, twice
         mdot(h, h->V, n, j + 1, h->w, n, h->hcol, 0, s);
-        k_mupdate<<<KGRID, KB, 0, s>>>(h->V, n, j + 1, h->hcol, h->w, n);
+        MGR_LAUNCH k_mupdate<<<KGRID, KB, 0, s>>>(h->V, n, j + 1, h->hcol, h->w, n);
         mdot(h, h->V, n, j + 1, h->w, n, h->yv, 0, s);
-        k_mupdate<<<KGRID, KB, 0, s>>>(h->V, n, j + 1, h->yv, h->w, n);
-        k_mdot_final<<<1, 32, 0, s>>>(h->yv, 1, j + 1, h->hcol, 1);   // h += h2
+        MGR_LAUNCH k_mupdate<<<KGRID, KB, 0, s>>>(h->V, n, j + 1, h->yv, h->w, n);
+        MGR_LAUNCH k_mdot_final<<<1, 32, 0, s>>>(h->yv, 1, j + 1, h->hcol, 1);   // h += h2
         mdot(h, h->w, n, 1, h->w, n, h->hcol + j + 1, 0, s);
-        k_scale_by_norm<<<grid_for(n, KB), KB, 0, s>>>(h->w, h->hcol + j + 1, vnext, n);
-        k_sqrt_inplace<<<1, 1, 0, s>>>(h->hcol + j + 1);
+        MGR_LAUNCH k_scale_by_norm<<<grid_for(n, KB), KB, 0, s>>>(h->w, h->hcol + j + 1, vnext, n);
+        MGR_LAUNCH k_sqrt_inplace<<<1, 1, 0, s>>>(h->hcol + j + 1);
         MGR_TRY_CUDA(cudaMemcpyAsync(hp, h->hcol, sizeof(double) * (j + 2), cudaMemcpyDeviceToHost, s));
         MGR_TRY_CUDA(cudaStreamSynchronize(s));
         MGR_TRY_CUDA(cudaGetLastError());
@@ -236,9 +236,9 @@ int fgmres_run(Handle* h, const mgr_matrix_t* A, const double* b, double* x,
       }
       MGR_TRY_CUDA(cudaMemcpyAsync(h->yv, y.data(), sizeof(double) * jend, cudaMemcpyHostToDevice, s));
       if (mixed)
-        k_xupdate<float><<<KGRID, KB, 0, s>>>((const float*)h->Z, n, jend, h->yv, x, n);
+        MGR_LAUNCH k_xupdate<float><<<KGRID, KB, 0, s>>>((const float*)h->Z, n, jend, h->yv, x, n);
       else
-        k_xupdate<double><<<KGRID, KB, 0, s>>>((const double*)h->Z, n, jend, h->yv, x, n);
+        MGR_LAUNCH k_xupdate<double><<<KGRID, KB, 0, s>>>((const double*)h->Z, n, jend, h->yv, x, n);
       // true residual in FP64
       residual64(A->row_ptr, A->col_idx, A->val, n, A->nnz, b, x, h->r, s);
       mdot(h, h->r, n, 1, h->r, n, h->hred, 0, s);

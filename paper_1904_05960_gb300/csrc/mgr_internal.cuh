@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
 #include <cstdio>
 #include <vector>
@@ -33,6 +34,11 @@ struct Status {
     int _s = (expr);             \
     if (_s != MGR_SUCCESS) return _s; \
   } while (0)
+
+// Host-side count of kernel launches made by this library (every launch site
+// is written `MGR_LAUNCH kernel<<<...>>>(...)`, a comma expression).
+extern std::atomic<long long> g_launches;
+#define MGR_LAUNCH ++mgr::g_launches,
 
 // device-side error word values (first error wins)
 enum DevErr : int { DEV_OK = 0, DEV_ZERO_DIAG = 1, DEV_BAD_ARG = 2, DEV_OVERFLOW = 3 };

@@ -87,12 +87,12 @@ int scan_exclusive(const int64_t* in, int64_t* out, int64_t n, cudaStream_t s, P
   int64_t nb = (m + SCAN_TILE - 1) / SCAN_TILE;
   int64_t* bsum = tmp.get<int64_t>(nb);
   if (!bsum) return tmp.err;
-  k_scan_tile<<<(unsigned)nb, SCAN_TPB, 0, s>>>(in, n, out, bsum);
+  MGR_LAUNCH k_scan_tile<<<(unsigned)nb, SCAN_TPB, 0, s>>>(in, n, out, bsum);
   if (nb > 1) {
     int64_t* boff = tmp.get<int64_t>(nb + 1);
     if (!boff) return tmp.err;
     MGR_TRY(scan_exclusive(bsum, boff, nb, s, tmp));
-    k_scan_add<<<(unsigned)nb, SCAN_TPB, 0, s>>>(out, n, boff);
+    MGR_LAUNCH k_scan_add<<<(unsigned)nb, SCAN_TPB, 0, s>>>(out, n, boff);
   }
   MGR_TRY_CUDA(cudaGetLastError());
   return MGR_SUCCESS;
@@ -174,12 +174,12 @@ static int extract(Pool& P, Pool& tmp, const Csr& A, const int64_t* rows, int64_
   out.nc = ncols;
   out.rp = P.get<int64_t>(nrows + 1);
   if (!out.rp) return P.err;
-  k_extract_count<<<nblocks(nrows, 256), 256, 0, s>>>(A.rp, A.ci, rows, nrows, colmap, cnt);
+  MGR_LAUNCH k_extract_count<<<nblocks(nrows, 256), 256, 0, s>>>(A.rp, A.ci, rows, nrows, colmap, cnt);
   MGR_TRY(rowptr_from_counts(cnt, out.rp, nrows, &out.nnz, s, tmp));
   out.ci = P.get<int32_t>(out.nnz);
   out.v = P.get<double>(out.nnz);
   if (P.err) return P.err;
-  k_extract_fill<<<nblocks(nrows, 256), 256, 0, s>>>(A.rp, A.ci, A.v, rows, nrows, colmap,
+  MGR_LAUNCH k_extract_fill<<<nblocks(nrows, 256), 256, 0, s>>>(A.rp, A.ci, A.v, rows, nrows, colmap,
                                                       out.rp, out.ci, out.v);
   MGR_TRY_CUDA(cudaGetLastError());
   return MGR_SUCCESS;
@@ -324,13 +324,13 @@ static int spgemm(Pool& P, Pool& tmp, const Csr& A, const Csr& B, Csr& C, cudaSt
     attr = true;
   }
   unsigned g = grid_for(A.nr, SPG_WARPS, 152 * 16);
-  k_spgemm_symbolic<false><<<g, SPG_WARPS * 32, sm, s>>>(A.rp, A.ci, A.nr, B.rp, B.ci, cnt, nullptr);
+  MGR_LAUNCH k_spgemm_symbolic<false><<<g, SPG_WARPS * 32, sm, s>>>(A.rp, A.ci, A.nr, B.rp, B.ci, cnt, nullptr);
   MGR_TRY(rowptr_from_counts(cnt, C.rp, A.nr, &C.nnz, s, tmp));
   C.ci = P.get<int32_t>(C.nnz);
   C.v = P.get<double>(C.nnz);
   if (P.err) return P.err;
-  k_spgemm_symbolic<true><<<g, SPG_WARPS * 32, sm, s>>>(A.rp, A.ci, A.nr, B.rp, B.ci, C.rp, C.ci);
-  k_spgemm_numeric<<<grid_for(A.nr, 8, 152 * 16), 256, 0, s>>>(A.rp, A.ci, A.v, A.nr, B.rp, B.ci,
+  MGR_LAUNCH k_spgemm_symbolic<true><<<g, SPG_WARPS * 32, sm, s>>>(A.rp, A.ci, A.nr, B.rp, B.ci, C.rp, C.ci);
+  MGR_LAUNCH k_spgemm_numeric<<<grid_for(A.nr, 8, 152 * 16), 256, 0, s>>>(A.rp, A.ci, A.v, A.nr, B.rp, B.ci,
                                                                 B.v, C.rp, C.ci, C.v);
   MGR_TRY_CUDA(cudaGetLastError());
   return MGR_SUCCESS;
@@ -390,11 +390,11 @@ static int transpose(Pool& P, Pool& tmp, const Csr& A, Csr& T, bool values, bool
   if (P.err || tmp.err) return P.err ? P.err : tmp.err;
   MGR_TRY_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int64_t) * (A.nc + 1), s));
   MGR_TRY_CUDA(cudaMemsetAsync(cur, 0, sizeof(int64_t) * (A.nc + 1), s));
-  k_count_cols<<<grid_for(A.nnz, 256), 256, 0, s>>>(A.ci, A.nnz, cnt);
+  MGR_LAUNCH k_count_cols<<<grid_for(A.nnz, 256), 256, 0, s>>>(A.ci, A.nnz, cnt);
   int64_t tot = 0;
   MGR_TRY(rowptr_from_counts(cnt, T.rp, A.nc, &tot, s, tmp));
-  k_transpose_fill<<<nblocks(A.nr, 256), 256, 0, s>>>(A.rp, A.ci, A.v, A.nr, T.rp, cur, T.ci, T.v);
-  if (sorted) k_sort_rows<<<nblocks(T.nr, 128), 128, 0, s>>>(T.rp, T.nr, T.ci, T.v);
+  MGR_LAUNCH k_transpose_fill<<<nblocks(A.nr, 256), 256, 0, s>>>(A.rp, A.ci, A.v, A.nr, T.rp, cur, T.ci, T.v);
+  if (sorted) MGR_LAUNCH k_sort_rows<<<nblocks(T.nr, 128), 128, 0, s>>>(T.rp, T.nr, T.ci, T.v);
   MGR_TRY_CUDA(cudaGetLastError());
   return MGR_SUCCESS;
 }
@@ -992,8 +992,8 @@ static int dense_coarsest(Handle* h, Amg* g, Pool& tmp, cudaStream_t s) {
   g->inv = P.get<double>(n * n);
   if (P.err || tmp.err) return P.err ? P.err : tmp.err;
   MGR_TRY_CUDA(cudaMemsetAsync(d, 0, sizeof(double) * n * n, s));
-  k_csr_to_dense<<<nblocks(n, 256), 256, 0, s>>>(A.rp, A.ci, A.v, n, d);
-  k_dense_lu_inverse<<<1, 1024, 0, s>>>(d, (int)n, piv, g->inv, h->derr);
+  MGR_LAUNCH k_csr_to_dense<<<nblocks(n, 256), 256, 0, s>>>(A.rp, A.ci, A.v, n, d);
+  MGR_LAUNCH k_dense_lu_inverse<<<1, 1024, 0, s>>>(d, (int)n, piv, g->inv, h->derr);
   MGR_TRY_CUDA(cudaGetLastError());
   return check_dev_err(h->derr, s);
 }
@@ -1024,19 +1024,19 @@ int build_amg(Handle* h, const Csr& A0, const int32_t* comp0, int slot, Amg** ou
     const int64_t n = L->A.nr;
     L->dinv = P.get<double>(n);
     if (!L->dinv) { rc = P.err; break; }
-    k_l1_inv<<<nblocks(n, 256), 256, 0, s>>>(L->A.rp, L->A.ci, L->A.v, n, L->dinv, h->derr);
+    MGR_LAUNCH k_l1_inv<<<nblocks(n, 256), 256, 0, s>>>(L->A.rp, L->A.ci, L->A.v, n, L->dinv, h->derr);
     if (n <= o.amg_max_coarse || k + 1 >= o.amg_max_levels || k + 1 >= 32) break;
     // strength graph
     int64_t* cnt = tmp.get<int64_t>(n + 1);
     L->S.nr = L->S.nc = n;
     L->S.rp = P.get<int64_t>(n + 1);
     if (tmp.err || P.err) { rc = tmp.err ? tmp.err : P.err; break; }
-    k_strength<false><<<nblocks(n, 128), 128, 0, s>>>(L->A.rp, L->A.ci, L->A.v, L->comp, n,
+    MGR_LAUNCH k_strength<false><<<nblocks(n, 128), 128, 0, s>>>(L->A.rp, L->A.ci, L->A.v, L->comp, n,
                                                      o.amg_theta, cnt, nullptr);
     if ((rc = rowptr_from_counts(cnt, L->S.rp, n, &L->S.nnz, s, tmp))) break;
     L->S.ci = P.get<int32_t>(L->S.nnz);
     if (P.err) { rc = P.err; break; }
-    k_strength<true><<<nblocks(n, 128), 128, 0, s>>>(L->A.rp, L->A.ci, L->A.v, L->comp, n,
+    MGR_LAUNCH k_strength<true><<<nblocks(n, 128), 128, 0, s>>>(L->A.rp, L->A.ci, L->A.v, L->comp, n,
                                                     o.amg_theta, L->S.rp, L->S.ci);
     Csr ST;
     if ((rc = transpose(tmp, tmp, L->S, ST, false, false, s))) break;
@@ -1046,12 +1046,12 @@ int build_amg(Handle* h, const Csr& A0, const int32_t* comp0, int slot, Amg** ou
     L->cf = P.get<int8_t>(n);
     unsigned long long* und = tmp.get<unsigned long long>(1);
     if (tmp.err || P.err) { rc = tmp.err ? tmp.err : P.err; break; }
-    k_pmis_init<<<nblocks(n, 256), 256, 0, s>>>(L->S.rp, ST.rp, n, o.seed, slot, k, w, L->cf);
+    MGR_LAUNCH k_pmis_init<<<nblocks(n, 256), 256, 0, s>>>(L->S.rp, ST.rp, n, o.seed, slot, k, w, L->cf);
     for (int round = 0; round < 100000; round++) {
-      k_pmis_select<<<nblocks(n, 256), 256, 0, s>>>(L->S.rp, L->S.ci, ST.rp, ST.ci, w, L->cf, n, newc);
-      k_pmis_apply_c<<<nblocks(n, 256), 256, 0, s>>>(newc, n, L->cf);
+      MGR_LAUNCH k_pmis_select<<<nblocks(n, 256), 256, 0, s>>>(L->S.rp, L->S.ci, ST.rp, ST.ci, w, L->cf, n, newc);
+      MGR_LAUNCH k_pmis_apply_c<<<nblocks(n, 256), 256, 0, s>>>(newc, n, L->cf);
       cudaMemsetAsync(und, 0, sizeof(unsigned long long), s);
-      k_pmis_mark_f<<<nblocks(n, 256), 256, 0, s>>>(L->S.rp, L->S.ci, n, L->cf, und);
+      MGR_LAUNCH k_pmis_mark_f<<<nblocks(n, 256), 256, 0, s>>>(L->S.rp, L->S.ci, n, L->cf, und);
       unsigned long long left = 0;
       if ((rc = read_back(&left, und, s))) break;
       if (left == 0) break;
@@ -1061,7 +1061,7 @@ int build_amg(Handle* h, const Csr& A0, const int32_t* comp0, int slot, Amg** ou
     int64_t* flag = tmp.get<int64_t>(n + 1);
     int64_t* cmap = tmp.get<int64_t>(n + 1);
     if (tmp.err) { rc = tmp.err; break; }
-    k_flag_c<<<nblocks(n, 256), 256, 0, s>>>(L->cf, n, flag);
+    MGR_LAUNCH k_flag_c<<<nblocks(n, 256), 256, 0, s>>>(L->cf, n, flag);
     int64_t nc = 0;
     if ((rc = rowptr_from_counts(flag, cmap, n, &nc, s, tmp))) break;
     if (nc == 0 || nc == n) break;
@@ -1071,14 +1071,14 @@ int build_amg(Handle* h, const Csr& A0, const int32_t* comp0, int slot, Amg** ou
     L->P.nc = nc;
     L->P.rp = P.get<int64_t>(n + 1);
     if (P.err) { rc = P.err; break; }
-    k_interp<false><<<nblocks(n, 128), 128, 0, s>>>(L->A.rp, L->A.ci, L->A.v, L->S.rp, L->S.ci,
+    MGR_LAUNCH k_interp<false><<<nblocks(n, 128), 128, 0, s>>>(L->A.rp, L->A.ci, L->A.v, L->S.rp, L->S.ci,
                                                    L->comp, L->cf, cmap, n, o.amg_pmax, cnt,
                                                    nullptr, nullptr);
     if ((rc = rowptr_from_counts(cnt, L->P.rp, n, &L->P.nnz, s, tmp))) break;
     L->P.ci = P.get<int32_t>(L->P.nnz);
     L->P.v = P.get<double>(L->P.nnz);
     if (P.err) { rc = P.err; break; }
-    k_interp<true><<<nblocks(n, 128), 128, 0, s>>>(L->A.rp, L->A.ci, L->A.v, L->S.rp, L->S.ci,
+    MGR_LAUNCH k_interp<true><<<nblocks(n, 128), 128, 0, s>>>(L->A.rp, L->A.ci, L->A.v, L->S.rp, L->S.ci,
                                                   L->comp, L->cf, cmap, n, o.amg_pmax, L->P.rp,
                                                   L->P.ci, L->P.v);
     if ((rc = transpose(P, tmp, L->P, L->R, true, true, s))) break;
@@ -1090,7 +1090,7 @@ int build_amg(Handle* h, const Csr& A0, const int32_t* comp0, int slot, Amg** ou
     if ((rc = spgemm(P, tmp, L->R, AP, C.A, s))) break;
     C.comp = P.get<int32_t>(nc);
     if (P.err) { rc = P.err; break; }
-    k_coarse_comp<<<nblocks(n, 256), 256, 0, s>>>(L->cf, cmap, L->comp, n, C.comp);
+    MGR_LAUNCH k_coarse_comp<<<nblocks(n, 256), 256, 0, s>>>(L->cf, cmap, L->comp, n, C.comp);
     MGR_TRY_CUDA(cudaGetLastError());
   }
   if (rc == MGR_SUCCESS) rc = check_dev_err(h->derr, s);
@@ -1125,7 +1125,7 @@ static int setup_level(Handle* h, int l, const int32_t* label, const int32_t* no
   int32_t* colF = tmp.get<int32_t>(n);
   int32_t* colC = tmp.get<int32_t>(n);
   if (tmp.err) return tmp.err;
-  k_flag_f<<<nblocks(n, 256), 256, 0, s>>>(label, n, o.f_label_mask[l], flag, h->derr);
+  MGR_LAUNCH k_flag_f<<<nblocks(n, 256), 256, 0, s>>>(label, n, o.f_label_mask[l], flag, h->derr);
   MGR_TRY(rowptr_from_counts(flag, fpos, n, &L.nF, s, tmp));
   MGR_TRY(check_dev_err(h->derr, s));
   L.nC = n - L.nF;
@@ -1133,7 +1133,7 @@ static int setup_level(Handle* h, int l, const int32_t* label, const int32_t* no
   L.Fidx = P.get<int64_t>(L.nF);
   L.Cidx = P.get<int64_t>(L.nC);
   if (P.err) return P.err;
-  k_split<<<nblocks(n, 256), 256, 0, s>>>(fpos, n, L.Fidx, L.Cidx, colF, colC);
+  MGR_LAUNCH k_split<<<nblocks(n, 256), 256, 0, s>>>(fpos, n, L.Fidx, L.Cidx, colF, colC);
   {
     int64_t last_f = -1;
     MGR_TRY(read_back(&last_f, L.Fidx + (L.nF - 1), s));
@@ -1156,7 +1156,7 @@ static int setup_level(Handle* h, int l, const int32_t* label, const int32_t* no
   if (P.err || tmp.err) return P.err ? P.err : tmp.err;
   MGR_TRY_CUDA(cudaMemcpyAsync(L.W.rp, Afc.rp, sizeof(int64_t) * (L.nF + 1), cudaMemcpyDeviceToDevice, s));
   MGR_TRY_CUDA(cudaMemcpyAsync(L.W.ci, Afc.ci, sizeof(int32_t) * Afc.nnz, cudaMemcpyDeviceToDevice, s));
-  k_dff_and_w<<<nblocks(L.nF, 256), 256, 0, s>>>(L.A.rp, L.A.ci, L.A.v, L.Fidx, L.nF, Afc.rp, Afc.v,
+  MGR_LAUNCH k_dff_and_w<<<nblocks(L.nF, 256), 256, 0, s>>>(L.A.rp, L.A.ci, L.A.v, L.Fidx, L.nF, Afc.rp, Afc.v,
                                                   T.v, L.W.v, L.dFinv, h->derr);
   MGR_TRY(check_dev_err(h->derr, s));
   // A_cor = A_CF T
@@ -1166,12 +1166,12 @@ static int setup_level(Handle* h, int l, const int32_t* label, const int32_t* no
   *nnode = P.get<int32_t>(L.nC);
   *ncomp = P.get<int32_t>(L.nC);
   if (P.err) return P.err;
-  k_gather3<<<nblocks(L.nC, 256), 256, 0, s>>>(label, node, comp, L.Cidx, L.nC, *nlabel, *nnode, *ncomp);
+  MGR_LAUNCH k_gather3<<<nblocks(L.nC, 256), 256, 0, s>>>(label, node, comp, L.Cidx, L.nC, *nlabel, *nnode, *ncomp);
   // G
   int8_t* keep = tmp.get<int8_t>(L.cor.nnz);
   int64_t* cnt = tmp.get<int64_t>(L.nC + 1);
   if (tmp.err) return tmp.err;
-  k_drop_mark<<<nblocks(L.nC, 128), 128, 0, s>>>(L.cor.rp, L.cor.ci, L.cor.v, L.nC, *nnode,
+  MGR_LAUNCH k_drop_mark<<<nblocks(L.nC, 128), 128, 0, s>>>(L.cor.rp, L.cor.ci, L.cor.v, L.nC, *nnode,
                                                   o.nmax_drop[l], keep, cnt);
   L.corkept.nr = L.corkept.nc = L.nC;
   L.corkept.rp = P.get<int64_t>(L.nC + 1);
@@ -1180,20 +1180,20 @@ static int setup_level(Handle* h, int l, const int32_t* label, const int32_t* no
   L.corkept.ci = P.get<int32_t>(L.corkept.nnz);
   L.corkept.v = P.get<double>(L.corkept.nnz);
   if (P.err) return P.err;
-  k_drop_fill<<<nblocks(L.nC, 256), 256, 0, s>>>(L.cor.rp, L.cor.ci, L.cor.v, L.nC, keep,
+  MGR_LAUNCH k_drop_fill<<<nblocks(L.nC, 256), 256, 0, s>>>(L.cor.rp, L.cor.ci, L.cor.v, L.nC, keep,
                                                   L.corkept.rp, L.corkept.ci, L.corkept.v);
   // S = A_CC - G(A_cor)
   Snext.nr = Snext.nc = L.nC;
   Snext.rp = P.get<int64_t>(L.nC + 1);
   if (P.err) return P.err;
-  k_union_sub<false><<<nblocks(L.nC, 256), 256, 0, s>>>(Acc.rp, Acc.ci, Acc.v, L.corkept.rp,
+  MGR_LAUNCH k_union_sub<false><<<nblocks(L.nC, 256), 256, 0, s>>>(Acc.rp, Acc.ci, Acc.v, L.corkept.rp,
                                                        L.corkept.ci, L.corkept.v, L.nC, cnt,
                                                        nullptr, nullptr);
   MGR_TRY(rowptr_from_counts(cnt, Snext.rp, L.nC, &Snext.nnz, s, tmp));
   Snext.ci = P.get<int32_t>(Snext.nnz);
   Snext.v = P.get<double>(Snext.nnz);
   if (P.err) return P.err;
-  k_union_sub<true><<<nblocks(L.nC, 256), 256, 0, s>>>(Acc.rp, Acc.ci, Acc.v, L.corkept.rp,
+  MGR_LAUNCH k_union_sub<true><<<nblocks(L.nC, 256), 256, 0, s>>>(Acc.rp, Acc.ci, Acc.v, L.corkept.rp,
                                                       L.corkept.ci, L.corkept.v, L.nC, Snext.rp,
                                                       Snext.ci, Snext.v);
   MGR_TRY_CUDA(cudaGetLastError());
@@ -1203,7 +1203,7 @@ static int setup_level(Handle* h, int l, const int32_t* label, const int32_t* no
     int32_t* dummy1 = tmp.get<int32_t>(L.nF);
     int32_t* dummy2 = tmp.get<int32_t>(L.nF);
     if (tmp.err) return tmp.err;
-    k_gather3<<<nblocks(L.nF, 256), 256, 0, s>>>(comp, label, node, L.Fidx, L.nF, fcomp, dummy1, dummy2);
+    MGR_LAUNCH k_gather3<<<nblocks(L.nF, 256), 256, 0, s>>>(comp, label, node, L.Fidx, L.nF, fcomp, dummy1, dummy2);
     MGR_TRY(build_amg(h, Aff, fcomp, l, &L.famg, s));
   }
   // point-block global smoother
@@ -1211,13 +1211,13 @@ static int setup_level(Handle* h, int l, const int32_t* label, const int32_t* no
     int64_t* head = tmp.get<int64_t>(n + 1);
     int64_t* hpos = tmp.get<int64_t>(n + 1);
     if (tmp.err) return tmp.err;
-    k_block_heads<<<nblocks(n, 256), 256, 0, s>>>(node, n, head);
+    MGR_LAUNCH k_block_heads<<<nblocks(n, 256), 256, 0, s>>>(node, n, head);
     MGR_TRY(rowptr_from_counts(head, hpos, n, &L.nblk, s, tmp));
     L.bstart = P.get<int64_t>(L.nblk + 1);
     L.binv = P.get<double>(16 * L.nblk);
     if (P.err) return P.err;
-    k_block_starts<<<nblocks(n + 1, 256), 256, 0, s>>>(hpos, n, L.bstart, L.nblk);
-    k_block_inv<<<nblocks(L.nblk, 128), 128, 0, s>>>(L.A.rp, L.A.ci, L.A.v, L.bstart, L.nblk,
+    MGR_LAUNCH k_block_starts<<<nblocks(n + 1, 256), 256, 0, s>>>(hpos, n, L.bstart, L.nblk);
+    MGR_LAUNCH k_block_inv<<<nblocks(L.nblk, 128), 128, 0, s>>>(L.A.rp, L.A.ci, L.A.v, L.bstart, L.nblk,
                                                       L.binv, h->derr);
     MGR_TRY(check_dev_err(h->derr, s));
   }
@@ -1290,7 +1290,7 @@ static int f32(Pool& P, const double* a, float** b, int64_t n, cudaStream_t s) {
   if (!a || n == 0) return MGR_SUCCESS;
   *b = P.get<float>(n);
   if (!*b) return P.err;
-  k_d2f<<<grid_for(n, 256), 256, 0, s>>>(a, *b, n);
+  MGR_LAUNCH k_d2f<<<grid_for(n, 256), 256, 0, s>>>(a, *b, n);
   return MGR_SUCCESS;
 }
 

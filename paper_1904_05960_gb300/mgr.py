@@ -26,7 +26,8 @@ Q_AMG_A, Q_AMG_S, Q_AMG_P, Q_AMG_R = 10, 11, 12, 13
 
 EXPORTED = ["mgr_options_default", "fgmres_options_default", "mgr_setup", "mgr_apply",
             "fgmres_solve", "mgr_destroy", "mgr_error_string", "mgr_get_csr",
-            "mgr_amg_levels", "mgr_get_cf", "mgr_vcycle", "mgr_splitmix64_device"]
+            "mgr_amg_levels", "mgr_get_cf", "mgr_vcycle", "mgr_splitmix64_device",
+            "mgr_launch_count"]
 
 
 class MgrMatrix(C.Structure):
@@ -94,6 +95,8 @@ def lib():
             L.mgr_get_cf.restype = I64
             L.mgr_vcycle.argtypes = [P, C.c_int, P, P, P]
             L.mgr_splitmix64_device.argtypes = [P, P, I64, P]
+            L.mgr_launch_count.argtypes = []
+            L.mgr_launch_count.restype = I64
             _lib = L
     return _lib
 
@@ -217,6 +220,14 @@ def mgr_get_csr(h, kind, slot=0, lvl=0):
     return nr, nc, rp, ci[:nnz], v[:nnz]
 
 
+def mgr_get_csr_dims(h, kind, slot=0, lvl=0):
+    """(rows, cols, nnz) of a hierarchy matrix, or None."""
+    dims = np.zeros(3, dtype=np.int64)
+    if lib().mgr_get_csr(h, kind, slot, lvl, dims.ctypes.data, None, None, None) != 0:
+        return None
+    return tuple(int(x) for x in dims)
+
+
 def mgr_get_scipy(h, kind, slot=0, lvl=0):
     import scipy.sparse as sp
     r = mgr_get_csr(h, kind, slot, lvl)
@@ -246,6 +257,11 @@ def mgr_vcycle(h, slot, b, x, stream=None):
 def mgr_splitmix64_device(inp, out, stream=None):
     return _check(lib().mgr_splitmix64_device(_ptr(inp), _ptr(out), inp.numel(),
                                               _stream_ptr(stream)), "mgr_splitmix64_device")
+
+
+def mgr_launch_count():
+    """Kernel launches issued by the library so far in this process."""
+    return int(lib().mgr_launch_count())
 
 
 class Solver:
