@@ -195,6 +195,27 @@ int mgr_vcycle(mgr_handle_t h, int slot, const double* b, double* x, void* strea
  * of the PMIS weight hash: out[i] = splitmix64(in[i]) for n values (device). */
 int mgr_splitmix64_device(const uint64_t* in, uint64_t* out, int64_t n, void* stream);
 
+/*
+ * One V-cycle of AMG slot `slot` from a zero guess, like mgr_vcycle, but
+ * allocating nothing and using none of the handle's workspace.  (The paper has
+ * no counterpart: this serves callers that cannot allocate device memory where
+ * they run, e.g. a program whose device memory is all handed to its own pool up
+ * front, or a loop that forbids allocation after start-up.)
+ *   b, x: DEVICE FP64 arrays of that AMG's size, supplied by the caller.
+ *   Workspace: one fixed 8 MiB buffer compiled into the library
+ *   (static __device__, held by every GPU that loads the library until exit).
+ *   A V-cycle whose level vectors need more than 8 MiB is rejected with
+ *   MGR_ERR_INVALID_ARG and a message on stderr; nothing is launched then.
+ *   The first call on a device looks up the buffer's device address
+ *   (cudaGetSymbolAddress, with that device current); make that first call
+ *   before any stream capture.  Every call on a device shares the buffer and it
+ *   keeps the last call's contents (each vector in it is written before it is
+ *   read, so nothing needs clearing); calls that overlap on the GPU (different
+ *   streams, or host threads) race on it and must be serialised by the caller.
+ * Asynchronous on `stream`.
+ */
+int mgr_vcycle_noalloc(mgr_handle_t h, int slot, const double* b, double* x, void* stream);
+
 /* Number of CUDA kernel launches this library has issued in this process
  * (all handles, all threads).  Lets a caller count the kernels of a region. */
 int64_t mgr_launch_count(void);

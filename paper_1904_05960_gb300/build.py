@@ -21,7 +21,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libmgr_gb300.so")
 ROOT = os.path.dirname(HERE)
 
-SOURCES = ["setup.cu", "apply.cu", "krylov.cu", "capi.cu"]
+SOURCES = ["setup.cu", "apply.cu", "krylov.cu", "capi.cu", "noalloc.cu"]
 NO_FMAD = {"setup.cu"}
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -421,4 +421,89 @@ int apply_vcycle64(Handle* h, Amg* g, const double* b, double* x, cudaStream_t s
   return MGR_SUCCESS;
 }
 
+
+// ----------------------------------------------------------------------------
+// V-cycle with caller-provided workspace (used by the allocation-free entry
+// point in noalloc.cu).  Same kernels and order as vcycle<T>; the level vectors
+// t, r (and b, x below the top level) are carved from `ws`, each 256-byte
+// aligned.  Every workspace vector is written before it is read.
+// ----------------------------------------------------------------------------
+static size_t ws_align(size_t b) { return (b + 255) & ~size_t(255); }
+
+size_t vcycle_ws_bytes(Handle* h, Amg* g) {
+  const size_t vb = (h->opt.precision == MGR_MIXED) ? sizeof(float) : sizeof(double);
+  size_t total = 0;
+  for (size_t k = 0; k < g->lev.size(); k++) {
+    const size_t n = (size_t)g->lev[k].A.nr;
+    const bool last = k + 1 == g->lev.size();
+    if (k > 0) total += 2 * ws_align(n * vb);          // b, x
+    if (!last) total += 2 * ws_align(n * vb);          // t, r
+  }
+  if (h->opt.precision == MGR_MIXED) total += 2 * ws_align((size_t)g->lev[0].A.nr * sizeof(float));
+  return total;
+}
+
+template <class T>
+struct WsLevel {
+  T *b, *x, *t, *r;
+};
+
+template <class T>
+static void vcycle_ws(Amg* g, int k, const T* b, T* x, WsLevel<T>* W, cudaStream_t s) {
+  AmgLevel& L = g->lev[k];
+  const int64_t n = L.A.nr;
+  if (k == (int)g->lev.size() - 1) {
+    const T* inv = pick<T>(g->inv, g->invf);
+    MGR_LAUNCH k_dense_gemv<T><<<grid_for(n * 32, 256), 256, 0, s>>>(inv, n, b, x);
+    return;
+  }
+  const T* dinv = pick<T>(L.dinv, L.dinvf);
+  T* t = W[k].t;
+  T* r = W[k].r;
+  MGR_LAUNCH k_scale<T><<<vgrid(n), 256, 0, s>>>(dinv, b, t, n);
+  spmv<T, MODE_RES>(L.A, t, r, b, nullptr, nullptr, s);
+  spmv<T, MODE_AX>(L.R, r, W[k + 1].b, nullptr, nullptr, nullptr, s);
+  vcycle_ws<T>(g, k + 1, W[k + 1].b, W[k + 1].x, W, s);
+  spmv<T, MODE_ADD>(L.P, W[k + 1].x, t, nullptr, nullptr, nullptr, s);
+  spmv<T, MODE_SMOOTH>(L.A, t, x, b, dinv, nullptr, s);
+}
+
+template <class T>
+static void carve(Amg* g, unsigned char*& p, std::vector<WsLevel<T>>& W) {
+  W.resize(g->lev.size());
+  for (size_t k = 0; k < g->lev.size(); k++) {
+    const size_t n = (size_t)g->lev[k].A.nr;
+    const bool last = k + 1 == g->lev.size();
+    W[k] = WsLevel<T>{nullptr, nullptr, nullptr, nullptr};
+    if (k > 0) {
+      W[k].b = (T*)p; p += ws_align(n * sizeof(T));
+      W[k].x = (T*)p; p += ws_align(n * sizeof(T));
+    }
+    if (!last) {
+      W[k].t = (T*)p; p += ws_align(n * sizeof(T));
+      W[k].r = (T*)p; p += ws_align(n * sizeof(T));
+    }
+  }
+}
+
+int apply_vcycle64_ws(Handle* h, Amg* g, const double* b, double* x, void* ws, cudaStream_t s) {
+  unsigned char* p = (unsigned char*)ws;
+  if (h->opt.precision == MGR_MIXED) {
+    std::vector<WsLevel<float>> W;
+    carve<float>(g, p, W);
+    const int64_t n = g->lev[0].A.nr;
+    float* b32 = (float*)p; p += ws_align((size_t)n * sizeof(float));
+    float* x32 = (float*)p; p += ws_align((size_t)n * sizeof(float));
+    MGR_LAUNCH k_cast<double, float><<<vgrid(n), 256, 0, s>>>(b, b32, n);
+    vcycle_ws<float>(g, 0, b32, x32, W.data(), s);
+    MGR_LAUNCH k_cast<float, double><<<vgrid(n), 256, 0, s>>>(x32, x, n);
+  } else {
+    std::vector<WsLevel<double>> W;
+    carve<double>(g, p, W);
+    vcycle_ws<double>(g, 0, b, x, W.data(), s);
+  }
+  MGR_TRY_CUDA(cudaGetLastError());
+  return MGR_SUCCESS;
+}
+
 }  // namespace mgr

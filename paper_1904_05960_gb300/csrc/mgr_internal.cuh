@@ -176,6 +176,9 @@ int apply_mgr(Handle* h, const double* v, double* z, cudaStream_t s);
 int apply_mgr32(Handle* h, const float* v, float* z, cudaStream_t s);
 int apply_mgr_mixed_into(Handle* h, const double* v, float* z, cudaStream_t s);
 int apply_vcycle64(Handle* h, Amg* g, const double* b, double* x, cudaStream_t s);
+// V-cycle with a caller-provided workspace of vcycle_ws_bytes() bytes
+size_t vcycle_ws_bytes(Handle* h, Amg* g);
+int apply_vcycle64_ws(Handle* h, Amg* g, const double* b, double* x, void* ws, cudaStream_t s);
 // generic CSR SpMV (FP64): y = A x
 void spmv64(const int64_t* rp, const int32_t* ci, const double* v, int64_t nr,
             int64_t nnz, const double* x, double* y, cudaStream_t s);

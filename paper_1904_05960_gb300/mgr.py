@@ -27,7 +27,7 @@ Q_AMG_A, Q_AMG_S, Q_AMG_P, Q_AMG_R = 10, 11, 12, 13
 EXPORTED = ["mgr_options_default", "fgmres_options_default", "mgr_setup", "mgr_apply",
             "fgmres_solve", "mgr_destroy", "mgr_error_string", "mgr_get_csr",
             "mgr_amg_levels", "mgr_get_cf", "mgr_vcycle", "mgr_splitmix64_device",
-            "mgr_launch_count"]
+            "mgr_launch_count", "mgr_vcycle_noalloc"]
 
 
 class MgrMatrix(C.Structure):
@@ -95,6 +95,7 @@ def lib():
             L.mgr_get_cf.restype = I64
             L.mgr_vcycle.argtypes = [P, C.c_int, P, P, P]
             L.mgr_splitmix64_device.argtypes = [P, P, I64, P]
+            L.mgr_vcycle_noalloc.argtypes = [P, C.c_int, P, P, P]
             L.mgr_launch_count.argtypes = []
             L.mgr_launch_count.restype = I64
             _lib = L
@@ -252,6 +253,14 @@ def mgr_get_cf(h, slot, lvl):
 
 def mgr_vcycle(h, slot, b, x, stream=None):
     return _check(lib().mgr_vcycle(h, slot, _ptr(b), _ptr(x), _stream_ptr(stream)), "mgr_vcycle")
+
+
+def mgr_vcycle_noalloc(h, slot, b, x, stream=None):
+    """One V-cycle like mgr_vcycle, with its workspace in the library's fixed
+    8 MiB device buffer instead of memory of the handle (for callers that
+    cannot allocate device memory where they run)."""
+    return _check(lib().mgr_vcycle_noalloc(h, slot, _ptr(b), _ptr(x), _stream_ptr(stream)),
+                  "mgr_vcycle_noalloc")
 
 
 def mgr_splitmix64_device(inp, out, stream=None):
