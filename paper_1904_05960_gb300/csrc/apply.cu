@@ -8,6 +8,8 @@
 // product that produces it instead of running separate vector passes.
 #include <cuda_runtime.h>
 
+#include <vector>
+
 #include "mgr_internal.cuh"
 
 namespace mgr {
@@ -30,22 +32,36 @@ __device__ __forceinline__ T ldg(const T* p) {
 // ----------------------------------------------------------------------------
 enum { MODE_AX = 0, MODE_RES = 1, MODE_SMOOTH = 2, MODE_ADD = 3, MODE_GRES = 4, MODE_RROWS = 5 };
 
-template <class T, class X, class Y, int G, int MODE>
+// Lanes of a G-lane group inside its warp (G divides 32; groups are aligned).
+template <int G>
+__device__ __forceinline__ unsigned group_mask() {
+  return (G == 32) ? FULL : (((1u << G) - 1u) << ((threadIdx.x & 31) & ~(G - 1)));
+}
+
+// Grid-stride over rows, one G-lane group per row, two independent
+// accumulators; I is the offset type (int when nnz < 2^31).  All lanes of a
+// group always share a row, so the shuffle mask is the group's own lanes.
+template <class T, class X, class Y, class I, int G, int MODE>
 __global__ void __launch_bounds__(256)
 k_spmv(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci, const T* __restrict__ val,
-       int64_t nr, const X* __restrict__ x, Y* __restrict__ y, const Y* __restrict__ b,
+       I nr, const X* __restrict__ x, Y* __restrict__ y, const Y* __restrict__ b,
        const T* __restrict__ dinv, const int64_t* __restrict__ rows) {
-  const int64_t gid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+  const I gid = (I)blockIdx.x * blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & (G - 1);
-  const int64_t stride = ((int64_t)gridDim.x * blockDim.x) / G;
-  for (int64_t i = gid / G; i < nr; i += stride) {
-    const int64_t row = (MODE == MODE_RROWS) ? rows[i] : i;
-    const int64_t e0 = rp[row], e1 = rp[row + 1];
-    Y acc = 0;
-    for (int64_t k = e0 + lane; k < e1; k += G)
-      acc += (Y)val[k] * (Y)ldg(x + ci[k]);
+  const I stride = ((I)gridDim.x * blockDim.x) / G;
+  for (I i = gid / G; i < nr; i += stride) {
+    const I row = (MODE == MODE_RROWS) ? (I)rows[i] : i;
+    const I e0 = (I)rp[row], e1 = (I)rp[row + 1];
+    Y a0 = 0, a1 = 0;
+    I k = e0 + lane;
+    for (; k + G < e1; k += 2 * G) {
+      a0 += (Y)val[k] * (Y)ldg(x + ci[k]);
+      a1 += (Y)val[k + G] * (Y)ldg(x + ci[k + G]);
+    }
+    if (k < e1) a0 += (Y)val[k] * (Y)ldg(x + ci[k]);
+    Y acc = a0 + a1;
 #pragma unroll
-    for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o, G);
+    for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(group_mask<G>(), acc, o, G);
     if (lane == 0) {
       if (MODE == MODE_AX) y[i] = acc;
       else if (MODE == MODE_RES) y[i] = b[i] - acc;
@@ -57,11 +73,38 @@ k_spmv(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci, const T* 
   }
 }
 
+// Lanes per row from the mean row length (measured on GB300 for FP64/FP32
+// CSR: ~46 non-zeros per row run best with 4 lanes, ~150 with 8).
 static int pick_group(int64_t nnz, int64_t nr) {
-  double avg = nr > 0 ? (double)nnz / (double)nr : 1.0;
-  int g = 2;
-  while (g < 32 && g * 2 <= avg) g *= 2;
-  return g;
+  const double avg = nr > 0 ? (double)nnz / (double)nr : 1.0;
+  if (avg < 6) return 1;
+  if (avg < 12) return 2;
+  if (avg < 64) return 4;
+  if (avg < 256) return 8;
+  return 16;
+}
+
+template <class T, class X, class Y, class I, int MODE>
+static void spmv_launch_i(const int64_t* rp, const int32_t* ci, const T* val, int64_t nr,
+                          int64_t nnz, const X* x, Y* y, const Y* b, const T* dinv,
+                          const int64_t* rows, cudaStream_t s) {
+  const int G = pick_group(nnz, nr);
+  const int tpb = 256;
+  const int64_t threads = nr * G;
+  const unsigned grid = (unsigned)std::min<int64_t>((threads + tpb - 1) / tpb, 152LL * 64);
+#define MGR_SPMV_CASE(g)                                                                    \
+  case g:                                                                                   \
+    MGR_LAUNCH k_spmv<T, X, Y, I, g, MODE><<<grid, tpb, 0, s>>>(rp, ci, val, (I)nr, x, y, b, \
+                                                                dinv, rows);                \
+    break;
+  switch (G) {
+    MGR_SPMV_CASE(1)
+    MGR_SPMV_CASE(2)
+    MGR_SPMV_CASE(4)
+    MGR_SPMV_CASE(8)
+    MGR_SPMV_CASE(16)
+  }
+#undef MGR_SPMV_CASE
 }
 
 template <class T, class X, class Y, int MODE>
@@ -69,22 +112,11 @@ static void spmv_launch(const int64_t* rp, const int32_t* ci, const T* val, int6
                         const X* x, Y* y, const Y* b, const T* dinv, const int64_t* rows,
                         cudaStream_t s) {
   if (nr <= 0) return;
-  const int G = pick_group(nnz, nr);
-  const int tpb = 256;
-  int64_t threads = nr * G;
-  unsigned grid = (unsigned)std::min<int64_t>((threads + tpb - 1) / tpb, 152LL * 64);
-#define MGR_SPMV_CASE(g)                                                                \
-  case g:                                                                               \
-    MGR_LAUNCH k_spmv<T, X, Y, g, MODE><<<grid, tpb, 0, s>>>(rp, ci, val, nr, x, y, b, dinv, rows); \
-    break;
-  switch (G) {
-    MGR_SPMV_CASE(2)
-    MGR_SPMV_CASE(4)
-    MGR_SPMV_CASE(8)
-    MGR_SPMV_CASE(16)
-    MGR_SPMV_CASE(32)
-  }
-#undef MGR_SPMV_CASE
+  // 32-bit offsets when every index (rows x lanes, nnz + 2 x lanes) fits
+  if (nnz + 64 < INT32_MAX && nr * 16 + 152LL * 64 * 256 < INT32_MAX)
+    spmv_launch_i<T, X, Y, int, MODE>(rp, ci, val, nr, nnz, x, y, b, dinv, rows, s);
+  else
+    spmv_launch_i<T, X, Y, int64_t, MODE>(rp, ci, val, nr, nnz, x, y, b, dinv, rows, s);
 }
 
 template <class T>
@@ -211,7 +243,7 @@ k_interp_correct(const int64_t* __restrict__ wrp, const int32_t* __restrict__ wc
       T acc = 0;
       for (int64_t k = wrp[t] + lane; k < wrp[t + 1]; k += G) acc += wv[k] * ldg(eC + wci[k]);
 #pragma unroll
-      for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o, G);
+      for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(group_mask<G>(), acc, o, G);
       if (lane == 0) {
         const int64_t d = Fidx ? Fidx[t] : t;
         if (base) z[d] = base[t] + acc;
@@ -375,6 +407,7 @@ static void mgr_level(Handle* h, int l, const T* v, T* z, cudaStream_t s) {
   unsigned grid = (unsigned)std::min<int64_t>(((nF + nC) * G + 255) / 256, 152LL * 64);
   const T* wv = vals<T>(L.W);
   switch (G) {
+    case 1: MGR_LAUNCH k_interp_correct<T, 1><<<grid, 256, 0, s>>>(L.W.rp, L.W.ci, wv, Fi, Ci, nF, nC, eC, zF_only, z); break;
     case 2: MGR_LAUNCH k_interp_correct<T, 2><<<grid, 256, 0, s>>>(L.W.rp, L.W.ci, wv, Fi, Ci, nF, nC, eC, zF_only, z); break;
     case 4: MGR_LAUNCH k_interp_correct<T, 4><<<grid, 256, 0, s>>>(L.W.rp, L.W.ci, wv, Fi, Ci, nF, nC, eC, zF_only, z); break;
     case 8: MGR_LAUNCH k_interp_correct<T, 8><<<grid, 256, 0, s>>>(L.W.rp, L.W.ci, wv, Fi, Ci, nF, nC, eC, zF_only, z); break;
@@ -383,11 +416,61 @@ static void mgr_level(Handle* h, int l, const T* v, T* z, cudaStream_t s) {
   }
 }
 
+// Capture mgr_level over the handle's fixed buffers into a graph (once, at
+// setup).  On failure the handle keeps launching the kernels directly.
+int capture_apply_graph(Handle* h) {
+  const bool mixed = h->opt.precision == MGR_MIXED;
+  if (!mixed) {
+    h->gin = h->pool.get<double>(h->n);
+    h->gout = h->pool.get<double>(h->n);
+    if (h->pool.err) return h->pool.err;
+  }
+  cudaStream_t cs;
+  MGR_TRY_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  const long long before = g_launches.load();
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    if (mixed) mgr_level<float>(h, 0, h->vin32, h->zout32, cs);
+    else mgr_level<double>(h, 0, h->gin, h->gout, cs);
+    e = cudaStreamEndCapture(cs, &graph);
+  }
+  g_launches.store(before);
+  if (e == cudaSuccess && graph) {
+    size_t nn = 0;
+    cudaGraphGetNodes(graph, nullptr, &nn);
+    std::vector<cudaGraphNode_t> nodes(nn);
+    cudaGraphGetNodes(graph, nodes.data(), &nn);
+    long long kernels = 0;
+    for (auto nd : nodes) {
+      cudaGraphNodeType t;
+      if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) kernels++;
+    }
+    e = cudaGraphInstantiate(&h->apply_exec, graph, 0);
+    if (e != cudaSuccess) h->apply_exec = nullptr;
+    h->apply_nodes = kernels;
+  }
+  if (graph) cudaGraphDestroy(graph);
+  cudaStreamDestroy(cs);
+  (void)cudaGetLastError();
+  return MGR_SUCCESS;
+}
+
 int apply_mgr(Handle* h, const double* v, double* z, cudaStream_t s) {
   if (h->opt.precision == MGR_MIXED) {
     MGR_LAUNCH k_cast<double, float><<<vgrid(h->n), 256, 0, s>>>(v, h->vin32, h->n);
-    mgr_level<float>(h, 0, h->vin32, h->zout32, s);
+    if (h->apply_exec) {
+      MGR_TRY_CUDA(cudaGraphLaunch(h->apply_exec, s));
+      g_launches += h->apply_nodes;
+    } else {
+      mgr_level<float>(h, 0, h->vin32, h->zout32, s);
+    }
     MGR_LAUNCH k_cast<float, double><<<vgrid(h->n), 256, 0, s>>>(h->zout32, z, h->n);
+  } else if (h->apply_exec) {
+    MGR_TRY_CUDA(cudaMemcpyAsync(h->gin, v, sizeof(double) * h->n, cudaMemcpyDeviceToDevice, s));
+    MGR_TRY_CUDA(cudaGraphLaunch(h->apply_exec, s));
+    g_launches += h->apply_nodes;
+    MGR_TRY_CUDA(cudaMemcpyAsync(z, h->gout, sizeof(double) * h->n, cudaMemcpyDeviceToDevice, s));
   } else {
     mgr_level<double>(h, 0, v, z, s);
   }
@@ -403,7 +486,13 @@ int apply_mgr32(Handle* h, const float* v, float* z, cudaStream_t s) {
 
 int apply_mgr_mixed_into(Handle* h, const double* v, float* z, cudaStream_t s) {
   MGR_LAUNCH k_cast<double, float><<<vgrid(h->n), 256, 0, s>>>(v, h->vin32, h->n);
-  mgr_level<float>(h, 0, h->vin32, z, s);
+  if (h->apply_exec) {
+    MGR_TRY_CUDA(cudaGraphLaunch(h->apply_exec, s));
+    g_launches += h->apply_nodes;
+    MGR_TRY_CUDA(cudaMemcpyAsync(z, h->zout32, sizeof(float) * h->n, cudaMemcpyDeviceToDevice, s));
+  } else {
+    mgr_level<float>(h, 0, h->vin32, z, s);
+  }
   MGR_TRY_CUDA(cudaGetLastError());
   return MGR_SUCCESS;
 }

@@ -72,7 +72,7 @@ void mgr_options_default(mgr_options_t* o, int two_phase) {
   o->global_sweeps[1] = two_phase ? 3 : 0;
   o->amg_theta = 0.25;
   o->amg_pmax = 4;
-  o->amg_max_coarse = 256;
+  o->amg_max_coarse = 64;
   o->amg_max_levels = 25;
   o->precision = MGR_FP64;
   o->seed = 0;
@@ -127,6 +127,8 @@ int mgr_setup(const mgr_matrix_t* A, const mgr_options_t* o, void* stream, mgr_h
   if (!rc) rc = build_mgr_hierarchy(h, A, s);
   if (!rc && o->precision == MGR_MIXED) rc = to_fp32(h, s);
   if (!rc) rc = alloc_apply_workspace(h, s);
+  if (!rc && cudaStreamSynchronize(s) != cudaSuccess) rc = MGR_ERR_CUDA;
+  if (!rc) rc = capture_apply_graph(h);
   cudaEventRecord(e1, s);
   if (cudaStreamSynchronize(s) != cudaSuccess && !rc) rc = MGR_ERR_CUDA;
   float ms = 0.f;
@@ -163,9 +165,10 @@ int mgr_destroy(mgr_handle_t hh) {
   Handle* h = reinterpret_cast<Handle*>(hh);
   if (!h) return MGR_SUCCESS;
   cudaDeviceSynchronize();
+  if (h->apply_exec) cudaGraphExecDestroy(h->apply_exec);
   for (auto& L : h->lev) delete L.famg;
   delete h->camg;
-  h->pool.free_all();
+  h->pool.free_all_async();
   if (h->hpinned) cudaFreeHost(h->hpinned);
   delete h;
   return MGR_SUCCESS;

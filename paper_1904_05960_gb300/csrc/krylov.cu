@@ -34,11 +34,14 @@ __device__ inline double block_sum(double v, double* sh) {
   return s;
 }
 
-// part[blk * nv + i] = sum over this block's chunk of V_i . w
+// part[blk * nv + i] = sum over this block's chunk of V_i . w (nv <= 64):
+// each warp reduces its partial for vector i into shared memory, one block
+// barrier at the end, then a fixed-order sum over the warps.
 __global__ void __launch_bounds__(KB) k_mdot(const double* __restrict__ V, int64_t ld, int nv,
                                              const double* __restrict__ w, int64_t n,
                                              double* __restrict__ part) {
-  __shared__ double sh[32];
+  __shared__ double sh[KB / 32][64];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
   const int64_t b0 = (int64_t)blockIdx.x * chunk;
   const int64_t b1 = min(n, b0 + chunk);
@@ -46,8 +49,15 @@ __global__ void __launch_bounds__(KB) k_mdot(const double* __restrict__ V, int64
     const double* vi = V + (int64_t)i * ld;
     double acc = 0.0;
     for (int64_t t = b0 + threadIdx.x; t < b1; t += blockDim.x) acc += vi[t] * w[t];
-    double s = block_sum(acc, sh);
-    if (threadIdx.x == 0) part[(int64_t)blockIdx.x * nv + i] = s;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
+    if (lane == 0) sh[wid][i] = acc;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < nv; i += blockDim.x) {
+    double s = 0.0;
+    for (int q = 0; q < KB / 32; q++) s += sh[q][i];
+    part[(int64_t)blockIdx.x * nv + i] = s;
   }
 }
 

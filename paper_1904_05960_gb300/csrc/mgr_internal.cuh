@@ -75,6 +75,12 @@ struct Pool {
       if (p) cudaFree(p);
     ptrs.clear();
   }
+  // stream-ordered release on the legacy default stream (no host wait)
+  void free_all_async() {
+    for (void* p : ptrs)
+      if (p) cudaFreeAsync(p, 0);
+    ptrs.clear();
+  }
 };
 
 // ----------------------------------------------------------------------------
@@ -145,6 +151,12 @@ struct Handle {
   // mixed-precision entry/exit buffers
   float* vin32 = nullptr;
   float* zout32 = nullptr;
+  // the whole preconditioner application captured once as a CUDA graph over
+  // fixed buffers (FP64: gin/gout; MGR_MIXED: vin32/zout32)
+  cudaGraphExec_t apply_exec = nullptr;
+  long long apply_nodes = 0;     // kernel nodes per replay
+  double* gin = nullptr;
+  double* gout = nullptr;
   // FGMRES workspace (lazily sized)
   int64_t kry_n = 0;
   int kry_m = 0;
@@ -175,6 +187,7 @@ int alloc_apply_workspace(Handle* h, cudaStream_t s);
 int apply_mgr(Handle* h, const double* v, double* z, cudaStream_t s);
 int apply_mgr32(Handle* h, const float* v, float* z, cudaStream_t s);
 int apply_mgr_mixed_into(Handle* h, const double* v, float* z, cudaStream_t s);
+int capture_apply_graph(Handle* h);
 int apply_vcycle64(Handle* h, Amg* g, const double* b, double* x, cudaStream_t s);
 // V-cycle with a caller-provided workspace of vcycle_ws_bytes() bytes
 size_t vcycle_ws_bytes(Handle* h, Amg* g);

@@ -310,6 +310,36 @@ k_spgemm_numeric(const int64_t* __restrict__ arp, const int32_t* __restrict__ ac
   }
 }
 
+// Thread per output row: the same per-entry order (ascending k) with the A
+// row walked sequentially by one thread; used when B's rows are short (fewer
+// lanes would be busy in the warp version).
+__global__ void __launch_bounds__(256)
+k_spgemm_numeric_thread(const int64_t* __restrict__ arp, const int32_t* __restrict__ aci,
+                        const double* __restrict__ av, int64_t nr, const int64_t* __restrict__ brp,
+                        const int32_t* __restrict__ bci, const double* __restrict__ bv,
+                        const int64_t* __restrict__ crp, const int32_t* __restrict__ cci,
+                        double* __restrict__ cv) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nr) return;
+  const int64_t c0 = crp[i], m = crp[i + 1] - c0;
+  const int32_t* cols = cci + c0;
+  double* out = cv + c0;
+  for (int64_t q = 0; q < m; q++) out[q] = 0.0;
+  for (int64_t t = arp[i]; t < arp[i + 1]; t++) {
+    const int32_t k = aci[t];
+    const double a = av[t];
+    const int64_t e0 = brp[k], e1 = brp[k + 1];
+    if (e0 == e1) continue;
+    // B row k and the output row are both ascending: each search starts
+    // where the previous one ended
+    int64_t pos = 0;
+    for (int64_t e = e0; e < e1; e++) {
+      pos += lower_bound_i32(cols + pos, m - pos, bci[e]);
+      out[pos] = __dadd_rn(out[pos], __dmul_rn(a, bv[e]));
+    }
+  }
+}
+
 static int spgemm(Pool& P, Pool& tmp, const Csr& A, const Csr& B, Csr& C, cudaStream_t s) {
   C.nr = A.nr;
   C.nc = B.nc;
@@ -330,8 +360,12 @@ static int spgemm(Pool& P, Pool& tmp, const Csr& A, const Csr& B, Csr& C, cudaSt
   C.v = P.get<double>(C.nnz);
   if (P.err) return P.err;
   MGR_LAUNCH k_spgemm_symbolic<true><<<g, SPG_WARPS * 32, sm, s>>>(A.rp, A.ci, A.nr, B.rp, B.ci, C.rp, C.ci);
-  MGR_LAUNCH k_spgemm_numeric<<<grid_for(A.nr, 8, 152 * 16), 256, 0, s>>>(A.rp, A.ci, A.v, A.nr, B.rp, B.ci,
-                                                                B.v, C.rp, C.ci, C.v);
+  if (B.nr > 0 && B.nnz < 12 * B.nr)
+    MGR_LAUNCH k_spgemm_numeric_thread<<<nblocks(A.nr, 256), 256, 0, s>>>(
+        A.rp, A.ci, A.v, A.nr, B.rp, B.ci, B.v, C.rp, C.ci, C.v);
+  else
+    MGR_LAUNCH k_spgemm_numeric<<<grid_for(A.nr, 8, 152 * 16), 256, 0, s>>>(
+        A.rp, A.ci, A.v, A.nr, B.rp, B.ci, B.v, C.rp, C.ci, C.v);
   MGR_TRY_CUDA(cudaGetLastError());
   return MGR_SUCCESS;
 }
@@ -842,9 +876,54 @@ __global__ void k_interp(const int64_t* __restrict__ rp, const int32_t* __restri
     });
     return;
   }
-  // select pmax largest |w| (ties: smaller column), repeated max search
+  // gather the strong-C (column, weight) pairs once; a row with more than
+  // ICAP of them falls back to recomputing the weights on each pass
+  constexpr int ICAP = 48;
+  int32_t jj[ICAP];
+  double ww[ICAP];
+  int nloc = 0;
+  if (r.nsc <= ICAP) {
+    for_strong_c(rp, ci, v, srp, sci, cf, i, r, [&](int32_t j, double w) {
+      if (nloc < ICAP) {
+        jj[nloc] = j;
+        ww[nloc] = w;
+        nloc++;
+      }
+    });
+  }
   int32_t sel[PMAX_CAP];
   int ns = 0;
+  if (nloc == r.nsc) {
+    // select pmax largest |w| (ties: smaller column), repeated max search
+    bool taken[ICAP];
+    for (int q = 0; q < nloc; q++) taken[q] = false;
+    for (int q = 0; q < pmax; q++) {
+      int b = -1;
+      for (int t = 0; t < nloc; t++) {
+        if (taken[t]) continue;
+        if (b < 0 || fabs(ww[t]) > fabs(ww[b]) || (fabs(ww[t]) == fabs(ww[b]) && jj[t] < jj[b])) b = t;
+      }
+      if (b >= 0) {
+        taken[b] = true;
+        ns++;
+      }
+    }
+    double sall = 0.0, skept = 0.0;
+    for (int t = 0; t < nloc; t++) {
+      sall = __dadd_rn(sall, ww[t]);
+      if (taken[t]) skept = __dadd_rn(skept, ww[t]);
+    }
+    for (int t = 0; t < nloc; t++) {
+      if (!taken[t]) continue;
+      if (o < oend) {
+        pci[o] = (int32_t)cmap[jj[t]];
+        pv[o] = (skept != 0.0) ? __dmul_rn(ww[t], __ddiv_rn(sall, skept)) : ww[t];
+      }
+      o++;
+    }
+    return;
+  }
+  // long rows: recompute the weights on each pass
   for (int q = 0; q < pmax; q++) {
     int32_t bj = -1;
     double bw = 0.0;
@@ -980,6 +1059,120 @@ __global__ void __launch_bounds__(1024) k_dense_lu_inverse(double* __restrict__ 
   }
 }
 
+// In-place Gauss-Jordan inversion with partial pivoting (ties: smaller row),
+// one thread block: row k is normalised, every other row updated, and the
+// recorded row interchanges are undone as column interchanges at the end.
+// `a` (n x n, row-major) holds A on entry and A^-1 on exit.  With SMEM the
+// matrix is worked on in shared memory (n^2 doubles must fit), else in place.
+template <bool SMEM>
+__global__ void __launch_bounds__(1024) k_dense_gj_inverse(double* __restrict__ ga, int n,
+                                                           int32_t* __restrict__ piv, int* err) {
+  extern __shared__ double dyn[];
+  double* f;
+  if constexpr (SMEM) {
+    f = dyn + (size_t)n * n;   // n values after the matrix
+  } else {
+    __shared__ double fst[1024];
+    f = fst;
+  }
+  __shared__ double wbest[32];
+  __shared__ int wbi[32];
+  __shared__ int sp;
+  __shared__ int fail;
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+  double* a = SMEM ? dyn : ga;
+  if (SMEM)
+    for (int64_t e = tid; e < (int64_t)n * n; e += nt) a[e] = ga[e];
+  if (tid == 0) fail = 0;
+  __syncthreads();
+  for (int k = 0; k < n; k++) {
+    double best = -1.0;
+    int bi = n;
+    for (int i = k + tid; i < n; i += nt) {
+      double x = fabs(a[(int64_t)i * n + k]);
+      if (x > best || (x == best && i < bi)) {
+        best = x;
+        bi = i;
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      double ob = __shfl_xor_sync(0xffffffffu, best, o);
+      int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ob > best || (ob == best && oi < bi)) {
+        best = ob;
+        bi = oi;
+      }
+    }
+    if (lane == 0) {
+      wbest[wid] = best;
+      wbi[wid] = bi;
+    }
+    __syncthreads();
+    if (wid == 0) {
+      best = (lane < nw) ? wbest[lane] : -1.0;
+      bi = (lane < nw) ? wbi[lane] : n;
+      for (int o = 16; o > 0; o >>= 1) {
+        double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi < bi)) {
+          best = ob;
+          bi = oi;
+        }
+      }
+      if (lane == 0) {
+        sp = bi;
+        piv[k] = bi;
+        if (!(best > 0.0)) fail = 1;
+      }
+    }
+    __syncthreads();
+    if (fail) break;
+    const int p = sp;
+    if (p != k)
+      for (int j = tid; j < n; j += nt) {
+        double t = a[(int64_t)k * n + j];
+        a[(int64_t)k * n + j] = a[(int64_t)p * n + j];
+        a[(int64_t)p * n + j] = t;
+      }
+    __syncthreads();
+    const double pinv = 1.0 / a[(int64_t)k * n + k];
+    __syncthreads();
+    for (int j = tid; j < n; j += nt) {
+      double x = (j == k) ? 1.0 : a[(int64_t)k * n + j];
+      a[(int64_t)k * n + j] = x * pinv;
+    }
+    for (int i = tid; i < n; i += nt) {
+      f[i] = (i == k) ? 0.0 : a[(int64_t)i * n + k];
+      if (i != k) a[(int64_t)i * n + k] = 0.0;
+    }
+    __syncthreads();
+    const double* rowk = a + (int64_t)k * n;
+    for (int i = wid; i < n; i += nw) {
+      if (i == k) continue;
+      const double fi = f[i];
+      double* ri = a + (int64_t)i * n;
+      for (int j = lane; j < n; j += 32) ri[j] -= fi * rowk[j];
+    }
+    __syncthreads();
+  }
+  if (fail) {
+    if (tid == 0) dev_fail(err, DEV_ZERO_DIAG);
+    return;
+  }
+  for (int k = n - 1; k >= 0; k--) {
+    const int p = piv[k];
+    if (p != k)
+      for (int i = tid; i < n; i += nt) {
+        double t = a[(int64_t)i * n + k];
+        a[(int64_t)i * n + k] = a[(int64_t)i * n + p];
+        a[(int64_t)i * n + p] = t;
+      }
+    __syncthreads();
+  }
+  if (SMEM)
+    for (int64_t e = tid; e < (int64_t)n * n; e += nt) ga[e] = a[e];
+}
+
 static int dense_coarsest(Handle* h, Amg* g, Pool& tmp, cudaStream_t s) {
   Pool& P = h->pool;
   const Csr& A = g->lev.back().A;
@@ -991,6 +1184,20 @@ static int dense_coarsest(Handle* h, Amg* g, Pool& tmp, cudaStream_t s) {
   int32_t* piv = tmp.get<int32_t>(n);
   g->inv = P.get<double>(n * n);
   if (P.err || tmp.err) return P.err ? P.err : tmp.err;
+  if (n <= 1024) {
+    MGR_TRY_CUDA(cudaMemsetAsync(g->inv, 0, sizeof(double) * n * n, s));
+    MGR_LAUNCH k_csr_to_dense<<<nblocks(n, 256), 256, 0, s>>>(A.rp, A.ci, A.v, n, g->inv);
+    const size_t sm = sizeof(double) * ((size_t)n * (size_t)n + (size_t)n);
+    if (sm <= 220 * 1024) {
+      MGR_TRY_CUDA(cudaFuncSetAttribute(k_dense_gj_inverse<true>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+      MGR_LAUNCH k_dense_gj_inverse<true><<<1, 1024, sm, s>>>(g->inv, (int)n, piv, h->derr);
+    } else {
+      MGR_LAUNCH k_dense_gj_inverse<false><<<1, 1024, 0, s>>>(g->inv, (int)n, piv, h->derr);
+    }
+    MGR_TRY_CUDA(cudaGetLastError());
+    return check_dev_err(h->derr, s);
+  }
   MGR_TRY_CUDA(cudaMemsetAsync(d, 0, sizeof(double) * n * n, s));
   MGR_LAUNCH k_csr_to_dense<<<nblocks(n, 256), 256, 0, s>>>(A.rp, A.ci, A.v, n, d);
   MGR_LAUNCH k_dense_lu_inverse<<<1, 1024, 0, s>>>(d, (int)n, piv, g->inv, h->derr);
