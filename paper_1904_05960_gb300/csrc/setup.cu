@@ -107,6 +107,21 @@ static int rowptr_from_counts(const int64_t* cnt, int64_t* rp, int64_t n, int64_
 
 __device__ inline void dev_fail(int* err, int code) { atomicCAS(err, DEV_OK, code); }
 
+// Magnitude and sign tests on the IEEE bit pattern (integer pipe; the FP64
+// pipe of GB300 is narrow).  For non-NaN x, y: |x| > |y| exactly when
+// absbits(x) > absbits(y); x < 0 exactly when the sign bit is set and x != 0.
+__device__ __forceinline__ uint64_t absbits(double x) {
+  return (uint64_t)__double_as_longlong(x) & 0x7fffffffffffffffull;
+}
+__device__ __forceinline__ bool is_neg(double x) {
+  const uint64_t b = (uint64_t)__double_as_longlong(x);
+  return (b >> 63) && (b << 1);
+}
+__device__ __forceinline__ bool is_pos(double x) {
+  const uint64_t b = (uint64_t)__double_as_longlong(x);
+  return !(b >> 63) && b;
+}
+
 static int check_dev_err(int* derr, cudaStream_t s) {
   int e = 0;
   MGR_TRY(read_back(&e, derr, s));
@@ -340,6 +355,97 @@ k_spgemm_numeric_thread(const int64_t* __restrict__ arp, const int32_t* __restri
   }
 }
 
+// Warp per output row, lane-dense: with LPG = the row's longest B row rounded
+// up to a power of two (<= 32), the warp takes 32/LPG consecutive A entries at
+// a time, one lane per product.  Products that land on the same output slot in
+// one step are found with __match_any_sync and added by the lowest such lane in
+// lane order, which is ascending k; every other lane adds its own product.  So
+// each entry is the same ascending-k sum from 0.0 as the sequential product,
+// and the FP64 adds run on all lanes at once.  The output row is staged in
+// shared memory when it has at most GRP_CAP entries; a row whose longest B row
+// exceeds 32 takes the one-B-row-at-a-time path.
+static constexpr int GRP_CAP = 512;
+static constexpr int GRP_WARPS = 4;
+struct GrpWarp {
+  int32_t cols[GRP_CAP];
+  double acc[GRP_CAP];
+  double lval[32];
+};
+
+__global__ void __launch_bounds__(GRP_WARPS * 32)
+k_spgemm_numeric_grp(const int64_t* __restrict__ arp, const int32_t* __restrict__ aci,
+                     const double* __restrict__ av, int64_t nr, const int64_t* __restrict__ brp,
+                     const int32_t* __restrict__ bci, const double* __restrict__ bv,
+                     const int64_t* __restrict__ crp, const int32_t* __restrict__ cci,
+                     double* __restrict__ cv) {
+  __shared__ GrpWarp sh[GRP_WARPS];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  GrpWarp& W = sh[wid];
+  for (int64_t i = (int64_t)blockIdx.x * GRP_WARPS + wid; i < nr; i += (int64_t)gridDim.x * GRP_WARPS) {
+    const int64_t c0 = crp[i];
+    const int m = (int)(crp[i + 1] - c0);
+    const int64_t a0 = arp[i], a1 = arp[i + 1];
+    int longest = 0;
+    for (int64_t t = a0 + lane; t < a1; t += 32) {
+      const int32_t k = aci[t];
+      longest = max(longest, (int)(brp[k + 1] - brp[k]));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) longest = max(longest, __shfl_xor_sync(FULL, longest, o));
+    const bool staged = m <= GRP_CAP;
+    const int32_t* cols = staged ? W.cols : cci + c0;
+    double* acc = staged ? W.acc : cv + c0;
+    for (int q = lane; q < m; q += 32) {
+      if (staged) W.cols[q] = cci[c0 + q];
+      acc[q] = 0.0;
+    }
+    __syncwarp();
+    if (longest > 32) {
+      for (int64_t t = a0; t < a1; t++) {
+        const int32_t k = aci[t];
+        const double a = av[t];
+        for (int64_t e = brp[k] + lane; e < brp[k + 1]; e += 32) {
+          const int pos = (int)lower_bound_i32(cols, m, bci[e]);
+          acc[pos] = __dadd_rn(acc[pos], __dmul_rn(a, bv[e]));
+        }
+        __syncwarp();
+      }
+    } else {
+      int sh2 = 0;
+      while ((1 << sh2) < longest) sh2++;
+      const int groups = 32 >> sh2;
+      const int g = lane >> sh2, e = lane & ((1 << sh2) - 1);
+      for (int64_t t0 = a0; t0 < a1; t0 += groups) {
+        const int64_t t = t0 + g;
+        bool valid = false;
+        int pos = 0;
+        double prod = 0.0;
+        if (t < a1) {
+          const int32_t k = aci[t];
+          const int64_t eb = brp[k];
+          if (e < brp[k + 1] - eb) {
+            prod = __dmul_rn(av[t], bv[eb + e]);
+            pos = (int)lower_bound_i32(cols, m, bci[eb + e]);
+            valid = true;
+          }
+        }
+        W.lval[lane] = prod;
+        const unsigned grp = __match_any_sync(FULL, valid ? pos : -1 - lane);
+        __syncwarp();
+        if (valid && lane == __ffs(grp) - 1) {
+          double x = acc[pos];
+          for (unsigned mm = grp; mm; mm &= mm - 1) x = __dadd_rn(x, W.lval[__ffs(mm) - 1]);
+          acc[pos] = x;
+        }
+        __syncwarp();
+      }
+    }
+    if (staged)
+      for (int q = lane; q < m; q += 32) cv[c0 + q] = W.acc[q];
+    __syncwarp();
+  }
+}
+
 static int spgemm(Pool& P, Pool& tmp, const Csr& A, const Csr& B, Csr& C, cudaStream_t s) {
   C.nr = A.nr;
   C.nc = B.nc;
@@ -361,7 +467,7 @@ static int spgemm(Pool& P, Pool& tmp, const Csr& A, const Csr& B, Csr& C, cudaSt
   if (P.err) return P.err;
   MGR_LAUNCH k_spgemm_symbolic<true><<<g, SPG_WARPS * 32, sm, s>>>(A.rp, A.ci, A.nr, B.rp, B.ci, C.rp, C.ci);
   if (B.nr > 0 && B.nnz < 12 * B.nr)
-    MGR_LAUNCH k_spgemm_numeric_thread<<<nblocks(A.nr, 256), 256, 0, s>>>(
+    MGR_LAUNCH k_spgemm_numeric_grp<<<grid_for(A.nr, GRP_WARPS, 152 * 32), GRP_WARPS * 32, 0, s>>>(
         A.rp, A.ci, A.v, A.nr, B.rp, B.ci, B.v, C.rp, C.ci, C.v);
   else
     MGR_LAUNCH k_spgemm_numeric<<<grid_for(A.nr, 8, 152 * 16), 256, 0, s>>>(
@@ -515,8 +621,8 @@ __global__ void k_drop_mark(const int64_t* __restrict__ rp, const int32_t* __res
       int64_t best = -1;
       for (int64_t k = b; k < e; k++) {
         if (keep[k]) continue;
-        if (best < 0 || fabs(v[k]) > fabs(v[best]) ||
-            (fabs(v[k]) == fabs(v[best]) && ci[k] < ci[best]))
+        if (best < 0 || absbits(v[k]) > absbits(v[best]) ||
+            (absbits(v[k]) == absbits(v[best]) && ci[k] < ci[best]))
           best = k;
       }
       if (best < 0) break;
@@ -678,38 +784,56 @@ __global__ void k_l1_inv(const int64_t* __restrict__ rp, const int32_t* __restri
 }
 
 // Strength of connection on negative couplings between equal components.
+// Warp per row.  m = max_j (-a_ij) over equal-component off-diagonals; S_i is
+// empty unless some such a_ij is negative and non-zero, and then m is the
+// largest |a_ij| among the negative ones: an exact integer max over the bit
+// patterns (order-free).  Strong entries are compacted with ballots, so S_i
+// keeps A's column order.
 template <bool FILL>
-__global__ void k_strength(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                           const double* __restrict__ v, const int32_t* __restrict__ comp,
-                           int64_t n, double theta, int64_t* __restrict__ cnt_or_rp,
-                           int32_t* __restrict__ sci) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const int32_t ci_ = comp[i];
-  double m = 0.0;
-  bool any = false;
-  for (int64_t k = rp[i]; k < rp[i + 1]; k++) {
-    int32_t j = ci[k];
-    if (j == i || comp[j] != ci_) continue;
-    double neg = -v[k];
-    if (!any || neg > m) {
-      m = neg;
-      any = true;
-    }
-  }
-  int64_t o = FILL ? cnt_or_rp[i] : 0;
-  if (any && m > 0.0) {
-    double thr = __dmul_rn(theta, m);
-    for (int64_t k = rp[i]; k < rp[i + 1]; k++) {
-      int32_t j = ci[k];
-      if (j == i || comp[j] != ci_) continue;
-      if (-v[k] >= thr) {
-        if (FILL) sci[o] = j;
-        o++;
+__global__ void __launch_bounds__(256)
+k_strength(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+           const double* __restrict__ v, const int32_t* __restrict__ comp, int64_t n,
+           double theta, int64_t* __restrict__ cnt_or_rp, int32_t* __restrict__ sci) {
+  const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+  for (int64_t i = (int64_t)blockIdx.x * wpb + (threadIdx.x >> 5); i < n;
+       i += (int64_t)gridDim.x * wpb) {
+    const int32_t c_i = comp[i];
+    const int64_t e0 = rp[i], e1 = rp[i + 1];
+    unsigned long long mb = 0;
+    for (int64_t k = e0 + lane; k < e1; k += 32) {
+      const int32_t j = ci[k];
+      const double a = v[k];
+      if (j != i && comp[j] == c_i && is_neg(a)) {
+        const unsigned long long ab = absbits(a);
+        if (ab > mb) mb = ab;
       }
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long y = __shfl_xor_sync(FULL, mb, o);
+      if (y > mb) mb = y;
+    }
+    int64_t o = FILL ? cnt_or_rp[i] : 0;
+    if (mb != 0) {
+      const double thr = __dmul_rn(theta, __longlong_as_double((long long)mb));
+      const uint64_t tb = absbits(thr);
+      for (int64_t k0 = e0; k0 < e1; k0 += 32) {
+        const int64_t k = k0 + lane;
+        bool strong = false;
+        int32_t j = -1;
+        if (k < e1) {
+          j = ci[k];
+          const double a = v[k];
+          if (j != i && comp[j] == c_i)
+            strong = (tb != 0) ? (is_neg(a) && absbits(a) >= tb) : (-a >= thr);
+        }
+        const unsigned bal = __ballot_sync(FULL, strong);
+        if (FILL && strong) sci[o + __popc(bal & ((1u << lane) - 1u))] = j;
+        o += __popc(bal);
+      }
+    }
+    if (!FILL && lane == 0) cnt_or_rp[i] = o;
   }
-  if (!FILL) cnt_or_rp[i] = o;
 }
 
 __global__ void k_pmis_init(const int64_t* __restrict__ srp, const int64_t* __restrict__ strp,
@@ -800,10 +924,10 @@ __device__ inline InterpRow interp_row(const int64_t* rp, const int32_t* ci, con
     bool strong = (sq < se && sci[sq] == j);
     if (comp[j] != comp[i]) continue;
     bool sc = strong && cf[j] == 1;
-    if (a < 0.0) {
+    if (is_neg(a)) {
       sn = __dadd_rn(sn, a);
       if (sc) cn = __dadd_rn(cn, a);
-    } else if (a > 0.0) {
+    } else if (is_pos(a)) {
       sp = __dadd_rn(sp, a);
       if (sc) cp = __dadd_rn(cp, a);
     }
@@ -830,7 +954,7 @@ __device__ inline void for_strong_c(const int64_t* rp, const int32_t* ci, const 
     while (sq < se && sci[sq] < j) sq++;
     if (!(sq < se && sci[sq] == j) || cf[j] != 1) continue;
     double a = v[k];
-    double coef = (a < 0.0) ? r.alpha : r.beta;
+    double coef = is_neg(a) ? r.alpha : r.beta;
     double w = __ddiv_rn(-__dmul_rn(coef, a), r.dd);
     f(j, w);
   }
@@ -839,14 +963,12 @@ __device__ inline void for_strong_c(const int64_t* rp, const int32_t* ci, const 
 static constexpr int PMAX_CAP = 16;
 
 template <bool FILL>
-__global__ void k_interp(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                         const double* __restrict__ v, const int64_t* __restrict__ srp,
-                         const int32_t* __restrict__ sci, const int32_t* __restrict__ comp,
-                         const int8_t* __restrict__ cf, const int64_t* __restrict__ cmap,
-                         int64_t n, int pmax, int64_t* __restrict__ cnt_or_rp,
-                         int32_t* __restrict__ pci, double* __restrict__ pv) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+__device__ void interp_row_seq(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                               const double* __restrict__ v, const int64_t* __restrict__ srp,
+                               const int32_t* __restrict__ sci, const int32_t* __restrict__ comp,
+                               const int8_t* __restrict__ cf, const int64_t* __restrict__ cmap,
+                               int64_t i, int pmax, int64_t* __restrict__ cnt_or_rp,
+                               int32_t* __restrict__ pci, double* __restrict__ pv) {
   if (cf[i] == 1) {
     if (FILL) {
       int64_t o = cnt_or_rp[i];
@@ -901,7 +1023,9 @@ __global__ void k_interp(const int64_t* __restrict__ rp, const int32_t* __restri
       int b = -1;
       for (int t = 0; t < nloc; t++) {
         if (taken[t]) continue;
-        if (b < 0 || fabs(ww[t]) > fabs(ww[b]) || (fabs(ww[t]) == fabs(ww[b]) && jj[t] < jj[b])) b = t;
+        if (b < 0 || absbits(ww[t]) > absbits(ww[b]) ||
+            (absbits(ww[t]) == absbits(ww[b]) && jj[t] < jj[b]))
+          b = t;
       }
       if (b >= 0) {
         taken[b] = true;
@@ -930,7 +1054,7 @@ __global__ void k_interp(const int64_t* __restrict__ rp, const int32_t* __restri
     for_strong_c(rp, ci, v, srp, sci, cf, i, r, [&](int32_t j, double w) {
       for (int t = 0; t < ns; t++)
         if (sel[t] == j) return;
-      if (bj < 0 || fabs(w) > fabs(bw) || (fabs(w) == fabs(bw) && j < bj)) {
+      if (bj < 0 || absbits(w) > absbits(bw) || (absbits(w) == absbits(bw) && j < bj)) {
         bj = j;
         bw = w;
       }
@@ -957,6 +1081,204 @@ __global__ void k_interp(const int64_t* __restrict__ rp, const int32_t* __restri
         break;
       }
   });
+}
+
+// Thread per row (lane-dense FP64 sums across 32 rows; for large levels).
+template <bool FILL>
+__global__ void __launch_bounds__(128)
+k_interp_thread(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                const double* __restrict__ v, const int64_t* __restrict__ srp,
+                const int32_t* __restrict__ sci, const int32_t* __restrict__ comp,
+                const int8_t* __restrict__ cf, const int64_t* __restrict__ cmap, int64_t n, int pmax,
+                int64_t* __restrict__ cnt_or_rp, int32_t* __restrict__ pci, double* __restrict__ pv) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) interp_row_seq<FILL>(rp, ci, v, srp, sci, comp, cf, cmap, i, pmax, cnt_or_rp, pci, pv);
+}
+
+// Warp per row (small levels: few rows, long rows).  Lanes stage the row
+// (value, column, flags) in shared memory
+// and form the weights (independent divisions) in parallel; lane 0 keeps every
+// order-sensitive sum sequential in ascending column order, as the direct
+// interpolation definition reads; the P_max largest |w| are picked by an exact
+// warp argmax (ties: smaller column).  Rows longer than IW_CAP entries (or S
+// rows longer than IW_SCAP) are done by lane 0 with the sequential row code.
+static constexpr int IW_CAP = 256;
+static constexpr int IW_SCAP = 256;
+static constexpr int IW_WARPS = 4;
+struct InterpWarp {
+  double a[IW_CAP];
+  double w[IW_CAP];
+  int32_t col[IW_CAP];
+  int32_t srow[IW_SCAP];
+  uint8_t fl[IW_CAP];     // bit0 diagonal, bit1 same component, bit2 strong C, bit3 selected
+  double bc[4];           // dd, alpha, beta, scale
+  int flag;
+};
+
+template <bool FILL>
+__global__ void __launch_bounds__(IW_WARPS * 32)
+k_interp(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+         const double* __restrict__ v, const int64_t* __restrict__ srp,
+         const int32_t* __restrict__ sci, const int32_t* __restrict__ comp,
+         const int8_t* __restrict__ cf, const int64_t* __restrict__ cmap, int64_t n, int pmax,
+         int64_t* __restrict__ cnt_or_rp, int32_t* __restrict__ pci, double* __restrict__ pv) {
+  __shared__ InterpWarp sh[IW_WARPS];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  InterpWarp& W = sh[wid];
+  for (int64_t i = (int64_t)blockIdx.x * IW_WARPS + wid; i < n; i += (int64_t)gridDim.x * IW_WARPS) {
+    if (cf[i] == 1) {
+      if (lane == 0) {
+        if (FILL) {
+          const int64_t o = cnt_or_rp[i];
+          pci[o] = (int32_t)cmap[i];
+          pv[o] = 1.0;
+        } else {
+          cnt_or_rp[i] = 1;
+        }
+      }
+      continue;
+    }
+    const int64_t e0 = rp[i], e1 = rp[i + 1], sb = srp[i], se = srp[i + 1];
+    const int L = (int)(e1 - e0), SL = (int)(se - sb);
+    if (L > IW_CAP || SL > IW_SCAP) {
+      if (lane == 0)
+        interp_row_seq<FILL>(rp, ci, v, srp, sci, comp, cf, cmap, i, pmax, cnt_or_rp, pci, pv);
+      __syncwarp();
+      continue;
+    }
+    for (int q = lane; q < SL; q += 32) W.srow[q] = sci[sb + q];
+    __syncwarp();
+    const int32_t c_i = comp[i];
+    int nsc = 0;
+    for (int t0 = 0; t0 < L; t0 += 32) {
+      const int t = t0 + lane;
+      bool sc = false;
+      if (t < L) {
+        const int32_t j = ci[e0 + t];
+        const double a = v[e0 + t];
+        int lo = 0, hi = SL;
+        while (lo < hi) {
+          const int mid = (lo + hi) >> 1;
+          if (W.srow[mid] < j) lo = mid + 1;
+          else hi = mid;
+        }
+        const bool strong = lo < SL && W.srow[lo] == j;
+        sc = (j != i) && strong && cf[j] == 1;
+        W.a[t] = a;
+        W.col[t] = j;
+        W.fl[t] = (uint8_t)((j == i ? 1 : 0) | (comp[j] == c_i ? 2 : 0) | (sc ? 4 : 0));
+      }
+      nsc += __popc(__ballot_sync(FULL, sc));
+    }
+    const bool trunc = pmax > 0 && nsc > pmax;
+    if (!FILL) {
+      if (lane == 0) cnt_or_rp[i] = (nsc == 0) ? 0 : (trunc ? pmax : nsc);
+      __syncwarp();
+      continue;
+    }
+    if (nsc == 0) {
+      __syncwarp();
+      continue;
+    }
+    __syncwarp();
+    if (lane == 0) {
+      double sn = 0.0, sp = 0.0, cn = 0.0, cp = 0.0, aii = 0.0;
+      for (int t = 0; t < L; t++) {
+        const uint8_t f = W.fl[t];
+        const double a = W.a[t];
+        if (f & 1) {
+          aii = a;
+          continue;
+        }
+        if (!(f & 2)) continue;
+        const bool sc = f & 4;
+        if (is_neg(a)) {
+          sn = __dadd_rn(sn, a);
+          if (sc) cn = __dadd_rn(cn, a);
+        } else if (is_pos(a)) {
+          sp = __dadd_rn(sp, a);
+          if (sc) cp = __dadd_rn(cp, a);
+        }
+      }
+      W.bc[0] = (cp == 0.0) ? __dadd_rn(aii, sp) : aii;
+      W.bc[1] = (cn != 0.0) ? __ddiv_rn(sn, cn) : 0.0;
+      W.bc[2] = (cp != 0.0) ? __ddiv_rn(sp, cp) : 0.0;
+    }
+    __syncwarp();
+    const double dd = W.bc[0], alpha = W.bc[1], beta = W.bc[2];
+    for (int t = lane; t < L; t += 32)
+      if (W.fl[t] & 4) {
+        const double a = W.a[t];
+        W.w[t] = __ddiv_rn(-__dmul_rn(is_neg(a) ? alpha : beta, a), dd);
+      }
+    __syncwarp();
+    int64_t o = cnt_or_rp[i];
+    if (!trunc) {
+      for (int t0 = 0; t0 < L; t0 += 32) {
+        const int t = t0 + lane;
+        const bool sc = t < L && (W.fl[t] & 4);
+        const unsigned bal = __ballot_sync(FULL, sc);
+        if (sc) {
+          const int64_t d = o + __popc(bal & ((1u << lane) - 1u));
+          pci[d] = (int32_t)cmap[W.col[t]];
+          pv[d] = W.w[t];
+        }
+        o += __popc(bal);
+      }
+      __syncwarp();
+      continue;
+    }
+    // pmax rounds of an exact warp argmax of |w| (ties: smaller column)
+    for (int q = 0; q < pmax; q++) {
+      unsigned long long bk = 0;
+      int bt = -1;
+      for (int t = lane; t < L; t += 32) {
+        if ((W.fl[t] & 12) != 4) continue;          // strong C, not yet selected
+        const unsigned long long k = absbits(W.w[t]);
+        if (bt < 0 || k > bk) {
+          bk = k;
+          bt = t;
+        }
+      }
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        const unsigned long long ok = __shfl_xor_sync(FULL, bk, off);
+        const int ot = __shfl_xor_sync(FULL, bt, off);
+        if (ot >= 0 && (bt < 0 || ok > bk || (ok == bk && ot < bt))) {
+          bk = ok;
+          bt = ot;
+        }
+      }
+      if (lane == 0 && bt >= 0) W.fl[bt] |= 8;
+      __syncwarp();
+    }
+    if (lane == 0) {
+      double sall = 0.0, skept = 0.0;
+      for (int t = 0; t < L; t++) {
+        const uint8_t f = W.fl[t];
+        if (!(f & 4)) continue;
+        sall = __dadd_rn(sall, W.w[t]);
+        if (f & 8) skept = __dadd_rn(skept, W.w[t]);
+      }
+      W.flag = (skept != 0.0);
+      W.bc[3] = (skept != 0.0) ? __ddiv_rn(sall, skept) : 1.0;
+    }
+    __syncwarp();
+    const bool scale = W.flag;
+    const double fct = W.bc[3];
+    for (int t0 = 0; t0 < L; t0 += 32) {
+      const int t = t0 + lane;
+      const bool kept = t < L && (W.fl[t] & 8);
+      const unsigned bal = __ballot_sync(FULL, kept);
+      if (kept) {
+        const int64_t d = o + __popc(bal & ((1u << lane) - 1u));
+        pci[d] = (int32_t)cmap[W.col[t]];
+        pv[d] = scale ? __dmul_rn(W.w[t], fct) : W.w[t];
+      }
+      o += __popc(bal);
+    }
+    __syncwarp();
+  }
 }
 
 __global__ void k_coarse_comp(const int8_t* __restrict__ cf, const int64_t* __restrict__ cmap,
@@ -1238,12 +1560,12 @@ int build_amg(Handle* h, const Csr& A0, const int32_t* comp0, int slot, Amg** ou
     L->S.nr = L->S.nc = n;
     L->S.rp = P.get<int64_t>(n + 1);
     if (tmp.err || P.err) { rc = tmp.err ? tmp.err : P.err; break; }
-    MGR_LAUNCH k_strength<false><<<nblocks(n, 128), 128, 0, s>>>(L->A.rp, L->A.ci, L->A.v, L->comp, n,
+    MGR_LAUNCH k_strength<false><<<grid_for(n, 8, 152 * 16), 256, 0, s>>>(L->A.rp, L->A.ci, L->A.v, L->comp, n,
                                                      o.amg_theta, cnt, nullptr);
     if ((rc = rowptr_from_counts(cnt, L->S.rp, n, &L->S.nnz, s, tmp))) break;
     L->S.ci = P.get<int32_t>(L->S.nnz);
     if (P.err) { rc = P.err; break; }
-    MGR_LAUNCH k_strength<true><<<nblocks(n, 128), 128, 0, s>>>(L->A.rp, L->A.ci, L->A.v, L->comp, n,
+    MGR_LAUNCH k_strength<true><<<grid_for(n, 8, 152 * 16), 256, 0, s>>>(L->A.rp, L->A.ci, L->A.v, L->comp, n,
                                                     o.amg_theta, L->S.rp, L->S.ci);
     Csr ST;
     if ((rc = transpose(tmp, tmp, L->S, ST, false, false, s))) break;
@@ -1278,14 +1600,27 @@ int build_amg(Handle* h, const Csr& A0, const int32_t* comp0, int slot, Amg** ou
     L->P.nc = nc;
     L->P.rp = P.get<int64_t>(n + 1);
     if (P.err) { rc = P.err; break; }
-    MGR_LAUNCH k_interp<false><<<nblocks(n, 128), 128, 0, s>>>(L->A.rp, L->A.ci, L->A.v, L->S.rp, L->S.ci,
+    // FP64 work is lane-dense in the thread-per-row form; the warp form wins
+    // only where a level has too few rows to fill the GPU
+    const bool big = n >= 20000;
+    if (big)
+      MGR_LAUNCH k_interp_thread<false><<<nblocks(n, 128), 128, 0, s>>>(L->A.rp, L->A.ci, L->A.v, L->S.rp, L->S.ci,
+                                                   L->comp, L->cf, cmap, n, o.amg_pmax, cnt,
+                                                   nullptr, nullptr);
+    else
+      MGR_LAUNCH k_interp<false><<<grid_for(n, IW_WARPS, 152 * 32), IW_WARPS * 32, 0, s>>>(L->A.rp, L->A.ci, L->A.v, L->S.rp, L->S.ci,
                                                    L->comp, L->cf, cmap, n, o.amg_pmax, cnt,
                                                    nullptr, nullptr);
     if ((rc = rowptr_from_counts(cnt, L->P.rp, n, &L->P.nnz, s, tmp))) break;
     L->P.ci = P.get<int32_t>(L->P.nnz);
     L->P.v = P.get<double>(L->P.nnz);
     if (P.err) { rc = P.err; break; }
-    MGR_LAUNCH k_interp<true><<<nblocks(n, 128), 128, 0, s>>>(L->A.rp, L->A.ci, L->A.v, L->S.rp, L->S.ci,
+    if (big)
+      MGR_LAUNCH k_interp_thread<true><<<nblocks(n, 128), 128, 0, s>>>(L->A.rp, L->A.ci, L->A.v, L->S.rp, L->S.ci,
+                                                  L->comp, L->cf, cmap, n, o.amg_pmax, L->P.rp,
+                                                  L->P.ci, L->P.v);
+    else
+      MGR_LAUNCH k_interp<true><<<grid_for(n, IW_WARPS, 152 * 32), IW_WARPS * 32, 0, s>>>(L->A.rp, L->A.ci, L->A.v, L->S.rp, L->S.ci,
                                                   L->comp, L->cf, cmap, n, o.amg_pmax, L->P.rp,
                                                   L->P.ci, L->P.v);
     if ((rc = transpose(P, tmp, L->P, L->R, true, true, s))) break;
