@@ -29,8 +29,13 @@ __device__ __forceinline__ T ldg(const T* p) {
 //   MODE_ADD    y = y + A x
 //   MODE_GRES   y[t] = b[rows[t]] - (A x)[t]           (A has one row per t)
 //   MODE_RROWS  y[t] = b[rows[t]] - (A x)[rows[t]]     (a subset of A's rows)
+//   MODE_RES0   y = b - A (dinv .* b)     (first l1-Jacobi sweep from zero fused in;
+//                                          x = b, gathers dinv too)
+//   MODE_PROL0  y = dinv .* b + A x       (prolongation onto that first sweep;
+//                                          b, dinv are the fine-level vectors)
 // ----------------------------------------------------------------------------
-enum { MODE_AX = 0, MODE_RES = 1, MODE_SMOOTH = 2, MODE_ADD = 3, MODE_GRES = 4, MODE_RROWS = 5 };
+enum { MODE_AX = 0, MODE_RES = 1, MODE_SMOOTH = 2, MODE_ADD = 3, MODE_GRES = 4, MODE_RROWS = 5,
+       MODE_RES0 = 6, MODE_PROL0 = 7 };
 
 // Lanes of a G-lane group inside its warp (G divides 32; groups are aligned).
 template <int G>
@@ -54,11 +59,23 @@ k_spmv(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci, const T* 
     const I e0 = (I)rp[row], e1 = (I)rp[row + 1];
     Y a0 = 0, a1 = 0;
     I k = e0 + lane;
-    for (; k + G < e1; k += 2 * G) {
-      a0 += (Y)val[k] * (Y)ldg(x + ci[k]);
-      a1 += (Y)val[k + G] * (Y)ldg(x + ci[k + G]);
+    if (MODE == MODE_RES0) {
+      for (; k + G < e1; k += 2 * G) {
+        const int32_t c0 = ci[k], c1 = ci[k + G];
+        a0 += (Y)val[k] * ((Y)ldg(dinv + c0) * (Y)ldg(x + c0));
+        a1 += (Y)val[k + G] * ((Y)ldg(dinv + c1) * (Y)ldg(x + c1));
+      }
+      if (k < e1) {
+        const int32_t c0 = ci[k];
+        a0 += (Y)val[k] * ((Y)ldg(dinv + c0) * (Y)ldg(x + c0));
+      }
+    } else {
+      for (; k + G < e1; k += 2 * G) {
+        a0 += (Y)val[k] * (Y)ldg(x + ci[k]);
+        a1 += (Y)val[k + G] * (Y)ldg(x + ci[k + G]);
+      }
+      if (k < e1) a0 += (Y)val[k] * (Y)ldg(x + ci[k]);
     }
-    if (k < e1) a0 += (Y)val[k] * (Y)ldg(x + ci[k]);
     Y acc = a0 + a1;
 #pragma unroll
     for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(group_mask<G>(), acc, o, G);
@@ -69,6 +86,8 @@ k_spmv(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci, const T* 
       else if (MODE == MODE_ADD) y[i] += acc;
       else if (MODE == MODE_GRES) y[i] = b[rows[i]] - acc;
       else if (MODE == MODE_RROWS) y[i] = b[row] - acc;
+      else if (MODE == MODE_RES0) y[i] = b[i] - acc;
+      else if (MODE == MODE_PROL0) y[i] = (Y)dinv[i] * b[i] + acc;
     }
   }
 }
@@ -77,11 +96,16 @@ k_spmv(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci, const T* 
 // CSR: ~46 non-zeros per row run best with 4 lanes, ~150 with 8).
 static int pick_group(int64_t nnz, int64_t nr) {
   const double avg = nr > 0 ? (double)nnz / (double)nr : 1.0;
-  if (avg < 6) return 1;
-  if (avg < 12) return 2;
-  if (avg < 64) return 4;
-  if (avg < 256) return 8;
-  return 16;
+  int g;
+  if (avg < 6) g = 1;
+  else if (avg < 12) g = 2;
+  else if (avg < 64) g = 4;
+  else if (avg < 256) g = 8;
+  else g = 16;
+  // small matrices: latency-bound, so spend more lanes per row (while a row
+  // still has entries for them) until about half the GPU's threads are busy
+  while (g < 32 && nr * g < 152LL * 1024 && g < avg) g *= 2;
+  return g;
 }
 
 template <class T, class X, class Y, class I, int MODE>
@@ -103,6 +127,7 @@ static void spmv_launch_i(const int64_t* rp, const int32_t* ci, const T* val, in
     MGR_SPMV_CASE(4)
     MGR_SPMV_CASE(8)
     MGR_SPMV_CASE(16)
+    MGR_SPMV_CASE(32)
   }
 #undef MGR_SPMV_CASE
 }
@@ -308,8 +333,19 @@ int alloc_apply_workspace(Handle* h, cudaStream_t s) {
 // ----------------------------------------------------------------------------
 // AMG V-cycle from a zero guess (one l1-Jacobi sweep down, one up)
 // ----------------------------------------------------------------------------
+// Levels with fewer rows fold the first sweep into their sparse products; above
+// it the extra gathered multiply per non-zero (FP64 pipe) costs more than the
+// separate vector kernel.
+static constexpr int64_t FUSE_SCALE_ROWS = 65536;
 template <class T>
-static void vcycle(Amg* g, int k, const T* b, T* x, cudaStream_t s) {
+struct WsLevel {
+  T *b, *x, *t, *r;
+};
+
+// One V-cycle on levels k.. of g; W[k'] holds the level vectors (for k' > k:
+// b, x; for every non-coarsest level: t, r).
+template <class T>
+static void vcycle_on(Amg* g, int k, const T* b, T* x, const WsLevel<T>* W, cudaStream_t s) {
   AmgLevel& L = g->lev[k];
   const int64_t n = L.A.nr;
   if (k == (int)g->lev.size() - 1) {
@@ -317,16 +353,34 @@ static void vcycle(Amg* g, int k, const T* b, T* x, cudaStream_t s) {
     MGR_LAUNCH k_dense_gemv<T><<<grid_for(n * 32, 256), 256, 0, s>>>(inv, n, b, x);
     return;
   }
-  AmgLevel& C = g->lev[k + 1];
   const T* dinv = pick<T>(L.dinv, L.dinvf);
-  T* t = (T*)L.t;
-  T* r = (T*)L.r;
-  MGR_LAUNCH k_scale<T><<<vgrid(n), 256, 0, s>>>(dinv, b, t, n);
-  spmv<T, MODE_RES>(L.A, t, r, b, nullptr, nullptr, s);
-  spmv<T, MODE_AX>(L.R, r, (T*)C.b, nullptr, nullptr, nullptr, s);
-  vcycle<T>(g, k + 1, (const T*)C.b, (T*)C.x, s);
-  spmv<T, MODE_ADD>(L.P, (const T*)C.x, t, nullptr, nullptr, nullptr, s);
+  T* t = W[k].t;
+  T* r = W[k].r;
+  T* cb = W[k + 1].b;
+  T* cx = W[k + 1].x;
+  if (n < FUSE_SCALE_ROWS) {
+    // small level: fold t = dinv .* b into the residual and the prolongation
+    spmv<T, MODE_RES0>(L.A, b, r, b, dinv, nullptr, s);
+    spmv<T, MODE_AX>(L.R, r, cb, nullptr, nullptr, nullptr, s);
+    vcycle_on<T>(g, k + 1, cb, cx, W, s);
+    spmv<T, MODE_PROL0>(L.P, cx, t, b, dinv, nullptr, s);
+  } else {
+    MGR_LAUNCH k_scale<T><<<vgrid(n), 256, 0, s>>>(dinv, b, t, n);
+    spmv<T, MODE_RES>(L.A, t, r, b, nullptr, nullptr, s);
+    spmv<T, MODE_AX>(L.R, r, cb, nullptr, nullptr, nullptr, s);
+    vcycle_on<T>(g, k + 1, cb, cx, W, s);
+    spmv<T, MODE_ADD>(L.P, cx, t, nullptr, nullptr, nullptr, s);
+  }
   spmv<T, MODE_SMOOTH>(L.A, t, x, b, dinv, nullptr, s);
+}
+
+// V-cycle with the handle's level workspace
+template <class T>
+static void vcycle(Amg* g, int k, const T* b, T* x, cudaStream_t s) {
+  WsLevel<T> W[32];
+  for (size_t q = 0; q < g->lev.size() && q < 32; q++)
+    W[q] = WsLevel<T>{(T*)g->lev[q].b, (T*)g->lev[q].x, (T*)g->lev[q].t, (T*)g->lev[q].r};
+  vcycle_on<T>(g, k, b, x, W, s);
 }
 
 // ----------------------------------------------------------------------------
@@ -513,7 +567,7 @@ int apply_vcycle64(Handle* h, Amg* g, const double* b, double* x, cudaStream_t s
 
 // ----------------------------------------------------------------------------
 // V-cycle with caller-provided workspace (used by the allocation-free entry
-// point in noalloc.cu).  Same kernels and order as vcycle<T>; the level vectors
+// point in noalloc.cu).  The same vcycle_on<T> as mgr_vcycle; the level vectors
 // t, r (and b, x below the top level) are carved from `ws`, each 256-byte
 // aligned.  Every workspace vector is written before it is read.
 // ----------------------------------------------------------------------------
@@ -530,31 +584,6 @@ size_t vcycle_ws_bytes(Handle* h, Amg* g) {
   }
   if (h->opt.precision == MGR_MIXED) total += 2 * ws_align((size_t)g->lev[0].A.nr * sizeof(float));
   return total;
-}
-
-template <class T>
-struct WsLevel {
-  T *b, *x, *t, *r;
-};
-
-template <class T>
-static void vcycle_ws(Amg* g, int k, const T* b, T* x, WsLevel<T>* W, cudaStream_t s) {
-  AmgLevel& L = g->lev[k];
-  const int64_t n = L.A.nr;
-  if (k == (int)g->lev.size() - 1) {
-    const T* inv = pick<T>(g->inv, g->invf);
-    MGR_LAUNCH k_dense_gemv<T><<<grid_for(n * 32, 256), 256, 0, s>>>(inv, n, b, x);
-    return;
-  }
-  const T* dinv = pick<T>(L.dinv, L.dinvf);
-  T* t = W[k].t;
-  T* r = W[k].r;
-  MGR_LAUNCH k_scale<T><<<vgrid(n), 256, 0, s>>>(dinv, b, t, n);
-  spmv<T, MODE_RES>(L.A, t, r, b, nullptr, nullptr, s);
-  spmv<T, MODE_AX>(L.R, r, W[k + 1].b, nullptr, nullptr, nullptr, s);
-  vcycle_ws<T>(g, k + 1, W[k + 1].b, W[k + 1].x, W, s);
-  spmv<T, MODE_ADD>(L.P, W[k + 1].x, t, nullptr, nullptr, nullptr, s);
-  spmv<T, MODE_SMOOTH>(L.A, t, x, b, dinv, nullptr, s);
 }
 
 template <class T>
@@ -584,12 +613,12 @@ int apply_vcycle64_ws(Handle* h, Amg* g, const double* b, double* x, void* ws, c
     float* b32 = (float*)p; p += ws_align((size_t)n * sizeof(float));
     float* x32 = (float*)p; p += ws_align((size_t)n * sizeof(float));
     MGR_LAUNCH k_cast<double, float><<<vgrid(n), 256, 0, s>>>(b, b32, n);
-    vcycle_ws<float>(g, 0, b32, x32, W.data(), s);
+    vcycle_on<float>(g, 0, b32, x32, W.data(), s);
     MGR_LAUNCH k_cast<float, double><<<vgrid(n), 256, 0, s>>>(x32, x, n);
   } else {
     std::vector<WsLevel<double>> W;
     carve<double>(g, p, W);
-    vcycle_ws<double>(g, 0, b, x, W.data(), s);
+    vcycle_on<double>(g, 0, b, x, W.data(), s);
   }
   MGR_TRY_CUDA(cudaGetLastError());
   return MGR_SUCCESS;
