@@ -543,7 +543,8 @@ int apply_mgr_mixed_into(Handle* h, const double* v, float* z, cudaStream_t s) {
   if (h->apply_exec) {
     MGR_TRY_CUDA(cudaGraphLaunch(h->apply_exec, s));
     g_launches += h->apply_nodes;
-    MGR_TRY_CUDA(cudaMemcpyAsync(z, h->zout32, sizeof(float) * h->n, cudaMemcpyDeviceToDevice, s));
+    if (z != h->zout32)
+      MGR_TRY_CUDA(cudaMemcpyAsync(z, h->zout32, sizeof(float) * h->n, cudaMemcpyDeviceToDevice, s));
   } else {
     mgr_level<float>(h, 0, h->vin32, z, s);
   }

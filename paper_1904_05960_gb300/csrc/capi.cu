@@ -2,6 +2,7 @@
 #include <cuda_runtime.h>
 
 #include <chrono>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 
@@ -9,6 +10,26 @@
 
 namespace mgr {
 std::atomic<long long> g_launches{0};
+Trace g_trace;
+
+static double now_ms() {
+  return std::chrono::duration<double, std::milli>(
+             std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+void Trace::start(cudaStream_t st) {
+  on = getenv("MGR_TRACE") != nullptr;
+  s = st;
+  if (!on) return;
+  cudaStreamSynchronize(s);
+  t0 = last = now_ms();
+}
+void Trace::mark(const char* what, int a, int b) {
+  if (!on) return;
+  cudaStreamSynchronize(s);
+  const double t = now_ms();
+  fprintf(stderr, "mgr_trace %-28s %3d %3d  %8.3f ms  (total %8.3f)\n", what, a, b, t - last, t - t0);
+  last = t;
+}
 
 int fgmres_run(Handle* h, const mgr_matrix_t* A, const double* b, double* x,
                const fgmres_options_t* o, fgmres_info_t* info, cudaStream_t s);
@@ -121,14 +142,18 @@ int mgr_setup(const mgr_matrix_t* A, const mgr_options_t* o, void* stream, mgr_h
   cudaEventCreate(&e1);
   cudaEventRecord(e0, s);
   int rc = MGR_SUCCESS;
+  g_trace.start(s);
   h->derr = h->pool.get<int>(1);
   if (!h->derr) rc = h->pool.err;
   if (!rc && cudaMemsetAsync(h->derr, 0, sizeof(int), s) != cudaSuccess) rc = MGR_ERR_CUDA;
   if (!rc) rc = build_mgr_hierarchy(h, A, s);
+  g_trace.mark("hierarchy");
   if (!rc && o->precision == MGR_MIXED) rc = to_fp32(h, s);
   if (!rc) rc = alloc_apply_workspace(h, s);
   if (!rc && cudaStreamSynchronize(s) != cudaSuccess) rc = MGR_ERR_CUDA;
+  g_trace.mark("fp32 copies + workspace");
   if (!rc) rc = capture_apply_graph(h);
+  g_trace.mark("apply graph capture");
   cudaEventRecord(e1, s);
   if (cudaStreamSynchronize(s) != cudaSuccess && !rc) rc = MGR_ERR_CUDA;
   float ms = 0.f;

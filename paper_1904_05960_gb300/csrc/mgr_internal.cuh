@@ -75,10 +75,10 @@ struct Pool {
       if (p) cudaFree(p);
     ptrs.clear();
   }
-  // stream-ordered release on the legacy default stream (no host wait)
-  void free_all_async() {
+  // stream-ordered release (no host wait); default: the legacy stream
+  void free_all_async(cudaStream_t fs = 0) {
     for (void* p : ptrs)
-      if (p) cudaFreeAsync(p, 0);
+      if (p) cudaFreeAsync(p, fs);
     ptrs.clear();
   }
 };
@@ -217,6 +217,18 @@ inline unsigned grid_for(int64_t work, int per_block, int cap = 152 * 32) {
   if (g > cap) g = cap;
   return (unsigned)g;
 }
+
+// Setup phase trace: with the environment variable MGR_TRACE set, phase
+// boundaries synchronise the stream and print the elapsed wall time (ms) to
+// stderr.  Off by default (no synchronisation added).
+struct Trace {
+  bool on = false;
+  cudaStream_t s = nullptr;
+  double t0 = 0.0, last = 0.0;
+  void start(cudaStream_t st);
+  void mark(const char* what, int a = -1, int b = -1);
+};
+extern Trace g_trace;
 
 template <class T>
 inline int read_back(T* host, const T* dev, cudaStream_t s) {

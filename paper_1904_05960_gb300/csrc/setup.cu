@@ -140,34 +140,32 @@ static inline unsigned nblocks(int64_t n, int tpb) {
 }
 
 // Row subset and column relabelling: out = A[rows, cols] with colmap[j] the new
-// index of column j (monotone in j) or -1.
-__global__ void k_extract_count(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                                const int64_t* __restrict__ rows, int64_t nrows,
-                                const int32_t* __restrict__ colmap, int64_t* __restrict__ cnt) {
-  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= nrows) return;
-  int64_t r = rows ? rows[t] : t;
-  int64_t c = 0;
-  for (int64_t k = rp[r]; k < rp[r + 1]; k++) c += (colmap[ci[k]] >= 0);
-  cnt[t] = c;
-}
-
-__global__ void k_extract_fill(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                               const double* __restrict__ v, const int64_t* __restrict__ rows,
-                               int64_t nrows, const int32_t* __restrict__ colmap,
-                               const int64_t* __restrict__ orp, int32_t* __restrict__ oci,
-                               double* __restrict__ ov) {
-  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= nrows) return;
-  int64_t r = rows ? rows[t] : t;
-  int64_t o = orp[t];
-  for (int64_t k = rp[r]; k < rp[r + 1]; k++) {
-    int32_t c = colmap[ci[k]];
-    if (c >= 0) {
-      oci[o] = c;
-      ov[o] = v[k];
-      o++;
+// index of column j (monotone in j) or -1.  Warp per row; ballots keep the
+// column order.
+template <bool FILL>
+__global__ void __launch_bounds__(256)
+k_extract(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+          const double* __restrict__ v, const int64_t* __restrict__ rows, int64_t nrows,
+          const int32_t* __restrict__ colmap, int64_t* __restrict__ cnt_or_rp,
+          int32_t* __restrict__ oci, double* __restrict__ ov) {
+  const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+  for (int64_t t = (int64_t)blockIdx.x * wpb + (threadIdx.x >> 5); t < nrows;
+       t += (int64_t)gridDim.x * wpb) {
+    const int64_t r = rows ? rows[t] : t;
+    int64_t o = FILL ? cnt_or_rp[t] : 0;
+    for (int64_t k0 = rp[r]; k0 < rp[r + 1]; k0 += 32) {
+      const int64_t k = k0 + lane;
+      int32_t c = -1;
+      if (k < rp[r + 1]) c = colmap[ci[k]];
+      const unsigned bal = __ballot_sync(FULL, c >= 0);
+      if (FILL && c >= 0) {
+        const int64_t d = o + __popc(bal & ((1u << lane) - 1u));
+        oci[d] = c;
+        ov[d] = v[k];
+      }
+      o += __popc(bal);
     }
+    if (!FILL && lane == 0) cnt_or_rp[t] = o;
   }
 }
 
@@ -189,13 +187,14 @@ static int extract(Pool& P, Pool& tmp, const Csr& A, const int64_t* rows, int64_
   out.nc = ncols;
   out.rp = P.get<int64_t>(nrows + 1);
   if (!out.rp) return P.err;
-  MGR_LAUNCH k_extract_count<<<nblocks(nrows, 256), 256, 0, s>>>(A.rp, A.ci, rows, nrows, colmap, cnt);
+  MGR_LAUNCH k_extract<false><<<grid_for(nrows, 8, 152 * 16), 256, 0, s>>>(A.rp, A.ci, A.v, rows, nrows, colmap, cnt,
+                                                                  nullptr, nullptr);
   MGR_TRY(rowptr_from_counts(cnt, out.rp, nrows, &out.nnz, s, tmp));
   out.ci = P.get<int32_t>(out.nnz);
   out.v = P.get<double>(out.nnz);
   if (P.err) return P.err;
-  MGR_LAUNCH k_extract_fill<<<nblocks(nrows, 256), 256, 0, s>>>(A.rp, A.ci, A.v, rows, nrows, colmap,
-                                                      out.rp, out.ci, out.v);
+  MGR_LAUNCH k_extract<true><<<grid_for(nrows, 8, 152 * 16), 256, 0, s>>>(A.rp, A.ci, A.v, rows, nrows, colmap,
+                                                                 out.rp, out.ci, out.v);
   MGR_TRY_CUDA(cudaGetLastError());
   return MGR_SUCCESS;
 }
@@ -249,7 +248,9 @@ k_spgemm_symbolic(const int64_t* __restrict__ arp, const int32_t* __restrict__ a
     int64_t running = 0;
     const int64_t out0 = FILL ? cnt_or_rp[i] : 0;
     for (int64_t w0 = lo; hi >= 0 && w0 <= hi; w0 += SPG_WBITS) {
-      for (int q = lane; q < SPG_WORDS; q += 32) bm[q] = 0u;
+      int64_t wend = (hi - w0) / 32 + 1;           // words that can hold bits
+      if (wend > SPG_WORDS) wend = SPG_WORDS;
+      for (int q = lane; q < wend; q += 32) bm[q] = 0u;
       __syncwarp();
       const int64_t w1 = w0 + SPG_WBITS;
       for (int64_t t = a0 + lane; t < a1; t += 32) {
@@ -263,8 +264,6 @@ k_spgemm_symbolic(const int64_t* __restrict__ arp, const int32_t* __restrict__ a
         }
       }
       __syncwarp();
-      int64_t wend = (hi - w0) / 32 + 1;           // words that can hold bits
-      if (wend > SPG_WORDS) wend = SPG_WORDS;
       for (int64_t q0 = 0; q0 < wend; q0 += 32) {
         int64_t q = q0 + lane;
         uint32_t word = (q < wend) ? bm[q] : 0u;
@@ -531,8 +530,7 @@ static int transpose(Pool& P, Pool& tmp, const Csr& A, Csr& T, bool values, bool
   MGR_TRY_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int64_t) * (A.nc + 1), s));
   MGR_TRY_CUDA(cudaMemsetAsync(cur, 0, sizeof(int64_t) * (A.nc + 1), s));
   MGR_LAUNCH k_count_cols<<<grid_for(A.nnz, 256), 256, 0, s>>>(A.ci, A.nnz, cnt);
-  int64_t tot = 0;
-  MGR_TRY(rowptr_from_counts(cnt, T.rp, A.nc, &tot, s, tmp));
+  MGR_TRY(scan_exclusive(cnt, T.rp, A.nc, s, tmp));   // total is A.nnz: no readback
   MGR_LAUNCH k_transpose_fill<<<nblocks(A.nr, 256), 256, 0, s>>>(A.rp, A.ci, A.v, A.nr, T.rp, cur, T.ci, T.v);
   if (sorted) MGR_LAUNCH k_sort_rows<<<nblocks(T.nr, 128), 128, 0, s>>>(T.rp, T.nr, T.ci, T.v);
   MGR_TRY_CUDA(cudaGetLastError());
@@ -765,22 +763,34 @@ __global__ void k_block_inv(const int64_t* __restrict__ rp, const int32_t* __res
 // ============================================================================
 // AMG setup (Sec. 6 solver settings)
 // ============================================================================
-// l1-Jacobi diagonal d_i = a_ii + sum_{j != i} |a_ij| (Baker et al. 2011).
-__global__ void k_l1_inv(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                         const double* __restrict__ v, int64_t n, double* __restrict__ dinv, int* err) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  double off = 0.0, aii = 0.0;
-  for (int64_t k = rp[i]; k < rp[i + 1]; k++) {
-    if (ci[k] == i) aii = v[k];
-    else off = __dadd_rn(off, fabs(v[k]));
+// l1-Jacobi diagonal d_i = a_ii + sum_{j != i} |a_ij| (Baker et al. 2011),
+// warp per row.  Only the smoother uses it (no integer decision depends on
+// it), so the sum is a warp tree.
+__global__ void __launch_bounds__(256)
+k_l1_inv(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+         const double* __restrict__ v, int64_t n, double* __restrict__ dinv, int* err) {
+  const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+  for (int64_t i = (int64_t)blockIdx.x * wpb + (threadIdx.x >> 5); i < n; i += (int64_t)gridDim.x * wpb) {
+    double off = 0.0, aii = 0.0;
+    for (int64_t k = rp[i] + lane; k < rp[i + 1]; k += 32) {
+      const double a = v[k];
+      if (ci[k] == i) aii = a;
+      else off += fabs(a);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      off += __shfl_xor_sync(FULL, off, o);
+      aii += __shfl_xor_sync(FULL, aii, o);
+    }
+    if (lane == 0) {
+      double d = aii + off;
+      if (d == 0.0) {
+        dev_fail(err, DEV_ZERO_DIAG);
+        d = 1.0;
+      }
+      dinv[i] = 1.0 / d;
+    }
   }
-  double d = __dadd_rn(aii, off);
-  if (d == 0.0) {
-    dev_fail(err, DEV_ZERO_DIAG);
-    d = 1.0;
-  }
-  dinv[i] = 1.0 / d;
 }
 
 // Strength of connection on negative couplings between equal components.
@@ -1553,8 +1563,9 @@ int build_amg(Handle* h, const Csr& A0, const int32_t* comp0, int slot, Amg** ou
     const int64_t n = L->A.nr;
     L->dinv = P.get<double>(n);
     if (!L->dinv) { rc = P.err; break; }
-    MGR_LAUNCH k_l1_inv<<<nblocks(n, 256), 256, 0, s>>>(L->A.rp, L->A.ci, L->A.v, n, L->dinv, h->derr);
+    MGR_LAUNCH k_l1_inv<<<grid_for(n, 8, 152 * 16), 256, 0, s>>>(L->A.rp, L->A.ci, L->A.v, n, L->dinv, h->derr);
     if (n <= o.amg_max_coarse || k + 1 >= o.amg_max_levels || k + 1 >= 32) break;
+    g_trace.mark("amg l1", slot, k);
     // strength graph
     int64_t* cnt = tmp.get<int64_t>(n + 1);
     L->S.nr = L->S.nc = n;
@@ -1567,6 +1578,7 @@ int build_amg(Handle* h, const Csr& A0, const int32_t* comp0, int slot, Amg** ou
     if (P.err) { rc = P.err; break; }
     MGR_LAUNCH k_strength<true><<<grid_for(n, 8, 152 * 16), 256, 0, s>>>(L->A.rp, L->A.ci, L->A.v, L->comp, n,
                                                     o.amg_theta, L->S.rp, L->S.ci);
+    g_trace.mark("amg strength", slot, k);
     Csr ST;
     if ((rc = transpose(tmp, tmp, L->S, ST, false, false, s))) break;
     // PMIS
@@ -1576,16 +1588,21 @@ int build_amg(Handle* h, const Csr& A0, const int32_t* comp0, int slot, Amg** ou
     unsigned long long* und = tmp.get<unsigned long long>(1);
     if (tmp.err || P.err) { rc = tmp.err ? tmp.err : P.err; break; }
     MGR_LAUNCH k_pmis_init<<<nblocks(n, 256), 256, 0, s>>>(L->S.rp, ST.rp, n, o.seed, slot, k, w, L->cf);
-    for (int round = 0; round < 100000; round++) {
-      MGR_LAUNCH k_pmis_select<<<nblocks(n, 256), 256, 0, s>>>(L->S.rp, L->S.ci, ST.rp, ST.ci, w, L->cf, n, newc);
-      MGR_LAUNCH k_pmis_apply_c<<<nblocks(n, 256), 256, 0, s>>>(newc, n, L->cf);
-      cudaMemsetAsync(und, 0, sizeof(unsigned long long), s);
-      MGR_LAUNCH k_pmis_mark_f<<<nblocks(n, 256), 256, 0, s>>>(L->S.rp, L->S.ci, n, L->cf, und);
+    // synchronous rounds, checked every 4th: a round after the last
+    // undecided point is gone changes nothing
+    for (int round = 0; round < 100000; round += 4) {
+      for (int q = 0; q < 4; q++) {
+        MGR_LAUNCH k_pmis_select<<<nblocks(n, 256), 256, 0, s>>>(L->S.rp, L->S.ci, ST.rp, ST.ci, w, L->cf, n, newc);
+        MGR_LAUNCH k_pmis_apply_c<<<nblocks(n, 256), 256, 0, s>>>(newc, n, L->cf);
+        cudaMemsetAsync(und, 0, sizeof(unsigned long long), s);
+        MGR_LAUNCH k_pmis_mark_f<<<nblocks(n, 256), 256, 0, s>>>(L->S.rp, L->S.ci, n, L->cf, und);
+      }
       unsigned long long left = 0;
       if ((rc = read_back(&left, und, s))) break;
       if (left == 0) break;
     }
     if (rc) break;
+    g_trace.mark("amg pmis", slot, k);
     // coarse numbering
     int64_t* flag = tmp.get<int64_t>(n + 1);
     int64_t* cmap = tmp.get<int64_t>(n + 1);
@@ -1623,9 +1640,12 @@ int build_amg(Handle* h, const Csr& A0, const int32_t* comp0, int slot, Amg** ou
       MGR_LAUNCH k_interp<true><<<grid_for(n, IW_WARPS, 152 * 32), IW_WARPS * 32, 0, s>>>(L->A.rp, L->A.ci, L->A.v, L->S.rp, L->S.ci,
                                                   L->comp, L->cf, cmap, n, o.amg_pmax, L->P.rp,
                                                   L->P.ci, L->P.v);
+    g_trace.mark("amg interp", slot, k);
     if ((rc = transpose(P, tmp, L->P, L->R, true, true, s))) break;
+    g_trace.mark("amg transpose P", slot, k);
     Csr AP;
     if ((rc = spgemm(tmp, tmp, L->A, L->P, AP, s))) break;
+    g_trace.mark("amg A*P", slot, k);
     g->lev.emplace_back();
     L = &g->lev[k];
     AmgLevel& C = g->lev[k + 1];
@@ -1634,11 +1654,12 @@ int build_amg(Handle* h, const Csr& A0, const int32_t* comp0, int slot, Amg** ou
     if (P.err) { rc = P.err; break; }
     MGR_LAUNCH k_coarse_comp<<<nblocks(n, 256), 256, 0, s>>>(L->cf, cmap, L->comp, n, C.comp);
     MGR_TRY_CUDA(cudaGetLastError());
+    g_trace.mark("amg R*(AP)", slot, k);
   }
   if (rc == MGR_SUCCESS) rc = check_dev_err(h->derr, s);
   if (rc == MGR_SUCCESS) rc = dense_coarsest(h, g, tmp, s);
-  cudaStreamSynchronize(s);
-  tmp.free_all();
+  g_trace.mark("amg coarsest inverse", slot, (int)g->lev.size() - 1);
+  tmp.free_all_async(s);
   return rc;
 }
 
@@ -1701,8 +1722,10 @@ static int setup_level(Handle* h, int l, const int32_t* label, const int32_t* no
   MGR_LAUNCH k_dff_and_w<<<nblocks(L.nF, 256), 256, 0, s>>>(L.A.rp, L.A.ci, L.A.v, L.Fidx, L.nF, Afc.rp, Afc.v,
                                                   T.v, L.W.v, L.dFinv, h->derr);
   MGR_TRY(check_dev_err(h->derr, s));
+  g_trace.mark("mgr split/extract/W", l);
   // A_cor = A_CF T
   MGR_TRY(spgemm(P, tmp, L.Acf, T, L.cor, s));
+  g_trace.mark("mgr A_CF*T", l);
   // next-level labels (needed for G's own-point rule)
   *nlabel = P.get<int32_t>(L.nC);
   *nnode = P.get<int32_t>(L.nC);
@@ -1739,6 +1762,7 @@ static int setup_level(Handle* h, int l, const int32_t* label, const int32_t* no
                                                       L.corkept.ci, L.corkept.v, L.nC, Snext.rp,
                                                       Snext.ci, Snext.v);
   MGR_TRY_CUDA(cudaGetLastError());
+  g_trace.mark("mgr drop + S", l);
   // F-relaxation AMG on A_FF
   if (L.frelax == MGR_FRELAX_AMG_VCYCLE && L.frelax_sweeps > 0) {
     int32_t* fcomp = tmp.get<int32_t>(L.nF);
@@ -1798,8 +1822,7 @@ int build_mgr_hierarchy(Handle* h, const mgr_matrix_t* A, cudaStream_t s) {
     Csr S;
     int32_t *nl = nullptr, *nn = nullptr, *nc = nullptr;
     rc = setup_level(h, l, label, node, comp, tmp, s, S, &nl, &nn, &nc);
-    cudaStreamSynchronize(s);
-    tmp.free_all();
+    tmp.free_all_async(s);
     if (rc) break;
     cur = S;
     label = nl;
@@ -1815,8 +1838,7 @@ int build_mgr_hierarchy(Handle* h, const mgr_matrix_t* A, cudaStream_t s) {
   if (!zero) return tmp.err;
   MGR_TRY_CUDA(cudaMemsetAsync(zero, 0, sizeof(int32_t) * cur.nr, s));
   rc = build_amg(h, cur, zero, L, &h->camg, s);
-  cudaStreamSynchronize(s);
-  tmp.free_all();
+  tmp.free_all_async(s);
   return rc;
 }
 
