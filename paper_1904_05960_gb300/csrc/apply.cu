@@ -333,10 +333,10 @@ int alloc_apply_workspace(Handle* h, cudaStream_t s) {
 // ----------------------------------------------------------------------------
 // AMG V-cycle from a zero guess (one l1-Jacobi sweep down, one up)
 // ----------------------------------------------------------------------------
-// Levels with fewer rows fold the first sweep into their sparse products; above
-// it the extra gathered multiply per non-zero (FP64 pipe) costs more than the
-// separate vector kernel.
-static constexpr int64_t FUSE_SCALE_ROWS = 65536;
+// Levels with fewer non-zeros fold the first sweep into their sparse products;
+// above it the extra gathered multiply per non-zero (FP64 pipe) costs more than
+// the separate vector kernel it saves.
+static constexpr int64_t FUSE_SCALE_NNZ = 2000000;
 template <class T>
 struct WsLevel {
   T *b, *x, *t, *r;
@@ -358,7 +358,7 @@ static void vcycle_on(Amg* g, int k, const T* b, T* x, const WsLevel<T>* W, cuda
   T* r = W[k].r;
   T* cb = W[k + 1].b;
   T* cx = W[k + 1].x;
-  if (n < FUSE_SCALE_ROWS) {
+  if (L.A.nnz < FUSE_SCALE_NNZ) {
     // small level: fold t = dinv .* b into the residual and the prolongation
     spmv<T, MODE_RES0>(L.A, b, r, b, dinv, nullptr, s);
     spmv<T, MODE_AX>(L.R, r, cb, nullptr, nullptr, nullptr, s);
