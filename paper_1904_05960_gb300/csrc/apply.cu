@@ -8,6 +8,7 @@
 // product that produces it instead of running separate vector passes.
 #include <cuda_runtime.h>
 
+#include <cstdio>
 #include <vector>
 
 #include "mgr_internal.cuh"
@@ -223,28 +224,54 @@ __global__ void k_cast(const A* __restrict__ a, B* __restrict__ b, int64_t n) {
     b[i] = (B)a[i];
 }
 
-// Point-block Jacobi (global smoother, Sec. 5.3 Remarks): one thread per block.
+// Point-block Jacobi (global smoother, Sec. 5.3 Remarks).
 //   first sweep from zero: z = B^-1 v
 //   later sweeps        : zout = zin + B^-1 (v - A zin)
-template <class T, bool FIRST>
-__global__ void k_block_jacobi(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                               const T* __restrict__ val, const int64_t* __restrict__ bstart,
-                               const T* __restrict__ binv, int64_t nblk, const T* __restrict__ v,
-                               const T* __restrict__ zin, T* __restrict__ zout) {
-  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nblk; k += (int64_t)gridDim.x * blockDim.x) {
+// Each CTA owns BJ_BLOCKS consecutive cell blocks (their rows are consecutive,
+// at most 4 per block).  Phase 1: G lanes per row form the residual of those
+// rows in shared memory; phase 2: one thread per cell block applies its
+// inverse.
+static constexpr int BJ_BLOCKS = 64;
+template <class T, int G, bool FIRST>
+__global__ void __launch_bounds__(256)
+k_block_jacobi(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+               const T* __restrict__ val, const int64_t* __restrict__ bstart,
+               const T* __restrict__ binv, int64_t nblk, const T* __restrict__ v,
+               const T* __restrict__ zin, T* __restrict__ zout) {
+  __shared__ T rs[4 * BJ_BLOCKS];
+  const int64_t k0 = (int64_t)blockIdx.x * BJ_BLOCKS;
+  const int64_t k1 = k0 + BJ_BLOCKS < nblk ? k0 + BJ_BLOCKS : nblk;
+  const int64_t r0 = bstart[k0];
+  const int nrow = (int)(bstart[k1] - r0);
+  if (FIRST) {
+    for (int q = threadIdx.x; q < nrow; q += blockDim.x) rs[q] = v[r0 + q];
+  } else {
+    const int lane = threadIdx.x & (G - 1);
+    for (int q = threadIdx.x / G; q < nrow; q += blockDim.x / G) {
+      const int64_t i = r0 + q;
+      const int64_t e1 = rp[i + 1];
+      int64_t e = rp[i] + lane;
+      T a0 = 0, a1 = 0;
+      for (; e + G < e1; e += 2 * G) {
+        a0 += val[e] * ldg(zin + ci[e]);
+        a1 += val[e + G] * ldg(zin + ci[e + G]);
+      }
+      if (e < e1) a0 += val[e] * ldg(zin + ci[e]);
+      T acc = a0 + a1;
+#pragma unroll
+      for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(group_mask<G>(), acc, o, G);
+      if (lane == 0) rs[q] = v[i] - acc;
+    }
+  }
+  __syncthreads();
+  for (int64_t k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
     const int64_t s0 = bstart[k];
     const int b = (int)(bstart[k + 1] - s0);
-    T r[4];
-    for (int i = 0; i < b; i++) {
-      T acc = v[s0 + i];
-      if (!FIRST)
-        for (int64_t q = rp[s0 + i]; q < rp[s0 + i + 1]; q++) acc -= val[q] * ldg(zin + ci[q]);
-      r[i] = acc;
-    }
+    const int q0 = (int)(s0 - r0);
     const T* M = binv + 16 * k;
     for (int i = 0; i < b; i++) {
       T d = 0;
-      for (int j = 0; j < b; j++) d += M[i * 4 + j] * r[j];
+      for (int j = 0; j < b; j++) d += M[i * 4 + j] * rs[q0 + j];
       zout[s0 + i] = FIRST ? d : zin[s0 + i] + d;
     }
   }
@@ -399,16 +426,35 @@ static void mgr_level(Handle* h, int l, const T* v, T* z, cudaStream_t s) {
   const int64_t* Ci = L.F_is_prefix ? nullptr : L.Cidx;
   bool zero = true;             // z == 0 (not materialised)
   // global relaxation z = M_glo^-1 v (point-block Jacobi sweeps from zero)
-  if (L.global_sweeps > 0) {
+  if (L.global_sweeps > 0 && L.nblk > 0) {
     const T* binv = pick<T>(L.binv, L.binvf);
     T* buf[2] = {((L.global_sweeps - 1) % 2 == 0) ? z : (T*)L.z2,
                  ((L.global_sweeps - 1) % 2 == 0) ? (T*)L.z2 : z};
-    MGR_LAUNCH k_block_jacobi<T, true><<<vgrid(L.nblk), 256, 0, s>>>(L.A.rp, L.A.ci, Av, L.bstart, binv,
-                                                          L.nblk, v, nullptr, buf[0]);
-    for (int sw = 1; sw < L.global_sweeps; sw++)
-      MGR_LAUNCH k_block_jacobi<T, false><<<vgrid(L.nblk), 256, 0, s>>>(L.A.rp, L.A.ci, Av, L.bstart, binv,
-                                                             L.nblk, v, buf[(sw - 1) % 2],
-                                                             buf[sw % 2]);
+    const unsigned bgrid = (unsigned)((L.nblk + BJ_BLOCKS - 1) / BJ_BLOCKS);
+    const int G = pick_group(L.A.nnz, L.A.nr);
+    bool first = true;
+    for (int sw = 0; sw < L.global_sweeps; sw++, first = false) {
+      const T* zi = first ? nullptr : buf[(sw - 1) % 2];
+      T* zo = buf[sw % 2];
+#define MGR_BJ_CASE(g)                                                                           \
+  case g:                                                                                        \
+    if (first)                                                                                   \
+      MGR_LAUNCH k_block_jacobi<T, g, true><<<bgrid, 256, 0, s>>>(L.A.rp, L.A.ci, Av, L.bstart, binv, \
+                 L.nblk, v, zi, zo);                                                             \
+    else                                                                                         \
+      MGR_LAUNCH k_block_jacobi<T, g, false><<<bgrid, 256, 0, s>>>(L.A.rp, L.A.ci, Av, L.bstart,     \
+                 binv, L.nblk, v, zi, zo);                                                       \
+    break;
+      switch (G) {
+        MGR_BJ_CASE(1)
+        MGR_BJ_CASE(2)
+        MGR_BJ_CASE(4)
+        MGR_BJ_CASE(8)
+        MGR_BJ_CASE(16)
+        default: MGR_BJ_CASE(32)
+      }
+#undef MGR_BJ_CASE
+        }
     zero = false;
   }
   // F-relaxation z <- z + Q M_FF^-1 Q^T (v - A z)
@@ -504,6 +550,10 @@ int capture_apply_graph(Handle* h) {
     if (e != cudaSuccess) h->apply_exec = nullptr;
     h->apply_nodes = kernels;
   }
+  if (g_trace.on)
+    fprintf(stderr, "mgr_trace apply graph: %s (%s, %lld kernel nodes)\n",
+            h->apply_exec ? "captured" : "not captured, eager launches", cudaGetErrorString(e),
+            (long long)h->apply_nodes);
   if (graph) cudaGraphDestroy(graph);
   cudaStreamDestroy(cs);
   (void)cudaGetLastError();

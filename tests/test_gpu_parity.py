@@ -215,3 +215,35 @@ def test_full_size_workload_hierarchy_and_solve():
     assert r["converged"] and abs(r["iters"] - ref["iters"]) <= 2
     assert _rel(r["x"].cpu().numpy(), ref["x"]) <= 1e-6
     s.close()
+
+
+def test_large_workload_properties():
+    """128x128x64 cells (5,342,147 unknowns), the mixed-precision large case:
+    too big for the oracle inside a test, so properties that hold at any size.
+    The true residual is recomputed independently on the host; the FP32 and
+    FP64 preconditioners must reach the same solution; the displacement AMG's
+    first coarsening keeps the PMIS invariants and P's row structure."""
+    import scipy.sparse as sp
+    from tests.test_oracle_pins import _pmis_invariants
+    p = synth.config(3)
+    A = p.to_scipy()
+    sols = {}
+    for prec in (mgr.MGR_MIXED, mgr.MGR_FP64):
+        s = mgr.Solver(p, precision=prec)
+        r = s.solve(torch.from_numpy(p.rhs).cuda())
+        x = r["x"].cpu().numpy()
+        assert r["converged"]
+        assert np.linalg.norm(p.rhs - A @ x) <= 1e-8 * np.linalg.norm(p.rhs) * 1.001
+        sols[prec] = x
+        if prec == mgr.MGR_FP64:
+            S = mgr.mgr_get_scipy(s.h, mgr.Q_AMG_S, 0, 0)
+            cf = mgr.mgr_get_cf(s.h, 0, 0)
+            _pmis_invariants(S, cf)
+            P = mgr.mgr_get_scipy(s.h, mgr.Q_AMG_P, 0, 0)
+            assert np.diff(P.indptr).max() <= 4
+            cidx = np.cumsum(cf == 1) - 1
+            Pc = P[cf == 1]
+            assert np.array_equal(Pc.indices, cidx[cf == 1]) and np.all(Pc.data == 1.0)
+        s.close()
+    assert _rel(sols[mgr.MGR_MIXED], sols[mgr.MGR_FP64]) <= 1e-6
+
