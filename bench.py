@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--vcycles", type=int, default=50)
     ap.add_argument("--no-large", action="store_true",
                     help="skip the 128x128x64 mixed-precision extra measurement")
+    ap.add_argument("--no-ensemble", action="store_true",
+                    help="skip the 64-system batched ensemble extra measurement")
+    ap.add_argument("--ensemble-size", type=int, default=64)
     ap.add_argument("--profile", action="store_true",
                     help="short run for ncu: FP64 steps and V-cycles only, no clock "
                          "sampling, no mixed/e2e/oracle legs; prints a partial line")
@@ -424,6 +427,10 @@ def run_ours(args):
                      fp64_iters=rd["iters"], speedup_mixed_vs_fp64=msd / msm)
         del Al, bl, xl
 
+    ensemble = None
+    if not args.no_ensemble:
+        ensemble = run_ensemble(args, mgr, stream, world)
+
     n = p.n
     value = n * world / (ms64 * 1e-3)
     line = dict(
@@ -454,6 +461,8 @@ def run_ours(args):
     )
     if large:
         line["large_mixed"] = large
+    if ensemble:
+        line["ensemble"] = ensemble
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         t0 = time.perf_counter()
@@ -473,6 +482,82 @@ def run_ours(args):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def run_ensemble(args, mgr, stream, world):
+    """The ensemble workload: 64 independent two-phase Jacobians (cubic sides
+    16-48, sigma in [1, 3], dt in [0.1, 10]), MGR_MIXED preconditioner with
+    FP64 FGMRES.  One step = mgr_setup_batched + fgmres_solve_batched +
+    mgr_destroy_batched; compared with the same systems solved one after
+    another through mgr_setup / fgmres_solve / mgr_destroy on one stream."""
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+    import torch
+    from paper_1904_05960_gb300 import synth
+    count = args.ensemble_size
+    As, bs = [], []
+    t0 = time.perf_counter()
+    # the generator is numpy; build members in spawned processes (this process
+    # already holds a CUDA context) and upload each as it arrives
+    with ProcessPoolExecutor(max_workers=min(16, os.cpu_count() or 1),
+                             mp_context=mp.get_context("spawn")) as ex:
+        for pm in ex.map(synth.ensemble_member, range(count)):
+            As.append(mgr.DeviceMatrix(pm))
+            bs.append(torch.from_numpy(pm.rhs).cuda())
+    gen_s = time.perf_counter() - t0
+    unknowns = sum(A.n for A in As)
+    nnz = sum(A.nnz for A in As)
+    opts = mgr.mgr_options_default(True, precision=mgr.MGR_MIXED)
+    fo = mgr.fgmres_options_default()
+    xs = [torch.zeros_like(b) for b in bs]
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+
+    def batched(workers):
+        bh = mgr.mgr_setup_batched(As, opts, workers, stream)
+        info = mgr.mgr_batch_info(bh)
+        st, infos = mgr.fgmres_solve_batched(bh, As, bs, xs, fo, stream)
+        mgr.mgr_destroy_batched(bh)
+        return info, st, infos
+
+    tune, _, _ = batched(0)                 # warm-up; the autotuner picks the workers
+    torch.cuda.synchronize()
+    e0.record(stream)
+    _, st, infos = batched(tune["workers"])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    batched_s = e0.elapsed_time(e1) * 1e-3
+    xb = [x.clone() for x in xs]
+
+    torch.cuda.synchronize()
+    e0.record(stream)
+    seq_iters = []
+    for A, b, x in zip(As, bs, xs):
+        h = mgr.mgr_setup(A, opts, stream)
+        r = mgr.fgmres_solve(h, A, b, x, fo, stream)
+        mgr.mgr_destroy(h)
+        seq_iters.append(r["iters"])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    seq_s = e0.elapsed_time(e1) * 1e-3
+    same = all(torch.equal(a, b) for a, b in zip(xb, xs))
+    iters = [i["iters"] for i in infos]
+    out = dict(
+        workload=f"{count} two-phase Jacobians, cubic sides 16-48 cells, sigma U[1,3], "
+                 "dt logU[0.1,10]; MGR_MIXED preconditioner, FP64 FGMRES",
+        systems=count, unknowns=unknowns, nnz=nnz,
+        value=unknowns * world / batched_s, unit="dofs/s",
+        batched_s=batched_s, sequential_s=seq_s, speedup_vs_sequential=seq_s / batched_s,
+        step="mgr_setup_batched + fgmres_solve_batched + mgr_destroy_batched",
+        workers=tune["workers"], autotune_round_ms=tune["tune_ms"],
+        iters_min=min(iters), iters_max=max(iters), iters_total=sum(iters),
+        all_converged=all(i["converged"] for i in infos) and st == mgr.MGR_SUCCESS,
+        max_rel_res_true=max(i["relres"] for i in infos),
+        iters_equal_to_single=iters == seq_iters, bitwise_equal_to_single=same,
+        generation_s=gen_s)
+    del As, bs, xs, xb
+    torch.cuda.empty_cache()
+    return out
 
 
 def main():

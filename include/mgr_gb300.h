@@ -216,6 +216,57 @@ int mgr_splitmix64_device(const uint64_t* in, uint64_t* out, int64_t n, void* st
  */
 int mgr_vcycle_noalloc(mgr_handle_t h, int slot, const double* b, double* x, void* stream);
 
+/*
+ * Batched ensemble: nsys independent Jacobians of uneven size (for instance
+ * permeability realisations or time steps), each with its own MGR hierarchy,
+ * FGMRES iteration and convergence test.  The paper solves one system per
+ * run; these entries add nothing to its method (Sec. 5-6): system i's
+ * hierarchy is exactly what mgr_setup builds for A[i] alone and its solution
+ * exactly what fgmres_solve returns for it alone.  They run the systems
+ * concurrently: host worker threads (native, one CUDA stream each) take the
+ * systems largest first, so that the GPU executes several systems' captured
+ * preconditioner graphs, Jacobian products and Gram-Schmidt kernels at once.
+ */
+typedef struct mgr_batch_s* mgr_batch_t;
+
+/* Set up nsys systems A[0..nsys) with the same options.  `workers` = number of
+ * concurrent workers (1..16); 0 lets the library choose it by timing one
+ * concurrent round of every system's preconditioner application with 1, 2, 4,
+ * 8 and 16 workers (the fastest is kept; see mgr_batch_info).  The setups
+ * themselves run on up to 16 workers.  Ordered after the caller's earlier work
+ * on `stream`; synchronises `stream` before returning.  A[i] is owned by the
+ * caller and may be freed afterwards.  Errors: INVALID_ARG (nsys <= 0, workers
+ * > 16, or any system's mgr_setup argument error), and every error of
+ * mgr_setup (the first one met; nothing is kept then). */
+int mgr_setup_batched(int nsys, const mgr_matrix_t* A, const mgr_options_t* o, int workers,
+                      void* stream, mgr_batch_t* out);
+
+/* Solve A[i] x[i] = b[i] for every system (device pointers; A[i] the matrices
+ * given to mgr_setup_batched, b[i], x[i] of A[i].n doubles; x[i] is
+ * overwritten, starting from zero).  info = array of nsys records or NULL.
+ * Returns the first negative error of any system (the others still run to
+ * their end), else MGR_NOT_CONVERGED if a system missed rtol, else
+ * MGR_SUCCESS.  Synchronous: ordered after the caller's work on `stream` and
+ * finished when it returns. */
+int fgmres_solve_batched(mgr_batch_t bh, const mgr_matrix_t* A, const double* const* b,
+                         double* const* x, const fgmres_options_t* o, fgmres_info_t* info,
+                         void* stream);
+
+/* Worker count in use, host wall time of the batched setup (s), and the
+ * autotuner's record: tune_workers[5] = the worker counts it timed (1, 2, 4,
+ * 8, 16, each capped at nsys, repeats dropped; 0 after the last) and
+ * tune_ms[5] = their round times in ms (-1 after the last).  Nothing is timed
+ * when workers were given to mgr_setup_batched.  Any pointer may be NULL. */
+int mgr_batch_info(mgr_batch_t bh, int* workers, double* setup_s, int* tune_workers,
+                   double* tune_ms);
+
+/* The handle of system i (for the inspection entries above); owned by the
+ * batch, valid until mgr_destroy_batched. */
+int mgr_batch_handle(mgr_batch_t bh, int i, mgr_handle_t* out);
+
+/* Wait for the batch's streams, free every system and the streams. */
+int mgr_destroy_batched(mgr_batch_t bh);
+
 /* Number of CUDA kernel launches this library has issued in this process
  * (all handles, all threads).  Lets a caller count the kernels of a region. */
 int64_t mgr_launch_count(void);

@@ -21,7 +21,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libmgr_gb300.so")
 ROOT = os.path.dirname(HERE)
 
-SOURCES = ["setup.cu", "apply.cu", "krylov.cu", "capi.cu", "noalloc.cu"]
+SOURCES = ["setup.cu", "apply.cu", "krylov.cu", "capi.cu", "noalloc.cu", "batched.cu"]
 NO_FMAD = {"setup.cu"}
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -64,7 +64,7 @@ def build(force=False, verbose=False):
     with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
     tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [cc] + ARCH + ["-shared", "-o", tmp] + objs + ["-cudart", "static"]
+    cmd = [cc] + ARCH + ["-shared", "-o", tmp] + objs + ["-cudart", "static", "-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")

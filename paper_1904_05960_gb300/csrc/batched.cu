@@ -1,0 +1,258 @@
+// Batched ensemble: many independent Jacobians of uneven size solved together.
+//
+// Each system keeps exactly the hierarchy mgr_setup builds for it alone and
+// the FGMRES iteration fgmres_solve runs for it alone (own Krylov basis, own
+// convergence test), so every system's result equals its single-system
+// result.  What batching adds is concurrency: a pool of native host workers,
+// each with its own CUDA stream, takes systems largest first, so the GPU runs
+// several systems' captured preconditioner graphs, Jacobian products and
+// Gram-Schmidt kernels at once; small systems, whose kernels are too short
+// to fill the GPU, overlap with large ones.  The number of workers is chosen
+// at setup by timing one concurrent round of every system's preconditioner
+// graph with 1, 2, 4, 8 and 16 workers (the schedule autotuner).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <new>
+#include <numeric>
+#include <thread>
+#include <vector>
+
+#include "mgr_internal.cuh"
+
+namespace mgr {
+
+static constexpr int BATCH_MAX_WORKERS = 16;
+static constexpr uint32_t BATCH_MAGIC = 0x4d475242u;
+
+struct Batch {
+  uint32_t magic = BATCH_MAGIC;
+  int nsys = 0;
+  int workers = 1;                    // chosen worker count
+  std::vector<Handle*> sys;
+  std::vector<int> order;             // systems by decreasing size
+  std::vector<cudaStream_t> streams;  // one per worker (BATCH_MAX_WORKERS)
+  std::vector<int> tune_workers;      // autotuner: worker counts timed
+  std::vector<double> tune_ms;        //   and their round times
+  double setup_s = 0.0;
+};
+
+// Runs f(system, stream) for every system on `workers` host threads, each
+// with its own stream, systems taken in `order`.  Returns the first negative
+// status, else the largest non-negative one.
+template <class F>
+static int run_workers(Batch* B, int workers, F&& f) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::atomic<int> next{0};
+  std::atomic<int> err{0};
+  std::atomic<int> worst{0};
+  auto body = [&](int w) {
+    cudaSetDevice(dev);
+    for (;;) {
+      const int k = next.fetch_add(1);
+      if (k >= B->nsys) break;
+      const int i = B->order[k];
+      const int rc = f(i, B->streams[w]);
+      if (rc < 0) {
+        int z = 0;
+        err.compare_exchange_strong(z, rc);
+      } else {
+        int cur = worst.load();
+        while (rc > cur && !worst.compare_exchange_weak(cur, rc)) {
+        }
+      }
+    }
+  };
+  std::vector<std::thread> th;
+  for (int w = 1; w < workers; w++) th.emplace_back(body, w);
+  body(0);
+  for (auto& t : th) t.join();
+  return err.load() ? err.load() : worst.load();
+}
+
+// Work on the worker streams follows the caller's earlier work on `caller`
+// (and, through end_on, the caller's later work follows the batch).
+static int begin_on(Batch* B, cudaStream_t caller) {
+  cudaEvent_t ev;
+  MGR_TRY_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  MGR_TRY_CUDA(cudaEventRecord(ev, caller));
+  for (cudaStream_t ws : B->streams) MGR_TRY_CUDA(cudaStreamWaitEvent(ws, ev, 0));
+  cudaEventDestroy(ev);
+  return MGR_SUCCESS;
+}
+static int end_on(Batch* B, cudaStream_t caller) {
+  for (cudaStream_t ws : B->streams) {
+    cudaEvent_t ev;
+    MGR_TRY_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    MGR_TRY_CUDA(cudaEventRecord(ev, ws));
+    MGR_TRY_CUDA(cudaStreamWaitEvent(caller, ev, 0));
+    cudaEventDestroy(ev);
+  }
+  return MGR_SUCCESS;
+}
+
+// One preconditioner application of system h on stream s, from the handle's
+// fixed buffers (the captured graph, or the same launches if capture failed).
+static int apply_fixed(Handle* h, cudaStream_t s) {
+  if (h->apply_exec) {
+    MGR_TRY_CUDA(cudaGraphLaunch(h->apply_exec, s));
+    return MGR_SUCCESS;
+  }
+  if (h->opt.precision == MGR_MIXED) return apply_mgr32(h, h->vin32, h->zout32, s);
+  return apply_mgr(h, h->gin, h->gout, s);
+}
+
+// Schedule autotuner: time one round (one application per system) for each
+// worker count and keep the fastest.
+static int autotune_workers(Batch* B, cudaStream_t caller) {
+  for (Handle* h : B->sys) {
+    if (h->opt.precision == MGR_MIXED) {
+      MGR_TRY_CUDA(cudaMemsetAsync(h->vin32, 0, sizeof(float) * h->n, caller));
+    } else if (h->gin) {
+      MGR_TRY_CUDA(cudaMemsetAsync(h->gin, 0, sizeof(double) * h->n, caller));
+    } else {
+      return MGR_SUCCESS;   // no fixed buffers: keep the default
+    }
+  }
+  MGR_TRY_CUDA(cudaStreamSynchronize(caller));
+  const int counts[5] = {1, 2, 4, 8, 16};
+  double best = 1e300;
+  B->tune_workers.clear();
+  B->tune_ms.clear();
+  for (int c = 0; c < 5; c++) {
+    const int w = std::min(counts[c], std::min(B->nsys, BATCH_MAX_WORKERS));
+    if (!B->tune_workers.empty() && w == B->tune_workers.back()) continue;
+    double t = 0.0;
+    for (int rep = 0; rep < 2; rep++) {   // the first round warms up
+      MGR_TRY_CUDA(cudaDeviceSynchronize());
+      const auto t0 = std::chrono::steady_clock::now();
+      const int rc = run_workers(B, w, [&](int i, cudaStream_t s) {
+        MGR_TRY(apply_fixed(B->sys[i], s));
+        MGR_TRY_CUDA(cudaStreamSynchronize(s));
+        return MGR_SUCCESS;
+      });
+      if (rc < 0) return rc;
+      t = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    }
+    B->tune_workers.push_back(w);
+    B->tune_ms.push_back(t);
+    if (t < best) {
+      best = t;
+      B->workers = w;
+    }
+  }
+  return MGR_SUCCESS;
+}
+
+}  // namespace mgr
+
+using namespace mgr;
+
+extern "C" {
+
+int mgr_setup_batched(int nsys, const mgr_matrix_t* A, const mgr_options_t* o, int workers,
+                      void* stream, mgr_batch_t* out) {
+  (void)cudaGetLastError();  // errors of earlier calls are not this call's
+  if (!out) return MGR_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (nsys <= 0 || !A || !o || workers > BATCH_MAX_WORKERS) return MGR_ERR_INVALID_ARG;
+  Batch* B = new (std::nothrow) Batch();
+  if (!B) return MGR_ERR_OOM;
+  B->nsys = nsys;
+  B->sys.assign(nsys, nullptr);
+  B->order.resize(nsys);
+  std::iota(B->order.begin(), B->order.end(), 0);
+  std::stable_sort(B->order.begin(), B->order.end(),
+                   [&](int a, int b) { return A[a].nnz > A[b].nnz; });
+  B->streams.assign(BATCH_MAX_WORKERS, nullptr);
+  cudaStream_t caller = (cudaStream_t)stream;
+  int rc = MGR_SUCCESS;
+  for (auto& ws : B->streams)
+    if (cudaStreamCreateWithFlags(&ws, cudaStreamNonBlocking) != cudaSuccess) rc = MGR_ERR_CUDA;
+  const auto t0 = std::chrono::steady_clock::now();
+  if (!rc) rc = begin_on(B, caller);
+  const int setup_workers = std::min(nsys, workers > 0 ? workers : BATCH_MAX_WORKERS);
+  if (!rc)
+    rc = run_workers(B, setup_workers, [&](int i, cudaStream_t s) {
+      (void)cudaGetLastError();
+      return setup_one(&A[i], o, s, &B->sys[i]);
+    });
+  if (rc >= 0) rc = end_on(B, caller);
+  if (rc >= 0 && cudaStreamSynchronize(caller) != cudaSuccess) rc = MGR_ERR_CUDA;
+  B->setup_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (rc >= 0) {
+    if (workers > 0) {
+      B->workers = std::min(workers, nsys);
+    } else {
+      rc = autotune_workers(B, caller);
+    }
+  }
+  if (rc < 0) {
+    mgr_destroy_batched(reinterpret_cast<mgr_batch_t>(B));
+    return rc;
+  }
+  *out = reinterpret_cast<mgr_batch_t>(B);
+  return MGR_SUCCESS;
+}
+
+int fgmres_solve_batched(mgr_batch_t bh, const mgr_matrix_t* A, const double* const* b,
+                         double* const* x, const fgmres_options_t* o, fgmres_info_t* info,
+                         void* stream) {
+  (void)cudaGetLastError();  // errors of earlier calls are not this call's
+  Batch* B = reinterpret_cast<Batch*>(bh);
+  if (!B || B->magic != BATCH_MAGIC || !A || !b || !x || !o) return MGR_ERR_INVALID_ARG;
+  for (int i = 0; i < B->nsys; i++)
+    if (A[i].n != B->sys[i]->n || !b[i] || !x[i]) return MGR_ERR_INVALID_ARG;
+  cudaStream_t caller = (cudaStream_t)stream;
+  MGR_TRY(begin_on(B, caller));
+  int rc = run_workers(B, B->workers, [&](int i, cudaStream_t s) {
+    (void)cudaGetLastError();
+    Handle* h = B->sys[i];
+    h->pool.s = s;   // Krylov workspace is allocated on the stream that uses it
+    return fgmres_run(h, &A[i], b[i], x[i], o, info ? &info[i] : nullptr, s);
+  });
+  const int rc2 = end_on(B, caller);
+  if (rc >= 0 && rc2 < 0) rc = rc2;
+  if (rc >= 0 && cudaStreamSynchronize(caller) != cudaSuccess) rc = MGR_ERR_CUDA;
+  return rc;
+}
+
+int mgr_batch_info(mgr_batch_t bh, int* workers, double* setup_s, int* tune_workers,
+                   double* tune_ms) {
+  Batch* B = reinterpret_cast<Batch*>(bh);
+  if (!B || B->magic != BATCH_MAGIC) return MGR_ERR_INVALID_ARG;
+  if (workers) *workers = B->workers;
+  if (setup_s) *setup_s = B->setup_s;
+  for (int c = 0; c < 5; c++) {
+    const bool have = c < (int)B->tune_ms.size();
+    if (tune_workers) tune_workers[c] = have ? B->tune_workers[c] : 0;
+    if (tune_ms) tune_ms[c] = have ? B->tune_ms[c] : -1.0;
+  }
+  return MGR_SUCCESS;
+}
+
+int mgr_batch_handle(mgr_batch_t bh, int i, mgr_handle_t* out) {
+  Batch* B = reinterpret_cast<Batch*>(bh);
+  if (!B || B->magic != BATCH_MAGIC || !out || i < 0 || i >= B->nsys) return MGR_ERR_INVALID_ARG;
+  *out = reinterpret_cast<mgr_handle_t>(B->sys[i]);
+  return MGR_SUCCESS;
+}
+
+int mgr_destroy_batched(mgr_batch_t bh) {
+  Batch* B = reinterpret_cast<Batch*>(bh);
+  if (!B || B->magic != BATCH_MAGIC) return MGR_ERR_INVALID_ARG;
+  for (cudaStream_t ws : B->streams)
+    if (ws) cudaStreamSynchronize(ws);
+  for (Handle* h : B->sys)
+    if (h) mgr_destroy(reinterpret_cast<mgr_handle_t>(h));
+  for (cudaStream_t ws : B->streams)
+    if (ws) cudaStreamDestroy(ws);
+  B->magic = 0;
+  delete B;
+  return MGR_SUCCESS;
+}
+
+}  // extern "C"

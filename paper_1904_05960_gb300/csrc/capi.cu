@@ -10,7 +10,7 @@
 
 namespace mgr {
 std::atomic<long long> g_launches{0};
-Trace g_trace;
+thread_local Trace g_trace;
 
 static double now_ms() {
   return std::chrono::duration<double, std::milli>(
@@ -30,9 +30,6 @@ void Trace::mark(const char* what, int a, int b) {
   fprintf(stderr, "mgr_trace %-28s %3d %3d  %8.3f ms  (total %8.3f)\n", what, a, b, t - last, t - t0);
   last = t;
 }
-
-int fgmres_run(Handle* h, const mgr_matrix_t* A, const double* b, double* x,
-               const fgmres_options_t* o, fgmres_info_t* info, cudaStream_t s);
 
 __global__ void k_splitmix(const uint64_t* __restrict__ in, uint64_t* __restrict__ out, int64_t n) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -122,6 +119,19 @@ const char* mgr_error_string(int code) {
 
 int mgr_setup(const mgr_matrix_t* A, const mgr_options_t* o, void* stream, mgr_handle_t* out) {
   (void)cudaGetLastError();  // errors of earlier calls are not this call's
+  if (!out) return MGR_ERR_INVALID_ARG;
+  *out = nullptr;
+  Handle* h = nullptr;
+  const int rc = mgr::setup_one(A, o, (cudaStream_t)stream, &h);
+  if (rc == MGR_SUCCESS) *out = reinterpret_cast<mgr_handle_t>(h);
+  return rc;
+}
+
+}  // extern "C"
+
+namespace mgr {
+// One system's setup (mgr_setup; also run by the batched setup's workers).
+int setup_one(const mgr_matrix_t* A, const mgr_options_t* o, cudaStream_t s, Handle** out) {
   if (!A || !o || !out || A->n <= 0 || A->nnz < 0 || !A->row_ptr || !A->col_idx || !A->val ||
       !A->dof_label || !A->dof_node)
     return MGR_ERR_INVALID_ARG;
@@ -129,7 +139,6 @@ int mgr_setup(const mgr_matrix_t* A, const mgr_options_t* o, void* stream, mgr_h
       o->amg_pmax < 0 || (o->precision != MGR_FP64 && o->precision != MGR_MIXED))
     return MGR_ERR_INVALID_ARG;
   if (A->n > INT32_MAX) return MGR_ERR_INVALID_ARG;
-  cudaStream_t s = (cudaStream_t)stream;
   Handle* h = new (std::nothrow) Handle();
   if (!h) return MGR_ERR_OOM;
   h->opt = *o;
@@ -165,9 +174,12 @@ int mgr_setup(const mgr_matrix_t* A, const mgr_options_t* o, void* stream, mgr_h
     mgr_destroy(reinterpret_cast<mgr_handle_t>(h));
     return rc;
   }
-  *out = reinterpret_cast<mgr_handle_t>(h);
+  *out = h;
   return MGR_SUCCESS;
 }
+}  // namespace mgr
+
+extern "C" {
 
 int mgr_apply(mgr_handle_t hh, const double* v, double* z, void* stream) {
   (void)cudaGetLastError();  // errors of earlier calls are not this call's

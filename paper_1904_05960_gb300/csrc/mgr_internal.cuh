@@ -188,6 +188,9 @@ int apply_mgr(Handle* h, const double* v, double* z, cudaStream_t s);
 int apply_mgr32(Handle* h, const float* v, float* z, cudaStream_t s);
 int apply_mgr_mixed_into(Handle* h, const double* v, float* z, cudaStream_t s);
 int capture_apply_graph(Handle* h);
+int setup_one(const mgr_matrix_t* A, const mgr_options_t* o, cudaStream_t s, Handle** out);
+int fgmres_run(Handle* h, const mgr_matrix_t* A, const double* b, double* x,
+               const fgmres_options_t* o, fgmres_info_t* info, cudaStream_t s);
 int apply_vcycle64(Handle* h, Amg* g, const double* b, double* x, cudaStream_t s);
 // V-cycle with a caller-provided workspace of vcycle_ws_bytes() bytes
 size_t vcycle_ws_bytes(Handle* h, Amg* g);
@@ -228,7 +231,7 @@ struct Trace {
   void start(cudaStream_t st);
   void mark(const char* what, int a = -1, int b = -1);
 };
-extern Trace g_trace;
+extern thread_local Trace g_trace;   // per host thread (batched workers)
 
 template <class T>
 inline int read_back(T* host, const T* dev, cudaStream_t s) {

@@ -21,6 +21,7 @@
 
 #include <chrono>
 #include <cmath>
+#include <mutex>
 
 #include "mgr_internal.cuh"
 
@@ -452,12 +453,15 @@ static int spgemm(Pool& P, Pool& tmp, const Csr& A, const Csr& B, Csr& C, cudaSt
   int64_t* cnt = tmp.get<int64_t>(A.nr + 1);
   if (P.err || tmp.err) return P.err ? P.err : tmp.err;
   const size_t sm = sizeof(uint32_t) * SPG_WORDS * SPG_WARPS;
-  static bool attr = false;
-  if (!attr) {
-    MGR_TRY_CUDA(cudaFuncSetAttribute(k_spgemm_symbolic<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    MGR_TRY_CUDA(cudaFuncSetAttribute(k_spgemm_symbolic<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    attr = true;
-  }
+  // once per process (setups may run concurrently on several host threads)
+  static std::once_flag attr_once;
+  static cudaError_t attr_err = cudaSuccess;
+  std::call_once(attr_once, [&] {
+    attr_err = cudaFuncSetAttribute(k_spgemm_symbolic<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (attr_err == cudaSuccess)
+      attr_err = cudaFuncSetAttribute(k_spgemm_symbolic<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  });
+  MGR_TRY_CUDA(attr_err);
   unsigned g = grid_for(A.nr, SPG_WARPS, 152 * 16);
   MGR_LAUNCH k_spgemm_symbolic<false><<<g, SPG_WARPS * 32, sm, s>>>(A.rp, A.ci, A.nr, B.rp, B.ci, cnt, nullptr);
   MGR_TRY(rowptr_from_counts(cnt, C.rp, A.nr, &C.nnz, s, tmp));

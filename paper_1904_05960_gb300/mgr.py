@@ -27,7 +27,8 @@ Q_AMG_A, Q_AMG_S, Q_AMG_P, Q_AMG_R = 10, 11, 12, 13
 EXPORTED = ["mgr_options_default", "fgmres_options_default", "mgr_setup", "mgr_apply",
             "fgmres_solve", "mgr_destroy", "mgr_error_string", "mgr_get_csr",
             "mgr_amg_levels", "mgr_get_cf", "mgr_vcycle", "mgr_splitmix64_device",
-            "mgr_launch_count", "mgr_vcycle_noalloc"]
+            "mgr_launch_count", "mgr_vcycle_noalloc", "mgr_setup_batched",
+            "fgmres_solve_batched", "mgr_batch_info", "mgr_batch_handle", "mgr_destroy_batched"]
 
 
 class MgrMatrix(C.Structure):
@@ -96,6 +97,14 @@ def lib():
             L.mgr_vcycle.argtypes = [P, C.c_int, P, P, P]
             L.mgr_splitmix64_device.argtypes = [P, P, I64, P]
             L.mgr_vcycle_noalloc.argtypes = [P, C.c_int, P, P, P]
+            L.mgr_setup_batched.argtypes = [C.c_int, C.POINTER(MgrMatrix), C.POINTER(MgrOptions),
+                                            C.c_int, P, C.POINTER(P)]
+            L.fgmres_solve_batched.argtypes = [P, C.POINTER(MgrMatrix), C.POINTER(P), C.POINTER(P),
+                                               C.POINTER(FgmresOptions), C.POINTER(FgmresInfo), P]
+            L.mgr_batch_info.argtypes = [P, C.POINTER(C.c_int), C.POINTER(C.c_double),
+                                         C.POINTER(C.c_int), C.POINTER(C.c_double)]
+            L.mgr_batch_handle.argtypes = [P, C.c_int, C.POINTER(P)]
+            L.mgr_destroy_batched.argtypes = [P]
             L.mgr_launch_count.argtypes = []
             L.mgr_launch_count.restype = I64
             _lib = L
@@ -205,6 +214,56 @@ def fgmres_solve(h, A: DeviceMatrix, b, x, opts: FgmresOptions | None = None, st
 def mgr_destroy(h):
     if h:
         lib().mgr_destroy(h)
+
+
+def _matrix_array(As):
+    arr = (MgrMatrix * len(As))()
+    for i, A in enumerate(As):
+        arr[i] = A.c
+    return arr
+
+
+def mgr_setup_batched(As, opts: MgrOptions, workers=0, stream=None):
+    """Set up every system of the list As (DeviceMatrix); workers = 0 lets the
+    library's autotuner pick the number of concurrent workers."""
+    h = C.c_void_p()
+    _check(lib().mgr_setup_batched(len(As), _matrix_array(As), C.byref(opts), int(workers),
+                                   _stream_ptr(stream), C.byref(h)), "mgr_setup_batched")
+    return h
+
+
+def fgmres_solve_batched(bh, As, bs, xs, opts: FgmresOptions | None = None, stream=None):
+    """Solve As[i] xs[i] = bs[i] for all systems; returns (status, [info dicts])."""
+    n = len(As)
+    infos = (FgmresInfo * n)()
+    bp = (C.c_void_p * n)(*[b.data_ptr() for b in bs])
+    xp = (C.c_void_p * n)(*[x.data_ptr() for x in xs])
+    o = opts if opts is not None else fgmres_options_default()
+    st = _check(lib().fgmres_solve_batched(bh, _matrix_array(As), bp, xp, C.byref(o), infos,
+                                           _stream_ptr(stream)), "fgmres_solve_batched")
+    return st, [dict(iters=i.iters, restarts=i.restarts, converged=bool(i.converged),
+                     relres=i.rel_res_true, setup_s=i.setup_s, solve_s=i.solve_s) for i in infos]
+
+
+def mgr_batch_info(bh):
+    w = C.c_int(0)
+    s = C.c_double(0.0)
+    tw = (C.c_int * 5)()
+    t = (C.c_double * 5)()
+    _check(lib().mgr_batch_info(bh, C.byref(w), C.byref(s), tw, t), "mgr_batch_info")
+    return dict(workers=w.value, setup_s=s.value,
+                tune_ms={k: v for k, v in zip(list(tw), list(t)) if k > 0})
+
+
+def mgr_batch_handle(bh, i):
+    h = C.c_void_p()
+    _check(lib().mgr_batch_handle(bh, int(i), C.byref(h)), "mgr_batch_handle")
+    return h
+
+
+def mgr_destroy_batched(bh):
+    if bh:
+        lib().mgr_destroy_batched(bh)
 
 
 def mgr_get_csr(h, kind, slot=0, lvl=0):

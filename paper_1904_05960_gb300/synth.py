@@ -441,11 +441,12 @@ def channels(nx=256, ny=256, nz=96, seed=0):
                                rhs_seed=seed + 1, meta=dict(kind="channels", seed=seed))
 
 
-def ensemble_member(i):
-    """Member i of the 64-system ensemble: cubic side in [16, 48], sigma in
-    [1, 3], dt log-uniform in [0.1, 10], seed i."""
+def ensemble_member(i, side_range=(16, 48)):
+    """Member i of the 64-system ensemble: cubic side uniform in side_range
+    (inclusive; [16, 48] for the ensemble workload), sigma in [1, 3], dt
+    log-uniform in [0.1, 10], seed i."""
     rng = np.random.default_rng(1000 + i)
-    side = int(rng.integers(16, 49))
+    side = int(rng.integers(side_range[0], side_range[1] + 1))
     sigma = float(rng.uniform(1.0, 3.0))
     dt = float(10.0 ** rng.uniform(-1.0, 1.0))
     return two_phase(side, side, side, seed=i, sigma=sigma, dt=dt)

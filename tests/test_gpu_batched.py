@@ -1,0 +1,124 @@
+"""Batched ensemble entry points (mgr_setup_batched / fgmres_solve_batched).
+
+Every system keeps the hierarchy and the FGMRES iteration of its single-system
+solve, so the batched solutions must equal the single-system solutions bit for
+bit, with the same iteration counts; one member is also checked against the
+oracle (Sec. 6 solver settings, iterations +-2, solution 1e-6).  Members are
+drawn by the ensemble recipe (cubic side, sigma in [1, 3], dt log-uniform in
+[0.1, 10]) with small sides so the oracle and the test stay fast.
+"""
+import numpy as np
+import pytest
+
+from paper_1904_05960_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_1904_05960_gb300 import mgr  # noqa: E402
+
+SIDES = (8, 14)
+NSYS = 6
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+@pytest.fixture(scope="module")
+def members():
+    return [synth.ensemble_member(i, SIDES) for i in range(NSYS)]
+
+
+def _solve_single(p, A, precision):
+    h = mgr.mgr_setup(A, mgr.mgr_options_default(True, precision=precision))
+    b = torch.from_numpy(p.rhs).cuda()
+    x = torch.zeros_like(b)
+    r = mgr.fgmres_solve(h, A, b, x)
+    mgr.mgr_destroy(h)
+    return x, r
+
+
+@pytest.mark.parametrize("precision", [mgr.MGR_MIXED, mgr.MGR_FP64])
+@pytest.mark.parametrize("workers", [0, 3])
+def test_batched_equals_single_solves(members, precision, workers):
+    As = [mgr.DeviceMatrix(p) for p in members]
+    bh = mgr.mgr_setup_batched(As, mgr.mgr_options_default(True, precision=precision),
+                               workers=workers)
+    info = mgr.mgr_batch_info(bh)
+    assert 1 <= info["workers"] <= min(16, NSYS)
+    if workers:
+        assert info["workers"] == workers and not info["tune_ms"]
+    else:
+        assert info["tune_ms"] and info["workers"] in info["tune_ms"]
+    bs = [torch.from_numpy(p.rhs).cuda() for p in members]
+    xs = [torch.full_like(b, float("nan")) for b in bs]
+    st, infos = mgr.fgmres_solve_batched(bh, As, bs, xs)
+    assert st == mgr.MGR_SUCCESS
+    torch.cuda.synchronize()
+    for i, (p, A) in enumerate(zip(members, As)):
+        assert infos[i]["converged"] and infos[i]["relres"] <= 1e-8
+        x1, r1 = _solve_single(p, A, precision)
+        assert infos[i]["iters"] == r1["iters"], i
+        assert torch.equal(xs[i], x1), i
+    # a second solve on the same batch gives the same answer
+    xs2 = [torch.zeros_like(b) for b in bs]
+    mgr.fgmres_solve_batched(bh, As, bs, xs2)
+    for i in range(NSYS):
+        assert torch.equal(xs2[i], xs[i])
+    mgr.mgr_destroy_batched(bh)
+
+
+def test_batched_member_matches_oracle(members):
+    import oracle
+    As = [mgr.DeviceMatrix(p) for p in members[:3]]
+    bh = mgr.mgr_setup_batched(As, mgr.mgr_options_default(True), workers=2)
+    bs = [torch.from_numpy(p.rhs).cuda() for p in members[:3]]
+    xs = [torch.zeros_like(b) for b in bs]
+    st, infos = mgr.fgmres_solve_batched(bh, As, bs, xs)
+    mgr.mgr_destroy_batched(bh)
+    assert st == mgr.MGR_SUCCESS
+    p = members[0]
+    ref = oracle.Oracle(p).fgmres(p.rhs)
+    assert ref["status"] == 0
+    assert abs(infos[0]["iters"] - ref["iters"]) <= 2
+    x = xs[0].cpu().numpy()
+    assert np.linalg.norm(x - ref["x"]) <= 1e-6 * np.linalg.norm(ref["x"])
+
+
+def test_batched_inspection_handle(members):
+    As = [mgr.DeviceMatrix(p) for p in members[:2]]
+    bh = mgr.mgr_setup_batched(As, mgr.mgr_options_default(True), workers=1)
+    h1 = mgr.mgr_batch_handle(bh, 1)
+    hs = mgr.mgr_setup(As[1], mgr.mgr_options_default(True))
+    for kind, slot, lvl in ((mgr.Q_MGR_S, 1, 0), (mgr.Q_AMG_P, 0, 0), (mgr.Q_AMG_A, 2, 1)):
+        a = mgr.mgr_get_csr(h1, kind, slot, lvl)
+        b = mgr.mgr_get_csr(hs, kind, slot, lvl)
+        assert a is not None and b is not None
+        for u, v in zip(a[2:], b[2:]):
+            assert np.array_equal(u, v)
+    mgr.mgr_destroy(hs)
+    with pytest.raises(mgr.MgrError):
+        mgr.mgr_batch_handle(bh, 2)
+    mgr.mgr_destroy_batched(bh)
+
+
+def test_batched_argument_errors(members):
+    As = [mgr.DeviceMatrix(p) for p in members[:2]]
+    with pytest.raises(mgr.MgrError) as e:
+        mgr.mgr_setup_batched([], mgr.mgr_options_default(True))
+    assert e.value.code == -1
+    with pytest.raises(mgr.MgrError) as e:
+        mgr.mgr_setup_batched(As, mgr.mgr_options_default(True), workers=17)
+    assert e.value.code == -1
+    bh = mgr.mgr_setup_batched(As, mgr.mgr_options_default(True), workers=1)
+    bs = [torch.from_numpy(p.rhs).cuda() for p in members[:2]]
+    xs = [torch.zeros_like(b) for b in bs]
+    with pytest.raises(mgr.MgrError) as e:          # systems given in the wrong order
+        mgr.fgmres_solve_batched(bh, As[::-1], bs[::-1], xs[::-1])
+    assert e.value.code == -1
+    mgr.mgr_destroy_batched(bh)
