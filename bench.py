@@ -513,8 +513,11 @@ def run_ensemble(args, mgr, stream, world):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
 
+    em = torch.cuda.Event(enable_timing=True)
+
     def batched(workers):
         bh = mgr.mgr_setup_batched(As, opts, workers, stream)
+        em.record(stream)
         info = mgr.mgr_batch_info(bh)
         st, infos = mgr.fgmres_solve_batched(bh, As, bs, xs, fo, stream)
         mgr.mgr_destroy_batched(bh)
@@ -527,6 +530,7 @@ def run_ensemble(args, mgr, stream, world):
     e1.record(stream)
     torch.cuda.synchronize()
     batched_s = e0.elapsed_time(e1) * 1e-3
+    setup_part = e0.elapsed_time(em) * 1e-3
     xb = [x.clone() for x in xs]
 
     torch.cuda.synchronize()
@@ -548,6 +552,7 @@ def run_ensemble(args, mgr, stream, world):
         systems=count, unknowns=unknowns, nnz=nnz,
         value=unknowns * world / batched_s, unit="dofs/s",
         batched_s=batched_s, sequential_s=seq_s, speedup_vs_sequential=seq_s / batched_s,
+        batched_setup_s=setup_part, batched_solve_and_destroy_s=batched_s - setup_part,
         step="mgr_setup_batched + fgmres_solve_batched + mgr_destroy_batched",
         workers=tune["workers"], autotune_round_ms=tune["tune_ms"],
         iters_min=min(iters), iters_max=max(iters), iters_total=sum(iters),
