@@ -206,6 +206,7 @@ int mgr_destroy(mgr_handle_t hh) {
   for (auto& L : h->lev) delete L.famg;
   delete h->camg;
   h->pool.free_all_async();
+  h->pool2.free_all_async();
   if (h->hpinned) cudaFreeHost(h->hpinned);
   delete h;
   return MGR_SUCCESS;

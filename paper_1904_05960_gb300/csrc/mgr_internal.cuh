@@ -170,6 +170,10 @@ struct Handle {
   double* yv = nullptr;
   double* hpinned = nullptr;     // pinned host mirror for small readbacks
   int* derr = nullptr;           // device error word
+  // the F-relaxation AMG built concurrently with the rest of the setup owns
+  // its allocations here (second stream) and reports through derr2
+  Pool pool2;
+  int* derr2 = nullptr;
 };
 
 // ----------------------------------------------------------------------------
@@ -177,7 +181,8 @@ struct Handle {
 // ----------------------------------------------------------------------------
 int scan_exclusive(const int64_t* in, int64_t* out, int64_t n, cudaStream_t s, Pool& tmp);
 int build_mgr_hierarchy(Handle* h, const mgr_matrix_t* A, cudaStream_t s);
-int build_amg(Handle* h, const Csr& A, const int32_t* comp, int slot, Amg** out, cudaStream_t s);
+int build_amg(Handle* h, Pool& P, int* derr, const Csr& A, bool own_input, const int32_t* comp,
+              int slot, Amg** out, cudaStream_t s);
 int to_fp32(Handle* h, cudaStream_t s);
 
 // ----------------------------------------------------------------------------

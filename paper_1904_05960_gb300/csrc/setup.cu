@@ -22,6 +22,7 @@
 #include <chrono>
 #include <cmath>
 #include <mutex>
+#include <thread>
 
 #include "mgr_internal.cuh"
 
@@ -1509,8 +1510,8 @@ __global__ void __launch_bounds__(1024) k_dense_gj_inverse(double* __restrict__ 
     for (int64_t e = tid; e < (int64_t)n * n; e += nt) ga[e] = a[e];
 }
 
-static int dense_coarsest(Handle* h, Amg* g, Pool& tmp, cudaStream_t s) {
-  Pool& P = h->pool;
+static constexpr size_t GJ_SMEM_MAX = 220 * 1024;
+static int dense_coarsest(Pool& P, int* derr, Amg* g, Pool& tmp, cudaStream_t s) {
   const Csr& A = g->lev.back().A;
   int64_t n = A.nr;
   g->ncoarse = n;
@@ -1524,26 +1525,31 @@ static int dense_coarsest(Handle* h, Amg* g, Pool& tmp, cudaStream_t s) {
     MGR_TRY_CUDA(cudaMemsetAsync(g->inv, 0, sizeof(double) * n * n, s));
     MGR_LAUNCH k_csr_to_dense<<<nblocks(n, 256), 256, 0, s>>>(A.rp, A.ci, A.v, n, g->inv);
     const size_t sm = sizeof(double) * ((size_t)n * (size_t)n + (size_t)n);
-    if (sm <= 220 * 1024) {
-      MGR_TRY_CUDA(cudaFuncSetAttribute(k_dense_gj_inverse<true>,
-                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-      MGR_LAUNCH k_dense_gj_inverse<true><<<1, 1024, sm, s>>>(g->inv, (int)n, piv, h->derr);
+    if (sm <= GJ_SMEM_MAX) {
+      // the attribute is a maximum, set once (setups may run on several threads)
+      static std::once_flag gj_once;
+      static cudaError_t gj_err = cudaSuccess;
+      std::call_once(gj_once, [] {
+        gj_err = cudaFuncSetAttribute(k_dense_gj_inverse<true>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GJ_SMEM_MAX);
+      });
+      MGR_TRY_CUDA(gj_err);
+      MGR_LAUNCH k_dense_gj_inverse<true><<<1, 1024, sm, s>>>(g->inv, (int)n, piv, derr);
     } else {
-      MGR_LAUNCH k_dense_gj_inverse<false><<<1, 1024, 0, s>>>(g->inv, (int)n, piv, h->derr);
+      MGR_LAUNCH k_dense_gj_inverse<false><<<1, 1024, 0, s>>>(g->inv, (int)n, piv, derr);
     }
     MGR_TRY_CUDA(cudaGetLastError());
-    return check_dev_err(h->derr, s);
+    return check_dev_err(derr, s);
   }
   MGR_TRY_CUDA(cudaMemsetAsync(d, 0, sizeof(double) * n * n, s));
   MGR_LAUNCH k_csr_to_dense<<<nblocks(n, 256), 256, 0, s>>>(A.rp, A.ci, A.v, n, d);
-  MGR_LAUNCH k_dense_lu_inverse<<<1, 1024, 0, s>>>(d, (int)n, piv, g->inv, h->derr);
+  MGR_LAUNCH k_dense_lu_inverse<<<1, 1024, 0, s>>>(d, (int)n, piv, g->inv, derr);
   MGR_TRY_CUDA(cudaGetLastError());
-  return check_dev_err(h->derr, s);
+  return check_dev_err(derr, s);
 }
 
-int build_amg(Handle* h, const Csr& A0, const int32_t* comp0, int slot, Amg** out,
-              cudaStream_t s) {
-  Pool& P = h->pool;
+int build_amg(Handle* h, Pool& P, int* derr, const Csr& A0, bool own_input,
+              const int32_t* comp0, int slot, Amg** out, cudaStream_t s) {
   Pool tmp;
   tmp.s = s;
   Amg* g = new Amg();
@@ -1552,14 +1558,20 @@ int build_amg(Handle* h, const Csr& A0, const int32_t* comp0, int slot, Amg** ou
   g->lev.emplace_back();
   {
     AmgLevel& L0 = g->lev[0];
-    int rc = copy_csr(P, A0, L0.A, s);
-    if (rc) return rc;
-    L0.comp = P.get<int32_t>(A0.nr);
-    if (!L0.comp) return P.err;
-    if (comp0)
-      MGR_TRY_CUDA(cudaMemcpyAsync(L0.comp, comp0, sizeof(int32_t) * A0.nr, cudaMemcpyDeviceToDevice, s));
-    else
-      MGR_TRY_CUDA(cudaMemsetAsync(L0.comp, 0, sizeof(int32_t) * A0.nr, s));
+    if (own_input && comp0) {
+      // A0 and comp0 already belong to P (handed over by the caller)
+      L0.A = A0;
+      L0.comp = const_cast<int32_t*>(comp0);
+    } else {
+      int rc = copy_csr(P, A0, L0.A, s);
+      if (rc) return rc;
+      L0.comp = P.get<int32_t>(A0.nr);
+      if (!L0.comp) return P.err;
+      if (comp0)
+        MGR_TRY_CUDA(cudaMemcpyAsync(L0.comp, comp0, sizeof(int32_t) * A0.nr, cudaMemcpyDeviceToDevice, s));
+      else
+        MGR_TRY_CUDA(cudaMemsetAsync(L0.comp, 0, sizeof(int32_t) * A0.nr, s));
+    }
   }
   int rc = MGR_SUCCESS;
   for (int k = 0;; k++) {
@@ -1567,7 +1579,7 @@ int build_amg(Handle* h, const Csr& A0, const int32_t* comp0, int slot, Amg** ou
     const int64_t n = L->A.nr;
     L->dinv = P.get<double>(n);
     if (!L->dinv) { rc = P.err; break; }
-    MGR_LAUNCH k_l1_inv<<<grid_for(n, 8, 152 * 16), 256, 0, s>>>(L->A.rp, L->A.ci, L->A.v, n, L->dinv, h->derr);
+    MGR_LAUNCH k_l1_inv<<<grid_for(n, 8, 152 * 16), 256, 0, s>>>(L->A.rp, L->A.ci, L->A.v, n, L->dinv, derr);
     if (n <= o.amg_max_coarse || k + 1 >= o.amg_max_levels || k + 1 >= 32) break;
     g_trace.mark("amg l1", slot, k);
     // strength graph
@@ -1660,8 +1672,8 @@ int build_amg(Handle* h, const Csr& A0, const int32_t* comp0, int slot, Amg** ou
     MGR_TRY_CUDA(cudaGetLastError());
     g_trace.mark("amg R*(AP)", slot, k);
   }
-  if (rc == MGR_SUCCESS) rc = check_dev_err(h->derr, s);
-  if (rc == MGR_SUCCESS) rc = dense_coarsest(h, g, tmp, s);
+  if (rc == MGR_SUCCESS) rc = check_dev_err(derr, s);
+  if (rc == MGR_SUCCESS) rc = dense_coarsest(P, derr, g, tmp, s);
   g_trace.mark("amg coarsest inverse", slot, (int)g->lev.size() - 1);
   tmp.free_all_async(s);
   return rc;
@@ -1670,9 +1682,89 @@ int build_amg(Handle* h, const Csr& A0, const int32_t* comp0, int slot, Amg** ou
 // ============================================================================
 // MGR hierarchy
 // ============================================================================
+// An F-relaxation AMG whose inputs (A_FF, component ids) are owned by h->pool2,
+// to be built by the caller on a second stream.
+struct AmgJob {
+  Csr A;
+  int32_t* comp = nullptr;
+  int slot = 0;
+  Amg** out = nullptr;
+};
+
+// The second stream and host thread of build_mgr_hierarchy.
+struct SideBuild {
+  bool busy = false;
+  std::thread th;
+  cudaStream_t ss = nullptr;
+  int rc = MGR_SUCCESS;
+
+  cudaStream_t hs = nullptr;   // high-priority stream of the main thread after the fork
+
+  // Starts the side build; *ms becomes the main thread's stream from here on
+  // (highest priority, so the main branch's short, host-synchronised kernels
+  // get SMs ahead of the side build's long ones).
+  int start(Handle* h, const AmgJob& job, cudaStream_t s, cudaStream_t* ms) {
+    int dev = 0, lo = 0, hi = 0;
+    MGR_TRY_CUDA(cudaGetDevice(&dev));
+    MGR_TRY_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+    MGR_TRY_CUDA(cudaStreamCreateWithPriority(&ss, cudaStreamNonBlocking, lo));
+    MGR_TRY_CUDA(cudaStreamCreateWithPriority(&hs, cudaStreamNonBlocking, hi));
+    if (!h->derr2) {
+      h->derr2 = h->pool2.get<int>(1);
+      if (!h->derr2) return h->pool2.err;
+      MGR_TRY_CUDA(cudaMemsetAsync(h->derr2, 0, sizeof(int), s));
+    }
+    cudaEvent_t fork;
+    MGR_TRY_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+    MGR_TRY_CUDA(cudaEventRecord(fork, s));
+    MGR_TRY_CUDA(cudaStreamWaitEvent(ss, fork, 0));
+    MGR_TRY_CUDA(cudaStreamWaitEvent(hs, fork, 0));
+    cudaEventDestroy(fork);
+    h->pool2.s = ss;   // from here on only the side thread allocates from pool2
+    h->pool.s = hs;    // and the main thread allocates in its new stream's order
+    g_trace.s = hs;
+    *ms = hs;
+    busy = true;
+    th = std::thread([this, h, job, dev] {
+      cudaSetDevice(dev);
+      rc = build_amg(h, h->pool2, h->derr2, job.A, true, job.comp, job.slot, job.out, ss);
+    });
+    return MGR_SUCCESS;
+  }
+  // join the thread; s then waits for both streams' work and is again the
+  // stream of the handle's pool
+  int finish(Handle* h, cudaStream_t s) {
+    if (!busy) return MGR_SUCCESS;
+    th.join();
+    busy = false;
+    int r = rc;
+    for (cudaStream_t x : {ss, hs}) {
+      cudaEvent_t join;
+      if (cudaEventCreateWithFlags(&join, cudaEventDisableTiming) == cudaSuccess) {
+        if (cudaEventRecord(join, x) != cudaSuccess || cudaStreamWaitEvent(s, join, 0) != cudaSuccess)
+          r = r ? r : MGR_ERR_CUDA;
+        cudaEventDestroy(join);
+      } else {
+        cudaStreamSynchronize(x);
+      }
+      cudaStreamDestroy(x);
+    }
+    ss = hs = nullptr;
+    h->pool.s = s;
+    g_trace.s = s;
+    return r;
+  }
+  ~SideBuild() {
+    if (th.joinable()) th.join();   // every path calls finish(); this is a backstop
+  }
+};
+
+// s is the calling thread's stream; it changes (to the main thread's
+// high-priority stream) when this level hands its F-relaxation AMG to the
+// side build.
 static int setup_level(Handle* h, int l, const int32_t* label, const int32_t* node,
-                       const int32_t* comp, Pool& tmp, cudaStream_t s, Csr& Snext,
-                       int32_t** nlabel, int32_t** nnode, int32_t** ncomp) {
+                       const int32_t* comp, Pool& tmp, cudaStream_t& s, Csr& Snext,
+                       int32_t** nlabel, int32_t** nnode, int32_t** ncomp, SideBuild* side) {
   Pool& P = h->pool;
   MgrLevel& L = h->lev[l];
   const mgr_options_t& o = h->opt;
@@ -1709,6 +1801,32 @@ static int setup_level(Handle* h, int l, const int32_t* label, const int32_t* no
   // blocks of A: A_FF (tmp), A_FC (tmp), A_CF, A_CC (tmp)
   Csr Aff, Afc, Acc;
   MGR_TRY(extract(tmp, tmp, L.A, L.Fidx, L.nF, colF, L.nF, Aff, s));
+  // F-relaxation AMG on A_FF: handed to the side build (second stream and
+  // thread) as soon as A_FF exists, when the side build is free
+  if (L.frelax == MGR_FRELAX_AMG_VCYCLE && L.frelax_sweeps > 0) {
+    int32_t* fcomp = tmp.get<int32_t>(L.nF);
+    int32_t* dummy1 = tmp.get<int32_t>(L.nF);
+    int32_t* dummy2 = tmp.get<int32_t>(L.nF);
+    if (tmp.err) return tmp.err;
+    MGR_LAUNCH k_gather3<<<nblocks(L.nF, 256), 256, 0, s>>>(comp, label, node, L.Fidx, L.nF, fcomp, dummy1, dummy2);
+    if (side && !side->busy) {
+      // its inputs are copied into the second pool (ordered on s; the side
+      // stream waits for s before using them)
+      AmgJob job;
+      Pool& P2 = h->pool2;
+      P2.s = s;
+      MGR_TRY(copy_csr(P2, Aff, job.A, s));
+      job.comp = P2.get<int32_t>(L.nF);
+      if (!job.comp) return P2.err;
+      MGR_TRY_CUDA(cudaMemcpyAsync(job.comp, fcomp, sizeof(int32_t) * L.nF, cudaMemcpyDeviceToDevice, s));
+      job.slot = l;
+      job.out = &L.famg;
+      MGR_TRY(side->start(h, job, s, &s));
+      tmp.s = s;
+    } else {
+      MGR_TRY(build_amg(h, P, h->derr, Aff, false, fcomp, l, &L.famg, s));
+    }
+  }
   MGR_TRY(extract(tmp, tmp, L.A, L.Fidx, L.nF, colC, L.nC, Afc, s));
   MGR_TRY(extract(P, tmp, L.A, L.Cidx, L.nC, colF, L.nF, L.Acf, s));
   MGR_TRY(extract(tmp, tmp, L.A, L.Cidx, L.nC, colC, L.nC, Acc, s));
@@ -1767,15 +1885,6 @@ static int setup_level(Handle* h, int l, const int32_t* label, const int32_t* no
                                                       Snext.ci, Snext.v);
   MGR_TRY_CUDA(cudaGetLastError());
   g_trace.mark("mgr drop + S", l);
-  // F-relaxation AMG on A_FF
-  if (L.frelax == MGR_FRELAX_AMG_VCYCLE && L.frelax_sweeps > 0) {
-    int32_t* fcomp = tmp.get<int32_t>(L.nF);
-    int32_t* dummy1 = tmp.get<int32_t>(L.nF);
-    int32_t* dummy2 = tmp.get<int32_t>(L.nF);
-    if (tmp.err) return tmp.err;
-    MGR_LAUNCH k_gather3<<<nblocks(L.nF, 256), 256, 0, s>>>(comp, label, node, L.Fidx, L.nF, fcomp, dummy1, dummy2);
-    MGR_TRY(build_amg(h, Aff, fcomp, l, &L.famg, s));
-  }
   // point-block global smoother
   if (L.global_sweeps > 0) {
     int64_t* head = tmp.get<int64_t>(n + 1);
@@ -1818,32 +1927,46 @@ int build_mgr_hierarchy(Handle* h, const mgr_matrix_t* A, cudaStream_t s) {
     MGR_TRY_CUDA(cudaMemsetAsync(comp, 0, sizeof(int32_t) * n, s));
   Csr cur;
   MGR_TRY(copy_csr(P, A0, cur, s));
+  // The F-relaxation AMG of the first level that has one (A_uu's, 60% of the
+  // setup) depends only on that level's A_FF: it is built on a second stream
+  // by a second host thread (own pool and error word) while this thread goes
+  // on with the next levels and the coarsest AMG.  Each AMG is built by the
+  // same kernels in the same order as when built alone, so the results do not
+  // depend on the overlap.
+  SideBuild side;
+  cudaStream_t ms = s;   // the main thread's stream (changes at the fork)
   int rc = MGR_SUCCESS;
   for (int l = 0; l < L && rc == MGR_SUCCESS; l++) {
     Pool tmp;
-    tmp.s = s;
+    tmp.s = ms;
     h->lev[l].A = cur;
     Csr S;
     int32_t *nl = nullptr, *nn = nullptr, *nc = nullptr;
-    rc = setup_level(h, l, label, node, comp, tmp, s, S, &nl, &nn, &nc);
-    tmp.free_all_async(s);
+    rc = setup_level(h, l, label, node, comp, tmp, ms, S, &nl, &nn, &nc, &side);
+    tmp.free_all_async(ms);
     if (rc) break;
     cur = S;
     label = nl;
     node = nn;
     comp = nc;
   }
-  if (rc) return rc;
-  h->Acoarse = cur;
-  // the coarsest MGR level is a scalar problem: one component
-  Pool tmp;
-  tmp.s = s;
-  int32_t* zero = tmp.get<int32_t>(cur.nr);
-  if (!zero) return tmp.err;
-  MGR_TRY_CUDA(cudaMemsetAsync(zero, 0, sizeof(int32_t) * cur.nr, s));
-  rc = build_amg(h, cur, zero, L, &h->camg, s);
-  tmp.free_all_async(s);
-  return rc;
+  if (!rc) {
+    h->Acoarse = cur;
+    // the coarsest MGR level is a scalar problem: one component
+    Pool tmp;
+    tmp.s = ms;
+    int32_t* zero = tmp.get<int32_t>(cur.nr);
+    if (!zero) {
+      rc = tmp.err;
+    } else if (cudaMemsetAsync(zero, 0, sizeof(int32_t) * cur.nr, ms) != cudaSuccess) {
+      rc = MGR_ERR_CUDA;
+    } else {
+      rc = build_amg(h, P, h->derr, cur, false, zero, L, &h->camg, ms);
+    }
+    tmp.free_all_async(ms);
+  }
+  const int rc2 = side.finish(h, s);   // always joined, also after an error
+  return rc ? rc : rc2;
 }
 
 // ============================================================================
