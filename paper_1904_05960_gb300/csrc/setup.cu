@@ -768,24 +768,28 @@ __global__ void k_block_inv(const int64_t* __restrict__ rp, const int32_t* __res
 // ============================================================================
 // AMG setup (Sec. 6 solver settings)
 // ============================================================================
-// l1-Jacobi diagonal d_i = a_ii + sum_{j != i} |a_ij| (Baker et al. 2011),
-// warp per row.  Only the smoother uses it (no integer decision depends on
-// it), so the sum is a warp tree.
+// l1-Jacobi diagonal inverse (Baker-Falgout-Kolev-Yang pointwise l1): 1 /
+// (a_ii + sum_{j != i} |a_ij|), G lanes per row (G from the mean row length,
+// as for the sparse products: FP64 work lane-dense).  Only the smoother uses
+// it (no integer decision depends on it), so the sum is a lane tree.
+template <int G>
 __global__ void __launch_bounds__(256)
 k_l1_inv(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
          const double* __restrict__ v, int64_t n, double* __restrict__ dinv, int* err) {
-  const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
-  for (int64_t i = (int64_t)blockIdx.x * wpb + (threadIdx.x >> 5); i < n; i += (int64_t)gridDim.x * wpb) {
+  const int lane = threadIdx.x & (G - 1);
+  const unsigned mask = (G == 32) ? FULL : (((1u << G) - 1u) << ((threadIdx.x & 31) & ~(G - 1)));
+  const int64_t stride = ((int64_t)gridDim.x * blockDim.x) / G;
+  for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G; i < n; i += stride) {
     double off = 0.0, aii = 0.0;
-    for (int64_t k = rp[i] + lane; k < rp[i + 1]; k += 32) {
+    for (int64_t k = rp[i] + lane; k < rp[i + 1]; k += G) {
       const double a = v[k];
       if (ci[k] == i) aii = a;
       else off += fabs(a);
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      off += __shfl_xor_sync(FULL, off, o);
-      aii += __shfl_xor_sync(FULL, aii, o);
+    for (int o = G / 2; o > 0; o >>= 1) {
+      off += __shfl_xor_sync(mask, off, o, G);
+      aii += __shfl_xor_sync(mask, aii, o, G);
     }
     if (lane == 0) {
       double d = aii + off;
@@ -795,6 +799,21 @@ k_l1_inv(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
       }
       dinv[i] = 1.0 / d;
     }
+  }
+}
+
+static void l1_inv(const Csr& A, double* dinv, int* err, cudaStream_t s) {
+  const int64_t n = A.nr;
+  if (n <= 0) return;
+  const double avg = (double)A.nnz / (double)n;
+  const int G = avg < 3 ? 1 : avg < 8 ? 2 : avg < 64 ? 4 : avg < 192 ? 8 : 16;
+  const unsigned grid = (unsigned)std::min<int64_t>((n * G + 255) / 256, 152LL * 32);
+  switch (G) {
+    case 1: MGR_LAUNCH k_l1_inv<1><<<grid, 256, 0, s>>>(A.rp, A.ci, A.v, n, dinv, err); break;
+    case 2: MGR_LAUNCH k_l1_inv<2><<<grid, 256, 0, s>>>(A.rp, A.ci, A.v, n, dinv, err); break;
+    case 4: MGR_LAUNCH k_l1_inv<4><<<grid, 256, 0, s>>>(A.rp, A.ci, A.v, n, dinv, err); break;
+    case 8: MGR_LAUNCH k_l1_inv<8><<<grid, 256, 0, s>>>(A.rp, A.ci, A.v, n, dinv, err); break;
+    default: MGR_LAUNCH k_l1_inv<16><<<grid, 256, 0, s>>>(A.rp, A.ci, A.v, n, dinv, err); break;
   }
 }
 
@@ -1579,7 +1598,7 @@ int build_amg(Handle* h, Pool& P, int* derr, const Csr& A0, bool own_input,
     const int64_t n = L->A.nr;
     L->dinv = P.get<double>(n);
     if (!L->dinv) { rc = P.err; break; }
-    MGR_LAUNCH k_l1_inv<<<grid_for(n, 8, 152 * 16), 256, 0, s>>>(L->A.rp, L->A.ci, L->A.v, n, L->dinv, derr);
+    l1_inv(L->A, L->dinv, derr, s);
     if (n <= o.amg_max_coarse || k + 1 >= o.amg_max_levels || k + 1 >= 32) break;
     g_trace.mark("amg l1", slot, k);
     // strength graph
@@ -1634,7 +1653,9 @@ int build_amg(Handle* h, Pool& P, int* derr, const Csr& A0, bool own_input,
     L->P.rp = P.get<int64_t>(n + 1);
     if (P.err) { rc = P.err; break; }
     // FP64 work is lane-dense in the thread-per-row form; the warp form wins
-    // only where a level has too few rows to fill the GPU
+    // only where a level has too few rows to fill the GPU (measured on GB300:
+    // on the 113k-row, 150-non-zero level the warp form took 2.4 ms against
+    // 0.8 ms)
     const bool big = n >= 20000;
     if (big)
       MGR_LAUNCH k_interp_thread<false><<<nblocks(n, 128), 128, 0, s>>>(L->A.rp, L->A.ci, L->A.v, L->S.rp, L->S.ci,
@@ -1727,6 +1748,7 @@ struct SideBuild {
     busy = true;
     th = std::thread([this, h, job, dev] {
       cudaSetDevice(dev);
+      g_trace.start(ss);   // MGR_TRACE: this thread's phases are printed too
       rc = build_amg(h, h->pool2, h->derr2, job.A, true, job.comp, job.slot, job.out, ss);
     });
     return MGR_SUCCESS;
