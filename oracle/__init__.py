@@ -28,7 +28,7 @@ _lib = None
 
 MAXL = 8
 
-Q_MGR_A, Q_MGR_W, Q_MGR_COR, Q_MGR_CORKEPT, Q_MGR_S = 0, 1, 2, 3, 4
+Q_MGR_A, Q_MGR_W, Q_MGR_COR, Q_MGR_CORKEPT, Q_MGR_S, Q_MGR_WR, Q_MGR_BD = 0, 1, 2, 3, 4, 5, 6
 Q_AMG_A, Q_AMG_S, Q_AMG_P, Q_AMG_R = 10, 11, 12, 13
 
 FRELAX_AMG, FRELAX_JACOBI = 0, 1
@@ -47,6 +47,9 @@ class OrcOpts(C.Structure):
         ("amg_max_coarse", C.c_int32),
         ("amg_max_levels", C.c_int32),
         ("seed", C.c_uint64),
+        ("restrict_jacobi", C.c_int32 * MAXL),
+        ("frelax_post", C.c_int32 * MAXL),
+        ("dff_block", C.c_int32 * MAXL),
     ]
 
 
@@ -91,12 +94,15 @@ def lib():
 
 
 def default_options(two_phase=True, **kw):
-    """The solver configuration of Sec. 5.3 / Sec. 6 as read for this build.
+    """The solver configuration of Sec. 5.3 / Sec. 6.
 
     two-phase: level 0 F = {u} (F-relaxation: one AMG V-cycle, N_max = 4),
                level 1 F = {s} (one Jacobi sweep, no dropping, 3 sweeps of
                cell-block Jacobi as global smoother), coarsest = {p} by AMG.
     single-phase: level 0 F = {u}, coarsest = {p}.
+    Operator variants of Sec. 5.1, per level, all off by default:
+    restrict_jacobi (W_r = -A_CF D_FF^-1), frelax_post (Eq. MGR-post),
+    dff_block (D_FF = point-block diagonal of A_FF).
     """
     d = dict(num_levels=2 if two_phase else 1,
              f_label_mask=[1 << 0, 1 << 1] if two_phase else [1 << 0],
@@ -104,7 +110,8 @@ def default_options(two_phase=True, **kw):
              frelax_sweeps=[1, 1] if two_phase else [1],
              nmax_drop=[4, -1] if two_phase else [4],
              global_sweeps=[0, 3] if two_phase else [0],
-             amg_theta=0.25, amg_pmax=4, amg_max_coarse=64, amg_max_levels=25, seed=0)
+             amg_theta=0.25, amg_pmax=4, amg_max_coarse=64, amg_max_levels=25, seed=0,
+             restrict_jacobi=[0] * MAXL, frelax_post=[0] * MAXL, dff_block=[0] * MAXL)
     d.update(kw)
     return d
 
@@ -112,7 +119,8 @@ def default_options(two_phase=True, **kw):
 def _opts_struct(d):
     o = OrcOpts()
     o.num_levels = d["num_levels"]
-    for name in ("f_label_mask", "frelax", "frelax_sweeps", "nmax_drop", "global_sweeps"):
+    for name in ("f_label_mask", "frelax", "frelax_sweeps", "nmax_drop", "global_sweeps",
+                 "restrict_jacobi", "frelax_post", "dff_block"):
         arr = getattr(o, name)
         for i, v in enumerate(d[name]):
             arr[i] = v

@@ -16,15 +16,19 @@
  *     dropping operator G (Sec. 5.2, Eq. "drop_operator"),
  *   - the multilevel MGR V-cycle with global smoothing and F-relaxation
  *     (Sec. 5.2, Algorithm 2),
+ *   - options of Sec. 5.1: Jacobi restriction W_r = -A_CF D_FF^-1 (full
+ *     triple product R~ A P~), F-relaxation after the coarse-grid correction
+ *     (Eq. "MGR-post"), and D_FF as the point-block diagonal of A_FF,
  *   - the inner AMG (Sec. 6 solver settings: unknown approach for A_uu, scalar
  *     AMG for the pressure Schur complement, coarsest level by Gaussian
  *     elimination), and
  *   - right-preconditioned flexible GMRES (Sec. 4).
- * Where the paper is silent the readings are fixed here and listed in the
- * design notes: strength threshold 0.25 on negative couplings, PMIS coarsening
+ * Where the paper is silent these readings are taken: strength threshold 0.25
+ * on negative couplings, PMIS coarsening
  * with splitmix64 weights, direct interpolation with positive entries lumped,
  * P_max truncation with row-sum rescaling, l1-Jacobi smoothing, 2x2 cell-block
- * Jacobi global smoother, modified Gram-Schmidt Arnoldi.
+ * Jacobi global smoother, modified Gram-Schmidt Arnoldi; with the Jacobi
+ * restriction the dropping G acts on the whole correction A_CC - R~ A P~.
  *
  * Summation order rule: every setup sum runs over ascending column / inner
  * index, starting from 0.0, one rounding per multiply and per add (build with
@@ -66,6 +70,12 @@ typedef struct {
   double amg_theta;
   int32_t amg_pmax, amg_max_coarse, amg_max_levels;
   uint64_t seed;
+  /* operator variants of Sec. 5.1 (all 0: the scheme of Sec. 5.3) */
+  int32_t restrict_jacobi[MAXL]; /* 1: W_r = -A_CF D_FF^-1 instead of W_r = 0 */
+  int32_t frelax_post[MAXL];     /* 1: F-relaxation after the coarse-grid
+                                    correction (Eq. MGR-post), else before */
+  int32_t dff_block[MAXL];       /* 1: D_FF = point-block diagonal of A_FF
+                                    (blocks of F dofs sharing dof_node) */
 } orc_opts;
 
 typedef struct {
@@ -93,7 +103,10 @@ typedef struct {
   ocsr W;                 /* W_p = -D_FF^-1 A_FC   (nF x nC) */
   ocsr Acf;               /* A_CF (nC x nF) */
   ocsr Afc;               /* A_FC (nF x nC) */
-  ocsr cor;               /* A_cor = A_CF D^-1 A_FC before dropping (nC x nC) */
+  ocsr Wr;                /* W_r = -A_CF D_FF^-1 (nC x nF; Jacobi restriction) */
+  ocsr Bd;                /* D_FF^-1 as a sparse matrix (nF x nF; point blocks) */
+  ocsr cor;               /* A_cor before dropping (nC x nC): A_CF D^-1 A_FC, or
+                             with Jacobi restriction A_CC - R~ A P~ */
   ocsr corkept;           /* G(A_cor) */
   amg_t *famg;            /* F-relaxation AMG on A_FF */
   int64_t nblk;           /* global smoother: blocks of equal dof_node */
@@ -579,6 +592,7 @@ static int small_inverse(const double *a, double *inv, int b) {
 
 static void mgr_level_free(mgr_level *l) {
   csr_free(&l->A); csr_free(&l->W); csr_free(&l->Acf); csr_free(&l->Afc);
+  csr_free(&l->Wr); csr_free(&l->Bd);
   csr_free(&l->cor); csr_free(&l->corkept);
   free(l->label); free(l->node); free(l->comp); free(l->Fidx); free(l->Cidx); free(l->pos);
   free(l->dF); free(l->bstart); free(l->bsize); free(l->binv);
@@ -619,16 +633,87 @@ static int mgr_level_setup(oracle_t *h, int l, ocsr *Snext) {
   csr_extract(&L->A, L->Fidx, nF, cpos, nC, &L->Afc);
   csr_extract(&L->A, L->Cidx, nC, fpos, nF, &L->Acf);
   csr_extract(&L->A, L->Cidx, nC, cpos, nC, &Acc);
-  /* T = D_FF^-1 A_FC (t = a / d); W_p = -T. */
+  /* T = D_FF^-1 A_FC; W_p = -T (Eq. injective_rp).  Pointwise D_FF: t = a / d.
+   * Point-block D_FF (blocks = runs of F dofs sharing dof_node, at most 4):
+   * Bd = the block inverses as a sparse matrix, T = Bd A_FC. */
   ocsr T;
-  csr_copy(&L->Afc, &T);
-  csr_copy(&L->Afc, &L->W);
-  for (int64_t f = 0; f < nF; f++)
-    for (int64_t k = T.rp[f]; k < T.rp[f + 1]; k++) {
-      T.v[k] = L->Afc.v[k] / L->dF[f];
-      L->W.v[k] = -T.v[k];
+  if (o->dff_block[l]) {
+    int64_t cap = 0;
+    for (int64_t f = 0; f < nF;) {
+      int64_t g = f + 1;
+      while (g < nF && L->node[L->Fidx[g]] == L->node[L->Fidx[f]]) g++;
+      if (g - f > 4) { free(fpos); free(cpos); csr_free(&Aff); csr_free(&Acc); return ORC_ERR_ARG; }
+      cap += (g - f) * (g - f);
+      f = g;
     }
-  csr_matmul(&L->Acf, &T, &L->cor);
+    csr_init(&L->Bd, nF, nF, cap);
+    int64_t nb = 0;
+    for (int64_t f = 0; f < nF;) {
+      int64_t g = f + 1;
+      while (g < nF && L->node[L->Fidx[g]] == L->node[L->Fidx[f]]) g++;
+      int b = (int)(g - f);
+      double blk[16], inv[16];
+      for (int r = 0; r < b; r++)
+        for (int c = 0; c < b; c++) blk[r * b + c] = csr_get(&Aff, f + r, f + c);
+      if (small_inverse(blk, inv, b) != ORC_OK) {
+        free(fpos); free(cpos); csr_free(&Aff); csr_free(&Acc); return ORC_ERR_ZERO_DIAG;
+      }
+      for (int r = 0; r < b; r++) {
+        for (int c = 0; c < b; c++) { L->Bd.ci[nb] = (int32_t)(f + c); L->Bd.v[nb] = inv[r * b + c]; nb++; }
+        L->Bd.rp[f + r + 1] = nb;
+      }
+      f = g;
+    }
+    csr_matmul(&L->Bd, &L->Afc, &T);
+  } else {
+    csr_copy(&L->Afc, &T);
+    for (int64_t f = 0; f < nF; f++)
+      for (int64_t k = T.rp[f]; k < T.rp[f + 1]; k++) T.v[k] = L->Afc.v[k] / L->dF[f];
+  }
+  csr_copy(&T, &L->W);
+  for (int64_t k = 0; k < T.nnz; k++) L->W.v[k] = -T.v[k];
+  ocsr C1;
+  csr_matmul(&L->Acf, &T, &C1);            /* A_CF D^-1 A_FC */
+  if (o->restrict_jacobi[l]) {
+    /* U = A_CF D_FF^-1 (pointwise: u = a / d of its column; point-block:
+     * U = A_CF Bd); W_r = -U.  R~ A P~ = A_CC + W_r A_FC + A_CF W_p
+     * + W_r A_FF W_p = A_CC - [2 A_CF T - U (A_FF T)], and the bracket is
+     * the correction that G sparsifies. */
+    ocsr U, K, E;
+    if (o->dff_block[l]) {
+      csr_matmul(&L->Acf, &L->Bd, &U);
+    } else {
+      csr_copy(&L->Acf, &U);
+      for (int64_t k = 0; k < U.nnz; k++) U.v[k] = L->Acf.v[k] / L->dF[L->Acf.ci[k]];
+    }
+    csr_copy(&U, &L->Wr);
+    for (int64_t k = 0; k < U.nnz; k++) L->Wr.v[k] = -U.v[k];
+    csr_matmul(&Aff, &T, &K);
+    csr_matmul(&U, &K, &E);
+    /* cor = 2 C1 - E on the union pattern: (2 c or 0) - (e or 0) */
+    csr_init(&L->cor, nC, nC, C1.nnz + E.nnz);
+    int64_t nn = 0;
+    for (int64_t i = 0; i < nC; i++) {
+      int64_t p = C1.rp[i], pe = C1.rp[i + 1], q = E.rp[i], qe = E.rp[i + 1];
+      while (p < pe || q < qe) {
+        int64_t cp = (p < pe) ? C1.ci[p] : INT64_MAX;
+        int64_t cq = (q < qe) ? E.ci[q] : INT64_MAX;
+        double a = 0.0, e = 0.0;
+        int64_t col;
+        if (cp == cq) { col = cp; a = 2.0 * C1.v[p++]; e = E.v[q++]; }
+        else if (cp < cq) { col = cp; a = 2.0 * C1.v[p++]; }
+        else { col = cq; e = E.v[q++]; }
+        L->cor.ci[nn] = (int32_t)col;
+        L->cor.v[nn] = a - e;
+        nn++;
+      }
+      L->cor.rp[i + 1] = nn;
+    }
+    L->cor.nnz = nn;
+    csr_free(&U); csr_free(&K); csr_free(&E); csr_free(&C1);
+  } else {
+    L->cor = C1;
+  }
   csr_free(&T);
   /* G: keep own-point columns plus the nmax largest |value| others. */
   int32_t *cnode = xcalloc((size_t)nC, sizeof(int32_t));
@@ -720,6 +805,23 @@ static int mgr_level_setup(oracle_t *h, int l, ocsr *Snext) {
 /* -------------------------------------------------------------------------- */
 /* MGR apply: Algorithm 2 (multilevel, pre-smoothing F-relaxation)            */
 /* -------------------------------------------------------------------------- */
+/* F-relaxation sweeps: z <- z + Q M_FF^-1 Q^T (v - A z), M_FF^-1 one AMG
+ * V-cycle or Jacobi with D_FF (pointwise, or the point-block inverse Bd). */
+static void mgr_frelax(const oracle_t *h, int l, const double *v, double *z, double *r,
+                       double *rf, double *ef) {
+  const mgr_level *L = &h->lev[l];
+  const orc_opts *o = &h->o;
+  int64_t nF = L->nF;
+  for (int sw = 0; sw < o->frelax_sweeps[l]; sw++) {
+    residual(&L->A, v, z, r);
+    for (int64_t f = 0; f < nF; f++) rf[f] = r[L->Fidx[f]];
+    if (o->frelax[l] == 0) amg_vcycle(L->famg, 0, rf, ef);
+    else if (o->dff_block[l]) spmv(&L->Bd, rf, ef);
+    else for (int64_t f = 0; f < nF; f++) ef[f] = rf[f] / L->dF[f];
+    for (int64_t f = 0; f < nF; f++) z[L->Fidx[f]] += ef[f];
+  }
+}
+
 static void mgr_apply_level(const oracle_t *h, int l, const double *v, double *z) {
   if (l == h->L) {           /* coarsest MGR level: one AMG V-cycle */
     amg_vcycle(h->camg, 0, v, z);
@@ -749,23 +851,27 @@ static void mgr_apply_level(const oracle_t *h, int l, const double *v, double *z
       for (int i = 0; i < b; i++) z[s0 + i] += d[i];
     }
   }
-  /* F-relaxation: z <- z + Q M_FF^-1 Q^T (v - A z) */
-  for (int sw = 0; sw < o->frelax_sweeps[l]; sw++) {
-    residual(&L->A, v, z, r);
-    for (int64_t f = 0; f < nF; f++) rf[f] = r[L->Fidx[f]];
-    if (o->frelax[l] == 0) amg_vcycle(L->famg, 0, rf, ef);
-    else for (int64_t f = 0; f < nF; f++) ef[f] = rf[f] / L->dF[f];
-    for (int64_t f = 0; f < nF; f++) z[L->Fidx[f]] += ef[f];
-  }
-  /* restrict: r_C = R~ (v - A z) with injection R~ = [0 I] */
+  /* F-relaxation before the coarse-grid correction (Eq. MGR-pre) */
+  if (!o->frelax_post[l]) mgr_frelax(h, l, v, z, r, rf, ef);
+  /* restrict: r_C = R~ (v - A z), R~ = [W_r I]: injection (W_r = 0) or
+   * Jacobi restriction r_C += W_r r_F */
   residual(&L->A, v, z, r);
   for (int64_t c = 0; c < nC; c++) rc[c] = r[L->Cidx[c]];
+  if (o->restrict_jacobi[l]) {
+    double *t = xcalloc((size_t)nC, sizeof(double));
+    for (int64_t f = 0; f < nF; f++) rf[f] = r[L->Fidx[f]];
+    spmv(&L->Wr, rf, t);
+    for (int64_t c = 0; c < nC; c++) rc[c] += t[c];
+    free(t);
+  }
   /* recursion */
   mgr_apply_level(h, l + 1, rc, ec);
   /* interpolate e = P~ e_C = [W_p e_C; e_C] and correct */
   spmv(&L->W, ec, ef);
   for (int64_t f = 0; f < nF; f++) z[L->Fidx[f]] += ef[f];
   for (int64_t c = 0; c < nC; c++) z[L->Cidx[c]] += ec[c];
+  /* F-relaxation after the correction (Eq. MGR-post) */
+  if (o->frelax_post[l]) mgr_frelax(h, l, v, z, r, rf, ef);
   free(r); free(rf); free(ef); free(rc); free(ec);
 }
 
@@ -942,6 +1048,8 @@ enum {
   Q_MGR_COR = 2,    /* A_cor before dropping (nC x nC)         */
   Q_MGR_CORKEPT = 3,/* G(A_cor)                                */
   Q_MGR_S = 4,      /* next level operator S_{l+1}             */
+  Q_MGR_WR = 5,     /* W_r of level l (nC x nF; Jacobi restriction) */
+  Q_MGR_BD = 6,     /* point-block D_FF^-1 of level l (nF x nF) */
   Q_AMG_A = 10,     /* AMG slot s, level k operator            */
   Q_AMG_S = 11,     /* strength pattern                        */
   Q_AMG_P = 12,     /* interpolation                           */
@@ -958,6 +1066,8 @@ static const ocsr *orc_csr_ptr(oracle_t *h, int kind, int slot, int lvl) {
       case Q_MGR_COR: return &L->cor;
       case Q_MGR_CORKEPT: return &L->corkept;
       case Q_MGR_S: return (slot + 1 < h->L) ? &h->lev[slot + 1].A : &h->Acoarse;
+      case Q_MGR_WR: return L->Wr.rp ? &L->Wr : NULL;
+      case Q_MGR_BD: return L->Bd.rp ? &L->Bd : NULL;
     }
     return NULL;
   }

@@ -356,3 +356,108 @@ def test_restarted_fgmres_converges():
     o = oracle.Oracle(p)
     r = o.fgmres(p.rhs, restart=5, maxit=500, rtol=1e-8)
     assert r["status"] == 0 and r["relres"] <= 1e-8
+
+
+# ---------------------------------------------------------------------------
+# Operator variants of Sec. 5.1: Jacobi restriction, MGR-post, point-block D_FF
+# ---------------------------------------------------------------------------
+def _dense_blocks(p, level_mask=1):
+    """Dense A and the F / C index sets of the first reduction (F = u)."""
+    A = p.to_scipy().toarray()
+    F = np.nonzero(((level_mask >> p.dof_label) & 1) == 1)[0]
+    C = np.nonzero(((level_mask >> p.dof_label) & 1) == 0)[0]
+    return A, F, C
+
+
+def _point_block_inverse(A, F, node):
+    """D_FF^-1 with D_FF = blocks of consecutive F dofs sharing dof_node."""
+    nF = len(F)
+    Bd = np.zeros((nF, nF))
+    f = 0
+    while f < nF:
+        g = f + 1
+        while g < nF and node[F[g]] == node[F[f]]:
+            g += 1
+        Bd[f:g, f:g] = np.linalg.inv(A[np.ix_(F[f:g], F[f:g])])
+        f = g
+    return Bd
+
+
+@pytest.mark.parametrize("block", [0, 1])
+def test_jacobi_restriction_gives_the_full_triple_product(block):
+    # Sec. 5.1: W_r = -A_CF D^-1, W_p = -D^-1 A_FC; with no dropping the coarse
+    # operator must be R~ A P~ = A_CC + W_r A_FC + A_CF W_p + W_r A_FF W_p.
+    # lognormal E: the nodal 3x3 blocks of A_uu are not diagonal
+    p = synth.two_phase(3, 3, 2, seed=1, E_sigma=1.0)
+    o = oracle.Oracle(p, num_levels=1, f_label_mask=[1], frelax=[0], frelax_sweeps=[1],
+                      nmax_drop=[-1], global_sweeps=[0], restrict_jacobi=[1], dff_block=[block])
+    A, F, C = _dense_blocks(p)
+    Aff, Afc, Acf, Acc = (A[np.ix_(F, F)], A[np.ix_(F, C)], A[np.ix_(C, F)], A[np.ix_(C, C)])
+    Dinv = _point_block_inverse(A, F, p.dof_node) if block else np.diag(1.0 / np.diag(Aff))
+    Wp = -Dinv @ Afc
+    Wr = -Acf @ Dinv
+    rap = Acc + Wr @ Afc + Acf @ Wp + Wr @ Aff @ Wp
+    S = o.scipy(oracle.Q_MGR_S, 0).toarray()
+    assert np.abs(S - rap).max() <= 1e-12 * np.abs(rap).max()
+    assert np.abs(o.scipy(oracle.Q_MGR_WR, 0).toarray() - Wr).max() <= 1e-14 * np.abs(Wr).max()
+    assert np.abs(o.scipy(oracle.Q_MGR_W, 0).toarray() - Wp).max() <= 1e-14 * np.abs(Wp).max()
+
+
+def test_point_block_dff_interpolation_and_coarse_grid():
+    # D_FF as the 3x3 nodal blocks of A_uu (and 1x1 for s): W_p = -Bd A_FC and
+    # S = A_CC - A_CF Bd A_FC, Bd = block inverses, with no dropping.
+    # lognormal E: with a uniform modulus the free nodes' 3x3 self-blocks are
+    # diagonal on this mesh and both choices of D_FF coincide
+    p = synth.two_phase(3, 3, 2, seed=2, E_sigma=1.0)
+    o = oracle.Oracle(p, num_levels=1, f_label_mask=[1], frelax=[0], frelax_sweeps=[1],
+                      nmax_drop=[-1], global_sweeps=[0], dff_block=[1])
+    A, F, C = _dense_blocks(p)
+    Bd = _point_block_inverse(A, F, p.dof_node)
+    assert np.abs(o.scipy(oracle.Q_MGR_BD, 0).toarray() - Bd).max() <= 1e-13 * np.abs(Bd).max()
+    Wp = -Bd @ A[np.ix_(F, C)]
+    S_ref = A[np.ix_(C, C)] + A[np.ix_(C, F)] @ Wp
+    assert np.abs(o.scipy(oracle.Q_MGR_W, 0).toarray() - Wp).max() <= 1e-13 * np.abs(Wp).max()
+    assert np.abs(o.scipy(oracle.Q_MGR_S, 0).toarray() - S_ref).max() <= 1e-12 * np.abs(S_ref).max()
+    # blocks are 3x3 on u: the interpolation differs from the pointwise one
+    o1 = oracle.Oracle(p, num_levels=1, f_label_mask=[1], frelax=[0], frelax_sweeps=[1],
+                       nmax_drop=[-1], global_sweeps=[0])
+    assert np.abs(o1.scipy(oracle.Q_MGR_W, 0).toarray() - Wp).max() > 1e-6 * np.abs(Wp).max()
+
+
+@pytest.mark.parametrize("post", [0, 1])
+@pytest.mark.parametrize("jac", [0, 1])
+def test_mgr_pre_and_post_error_propagation(post, jac):
+    # Eqs. MGR-pre / MGR-post with exact components: F-relaxation
+    # M_FF^-1 = Q (Q^T A Q)^-1 Q^T and coarse solve (R~ A P~)^-1 (both AMGs are
+    # a single dense level on this tiny system, and nothing is dropped), so
+    #   pre:  I - M^-1 A = (I - P~ M_CC^-1 R~ A)(I - M_FF^-1 A)
+    #   post: I - M^-1 A = (I - M_FF^-1 A)(I - P~ M_CC^-1 R~ A).
+    p = synth.two_phase(2, 2, 2, seed=3)
+    o = oracle.Oracle(p, num_levels=1, f_label_mask=[1], frelax=[0], frelax_sweeps=[1],
+                      nmax_drop=[-1], global_sweeps=[0], amg_max_coarse=200,
+                      restrict_jacobi=[jac], frelax_post=[post])
+    assert o.amg_levels(0) == 1 and o.amg_levels(1) == 1
+    A, F, C = _dense_blocks(p)
+    n, nF, nC = p.n, len(F), len(C)
+    Dinv = np.diag(1.0 / np.diag(A[np.ix_(F, F)]))
+    Pt = np.zeros((n, nC))
+    Pt[np.ix_(F, np.arange(nC))] = -Dinv @ A[np.ix_(F, C)]
+    Pt[C, np.arange(nC)] = 1.0
+    Rt = np.zeros((nC, n))
+    Rt[np.arange(nC), C] = 1.0
+    if jac:
+        Rt[np.ix_(np.arange(nC), F)] = -A[np.ix_(C, F)] @ Dinv
+    Mcc_inv = np.linalg.inv(Rt @ A @ Pt)
+    Q = np.zeros((n, nF))
+    Q[F, np.arange(nF)] = 1.0
+    Mff_inv = Q @ np.linalg.inv(Q.T @ A @ Q) @ Q.T
+    I = np.eye(n)
+    Ecg = I - Pt @ Mcc_inv @ Rt @ A
+    Ef = I - Mff_inv @ A
+    E_ref = Ef @ Ecg if post else Ecg @ Ef
+    MinvA = np.column_stack([o.apply(A[:, j]) for j in range(n)])
+    E = I - MinvA
+    assert np.abs(E - E_ref).max() <= 1e-9
+    # the two orderings are different operators
+    E_other = Ecg @ Ef if post else Ef @ Ecg
+    assert np.abs(E - E_other).max() > 1e-6
