@@ -106,6 +106,19 @@ typedef struct {
   int32_t amg_max_levels;
   int32_t precision;                        /* MGR_FP64 or MGR_MIXED */
   uint64_t seed;                            /* PMIS weight hash seed */
+  /* Operator variants of Sec. 5.1, per level (all 0 in the defaults):
+   * restrict_jacobi: restriction R~ = [W_r I] with W_r = -A_CF D_FF^-1
+   *   instead of injection; the coarse grid is then the full triple product
+   *   A_CC - G(A_cor) with A_cor = A_CC - R~ A P~ = 2 A_CF T - W'(A_FF T),
+   *   T = D_FF^-1 A_FC, W' = A_CF D_FF^-1, and r_C = (v - A z)_C + W_r (v - A z)_F;
+   * frelax_post: F-relaxation after the coarse-grid correction (Eq.
+   *   "MGR-post") instead of before it (Eq. "MGR-pre");
+   * dff_block: D_FF = the point-block diagonal of A_FF (runs of F dofs sharing
+   *   dof_node, at most 4: the 3x3 nodal blocks of A_uu) instead of
+   *   diag(A_FF), in W_p, W_r and the Jacobi F-relaxation. */
+  int32_t restrict_jacobi[MGR_MAX_LEVELS];
+  int32_t frelax_post[MGR_MAX_LEVELS];
+  int32_t dff_block[MGR_MAX_LEVELS];
 } mgr_options_t;
 
 typedef struct {
@@ -170,8 +183,11 @@ const char* mgr_error_string(int code);
 
 /* Hierarchy matrices, copied to HOST buffers.  kind:
  *   0 A_l of MGR level `slot`;   1 W_p of level slot (nF x nC);
- *   2 A_cor = A_CF D_FF^-1 A_FC before dropping;  3 G(A_cor);
+ *   2 A_cor before dropping (A_CF D_FF^-1 A_FC, or A_CC - R~ A P~ with the
+ *     Jacobi restriction);  3 G(A_cor);
  *   4 the next-level operator S_{slot+1};
+ *   5 W_r of level slot (nC x nF; only with restrict_jacobi);
+ *   6 D_FF^-1 of level slot as a sparse matrix (nF x nF; only with dff_block);
  *   10 AMG operator, 11 strength pattern, 12 interpolation P, 13 R = P^T of
  *   AMG slot `slot` (0..L-1: F-relaxation AMG of MGR level slot; L: the AMG
  *   of the coarsest MGR level), level `lvl`.

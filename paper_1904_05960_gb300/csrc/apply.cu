@@ -457,39 +457,66 @@ static void mgr_level(Handle* h, int l, const T* v, T* z, cudaStream_t s) {
         }
     zero = false;
   }
-  // F-relaxation z <- z + Q M_FF^-1 Q^T (v - A z)
   T* rF = (T*)L.rF;
   T* eF = (T*)L.eF;
   const T* zF_only = nullptr;   // z = [e_F at F, 0 at C], not materialised
-  for (int sw = 0; sw < L.frelax_sweeps; sw++) {
+  // F-relaxation sweeps z <- z + Q M_FF^-1 Q^T (v - A z), M_FF^-1 one AMG
+  // V-cycle or Jacobi (pointwise or point-block D_FF): before the coarse-grid
+  // correction (Eq. MGR-pre) or after it (Eq. MGR-post)
+  auto frelax = [&]() {
+    for (int sw = 0; sw < L.frelax_sweeps; sw++) {
+      if (zF_only) {
+        cudaMemsetAsync(z, 0, sizeof(T) * n, s);
+        MGR_LAUNCH k_scatter_add<T><<<vgrid(nF), 256, 0, s>>>(z, L.Fidx, eF, nullptr, nF);
+        zF_only = nullptr;
+        zero = false;
+      }
+      const T* rhs;
+      if (zero) {
+        if (L.F_is_prefix) {
+          rhs = v;
+        } else {
+          MGR_LAUNCH k_gather<T><<<vgrid(nF), 256, 0, s>>>(v, L.Fidx, nF, rF);
+          rhs = rF;
+        }
+      } else {
+        spmv_launch<T, T, T, MODE_RROWS>(L.A.rp, L.A.ci, Av, nF, L.A.nnz * nF / (n > 0 ? n : 1), z,
+                                         rF, v, nullptr, L.Fidx, s);
+        rhs = rF;
+      }
+      if (L.frelax == MGR_FRELAX_AMG_VCYCLE) vcycle<T>(L.famg, 0, rhs, eF, s);
+      else if (L.dff_block) spmv<T, MODE_AX>(L.Bd, rhs, eF, nullptr, nullptr, nullptr, s);
+      else MGR_LAUNCH k_scale<T><<<vgrid(nF), 256, 0, s>>>(pick<T>(L.dFinv, L.dFinvf), rhs, eF, nF);
+      if (zero) zF_only = eF;
+      else MGR_LAUNCH k_scatter_add<T><<<vgrid(nF), 256, 0, s>>>(z, L.Fidx, eF, nullptr, nF);
+    }
+  };
+  if (!L.frelax_post) frelax();
+  // restrict r_C = R~ (v - A z): injection (W_r = 0), plus W_r r_F with the
+  // Jacobi restriction
+  T* rC = (T*)L.rC;
+  T* eC = (T*)L.eC;
+  if (L.restrict_jacobi) {
     if (zF_only) {
       cudaMemsetAsync(z, 0, sizeof(T) * n, s);
       MGR_LAUNCH k_scatter_add<T><<<vgrid(nF), 256, 0, s>>>(z, L.Fidx, eF, nullptr, nF);
       zF_only = nullptr;
       zero = false;
     }
-    const T* rhs;
+    const T* rFsrc = rF;
     if (zero) {
-      if (L.F_is_prefix) {
-        rhs = v;
-      } else {
-        MGR_LAUNCH k_gather<T><<<vgrid(nF), 256, 0, s>>>(v, L.Fidx, nF, rF);
-        rhs = rF;
-      }
+      if (L.F_is_prefix) rFsrc = v;
+      else MGR_LAUNCH k_gather<T><<<vgrid(nF), 256, 0, s>>>(v, L.Fidx, nF, rF);
+      MGR_LAUNCH k_gather<T><<<vgrid(nC), 256, 0, s>>>(v, L.Cidx, nC, rC);
+      cudaMemsetAsync(z, 0, sizeof(T) * n, s);
     } else {
       spmv_launch<T, T, T, MODE_RROWS>(L.A.rp, L.A.ci, Av, nF, L.A.nnz * nF / (n > 0 ? n : 1), z,
                                        rF, v, nullptr, L.Fidx, s);
-      rhs = rF;
+      spmv_launch<T, T, T, MODE_RROWS>(L.A.rp, L.A.ci, Av, nC, L.A.nnz * nC / (n > 0 ? n : 1), z,
+                                       rC, v, nullptr, L.Cidx, s);
     }
-    if (L.frelax == MGR_FRELAX_AMG_VCYCLE) vcycle<T>(L.famg, 0, rhs, eF, s);
-    else MGR_LAUNCH k_scale<T><<<vgrid(nF), 256, 0, s>>>(pick<T>(L.dFinv, L.dFinvf), rhs, eF, nF);
-    if (zero) zF_only = eF;
-    else MGR_LAUNCH k_scatter_add<T><<<vgrid(nF), 256, 0, s>>>(z, L.Fidx, eF, nullptr, nF);
-  }
-  // restrict r_C = (v - A z)_C (injection restriction, W_r = 0)
-  T* rC = (T*)L.rC;
-  T* eC = (T*)L.eC;
-  if (zF_only) {
+    spmv<T, MODE_ADD>(L.Wr, rFsrc, rC, nullptr, nullptr, nullptr, s);
+  } else if (zF_only) {
     // z is zero outside F, so (A z)_C = A_CF z_F
     spmv_launch<T, T, T, MODE_GRES>(L.Acf.rp, L.Acf.ci, vals<T>(L.Acf), nC, L.Acf.nnz, zF_only,
                                     rC, v, nullptr, L.Cidx, s);
@@ -513,6 +540,12 @@ static void mgr_level(Handle* h, int l, const T* v, T* z, cudaStream_t s) {
     case 8: MGR_LAUNCH k_interp_correct<T, 8><<<grid, 256, 0, s>>>(L.W.rp, L.W.ci, wv, Fi, Ci, nF, nC, eC, zF_only, z); break;
     case 16: MGR_LAUNCH k_interp_correct<T, 16><<<grid, 256, 0, s>>>(L.W.rp, L.W.ci, wv, Fi, Ci, nF, nC, eC, zF_only, z); break;
     default: MGR_LAUNCH k_interp_correct<T, 32><<<grid, 256, 0, s>>>(L.W.rp, L.W.ci, wv, Fi, Ci, nF, nC, eC, zF_only, z); break;
+  }
+  if (L.frelax_post) {
+    // z is materialised by the correction
+    zF_only = nullptr;
+    zero = false;
+    frelax();
   }
 }
 

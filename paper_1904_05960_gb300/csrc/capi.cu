@@ -48,6 +48,8 @@ static const Csr* find_csr(Handle* h, int kind, int slot, int lvl) {
       case 2: return &L.cor;
       case 3: return &L.corkept;
       case 4: return (slot + 1 < h->L) ? &h->lev[slot + 1].A : &h->Acoarse;
+      case 5: return L.Wr.rp ? &L.Wr : nullptr;
+      case 6: return L.Bd.rp ? &L.Bd : nullptr;
     }
     return nullptr;
   }
@@ -84,6 +86,7 @@ void mgr_options_default(mgr_options_t* o, int two_phase) {
   o->frelax[0] = MGR_FRELAX_AMG_VCYCLE;
   o->frelax[1] = MGR_FRELAX_JACOBI;
   for (int l = 0; l < MGR_MAX_LEVELS; l++) o->frelax_sweeps[l] = 1;
+  // restrict_jacobi, frelax_post, dff_block: 0 (memset above)
   o->nmax_drop[0] = 4;
   for (int l = 1; l < MGR_MAX_LEVELS; l++) o->nmax_drop[l] = -1;
   o->global_sweeps[0] = 0;

@@ -126,6 +126,9 @@ struct MgrLevel {
   double* dFinv = nullptr;       // 1 / diag(A_FF)
   float* dFinvf = nullptr;
   Csr W;                         // W_p = -D_FF^-1 A_FC (nF x nC)
+  Csr Wr;                        // W_r = -A_CF D_FF^-1 (nC x nF; Jacobi restriction)
+  Csr Bd;                        // point-block D_FF^-1 (nF x nF; dff_block)
+  bool restrict_jacobi = false, frelax_post = false, dff_block = false;
   Csr Acf;                       // A_CF (nC x nF)
   Csr cor, corkept;              // A_cor before / after G (inspection)
   Amg* famg = nullptr;           // F-relaxation AMG on A_FF

@@ -581,7 +581,8 @@ __global__ void k_dff_and_w(const int64_t* __restrict__ arp, const int32_t* __re
                             const double* __restrict__ av, const int64_t* __restrict__ Fidx,
                             int64_t nF, const int64_t* __restrict__ frp,
                             const double* __restrict__ fv, double* __restrict__ tv,
-                            double* __restrict__ wv, double* __restrict__ dinv, int* err) {
+                            double* __restrict__ wv, double* __restrict__ dinv,
+                            double* __restrict__ dval, int* err) {
   int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (f >= nF) return;
   int64_t r = Fidx[f];
@@ -593,11 +594,55 @@ __global__ void k_dff_and_w(const int64_t* __restrict__ arp, const int32_t* __re
     d = 1.0;
   }
   dinv[f] = 1.0 / d;
+  dval[f] = d;
   for (int64_t k = frp[f]; k < frp[f + 1]; k++) {
     double t = __ddiv_rn(fv[k], d);
     tv[k] = t;
     wv[k] = -t;
   }
+}
+
+// U = A_CF D_FF^-1 for a pointwise D_FF: u = a / d of its column (exact
+// division, as T = D^-1 A_FC); W_r = -U.
+__global__ void k_acf_dinv(const int32_t* __restrict__ ci, const double* __restrict__ v, int64_t nnz,
+                           const double* __restrict__ dval, double* __restrict__ u,
+                           double* __restrict__ wr) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nnz) return;
+  const double t = __ddiv_rn(v[k], dval[ci[k]]);
+  u[k] = t;
+  wr[k] = -t;
+}
+
+// point-block D_FF^-1 as a CSR matrix: block k (rows bstart[k] .. +b) holds
+// its b x b inverse (binv: 16 per block, row-major 4 x 4)
+__global__ void k_bd_counts(const int64_t* __restrict__ bstart, int64_t nblk, int64_t* __restrict__ cnt) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nblk) return;
+  const int64_t s0 = bstart[k];
+  const int b = (int)(bstart[k + 1] - s0);
+  for (int r = 0; r < b; r++) cnt[s0 + r] = b;
+}
+__global__ void k_bd_fill(const int64_t* __restrict__ bstart, int64_t nblk, const double* __restrict__ binv,
+                          const int64_t* __restrict__ rp, int32_t* __restrict__ ci, double* __restrict__ v) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nblk) return;
+  const int64_t s0 = bstart[k];
+  const int b = (int)(bstart[k + 1] - s0);
+  for (int r = 0; r < b; r++)
+    for (int c = 0; c < b; c++) {
+      ci[rp[s0 + r] + c] = (int32_t)(s0 + c);
+      v[rp[s0 + r] + c] = binv[k * 16 + r * 4 + c];
+    }
+}
+
+__global__ void k_neg(const double* __restrict__ a, double* __restrict__ b, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = -a[i];
+}
+__global__ void k_twice(double* __restrict__ a, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    a[i] = 2.0 * a[i];   // exact
 }
 
 // G: keep the own-point columns plus the nmax others of largest |value|
@@ -1798,6 +1843,9 @@ static int setup_level(Handle* h, int l, const int32_t* label, const int32_t* no
   L.frelax = o.frelax[l];
   L.frelax_sweeps = o.frelax_sweeps[l];
   L.global_sweeps = o.global_sweeps[l];
+  L.restrict_jacobi = o.restrict_jacobi[l] != 0;
+  L.frelax_post = o.frelax_post[l] != 0;
+  L.dff_block = o.dff_block[l] != 0;
   if (L.frelax != MGR_FRELAX_AMG_VCYCLE && L.frelax != MGR_FRELAX_JACOBI) return MGR_ERR_INVALID_ARG;
   if (L.frelax_sweeps < 0 || L.global_sweeps < 0) return MGR_ERR_INVALID_ARG;
 
@@ -1852,23 +1900,107 @@ static int setup_level(Handle* h, int l, const int32_t* label, const int32_t* no
   MGR_TRY(extract(tmp, tmp, L.A, L.Fidx, L.nF, colC, L.nC, Afc, s));
   MGR_TRY(extract(P, tmp, L.A, L.Cidx, L.nC, colF, L.nF, L.Acf, s));
   MGR_TRY(extract(tmp, tmp, L.A, L.Cidx, L.nC, colC, L.nC, Acc, s));
-  // D_FF, T = D^-1 A_FC, W_p = -T
+  // D_FF, T = D^-1 A_FC, W_p = -T (pointwise D_FF: t = a / d)
   L.dFinv = P.get<double>(L.nF);
+  double* dval = tmp.get<double>(L.nF);
+  Pool& Pw = L.dff_block ? tmp : P;   // the point-block W_p replaces this one
   L.W = Afc;
-  L.W.rp = P.get<int64_t>(L.nF + 1);
-  L.W.ci = P.get<int32_t>(Afc.nnz);
-  L.W.v = P.get<double>(Afc.nnz);
+  L.W.rp = Pw.get<int64_t>(L.nF + 1);
+  L.W.ci = Pw.get<int32_t>(Afc.nnz);
+  L.W.v = Pw.get<double>(Afc.nnz);
   Csr T = Afc;
   T.v = tmp.get<double>(Afc.nnz);
   if (P.err || tmp.err) return P.err ? P.err : tmp.err;
   MGR_TRY_CUDA(cudaMemcpyAsync(L.W.rp, Afc.rp, sizeof(int64_t) * (L.nF + 1), cudaMemcpyDeviceToDevice, s));
   MGR_TRY_CUDA(cudaMemcpyAsync(L.W.ci, Afc.ci, sizeof(int32_t) * Afc.nnz, cudaMemcpyDeviceToDevice, s));
   MGR_LAUNCH k_dff_and_w<<<nblocks(L.nF, 256), 256, 0, s>>>(L.A.rp, L.A.ci, L.A.v, L.Fidx, L.nF, Afc.rp, Afc.v,
-                                                  T.v, L.W.v, L.dFinv, h->derr);
+                                                  T.v, L.W.v, L.dFinv, dval, h->derr);
   MGR_TRY(check_dev_err(h->derr, s));
+  if (L.dff_block) {
+    // point-block D_FF: runs of F dofs sharing dof_node (at most 4), their
+    // inverses (Gauss-Jordan, as the global smoother's blocks) as a sparse
+    // matrix Bd; T = Bd A_FC, W_p = -T
+    int32_t* nodeF = tmp.get<int32_t>(L.nF);
+    int32_t* dumA = tmp.get<int32_t>(L.nF);
+    int32_t* dumB = tmp.get<int32_t>(L.nF);
+    int64_t* head = tmp.get<int64_t>(L.nF + 1);
+    int64_t* hpos = tmp.get<int64_t>(L.nF + 1);
+    if (tmp.err) return tmp.err;
+    MGR_LAUNCH k_gather3<<<nblocks(L.nF, 256), 256, 0, s>>>(node, node, node, L.Fidx, L.nF, nodeF, dumA, dumB);
+    MGR_LAUNCH k_block_heads<<<nblocks(L.nF, 256), 256, 0, s>>>(nodeF, L.nF, head);
+    int64_t nb = 0;
+    MGR_TRY(rowptr_from_counts(head, hpos, L.nF, &nb, s, tmp));
+    int64_t* bst = tmp.get<int64_t>(nb + 1);
+    double* binv = tmp.get<double>(16 * nb);
+    int64_t* cnt = tmp.get<int64_t>(L.nF + 1);
+    if (tmp.err) return tmp.err;
+    MGR_LAUNCH k_block_starts<<<nblocks(L.nF + 1, 256), 256, 0, s>>>(hpos, L.nF, bst, nb);
+    MGR_LAUNCH k_block_inv<<<nblocks(nb, 128), 128, 0, s>>>(Aff.rp, Aff.ci, Aff.v, bst, nb, binv, h->derr);
+    MGR_TRY(check_dev_err(h->derr, s));
+    MGR_LAUNCH k_bd_counts<<<nblocks(nb, 256), 256, 0, s>>>(bst, nb, cnt);
+    L.Bd.nr = L.Bd.nc = L.nF;
+    L.Bd.rp = P.get<int64_t>(L.nF + 1);
+    if (P.err) return P.err;
+    MGR_TRY(rowptr_from_counts(cnt, L.Bd.rp, L.nF, &L.Bd.nnz, s, tmp));
+    L.Bd.ci = P.get<int32_t>(L.Bd.nnz);
+    L.Bd.v = P.get<double>(L.Bd.nnz);
+    if (P.err) return P.err;
+    MGR_LAUNCH k_bd_fill<<<nblocks(nb, 256), 256, 0, s>>>(bst, nb, binv, L.Bd.rp, L.Bd.ci, L.Bd.v);
+    Csr Tb;
+    MGR_TRY(spgemm(tmp, tmp, L.Bd, Afc, Tb, s));
+    T = Tb;
+    L.W = Tb;
+    L.W.rp = P.get<int64_t>(L.nF + 1);
+    L.W.ci = P.get<int32_t>(Tb.nnz);
+    L.W.v = P.get<double>(Tb.nnz);
+    if (P.err) return P.err;
+    MGR_TRY_CUDA(cudaMemcpyAsync(L.W.rp, Tb.rp, sizeof(int64_t) * (L.nF + 1), cudaMemcpyDeviceToDevice, s));
+    MGR_TRY_CUDA(cudaMemcpyAsync(L.W.ci, Tb.ci, sizeof(int32_t) * Tb.nnz, cudaMemcpyDeviceToDevice, s));
+    MGR_LAUNCH k_neg<<<grid_for(Tb.nnz, 256, 152 * 16), 256, 0, s>>>(Tb.v, L.W.v, Tb.nnz);
+  }
   g_trace.mark("mgr split/extract/W", l);
   // A_cor = A_CF T
-  MGR_TRY(spgemm(P, tmp, L.Acf, T, L.cor, s));
+  if (!L.restrict_jacobi) {
+    MGR_TRY(spgemm(P, tmp, L.Acf, T, L.cor, s));
+  } else {
+    // Jacobi restriction: U = A_CF D_FF^-1, W_r = -U; R~ A P~ = A_CC - A_cor
+    // with A_cor = 2 A_CF T - U (A_FF T), formed on the union pattern
+    Csr C1, U, K, E;
+    MGR_TRY(spgemm(tmp, tmp, L.Acf, T, C1, s));
+    if (L.dff_block) {
+      MGR_TRY(spgemm(tmp, tmp, L.Acf, L.Bd, U, s));
+      L.Wr = U;
+      L.Wr.rp = P.get<int64_t>(L.nC + 1);
+      L.Wr.ci = P.get<int32_t>(U.nnz);
+      L.Wr.v = P.get<double>(U.nnz);
+      if (P.err) return P.err;
+      MGR_TRY_CUDA(cudaMemcpyAsync(L.Wr.rp, U.rp, sizeof(int64_t) * (L.nC + 1), cudaMemcpyDeviceToDevice, s));
+      MGR_TRY_CUDA(cudaMemcpyAsync(L.Wr.ci, U.ci, sizeof(int32_t) * U.nnz, cudaMemcpyDeviceToDevice, s));
+      MGR_LAUNCH k_neg<<<grid_for(U.nnz, 256, 152 * 16), 256, 0, s>>>(U.v, L.Wr.v, U.nnz);
+    } else {
+      U = L.Acf;
+      U.v = tmp.get<double>(L.Acf.nnz);
+      L.Wr = L.Acf;
+      L.Wr.v = P.get<double>(L.Acf.nnz);   // shares A_CF's row pointers and columns
+      if (P.err || tmp.err) return P.err ? P.err : tmp.err;
+      MGR_LAUNCH k_acf_dinv<<<nblocks(L.Acf.nnz, 256), 256, 0, s>>>(L.Acf.ci, L.Acf.v, L.Acf.nnz, dval, U.v, L.Wr.v);
+    }
+    MGR_TRY(spgemm(tmp, tmp, Aff, T, K, s));
+    MGR_TRY(spgemm(tmp, tmp, U, K, E, s));
+    MGR_LAUNCH k_twice<<<grid_for(C1.nnz, 256, 152 * 16), 256, 0, s>>>(C1.v, C1.nnz);
+    int64_t* ucnt = tmp.get<int64_t>(L.nC + 1);
+    L.cor.nr = L.cor.nc = L.nC;
+    L.cor.rp = P.get<int64_t>(L.nC + 1);
+    if (P.err || tmp.err) return P.err ? P.err : tmp.err;
+    MGR_LAUNCH k_union_sub<false><<<nblocks(L.nC, 256), 256, 0, s>>>(C1.rp, C1.ci, C1.v, E.rp, E.ci, E.v,
+                                                                   L.nC, ucnt, nullptr, nullptr);
+    MGR_TRY(rowptr_from_counts(ucnt, L.cor.rp, L.nC, &L.cor.nnz, s, tmp));
+    L.cor.ci = P.get<int32_t>(L.cor.nnz);
+    L.cor.v = P.get<double>(L.cor.nnz);
+    if (P.err) return P.err;
+    MGR_LAUNCH k_union_sub<true><<<nblocks(L.nC, 256), 256, 0, s>>>(C1.rp, C1.ci, C1.v, E.rp, E.ci, E.v,
+                                                                  L.nC, L.cor.rp, L.cor.ci, L.cor.v);
+  }
   g_trace.mark("mgr A_CF*T", l);
   // next-level labels (needed for G's own-point rule)
   *nlabel = P.get<int32_t>(L.nC);
@@ -2028,6 +2160,8 @@ int to_fp32(Handle* h, cudaStream_t s) {
     MGR_TRY(f32(P, L.Acf.v, &L.Acf.vf, L.Acf.nnz, s));
     MGR_TRY(f32(P, L.dFinv, &L.dFinvf, L.nF, s));
     MGR_TRY(f32(P, L.binv, &L.binvf, 16 * L.nblk, s));
+    if (L.Wr.v) MGR_TRY(f32(P, L.Wr.v, &L.Wr.vf, L.Wr.nnz, s));
+    if (L.Bd.v) MGR_TRY(f32(P, L.Bd.v, &L.Bd.vf, L.Bd.nnz, s));
     MGR_TRY(amg_to_fp32(h, L.famg, s));
   }
   MGR_TRY(amg_to_fp32(h, h->camg, s));
