@@ -50,6 +50,7 @@ class OrcOpts(C.Structure):
         ("restrict_jacobi", C.c_int32 * MAXL),
         ("frelax_post", C.c_int32 * MAXL),
         ("dff_block", C.c_int32 * MAXL),
+        ("global_smoother", C.c_int32 * MAXL),
     ]
 
 
@@ -87,6 +88,9 @@ def lib():
             L.orc_get_cf.argtypes = [P, C.c_int, C.c_int, P]
             L.orc_get_l1.restype = C.c_int64
             L.orc_get_l1.argtypes = [P, C.c_int, C.c_int, P]
+            L.orc_global_relax.argtypes = [P, C.c_int, P, P]
+            L.orc_get_block_colors.restype = C.c_int64
+            L.orc_get_block_colors.argtypes = [P, C.c_int, P, P]
             L.orc_splitmix64.restype = C.c_uint64
             L.orc_splitmix64.argtypes = [C.c_uint64]
             _lib = L
@@ -102,7 +106,8 @@ def default_options(two_phase=True, **kw):
     single-phase: level 0 F = {u}, coarsest = {p}.
     Operator variants of Sec. 5.1, per level, all off by default:
     restrict_jacobi (W_r = -A_CF D_FF^-1), frelax_post (Eq. MGR-post),
-    dff_block (D_FF = point-block diagonal of A_FF).
+    dff_block (D_FF = point-block diagonal of A_FF); global_smoother 1 =
+    multicolour point-block Gauss-Seidel instead of point-block Jacobi.
     """
     d = dict(num_levels=2 if two_phase else 1,
              f_label_mask=[1 << 0, 1 << 1] if two_phase else [1 << 0],
@@ -111,7 +116,8 @@ def default_options(two_phase=True, **kw):
              nmax_drop=[4, -1] if two_phase else [4],
              global_sweeps=[0, 3] if two_phase else [0],
              amg_theta=0.25, amg_pmax=4, amg_max_coarse=64, amg_max_levels=25, seed=0,
-             restrict_jacobi=[0] * MAXL, frelax_post=[0] * MAXL, dff_block=[0] * MAXL)
+             restrict_jacobi=[0] * MAXL, frelax_post=[0] * MAXL, dff_block=[0] * MAXL,
+             global_smoother=[0] * MAXL)
     d.update(kw)
     return d
 
@@ -120,7 +126,7 @@ def _opts_struct(d):
     o = OrcOpts()
     o.num_levels = d["num_levels"]
     for name in ("f_label_mask", "frelax", "frelax_sweeps", "nmax_drop", "global_sweeps",
-                 "restrict_jacobi", "frelax_post", "dff_block"):
+                 "restrict_jacobi", "frelax_post", "dff_block", "global_smoother"):
         arr = getattr(o, name)
         for i, v in enumerate(d[name]):
             arr[i] = v
@@ -227,6 +233,24 @@ class Oracle:
         out = np.zeros(n, dtype=np.int8)
         lib().orc_get_cf(self.h, slot, lvl, _p(out))
         return out
+
+    def global_relax(self, l, v):
+        """z = M_glo^-1 v of MGR level l alone."""
+        v = np.ascontiguousarray(v, dtype=np.float64)
+        z = np.zeros_like(v)
+        if lib().orc_global_relax(self.h, l, _p(v), _p(z)) != 0:
+            raise ValueError("no such level")
+        return z
+
+    def block_colors(self, l):
+        """(colours of level l's point blocks, colour count), or None."""
+        nc = C.c_int32(0)
+        n = lib().orc_get_block_colors(self.h, l, None, C.byref(nc))
+        if n < 0:
+            return None
+        out = np.zeros(n, dtype=np.int32)
+        lib().orc_get_block_colors(self.h, l, _p(out), C.byref(nc))
+        return out, nc.value
 
     def l1(self, slot, lvl):
         n = lib().orc_get_l1(self.h, slot, lvl, None)

@@ -19,6 +19,8 @@
  *   - options of Sec. 5.1: Jacobi restriction W_r = -A_CF D_FF^-1 (full
  *     triple product R~ A P~), F-relaxation after the coarse-grid correction
  *     (Eq. "MGR-post"), and D_FF as the point-block diagonal of A_FF,
+ *   - global smoother: point-block Jacobi, or multicolour point-block
+ *     Gauss-Seidel (the parallel reading of hybrid block Gauss-Seidel),
  *   - the inner AMG (Sec. 6 solver settings: unknown approach for A_uu, scalar
  *     AMG for the pressure Schur complement, coarsest level by Gaussian
  *     elimination), and
@@ -76,6 +78,8 @@ typedef struct {
                                     correction (Eq. MGR-post), else before */
   int32_t dff_block[MAXL];       /* 1: D_FF = point-block diagonal of A_FF
                                     (blocks of F dofs sharing dof_node) */
+  int32_t global_smoother[MAXL]; /* 0: point-block Jacobi sweeps; 1: multicolour
+                                    point-block Gauss-Seidel sweeps */
 } orc_opts;
 
 typedef struct {
@@ -113,6 +117,8 @@ typedef struct {
   int64_t *bstart;
   int32_t *bsize;
   double *binv;           /* 16 doubles per block (row-major, size b) */
+  int32_t *bcolor;        /* multicolour Gauss-Seidel: colour of each block */
+  int32_t ncolor;
 } mgr_level;
 
 typedef struct {
@@ -595,9 +601,60 @@ static void mgr_level_free(mgr_level *l) {
   csr_free(&l->Wr); csr_free(&l->Bd);
   csr_free(&l->cor); csr_free(&l->corkept);
   free(l->label); free(l->node); free(l->comp); free(l->Fidx); free(l->Cidx); free(l->pos);
-  free(l->dF); free(l->bstart); free(l->bsize); free(l->binv);
+  free(l->dF); free(l->bstart); free(l->bsize); free(l->binv); free(l->bcolor);
   amg_free(l->famg);
   memset(l, 0, sizeof(*l));
+}
+
+/* Colouring of the point-block graph for the multicolour block Gauss-Seidel
+ * global smoother (the GPU reading of the paper's hybrid block Gauss-Seidel,
+ * Sec. 5.3 Remarks / Sec. 6): blocks k and m are adjacent when a row of
+ * either has a column in the other (the pattern of A + A^T: S_l is not
+ * structurally symmetric after dropping, and two blocks of one colour must not
+ * read each other's unknowns).  Jones-Plassmann rounds: block k has the weight
+ * w_k = splitmix64(seed ^ 0xC0 << 56 ^ l << 40 ^ k); in round c every block
+ * still uncoloured at the start of the round whose (w_k, -k) exceeds that of
+ * each neighbour uncoloured at the start of the round takes colour c. */
+static void block_coloring(const ocsr *a, const int64_t *bstart, const int32_t *bsize, int64_t nb,
+                           uint64_t seed, int l, int32_t *color, int32_t *ncolor) {
+  int64_t n = a->nr;
+  ocsr at;
+  csr_transpose(a, &at);
+  int64_t *blk = xcalloc((size_t)n + 1, sizeof(int64_t));
+  for (int64_t k = 0; k < nb; k++)
+    for (int r = 0; r < bsize[k]; r++) blk[bstart[k] + r] = k;
+  uint64_t *w = xcalloc((size_t)nb + 1, sizeof(uint64_t));
+  for (int64_t k = 0; k < nb; k++)
+    w[k] = orc_splitmix64(seed ^ (0xC0ULL << 56) ^ ((uint64_t)l << 40) ^ (uint64_t)k);
+  for (int64_t k = 0; k < nb; k++) color[k] = -1;
+  int8_t *win = xcalloc((size_t)nb + 1, 1);
+  int64_t left = nb;
+  int32_t c = 0;
+  while (left > 0) {
+    for (int64_t k = 0; k < nb; k++) {
+      win[k] = 0;
+      if (color[k] != -1) continue;
+      int ok = 1;
+      for (int pass = 0; pass < 2 && ok; pass++) {
+        const ocsr *g = pass ? &at : a;
+        for (int r = 0; r < bsize[k] && ok; r++) {
+          int64_t i = bstart[k] + r;
+          for (int64_t q = g->rp[i]; q < g->rp[i + 1]; q++) {
+            int64_t m = blk[g->ci[q]];
+            if (m == k || color[m] != -1) continue;
+            if (w[m] > w[k] || (w[m] == w[k] && m < k)) { ok = 0; break; }
+          }
+        }
+      }
+      win[k] = (int8_t)ok;
+    }
+    for (int64_t k = 0; k < nb; k++)
+      if (win[k]) { color[k] = c; left--; }
+    c++;
+  }
+  *ncolor = c;
+  free(blk); free(w); free(win);
+  csr_free(&at);
 }
 
 /* One reduction level: C/F split from the labels; D_FF = diag(A_FF);
@@ -796,6 +853,10 @@ static int mgr_level_setup(oracle_t *h, int l, ocsr *Snext) {
           blk[r * b + c] = csr_get(&L->A, L->bstart[bk] + r, L->bstart[bk] + c);
       st = small_inverse(blk, &L->binv[bk * 16], b);
     }
+    if (st == ORC_OK && o->global_smoother[l]) {
+      L->bcolor = xcalloc((size_t)nb + 1, sizeof(int32_t));
+      block_coloring(&L->A, L->bstart, L->bsize, nb, o->seed, l, L->bcolor, &L->ncolor);
+    }
   }
   csr_free(&Aff); csr_free(&Acc);
   free(fpos); free(cpos);
@@ -805,6 +866,54 @@ static int mgr_level_setup(oracle_t *h, int l, ocsr *Snext) {
 /* -------------------------------------------------------------------------- */
 /* MGR apply: Algorithm 2 (multilevel, pre-smoothing F-relaxation)            */
 /* -------------------------------------------------------------------------- */
+/* Global relaxation z = M_glo^-1 v of level l: sweeps from zero of
+ * multicolour point-block Gauss-Seidel (colours in ascending order, each block
+ * updated from the latest z) or of point-block Jacobi; r is scratch (n). */
+static void global_relax(const mgr_level *L, const orc_opts *o, int l, const double *v, double *z,
+                         double *r) {
+  int64_t n = L->A.nr;
+  for (int64_t i = 0; i < n; i++) z[i] = 0.0;
+  /* global relaxation: z = M_glo^-1 v, sweeps from zero of multicolour block
+   * Gauss-Seidel (colours in ascending order, each block updated from the
+   * latest z) or of block Jacobi */
+  if (o->global_smoother[l]) {
+    for (int sw = 0; sw < o->global_sweeps[l]; sw++)
+      for (int32_t c = 0; c < L->ncolor; c++)
+        for (int64_t bk = 0; bk < L->nblk; bk++) {
+          if (L->bcolor[bk] != c) continue;
+          int b = L->bsize[bk];
+          int64_t s0 = L->bstart[bk];
+          double rb[4], d[4];
+          for (int i = 0; i < b; i++) {
+            double acc = v[s0 + i];
+            for (int64_t q = L->A.rp[s0 + i]; q < L->A.rp[s0 + i + 1]; q++)
+              acc -= L->A.v[q] * z[L->A.ci[q]];
+            rb[i] = acc;
+          }
+          for (int i = 0; i < b; i++) {
+            double acc = 0.0;
+            for (int j = 0; j < b; j++) acc += L->binv[bk * 16 + i * b + j] * rb[j];
+            d[i] = acc;
+          }
+          for (int i = 0; i < b; i++) z[s0 + i] += d[i];
+        }
+  }
+  for (int sw = 0; sw < (o->global_smoother[l] ? 0 : o->global_sweeps[l]); sw++) {
+    residual(&L->A, v, z, r);
+    for (int64_t bk = 0; bk < L->nblk; bk++) {
+      int b = L->bsize[bk];
+      int64_t s0 = L->bstart[bk];
+      double d[4];
+      for (int i = 0; i < b; i++) {
+        double acc = 0.0;
+        for (int j = 0; j < b; j++) acc += L->binv[bk * 16 + i * b + j] * r[s0 + j];
+        d[i] = acc;
+      }
+      for (int i = 0; i < b; i++) z[s0 + i] += d[i];
+    }
+  }
+}
+
 /* F-relaxation sweeps: z <- z + Q M_FF^-1 Q^T (v - A z), M_FF^-1 one AMG
  * V-cycle or Jacobi with D_FF (pointwise, or the point-block inverse Bd). */
 static void mgr_frelax(const oracle_t *h, int l, const double *v, double *z, double *r,
@@ -835,22 +944,7 @@ static void mgr_apply_level(const oracle_t *h, int l, const double *v, double *z
   double *ef = xcalloc((size_t)nF, sizeof(double));
   double *rc = xcalloc((size_t)nC, sizeof(double));
   double *ec = xcalloc((size_t)nC, sizeof(double));
-  for (int64_t i = 0; i < n; i++) z[i] = 0.0;
-  /* global relaxation: z = M_glo^-1 v (block Jacobi sweeps from zero) */
-  for (int sw = 0; sw < o->global_sweeps[l]; sw++) {
-    residual(&L->A, v, z, r);
-    for (int64_t bk = 0; bk < L->nblk; bk++) {
-      int b = L->bsize[bk];
-      int64_t s0 = L->bstart[bk];
-      double d[4];
-      for (int i = 0; i < b; i++) {
-        double acc = 0.0;
-        for (int j = 0; j < b; j++) acc += L->binv[bk * 16 + i * b + j] * r[s0 + j];
-        d[i] = acc;
-      }
-      for (int i = 0; i < b; i++) z[s0 + i] += d[i];
-    }
-  }
+  global_relax(L, o, l, v, z, r);
   /* F-relaxation before the coarse-grid correction (Eq. MGR-pre) */
   if (!o->frelax_post[l]) mgr_frelax(h, l, v, z, r, rf, ef);
   /* restrict: r_C = R~ (v - A z), R~ = [W_r I]: injection (W_r = 0) or
@@ -1110,6 +1204,27 @@ int64_t orc_get_cf(void *hv, int slot, int lvl, int8_t *out) {
   int64_t n = g->lev[lvl].A.nr;
   if (out) memcpy(out, g->lev[lvl].cf, (size_t)n);
   return n;
+}
+
+/* The global relaxation of MGR level l alone (z = M_glo^-1 v; z = 0 if the
+ * level has none), for the smoother's pins. */
+int orc_global_relax(void *hv, int l, const double *v, double *z) {
+  oracle_t *h = hv;
+  if (l < 0 || l >= h->L) return ORC_ERR_ARG;
+  double *r = xcalloc((size_t)h->lev[l].A.nr + 1, sizeof(double));
+  global_relax(&h->lev[l], &h->o, l, v, z, r);
+  free(r);
+  return ORC_OK;
+}
+
+/* Multicolour Gauss-Seidel colours of MGR level l's point blocks (returns
+ * the block count, -1 if the level has none); *ncolor receives the count. */
+int64_t orc_get_block_colors(void *hv, int l, int32_t *out, int32_t *ncolor) {
+  oracle_t *h = hv;
+  if (l < 0 || l >= h->L || !h->lev[l].bcolor) return -1;
+  if (out) memcpy(out, h->lev[l].bcolor, sizeof(int32_t) * (size_t)h->lev[l].nblk);
+  if (ncolor) *ncolor = h->lev[l].ncolor;
+  return h->lev[l].nblk;
 }
 
 /* Dense l1 diagonal of AMG slot s, level k. */

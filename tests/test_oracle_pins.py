@@ -461,3 +461,74 @@ def test_mgr_pre_and_post_error_propagation(post, jac):
     # the two orderings are different operators
     E_other = Ecg @ Ef if post else Ef @ Ecg
     assert np.abs(E - E_other).max() > 1e-6
+
+
+# ---------------------------------------------------------------------------
+# Global smoother: point-block Jacobi and multicolour point-block Gauss-Seidel
+# ---------------------------------------------------------------------------
+def _level1_blocks(o, p):
+    """Level-1 operator S_1 (dense) and its point blocks (runs of equal node)."""
+    S = o.scipy(oracle.Q_MGR_A, 1).toarray()
+    node = p.dof_node[p.dof_label != 0]           # level-1 dofs: s and p of each cell
+    blocks, i = [], 0
+    while i < len(node):
+        j = i + 1
+        while j < len(node) and node[j] == node[i]:
+            j += 1
+        blocks.append(np.arange(i, j))
+        i = j
+    return S, blocks
+
+
+def test_multicolour_coloring_is_proper():
+    p = synth.two_phase(6, 5, 4, seed=8)
+    o = oracle.Oracle(p, global_smoother=[0, 1])
+    S, blocks = _level1_blocks(o, p)
+    colors, nc = o.block_colors(1)
+    assert len(colors) == len(blocks) and colors.min() == 0 and colors.max() == nc - 1
+    owner = np.empty(S.shape[0], dtype=np.int64)
+    for k, b in enumerate(blocks):
+        owner[b] = k
+    rows, cols = np.nonzero(S)
+    adj = owner[rows] != owner[cols]
+    assert np.all(colors[owner[rows[adj]]] != colors[owner[cols[adj]]])
+    assert 3 <= nc <= 40
+
+
+@pytest.mark.parametrize("sweeps", [1, 3])
+def test_multicolour_gauss_seidel_is_block_gauss_seidel(sweeps):
+    # Forward block Gauss-Seidel in the ordering (colour, block): with the
+    # block lower triangle L_D (block diagonal included) of that ordering,
+    # z_{k+1} = z_k + L_D^-1 (v - S z_k) from z_0 = 0 -- the textbook sweep.
+    p = synth.two_phase(4, 4, 3, seed=9)
+    o = oracle.Oracle(p, global_smoother=[0, 1], global_sweeps=[0, sweeps])
+    S, blocks = _level1_blocks(o, p)
+    colors, _ = o.block_colors(1)
+    order = sorted(range(len(blocks)), key=lambda k: (colors[k], k))
+    rank = np.empty(len(blocks), dtype=np.int64)
+    rank[order] = np.arange(len(blocks))
+    owner = np.empty(S.shape[0], dtype=np.int64)
+    for k, b in enumerate(blocks):
+        owner[b] = k
+    LD = np.where(rank[owner][:, None] >= rank[owner][None, :], S, 0.0)
+    v = np.random.default_rng(3).standard_normal(S.shape[0])
+    z = np.zeros_like(v)
+    for _ in range(sweeps):
+        z = z + np.linalg.solve(LD, v - S @ z)
+    got = o.global_relax(1, v)
+    assert np.abs(got - z).max() <= 1e-11 * np.abs(z).max()
+
+
+def test_block_jacobi_smoother_is_block_jacobi():
+    p = synth.two_phase(4, 4, 3, seed=9)
+    o = oracle.Oracle(p, global_sweeps=[0, 3])
+    S, blocks = _level1_blocks(o, p)
+    D = np.zeros_like(S)
+    for b in blocks:
+        D[np.ix_(b, b)] = S[np.ix_(b, b)]
+    v = np.random.default_rng(4).standard_normal(S.shape[0])
+    z = np.zeros_like(v)
+    for _ in range(3):
+        z = z + np.linalg.solve(D, v - S @ z)
+    got = o.global_relax(1, v)
+    assert np.abs(got - z).max() <= 1e-11 * np.abs(z).max()
