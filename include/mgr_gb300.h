@@ -119,6 +119,14 @@ typedef struct {
   int32_t restrict_jacobi[MGR_MAX_LEVELS];
   int32_t frelax_post[MGR_MAX_LEVELS];
   int32_t dff_block[MGR_MAX_LEVELS];
+  /* Global smoother per level (global_sweeps of it): 0 point-block Jacobi;
+   * 1 multicolour point-block Gauss-Seidel, the parallel reading of the
+   * paper's hybrid block Gauss-Seidel (Sec. 5.3 Remarks, Sec. 6): blocks
+   * coloured by Jones-Plassmann rounds on the block graph of A + A^T
+   * (weights splitmix64(seed ^ 0xC0 << 56 ^ level << 40 ^ block), ties to
+   * the smaller block), each sweep visiting the colours in ascending order
+   * and updating every block of a colour from the latest z. */
+  int32_t global_smoother[MGR_MAX_LEVELS];
 } mgr_options_t;
 
 typedef struct {
@@ -282,6 +290,13 @@ int mgr_batch_handle(mgr_batch_t bh, int i, mgr_handle_t* out);
 
 /* Wait for the batch's streams, free every system and the streams. */
 int mgr_destroy_batched(mgr_batch_t bh);
+
+/* Colours of MGR level `level`'s point blocks under the multicolour
+ * Gauss-Seidel global smoother, copied to the HOST array out (NULL: size
+ * query); *ncolor (may be NULL) receives the colour count.  Returns the number
+ * of blocks, MGR_ERR_INVALID_ARG if the level has no such smoother.
+ * Synchronises the device. */
+int64_t mgr_get_block_colors(mgr_handle_t h, int level, int32_t* out, int32_t* ncolor);
 
 /* Number of CUDA kernel launches this library has issued in this process
  * (all handles, all threads).  Lets a caller count the kernels of a region. */

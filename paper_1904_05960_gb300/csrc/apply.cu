@@ -277,6 +277,41 @@ k_block_jacobi(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
   }
 }
 
+// Multicolour point-block Gauss-Seidel: one colour's blocks (list[0..count)),
+// z_b += B_b^-1 (v - A z)_b in place.  A warp per block, 8 lanes per row (at
+// most 4 rows); blocks of one colour are not adjacent in A + A^T, so a warp
+// reads no unknown that another warp of the launch writes.
+template <class T>
+__global__ void __launch_bounds__(256)
+k_block_gs(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci, const T* __restrict__ val,
+           const int64_t* __restrict__ bstart, const T* __restrict__ binv,
+           const int64_t* __restrict__ list, int64_t count, const T* __restrict__ v, T* z) {
+  const int lane = threadIdx.x & 31, g = lane >> 3, sub = lane & 7;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < count; t += nw) {
+    const int64_t k = list[t];
+    const int64_t s0 = bstart[k];
+    const int b = (int)(bstart[k + 1] - s0);
+    T acc = 0;
+    if (g < b) {
+      const int64_t i = s0 + g;
+      for (int64_t q = rp[i] + sub; q < rp[i + 1]; q += 8) acc += val[q] * z[ci[q]];
+    }
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
+    const T r = (g < b) ? v[s0 + g] - acc : (T)0;
+    T rr[4];
+#pragma unroll
+    for (int j = 0; j < 4; j++) rr[j] = __shfl_sync(FULL, r, j * 8);
+    if (lane < b) {
+      const T* M = binv + 16 * k;
+      T d = 0;
+      for (int j = 0; j < b; j++) d += M[lane * 4 + j] * rr[j];
+      z[s0 + lane] += d;
+    }
+  }
+}
+
 // Interpolation and correction of Algorithm 2: z_F += W_p e_C, z_C += e_C.
 // With base != null the F part of z is zero except base (= e_F of the
 // F-relaxation) and C is zero, so z is written instead: z_F = base + W_p e_C,
@@ -425,7 +460,8 @@ static void mgr_level(Handle* h, int l, const T* v, T* z, cudaStream_t s) {
   const int64_t* Fi = L.F_is_prefix ? nullptr : L.Fidx;
   const int64_t* Ci = L.F_is_prefix ? nullptr : L.Cidx;
   bool zero = true;             // z == 0 (not materialised)
-  // global relaxation z = M_glo^-1 v (point-block Jacobi sweeps from zero)
+  // global relaxation z = M_glo^-1 v: sweeps from zero of point-block Jacobi
+  // or of multicolour point-block Gauss-Seidel
   if (L.global_sweeps > 0 && L.nblk > 0) {
     const T* binv = pick<T>(L.binv, L.binvf);
     T* buf[2] = {((L.global_sweeps - 1) % 2 == 0) ? z : (T*)L.z2,
@@ -433,7 +469,19 @@ static void mgr_level(Handle* h, int l, const T* v, T* z, cudaStream_t s) {
     const unsigned bgrid = (unsigned)((L.nblk + BJ_BLOCKS - 1) / BJ_BLOCKS);
     const int G = pick_group(L.A.nnz, L.A.nr);
     bool first = true;
-    for (int sw = 0; sw < L.global_sweeps; sw++, first = false) {
+    if (L.gs) {
+      // multicolour Gauss-Seidel sweeps from zero, in place on z
+      cudaMemsetAsync(z, 0, sizeof(T) * n, s);
+      for (int sw = 0; sw < L.global_sweeps; sw++)
+        for (int c = 0; c < L.ncolor; c++) {
+          const int64_t cnt = L.coff[c + 1] - L.coff[c];
+          if (cnt == 0) continue;
+          const unsigned gg = (unsigned)std::min<int64_t>((cnt + 7) / 8, 152LL * 16);
+          MGR_LAUNCH k_block_gs<T><<<gg, 256, 0, s>>>(L.A.rp, L.A.ci, Av, L.bstart, binv,
+                                                      L.border + L.coff[c], cnt, v, z);
+        }
+    }
+    for (int sw = 0; sw < (L.gs ? 0 : L.global_sweeps); sw++, first = false) {
       const T* zi = first ? nullptr : buf[(sw - 1) % 2];
       T* zo = buf[sw % 2];
 #define MGR_BJ_CASE(g)                                                                           \

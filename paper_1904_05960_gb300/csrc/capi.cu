@@ -275,4 +275,17 @@ int mgr_splitmix64_device(const uint64_t* in, uint64_t* out, int64_t n, void* st
 
 int64_t mgr_launch_count(void) { return (int64_t)g_launches.load(); }
 
+int64_t mgr_get_block_colors(mgr_handle_t hh, int level, int32_t* out, int32_t* ncolor) {
+  (void)cudaGetLastError();  // errors of earlier calls are not this call's
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (!h || level < 0 || level >= h->L || !h->lev[level].gs) return MGR_ERR_INVALID_ARG;
+  const MgrLevel& L = h->lev[level];
+  if (ncolor) *ncolor = L.ncolor;
+  if (out) {
+    MGR_TRY_CUDA(cudaDeviceSynchronize());
+    MGR_TRY_CUDA(cudaMemcpy(out, L.bcolor, sizeof(int32_t) * L.nblk, cudaMemcpyDeviceToHost));
+  }
+  return L.nblk;
+}
+
 }  // extern "C"

@@ -135,6 +135,12 @@ struct MgrLevel {
   int frelax = MGR_FRELAX_AMG_VCYCLE, frelax_sweeps = 1, global_sweeps = 0;
   int64_t nblk = 0;
   int64_t* bstart = nullptr;     // block starts (nblk + 1 entries)
+  // multicolour point-block Gauss-Seidel global smoother
+  bool gs = false;
+  int32_t* bcolor = nullptr;     // colour of each block
+  int ncolor = 0;
+  int64_t* border = nullptr;     // blocks grouped by colour
+  std::vector<int64_t> coff;     // colour c's blocks: border[coff[c] .. coff[c+1])
   double* binv = nullptr;        // 16 values per block, row-major b x b
   float* binvf = nullptr;
   // apply workspace (precision of the handle), sized n / nF / nC

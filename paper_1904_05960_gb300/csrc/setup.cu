@@ -645,6 +645,64 @@ __global__ void k_twice(double* __restrict__ a, int64_t n) {
     a[i] = 2.0 * a[i];   // exact
 }
 
+// ---- multicolour point-block Gauss-Seidel: colouring of the block graph ----
+// Blocks k, m adjacent when a row of either has a column in the other (A and
+// A^T).  Jones-Plassmann rounds with w_k = splitmix64(seed ^ 0xC0 << 56 ^
+// l << 40 ^ k): in round c a block uncoloured at the start of the round takes
+// colour c when its (w_k, -k) beats every neighbour uncoloured at the start of
+// the round (colour -1, or c: coloured during this same round).
+__global__ void k_blk_of(const int64_t* __restrict__ bstart, int64_t nblk, int64_t* __restrict__ blk) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nblk) return;
+  for (int64_t i = bstart[k]; i < bstart[k + 1]; i++) blk[i] = k;
+}
+__global__ void k_color_init(int64_t nblk, uint64_t seed, int l, uint64_t* __restrict__ w,
+                             int32_t* __restrict__ color) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nblk) return;
+  w[k] = splitmix64(seed ^ (0xC0ull << 56) ^ ((uint64_t)l << 40) ^ (uint64_t)k);
+  color[k] = -1;
+}
+__global__ void k_color_round(const int64_t* __restrict__ arp, const int32_t* __restrict__ aci,
+                              const int64_t* __restrict__ trp, const int32_t* __restrict__ tci,
+                              const int64_t* __restrict__ blk, const int64_t* __restrict__ bstart,
+                              int64_t nblk, const uint64_t* __restrict__ w, int32_t* color, int c,
+                              unsigned long long* __restrict__ left) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nblk || color[k] != -1) return;
+  const uint64_t wk = w[k];
+  bool win = true;
+  for (int pass = 0; pass < 2 && win; pass++) {
+    const int64_t* rp = pass ? trp : arp;
+    const int32_t* ci = pass ? tci : aci;
+    for (int64_t i = bstart[k]; i < bstart[k + 1] && win; i++)
+      for (int64_t q = rp[i]; q < rp[i + 1]; q++) {
+        const int64_t m = blk[ci[q]];
+        if (m == k) continue;
+        const int32_t cm = ((volatile int32_t*)color)[m];
+        if (cm != -1 && cm != c) continue;
+        const uint64_t wm = w[m];
+        if (wm > wk || (wm == wk && m < k)) {
+          win = false;
+          break;
+        }
+      }
+  }
+  if (win) color[k] = c;
+  else atomicAdd(left, 1ull);
+}
+__global__ void k_color_count(const int32_t* __restrict__ color, int64_t nblk, int64_t* __restrict__ cnt) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < nblk) atomicAdd((unsigned long long*)&cnt[color[k]], 1ull);
+}
+// blocks grouped by colour (order inside a colour is free: its blocks are
+// independent)
+__global__ void k_color_place(const int32_t* __restrict__ color, int64_t nblk, int64_t* cursor,
+                              int64_t* __restrict__ order) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < nblk) order[atomicAdd((unsigned long long*)&cursor[color[k]], 1ull)] = k;
+}
+
 // G: keep the own-point columns plus the nmax others of largest |value|
 // (ties: smaller column); nmax < 0 keeps everything.
 __global__ void k_drop_mark(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
@@ -2053,6 +2111,52 @@ static int setup_level(Handle* h, int l, const int32_t* label, const int32_t* no
     MGR_LAUNCH k_block_inv<<<nblocks(L.nblk, 128), 128, 0, s>>>(L.A.rp, L.A.ci, L.A.v, L.bstart, L.nblk,
                                                       L.binv, h->derr);
     MGR_TRY(check_dev_err(h->derr, s));
+    if (o.global_smoother[l]) {
+      // multicolour point-block Gauss-Seidel: colour the block graph, then
+      // group the blocks by colour
+      L.gs = true;
+      Csr AT;
+      MGR_TRY(transpose(tmp, tmp, L.A, AT, false, false, s));
+      int64_t* blk = tmp.get<int64_t>(n + 1);
+      uint64_t* w = tmp.get<uint64_t>(L.nblk);
+      static constexpr int MAX_COLORS = 1024;
+      unsigned long long* left = tmp.get<unsigned long long>(MAX_COLORS);
+      L.bcolor = P.get<int32_t>(L.nblk);
+      if (tmp.err || P.err) return tmp.err ? tmp.err : P.err;
+      MGR_TRY_CUDA(cudaMemsetAsync(left, 0, sizeof(unsigned long long) * MAX_COLORS, s));
+      MGR_LAUNCH k_blk_of<<<nblocks(L.nblk, 256), 256, 0, s>>>(L.bstart, L.nblk, blk);
+      MGR_LAUNCH k_color_init<<<nblocks(L.nblk, 256), 256, 0, s>>>(L.nblk, o.seed, l, w, L.bcolor);
+      int nc = -1;
+      for (int c0 = 0; c0 < MAX_COLORS && nc < 0; c0 += 4) {
+        for (int c = c0; c < c0 + 4; c++)
+          MGR_LAUNCH k_color_round<<<nblocks(L.nblk, 128), 128, 0, s>>>(L.A.rp, L.A.ci, AT.rp, AT.ci, blk,
+                                                                        L.bstart, L.nblk, w, L.bcolor, c,
+                                                                        left + c);
+        unsigned long long lh[4];
+        MGR_TRY_CUDA(cudaMemcpyAsync(lh, left + c0, sizeof(lh), cudaMemcpyDeviceToHost, s));
+        MGR_TRY_CUDA(cudaStreamSynchronize(s));
+        for (int q = 0; q < 4; q++)
+          if (lh[q] == 0) {
+            nc = c0 + q + 1;
+            break;
+          }
+      }
+      if (nc < 0) return MGR_ERR_INVALID_ARG;   // more than MAX_COLORS colours
+      L.ncolor = nc;
+      int64_t* cnt = tmp.get<int64_t>(nc + 1);
+      L.border = P.get<int64_t>(L.nblk);
+      if (tmp.err || P.err) return tmp.err ? tmp.err : P.err;
+      MGR_TRY_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int64_t) * (nc + 1), s));
+      MGR_LAUNCH k_color_count<<<nblocks(L.nblk, 256), 256, 0, s>>>(L.bcolor, L.nblk, cnt);
+      std::vector<int64_t> hc(nc);
+      MGR_TRY_CUDA(cudaMemcpyAsync(hc.data(), cnt, sizeof(int64_t) * nc, cudaMemcpyDeviceToHost, s));
+      MGR_TRY_CUDA(cudaStreamSynchronize(s));
+      L.coff.assign(nc + 1, 0);
+      for (int c = 0; c < nc; c++) L.coff[c + 1] = L.coff[c] + hc[c];
+      MGR_TRY_CUDA(cudaMemcpyAsync(cnt, L.coff.data(), sizeof(int64_t) * nc, cudaMemcpyHostToDevice, s));
+      MGR_LAUNCH k_color_place<<<nblocks(L.nblk, 256), 256, 0, s>>>(L.bcolor, L.nblk, cnt, L.border);
+      MGR_TRY_CUDA(cudaStreamSynchronize(s));   // coff's host copy outlives the async copy
+    }
   }
   return MGR_SUCCESS;
 }

@@ -28,7 +28,8 @@ EXPORTED = ["mgr_options_default", "fgmres_options_default", "mgr_setup", "mgr_a
             "fgmres_solve", "mgr_destroy", "mgr_error_string", "mgr_get_csr",
             "mgr_amg_levels", "mgr_get_cf", "mgr_vcycle", "mgr_splitmix64_device",
             "mgr_launch_count", "mgr_vcycle_noalloc", "mgr_setup_batched",
-            "fgmres_solve_batched", "mgr_batch_info", "mgr_batch_handle", "mgr_destroy_batched"]
+            "fgmres_solve_batched", "mgr_batch_info", "mgr_batch_handle", "mgr_destroy_batched",
+            "mgr_get_block_colors"]
 
 
 class MgrMatrix(C.Structure):
@@ -49,7 +50,8 @@ class MgrOptions(C.Structure):
                 ("precision", C.c_int32), ("seed", C.c_uint64),
                 ("restrict_jacobi", C.c_int32 * MGR_MAX_LEVELS),
                 ("frelax_post", C.c_int32 * MGR_MAX_LEVELS),
-                ("dff_block", C.c_int32 * MGR_MAX_LEVELS)]
+                ("dff_block", C.c_int32 * MGR_MAX_LEVELS),
+                ("global_smoother", C.c_int32 * MGR_MAX_LEVELS)]
 
 
 class FgmresOptions(C.Structure):
@@ -108,6 +110,8 @@ def lib():
                                          C.POINTER(C.c_int), C.POINTER(C.c_double)]
             L.mgr_batch_handle.argtypes = [P, C.c_int, C.POINTER(P)]
             L.mgr_destroy_batched.argtypes = [P]
+            L.mgr_get_block_colors.argtypes = [P, C.c_int, P, P]
+            L.mgr_get_block_colors.restype = I64
             L.mgr_launch_count.argtypes = []
             L.mgr_launch_count.restype = I64
             _lib = L
@@ -328,6 +332,18 @@ def mgr_vcycle_noalloc(h, slot, b, x, stream=None):
 def mgr_splitmix64_device(inp, out, stream=None):
     return _check(lib().mgr_splitmix64_device(_ptr(inp), _ptr(out), inp.numel(),
                                               _stream_ptr(stream)), "mgr_splitmix64_device")
+
+
+def mgr_get_block_colors(h, level):
+    """(colours of the level's point blocks, colour count) or None."""
+    nc = C.c_int32(0)
+    n = lib().mgr_get_block_colors(h, int(level), None, C.byref(nc))
+    if n < 0:
+        return None
+    out = np.zeros(n, dtype=np.int32)
+    _check(lib().mgr_get_block_colors(h, int(level), out.ctypes.data, C.byref(nc)),
+           "mgr_get_block_colors")
+    return out, nc.value
 
 
 def mgr_launch_count():

@@ -291,3 +291,29 @@ def test_operator_variants_match_oracle(name, kw):
     assert rm["converged"] and rm["relres"] <= 1e-8
     assert _rel(rm["x"].cpu().numpy(), ref["x"]) <= 1e-6
     sm.close()
+
+
+@pytest.mark.parametrize("precision", [mgr.MGR_FP64, mgr.MGR_MIXED])
+def test_multicolour_gauss_seidel_smoother_matches_oracle(precision):
+    """Global smoother option 1 (multicolour point-block Gauss-Seidel at the
+    second reduction): colouring bit-exact, application and FGMRES as the
+    oracle's."""
+    p = synth.two_phase(13, 11, 7, seed=3, sigma=1.5)
+    kw = dict(global_smoother=[0, 1])
+    o = oracle.Oracle(p, **kw)
+    s = mgr.Solver(p, precision=precision, **kw)
+    assert mgr.mgr_get_block_colors(s.h, 0) is None
+    cg, ncg = mgr.mgr_get_block_colors(s.h, 1)
+    co, nco = o.block_colors(1)
+    assert ncg == nco and np.array_equal(cg, co)
+    if precision == mgr.MGR_FP64:
+        compare_hierarchy(o, s.h, 2)
+        v = np.random.default_rng(5).standard_normal(p.n)
+        z = s.apply(torch.from_numpy(v).cuda()).cpu().numpy()
+        assert _rel(z, o.apply(v)) <= 1e-10
+    ref = o.fgmres(p.rhs)
+    r = s.solve(torch.from_numpy(p.rhs).cuda())
+    assert r["converged"] and r["relres"] <= 1e-8
+    assert abs(r["iters"] - ref["iters"]) <= 2, (r["iters"], ref["iters"])
+    assert _rel(r["x"].cpu().numpy(), ref["x"]) <= 1e-6
+    s.close()
