@@ -427,6 +427,32 @@ def run_ours(args):
                      fp64_iters=rd["iters"], speedup_mixed_vs_fp64=msd / msm)
         del Al, bl, xl
 
+    # operator and smoother variants (Sec. 5.1 options, multicolour block
+    # Gauss-Seidel): the same FP64 step on the same workload
+    variants = {}
+    for vname, vkw in (("jacobi_restriction", dict(restrict_jacobi=[1, 1])),
+                       ("mgr_post", dict(frelax_post=[1, 1])),
+                       ("point_block_dff", dict(dff_block=[1, 1])),
+                       ("block_gauss_seidel", dict(global_smoother=[0, 1]))):
+        vo = mgr.mgr_options_default(True, **vkw)
+
+        def vstep():
+            hh = mgr.mgr_setup(A, vo, stream)
+            rr = mgr.fgmres_solve(hh, A, b, x, fo, stream)
+            mgr.mgr_destroy(hh)
+            return rr
+        vstep()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(3):
+            rv = vstep()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        msv = e0.elapsed_time(e1) / 3
+        variants[vname] = dict(ms_per_step=msv, iters=rv["iters"], setup_s=rv["setup_s"],
+                               solve_s=rv["solve_s"], converged=rv["converged"],
+                               relres=rv["relres"])
+
     ensemble = None
     if not args.no_ensemble:
         ensemble = run_ensemble(args, mgr, stream, world)
@@ -463,6 +489,8 @@ def run_ours(args):
         line["large_mixed"] = large
     if ensemble:
         line["ensemble"] = ensemble
+    if variants:
+        line["variants"] = variants
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         t0 = time.perf_counter()
