@@ -51,6 +51,7 @@ class OrcOpts(C.Structure):
         ("frelax_post", C.c_int32 * MAXL),
         ("dff_block", C.c_int32 * MAXL),
         ("global_smoother", C.c_int32 * MAXL),
+        ("agg_levels", C.c_int32 * MAXL),
     ]
 
 
@@ -107,7 +108,8 @@ def default_options(two_phase=True, **kw):
     Operator variants of Sec. 5.1, per level, all off by default:
     restrict_jacobi (W_r = -A_CF D_FF^-1), frelax_post (Eq. MGR-post),
     dff_block (D_FF = point-block diagonal of A_FF); global_smoother 1 =
-    multicolour point-block Gauss-Seidel instead of point-block Jacobi.
+    multicolour point-block Gauss-Seidel instead of point-block Jacobi;
+    agg_levels[s] = leading levels of AMG slot s coarsened aggressively.
     """
     d = dict(num_levels=2 if two_phase else 1,
              f_label_mask=[1 << 0, 1 << 1] if two_phase else [1 << 0],
@@ -117,7 +119,7 @@ def default_options(two_phase=True, **kw):
              global_sweeps=[0, 3] if two_phase else [0],
              amg_theta=0.25, amg_pmax=4, amg_max_coarse=64, amg_max_levels=25, seed=0,
              restrict_jacobi=[0] * MAXL, frelax_post=[0] * MAXL, dff_block=[0] * MAXL,
-             global_smoother=[0] * MAXL)
+             global_smoother=[0] * MAXL, agg_levels=[0] * MAXL)
     d.update(kw)
     return d
 
@@ -126,7 +128,8 @@ def _opts_struct(d):
     o = OrcOpts()
     o.num_levels = d["num_levels"]
     for name in ("f_label_mask", "frelax", "frelax_sweeps", "nmax_drop", "global_sweeps",
-                 "restrict_jacobi", "frelax_post", "dff_block", "global_smoother"):
+                 "restrict_jacobi", "frelax_post", "dff_block", "global_smoother",
+                 "agg_levels"):
         arr = getattr(o, name)
         for i, v in enumerate(d[name]):
             arr[i] = v

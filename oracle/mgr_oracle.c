@@ -21,6 +21,7 @@
  *     (Eq. "MGR-post"), and D_FF as the point-block diagonal of A_FF,
  *   - global smoother: point-block Jacobi, or multicolour point-block
  *     Gauss-Seidel (the parallel reading of hybrid block Gauss-Seidel),
+ *   - optional aggressive (two-stage) coarsening of the first AMG levels,
  *   - the inner AMG (Sec. 6 solver settings: unknown approach for A_uu, scalar
  *     AMG for the pressure Schur complement, coarsest level by Gaussian
  *     elimination), and
@@ -80,6 +81,8 @@ typedef struct {
                                     (blocks of F dofs sharing dof_node) */
   int32_t global_smoother[MAXL]; /* 0: point-block Jacobi sweeps; 1: multicolour
                                     point-block Gauss-Seidel sweeps */
+  int32_t agg_levels[MAXL];      /* AMG slot s: its first agg_levels[s] levels
+                                    are coarsened aggressively (two stages) */
 } orc_opts;
 
 typedef struct {
@@ -391,6 +394,26 @@ static void top_abs(const int32_t *col, const double *val, int64_t m, int64_t ke
 /* Direct interpolation (Stueben), restricted to equal components; positive
  * couplings are lumped into the diagonal when no positive strong C neighbour
  * exists; then truncation to the pmax largest |w| with the row sum kept. */
+/* P_max truncation of one interpolation row (columns ascending): keep the
+ * pmax entries of largest |w| (ties: smaller column) and rescale them by
+ * (sum of all w) / (sum of kept w), both sums in row order.  Returns the new
+ * length. */
+static int64_t truncate_row(int32_t *tc, double *tv, int64_t m, int pmax, int8_t *mask) {
+  if (pmax <= 0 || m <= pmax) return m;
+  top_abs(tc, tv, m, pmax, mask);
+  double sall = 0.0, skept = 0.0;
+  for (int64_t t = 0; t < m; t++) sall = sall + tv[t];
+  for (int64_t t = 0; t < m; t++) if (mask[t]) skept = skept + tv[t];
+  int64_t q = 0;
+  for (int64_t t = 0; t < m; t++) {
+    if (!mask[t]) continue;
+    tc[q] = tc[t];
+    tv[q] = (skept != 0.0) ? tv[t] * (sall / skept) : tv[t];
+    q++;
+  }
+  return q;
+}
+
 static void amg_interp(const ocsr *a, const ocsr *s, const int32_t *comp, const int8_t *cf,
                        int pmax, ocsr *p, int64_t *nc_out) {
   int64_t n = a->nr;
@@ -438,20 +461,7 @@ static void amg_interp(const ocsr *a, const ocsr *s, const int32_t *comp, const 
         }
       }
       for (int64_t k = s->rp[i]; k < s->rp[i + 1]; k++) strong[s->ci[k]] = 0;
-      if (pmax > 0 && m > pmax) {
-        top_abs(tc, tv, m, pmax, mask);
-        double sall = 0.0, skept = 0.0;
-        for (int64_t t = 0; t < m; t++) sall = sall + tv[t];
-        for (int64_t t = 0; t < m; t++) if (mask[t]) skept = skept + tv[t];
-        int64_t q = 0;
-        for (int64_t t = 0; t < m; t++) {
-          if (!mask[t]) continue;
-          tc[q] = tc[t];
-          tv[q] = (skept != 0.0) ? tv[t] * (sall / skept) : tv[t];
-          q++;
-        }
-        m = q;
-      }
+      m = truncate_row(tc, tv, m, pmax, mask);
     }
     if (nnz + m > cap) {
       while (nnz + m > cap) cap *= 2;
@@ -519,6 +529,56 @@ static int amg_setup(const ocsr *a, const int32_t *comp, const orc_opts *o, int 
     for (int64_t i = 0; i < n; i++) nc += (L->cf[i] == 1);
     if (nc == 0 || nc == n) break;
     amg_interp(&L->A, &L->S, L->comp, L->cf, o->amg_pmax, &L->P, &nc);
+    if (slot < MAXL && k < o->agg_levels[slot]) {
+      /* Aggressive coarsening, two stages (Sec. 6 names one level of it for
+       * A_uu): PMIS and direct interpolation P1 as above, then the same on the
+       * Galerkin operator of the first C points (PMIS key level 32 + k), and
+       * P = P1 P2 truncated to P_max by the rule of the direct interpolation.
+       * If the second stage cannot coarsen, the level stays an ordinary one. */
+      ocsr R1, AP1, A1, S1, P2;
+      csr_transpose(&L->P, &R1);
+      csr_matmul(&L->A, &L->P, &AP1);
+      csr_matmul(&R1, &AP1, &A1);
+      int32_t *comp1 = xcalloc((size_t)nc + 1, sizeof(int32_t));
+      int64_t *cmap1 = xcalloc((size_t)n + 1, sizeof(int64_t));
+      for (int64_t i = 0, c = 0; i < n; i++) {
+        cmap1[i] = (L->cf[i] == 1) ? c : -1;
+        if (L->cf[i] == 1) comp1[c++] = L->comp[i];
+      }
+      amg_strength(&A1, comp1, o->amg_theta, &S1);
+      int8_t *cf2 = xcalloc((size_t)nc + 1, 1);
+      amg_pmis(&S1, o->seed, slot, 32 + k, cf2);
+      int64_t nc2 = 0;
+      for (int64_t c = 0; c < nc; c++) nc2 += (cf2[c] == 1);
+      if (nc2 > 0 && nc2 < nc) {
+        amg_interp(&A1, &S1, comp1, cf2, o->amg_pmax, &P2, &nc2);
+        ocsr PP;
+        csr_matmul(&L->P, &P2, &PP);
+        int32_t *tc = xcalloc((size_t)nc2 + 1, sizeof(int32_t));
+        double *tv = xcalloc((size_t)nc2 + 1, sizeof(double));
+        int8_t *mask = xcalloc((size_t)nc2 + 1, 1);
+        ocsr Pt;
+        csr_init(&Pt, n, nc2, PP.nnz);
+        int64_t nz = 0;
+        for (int64_t i = 0; i < n; i++) {
+          int64_t m = 0;
+          for (int64_t q = PP.rp[i]; q < PP.rp[i + 1]; q++) { tc[m] = PP.ci[q]; tv[m] = PP.v[q]; m++; }
+          m = truncate_row(tc, tv, m, o->amg_pmax, mask);
+          for (int64_t t = 0; t < m; t++) { Pt.ci[nz] = tc[t]; Pt.v[nz] = tv[t]; nz++; }
+          Pt.rp[i + 1] = nz;
+        }
+        Pt.nnz = nz;
+        csr_free(&L->P);
+        L->P = Pt;
+        for (int64_t i = 0; i < n; i++)
+          if (L->cf[i] == 1 && cf2[cmap1[i]] != 1) L->cf[i] = -1;
+        nc = nc2;
+        csr_free(&PP); csr_free(&P2);
+        free(tc); free(tv); free(mask);
+      }
+      csr_free(&R1); csr_free(&AP1); csr_free(&A1); csr_free(&S1);
+      free(comp1); free(cmap1); free(cf2);
+    }
     csr_transpose(&L->P, &L->R);
     ocsr AP;
     csr_matmul(&L->A, &L->P, &AP);

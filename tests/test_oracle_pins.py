@@ -532,3 +532,49 @@ def test_block_jacobi_smoother_is_block_jacobi():
         z = z + np.linalg.solve(D, v - S @ z)
     got = o.global_relax(1, v)
     assert np.abs(got - z).max() <= 1e-11 * np.abs(z).max()
+
+
+# ---------------------------------------------------------------------------
+# Aggressive (two-stage) coarsening of the first A_uu AMG level
+# ---------------------------------------------------------------------------
+def test_aggressive_level_composes_two_stages():
+    # With no truncation the aggressive interpolation must be P = P1 P2: P1 is
+    # the ordinary first level's interpolation (same first stage), and since
+    # P1 has identity rows at its C points, P2 = P[C1 rows]; P2 is the identity
+    # on the final C points, C2 is a subset of C1, and the next operator is the
+    # Galerkin product P^T A P.
+    p = synth.two_phase(8, 7, 5, seed=6)
+    base = oracle.Oracle(p, amg_pmax=0)
+    agg = oracle.Oracle(p, amg_pmax=0, agg_levels=[1, 0, 0])
+    A = agg.scipy(oracle.Q_AMG_A, 0, 0).toarray()
+    P1 = base.scipy(oracle.Q_AMG_P, 0, 0).toarray()
+    P = agg.scipy(oracle.Q_AMG_P, 0, 0).toarray()
+    cf1, cf = base.cf(0, 0), agg.cf(0, 0)
+    C1, C = np.nonzero(cf1 == 1)[0], np.nonzero(cf == 1)[0]
+    assert set(C) < set(C1) and len(C) < len(C1)
+    P2 = P[C1, :]
+    assert np.abs(P - P1 @ P2).max() <= 1e-13 * np.abs(P).max()
+    pos = {c: t for t, c in enumerate(C1)}
+    assert np.array_equal(P2[[pos[c] for c in C], :], np.eye(len(C)))
+    Ac = agg.scipy(oracle.Q_AMG_A, 0, 1).toarray()
+    assert np.abs(Ac - P.T @ A @ P).max() <= 1e-12 * np.abs(Ac).max()
+    # the intermediate Galerkin operator is the ordinary hierarchy's level 1
+    A1 = base.scipy(oracle.Q_AMG_A, 0, 1).toarray()
+    assert np.abs(A1 - P1.T @ A @ P1).max() <= 1e-12 * np.abs(A1).max()
+
+
+def test_aggressive_level_truncation_and_hierarchy():
+    p = synth.two_phase(8, 7, 5, seed=6)
+    base = oracle.Oracle(p)
+    agg = oracle.Oracle(p, agg_levels=[1, 0, 0])
+    P = agg.scipy(oracle.Q_AMG_P, 0, 0)
+    assert np.diff(P.indptr).max() <= 4                        # P_max = 4
+    C = np.nonzero(agg.cf(0, 0) == 1)[0]
+    Pd = P.toarray()
+    assert np.array_equal(Pd[C, :], np.eye(len(C)))
+    n0 = [base.scipy(oracle.Q_AMG_A, 0, k).shape[0] for k in range(base.amg_levels(0))]
+    n1 = [agg.scipy(oracle.Q_AMG_A, 0, k).shape[0] for k in range(agg.amg_levels(0))]
+    assert n1[0] == n0[0] and n1[1] < n0[1] // 3               # one aggressive step
+    assert agg.amg_levels(2) == base.amg_levels(2)             # other AMGs untouched
+    r = agg.fgmres(p.rhs)
+    assert r["status"] == 0 and r["relres"] <= 1e-8
