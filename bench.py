@@ -433,7 +433,8 @@ def run_ours(args):
     for vname, vkw in (("jacobi_restriction", dict(restrict_jacobi=[1, 1])),
                        ("mgr_post", dict(frelax_post=[1, 1])),
                        ("point_block_dff", dict(dff_block=[1, 1])),
-                       ("block_gauss_seidel", dict(global_smoother=[0, 1]))):
+                       ("block_gauss_seidel", dict(global_smoother=[0, 1])),
+                       ("aggressive_uu_amg", dict(agg_levels=[1, 0, 0]))):
         vo = mgr.mgr_options_default(True, **vkw)
 
         def vstep():

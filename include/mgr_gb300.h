@@ -127,6 +127,13 @@ typedef struct {
    * the smaller block), each sweep visiting the colours in ascending order
    * and updating every block of a colour from the latest z. */
   int32_t global_smoother[MGR_MAX_LEVELS];
+  /* Aggressive coarsening (Sec. 6 names one level of it for A_uu): the first
+   * agg_levels[s] levels of AMG slot s (slot l < num_levels: the F-relaxation
+   * AMG of MGR level l; slot num_levels: the coarsest AMG) coarsen in two
+   * stages -- PMIS + direct interpolation P1, then the same on P1^T A P1
+   * (PMIS weights keyed by level 32 + k), P = P1 P2 truncated to amg_pmax by
+   * the direct interpolation's rule.  0 in the defaults. */
+  int32_t agg_levels[MGR_MAX_LEVELS];
 } mgr_options_t;
 
 typedef struct {

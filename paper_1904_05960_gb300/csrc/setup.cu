@@ -1670,6 +1670,160 @@ static int dense_coarsest(Pool& P, int* derr, Amg* g, Pool& tmp, cudaStream_t s)
   return check_dev_err(derr, s);
 }
 
+// P_max truncation of the rows of a product interpolation P1 P2 (columns
+// ascending): keep the pmax entries of largest |w| (ties: the earlier entry,
+// i.e. the smaller column) and rescale them by (sum of all w) / (sum of kept
+// w), both sums in row order -- the rule of the direct interpolation.  Thread
+// per row; an entry is kept when fewer than pmax entries beat it.
+__device__ __forceinline__ uint64_t abs_bits(double x) {
+  return (uint64_t)__double_as_longlong(x) & 0x7fffffffffffffffull;
+}
+template <bool FILL>
+__global__ void k_trunc_rows(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                             const double* __restrict__ v, int64_t n, int pmax,
+                             int64_t* __restrict__ cnt_or_rp, int32_t* __restrict__ oci,
+                             double* __restrict__ ov) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int64_t e0 = rp[i], e1 = rp[i + 1], m = e1 - e0;
+  if (pmax <= 0 || m <= pmax) {
+    if (!FILL) {
+      cnt_or_rp[i] = m;
+    } else {
+      int64_t o = cnt_or_rp[i];
+      for (int64_t q = e0; q < e1; q++, o++) {
+        oci[o] = ci[q];
+        ov[o] = v[q];
+      }
+    }
+    return;
+  }
+  if (!FILL) {
+    cnt_or_rp[i] = pmax;
+    return;
+  }
+  double sall = 0.0, skept = 0.0;
+  for (int64_t q = e0; q < e1; q++) sall = __dadd_rn(sall, v[q]);
+  for (int64_t q = e0; q < e1; q++) {
+    const uint64_t aq = abs_bits(v[q]);
+    int r = 0;
+    for (int64_t u = e0; u < e1; u++) {
+      const uint64_t au = abs_bits(v[u]);
+      r += (au > aq || (au == aq && u < q));
+    }
+    if (r < pmax) skept = __dadd_rn(skept, v[q]);
+  }
+  const double ratio = (skept != 0.0) ? __ddiv_rn(sall, skept) : 1.0;
+  int64_t o = cnt_or_rp[i];
+  for (int64_t q = e0; q < e1; q++) {
+    const uint64_t aq = abs_bits(v[q]);
+    int r = 0;
+    for (int64_t u = e0; u < e1; u++) {
+      const uint64_t au = abs_bits(v[u]);
+      r += (au > aq || (au == aq && u < q));
+    }
+    if (r < pmax) {
+      oci[o] = ci[q];
+      ov[o] = (skept != 0.0) ? __dmul_rn(v[q], ratio) : v[q];
+      o++;
+    }
+  }
+}
+
+// the aggressive level's C points: first-stage C points that the second stage
+// kept C
+__global__ void k_agg_cf(int8_t* __restrict__ cf, const int64_t* __restrict__ cmap,
+                         const int8_t* __restrict__ cf2, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && cf[i] == 1 && cf2[cmap[i]] != 1) cf[i] = -1;
+}
+
+// One coarsening step on (A, comp): strength S (into Ps), PMIS C/F marks
+// (weights keyed by `level`; into Ps), coarse numbering cmap (tmp), direct
+// interpolation with P_max truncation (into Pi).  *nc = number of C points
+// (no interpolation is built when it is 0 or n).
+static int coarsen_step(const mgr_options_t& o, Pool& Ps, Pool& Pi, Pool& tmp, const Csr& A,
+                        const int32_t* comp, int slot, int level, Csr& S, int8_t** cf_out,
+                        int64_t** cmap_out, Csr& Pm, int64_t* nc_out, cudaStream_t s) {
+  const int64_t n = A.nr;
+  *nc_out = 0;
+  int64_t* cnt = tmp.get<int64_t>(n + 1);
+  S.nr = S.nc = n;
+  S.rp = Ps.get<int64_t>(n + 1);
+  if (tmp.err || Ps.err) return tmp.err ? tmp.err : Ps.err;
+  MGR_LAUNCH k_strength<false><<<grid_for(n, 8, 152 * 16), 256, 0, s>>>(A.rp, A.ci, A.v, comp, n,
+                                                                       o.amg_theta, cnt, nullptr);
+  MGR_TRY(rowptr_from_counts(cnt, S.rp, n, &S.nnz, s, tmp));
+  S.ci = Ps.get<int32_t>(S.nnz);
+  if (Ps.err) return Ps.err;
+  MGR_LAUNCH k_strength<true><<<grid_for(n, 8, 152 * 16), 256, 0, s>>>(A.rp, A.ci, A.v, comp, n,
+                                                                      o.amg_theta, S.rp, S.ci);
+  g_trace.mark("amg strength", slot, level);
+  Csr ST;
+  MGR_TRY(transpose(tmp, tmp, S, ST, false, false, s));
+  // PMIS
+  double* w = tmp.get<double>(n);
+  int8_t* newc = tmp.get<int8_t>(n);
+  int8_t* cf = Ps.get<int8_t>(n);
+  unsigned long long* und = tmp.get<unsigned long long>(1);
+  if (tmp.err || Ps.err) return tmp.err ? tmp.err : Ps.err;
+  *cf_out = cf;
+  MGR_LAUNCH k_pmis_init<<<nblocks(n, 256), 256, 0, s>>>(S.rp, ST.rp, n, o.seed, slot, level, w, cf);
+  // synchronous rounds, checked every 4th: a round after the last
+  // undecided point is gone changes nothing
+  for (int round = 0; round < 100000; round += 4) {
+    for (int q = 0; q < 4; q++) {
+      MGR_LAUNCH k_pmis_select<<<nblocks(n, 256), 256, 0, s>>>(S.rp, S.ci, ST.rp, ST.ci, w, cf, n, newc);
+      MGR_LAUNCH k_pmis_apply_c<<<nblocks(n, 256), 256, 0, s>>>(newc, n, cf);
+      cudaMemsetAsync(und, 0, sizeof(unsigned long long), s);
+      MGR_LAUNCH k_pmis_mark_f<<<nblocks(n, 256), 256, 0, s>>>(S.rp, S.ci, n, cf, und);
+    }
+    unsigned long long left = 0;
+    MGR_TRY(read_back(&left, und, s));
+    if (left == 0) break;
+  }
+  g_trace.mark("amg pmis", slot, level);
+  // coarse numbering
+  int64_t* flag = tmp.get<int64_t>(n + 1);
+  int64_t* cmap = tmp.get<int64_t>(n + 1);
+  if (tmp.err) return tmp.err;
+  *cmap_out = cmap;
+  MGR_LAUNCH k_flag_c<<<nblocks(n, 256), 256, 0, s>>>(cf, n, flag);
+  int64_t nc = 0;
+  MGR_TRY(rowptr_from_counts(flag, cmap, n, &nc, s, tmp));
+  *nc_out = nc;
+  if (nc == 0 || nc == n) return MGR_SUCCESS;
+  // interpolation
+  if (o.amg_pmax > PMAX_CAP) return MGR_ERR_INVALID_ARG;
+  Pm.nr = n;
+  Pm.nc = nc;
+  Pm.rp = Pi.get<int64_t>(n + 1);
+  if (Pi.err) return Pi.err;
+  // FP64 work is lane-dense in the thread-per-row form; the warp form wins
+  // only where a level has too few rows to fill the GPU (measured on GB300:
+  // on the 113k-row, 150-non-zero level the warp form took 2.4 ms against
+  // 0.8 ms)
+  const bool big = n >= 20000;
+  if (big)
+    MGR_LAUNCH k_interp_thread<false><<<nblocks(n, 128), 128, 0, s>>>(A.rp, A.ci, A.v, S.rp, S.ci, comp, cf,
+                                                                     cmap, n, o.amg_pmax, cnt, nullptr, nullptr);
+  else
+    MGR_LAUNCH k_interp<false><<<grid_for(n, IW_WARPS, 152 * 32), IW_WARPS * 32, 0, s>>>(
+        A.rp, A.ci, A.v, S.rp, S.ci, comp, cf, cmap, n, o.amg_pmax, cnt, nullptr, nullptr);
+  MGR_TRY(rowptr_from_counts(cnt, Pm.rp, n, &Pm.nnz, s, tmp));
+  Pm.ci = Pi.get<int32_t>(Pm.nnz);
+  Pm.v = Pi.get<double>(Pm.nnz);
+  if (Pi.err) return Pi.err;
+  if (big)
+    MGR_LAUNCH k_interp_thread<true><<<nblocks(n, 128), 128, 0, s>>>(A.rp, A.ci, A.v, S.rp, S.ci, comp, cf,
+                                                                    cmap, n, o.amg_pmax, Pm.rp, Pm.ci, Pm.v);
+  else
+    MGR_LAUNCH k_interp<true><<<grid_for(n, IW_WARPS, 152 * 32), IW_WARPS * 32, 0, s>>>(
+        A.rp, A.ci, A.v, S.rp, S.ci, comp, cf, cmap, n, o.amg_pmax, Pm.rp, Pm.ci, Pm.v);
+  g_trace.mark("amg interp", slot, level);
+  return MGR_SUCCESS;
+}
+
 int build_amg(Handle* h, Pool& P, int* derr, const Csr& A0, bool own_input,
               const int32_t* comp0, int slot, Amg** out, cudaStream_t s) {
   Pool tmp;
@@ -1704,83 +1858,60 @@ int build_amg(Handle* h, Pool& P, int* derr, const Csr& A0, bool own_input,
     l1_inv(L->A, L->dinv, derr, s);
     if (n <= o.amg_max_coarse || k + 1 >= o.amg_max_levels || k + 1 >= 32) break;
     g_trace.mark("amg l1", slot, k);
-    // strength graph
-    int64_t* cnt = tmp.get<int64_t>(n + 1);
-    L->S.nr = L->S.nc = n;
-    L->S.rp = P.get<int64_t>(n + 1);
-    if (tmp.err || P.err) { rc = tmp.err ? tmp.err : P.err; break; }
-    MGR_LAUNCH k_strength<false><<<grid_for(n, 8, 152 * 16), 256, 0, s>>>(L->A.rp, L->A.ci, L->A.v, L->comp, n,
-                                                     o.amg_theta, cnt, nullptr);
-    if ((rc = rowptr_from_counts(cnt, L->S.rp, n, &L->S.nnz, s, tmp))) break;
-    L->S.ci = P.get<int32_t>(L->S.nnz);
-    if (P.err) { rc = P.err; break; }
-    MGR_LAUNCH k_strength<true><<<grid_for(n, 8, 152 * 16), 256, 0, s>>>(L->A.rp, L->A.ci, L->A.v, L->comp, n,
-                                                    o.amg_theta, L->S.rp, L->S.ci);
-    g_trace.mark("amg strength", slot, k);
-    Csr ST;
-    if ((rc = transpose(tmp, tmp, L->S, ST, false, false, s))) break;
-    // PMIS
-    double* w = tmp.get<double>(n);
-    int8_t* newc = tmp.get<int8_t>(n);
-    L->cf = P.get<int8_t>(n);
-    unsigned long long* und = tmp.get<unsigned long long>(1);
-    if (tmp.err || P.err) { rc = tmp.err ? tmp.err : P.err; break; }
-    MGR_LAUNCH k_pmis_init<<<nblocks(n, 256), 256, 0, s>>>(L->S.rp, ST.rp, n, o.seed, slot, k, w, L->cf);
-    // synchronous rounds, checked every 4th: a round after the last
-    // undecided point is gone changes nothing
-    for (int round = 0; round < 100000; round += 4) {
-      for (int q = 0; q < 4; q++) {
-        MGR_LAUNCH k_pmis_select<<<nblocks(n, 256), 256, 0, s>>>(L->S.rp, L->S.ci, ST.rp, ST.ci, w, L->cf, n, newc);
-        MGR_LAUNCH k_pmis_apply_c<<<nblocks(n, 256), 256, 0, s>>>(newc, n, L->cf);
-        cudaMemsetAsync(und, 0, sizeof(unsigned long long), s);
-        MGR_LAUNCH k_pmis_mark_f<<<nblocks(n, 256), 256, 0, s>>>(L->S.rp, L->S.ci, n, L->cf, und);
-      }
-      unsigned long long left = 0;
-      if ((rc = read_back(&left, und, s))) break;
-      if (left == 0) break;
-    }
-    if (rc) break;
-    g_trace.mark("amg pmis", slot, k);
-    // coarse numbering
-    int64_t* flag = tmp.get<int64_t>(n + 1);
-    int64_t* cmap = tmp.get<int64_t>(n + 1);
-    if (tmp.err) { rc = tmp.err; break; }
-    MGR_LAUNCH k_flag_c<<<nblocks(n, 256), 256, 0, s>>>(L->cf, n, flag);
     int64_t nc = 0;
-    if ((rc = rowptr_from_counts(flag, cmap, n, &nc, s, tmp))) break;
+    int64_t* cmap = nullptr;
+    const bool agg = slot < MGR_MAX_LEVELS && k < o.agg_levels[slot];
+    // an aggressive level's first-stage interpolation is scratch
+    if ((rc = coarsen_step(o, P, agg ? tmp : P, tmp, L->A, L->comp, slot, k, L->S, &L->cf, &cmap, L->P,
+                           &nc, s)))
+      break;
     if (nc == 0 || nc == n) break;
-    // interpolation
-    if (o.amg_pmax > PMAX_CAP) { rc = MGR_ERR_INVALID_ARG; break; }
-    L->P.nr = n;
-    L->P.nc = nc;
-    L->P.rp = P.get<int64_t>(n + 1);
-    if (P.err) { rc = P.err; break; }
-    // FP64 work is lane-dense in the thread-per-row form; the warp form wins
-    // only where a level has too few rows to fill the GPU (measured on GB300:
-    // on the 113k-row, 150-non-zero level the warp form took 2.4 ms against
-    // 0.8 ms)
-    const bool big = n >= 20000;
-    if (big)
-      MGR_LAUNCH k_interp_thread<false><<<nblocks(n, 128), 128, 0, s>>>(L->A.rp, L->A.ci, L->A.v, L->S.rp, L->S.ci,
-                                                   L->comp, L->cf, cmap, n, o.amg_pmax, cnt,
-                                                   nullptr, nullptr);
-    else
-      MGR_LAUNCH k_interp<false><<<grid_for(n, IW_WARPS, 152 * 32), IW_WARPS * 32, 0, s>>>(L->A.rp, L->A.ci, L->A.v, L->S.rp, L->S.ci,
-                                                   L->comp, L->cf, cmap, n, o.amg_pmax, cnt,
-                                                   nullptr, nullptr);
-    if ((rc = rowptr_from_counts(cnt, L->P.rp, n, &L->P.nnz, s, tmp))) break;
-    L->P.ci = P.get<int32_t>(L->P.nnz);
-    L->P.v = P.get<double>(L->P.nnz);
-    if (P.err) { rc = P.err; break; }
-    if (big)
-      MGR_LAUNCH k_interp_thread<true><<<nblocks(n, 128), 128, 0, s>>>(L->A.rp, L->A.ci, L->A.v, L->S.rp, L->S.ci,
-                                                  L->comp, L->cf, cmap, n, o.amg_pmax, L->P.rp,
-                                                  L->P.ci, L->P.v);
-    else
-      MGR_LAUNCH k_interp<true><<<grid_for(n, IW_WARPS, 152 * 32), IW_WARPS * 32, 0, s>>>(L->A.rp, L->A.ci, L->A.v, L->S.rp, L->S.ci,
-                                                  L->comp, L->cf, cmap, n, o.amg_pmax, L->P.rp,
-                                                  L->P.ci, L->P.v);
-    g_trace.mark("amg interp", slot, k);
+    if (agg) {
+      // aggressive coarsening, second stage: the same step on the Galerkin
+      // operator of the first C points (PMIS weights keyed by level 32 + k),
+      // then P = P1 P2 truncated to P_max
+      Csr R1, AP1, A1, S1, P2;
+      if ((rc = transpose(tmp, tmp, L->P, R1, true, true, s))) break;
+      if ((rc = spgemm(tmp, tmp, L->A, L->P, AP1, s))) break;
+      if ((rc = spgemm(tmp, tmp, R1, AP1, A1, s))) break;
+      int32_t* comp1 = tmp.get<int32_t>(nc);
+      if (tmp.err) { rc = tmp.err; break; }
+      MGR_LAUNCH k_coarse_comp<<<nblocks(n, 256), 256, 0, s>>>(L->cf, cmap, L->comp, n, comp1);
+      int8_t* cf2 = nullptr;
+      int64_t* cmap2 = nullptr;
+      int64_t nc2 = 0;
+      if ((rc = coarsen_step(o, tmp, tmp, tmp, A1, comp1, slot, 32 + k, S1, &cf2, &cmap2, P2, &nc2, s))) break;
+      Csr Pfin = L->P;
+      if (nc2 > 0 && nc2 < nc) {
+        Csr PP;
+        if ((rc = spgemm(tmp, tmp, L->P, P2, PP, s))) break;
+        int64_t* tcnt = tmp.get<int64_t>(n + 1);
+        Pfin.nr = n;
+        Pfin.nc = nc2;
+        Pfin.rp = P.get<int64_t>(n + 1);
+        if (tmp.err || P.err) { rc = tmp.err ? tmp.err : P.err; break; }
+        MGR_LAUNCH k_trunc_rows<false><<<nblocks(n, 128), 128, 0, s>>>(PP.rp, PP.ci, PP.v, n, o.amg_pmax,
+                                                                       tcnt, nullptr, nullptr);
+        if ((rc = rowptr_from_counts(tcnt, Pfin.rp, n, &Pfin.nnz, s, tmp))) break;
+        Pfin.ci = P.get<int32_t>(Pfin.nnz);
+        Pfin.v = P.get<double>(Pfin.nnz);
+        if (P.err) { rc = P.err; break; }
+        MGR_LAUNCH k_trunc_rows<true><<<nblocks(n, 128), 128, 0, s>>>(PP.rp, PP.ci, PP.v, n, o.amg_pmax,
+                                                                      Pfin.rp, Pfin.ci, Pfin.v);
+        MGR_LAUNCH k_agg_cf<<<nblocks(n, 256), 256, 0, s>>>(L->cf, cmap, cf2, n);
+        // numbering of the final C points
+        int64_t* flag = tmp.get<int64_t>(n + 1);
+        cmap = tmp.get<int64_t>(n + 1);
+        if (tmp.err) { rc = tmp.err; break; }
+        MGR_LAUNCH k_flag_c<<<nblocks(n, 256), 256, 0, s>>>(L->cf, n, flag);
+        if ((rc = rowptr_from_counts(flag, cmap, n, &nc, s, tmp))) break;
+      } else {
+        // the second stage cannot coarsen: an ordinary level (keep P1)
+        if ((rc = copy_csr(P, L->P, Pfin, s))) break;
+      }
+      L->P = Pfin;
+      g_trace.mark("amg aggressive stage 2", slot, k);
+    }
     if ((rc = transpose(P, tmp, L->P, L->R, true, true, s))) break;
     g_trace.mark("amg transpose P", slot, k);
     Csr AP;

@@ -51,7 +51,8 @@ class MgrOptions(C.Structure):
                 ("restrict_jacobi", C.c_int32 * MGR_MAX_LEVELS),
                 ("frelax_post", C.c_int32 * MGR_MAX_LEVELS),
                 ("dff_block", C.c_int32 * MGR_MAX_LEVELS),
-                ("global_smoother", C.c_int32 * MGR_MAX_LEVELS)]
+                ("global_smoother", C.c_int32 * MGR_MAX_LEVELS),
+                ("agg_levels", C.c_int32 * MGR_MAX_LEVELS)]
 
 
 class FgmresOptions(C.Structure):

@@ -317,3 +317,25 @@ def test_multicolour_gauss_seidel_smoother_matches_oracle(precision):
     assert abs(r["iters"] - ref["iters"]) <= 2, (r["iters"], ref["iters"])
     assert _rel(r["x"].cpu().numpy(), ref["x"]) <= 1e-6
     s.close()
+
+
+@pytest.mark.parametrize("precision", [mgr.MGR_FP64, mgr.MGR_MIXED])
+def test_aggressive_coarsening_matches_oracle(precision):
+    """One level of two-stage aggressive coarsening in the A_uu AMG: hierarchy
+    bit-exact (C/F marks, strength, P = P1 P2 truncated, Galerkin products),
+    FGMRES as the oracle's."""
+    p = synth.two_phase(13, 11, 7, seed=3, sigma=1.5)
+    kw = dict(agg_levels=[1, 0, 0])
+    o = oracle.Oracle(p, **kw)
+    s = mgr.Solver(p, precision=precision, **kw)
+    if precision == mgr.MGR_FP64:
+        compare_hierarchy(o, s.h, 2)
+        base = oracle.Oracle(p)
+        assert o.amg_levels(0) < base.amg_levels(0) or \
+            o.scipy(oracle.Q_AMG_A, 0, 1).shape[0] < base.scipy(oracle.Q_AMG_A, 0, 1).shape[0]
+    ref = o.fgmres(p.rhs)
+    r = s.solve(torch.from_numpy(p.rhs).cuda())
+    assert r["converged"] and r["relres"] <= 1e-8
+    assert abs(r["iters"] - ref["iters"]) <= 2, (r["iters"], ref["iters"])
+    assert _rel(r["x"].cpu().numpy(), ref["x"]) <= 1e-6
+    s.close()
