@@ -29,6 +29,7 @@ _lib = None
 MAXL = 8
 
 Q_MGR_A, Q_MGR_W, Q_MGR_COR, Q_MGR_CORKEPT, Q_MGR_S, Q_MGR_WR, Q_MGR_BD = 0, 1, 2, 3, 4, 5, 6
+Q_MGR_ILU = 7
 Q_AMG_A, Q_AMG_S, Q_AMG_P, Q_AMG_R = 10, 11, 12, 13
 
 FRELAX_AMG, FRELAX_JACOBI = 0, 1
@@ -52,6 +53,7 @@ class OrcOpts(C.Structure):
         ("dff_block", C.c_int32 * MAXL),
         ("global_smoother", C.c_int32 * MAXL),
         ("agg_levels", C.c_int32 * MAXL),
+        ("ilu_solve_sweeps", C.c_int32),
     ]
 
 
@@ -108,7 +110,8 @@ def default_options(two_phase=True, **kw):
     Operator variants of Sec. 5.1, per level, all off by default:
     restrict_jacobi (W_r = -A_CF D_FF^-1), frelax_post (Eq. MGR-post),
     dff_block (D_FF = point-block diagonal of A_FF); global_smoother 1 =
-    multicolour point-block Gauss-Seidel instead of point-block Jacobi;
+    multicolour point-block Gauss-Seidel, 2 = ILU(1) (ilu_solve_sweeps Jacobi
+    iterations per triangular solve), instead of point-block Jacobi;
     agg_levels[s] = leading levels of AMG slot s coarsened aggressively.
     """
     d = dict(num_levels=2 if two_phase else 1,
@@ -119,7 +122,8 @@ def default_options(two_phase=True, **kw):
              global_sweeps=[0, 3] if two_phase else [0],
              amg_theta=0.25, amg_pmax=4, amg_max_coarse=64, amg_max_levels=25, seed=0,
              restrict_jacobi=[0] * MAXL, frelax_post=[0] * MAXL, dff_block=[0] * MAXL,
-             global_smoother=[0] * MAXL, agg_levels=[0] * MAXL)
+             global_smoother=[0] * MAXL, agg_levels=[0] * MAXL,
+             ilu_solve_sweeps=3)
     d.update(kw)
     return d
 
@@ -138,6 +142,7 @@ def _opts_struct(d):
     o.amg_max_coarse = d["amg_max_coarse"]
     o.amg_max_levels = d["amg_max_levels"]
     o.seed = d["seed"]
+    o.ilu_solve_sweeps = d["ilu_solve_sweeps"]
     return o
 
 

@@ -19,8 +19,9 @@
  *   - options of Sec. 5.1: Jacobi restriction W_r = -A_CF D_FF^-1 (full
  *     triple product R~ A P~), F-relaxation after the coarse-grid correction
  *     (Eq. "MGR-post"), and D_FF as the point-block diagonal of A_FF,
- *   - global smoother: point-block Jacobi, or multicolour point-block
- *     Gauss-Seidel (the parallel reading of hybrid block Gauss-Seidel),
+ *   - global smoother: point-block Jacobi, multicolour point-block
+ *     Gauss-Seidel (the parallel reading of hybrid block Gauss-Seidel), or
+ *     ILU(1) with Jacobi iterations for its triangular solves,
  *   - optional aggressive (two-stage) coarsening of the first AMG levels,
  *   - the inner AMG (Sec. 6 solver settings: unknown approach for A_uu, scalar
  *     AMG for the pressure Schur complement, coarsest level by Gaussian
@@ -83,6 +84,8 @@ typedef struct {
                                     point-block Gauss-Seidel sweeps */
   int32_t agg_levels[MAXL];      /* AMG slot s: its first agg_levels[s] levels
                                     are coarsened aggressively (two stages) */
+  int32_t ilu_solve_sweeps;      /* global smoother 2 (ILU(1)): Jacobi iterations
+                                    per triangular solve */
 } orc_opts;
 
 typedef struct {
@@ -122,6 +125,8 @@ typedef struct {
   double *binv;           /* 16 doubles per block (row-major, size b) */
   int32_t *bcolor;        /* multicolour Gauss-Seidel: colour of each block */
   int32_t ncolor;
+  ocsr ilu;               /* ILU(1) smoother: L (strict, unit diagonal) and U on
+                             one pattern, l_ij for i > j, u_ij for i <= j */
 } mgr_level;
 
 typedef struct {
@@ -658,7 +663,7 @@ static int small_inverse(const double *a, double *inv, int b) {
 
 static void mgr_level_free(mgr_level *l) {
   csr_free(&l->A); csr_free(&l->W); csr_free(&l->Acf); csr_free(&l->Afc);
-  csr_free(&l->Wr); csr_free(&l->Bd);
+  csr_free(&l->Wr); csr_free(&l->Bd); csr_free(&l->ilu);
   csr_free(&l->cor); csr_free(&l->corkept);
   free(l->label); free(l->node); free(l->comp); free(l->Fidx); free(l->Cidx); free(l->pos);
   free(l->dF); free(l->bstart); free(l->bsize); free(l->binv); free(l->bcolor);
@@ -715,6 +720,73 @@ static void block_coloring(const ocsr *a, const int64_t *bstart, const int32_t *
   *ncolor = c;
   free(blk); free(w); free(win);
   csr_free(&at);
+}
+
+/* ILU(1) of A for the global smoother (the paper's processor-local ILU(1),
+ * Sec. 6).  Pattern: level-1 fill, pattern(A) + pattern(L_A U_A) with L_A,
+ * U_A the strictly lower / upper parts of A (entries (i,j) reached through
+ * one k < min(i,j) with a_ik, a_kj in A).  Factors by incomplete row-wise
+ * (IKJ) elimination on that pattern: for each row i, for k over its lower
+ * entries in ascending order, l_ik = w_ik / u_kk and w_ij -= l_ik u_kj for
+ * every j > k that is in both row k and row i; L is unit lower (l_ij, i > j),
+ * U upper (u_ij, i <= j), both stored on the pattern. */
+static int ilu1_setup(const ocsr *a, ocsr *f) {
+  int64_t n = a->nr;
+  ocsr lo, up, lu;
+  csr_init(&lo, n, n, a->nnz);
+  csr_init(&up, n, n, a->nnz);
+  int64_t nl = 0, nu = 0;
+  for (int64_t i = 0; i < n; i++) {
+    for (int64_t q = a->rp[i]; q < a->rp[i + 1]; q++) {
+      if (a->ci[q] < i) { lo.ci[nl] = a->ci[q]; lo.v[nl] = 1.0; nl++; }
+      else if (a->ci[q] > i) { up.ci[nu] = a->ci[q]; up.v[nu] = 1.0; nu++; }
+    }
+    lo.rp[i + 1] = nl; up.rp[i + 1] = nu;
+  }
+  lo.nnz = nl; up.nnz = nu;
+  csr_matmul(&lo, &up, &lu);
+  /* pattern = A union L_A U_A; values: a_ij or 0 */
+  csr_init(f, n, n, a->nnz + lu.nnz);
+  int64_t np = 0;
+  for (int64_t i = 0; i < n; i++) {
+    int64_t p = a->rp[i], pe = a->rp[i + 1], q = lu.rp[i], qe = lu.rp[i + 1];
+    while (p < pe || q < qe) {
+      int64_t cp = (p < pe) ? a->ci[p] : INT64_MAX, cq = (q < qe) ? lu.ci[q] : INT64_MAX;
+      if (cp <= cq) { f->ci[np] = (int32_t)cp; f->v[np] = a->v[p]; p++; if (cp == cq) q++; }
+      else { f->ci[np] = (int32_t)cq; f->v[np] = 0.0; q++; }
+      np++;
+    }
+    f->rp[i + 1] = np;
+  }
+  f->nnz = np;
+  csr_free(&lo); csr_free(&up); csr_free(&lu);
+  int64_t *dpos = xcalloc((size_t)n, sizeof(int64_t));
+  for (int64_t i = 0; i < n; i++) {
+    int64_t r = f->rp[i];
+    while (r < f->rp[i + 1] && f->ci[r] != i) r++;
+    if (r == f->rp[i + 1]) { free(dpos); return ORC_ERR_ZERO_DIAG; }
+    dpos[i] = r;
+  }
+  for (int64_t i = 0; i < n; i++) {
+    for (int64_t q = f->rp[i]; q < f->rp[i + 1] && f->ci[q] < i; q++) {
+      int64_t k = f->ci[q];
+      double ukk = f->v[dpos[k]];
+      if (ukk == 0.0) { free(dpos); return ORC_ERR_ZERO_DIAG; }
+      double lik = f->v[q] / ukk;
+      f->v[q] = lik;
+      /* w_ij -= l_ik u_kj for j > k in both rows (merge of ascending columns) */
+      int64_t pi = q + 1, pk = dpos[k] + 1;
+      while (pi < f->rp[i + 1] && pk < f->rp[k + 1]) {
+        int64_t ji = f->ci[pi], jk = f->ci[pk];
+        if (ji == jk) { f->v[pi] = f->v[pi] - lik * f->v[pk]; pi++; pk++; }
+        else if (ji < jk) pi++;
+        else pk++;
+      }
+    }
+    if (f->v[dpos[i]] == 0.0) { free(dpos); return ORC_ERR_ZERO_DIAG; }
+  }
+  free(dpos);
+  return ORC_OK;
 }
 
 /* One reduction level: C/F split from the labels; D_FF = diag(A_FF);
@@ -913,7 +985,9 @@ static int mgr_level_setup(oracle_t *h, int l, ocsr *Snext) {
           blk[r * b + c] = csr_get(&L->A, L->bstart[bk] + r, L->bstart[bk] + c);
       st = small_inverse(blk, &L->binv[bk * 16], b);
     }
-    if (st == ORC_OK && o->global_smoother[l]) {
+    if (st == ORC_OK && o->global_smoother[l] == 2)
+      st = ilu1_setup(&L->A, &L->ilu);
+    if (st == ORC_OK && o->global_smoother[l] == 1) {
       L->bcolor = xcalloc((size_t)nb + 1, sizeof(int32_t));
       block_coloring(&L->A, L->bstart, L->bsize, nb, o->seed, l, L->bcolor, &L->ncolor);
     }
@@ -933,6 +1007,44 @@ static void global_relax(const mgr_level *L, const orc_opts *o, int l, const dou
                          double *r) {
   int64_t n = L->A.nr;
   for (int64_t i = 0; i < n; i++) z[i] = 0.0;
+  if (o->global_smoother[l] == 2) {
+    /* ILU(1): z <- z + U^-1 L^-1 (v - A z), each triangular system solved by
+     * `ilu_solve_sweeps` Jacobi iterations from y = r and w = D_U^-1 y:
+     *   y <- r - (L - I) y;   w <- D_U^-1 (y - (U - D_U) w) */
+    const ocsr *F = &L->ilu;
+    double *y = xcalloc((size_t)n + 1, sizeof(double));
+    double *y2 = xcalloc((size_t)n + 1, sizeof(double));
+    double *w = xcalloc((size_t)n + 1, sizeof(double));
+    double *w2 = xcalloc((size_t)n + 1, sizeof(double));
+    double *du = xcalloc((size_t)n + 1, sizeof(double));
+    for (int64_t i = 0; i < n; i++) du[i] = csr_get(F, i, i);
+    for (int sw = 0; sw < o->global_sweeps[l]; sw++) {
+      residual(&L->A, v, z, r);
+      for (int64_t i = 0; i < n; i++) y[i] = r[i];
+      for (int it = 0; it < o->ilu_solve_sweeps; it++) {
+        for (int64_t i = 0; i < n; i++) {
+          double acc = 0.0;
+          for (int64_t q = F->rp[i]; q < F->rp[i + 1]; q++)
+            if (F->ci[q] < i) acc += F->v[q] * y[F->ci[q]];
+          y2[i] = r[i] - acc;
+        }
+        memcpy(y, y2, sizeof(double) * (size_t)n);
+      }
+      for (int64_t i = 0; i < n; i++) w[i] = y[i] / du[i];
+      for (int it = 0; it < o->ilu_solve_sweeps; it++) {
+        for (int64_t i = 0; i < n; i++) {
+          double acc = 0.0;
+          for (int64_t q = F->rp[i]; q < F->rp[i + 1]; q++)
+            if (F->ci[q] > i) acc += F->v[q] * w[F->ci[q]];
+          w2[i] = (y[i] - acc) / du[i];
+        }
+        memcpy(w, w2, sizeof(double) * (size_t)n);
+      }
+      for (int64_t i = 0; i < n; i++) z[i] += w[i];
+    }
+    free(y); free(y2); free(w); free(w2); free(du);
+    return;
+  }
   /* global relaxation: z = M_glo^-1 v, sweeps from zero of multicolour block
    * Gauss-Seidel (colours in ascending order, each block updated from the
    * latest z) or of block Jacobi */
@@ -1204,6 +1316,7 @@ enum {
   Q_MGR_S = 4,      /* next level operator S_{l+1}             */
   Q_MGR_WR = 5,     /* W_r of level l (nC x nF; Jacobi restriction) */
   Q_MGR_BD = 6,     /* point-block D_FF^-1 of level l (nF x nF) */
+  Q_MGR_ILU = 7,    /* ILU(1) factors of level l (L strict + U, one pattern) */
   Q_AMG_A = 10,     /* AMG slot s, level k operator            */
   Q_AMG_S = 11,     /* strength pattern                        */
   Q_AMG_P = 12,     /* interpolation                           */
@@ -1222,6 +1335,7 @@ static const ocsr *orc_csr_ptr(oracle_t *h, int kind, int slot, int lvl) {
       case Q_MGR_S: return (slot + 1 < h->L) ? &h->lev[slot + 1].A : &h->Acoarse;
       case Q_MGR_WR: return L->Wr.rp ? &L->Wr : NULL;
       case Q_MGR_BD: return L->Bd.rp ? &L->Bd : NULL;
+      case Q_MGR_ILU: return L->ilu.rp ? &L->ilu : NULL;
     }
     return NULL;
   }

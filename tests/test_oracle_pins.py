@@ -578,3 +578,78 @@ def test_aggressive_level_truncation_and_hierarchy():
     assert agg.amg_levels(2) == base.amg_levels(2)             # other AMGs untouched
     r = agg.fgmres(p.rhs)
     assert r["status"] == 0 and r["relres"] <= 1e-8
+
+
+# ---------------------------------------------------------------------------
+# ILU(1) global smoother
+# ---------------------------------------------------------------------------
+def _ilu_parts(o, l):
+    F = o.scipy(oracle.Q_MGR_ILU, l)
+    Fd = F.toarray()
+    n = Fd.shape[0]
+    return F, np.tril(Fd, -1) + np.eye(n), np.triu(Fd)
+
+
+def test_ilu1_pattern_and_defining_property():
+    # ILU on a pattern P: (L U)_ij = a_ij for every (i, j) in P, and P for
+    # level 1 is pattern(A) + pattern(L_A U_A) (strict triangles of A).
+    import scipy.sparse as sp
+    p = synth.two_phase(5, 4, 3, seed=7)
+    o = oracle.Oracle(p, global_smoother=[0, 2])
+    S = o.scipy(oracle.Q_MGR_A, 1)
+    F, L, U = _ilu_parts(o, 1)
+    pat_a = (abs(S) > 0).astype(np.int8)
+    lo = sp.tril(pat_a, -1, format="csr")
+    up = sp.triu(pat_a, 1, format="csr")
+    want = ((pat_a + (lo @ up)) > 0).astype(np.int8).tocsr()
+    want.sort_indices()
+    got = sp.csr_matrix((np.ones(F.nnz), F.indices, F.indptr), shape=F.shape)
+    assert np.array_equal(got.indptr, want.indptr) and np.array_equal(got.indices, want.indices)
+    LU = L @ U
+    mask = want.toarray() > 0
+    Sd = S.toarray()
+    assert np.abs((LU - Sd)[mask]).max() <= 1e-13 * np.abs(Sd).max()
+    assert np.abs((LU - Sd)[~mask]).max() > 1e-8 * np.abs(Sd).max()   # incomplete
+
+
+def test_ilu1_without_fill_is_the_exact_lu():
+    # When pattern(L_A U_A) adds nothing to pattern(A), elimination creates
+    # no fill at any level, so ILU(1) is the exact LU factorization.  The
+    # level-1 operator of a single column of cells (1 x 1 x nz) is banded
+    # and has that property.
+    p = synth.two_phase(1, 1, 12, seed=1)
+    o = oracle.Oracle(p, global_smoother=[0, 2])
+    S = o.scipy(oracle.Q_MGR_A, 1)
+    F, L, U = _ilu_parts(o, 1)
+    assert F.nnz == (abs(S) > 0).sum()
+    Sd = S.toarray()
+    assert np.abs(L @ U - Sd).max() <= 1e-12 * np.abs(Sd).max()
+    assert np.abs(np.linalg.solve(L @ U, np.ones(len(Sd))) -
+                  np.linalg.solve(Sd, np.ones(len(Sd)))).max() < 1e-9
+
+
+@pytest.mark.parametrize("solve_sweeps", [3, 400])
+def test_ilu1_smoother_sweep(solve_sweeps):
+    # One smoother sweep from zero: z = w with L y = v, U w = y solved by
+    # Jacobi iterations y <- v - (L - I) y, w <- D_U^-1 (y - (U - D_U) w),
+    # starting from y = v, w = D_U^-1 y; with enough iterations the solves are
+    # exact and z = (L U)^-1 v.
+    p = synth.two_phase(4, 3, 3, seed=2)
+    o = oracle.Oracle(p, global_smoother=[0, 2], global_sweeps=[0, 1],
+                      ilu_solve_sweeps=solve_sweeps)
+    F, L, U = _ilu_parts(o, 1)
+    n = L.shape[0]
+    v = np.random.default_rng(1).standard_normal(n)
+    got = o.global_relax(1, v)
+    if solve_sweeps >= n:
+        want = np.linalg.solve(L @ U, v)
+    else:
+        Ls, D, Us = L - np.eye(n), np.diag(np.diag(U)), U - np.diag(np.diag(U))
+        y = v.copy()
+        for _ in range(solve_sweeps):
+            y = v - Ls @ y
+        w = np.linalg.solve(D, y)
+        for _ in range(solve_sweeps):
+            w = np.linalg.solve(D, y - Us @ w)
+        want = w
+    assert np.abs(got - want).max() <= 1e-10 * np.abs(want).max()
