@@ -428,13 +428,16 @@ def run_ours(args):
         del Al, bl, xl
 
     # operator and smoother variants (Sec. 5.1 options, multicolour block
-    # Gauss-Seidel): the same FP64 step on the same workload
+    # Gauss-Seidel, one sweep of ILU(1) as the level-2 global smoother as in
+    # Sec. 6): the same FP64 step on the same workload
     variants = {}
     for vname, vkw in (("jacobi_restriction", dict(restrict_jacobi=[1, 1])),
                        ("mgr_post", dict(frelax_post=[1, 1])),
                        ("point_block_dff", dict(dff_block=[1, 1])),
                        ("block_gauss_seidel", dict(global_smoother=[0, 1])),
-                       ("aggressive_uu_amg", dict(agg_levels=[1, 0, 0]))):
+                       ("aggressive_uu_amg", dict(agg_levels=[1, 0, 0])),
+                       ("ilu1_smoother", dict(global_smoother=[0, 2], global_sweeps=[0, 1],
+                                              ilu_solve_sweeps=3))):
         vo = mgr.mgr_options_default(True, **vkw)
 
         def vstep():

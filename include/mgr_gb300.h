@@ -125,7 +125,13 @@ typedef struct {
    * coloured by Jones-Plassmann rounds on the block graph of A + A^T
    * (weights splitmix64(seed ^ 0xC0 << 56 ^ level << 40 ^ block), ties to
    * the smaller block), each sweep visiting the colours in ascending order
-   * and updating every block of a colour from the latest z. */
+   * and updating every block of a colour from the latest z;
+   * 2 pointwise ILU(1) (Sec. 6 uses one sweep of it as the level-2 global
+   *   smoother): the exact incomplete factors L U on the level-1 fill pattern
+   *   pattern(A) + pattern(L_A U_A) ((L U)_ij = a_ij there), each sweep
+   *   z <- z + U^-1 L^-1 (v - A z) with both triangular systems solved by
+   *   ilu_solve_sweeps Jacobi iterations (y <- r - (L - I) y from y = r;
+   *   w <- D_U^-1 (y - (U - D_U) w) from w = D_U^-1 y). */
   int32_t global_smoother[MGR_MAX_LEVELS];
   /* Aggressive coarsening (Sec. 6 names one level of it for A_uu): the first
    * agg_levels[s] levels of AMG slot s (slot l < num_levels: the F-relaxation
@@ -134,6 +140,9 @@ typedef struct {
    * (PMIS weights keyed by level 32 + k), P = P1 P2 truncated to amg_pmax by
    * the direct interpolation's rule.  0 in the defaults. */
   int32_t agg_levels[MGR_MAX_LEVELS];
+  /* Jacobi iterations per triangular solve of the ILU(1) global smoother
+   * (0..1000; default 3). */
+  int32_t ilu_solve_sweeps;
 } mgr_options_t;
 
 typedef struct {
@@ -203,6 +212,8 @@ const char* mgr_error_string(int code);
  *   4 the next-level operator S_{slot+1};
  *   5 W_r of level slot (nC x nF; only with restrict_jacobi);
  *   6 D_FF^-1 of level slot as a sparse matrix (nF x nF; only with dff_block);
+ *   7 the ILU(1) factors of level slot on one pattern: strict lower part of L
+ *     (unit diagonal implied) and U (only with global_smoother 2);
  *   10 AMG operator, 11 strength pattern, 12 interpolation P, 13 R = P^T of
  *   AMG slot `slot` (0..L-1: F-relaxation AMG of MGR level slot; L: the AMG
  *   of the coarsest MGR level), level `lvl`.

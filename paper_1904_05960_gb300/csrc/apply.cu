@@ -34,9 +34,12 @@ __device__ __forceinline__ T ldg(const T* p) {
 //                                          x = b, gathers dinv too)
 //   MODE_PROL0  y = dinv .* b + A x       (prolongation onto that first sweep;
 //                                          b, dinv are the fine-level vectors)
+//   MODE_DRES   y = dinv .* (b - A x)     (Jacobi iteration of a triangular system)
+//   MODE_DRES0  y = dinv .* (b - A (dinv .* b))   (its first iteration from
+//                                          x = dinv .* b; x = b, gathers dinv)
 // ----------------------------------------------------------------------------
 enum { MODE_AX = 0, MODE_RES = 1, MODE_SMOOTH = 2, MODE_ADD = 3, MODE_GRES = 4, MODE_RROWS = 5,
-       MODE_RES0 = 6, MODE_PROL0 = 7 };
+       MODE_RES0 = 6, MODE_PROL0 = 7, MODE_DRES = 8, MODE_DRES0 = 9 };
 
 // Lanes of a G-lane group inside its warp (G divides 32; groups are aligned).
 template <int G>
@@ -60,7 +63,7 @@ k_spmv(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci, const T* 
     const I e0 = (I)rp[row], e1 = (I)rp[row + 1];
     Y a0 = 0, a1 = 0;
     I k = e0 + lane;
-    if (MODE == MODE_RES0) {
+    if (MODE == MODE_RES0 || MODE == MODE_DRES0) {
       for (; k + G < e1; k += 2 * G) {
         const int32_t c0 = ci[k], c1 = ci[k + G];
         a0 += (Y)val[k] * ((Y)ldg(dinv + c0) * (Y)ldg(x + c0));
@@ -89,6 +92,7 @@ k_spmv(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci, const T* 
       else if (MODE == MODE_RROWS) y[i] = b[row] - acc;
       else if (MODE == MODE_RES0) y[i] = b[i] - acc;
       else if (MODE == MODE_PROL0) y[i] = (Y)dinv[i] * b[i] + acc;
+      else if (MODE == MODE_DRES || MODE == MODE_DRES0) y[i] = (Y)dinv[i] * (b[i] - acc);
     }
   }
 }
@@ -187,6 +191,12 @@ template <class T>
 __global__ void k_scale(const T* __restrict__ d, const T* __restrict__ b, T* __restrict__ x, int64_t n) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     x[i] = d[i] * b[i];
+}
+
+template <class T>
+__global__ void k_add(T* __restrict__ z, const T* __restrict__ e, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    z[i] += e[i];
 }
 
 template <class T>
@@ -375,6 +385,11 @@ static int alloc_ws(Handle* h) {
     L.eF = P.get<T>(L.nF);
     L.rC = P.get<T>(L.nC);
     L.eC = P.get<T>(L.nC);
+    if (L.ilu1) {
+      L.y1 = P.get<T>(L.n);
+      L.y2 = P.get<T>(L.n);
+      L.y3 = P.get<T>(L.n);
+    }
     MGR_TRY(alloc_amg_ws<T>(P, L.famg));
   }
   MGR_TRY(alloc_amg_ws<T>(P, h->camg));
@@ -469,7 +484,42 @@ static void mgr_level(Handle* h, int l, const T* v, T* z, cudaStream_t s) {
     const unsigned bgrid = (unsigned)((L.nblk + BJ_BLOCKS - 1) / BJ_BLOCKS);
     const int G = pick_group(L.A.nnz, L.A.nr);
     bool first = true;
-    if (L.gs) {
+    if (L.ilu1) {
+      // ILU(1) sweeps from zero: r = v - A z; y = L^-1 r and w = U^-1 y by
+      // Jacobi iterations; z += w.  The last iteration writes z itself in
+      // the first sweep.
+      const T* di = pick<T>(L.ilu_dinv, L.ilu_dinvf);
+      const int it = L.ilu_solve_sweeps;
+      T* ya = (T*)L.y1;
+      T* yb = (T*)L.y2;
+      T* wb = (T*)L.y3;
+      T* z2 = (T*)L.z2;
+      for (int sw = 0; sw < L.global_sweeps; sw++) {
+        const T* rr = v;
+        if (sw > 0) {
+          spmv<T, MODE_RES>(L.A, z, wb, v, nullptr, nullptr, s);
+          rr = wb;
+        }
+        const T* y = rr;
+        for (int t = 1; t <= it; t++) {
+          T* yo = (t % 2) ? ya : yb;
+          spmv<T, MODE_RES>(L.Ilo, y, yo, rr, nullptr, nullptr, s);
+          y = yo;
+        }
+        T* last = (sw == 0) ? z : (it == 0 ? z2 : wb);   // never the buffer y is in
+        if (it == 0) {
+          MGR_LAUNCH k_scale<T><<<vgrid(n), 256, 0, s>>>(di, y, last, n);
+        }
+        const T* w = nullptr;
+        for (int t = 1; t <= it; t++) {
+          T* wo = ((it - t) % 2 == 0) ? last : z2;
+          if (t == 1) spmv<T, MODE_DRES0>(L.Iup, y, wo, y, di, nullptr, s);
+          else spmv<T, MODE_DRES>(L.Iup, w, wo, y, di, nullptr, s);
+          w = wo;
+        }
+        if (sw > 0) MGR_LAUNCH k_add<T><<<vgrid(n), 256, 0, s>>>(z, last, n);
+      }
+    } else if (L.gs) {
       // multicolour Gauss-Seidel sweeps from zero, in place on z
       cudaMemsetAsync(z, 0, sizeof(T) * n, s);
       for (int sw = 0; sw < L.global_sweeps; sw++)
@@ -481,7 +531,7 @@ static void mgr_level(Handle* h, int l, const T* v, T* z, cudaStream_t s) {
                                                       L.border + L.coff[c], cnt, v, z);
         }
     }
-    for (int sw = 0; sw < (L.gs ? 0 : L.global_sweeps); sw++, first = false) {
+    for (int sw = 0; sw < ((L.gs || L.ilu1) ? 0 : L.global_sweeps); sw++, first = false) {
       const T* zi = first ? nullptr : buf[(sw - 1) % 2];
       T* zo = buf[sw % 2];
 #define MGR_BJ_CASE(g)                                                                           \

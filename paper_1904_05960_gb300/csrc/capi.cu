@@ -50,6 +50,7 @@ static const Csr* find_csr(Handle* h, int kind, int slot, int lvl) {
       case 4: return (slot + 1 < h->L) ? &h->lev[slot + 1].A : &h->Acoarse;
       case 5: return L.Wr.rp ? &L.Wr : nullptr;
       case 6: return L.Bd.rp ? &L.Bd : nullptr;
+      case 7: return L.ilu.rp ? &L.ilu : nullptr;
     }
     return nullptr;
   }
@@ -97,6 +98,7 @@ void mgr_options_default(mgr_options_t* o, int two_phase) {
   o->amg_max_levels = 25;
   o->precision = MGR_FP64;
   o->seed = 0;
+  o->ilu_solve_sweeps = 3;
 }
 
 void fgmres_options_default(fgmres_options_t* o) {
@@ -142,6 +144,9 @@ int setup_one(const mgr_matrix_t* A, const mgr_options_t* o, cudaStream_t s, Han
       o->amg_pmax < 0 || (o->precision != MGR_FP64 && o->precision != MGR_MIXED))
     return MGR_ERR_INVALID_ARG;
   if (A->n > INT32_MAX) return MGR_ERR_INVALID_ARG;
+  for (int l = 0; l < MGR_MAX_LEVELS; l++)
+    if (o->global_smoother[l] < 0 || o->global_smoother[l] > 2) return MGR_ERR_INVALID_ARG;
+  if (o->ilu_solve_sweeps < 0 || o->ilu_solve_sweeps > 1000) return MGR_ERR_INVALID_ARG;
   Handle* h = new (std::nothrow) Handle();
   if (!h) return MGR_ERR_OOM;
   h->opt = *o;

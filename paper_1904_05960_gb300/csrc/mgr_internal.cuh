@@ -143,6 +143,14 @@ struct MgrLevel {
   std::vector<int64_t> coff;     // colour c's blocks: border[coff[c] .. coff[c+1])
   double* binv = nullptr;        // 16 values per block, row-major b x b
   float* binvf = nullptr;
+  // ILU(1) global smoother: the factors on one pattern (ilu: strict L with
+  // unit diagonal implied, plus U), split for the triangular iterations
+  bool ilu1 = false;
+  int ilu_solve_sweeps = 0;
+  Csr ilu, Ilo, Iup;
+  double* ilu_dinv = nullptr;    // 1 / u_ii
+  float* ilu_dinvf = nullptr;
+  void *y1 = nullptr, *y2 = nullptr, *y3 = nullptr;   // apply workspace (n each)
   // apply workspace (precision of the handle), sized n / nF / nC
   void *z = nullptr, *z2 = nullptr, *r = nullptr, *rF = nullptr, *eF = nullptr,
        *rC = nullptr, *eC = nullptr;

@@ -447,9 +447,11 @@ k_spgemm_numeric_grp(const int64_t* __restrict__ arp, const int32_t* __restrict_
   }
 }
 
-static int spgemm(Pool& P, Pool& tmp, const Csr& A, const Csr& B, Csr& C, cudaStream_t s) {
+// Pattern of C = A * B (C.v stays null; A.v and B.v are not read).
+static int spgemm_pattern(Pool& P, Pool& tmp, const Csr& A, const Csr& B, Csr& C, cudaStream_t s) {
   C.nr = A.nr;
   C.nc = B.nc;
+  C.v = nullptr;
   C.rp = P.get<int64_t>(A.nr + 1);
   int64_t* cnt = tmp.get<int64_t>(A.nr + 1);
   if (P.err || tmp.err) return P.err ? P.err : tmp.err;
@@ -467,9 +469,16 @@ static int spgemm(Pool& P, Pool& tmp, const Csr& A, const Csr& B, Csr& C, cudaSt
   MGR_LAUNCH k_spgemm_symbolic<false><<<g, SPG_WARPS * 32, sm, s>>>(A.rp, A.ci, A.nr, B.rp, B.ci, cnt, nullptr);
   MGR_TRY(rowptr_from_counts(cnt, C.rp, A.nr, &C.nnz, s, tmp));
   C.ci = P.get<int32_t>(C.nnz);
-  C.v = P.get<double>(C.nnz);
   if (P.err) return P.err;
   MGR_LAUNCH k_spgemm_symbolic<true><<<g, SPG_WARPS * 32, sm, s>>>(A.rp, A.ci, A.nr, B.rp, B.ci, C.rp, C.ci);
+  MGR_TRY_CUDA(cudaGetLastError());
+  return MGR_SUCCESS;
+}
+
+static int spgemm(Pool& P, Pool& tmp, const Csr& A, const Csr& B, Csr& C, cudaStream_t s) {
+  MGR_TRY(spgemm_pattern(P, tmp, A, B, C, s));
+  C.v = P.get<double>(C.nnz);
+  if (P.err) return P.err;
   if (B.nr > 0 && B.nnz < 12 * B.nr)
     MGR_LAUNCH k_spgemm_numeric_grp<<<grid_for(A.nr, GRP_WARPS, 152 * 32), GRP_WARPS * 32, 0, s>>>(
         A.rp, A.ci, A.v, A.nr, B.rp, B.ci, B.v, C.rp, C.ci, C.v);
@@ -2015,6 +2024,251 @@ struct SideBuild {
   }
 };
 
+// ============================================================================
+// ILU(1) global smoother (Sec. 6: one sweep of pointwise ILU(1) is the global
+// smoother of the second reduction level).  The pattern is level-1 fill:
+// pattern(A) + pattern(L_A U_A) with L_A, U_A the strict triangles of A.  The
+// factors are the exact incomplete factors on that pattern (the fixed point of
+// the fine-grained iteration the paper cites), computed by IKJ elimination:
+// rows are grouped by dependency depth and each group is eliminated in one
+// launch, every row by one warp in ascending k, so each entry receives the
+// same sequence of roundings as sequential elimination.
+// ============================================================================
+// Strict lower (LOWER) or strict upper triangle of a CSR matrix; values are
+// copied when ov is non-null.  Thread per row.
+template <bool FILL, bool LOWER>
+__global__ void k_tri(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                      const double* __restrict__ v, int64_t n, int64_t* __restrict__ cnt_or_rp,
+                      int32_t* __restrict__ oci, double* __restrict__ ov) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int64_t o = FILL ? cnt_or_rp[i] : 0;
+  for (int64_t q = rp[i]; q < rp[i + 1]; q++) {
+    const int64_t c = ci[q];
+    if (LOWER ? (c < i) : (c > i)) {
+      if (FILL) {
+        oci[o] = (int32_t)c;
+        if (ov) ov[o] = v[q];
+      }
+      o++;
+    }
+  }
+  if (!FILL) cnt_or_rp[i] = o;
+}
+
+static int tri_part(Pool& P, Pool& tmp, const Csr& A, bool lower, bool values, Csr& T,
+                    cudaStream_t s) {
+  int64_t* cnt = tmp.get<int64_t>(A.nr + 1);
+  T.nr = A.nr;
+  T.nc = A.nc;
+  T.rp = P.get<int64_t>(A.nr + 1);
+  if (tmp.err || P.err) return tmp.err ? tmp.err : P.err;
+  const unsigned g = nblocks(A.nr, 256);
+  if (lower) MGR_LAUNCH k_tri<false, true><<<g, 256, 0, s>>>(A.rp, A.ci, nullptr, A.nr, cnt, nullptr, nullptr);
+  else MGR_LAUNCH k_tri<false, false><<<g, 256, 0, s>>>(A.rp, A.ci, nullptr, A.nr, cnt, nullptr, nullptr);
+  MGR_TRY(rowptr_from_counts(cnt, T.rp, A.nr, &T.nnz, s, tmp));
+  T.ci = P.get<int32_t>(T.nnz);
+  T.v = values ? P.get<double>(T.nnz) : nullptr;
+  if (P.err) return P.err;
+  const double* av = values ? A.v : nullptr;
+  if (lower) MGR_LAUNCH k_tri<true, true><<<g, 256, 0, s>>>(A.rp, A.ci, av, A.nr, T.rp, T.ci, T.v);
+  else MGR_LAUNCH k_tri<true, false><<<g, 256, 0, s>>>(A.rp, A.ci, av, A.nr, T.rp, T.ci, T.v);
+  MGR_TRY_CUDA(cudaGetLastError());
+  return MGR_SUCCESS;
+}
+
+// F = pattern(A) + pattern(K) with values a_ij, or +0.0 where A has no entry.
+template <bool FILL>
+__global__ void k_union_fill0(const int64_t* __restrict__ arp, const int32_t* __restrict__ aci,
+                              const double* __restrict__ av, const int64_t* __restrict__ krp,
+                              const int32_t* __restrict__ kci, int64_t nr,
+                              int64_t* __restrict__ cnt_or_rp, int32_t* __restrict__ fci,
+                              double* __restrict__ fv) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nr) return;
+  int64_t p = arp[i], pe = arp[i + 1], q = krp[i], qe = krp[i + 1];
+  int64_t o = FILL ? cnt_or_rp[i] : 0;
+  while (p < pe || q < qe) {
+    const int64_t cp = (p < pe) ? aci[p] : INT64_MAX;
+    const int64_t cq = (q < qe) ? kci[q] : INT64_MAX;
+    if (FILL) {
+      fci[o] = (int32_t)(cp <= cq ? cp : cq);
+      fv[o] = (cp <= cq) ? av[p] : 0.0;
+    }
+    if (cp <= cq) {
+      p++;
+      if (cp == cq) q++;
+    } else {
+      q++;
+    }
+    o++;
+  }
+  if (!FILL) cnt_or_rp[i] = o;
+}
+
+// position of the diagonal entry of each row (a missing one is a zero pivot)
+__global__ void k_diag_pos(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci, int64_t n,
+                           int64_t* __restrict__ dpos, int* err) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int64_t r = rp[i];
+  while (r < rp[i + 1] && ci[r] != i) r++;
+  if (r == rp[i + 1]) {
+    dev_fail(err, DEV_ZERO_DIAG);
+    r = rp[i];
+  }
+  dpos[i] = r;
+}
+
+// One relaxation pass of depth(i) = max over the lower entries k of row i of
+// depth(k) + 1 (0 without lower entries), in place.  Depths only grow and
+// never pass the longest dependency chain, so a pass that changes nothing
+// has reached the unique solution.
+__global__ void k_ilu_depth(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                            const int64_t* __restrict__ dpos, int64_t n, int32_t* depth,
+                            unsigned long long* changed) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int32_t m = 0;
+  for (int64_t q = rp[i]; q < dpos[i]; q++) {
+    const int32_t d = depth[ci[q]] + 1;
+    m = d > m ? d : m;
+  }
+  if (m != depth[i]) {
+    depth[i] = m;
+    atomicAdd(changed, 1ull);
+  }
+}
+
+__global__ void k_imax(const int32_t* __restrict__ a, int64_t n, int* out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) atomicMax(out, a[i]);
+}
+
+// IKJ elimination of the rows of one depth, a warp per row.  Row i takes its
+// lower entries in ascending k: l_ik = w_ik / u_kk, then w_ij -= l_ik u_kj for
+// every column j > k present in both rows (rows k < i are final: they have a
+// smaller depth).  Each lane updates distinct entries of row i.
+__global__ void __launch_bounds__(256)
+k_ilu_rows(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci, double* v,
+           const int64_t* __restrict__ dpos, const int64_t* __restrict__ rows, int64_t cnt,
+           int* err) {
+  const int lane = threadIdx.x & 31;
+  const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (t >= cnt) return;   // whole warps
+  const int64_t i = rows[t];
+  const int64_t r1 = rp[i + 1], di = dpos[i];
+  for (int64_t q = rp[i]; q < di; q++) {
+    const int64_t k = ci[q];
+    const int64_t dk = dpos[k];
+    const double ukk = v[dk];
+    if (ukk == 0.0) {
+      if (lane == 0) dev_fail(err, DEV_ZERO_DIAG);
+      return;
+    }
+    const double lik = __ddiv_rn(v[q], ukk);
+    __syncwarp();
+    if (lane == 0) v[q] = lik;
+    const int64_t k1 = rp[k + 1];
+    for (int64_t pk = dk + 1 + lane; pk < k1; pk += 32) {
+      const int32_t j = ci[pk];
+      int64_t lo = q + 1, hi = r1;   // first position in (q, r1) with column >= j
+      while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (ci[mid] < j) lo = mid + 1;
+        else hi = mid;
+      }
+      if (lo < r1 && ci[lo] == j) v[lo] = __dsub_rn(v[lo], __dmul_rn(lik, v[pk]));
+    }
+    __syncwarp();
+  }
+  if (lane == 0 && v[di] == 0.0) dev_fail(err, DEV_ZERO_DIAG);
+}
+
+__global__ void k_diag_inv(const double* __restrict__ v, const int64_t* __restrict__ dpos, int64_t n,
+                           double* __restrict__ dinv) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dinv[i] = __ddiv_rn(1.0, v[dpos[i]]);
+}
+
+static int ilu1_build(Handle* h, Pool& P, Pool& tmp, MgrLevel& L, cudaStream_t s) {
+  const Csr& A = L.A;
+  const int64_t n = A.nr;
+  // level-1 pattern and the values of A on it
+  Csr lo, up, lu;
+  MGR_TRY(tri_part(tmp, tmp, A, true, false, lo, s));
+  MGR_TRY(tri_part(tmp, tmp, A, false, false, up, s));
+  MGR_TRY(spgemm_pattern(tmp, tmp, lo, up, lu, s));
+  Csr& F = L.ilu;
+  F.nr = F.nc = n;
+  F.rp = P.get<int64_t>(n + 1);
+  int64_t* cnt = tmp.get<int64_t>(n + 1);
+  if (P.err || tmp.err) return P.err ? P.err : tmp.err;
+  const unsigned g = nblocks(n, 256);
+  MGR_LAUNCH k_union_fill0<false><<<g, 256, 0, s>>>(A.rp, A.ci, A.v, lu.rp, lu.ci, n, cnt, nullptr, nullptr);
+  MGR_TRY(rowptr_from_counts(cnt, F.rp, n, &F.nnz, s, tmp));
+  F.ci = P.get<int32_t>(F.nnz);
+  F.v = P.get<double>(F.nnz);
+  int64_t* dpos = tmp.get<int64_t>(n);
+  int32_t* depth = tmp.get<int32_t>(n);
+  if (P.err || tmp.err) return P.err ? P.err : tmp.err;
+  MGR_LAUNCH k_union_fill0<true><<<g, 256, 0, s>>>(A.rp, A.ci, A.v, lu.rp, lu.ci, n, F.rp, F.ci, F.v);
+  MGR_LAUNCH k_diag_pos<<<g, 256, 0, s>>>(F.rp, F.ci, n, dpos, h->derr);
+  MGR_TRY(check_dev_err(h->derr, s));
+  // dependency depths: relaxation passes, four per host check, at most n + 1
+  // passes (the longest chain has at most n rows)
+  static constexpr int PASSES = 4;
+  unsigned long long* chg = tmp.get<unsigned long long>(PASSES);
+  int* dmax = tmp.get<int>(1);
+  if (tmp.err) return tmp.err;
+  MGR_TRY_CUDA(cudaMemsetAsync(depth, 0, sizeof(int32_t) * n, s));
+  bool done = false;
+  for (int64_t p0 = 0; p0 <= n + PASSES && !done; p0 += PASSES) {
+    MGR_TRY_CUDA(cudaMemsetAsync(chg, 0, sizeof(unsigned long long) * PASSES, s));
+    for (int q = 0; q < PASSES; q++)
+      MGR_LAUNCH k_ilu_depth<<<g, 256, 0, s>>>(F.rp, F.ci, dpos, n, depth, chg + q);
+    unsigned long long hc[PASSES];
+    MGR_TRY_CUDA(cudaMemcpyAsync(hc, chg, sizeof(hc), cudaMemcpyDeviceToHost, s));
+    MGR_TRY_CUDA(cudaStreamSynchronize(s));
+    for (int q = 0; q < PASSES; q++) done = done || hc[q] == 0;
+  }
+  if (!done) return MGR_ERR_CUDA;   // cannot happen: depths are bounded by n
+  MGR_TRY_CUDA(cudaMemsetAsync(dmax, 0, sizeof(int), s));
+  MGR_LAUNCH k_imax<<<g, 256, 0, s>>>(depth, n, dmax);
+  int nd = 0;
+  MGR_TRY(read_back(&nd, dmax, s));
+  nd += 1;
+  // rows grouped by depth
+  int64_t* dcnt = tmp.get<int64_t>(nd + 1);
+  int64_t* order = tmp.get<int64_t>(n);
+  if (tmp.err) return tmp.err;
+  MGR_TRY_CUDA(cudaMemsetAsync(dcnt, 0, sizeof(int64_t) * (nd + 1), s));
+  MGR_LAUNCH k_color_count<<<g, 256, 0, s>>>(depth, n, dcnt);
+  std::vector<int64_t> hcnt(nd), off(nd + 1, 0);
+  MGR_TRY_CUDA(cudaMemcpyAsync(hcnt.data(), dcnt, sizeof(int64_t) * nd, cudaMemcpyDeviceToHost, s));
+  MGR_TRY_CUDA(cudaStreamSynchronize(s));
+  for (int d = 0; d < nd; d++) off[d + 1] = off[d] + hcnt[d];
+  MGR_TRY_CUDA(cudaMemcpyAsync(dcnt, off.data(), sizeof(int64_t) * nd, cudaMemcpyHostToDevice, s));
+  MGR_LAUNCH k_color_place<<<g, 256, 0, s>>>(depth, n, dcnt, order);
+  // elimination, one launch per depth
+  for (int d = 0; d < nd; d++) {
+    const int64_t c = off[d + 1] - off[d];
+    if (c == 0) continue;
+    MGR_LAUNCH k_ilu_rows<<<nblocks(c * 32, 256), 256, 0, s>>>(F.rp, F.ci, F.v, dpos, order + off[d], c,
+                                                                h->derr);
+  }
+  MGR_TRY(check_dev_err(h->derr, s));
+  // split for the triangular iterations
+  MGR_TRY(tri_part(P, tmp, F, true, true, L.Ilo, s));
+  MGR_TRY(tri_part(P, tmp, F, false, true, L.Iup, s));
+  L.ilu_dinv = P.get<double>(n);
+  if (P.err) return P.err;
+  MGR_LAUNCH k_diag_inv<<<g, 256, 0, s>>>(F.v, dpos, n, L.ilu_dinv);
+  MGR_TRY_CUDA(cudaGetLastError());
+  L.ilu1 = true;
+  return MGR_SUCCESS;
+}
+
 // s is the calling thread's stream; it changes (to the main thread's
 // high-priority stream) when this level hands its F-relaxation AMG to the
 // side build.
@@ -2242,7 +2496,11 @@ static int setup_level(Handle* h, int l, const int32_t* label, const int32_t* no
     MGR_LAUNCH k_block_inv<<<nblocks(L.nblk, 128), 128, 0, s>>>(L.A.rp, L.A.ci, L.A.v, L.bstart, L.nblk,
                                                       L.binv, h->derr);
     MGR_TRY(check_dev_err(h->derr, s));
-    if (o.global_smoother[l]) {
+    if (o.global_smoother[l] == 2) {
+      L.ilu_solve_sweeps = o.ilu_solve_sweeps;
+      MGR_TRY(ilu1_build(h, P, tmp, L, s));
+      g_trace.mark("mgr ILU(1)", l);
+    } else if (o.global_smoother[l] == 1) {
       // multicolour point-block Gauss-Seidel: colour the block graph, then
       // group the blocks by colour
       L.gs = true;
@@ -2397,6 +2655,11 @@ int to_fp32(Handle* h, cudaStream_t s) {
     MGR_TRY(f32(P, L.binv, &L.binvf, 16 * L.nblk, s));
     if (L.Wr.v) MGR_TRY(f32(P, L.Wr.v, &L.Wr.vf, L.Wr.nnz, s));
     if (L.Bd.v) MGR_TRY(f32(P, L.Bd.v, &L.Bd.vf, L.Bd.nnz, s));
+    if (L.ilu1) {
+      MGR_TRY(f32(P, L.Ilo.v, &L.Ilo.vf, L.Ilo.nnz, s));
+      MGR_TRY(f32(P, L.Iup.v, &L.Iup.vf, L.Iup.nnz, s));
+      MGR_TRY(f32(P, L.ilu_dinv, &L.ilu_dinvf, L.n, s));
+    }
     MGR_TRY(amg_to_fp32(h, L.famg, s));
   }
   MGR_TRY(amg_to_fp32(h, h->camg, s));

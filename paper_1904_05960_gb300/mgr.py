@@ -21,7 +21,7 @@ MGR_FRELAX_AMG_VCYCLE, MGR_FRELAX_JACOBI = 0, 1
 MGR_FP64, MGR_MIXED = 0, 1
 
 # hierarchy inspection kinds (mgr_get_csr)
-Q_MGR_A, Q_MGR_W, Q_MGR_COR, Q_MGR_CORKEPT, Q_MGR_S, Q_MGR_WR, Q_MGR_BD = 0, 1, 2, 3, 4, 5, 6
+Q_MGR_A, Q_MGR_W, Q_MGR_COR, Q_MGR_CORKEPT, Q_MGR_S, Q_MGR_WR, Q_MGR_BD, Q_MGR_ILU = 0, 1, 2, 3, 4, 5, 6, 7
 Q_AMG_A, Q_AMG_S, Q_AMG_P, Q_AMG_R = 10, 11, 12, 13
 
 EXPORTED = ["mgr_options_default", "fgmres_options_default", "mgr_setup", "mgr_apply",
@@ -52,7 +52,8 @@ class MgrOptions(C.Structure):
                 ("frelax_post", C.c_int32 * MGR_MAX_LEVELS),
                 ("dff_block", C.c_int32 * MGR_MAX_LEVELS),
                 ("global_smoother", C.c_int32 * MGR_MAX_LEVELS),
-                ("agg_levels", C.c_int32 * MGR_MAX_LEVELS)]
+                ("agg_levels", C.c_int32 * MGR_MAX_LEVELS),
+                ("ilu_solve_sweeps", C.c_int32)]
 
 
 class FgmresOptions(C.Structure):

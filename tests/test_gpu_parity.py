@@ -339,3 +339,37 @@ def test_aggressive_coarsening_matches_oracle(precision):
     assert abs(r["iters"] - ref["iters"]) <= 2, (r["iters"], ref["iters"])
     assert _rel(r["x"].cpu().numpy(), ref["x"]) <= 1e-6
     s.close()
+
+
+@pytest.mark.parametrize("precision", [mgr.MGR_FP64, mgr.MGR_MIXED])
+@pytest.mark.parametrize("level,sweeps,solve", [(1, 1, 3), (1, 2, 1), (1, 1, 0), (0, 1, 2)],
+                         ids=["l1-s1-j3", "l1-s2-j1", "l1-s1-j0", "l0-s1-j2"])
+def test_ilu1_smoother_matches_oracle(precision, level, sweeps, solve):
+    """Global smoother option 2 (pointwise ILU(1), Sec. 6): the incomplete
+    factors on the level-1 fill pattern as the oracle's (pattern bit-exact,
+    values to 1e-12), the smoother's application and FGMRES as the
+    oracle's."""
+    p = synth.two_phase(13, 11, 7, seed=3, sigma=1.5)
+    gsm, gsw = [0, 0], [0, 0]
+    gsm[level], gsw[level] = 2, sweeps
+    if level == 0:
+        gsw[1] = 3
+    kw = dict(global_smoother=gsm, global_sweeps=gsw, ilu_solve_sweeps=solve)
+    o = oracle.Oracle(p, **kw)
+    s = mgr.Solver(p, precision=precision, **kw)
+    if precision == mgr.MGR_FP64:
+        compare_hierarchy(o, s.h, 2)
+        fo = o.scipy(oracle.Q_MGR_ILU, level)
+        fg = mgr.mgr_get_scipy(s.h, mgr.Q_MGR_ILU, level)
+        _same_pattern(fo, fg, "ILU(1) factors")
+        _close_values(fo, fg, "ILU(1) factors")
+        assert mgr.mgr_get_csr_dims(s.h, mgr.Q_MGR_ILU, 1 - level) is None
+        v = np.random.default_rng(5).standard_normal(p.n)
+        z = s.apply(torch.from_numpy(v).cuda()).cpu().numpy()
+        assert _rel(z, o.apply(v)) <= 1e-10
+    ref = o.fgmres(p.rhs)
+    r = s.solve(torch.from_numpy(p.rhs).cuda())
+    assert r["converged"] and r["relres"] <= 1e-8
+    assert abs(r["iters"] - ref["iters"]) <= 2, (r["iters"], ref["iters"])
+    assert _rel(r["x"].cpu().numpy(), ref["x"]) <= 1e-6
+    s.close()
