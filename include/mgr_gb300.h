@@ -28,6 +28,7 @@
 #ifndef MGR_GB300_H
 #define MGR_GB300_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -319,6 +320,13 @@ int64_t mgr_get_block_colors(mgr_handle_t h, int level, int32_t* out, int32_t* n
 /* Number of CUDA kernel launches this library has issued in this process
  * (all handles, all threads).  Lets a caller count the kernels of a region. */
 int64_t mgr_launch_count(void);
+
+/* Device memory: the library allocates from its own stream-ordered memory
+ * pool on each device, which keeps freed blocks mapped so that the next setup
+ * reuses them without driver calls.  This entry point synchronises the
+ * current device and returns the pool's unused memory to the driver until at
+ * most keep_bytes stay reserved (0: all).  Handles stay valid. */
+int mgr_trim_memory(size_t keep_bytes);
 
 #ifdef __cplusplus
 }

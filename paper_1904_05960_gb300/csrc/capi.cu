@@ -4,6 +4,7 @@
 #include <chrono>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 
 #include "mgr_internal.cuh"
@@ -135,6 +136,33 @@ int mgr_setup(const mgr_matrix_t* A, const mgr_options_t* o, void* stream, mgr_h
 }  // extern "C"
 
 namespace mgr {
+cudaMemPool_t lib_pool() {
+  static constexpr int MAX_DEV = 64;
+  static std::once_flag once[MAX_DEV];
+  static cudaMemPool_t pools[MAX_DEV] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEV) {
+    (void)cudaGetLastError();
+    return nullptr;
+  }
+  std::call_once(once[dev], [dev] {
+    cudaMemPoolProps props;
+    std::memset(&props, 0, sizeof(props));
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t p = nullptr;
+    if (cudaMemPoolCreate(&p, &props) == cudaSuccess) {
+      uint64_t keep = UINT64_MAX;
+      if (cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep) == cudaSuccess) pools[dev] = p;
+      else cudaMemPoolDestroy(p);
+    }
+    (void)cudaGetLastError();
+  });
+  return pools[dev];
+}
+
 // One system's setup (mgr_setup; also run by the batched setup's workers).
 int setup_one(const mgr_matrix_t* A, const mgr_options_t* o, cudaStream_t s, Handle** out) {
   if (!A || !o || !out || A->n <= 0 || A->nnz < 0 || !A->row_ptr || !A->col_idx || !A->val ||
@@ -215,7 +243,6 @@ int mgr_destroy(mgr_handle_t hh) {
   delete h->camg;
   h->pool.free_all_async();
   h->pool2.free_all_async();
-  if (h->hpinned) cudaFreeHost(h->hpinned);
   delete h;
   return MGR_SUCCESS;
 }
@@ -279,6 +306,15 @@ int mgr_splitmix64_device(const uint64_t* in, uint64_t* out, int64_t n, void* st
 }
 
 int64_t mgr_launch_count(void) { return (int64_t)g_launches.load(); }
+
+int mgr_trim_memory(size_t keep_bytes) {
+  (void)cudaGetLastError();  // errors of earlier calls are not this call's
+  cudaMemPool_t mp = lib_pool();
+  if (!mp) return MGR_SUCCESS;
+  MGR_TRY_CUDA(cudaDeviceSynchronize());
+  MGR_TRY_CUDA(cudaMemPoolTrimTo(mp, keep_bytes));
+  return MGR_SUCCESS;
+}
 
 int64_t mgr_get_block_colors(mgr_handle_t hh, int level, int32_t* out, int32_t* ncolor) {
   (void)cudaGetLastError();  // errors of earlier calls are not this call's

@@ -234,7 +234,6 @@ static int ensure_krylov(Handle* h, int m, cudaStream_t s) {
   h->hred = P.get<double>(4);
   h->yv = P.get<double>(m + 2);
   if (P.err) return P.err;
-  if (!h->hpinned) MGR_TRY_CUDA(cudaMallocHost(&h->hpinned, sizeof(double) * 72));  // m <= 60
   (void)s;
   return MGR_SUCCESS;
 }
@@ -256,7 +255,11 @@ int fgmres_run(Handle* h, const mgr_matrix_t* A, const double* b, double* x,
   const double rtol = o->rtol > 0 ? o->rtol : 1e-8;
   MGR_TRY(ensure_krylov(h, m, s));
   const bool mixed = h->opt.precision == MGR_MIXED;
-  double* hp = h->hpinned;
+  // pinned host mirror for the per-iteration readbacks: one per host thread,
+  // allocated on its first solve and kept (pinning memory costs far more than
+  // a solve step's other host work)
+  static thread_local double* hp = nullptr;
+  if (!hp) MGR_TRY_CUDA(cudaMallocHost(&hp, sizeof(double) * 72));   // m <= 60
   cudaEvent_t e0, e1;
   MGR_TRY_CUDA(cudaEventCreate(&e0));
   MGR_TRY_CUDA(cudaEventCreate(&e1));

@@ -46,6 +46,12 @@ enum DevErr : int { DEV_OK = 0, DEV_ZERO_DIAG = 1, DEV_BAD_ARG = 2, DEV_OVERFLOW
 // ----------------------------------------------------------------------------
 // Device memory owned by a handle (stream-ordered allocations)
 // ----------------------------------------------------------------------------
+// The library's memory pool on the current device (created on first use; null
+// if it cannot be created, and allocations then use the device's default
+// pool).  Freed blocks stay mapped in it for the next setup instead of going
+// back to the driver at each synchronisation; mgr_trim_memory releases them.
+cudaMemPool_t lib_pool();
+
 struct Pool {
   std::vector<void*> ptrs;
   cudaStream_t s = nullptr;
@@ -54,7 +60,8 @@ struct Pool {
   T* get(size_t n) {
     void* p = nullptr;
     size_t bytes = (n ? n : 1) * sizeof(T);
-    cudaError_t e = cudaMallocAsync(&p, bytes, s);
+    cudaMemPool_t mp = lib_pool();
+    cudaError_t e = mp ? cudaMallocFromPoolAsync(&p, bytes, mp, s) : cudaMallocAsync(&p, bytes, s);
     if (e != cudaSuccess) {
       err = (e == cudaErrorMemoryAllocation) ? MGR_ERR_OOM : MGR_ERR_CUDA;
       (void)cudaGetLastError();
@@ -185,7 +192,6 @@ struct Handle {
   double* hcol = nullptr;        // device Hessenberg column scratch
   double* hred = nullptr;
   double* yv = nullptr;
-  double* hpinned = nullptr;     // pinned host mirror for small readbacks
   int* derr = nullptr;           // device error word
   // the F-relaxation AMG built concurrently with the rest of the setup owns
   // its allocations here (second stream) and reports through derr2

@@ -27,7 +27,7 @@ Q_AMG_A, Q_AMG_S, Q_AMG_P, Q_AMG_R = 10, 11, 12, 13
 EXPORTED = ["mgr_options_default", "fgmres_options_default", "mgr_setup", "mgr_apply",
             "fgmres_solve", "mgr_destroy", "mgr_error_string", "mgr_get_csr",
             "mgr_amg_levels", "mgr_get_cf", "mgr_vcycle", "mgr_splitmix64_device",
-            "mgr_launch_count", "mgr_vcycle_noalloc", "mgr_setup_batched",
+            "mgr_launch_count", "mgr_trim_memory", "mgr_vcycle_noalloc", "mgr_setup_batched",
             "fgmres_solve_batched", "mgr_batch_info", "mgr_batch_handle", "mgr_destroy_batched",
             "mgr_get_block_colors"]
 
@@ -116,6 +116,7 @@ def lib():
             L.mgr_get_block_colors.restype = I64
             L.mgr_launch_count.argtypes = []
             L.mgr_launch_count.restype = I64
+            L.mgr_trim_memory.argtypes = [C.c_size_t]
             _lib = L
     return _lib
 
@@ -351,6 +352,11 @@ def mgr_get_block_colors(h, level):
 def mgr_launch_count():
     """Kernel launches issued by the library so far in this process."""
     return int(lib().mgr_launch_count())
+
+
+def mgr_trim_memory(keep_bytes=0):
+    """Return the library pool's unused device memory to the driver."""
+    return _check(lib().mgr_trim_memory(int(keep_bytes)), "mgr_trim_memory")
 
 
 class Solver:

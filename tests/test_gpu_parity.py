@@ -189,6 +189,27 @@ def test_invalid_arguments_are_rejected():
     with pytest.raises(mgr.MgrError) as e:   # F = every label: empty C set
         mgr.mgr_setup(A, mgr.mgr_options_default(True, f_label_mask=[0b111, 0b10]))
     assert e.value.code == -1
+    for bad in (dict(global_smoother=[0, 3]), dict(ilu_solve_sweeps=-1)):
+        with pytest.raises(mgr.MgrError) as e:
+            mgr.mgr_setup(A, mgr.mgr_options_default(True, **bad))
+        assert e.value.code == -1
+
+
+def test_memory_pool_trim_keeps_handles_valid():
+    """The library's pool keeps freed memory for the next setup; trimming it
+    returns that memory and leaves live handles working."""
+    p = synth.two_phase(10, 9, 6, seed=4)
+    o = oracle.Oracle(p)
+    ref = o.fgmres(p.rhs)
+    s1 = mgr.Solver(p)
+    s1.close()
+    s2 = mgr.Solver(p)
+    mgr.mgr_trim_memory(0)
+    r = s2.solve(torch.from_numpy(p.rhs).cuda())
+    assert r["converged"] and abs(r["iters"] - ref["iters"]) <= 2
+    assert _rel(r["x"].cpu().numpy(), ref["x"]) <= 1e-6
+    s2.close()
+    mgr.mgr_trim_memory(0)
 
 
 def test_zero_diagonal_reported():
