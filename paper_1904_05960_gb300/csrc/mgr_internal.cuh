@@ -70,10 +70,11 @@ struct Pool {
     ptrs.push_back(p);
     return static_cast<T*>(p);
   }
-  void release(void* p) {
+  // stream-ordered release of one allocation after the work queued on fs
+  void release(void* p, cudaStream_t fs) {
     for (auto& q : ptrs)
       if (q == p) {
-        cudaFreeAsync(q, s);
+        cudaFreeAsync(q, fs);
         q = nullptr;
       }
   }

@@ -227,7 +227,8 @@ template <bool FILL>
 __global__ void __launch_bounds__(SPG_WARPS * 32)
 k_spgemm_symbolic(const int64_t* __restrict__ arp, const int32_t* __restrict__ aci, int64_t nr,
                   const int64_t* __restrict__ brp, const int32_t* __restrict__ bci,
-                  int64_t* __restrict__ cnt_or_rp, int32_t* __restrict__ cci) {
+                  int64_t* __restrict__ cnt_or_rp, int32_t* __restrict__ cci,
+                  int64_t* __restrict__ cnt_out) {
   extern __shared__ uint32_t smem[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   uint32_t* bm = smem + wid * SPG_WORDS;
@@ -290,6 +291,32 @@ k_spgemm_symbolic(const int64_t* __restrict__ arp, const int32_t* __restrict__ a
       __syncwarp();
     }
     if (!FILL && lane == 0) cnt_or_rp[i] = running;
+    if (FILL && cnt_out && lane == 0) cnt_out[i] = running;
+  }
+}
+
+// Product count of each output row, sum over k in A's row of nnz(B_k): an
+// upper bound of the row's distinct columns.
+__global__ void k_spgemm_ub(const int64_t* __restrict__ arp, const int32_t* __restrict__ aci, int64_t nr,
+                            const int64_t* __restrict__ brp, int64_t* __restrict__ ub) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nr) return;
+  int64_t u = 0;
+  for (int64_t t = arp[i]; t < arp[i + 1]; t++) {
+    const int32_t k = aci[t];
+    u += brp[k + 1] - brp[k];
+  }
+  ub[i] = u;
+}
+
+// Rows written at upper-bound offsets, moved to their compact offsets; warp
+// per row.
+__global__ void k_compact_rows(const int64_t* __restrict__ srp, const int32_t* __restrict__ sci, int64_t nr,
+                               const int64_t* __restrict__ drp, int32_t* __restrict__ dci) {
+  const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+  for (int64_t i = (int64_t)blockIdx.x * wpb + (threadIdx.x >> 5); i < nr; i += (int64_t)gridDim.x * wpb) {
+    const int64_t s0 = srp[i], d0 = drp[i], m = drp[i + 1] - d0;
+    for (int64_t q = lane; q < m; q += 32) dci[d0 + q] = sci[s0 + q];
   }
 }
 
@@ -466,11 +493,35 @@ static int spgemm_pattern(Pool& P, Pool& tmp, const Csr& A, const Csr& B, Csr& C
   });
   MGR_TRY_CUDA(attr_err);
   unsigned g = grid_for(A.nr, SPG_WARPS, 152 * 16);
-  MGR_LAUNCH k_spgemm_symbolic<false><<<g, SPG_WARPS * 32, sm, s>>>(A.rp, A.ci, A.nr, B.rp, B.ci, cnt, nullptr);
+  // One bitmap pass: rows are written at upper-bound offsets (the product
+  // counts) with their exact lengths, then moved to compact offsets.  When the
+  // upper bounds would take more than SPG_UB_BYTES, count first and fill
+  // exactly (two bitmap passes).
+  static constexpr int64_t SPG_UB_BYTES = 2LL << 30;
+  int64_t* ubrp = tmp.get<int64_t>(A.nr + 1);
+  if (tmp.err) return tmp.err;
+  MGR_LAUNCH k_spgemm_ub<<<nblocks(A.nr, 256), 256, 0, s>>>(A.rp, A.ci, A.nr, B.rp, cnt);
+  int64_t ubtot = 0;
+  MGR_TRY(rowptr_from_counts(cnt, ubrp, A.nr, &ubtot, s, tmp));
+  if (ubtot * (int64_t)sizeof(int32_t) <= SPG_UB_BYTES) {
+    int32_t* ubci = tmp.get<int32_t>(ubtot);
+    if (tmp.err) return tmp.err;
+    MGR_LAUNCH k_spgemm_symbolic<true><<<g, SPG_WARPS * 32, sm, s>>>(A.rp, A.ci, A.nr, B.rp, B.ci, ubrp, ubci, cnt);
+    MGR_TRY(rowptr_from_counts(cnt, C.rp, A.nr, &C.nnz, s, tmp));
+    C.ci = P.get<int32_t>(C.nnz);
+    if (P.err) return P.err;
+    MGR_LAUNCH k_compact_rows<<<grid_for(A.nr, 8, 152 * 16), 256, 0, s>>>(ubrp, ubci, A.nr, C.rp, C.ci);
+    MGR_TRY_CUDA(cudaGetLastError());
+    tmp.release(ubci, s);
+    return MGR_SUCCESS;
+  }
+  MGR_LAUNCH k_spgemm_symbolic<false><<<g, SPG_WARPS * 32, sm, s>>>(A.rp, A.ci, A.nr, B.rp, B.ci, cnt, nullptr,
+                                                                    nullptr);
   MGR_TRY(rowptr_from_counts(cnt, C.rp, A.nr, &C.nnz, s, tmp));
   C.ci = P.get<int32_t>(C.nnz);
   if (P.err) return P.err;
-  MGR_LAUNCH k_spgemm_symbolic<true><<<g, SPG_WARPS * 32, sm, s>>>(A.rp, A.ci, A.nr, B.rp, B.ci, C.rp, C.ci);
+  MGR_LAUNCH k_spgemm_symbolic<true><<<g, SPG_WARPS * 32, sm, s>>>(A.rp, A.ci, A.nr, B.rp, B.ci, C.rp, C.ci,
+                                                                   nullptr);
   MGR_TRY_CUDA(cudaGetLastError());
   return MGR_SUCCESS;
 }
