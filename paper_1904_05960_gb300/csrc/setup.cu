@@ -299,14 +299,17 @@ k_spgemm_symbolic(const int64_t* __restrict__ arp, const int32_t* __restrict__ a
 // upper bound of the row's distinct columns.
 __global__ void k_spgemm_ub(const int64_t* __restrict__ arp, const int32_t* __restrict__ aci, int64_t nr,
                             const int64_t* __restrict__ brp, int64_t* __restrict__ ub) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= nr) return;
-  int64_t u = 0;
-  for (int64_t t = arp[i]; t < arp[i + 1]; t++) {
-    const int32_t k = aci[t];
-    u += brp[k + 1] - brp[k];
+  const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+  for (int64_t i = (int64_t)blockIdx.x * wpb + (threadIdx.x >> 5); i < nr; i += (int64_t)gridDim.x * wpb) {
+    int64_t u = 0;
+    for (int64_t t = arp[i] + lane; t < arp[i + 1]; t += 32) {
+      const int32_t k = aci[t];
+      u += brp[k + 1] - brp[k];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) u += __shfl_xor_sync(FULL, u, o);
+    if (lane == 0) ub[i] = u;
   }
-  ub[i] = u;
 }
 
 // Rows written at upper-bound offsets, moved to their compact offsets; warp
@@ -500,7 +503,7 @@ static int spgemm_pattern(Pool& P, Pool& tmp, const Csr& A, const Csr& B, Csr& C
   static constexpr int64_t SPG_UB_BYTES = 2LL << 30;
   int64_t* ubrp = tmp.get<int64_t>(A.nr + 1);
   if (tmp.err) return tmp.err;
-  MGR_LAUNCH k_spgemm_ub<<<nblocks(A.nr, 256), 256, 0, s>>>(A.rp, A.ci, A.nr, B.rp, cnt);
+  MGR_LAUNCH k_spgemm_ub<<<grid_for(A.nr, 8, 152 * 16), 256, 0, s>>>(A.rp, A.ci, A.nr, B.rp, cnt);
   int64_t ubtot = 0;
   MGR_TRY(rowptr_from_counts(cnt, ubrp, A.nr, &ubtot, s, tmp));
   if (ubtot * (int64_t)sizeof(int32_t) <= SPG_UB_BYTES) {
@@ -1072,20 +1075,27 @@ __global__ void k_pmis_select(const int64_t* __restrict__ srp, const int32_t* __
   newc[i] = best ? 1 : 0;
 }
 
-__global__ void k_pmis_apply_c(const int8_t* __restrict__ newc, int64_t n, int8_t* __restrict__ cf) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n && newc[i]) cf[i] = 1;
-}
-
-__global__ void k_pmis_mark_f(const int64_t* __restrict__ srp, const int32_t* __restrict__ sci,
-                              int64_t n, int8_t* __restrict__ cf, unsigned long long* undecided) {
-  int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= n || cf[j] != 0) return;
-  for (int64_t k = srp[j]; k < srp[j + 1]; k++)
-    if (cf[sci[k]] == 1) {
+// New C points of the round take C; an undecided point with a strong
+// neighbour in C (old or new) becomes F.  A neighbour's mark may change
+// during the kernel only from 0 to -1 or, for a new C point, to 1, which the
+// newc test already sees, so the outcome does not depend on thread order.
+__global__ void k_pmis_apply_mark(const int64_t* __restrict__ srp, const int32_t* __restrict__ sci,
+                                  const int8_t* __restrict__ newc, int64_t n, int8_t* cf,
+                                  unsigned long long* undecided) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  if (newc[j]) {
+    cf[j] = 1;
+    return;
+  }
+  if (cf[j] != 0) return;
+  for (int64_t k = srp[j]; k < srp[j + 1]; k++) {
+    const int32_t c = sci[k];
+    if (newc[c] || cf[c] == 1) {
       cf[j] = -1;
       return;
     }
+  }
   atomicAdd(undecided, 1ull);
 }
 
@@ -1158,6 +1168,56 @@ __device__ inline void for_strong_c(const int64_t* rp, const int32_t* ci, const 
 }
 
 static constexpr int PMAX_CAP = 16;
+
+// Entries of each row of P (the count pass of the interpolation), warp per
+// row, without the weights: a C point has 1; an F point has its strong-C
+// neighbours of the same component (nsc), capped at pmax, or none when their
+// negative and positive sums (cn, cp of the weight formula) are both zero.  A
+// sum of same-signed nonzero values is nonzero, so cn != 0 exactly when some
+// strong-C entry is negative (the IEEE bit test is_neg), likewise cp; the
+// counts are the weight pass's.
+__global__ void __launch_bounds__(256)
+k_interp_count(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci, const double* __restrict__ v,
+               const int64_t* __restrict__ srp, const int32_t* __restrict__ sci,
+               const int32_t* __restrict__ comp, const int8_t* __restrict__ cf, int64_t n, int pmax,
+               int64_t* __restrict__ cnt) {
+  const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+  for (int64_t i = (int64_t)blockIdx.x * wpb + (threadIdx.x >> 5); i < n; i += (int64_t)gridDim.x * wpb) {
+    if (cf[i] == 1) {
+      if (lane == 0) cnt[i] = 1;
+      continue;
+    }
+    const int64_t sb = srp[i], se = srp[i + 1];
+    const int32_t c_i = comp[i];
+    int nsc = 0;
+    bool sign = false;
+    for (int64_t k = rp[i] + lane; k < rp[i + 1]; k += 32) {
+      const int32_t j = ci[k];
+      bool sc = false;
+      if (j != i && comp[j] == c_i && cf[j] == 1) {
+        int64_t lo = sb, hi = se;
+        while (lo < hi) {
+          const int64_t mid = (lo + hi) >> 1;
+          if (sci[mid] < j) lo = mid + 1;
+          else hi = mid;
+        }
+        sc = lo < se && sci[lo] == j;
+      }
+      if (sc) {
+        nsc++;
+        const double a = v[k];
+        sign = sign || is_neg(a) || is_pos(a);
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) nsc += __shfl_xor_sync(FULL, nsc, o);
+    sign = __any_sync(FULL, sign);
+    if (lane == 0) {
+      const int r = sign ? nsc : 0;
+      cnt[i] = (pmax > 0 && r > pmax) ? pmax : r;
+    }
+  }
+}
 
 template <bool FILL>
 __device__ void interp_row_seq(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
@@ -1825,21 +1885,20 @@ static int coarsen_step(const mgr_options_t& o, Pool& Ps, Pool& Pi, Pool& tmp, c
   double* w = tmp.get<double>(n);
   int8_t* newc = tmp.get<int8_t>(n);
   int8_t* cf = Ps.get<int8_t>(n);
-  unsigned long long* und = tmp.get<unsigned long long>(1);
+  unsigned long long* und = tmp.get<unsigned long long>(4);
   if (tmp.err || Ps.err) return tmp.err ? tmp.err : Ps.err;
   *cf_out = cf;
   MGR_LAUNCH k_pmis_init<<<nblocks(n, 256), 256, 0, s>>>(S.rp, ST.rp, n, o.seed, slot, level, w, cf);
   // synchronous rounds, checked every 4th: a round after the last
   // undecided point is gone changes nothing
   for (int round = 0; round < 100000; round += 4) {
+    MGR_TRY_CUDA(cudaMemsetAsync(und, 0, 4 * sizeof(unsigned long long), s));
     for (int q = 0; q < 4; q++) {
       MGR_LAUNCH k_pmis_select<<<nblocks(n, 256), 256, 0, s>>>(S.rp, S.ci, ST.rp, ST.ci, w, cf, n, newc);
-      MGR_LAUNCH k_pmis_apply_c<<<nblocks(n, 256), 256, 0, s>>>(newc, n, cf);
-      cudaMemsetAsync(und, 0, sizeof(unsigned long long), s);
-      MGR_LAUNCH k_pmis_mark_f<<<nblocks(n, 256), 256, 0, s>>>(S.rp, S.ci, n, cf, und);
+      MGR_LAUNCH k_pmis_apply_mark<<<nblocks(n, 256), 256, 0, s>>>(S.rp, S.ci, newc, n, cf, und + q);
     }
     unsigned long long left = 0;
-    MGR_TRY(read_back(&left, und, s));
+    MGR_TRY(read_back(&left, und + 3, s));
     if (left == 0) break;
   }
   g_trace.mark("amg pmis", slot, level);
@@ -1864,12 +1923,8 @@ static int coarsen_step(const mgr_options_t& o, Pool& Ps, Pool& Pi, Pool& tmp, c
   // on the 113k-row, 150-non-zero level the warp form took 2.4 ms against
   // 0.8 ms)
   const bool big = n >= 20000;
-  if (big)
-    MGR_LAUNCH k_interp_thread<false><<<nblocks(n, 128), 128, 0, s>>>(A.rp, A.ci, A.v, S.rp, S.ci, comp, cf,
-                                                                     cmap, n, o.amg_pmax, cnt, nullptr, nullptr);
-  else
-    MGR_LAUNCH k_interp<false><<<grid_for(n, IW_WARPS, 152 * 32), IW_WARPS * 32, 0, s>>>(
-        A.rp, A.ci, A.v, S.rp, S.ci, comp, cf, cmap, n, o.amg_pmax, cnt, nullptr, nullptr);
+  MGR_LAUNCH k_interp_count<<<grid_for(n, 8, 152 * 16), 256, 0, s>>>(A.rp, A.ci, A.v, S.rp, S.ci, comp, cf, n,
+                                                                   o.amg_pmax, cnt);
   MGR_TRY(rowptr_from_counts(cnt, Pm.rp, n, &Pm.nnz, s, tmp));
   Pm.ci = Pi.get<int32_t>(Pm.nnz);
   Pm.v = Pi.get<double>(Pm.nnz);
