@@ -993,7 +993,8 @@ template <bool FILL>
 __global__ void __launch_bounds__(256)
 k_strength(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
            const double* __restrict__ v, const int32_t* __restrict__ comp, int64_t n,
-           double theta, int64_t* __restrict__ cnt_or_rp, int32_t* __restrict__ sci) {
+           double theta, int64_t* __restrict__ cnt_or_rp, int32_t* __restrict__ sci,
+           int64_t* __restrict__ cnt_out) {
   const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
   for (int64_t i = (int64_t)blockIdx.x * wpb + (threadIdx.x >> 5); i < n;
        i += (int64_t)gridDim.x * wpb) {
@@ -1033,6 +1034,7 @@ k_strength(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
       }
     }
     if (!FILL && lane == 0) cnt_or_rp[i] = o;
+    if (FILL && cnt_out && lane == 0) cnt_out[i] = o - cnt_or_rp[i];
   }
 }
 
@@ -1871,13 +1873,17 @@ static int coarsen_step(const mgr_options_t& o, Pool& Ps, Pool& Pi, Pool& tmp, c
   S.nr = S.nc = n;
   S.rp = Ps.get<int64_t>(n + 1);
   if (tmp.err || Ps.err) return tmp.err ? tmp.err : Ps.err;
-  MGR_LAUNCH k_strength<false><<<grid_for(n, 8, 152 * 16), 256, 0, s>>>(A.rp, A.ci, A.v, comp, n,
-                                                                       o.amg_theta, cnt, nullptr);
+  // one pass: S is a subset of A's pattern, so each row is written at A's row
+  // offset with its exact length, then moved to its compact offset
+  int32_t* sfull = tmp.get<int32_t>(A.nnz);
+  if (tmp.err) return tmp.err;
+  MGR_LAUNCH k_strength<true><<<grid_for(n, 8, 152 * 16), 256, 0, s>>>(A.rp, A.ci, A.v, comp, n,
+                                                                      o.amg_theta, A.rp, sfull, cnt);
   MGR_TRY(rowptr_from_counts(cnt, S.rp, n, &S.nnz, s, tmp));
   S.ci = Ps.get<int32_t>(S.nnz);
   if (Ps.err) return Ps.err;
-  MGR_LAUNCH k_strength<true><<<grid_for(n, 8, 152 * 16), 256, 0, s>>>(A.rp, A.ci, A.v, comp, n,
-                                                                      o.amg_theta, S.rp, S.ci);
+  MGR_LAUNCH k_compact_rows<<<grid_for(n, 8, 152 * 16), 256, 0, s>>>(A.rp, sfull, n, S.rp, S.ci);
+  tmp.release(sfull, s);
   g_trace.mark("amg strength", slot, level);
   Csr ST;
   MGR_TRY(transpose(tmp, tmp, S, ST, false, false, s));
