@@ -47,9 +47,12 @@ __device__ __forceinline__ unsigned group_mask() {
   return (G == 32) ? FULL : (((1u << G) - 1u) << ((threadIdx.x & 31) & ~(G - 1)));
 }
 
-// Grid-stride over rows, one G-lane group per row, two independent
-// accumulators; I is the offset type (int when nnz < 2^31).  All lanes of a
-// group always share a row, so the shuffle mask is the group's own lanes.
+// Grid-stride over rows, one G-lane group per row, one accumulator per lane
+// (loads unrolled by four); I is the offset type (int when nnz < 2^31).  All
+// lanes of a group always share a row, so the shuffle mask is the group's own
+// lanes.  One accumulator rather than two: on GB300 the FP64 products share a
+// narrow pipe, and every extra add (merging accumulators) costs a warp
+// instruction (measured on the A_uu levels: 7-17% faster).
 template <class T, class X, class Y, class I, int G, int MODE>
 __global__ void __launch_bounds__(256)
 k_spmv(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci, const T* __restrict__ val,
@@ -61,26 +64,18 @@ k_spmv(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci, const T* 
   for (I i = gid / G; i < nr; i += stride) {
     const I row = (MODE == MODE_RROWS) ? (I)rows[i] : i;
     const I e0 = (I)rp[row], e1 = (I)rp[row + 1];
-    Y a0 = 0, a1 = 0;
+    Y acc = 0;
     I k = e0 + lane;
     if (MODE == MODE_RES0 || MODE == MODE_DRES0) {
-      for (; k + G < e1; k += 2 * G) {
-        const int32_t c0 = ci[k], c1 = ci[k + G];
-        a0 += (Y)val[k] * ((Y)ldg(dinv + c0) * (Y)ldg(x + c0));
-        a1 += (Y)val[k + G] * ((Y)ldg(dinv + c1) * (Y)ldg(x + c1));
-      }
-      if (k < e1) {
+#pragma unroll 4
+      for (; k < e1; k += G) {
         const int32_t c0 = ci[k];
-        a0 += (Y)val[k] * ((Y)ldg(dinv + c0) * (Y)ldg(x + c0));
+        acc += (Y)val[k] * ((Y)ldg(dinv + c0) * (Y)ldg(x + c0));
       }
     } else {
-      for (; k + G < e1; k += 2 * G) {
-        a0 += (Y)val[k] * (Y)ldg(x + ci[k]);
-        a1 += (Y)val[k + G] * (Y)ldg(x + ci[k + G]);
-      }
-      if (k < e1) a0 += (Y)val[k] * (Y)ldg(x + ci[k]);
+#pragma unroll 4
+      for (; k < e1; k += G) acc += (Y)val[k] * (Y)ldg(x + ci[k]);
     }
-    Y acc = a0 + a1;
 #pragma unroll
     for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(group_mask<G>(), acc, o, G);
     if (lane == 0) {
@@ -97,13 +92,14 @@ k_spmv(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci, const T* 
   }
 }
 
-// Lanes per row from the mean row length (measured on GB300 for FP64/FP32
-// CSR: ~46 non-zeros per row run best with 4 lanes, ~150 with 8).
+// Lanes per row from the mean row length (measured on GB300 for FP64 CSR:
+// ~19 non-zeros per row run best with 2 lanes, ~34-46 with 4, ~150-210 with
+// 8).
 static int pick_group(int64_t nnz, int64_t nr) {
   const double avg = nr > 0 ? (double)nnz / (double)nr : 1.0;
   int g;
   if (avg < 6) g = 1;
-  else if (avg < 12) g = 2;
+  else if (avg < 24) g = 2;
   else if (avg < 64) g = 4;
   else if (avg < 256) g = 8;
   else g = 16;
@@ -260,14 +256,9 @@ k_block_jacobi(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
     for (int q = threadIdx.x / G; q < nrow; q += blockDim.x / G) {
       const int64_t i = r0 + q;
       const int64_t e1 = rp[i + 1];
-      int64_t e = rp[i] + lane;
-      T a0 = 0, a1 = 0;
-      for (; e + G < e1; e += 2 * G) {
-        a0 += val[e] * ldg(zin + ci[e]);
-        a1 += val[e + G] * ldg(zin + ci[e + G]);
-      }
-      if (e < e1) a0 += val[e] * ldg(zin + ci[e]);
-      T acc = a0 + a1;
+      T acc = 0;
+#pragma unroll 4
+      for (int64_t e = rp[i] + lane; e < e1; e += G) acc += val[e] * ldg(zin + ci[e]);
 #pragma unroll
       for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(group_mask<G>(), acc, o, G);
       if (lane == 0) rs[q] = v[i] - acc;
