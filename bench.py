@@ -315,27 +315,20 @@ def run_ours(args):
     ms32, info32, _, _ = timed(mgr.MGR_MIXED, args.steps, args.warmup)
     x32 = x.cpu().numpy().copy()
 
-    # end to end through the public API with host buffers (pinned), copies timed
-    host = dict(rp=torch.from_numpy(p.row_ptr).pin_memory(), ci=torch.from_numpy(p.col).pin_memory(),
-                v=torch.from_numpy(p.val).pin_memory(),
-                lab=torch.from_numpy(p.dof_label).pin_memory(),
-                nod=torch.from_numpy(p.dof_node).pin_memory(),
-                cmp=torch.from_numpy(p.dof_comp).pin_memory(),
-                rhs=torch.from_numpy(p.rhs).pin_memory())
+    # end to end through the public API with host buffers (pinned): one
+    # mgr_solve_host call copies the matrix and rhs in, runs setup + FGMRES +
+    # teardown and copies x out
+    Ah = mgr.HostMatrix(p, pin=True)
+    bh = torch.from_numpy(p.rhs).pin_memory()
     xh = torch.empty(p.n, dtype=torch.float64).pin_memory()
-    h2d = sum(t.numel() * t.element_size() for t in host.values())
+    h2d = Ah.nbytes + bh.numel() * bh.element_size()
     d2h = xh.numel() * xh.element_size()
+    o64 = mgr.mgr_options_default(True)
 
     def e2e_step():
-        A.row_ptr.copy_(host["rp"], non_blocking=True)
-        A.col_idx.copy_(host["ci"], non_blocking=True)
-        A.val.copy_(host["v"], non_blocking=True)
-        A.dof_label.copy_(host["lab"], non_blocking=True)
-        A.dof_node.copy_(host["nod"], non_blocking=True)
-        A.dof_comp.copy_(host["cmp"], non_blocking=True)
-        b.copy_(host["rhs"], non_blocking=True)
-        step(mgr.MGR_FP64, x)
-        xh.copy_(x, non_blocking=True)
+        r = mgr.mgr_solve_host(Ah, bh, xh, o64, fo, stream)
+        if not r["converged"]:
+            raise RuntimeError(f"FGMRES did not converge: {r}")
 
     for _ in range(args.warmup):
         e2e_step()

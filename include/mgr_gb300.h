@@ -199,6 +199,21 @@ int mgr_apply(mgr_handle_t h, const double* v, double* z, void* stream);
 int fgmres_solve(mgr_handle_t h, const mgr_matrix_t* A, const double* b, double* x,
                  const fgmres_options_t* o, fgmres_info_t* info, void* stream);
 
+/*
+ * The whole path from HOST memory in one call: copies A (row pointers,
+ * columns, values, dof_label, dof_node, dof_comp if not NULL) and b to the
+ * device, builds the preconditioner (mgr_setup with options o), solves with
+ * fgmres_solve (options fo; NULL: defaults), copies x back and frees every
+ * device buffer.  All pointers in A and b, x are HOST pointers; pinned host
+ * memory gives the full transfer rate (on GB300 ~210 GB/s host to device),
+ * pageable memory works at a lower rate.  info (host) may be NULL; its
+ * setup_s and solve_s are the device phases, without the transfers.  Returns
+ * what mgr_setup or fgmres_solve returns; x is written only on success or
+ * MGR_NOT_CONVERGED.  Synchronises the stream.
+ */
+int mgr_solve_host(const mgr_matrix_t* A, const double* b, double* x, const mgr_options_t* o,
+                   const fgmres_options_t* fo, fgmres_info_t* info, void* stream);
+
 /* Release every device allocation of the handle (synchronises the device). */
 int mgr_destroy(mgr_handle_t h);
 

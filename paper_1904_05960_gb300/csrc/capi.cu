@@ -234,6 +234,60 @@ int fgmres_solve(mgr_handle_t hh, const mgr_matrix_t* A, const double* b, double
   return fgmres_run(h, A, b, x, o ? o : &d, info, (cudaStream_t)stream);
 }
 
+int mgr_solve_host(const mgr_matrix_t* A, const double* b, double* x, const mgr_options_t* o,
+                   const fgmres_options_t* fo, fgmres_info_t* info, void* stream) {
+  (void)cudaGetLastError();  // errors of earlier calls are not this call's
+  if (!A || !b || !x || !o || A->n <= 0 || A->nnz < 0 || !A->row_ptr || !A->col_idx || !A->val ||
+      !A->dof_label || !A->dof_node)
+    return MGR_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t n = A->n, nnz = A->nnz;
+  Pool P;
+  P.s = s;
+  mgr_matrix_t D = *A;
+  int64_t* rp = P.get<int64_t>(n + 1);
+  int32_t* ci = P.get<int32_t>(nnz);
+  double* v = P.get<double>(nnz);
+  int32_t* lab = P.get<int32_t>(n);
+  int32_t* nod = P.get<int32_t>(n);
+  int32_t* cmp = A->dof_comp ? P.get<int32_t>(n) : nullptr;
+  double* db = P.get<double>(n);
+  double* dx = P.get<double>(n);
+  int rc = P.err;
+  auto h2d = [&](void* d, const void* hsrc, size_t bytes) {
+    if (rc == MGR_SUCCESS && bytes && cudaMemcpyAsync(d, hsrc, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
+      rc = MGR_ERR_CUDA;
+  };
+  h2d(rp, A->row_ptr, sizeof(int64_t) * (n + 1));
+  h2d(ci, A->col_idx, sizeof(int32_t) * nnz);
+  h2d(v, A->val, sizeof(double) * nnz);
+  h2d(lab, A->dof_label, sizeof(int32_t) * n);
+  h2d(nod, A->dof_node, sizeof(int32_t) * n);
+  if (cmp) h2d(cmp, A->dof_comp, sizeof(int32_t) * n);
+  h2d(db, b, sizeof(double) * n);
+  D.row_ptr = rp;
+  D.col_idx = ci;
+  D.val = v;
+  D.dof_label = lab;
+  D.dof_node = nod;
+  D.dof_comp = cmp;
+  Handle* h = nullptr;
+  if (rc == MGR_SUCCESS) rc = mgr::setup_one(&D, o, s, &h);
+  if (rc == MGR_SUCCESS) {
+    fgmres_options_t d;
+    fgmres_options_default(&d);
+    rc = fgmres_run(h, &D, db, dx, fo ? fo : &d, info, s);
+    if ((rc == MGR_SUCCESS || rc == MGR_NOT_CONVERGED) &&
+        (cudaMemcpyAsync(x, dx, sizeof(double) * n, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+         cudaStreamSynchronize(s) != cudaSuccess))
+      rc = MGR_ERR_CUDA;
+  }
+  if (h) mgr_destroy(reinterpret_cast<mgr_handle_t>(h));
+  cudaStreamSynchronize(s);
+  P.free_all_async(s);
+  return rc;
+}
+
 int mgr_destroy(mgr_handle_t hh) {
   Handle* h = reinterpret_cast<Handle*>(hh);
   if (!h) return MGR_SUCCESS;

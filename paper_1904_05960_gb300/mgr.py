@@ -27,7 +27,7 @@ Q_AMG_A, Q_AMG_S, Q_AMG_P, Q_AMG_R = 10, 11, 12, 13
 EXPORTED = ["mgr_options_default", "fgmres_options_default", "mgr_setup", "mgr_apply",
             "fgmres_solve", "mgr_destroy", "mgr_error_string", "mgr_get_csr",
             "mgr_amg_levels", "mgr_get_cf", "mgr_vcycle", "mgr_splitmix64_device",
-            "mgr_launch_count", "mgr_trim_memory", "mgr_vcycle_noalloc", "mgr_setup_batched",
+            "mgr_launch_count", "mgr_trim_memory", "mgr_solve_host", "mgr_vcycle_noalloc", "mgr_setup_batched",
             "fgmres_solve_batched", "mgr_batch_info", "mgr_batch_handle", "mgr_destroy_batched",
             "mgr_get_block_colors"]
 
@@ -117,6 +117,8 @@ def lib():
             L.mgr_launch_count.argtypes = []
             L.mgr_launch_count.restype = I64
             L.mgr_trim_memory.argtypes = [C.c_size_t]
+            L.mgr_solve_host.argtypes = [C.POINTER(MgrMatrix), P, P, C.POINTER(MgrOptions),
+                                         C.POINTER(FgmresOptions), C.POINTER(FgmresInfo), P]
             _lib = L
     return _lib
 
@@ -191,6 +193,53 @@ class DeviceMatrix:
     @property
     def c(self):
         return self._s
+
+
+class HostMatrix:
+    """A problem's CSR and labels in host tensors (pinned by default), for
+    mgr_solve_host."""
+
+    def __init__(self, prob, pin=True):
+        import torch
+        self.n = int(prob.n)
+        self.nnz = int(prob.row_ptr[-1])
+
+        def t(a, dt):
+            x = torch.from_numpy(np.ascontiguousarray(a, dtype=dt))
+            return x.pin_memory() if pin else x
+        self.row_ptr = t(prob.row_ptr, np.int64)
+        self.col_idx = t(prob.col, np.int32)
+        self.val = t(prob.val, np.float64)
+        self.dof_label = t(prob.dof_label, np.int32)
+        self.dof_node = t(prob.dof_node, np.int32)
+        self.dof_comp = t(prob.dof_comp, np.int32) if prob.dof_comp is not None else None
+        self._s = MgrMatrix(self.n, self.nnz, self.row_ptr.data_ptr(), self.col_idx.data_ptr(),
+                            self.val.data_ptr(), self.dof_label.data_ptr(),
+                            self.dof_node.data_ptr(),
+                            self.dof_comp.data_ptr() if self.dof_comp is not None else None)
+
+    @property
+    def c(self):
+        return self._s
+
+    @property
+    def nbytes(self):
+        ts = [self.row_ptr, self.col_idx, self.val, self.dof_label, self.dof_node]
+        if self.dof_comp is not None:
+            ts.append(self.dof_comp)
+        return sum(x.numel() * x.element_size() for x in ts)
+
+
+def mgr_solve_host(A: HostMatrix, b, x, opts: MgrOptions, fo: FgmresOptions | None = None,
+                   stream=None):
+    """Setup + FGMRES + teardown from host buffers (b, x: host FP64 tensors)."""
+    info = FgmresInfo()
+    st = _check(lib().mgr_solve_host(C.byref(A.c), _ptr(b), _ptr(x), C.byref(opts),
+                                     C.byref(fo) if fo is not None else None, C.byref(info),
+                                     _stream_ptr(stream)), "mgr_solve_host")
+    return dict(status=st, iters=info.iters, restarts=info.restarts,
+                converged=bool(info.converged), relres=info.rel_res_true,
+                setup_s=info.setup_s, solve_s=info.solve_s)
 
 
 def mgr_setup(A: DeviceMatrix, opts: MgrOptions, stream=None):

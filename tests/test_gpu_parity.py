@@ -394,3 +394,23 @@ def test_ilu1_smoother_matches_oracle(precision, level, sweeps, solve):
     assert abs(r["iters"] - ref["iters"]) <= 2, (r["iters"], ref["iters"])
     assert _rel(r["x"].cpu().numpy(), ref["x"]) <= 1e-6
     s.close()
+
+
+def test_solve_from_host_buffers_matches_device_path():
+    """mgr_solve_host (host CSR, rhs and solution) gives the device path's
+    solution bit for bit and the oracle's to the solution bar."""
+    p = synth.two_phase(11, 9, 6, seed=8)
+    o = oracle.Oracle(p)
+    ref = o.fgmres(p.rhs)
+    s = mgr.Solver(p)
+    rd = s.solve(torch.from_numpy(p.rhs).cuda())
+    s.close()
+    for pin in (True, False):
+        Ah = mgr.HostMatrix(p, pin=pin)
+        bh = torch.from_numpy(p.rhs.copy())
+        xh = torch.zeros(p.n, dtype=torch.float64)
+        r = mgr.mgr_solve_host(Ah, bh, xh, mgr.mgr_options_default(True))
+        assert r["converged"] and r["iters"] == rd["iters"]
+        assert np.array_equal(xh.numpy(), rd["x"].cpu().numpy())
+        assert abs(r["iters"] - ref["iters"]) <= 2
+        assert _rel(xh.numpy(), ref["x"]) <= 1e-6
