@@ -35,6 +35,7 @@ sys.path.insert(0, ROOT)
 METRIC = "MGR-FGMRES solve s & dofs/s to rel-res 1e-8; V-cycle HBM GB/s; mixed vs FP64"
 WORKLOAD = dict(nx=64, ny=64, nz=32, seed=0, sigma=2.0)
 SAMPLE = dict(nx=32, ny=32, nz=16, seed=0, sigma=2.0)
+WORKLOAD_NAME = "two-phase poromechanics Jacobian, 64x64x32 cells, FP64 plain MGR"
 # the mixed-precision large case (128x128x64 cells, lognormal E): extra keys
 LARGE = dict(nx=128, ny=128, nz=64, seed=0, sigma=2.0, E_sigma=1.5)
 PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "vcycle_uu_traffic.txt")
@@ -62,6 +63,25 @@ def parse():
 def dist_env():
     return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
             int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def dist_max(x, world):
+    """Max of a per-rank number over all ranks (identity for one rank); the
+    reduction buffer lives where the process group's backend wants it."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(units_per_rank, world, ms_max):
+    """Whole-job throughput: the units every rank processed in one step,
+    over the slowest rank's step time."""
+    return units_per_rank * world / (ms_max * 1e-3)
 
 
 # --------------------------------------------------------------------------- clocks
@@ -217,8 +237,9 @@ def run_reference(args):
     line = dict(metric=METRIC, value=value, unit="dofs/s", n_gpus=args.gpus, steps=args.steps,
                 warmup=args.warmup, ms_per_step=ms, higher_is_better=True, scaling="weak",
                 vs_baseline=None, dtype="f64", data="synthetic", impl="reference",
-                config=dict(workload="two-phase poromechanics Jacobian (bounded CPU sample)",
-                            unknowns=p.n, iters=iters),
+                config=dict(workload=WORKLOAD_NAME, parallelism=f"replicas x{world}",
+                            sample=f"bounded CPU sample: {p.n:,} unknowns, {iters} iterations; "
+                                   "value scaled to dofs/s of the sample"),
                 cpu_baseline=dict(value=value, unit="dofs/s", cores=1, kind="oracle",
                                   sample=sample),
                 e2e=dict(value=value, unit="dofs/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
@@ -244,12 +265,7 @@ def run_ours(args):
             dist.barrier()
 
     def reduce_max(x):
-        if world == 1:
-            return x
-        import torch.distributed as dist
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return dist_max(x, world)
 
     p = synth.two_phase(**WORKLOAD)
     stream = torch.cuda.current_stream()
@@ -414,7 +430,7 @@ def run_ours(args):
         msm, rm = res[mgr.MGR_MIXED]
         msd, rd = res[mgr.MGR_FP64]
         large = dict(workload="two-phase 128x128x64 cells, lognormal E (sigma 1.5), MGR_MIXED",
-                     unknowns=pl.n, nnz=pl.nnz, value=pl.n * world / (msm * 1e-3), unit="dofs/s",
+                     unknowns=pl.n, nnz=pl.nnz, value=job_value(pl.n, world, msm), unit="dofs/s",
                      ms_per_step=msm, iters=rm["iters"], rel_res_true=rm["relres"],
                      setup_s=rm["setup_s"], solve_s=rm["solve_s"], fp64_ms_per_step=msd,
                      fp64_iters=rd["iters"], speedup_mixed_vs_fp64=msd / msm)
@@ -455,12 +471,12 @@ def run_ours(args):
         ensemble = run_ensemble(args, mgr, stream, world)
 
     n = p.n
-    value = n * world / (ms64 * 1e-3)
+    value = job_value(n, world, ms64)
     line = dict(
         metric=METRIC, value=value, unit="dofs/s", n_gpus=world, steps=args.steps,
         warmup=args.warmup, ms_per_step=ms64, higher_is_better=True, scaling="weak",
         vs_baseline=None, dtype="f64", data="synthetic",
-        config=dict(workload="two-phase poromechanics Jacobian, 64x64x32 cells, FP64 plain MGR",
+        config=dict(workload=WORKLOAD_NAME,
                     unknowns=n, nnz=p.nnz, parallelism=f"replicas x{world}",
                     step="mgr_setup + fgmres_solve (m=50, rtol 1e-8 true residual) + mgr_destroy",
                     l2="inputs larger than L2 (CSR of A: %.0f MB)" % (p.nnz * 12 / 1e6),
@@ -472,12 +488,12 @@ def run_ours(args):
                       traffic=profiled_traffic(), algorithmic_bytes=vc[mgr.MGR_FP64]["bytes"],
                       ms=vc[mgr.MGR_FP64]["ms"], timing="CUDA-graph replay of mgr_vcycle",
                       ms_eager_launches=vc[mgr.MGR_FP64]["ms_eager"]),
-        mixed=dict(value=n * world / (ms32 * 1e-3), ms_per_step=ms32,
+        mixed=dict(value=job_value(n, world, ms32), ms_per_step=ms32,
                    speedup_vs_fp64=ms64 / ms32, iters=info32["iters"],
                    setup_s=info32["setup_s"], solve_s=info32["solve_s"],
                    vcycle_gbs=vc[mgr.MGR_MIXED]["gbs"],
                    vcycle_frac=vc[mgr.MGR_MIXED]["gbs"] / peak),
-        e2e=dict(value=n * world / (ms_e2e * 1e-3), unit="dofs/s", h2d_bytes_per_step=h2d,
+        e2e=dict(value=job_value(n, world, ms_e2e), unit="dofs/s", h2d_bytes_per_step=h2d,
                  d2h_bytes_per_step=d2h, ms_per_step=ms_e2e),
         clocks=clocks,
         gpu_launches=launches,
