@@ -10,6 +10,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdlib>
+#include <mutex>
 #include <utility>
 #include <vector>
 
@@ -246,6 +247,43 @@ static void mdot(Handle* h, const double* V, int64_t ld, int nv, const double* w
   MGR_LAUNCH k_mdot_final<false><<<(nv + 7) / 8, 256, 0, s>>>(h->part, nb, nv, dst, accumulate, nullptr);
 }
 
+// Pinned host buffers of 72 doubles (m <= 60) for the Hessenberg readbacks.
+// Pinning memory costs far more than a solve step's other host work, so a
+// host thread leases one on its first solve and hands it back to a free list
+// when it exits (the batched solves run on short-lived worker threads); the
+// buffers are never unpinned, their number is bounded by the peak number of
+// threads solving at once.
+static std::mutex g_pin_mu;
+static std::vector<double*> g_pin_free;
+struct PinLease {
+  double* p = nullptr;
+  ~PinLease() {
+    if (!p) return;
+    std::lock_guard<std::mutex> g(g_pin_mu);
+    g_pin_free.push_back(p);
+  }
+};
+static thread_local PinLease t_pin;
+
+static int pinned_scratch(double** out) {
+  if (!t_pin.p) {
+    {
+      std::lock_guard<std::mutex> g(g_pin_mu);
+      if (!g_pin_free.empty()) {
+        t_pin.p = g_pin_free.back();
+        g_pin_free.pop_back();
+      }
+    }
+    if (!t_pin.p) {
+      void* q = nullptr;
+      MGR_TRY_CUDA(cudaMallocHost(&q, sizeof(double) * 72));
+      t_pin.p = static_cast<double*>(q);
+    }
+  }
+  *out = t_pin.p;
+  return MGR_SUCCESS;
+}
+
 int fgmres_run(Handle* h, const mgr_matrix_t* A, const double* b, double* x,
                const fgmres_options_t* o, fgmres_info_t* info, cudaStream_t s) {
   const int64_t n = h->n;
@@ -255,11 +293,9 @@ int fgmres_run(Handle* h, const mgr_matrix_t* A, const double* b, double* x,
   const double rtol = o->rtol > 0 ? o->rtol : 1e-8;
   MGR_TRY(ensure_krylov(h, m, s));
   const bool mixed = h->opt.precision == MGR_MIXED;
-  // pinned host mirror for the per-iteration readbacks: one per host thread,
-  // allocated on its first solve and kept (pinning memory costs far more than
-  // a solve step's other host work)
-  static thread_local double* hp = nullptr;
-  if (!hp) MGR_TRY_CUDA(cudaMallocHost(&hp, sizeof(double) * 72));   // m <= 60
+  // pinned host mirror for the per-iteration readbacks, leased per host thread
+  double* hp = nullptr;
+  MGR_TRY(pinned_scratch(&hp));
   cudaEvent_t e0, e1;
   MGR_TRY_CUDA(cudaEventCreate(&e0));
   MGR_TRY_CUDA(cudaEventCreate(&e1));
