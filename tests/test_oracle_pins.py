@@ -653,3 +653,24 @@ def test_ilu1_smoother_sweep(solve_sweeps):
             w = np.linalg.solve(D, y - Us @ w)
         want = w
     assert np.abs(got - want).max() <= 1e-10 * np.abs(want).max()
+
+
+def test_ilu1_two_sweeps_are_a_stationary_iteration():
+    # Two sweeps from zero: z1 = B v, z2 = z1 + B (v - A z1), B the one-sweep
+    # operator (approximate triangular solves); with exact solves, z2 is two
+    # steps of the iteration z <- z + (LU)^-1 (v - A z).
+    p = synth.two_phase(4, 3, 3, seed=5)
+    o1 = oracle.Oracle(p, global_smoother=[0, 2], global_sweeps=[0, 1], ilu_solve_sweeps=400)
+    o2 = oracle.Oracle(p, global_smoother=[0, 2], global_sweeps=[0, 2], ilu_solve_sweeps=400)
+    A = o1.scipy(oracle.Q_MGR_A, 1).toarray()
+    F, L, U = _ilu_parts(o1, 1)
+    n = A.shape[0]
+    v = np.random.default_rng(3).standard_normal(n)
+    z1 = np.linalg.solve(L @ U, v)
+    z2 = z1 + np.linalg.solve(L @ U, v - A @ z1)
+    assert np.abs(o1.global_relax(1, v) - z1).max() <= 1e-10 * np.abs(z1).max()
+    assert np.abs(o2.global_relax(1, v) - z2).max() <= 1e-10 * np.abs(z2).max()
+    # the second sweep reduces the error of the smoother (A z = v) on this SPD-like block
+    e1 = np.linalg.norm(v - A @ z1)
+    e2 = np.linalg.norm(v - A @ z2)
+    assert e2 < e1
