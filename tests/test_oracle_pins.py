@@ -674,3 +674,32 @@ def test_ilu1_two_sweeps_are_a_stationary_iteration():
     e1 = np.linalg.norm(v - A @ z1)
     e2 = np.linalg.norm(v - A @ z2)
     assert e2 < e1
+
+
+def test_fgmres_residual_history_is_the_krylov_minimum():
+    # With a fixed preconditioner M, flexible GMRES is right-preconditioned
+    # GMRES: after k steps its residual is min ||b - A M^-1 y|| over y in the
+    # Krylov space K_k(A M^-1, b).  The minimum is formed here from the dense
+    # operator A M^-1 (M^-1 applied to every unit vector) with a QR of the
+    # Krylov basis, independently of the oracle's Arnoldi and Givens updates.
+    p = synth.two_phase(4, 3, 3, seed=11)
+    o = oracle.Oracle(p)
+    n = p.n
+    A = p.to_scipy().toarray()
+    Minv = np.column_stack([o.apply(e) for e in np.eye(n)])
+    B = A @ Minv
+    b = p.rhs / np.linalg.norm(p.rhs)
+    r = o.fgmres(b, restart=50, maxit=30, rtol=1e-12, hist_cap=40)
+    hist = r["hist"]
+    K = np.empty((n, 0))
+    v = b.copy()
+    for k in range(1, min(len(hist) - 1, 12) + 1):
+        K = np.column_stack([K, v])
+        Q, _ = np.linalg.qr(K)            # orthonormal basis of K_k
+        Q, _ = np.linalg.qr(Q)
+        BQ = B @ Q
+        y, *_ = np.linalg.lstsq(BQ, b, rcond=None)
+        res = np.linalg.norm(b - BQ @ y)
+        assert abs(hist[k] - res) <= 1e-6 * max(res, 1e-8), (k, hist[k], res)
+        v = B @ Q[:, -1]
+    assert np.all(np.diff(hist[:13]) <= 1e-14)     # non-increasing within a cycle
