@@ -90,22 +90,41 @@ CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.a
                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
 
+def smi_device_id(device):
+    """The identifier nvidia-smi -i needs for a torch device: its UUID (or PCI
+    bus id), not the process-local index, which under CUDA_VISIBLE_DEVICES can
+    name another GPU of the machine."""
+    import torch
+    props = torch.cuda.get_device_properties(device)
+    uuid = getattr(props, "uuid", None)
+    if uuid is not None:
+        u = str(uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    bus = getattr(props, "pci_bus_id", None)
+    if bus is not None:
+        return "%08X:%02X:%02X.0" % (getattr(props, "pci_domain_id", 0), bus,
+                                     getattr(props, "pci_device_id", 0))
+    return str(device)
+
+
 class ClockSampler:
     """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
 
-    def __init__(self, gpu_index):
-        self.idx = gpu_index
+    def __init__(self, smi_id):
+        self.idx = smi_id
         self.proc = None
         self.path = None
+        self.out = None
 
     def __enter__(self):
         fd, self.path = tempfile.mkstemp(suffix=".csv")
         os.close(fd)
         try:
+            self.out = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--query-gpu={CLOCK_FIELDS}", "--format=csv,noheader,nounits",
                  "-i", str(self.idx), "-lms", "100"],
-                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+                stdout=self.out, stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
         time.sleep(0.3)
@@ -116,6 +135,9 @@ class ClockSampler:
         if self.proc:
             self.proc.terminate()
             self.proc.wait()
+        if self.out:
+            self.out.close()
+            self.out = None
 
     def summary(self):
         if not self.path or not os.path.exists(self.path):
@@ -287,7 +309,7 @@ def run_ours(args):
             step(prec, x)
         barrier()
         torch.cuda.synchronize()
-        sampler = ClockSampler(local) if clocks else None
+        sampler = ClockSampler(smi_device_id(local)) if clocks else None
         if sampler:
             sampler.__enter__()
         l0 = mgr.mgr_launch_count()

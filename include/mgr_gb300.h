@@ -45,7 +45,6 @@ extern "C" {
 #define MGR_ERR_OOM (-3)
 #define MGR_ERR_ZERO_DIAG (-4)   /* zero pivot: D_FF, a smoother block, the coarsest LU */
 #define MGR_ERR_BREAKDOWN (-5)   /* NaN/Inf in the Arnoldi process */
-#define MGR_ERR_TIMEOUT (-6)     /* a bounded device wait expired */
 #define MGR_ERR_COARSE (-7)      /* coarsest AMG level larger than the dense-LU cap */
 
 /* F-relaxation kinds (per MGR level) */
@@ -264,9 +263,13 @@ int mgr_splitmix64_device(const uint64_t* in, uint64_t* out, int64_t n, void* st
  *   (static __device__, held by every GPU that loads the library until exit).
  *   A V-cycle whose level vectors need more than 8 MiB is rejected with
  *   MGR_ERR_INVALID_ARG and a message on stderr; nothing is launched then.
- *   The first call on a device looks up the buffer's device address
- *   (cudaGetSymbolAddress, with that device current); make that first call
- *   before any stream capture.  Every call on a device shares the buffer and it
+ *   Every call made outside stream capture looks up the buffer's device
+ *   address (cudaGetSymbolAddress, with the device current), so a device reset
+ *   between calls is harmless; a call on a capturing stream reuses the address
+ *   of the last uncaptured call on that device, so make the first call on a
+ *   device before any stream capture (a captured first call is rejected with
+ *   MGR_ERR_INVALID_ARG), and make an uncaptured call again after a device
+ *   reset before capturing.  Every call on a device shares the buffer and it
  *   keeps the last call's contents (each vector in it is written before it is
  *   read, so nothing needs clearing); calls that overlap on the GPU (different
  *   streams, or host threads) race on it and must be serialised by the caller.
@@ -335,6 +338,18 @@ int64_t mgr_get_block_colors(mgr_handle_t h, int level, int32_t* out, int32_t* n
 /* Number of CUDA kernel launches this library has issued in this process
  * (all handles, all threads).  Lets a caller count the kernels of a region. */
 int64_t mgr_launch_count(void);
+
+/* Identifier of the sources this library was compiled from: the first 16 hex
+ * digits of a SHA-256 over the CUDA sources, this header and the compiler
+ * flags (the build step passes it in).  Lets a caller check that the loaded
+ * library was built from the sources it expects. */
+const char* mgr_build_id(void);
+
+/* Bytes of the library's memory pool on the current device: *used = held by
+ * live allocations (handle hierarchies and workspaces), *reserved = mapped by
+ * the pool, used or kept for reuse.  Either pointer may be NULL.  Host-side
+ * query; no device work. */
+int mgr_memory_usage(size_t* used, size_t* reserved);
 
 /* Device memory: the library allocates from its own stream-ordered memory
  * pool on each device, which keeps freed blocks mapped so that the next setup

@@ -57,17 +57,32 @@ class OrcOpts(C.Structure):
     ]
 
 
+def _hash():
+    import hashlib
+    with open(_SRC, "rb") as f:
+        return hashlib.sha256(f.read() + " ".join(_CFLAGS).encode()).hexdigest()[:16]
+
+
+_CFLAGS = ["-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared"]
+
+
 def build(force=False):
-    """Compile the oracle into oracle/_build (plain gcc, no GPU needed)."""
+    """Compile the oracle into oracle/_build (plain gcc, no GPU needed); a
+    build is reused only when the source hash recorded beside it matches."""
     os.makedirs(_BUILD, exist_ok=True)
-    if (not force and os.path.exists(_LIB)
-            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
-        return _LIB
+    stamp = _LIB + ".build_id"
+    want = _hash()
+    if not force and os.path.exists(_LIB) and os.path.exists(stamp):
+        with open(stamp) as f:
+            if f.read().strip() == want:
+                return _LIB
     tmp = _LIB + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
-           "-shared", "-o", tmp, _SRC, "-lm"]
+    cmd = ["gcc"] + _CFLAGS + ["-o", tmp, _SRC, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB)
+    with open(stamp + ".tmp", "w") as f:
+        f.write(want + "\n")
+    os.replace(stamp + ".tmp", stamp)
     return _LIB
 
 
@@ -94,6 +109,12 @@ def lib():
             L.orc_global_relax.argtypes = [P, C.c_int, P, P]
             L.orc_get_block_colors.restype = C.c_int64
             L.orc_get_block_colors.argtypes = [P, C.c_int, P, P]
+            L.orc_pmis.argtypes = [C.c_int64, P, P, C.c_uint64, C.c_int, C.c_int, P]
+            L.orc_interp.argtypes = [C.c_int64, P, P, P, P, P, P, P, C.c_int, P,
+                                     C.POINTER(C.POINTER(C.c_int64)),
+                                     C.POINTER(C.POINTER(C.c_int32)),
+                                     C.POINTER(C.POINTER(C.c_double))]
+            L.orc_free_buffer.argtypes = [P]
             L.orc_splitmix64.restype = C.c_uint64
             L.orc_splitmix64.argtypes = [C.c_uint64]
             _lib = L
@@ -265,6 +286,48 @@ class Oracle:
         out = np.zeros(n)
         lib().orc_get_l1(self.h, slot, lvl, _p(out))
         return out
+
+
+def pmis(S, seed=0, slot=0, level=0):
+    """PMIS C/F marks (+1/-1) of the strength graph S (scipy CSR, n x n)."""
+    S = S.tocsr()
+    S.sort_indices()
+    rp = np.ascontiguousarray(S.indptr, dtype=np.int64)
+    ci = np.ascontiguousarray(S.indices, dtype=np.int32)
+    cf = np.zeros(S.shape[0], dtype=np.int8)
+    if lib().orc_pmis(S.shape[0], _p(rp), _p(ci), seed, slot, level, _p(cf)) != 0:
+        raise ValueError("orc_pmis failed")
+    return cf
+
+
+def interp(A, S, cf, comp=None, pmax=0):
+    """Direct interpolation P (scipy CSR) of A with the given strength graph S,
+    C/F marks and components."""
+    import scipy.sparse as sp
+    A = A.tocsr()
+    A.sort_indices()
+    S = S.tocsr()
+    S.sort_indices()
+    n = A.shape[0]
+    arrs = [np.ascontiguousarray(A.indptr, dtype=np.int64),
+            np.ascontiguousarray(A.indices, dtype=np.int32),
+            np.ascontiguousarray(A.data, dtype=np.float64),
+            np.ascontiguousarray(S.indptr, dtype=np.int64),
+            np.ascontiguousarray(S.indices, dtype=np.int32),
+            np.ascontiguousarray(np.zeros(n) if comp is None else comp, dtype=np.int32),
+            np.ascontiguousarray(cf, dtype=np.int8)]
+    dims = np.zeros(3, dtype=np.int64)
+    prp, pci, pv = C.POINTER(C.c_int64)(), C.POINTER(C.c_int32)(), C.POINTER(C.c_double)()
+    if lib().orc_interp(n, *[_p(a) for a in arrs], pmax, _p(dims), C.byref(prp), C.byref(pci),
+                        C.byref(pv)) != 0:
+        raise ValueError("orc_interp failed")
+    nr, nc, nnz = (int(x) for x in dims)
+    rp = np.ctypeslib.as_array(prp, shape=(nr + 1,)).copy()
+    ci = np.ctypeslib.as_array(pci, shape=(max(nnz, 1),))[:nnz].copy()
+    v = np.ctypeslib.as_array(pv, shape=(max(nnz, 1),))[:nnz].copy()
+    for q in (prp, pci, pv):
+        lib().orc_free_buffer(C.cast(q, C.c_void_p))
+    return sp.csr_matrix((v, ci, rp), shape=(nr, nc))
 
 
 def splitmix64(x):

@@ -1410,3 +1410,46 @@ int64_t orc_get_l1(void *hv, int slot, int lvl, double *out) {
   if (out) memcpy(out, g->lev[lvl].l1, sizeof(double) * (size_t)n);
   return n;
 }
+
+/* ---- direct entry to two AMG steps, for their pins ------------------------ */
+
+/* PMIS on a caller-given strength graph S (CSR, n x n, columns ascending):
+ * cf[i] = +1 (C) / -1 (F), with the weight key of AMG slot `slot`, level
+ * `level`. */
+int orc_pmis(int64_t n, const int64_t *srp, const int32_t *sci, uint64_t seed, int slot,
+             int level, int8_t *cf) {
+  if (n <= 0) return ORC_ERR_ARG;
+  ocsr s;
+  s.nr = n; s.nc = n; s.nnz = srp[n];
+  s.rp = (int64_t *)srp; s.ci = (int32_t *)sci;
+  s.v = xcalloc((size_t)s.nnz, sizeof(double));   /* pattern values, as the strength rule writes */
+  for (int64_t k = 0; k < s.nnz; k++) s.v[k] = 1.0;
+  amg_pmis(&s, seed, slot, level, cf);
+  free(s.v);
+  return ORC_OK;
+}
+
+/* Direct interpolation on caller-given A, strength graph S (it need not come
+ * from the strength rule: positive couplings may be strong), components and
+ * C/F marks; P (n x nc) is returned through *p_rp, *p_ci, *p_v, allocated here
+ * and released with orc_free_buffer. */
+int orc_interp(int64_t n, const int64_t *rp, const int32_t *ci, const double *v,
+               const int64_t *srp, const int32_t *sci, const int32_t *comp, const int8_t *cf,
+               int pmax, int64_t *dims, int64_t **p_rp, int32_t **p_ci, double **p_v) {
+  if (n <= 0) return ORC_ERR_ARG;
+  ocsr a, s, p;
+  a.nr = n; a.nc = n; a.nnz = rp[n];
+  a.rp = (int64_t *)rp; a.ci = (int32_t *)ci; a.v = (double *)v;
+  s.nr = n; s.nc = n; s.nnz = srp[n];
+  s.rp = (int64_t *)srp; s.ci = (int32_t *)sci;
+  s.v = xcalloc((size_t)s.nnz, sizeof(double));
+  for (int64_t k = 0; k < s.nnz; k++) s.v[k] = 1.0;
+  int64_t nc = 0;
+  amg_interp(&a, &s, comp, cf, pmax, &p, &nc);
+  free(s.v);
+  dims[0] = p.nr; dims[1] = nc; dims[2] = p.nnz;
+  *p_rp = p.rp; *p_ci = p.ci; *p_v = p.v;
+  return ORC_OK;
+}
+
+void orc_free_buffer(void *q) { free(q); }

@@ -2,13 +2,16 @@
 compiled in parallel, linked into _build/libmgr_gb300.so.
 
 Run as ``python -m paper_1904_05960_gb300.build`` or through
-``__graft_entry__.build()``.  The setup kernels are compiled with
+``__graft_entry__.build()``.  A build is reused only when the source hash
+recorded beside it (and compiled into it, ``mgr_build_id``) equals the hash of
+the current sources and flags.  The setup kernels are compiled with
 ``-fmad=false`` so that no multiply-add is contracted there: the setup's
 integer outputs (C/F marks, strength graphs, sparsity patterns) depend on
 separately rounded products and sums.
 """
 from __future__ import annotations
 
+import hashlib
 import os
 import shutil
 import subprocess
@@ -19,6 +22,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libmgr_gb300.so")
+STAMP = os.path.join(BUILD, "libmgr_gb300.build_id")
 ROOT = os.path.dirname(HERE)
 
 SOURCES = ["setup.cu", "apply.cu", "krylov.cu", "capi.cu", "noalloc.cu", "batched.cu"]
@@ -33,21 +37,46 @@ def nvcc():
     raise RuntimeError("nvcc not found: the CUDA toolkit is required to build libmgr_gb300")
 
 
-def _deps():
-    files = [os.path.join(CSRC, f) for f in os.listdir(CSRC)]
-    files.append(os.path.join(ROOT, "include", "mgr_gb300.h"))
-    return max(os.path.getmtime(f) for f in files)
-
-
-def build(force=False, verbose=False):
-    os.makedirs(BUILD, exist_ok=True)
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _deps():
-        return LIB
-    cc = nvcc()
+def _flags(verbose=False):
     common = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
                      "-I", os.path.join(ROOT, "include")]
     if verbose:
         common += ["-Xptxas", "-v"]
+    return common
+
+
+def source_hash():
+    """First 16 hex digits of a SHA-256 over every CUDA source, the C header
+    and the compiler flags: the identity of a build.  It is compiled into the
+    library (mgr_build_id) and written beside it; build() rebuilds whenever
+    the recorded hash differs, whatever the file times say."""
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(CSRC)):
+        with open(os.path.join(CSRC, f), "rb") as fh:
+            h.update(f.encode() + b"\0" + fh.read() + b"\0")
+    with open(os.path.join(ROOT, "include", "mgr_gb300.h"), "rb") as fh:
+        h.update(fh.read())
+    flags = [f.replace(ROOT, "<root>") for f in _flags()]
+    h.update(" ".join(flags + sorted(NO_FMAD)).encode())
+    return h.hexdigest()[:16]
+
+
+def built_hash():
+    """Hash recorded by the last successful build, or None."""
+    try:
+        with open(STAMP) as f:
+            return f.read().strip()
+    except OSError:
+        return None
+
+
+def build(force=False, verbose=False):
+    os.makedirs(BUILD, exist_ok=True)
+    want = source_hash()
+    if not force and os.path.exists(LIB) and built_hash() == want:
+        return LIB
+    cc = nvcc()
+    common = _flags(verbose) + [f'-DMGR_BUILD_ID="{want}"']
 
     def compile_one(src):
         obj = os.path.join(BUILD, src.replace(".cu", ".o"))
@@ -69,6 +98,9 @@ def build(force=False, verbose=False):
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
     os.replace(tmp, LIB)
+    with open(STAMP + ".tmp", "w") as f:
+        f.write(want + "\n")
+    os.replace(STAMP + ".tmp", STAMP)
     return LIB
 
 

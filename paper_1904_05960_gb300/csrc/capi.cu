@@ -117,7 +117,6 @@ const char* mgr_error_string(int code) {
     case MGR_ERR_OOM: return "out of device memory";
     case MGR_ERR_ZERO_DIAG: return "zero pivot (D_FF, smoother block or coarsest LU)";
     case MGR_ERR_BREAKDOWN: return "NaN/Inf in the Arnoldi process";
-    case MGR_ERR_TIMEOUT: return "bounded device wait expired";
     case MGR_ERR_COARSE: return "coarsest AMG level exceeds the dense-LU cap";
   }
   return "unknown status";
@@ -360,6 +359,25 @@ int mgr_splitmix64_device(const uint64_t* in, uint64_t* out, int64_t n, void* st
 }
 
 int64_t mgr_launch_count(void) { return (int64_t)g_launches.load(); }
+
+#ifndef MGR_BUILD_ID
+#define MGR_BUILD_ID "unversioned"
+#endif
+const char* mgr_build_id(void) { return MGR_BUILD_ID; }
+
+int mgr_memory_usage(size_t* used, size_t* reserved) {
+  (void)cudaGetLastError();  // errors of earlier calls are not this call's
+  if (used) *used = 0;
+  if (reserved) *reserved = 0;
+  cudaMemPool_t mp = lib_pool();
+  if (!mp) return MGR_SUCCESS;
+  uint64_t u = 0, r = 0;
+  MGR_TRY_CUDA(cudaMemPoolGetAttribute(mp, cudaMemPoolAttrUsedMemCurrent, &u));
+  MGR_TRY_CUDA(cudaMemPoolGetAttribute(mp, cudaMemPoolAttrReservedMemCurrent, &r));
+  if (used) *used = (size_t)u;
+  if (reserved) *reserved = (size_t)r;
+  return MGR_SUCCESS;
+}
 
 int mgr_trim_memory(size_t keep_bytes) {
   (void)cudaGetLastError();  // errors of earlier calls are not this call's

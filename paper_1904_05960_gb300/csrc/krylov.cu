@@ -296,18 +296,26 @@ int fgmres_run(Handle* h, const mgr_matrix_t* A, const double* b, double* x,
   // pinned host mirror for the per-iteration readbacks, leased per host thread
   double* hp = nullptr;
   MGR_TRY(pinned_scratch(&hp));
-  cudaEvent_t e0, e1;
-  MGR_TRY_CUDA(cudaEventCreate(&e0));
-  MGR_TRY_CUDA(cudaEventCreate(&e1));
+  // events are destroyed on every return path
+  struct Events {
+    cudaEvent_t e[7] = {};
+    ~Events() {
+      for (auto& x : e)
+        if (x) cudaEventDestroy(x);
+    }
+  } ev;
+  MGR_TRY_CUDA(cudaEventCreate(&ev.e[0]));
+  MGR_TRY_CUDA(cudaEventCreate(&ev.e[1]));
+  cudaEvent_t e0 = ev.e[0], e1 = ev.e[1];
   MGR_TRY_CUDA(cudaEventRecord(e0, s));
 
   std::vector<double> H((size_t)(m + 1) * m, 0.0), cs(m), sn(m), g(m + 1), y(m);
   // per-phase device times (MGR_TRACE): apply, A z, Gram-Schmidt, gaps
   const bool tr = g_trace.on || getenv("MGR_TRACE") != nullptr;
-  cudaEvent_t tev[5];
+  cudaEvent_t* tev = ev.e + 2;   // 5 trace events
   double tsum[4] = {0, 0, 0, 0};
   if (tr)
-    for (auto& e : tev) cudaEventCreate(&e);
+    for (int q = 0; q < 5; q++) cudaEventCreate(&tev[q]);
   MGR_LAUNCH k_fill0<<<grid_for(n, KB), KB, 0, s>>>(x, n);
   // ||b||
   mdot(h, b, n, 1, b, n, h->hred, 0, s);
@@ -442,14 +450,11 @@ int fgmres_run(Handle* h, const mgr_matrix_t* A, const double* b, double* x,
   if (tr) {
     fprintf(stderr, "mgr_trace fgmres %d iters: apply %.3f ms, A*z %.3f ms, Gram-Schmidt %.3f ms, "
                     "between iterations %.3f ms (totals)\n", iters, tsum[0], tsum[1], tsum[2], tsum[3]);
-    for (auto& e : tev) cudaEventDestroy(e);
   }
   MGR_TRY_CUDA(cudaEventRecord(e1, s));
   MGR_TRY_CUDA(cudaEventSynchronize(e1));
   float ms = 0.f;
   cudaEventElapsedTime(&ms, e0, e1);
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
   if (info) {
     info->iters = iters;
     info->restarts = restarts;

@@ -11,8 +11,8 @@
 // That buffer is a file-scope static __device__ array, so every GPU that loads
 // the library holds MGR_NOALLOC_SCRATCH_BYTES of it until the process exits.
 // In host code its name is only a host-side stand-in, not a device address; the
-// device address is obtained once per device with cudaGetSymbolAddress (with
-// that device current) and passed to the kernels.  All calls on a device share
+// device address is obtained with cudaGetSymbolAddress (with the device
+// current) and passed to the kernels.  All calls on a device share
 // the buffer, and it keeps the last call's contents.
 #include <cuda_runtime.h>
 
@@ -30,14 +30,22 @@ namespace {
 std::mutex g_noalloc_mu;
 void* g_noalloc_addr[MGR_NOALLOC_MAX_DEVICES] = {};
 
-// Device address of the scratch buffer on the current device; looked up on the
-// first call per device.
-int scratch_address(void** out) {
+// Device address of the scratch buffer on the current device.  Looked up
+// again on every call made outside stream capture (a cheap host-side query), so
+// that a device reset or a new primary context never leaves a stale address in
+// use; during capture the address of the last uncaptured call on this device
+// is used, and without one the call is rejected.
+int scratch_address(cudaStream_t s, void** out) {
   int dev = 0;
   MGR_TRY_CUDA(cudaGetDevice(&dev));
   if (dev < 0 || dev >= MGR_NOALLOC_MAX_DEVICES) return MGR_ERR_INVALID_ARG;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) {
+    (void)cudaGetLastError();
+    cap = cudaStreamCaptureStatusActive;
+  }
   std::lock_guard<std::mutex> lock(g_noalloc_mu);
-  if (!g_noalloc_addr[dev]) {
+  if (cap == cudaStreamCaptureStatusNone) {
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess || !p) {
@@ -46,6 +54,10 @@ int scratch_address(void** out) {
       return MGR_ERR_CUDA;
     }
     g_noalloc_addr[dev] = p;
+  } else if (!g_noalloc_addr[dev]) {
+    fprintf(stderr, "mgr_vcycle_noalloc: the first call on a device must come before any "
+                    "stream capture\n");
+    return MGR_ERR_INVALID_ARG;
   }
   *out = g_noalloc_addr[dev];
   return MGR_SUCCESS;
@@ -70,6 +82,6 @@ extern "C" int mgr_vcycle_noalloc(mgr_handle_t hh, int slot, const double* b, do
     return MGR_ERR_INVALID_ARG;
   }
   void* ws = nullptr;
-  MGR_TRY(scratch_address(&ws));
+  MGR_TRY(scratch_address((cudaStream_t)stream, &ws));
   return apply_vcycle64_ws(h, g, b, x, ws, (cudaStream_t)stream);
 }

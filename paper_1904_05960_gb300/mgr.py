@@ -29,7 +29,7 @@ EXPORTED = ["mgr_options_default", "fgmres_options_default", "mgr_setup", "mgr_a
             "mgr_amg_levels", "mgr_get_cf", "mgr_vcycle", "mgr_splitmix64_device",
             "mgr_launch_count", "mgr_trim_memory", "mgr_solve_host", "mgr_vcycle_noalloc", "mgr_setup_batched",
             "fgmres_solve_batched", "mgr_batch_info", "mgr_batch_handle", "mgr_destroy_batched",
-            "mgr_get_block_colors"]
+            "mgr_get_block_colors", "mgr_build_id", "mgr_memory_usage"]
 
 
 class MgrMatrix(C.Structure):
@@ -117,6 +117,9 @@ def lib():
             L.mgr_launch_count.argtypes = []
             L.mgr_launch_count.restype = I64
             L.mgr_trim_memory.argtypes = [C.c_size_t]
+            L.mgr_build_id.argtypes = []
+            L.mgr_build_id.restype = C.c_char_p
+            L.mgr_memory_usage.argtypes = [C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)]
             L.mgr_solve_host.argtypes = [C.POINTER(MgrMatrix), P, P, C.POINTER(MgrOptions),
                                          C.POINTER(FgmresOptions), C.POINTER(FgmresInfo), P]
             _lib = L
@@ -401,6 +404,18 @@ def mgr_get_block_colors(h, level):
 def mgr_launch_count():
     """Kernel launches issued by the library so far in this process."""
     return int(lib().mgr_launch_count())
+
+
+def mgr_build_id():
+    """Source hash the loaded library was compiled from."""
+    return lib().mgr_build_id().decode()
+
+
+def mgr_memory_usage():
+    """(used, reserved) bytes of the library's device memory pool."""
+    u, r = C.c_size_t(0), C.c_size_t(0)
+    _check(lib().mgr_memory_usage(C.byref(u), C.byref(r)), "mgr_memory_usage")
+    return u.value, r.value
 
 
 def mgr_trim_memory(keep_bytes=0):

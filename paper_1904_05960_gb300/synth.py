@@ -34,6 +34,7 @@ the opposite corner cell with WI = 1 and p_bh = -1.
 from __future__ import annotations
 
 from dataclasses import dataclass, field
+import os
 from fractions import Fraction
 
 import numpy as np
@@ -168,13 +169,21 @@ def _compress(cols, vals, valid):
     return counts, cols[keep].astype(np.int32), vals[keep]
 
 
+def _chunks(total, size):
+    return [(a, min(a + size, total)) for a in range(0, total, size)]
+
+
 def build_poromechanics(nx, ny, nz, *, two_phase=True, E=1e4, nu=0.25, biot=1.0,
                         dt=1.0, perm=None, sat=None, inv_N=None, phi0=0.2,
                         mu_w=1.0, mu_o=5.0, wi=1.0, p_bh=-1.0, rhs_seed=1,
-                        meta=None):
+                        meta=None, threads=None, chunk_rows=65536):
     """Assemble the fully implicit Jacobian on an nx*ny*nz grid of unit cells.
 
     E may be a scalar or a per-cell array (nz, ny, nx); perm a per-cell array.
+    Rows are assembled in chunks of about chunk_rows points (vertices, then
+    cells) on `threads` threads (default: the machine's cores, at most 16), so
+    that the working memory stays a small multiple of the final CSR; the result
+    does not depend on either setting.
     """
     nnx, nny, nnz_ = nx + 1, ny + 1, nz + 1
     n_nodes = nnx * nny * nnz_
@@ -184,6 +193,8 @@ def build_poromechanics(nx, ny, nz, *, two_phase=True, E=1e4, nu=0.25, biot=1.0,
     n = n_u + ncd * n_cells
     if inv_N is None:
         inv_N = 1e-3 if two_phase else 0.0
+    if threads is None:
+        threads = max(1, min(16, os.cpu_count() or 1))
 
     Ec = np.broadcast_to(np.asarray(E, dtype=np.float64), (nz, ny, nx))
     nuc = np.broadcast_to(np.asarray(nu, dtype=np.float64), (nz, ny, nx))
@@ -193,17 +204,17 @@ def build_poromechanics(nx, ny, nz, *, two_phase=True, E=1e4, nu=0.25, biot=1.0,
     mu_p = np.zeros((nz + 2, ny + 2, nx + 2))
     lam_p[1:-1, 1:-1, 1:-1] = lam_c
     mu_p[1:-1, 1:-1, 1:-1] = mu_c
-
-    iz, iy, ix = np.meshgrid(np.arange(nnz_), np.arange(nny), np.arange(nnx), indexing="ij")
-    iz, iy, ix = iz.ravel(), iy.ravel(), ix.ravel()          # node order: x fastest
-    node_id = ix + nnx * (iy + nny * iz)
+    del lam_c, mu_c
 
     # --- Dirichlet set: bottom fixed, rollers on the four sides ------------
-    fixed = np.zeros((n_nodes, 3), dtype=bool)
-    fixed[iz == 0, :] = True
-    fixed[(ix == 0) | (ix == nx), 0] = True
-    fixed[(iy == 0) | (iy == ny), 1] = True
-    fixed_dof = fixed.ravel()                                # index 3*node+comp
+    # (index 3*node+comp; node order: x fastest)
+    fixed = np.zeros((nnz_, nny, nnx, 3), dtype=bool)
+    fixed[0, :, :, :] = True
+    fixed[:, :, 0, 0] = True
+    fixed[:, :, nx, 0] = True
+    fixed[:, 0, :, 1] = True
+    fixed[:, ny, :, 1] = True
+    fixed_dof = fixed.reshape(-1)
 
     offs = [(dx, dy, dz) for dz in (-1, 0, 1) for dy in (-1, 0, 1) for dx in (-1, 0, 1)]
     eoffs = [(ox, oy, oz) for oz in (-1, 0) for oy in (-1, 0) for ox in (-1, 0)]
@@ -215,59 +226,66 @@ def build_poromechanics(nx, ny, nz, *, two_phase=True, E=1e4, nu=0.25, biot=1.0,
 
     # ---------------- displacement rows: 27*3 u columns + 8 p columns ------
     Wu = 27 * 3 + 8
-    ucols = np.zeros((n_nodes, 3, Wu), dtype=np.int64)
-    uvals = np.zeros((n_nodes, 3, Wu))
-    uvalid = np.zeros((n_nodes, 3, Wu), dtype=bool)
-    for t, (dx, dy, dz) in enumerate(offs):
-        jx, jy, jz = ix + dx, iy + dy, iz + dz
-        inr = (jx >= 0) & (jx < nnx) & (jy >= 0) & (jy < nny) & (jz >= 0) & (jz < nnz_)
-        nb = np.where(inr, jx + nnx * (jy + nny * jz), 0)
-        blk = np.zeros((n_nodes, 3, 3))
-        for (ox, oy, oz) in eoffs:
-            ax, ay, az = -ox, -oy, -oz
-            bx, by, bz = dx - ox, dy - oy, dz - oz
-            if not (0 <= bx <= 1 and 0 <= by <= 1 and 0 <= bz <= 1):
-                continue
-            a = ax + 2 * ay + 4 * az
-            b = bx + 2 * by + 4 * bz
-            cl = lam_p[iz + oz + 1, iy + oy + 1, ix + ox + 1]
-            cm = mu_p[iz + oz + 1, iy + oy + 1, ix + ox + 1]
-            kl = KLAM[3 * a:3 * a + 3, 3 * b:3 * b + 3]
-            km = KMU[3 * a:3 * a + 3, 3 * b:3 * b + 3]
-            blk += cl[:, None, None] * kl[None] + cm[:, None, None] * km[None]
-        for i in range(3):
-            for j in range(3):
-                ucols[:, i, 3 * t + j] = 3 * nb + j
-                uvals[:, i, 3 * t + j] = blk[:, i, j]
-                uvalid[:, i, 3 * t + j] = inr
-    for t, (ox, oy, oz) in enumerate(eoffs):
-        cx, cy, cz = ix + ox, iy + oy, iz + oz
-        inr = (cx >= 0) & (cx < nx) & (cy >= 0) & (cy < ny) & (cz >= 0) & (cz < nz)
-        cid = cx + nx * (cy + ny * cz)
-        a = (-ox) + 2 * (-oy) + 4 * (-oz)
-        for i in range(3):
-            ucols[:, i, 81 + t] = np.where(inr, cell_dof(cid, pcomp), 0)
-            uvals[:, i, 81 + t] = -biot * QDIV[3 * a + i]
-            uvalid[:, i, 81 + t] = inr
-    ucols = ucols.reshape(n_u, Wu)
-    uvals = uvals.reshape(n_u, Wu)
-    uvalid = uvalid.reshape(n_u, Wu)
-    # Dirichlet: remove fixed columns everywhere, fixed rows become identity.
-    colfixed = np.zeros_like(uvalid)
-    colfixed[:, :81] = fixed_dof[ucols[:, :81]]
-    uvalid &= ~colfixed
-    uvalid[fixed_dof, :] = False
     diag_slot = 3 * 13  # offset (0,0,0) is template entry 13
-    rows_fixed = np.nonzero(fixed_dof)[0]
-    comp_fixed = rows_fixed % 3
-    uvals[rows_fixed, diag_slot + comp_fixed] = 1.0
-    uvalid[rows_fixed, diag_slot + comp_fixed] = True
-    ucnt, ucol_c, uval_c = _compress(ucols, uvals, uvalid)
+
+    def u_rows(a0, a1):
+        node = np.arange(a0, a1, dtype=np.int64)
+        m = a1 - a0
+        ix = node % nnx
+        iy = (node // nnx) % nny
+        iz = node // (nnx * nny)
+        ucols = np.zeros((m, 3, Wu), dtype=np.int64)
+        uvals = np.zeros((m, 3, Wu))
+        uvalid = np.zeros((m, 3, Wu), dtype=bool)
+        for t, (dx, dy, dz) in enumerate(offs):
+            jx, jy, jz = ix + dx, iy + dy, iz + dz
+            inr = (jx >= 0) & (jx < nnx) & (jy >= 0) & (jy < nny) & (jz >= 0) & (jz < nnz_)
+            nb = np.where(inr, jx + nnx * (jy + nny * jz), 0)
+            blk = np.zeros((m, 3, 3))
+            for (ox, oy, oz) in eoffs:
+                ax, ay, az = -ox, -oy, -oz
+                bx, by, bz = dx - ox, dy - oy, dz - oz
+                if not (0 <= bx <= 1 and 0 <= by <= 1 and 0 <= bz <= 1):
+                    continue
+                a = ax + 2 * ay + 4 * az
+                b = bx + 2 * by + 4 * bz
+                cl = lam_p[iz + oz + 1, iy + oy + 1, ix + ox + 1]
+                cm = mu_p[iz + oz + 1, iy + oy + 1, ix + ox + 1]
+                kl = KLAM[3 * a:3 * a + 3, 3 * b:3 * b + 3]
+                km = KMU[3 * a:3 * a + 3, 3 * b:3 * b + 3]
+                blk += cl[:, None, None] * kl[None] + cm[:, None, None] * km[None]
+            for i in range(3):
+                for j in range(3):
+                    ucols[:, i, 3 * t + j] = 3 * nb + j
+                    uvals[:, i, 3 * t + j] = blk[:, i, j]
+                    uvalid[:, i, 3 * t + j] = inr
+        for t, (ox, oy, oz) in enumerate(eoffs):
+            cx, cy, cz = ix + ox, iy + oy, iz + oz
+            inr = (cx >= 0) & (cx < nx) & (cy >= 0) & (cy < ny) & (cz >= 0) & (cz < nz)
+            cid = cx + nx * (cy + ny * cz)
+            a = (-ox) + 2 * (-oy) + 4 * (-oz)
+            for i in range(3):
+                ucols[:, i, 81 + t] = np.where(inr, cell_dof(cid, pcomp), 0)
+                uvals[:, i, 81 + t] = -biot * QDIV[3 * a + i]
+                uvalid[:, i, 81 + t] = inr
+        ucols = ucols.reshape(3 * m, Wu)
+        uvals = uvals.reshape(3 * m, Wu)
+        uvalid = uvalid.reshape(3 * m, Wu)
+        # Dirichlet: remove fixed columns everywhere, fixed rows become identity.
+        uvalid[:, :81] &= ~fixed_dof[ucols[:, :81]]
+        rfix = fixed_dof[3 * a0:3 * a1]
+        uvalid[rfix, :] = False
+        rows_fixed = np.nonzero(rfix)[0]
+        comp_fixed = (3 * a0 + rows_fixed) % 3
+        uvals[rows_fixed, diag_slot + comp_fixed] = 1.0
+        uvalid[rows_fixed, diag_slot + comp_fixed] = True
+        return _compress(ucols, uvals, uvalid)
 
     # ---------------- cell rows ------------------------------------------
-    cz_, cy_, cx_ = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
-    cz_, cy_, cx_ = cz_.ravel(), cy_.ravel(), cx_.ravel()
-    cid_all = cx_ + nx * (cy_ + ny * cz_)
+    cid_all = np.arange(n_cells, dtype=np.int64)
+    cx_ = cid_all % nx
+    cy_ = (cid_all // nx) % ny
+    cz_ = cid_all // (nx * ny)
     k = np.asarray(perm, dtype=np.float64).reshape(n_cells)
     s = (np.asarray(sat, dtype=np.float64).reshape(n_cells) if two_phase else None)
 
@@ -282,6 +300,7 @@ def build_poromechanics(nx, ny, nz, *, two_phase=True, E=1e4, nu=0.25, biot=1.0,
     d = cx_ + cy_ + cz_
     dmax = max((nx - 1) + (ny - 1) + (nz - 1), 1)
     pst = 1.0 - d / dmax
+    del d
 
     def lam(sv):
         return sv * sv / mu_w, (1.0 - sv) * (1.0 - sv) / mu_o
@@ -289,6 +308,9 @@ def build_poromechanics(nx, ny, nz, *, two_phase=True, E=1e4, nu=0.25, biot=1.0,
     def dlam(sv):
         return 2.0 * sv / mu_w, -2.0 * (1.0 - sv) / mu_o
 
+    # Each cell is the K side of at most one face per axis and the L side of
+    # at most one, so the index arrays of one update hold no repeats and a
+    # plain indexed add is exact.
     for axis, (slot_plus, slot_minus) in enumerate(((4, 2), (5, 1), (6, 0))):
         step = (1, nx, nx * ny)[axis]
         coord = (cx_, cy_, cz_)[axis]
@@ -307,18 +329,18 @@ def build_poromechanics(nx, ny, nz, *, two_phase=True, E=1e4, nu=0.25, biot=1.0,
             for ph, lm, dl in (("s", lw, dlw), ("p", lo, dlo)):
                 Jp = J[(ph, "p")]
                 Js = J[(ph, "s")]
-                np.add.at(Jp, (K, SELF), T * lm)
-                np.add.at(Jp, (K, slot_plus), -T * lm)
-                np.add.at(Jp, (L, slot_minus), -T * lm)
-                np.add.at(Jp, (L, SELF), T * lm)
-                np.add.at(Js, (K, slotU_K), T * dl * dp)
-                np.add.at(Js, (L, slotU_L), -T * dl * dp)
+                Jp[K, SELF] += T * lm
+                Jp[K, slot_plus] += -T * lm
+                Jp[L, slot_minus] += -T * lm
+                Jp[L, SELF] += T * lm
+                Js[K, slotU_K] += T * dl * dp
+                Js[L, slotU_L] += -T * dl * dp
         else:
             Jp = J[("p", "p")]
-            np.add.at(Jp, (K, SELF), T)
-            np.add.at(Jp, (K, slot_plus), -T)
-            np.add.at(Jp, (L, slot_minus), -T)
-            np.add.at(Jp, (L, SELF), T)
+            Jp[K, SELF] += T
+            Jp[K, slot_plus] += -T
+            Jp[L, slot_minus] += -T
+            Jp[L, SELF] += T
     if two_phase:
         J[("s", "s")][:, SELF] += phi0 / dt
         J[("s", "p")][:, SELF] += s * inv_N / dt
@@ -338,43 +360,64 @@ def build_poromechanics(nx, ny, nz, *, two_phase=True, E=1e4, nu=0.25, biot=1.0,
 
     # u columns of a cell row: its 8 vertices (ascending node id)
     Wc = 24 + 7 * ncd
-    ccols = np.zeros((n_cells, ncd, Wc), dtype=np.int64)
-    cvals = np.zeros((n_cells, ncd, Wc))
-    cvalid = np.zeros((n_cells, ncd, Wc), dtype=bool)
-    for a in range(8):
-        ax, ay, az = _corner(a)
-        nid = (cx_ + ax) + nnx * ((cy_ + ay) + nny * (cz_ + az))
-        for i in range(3):
-            for r in range(ncd):
-                if two_phase:
-                    coef = biot * (s if r == 0 else (1.0 - s)) / dt
-                else:
-                    coef = np.full(n_cells, biot / dt)
-                ccols[:, r, 3 * a + i] = 3 * nid + i
-                cvals[:, r, 3 * a + i] = coef * QDIV[3 * a + i]
-                cvalid[:, r, 3 * a + i] = ~fixed_dof[3 * nid + i]
-    for t, (dx, dy, dz) in enumerate(nbr_off):
-        jx, jy, jz = cx_ + dx, cy_ + dy, cz_ + dz
-        inr = (jx >= 0) & (jx < nx) & (jy >= 0) & (jy < ny) & (jz >= 0) & (jz < nz)
-        nb = np.where(inr, jx + nx * (jy + ny * jz), 0)
-        if two_phase:
-            for r, ph in enumerate(("s", "p")):
-                for q, var in enumerate(("s", "p")):
-                    ccols[:, r, 24 + 2 * t + q] = cell_dof(nb, q)
-                    cvals[:, r, 24 + 2 * t + q] = J[(ph, var)][:, t]
-                    cvalid[:, r, 24 + 2 * t + q] = inr
-        else:
-            ccols[:, 0, 24 + t] = cell_dof(nb, 0)
-            cvals[:, 0, 24 + t] = J[("p", "p")][:, t]
-            cvalid[:, 0, 24 + t] = inr
-    ccnt, ccol_c, cval_c = _compress(ccols.reshape(-1, Wc), cvals.reshape(-1, Wc),
-                                     cvalid.reshape(-1, Wc))
 
-    counts = np.concatenate([ucnt, ccnt]).astype(np.int64)
+    def cell_rows(c0, c1):
+        m = c1 - c0
+        cx, cy, cz = cx_[c0:c1], cy_[c0:c1], cz_[c0:c1]
+        sc = s[c0:c1] if two_phase else None
+        ccols = np.zeros((m, ncd, Wc), dtype=np.int64)
+        cvals = np.zeros((m, ncd, Wc))
+        cvalid = np.zeros((m, ncd, Wc), dtype=bool)
+        for a in range(8):
+            ax, ay, az = _corner(a)
+            nid = (cx + ax) + nnx * ((cy + ay) + nny * (cz + az))
+            for i in range(3):
+                for r in range(ncd):
+                    if two_phase:
+                        coef = biot * (sc if r == 0 else (1.0 - sc)) / dt
+                    else:
+                        coef = np.full(m, biot / dt)
+                    ccols[:, r, 3 * a + i] = 3 * nid + i
+                    cvals[:, r, 3 * a + i] = coef * QDIV[3 * a + i]
+                    cvalid[:, r, 3 * a + i] = ~fixed_dof[3 * nid + i]
+        for t, (dx, dy, dz) in enumerate(nbr_off):
+            jx, jy, jz = cx + dx, cy + dy, cz + dz
+            inr = (jx >= 0) & (jx < nx) & (jy >= 0) & (jy < ny) & (jz >= 0) & (jz < nz)
+            nb = np.where(inr, jx + nx * (jy + ny * jz), 0)
+            if two_phase:
+                for r, ph in enumerate(("s", "p")):
+                    for q, var in enumerate(("s", "p")):
+                        ccols[:, r, 24 + 2 * t + q] = cell_dof(nb, q)
+                        cvals[:, r, 24 + 2 * t + q] = J[(ph, var)][c0:c1, t]
+                        cvalid[:, r, 24 + 2 * t + q] = inr
+            else:
+                ccols[:, 0, 24 + t] = cell_dof(nb, 0)
+                cvals[:, 0, 24 + t] = J[("p", "p")][c0:c1, t]
+                cvalid[:, 0, 24 + t] = inr
+        return _compress(ccols.reshape(-1, Wc), cvals.reshape(-1, Wc), cvalid.reshape(-1, Wc))
+
+    jobs = ([(u_rows, a, b) for a, b in _chunks(n_nodes, chunk_rows)]
+            + [(cell_rows, a, b) for a, b in _chunks(n_cells, chunk_rows)])
+    if threads > 1 and len(jobs) > 1:
+        from concurrent.futures import ThreadPoolExecutor
+        with ThreadPoolExecutor(max_workers=threads) as ex:
+            parts = list(ex.map(lambda j: j[0](j[1], j[2]), jobs))
+    else:
+        parts = [f(a, b) for f, a, b in jobs]
+    del J
     row_ptr = np.zeros(n + 1, dtype=np.int64)
-    np.cumsum(counts, out=row_ptr[1:])
-    col = np.concatenate([ucol_c, ccol_c]).astype(np.int32)
-    val = np.concatenate([uval_c, cval_c])
+    np.cumsum(np.concatenate([c for c, _, _ in parts]), out=row_ptr[1:])
+    nnz_total = int(row_ptr[-1])
+    col = np.empty(nnz_total, dtype=np.int32)
+    val = np.empty(nnz_total)
+    pos = 0
+    for q in range(len(parts)):
+        _, cc, vv = parts[q]
+        col[pos:pos + len(cc)] = cc
+        val[pos:pos + len(vv)] = vv
+        pos += len(cc)
+        parts[q] = None
+    del parts
 
     dof_label = np.empty(n, dtype=np.int32)
     dof_label[:n_u] = LABEL_U

@@ -33,6 +33,15 @@ def test_library_builds_and_exports_every_declared_symbol():
     assert sorted(mgr.EXPORTED) == declared_functions()
 
 
+def test_loaded_library_was_built_from_the_current_sources():
+    """The build id compiled into the library equals the hash of the sources
+    and flags in this tree (a stale library would be rebuilt by build())."""
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1904_05960_gb300 import build, mgr
+    assert mgr.mgr_build_id() == build.source_hash() == build.built_hash()
+
+
 def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     from paper_1904_05960_gb300 import mgr
     monkeypatch.setattr(mgr, "_lib", None)

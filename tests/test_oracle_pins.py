@@ -274,6 +274,123 @@ def test_interpolation_structure_and_constant_preservation():
             assert abs(Pone[i] - 1.0) <= 1e-14
 
 
+def neumann_elasticity(nx, ny, nz, lam=72.0, mu=72.0):
+    """Q1 stiffness of an nx x ny x nz box of unit cells with no boundary
+    condition (3 dofs per vertex, vertex-major).  With lam = mu = 72 every
+    entry is an integer, so the rigid translations are exact null vectors in
+    floating point: within each displacement component every row sums to 0,
+    with off-diagonals of both signs."""
+    nnx, nny = nx + 1, ny + 1
+    K = lam * synth.KLAM + mu * synth.KMU
+    rows, cols, vals = [], [], []
+    for cz in range(nz):
+        for cy in range(ny):
+            for cx in range(nx):
+                nodes = [(cx + (a & 1)) + nnx * ((cy + ((a >> 1) & 1)) + nny * (cz + ((a >> 2) & 1)))
+                         for a in range(8)]
+                for a in range(8):
+                    for b in range(8):
+                        for i in range(3):
+                            for j in range(3):
+                                rows.append(3 * nodes[a] + i)
+                                cols.append(3 * nodes[b] + j)
+                                vals.append(K[3 * a + i, 3 * b + j])
+    n = 3 * nnx * nny * (nz + 1)
+    A = sp.csr_matrix((vals, (rows, cols)), shape=(n, n))
+    A.sum_duplicates()
+    A.eliminate_zeros()
+    A.sort_indices()
+    return A, np.tile(np.arange(3), n // 3).astype(np.int32)
+
+
+@pytest.mark.parametrize("pmax", [0, 4])
+def test_interpolation_preserves_constants_with_positive_couplings(pmax):
+    """Direct interpolation on the elasticity operator (zero row sums within
+    each component, off-diagonals of both signs), with a strength graph that
+    also marks positive couplings strong.  Where a row has a positive strong C
+    neighbour its positive entries are scaled by beta = sum_pos / sum_pos_C;
+    where it has none they are lumped into the diagonal.  Both branches must
+    interpolate the constant exactly: P 1 = 1 on every F row with a negative
+    strong C neighbour, with and without truncation to P_max (rows rescaled to
+    keep their sums).  A sign slip in either branch, or a wrong lumping rule,
+    breaks this."""
+    A, comp = neumann_elasticity(3, 3, 2)
+    n = A.shape[0]
+    Ac = A.tocoo()
+    off = (Ac.row != Ac.col) & (comp[Ac.row] == comp[Ac.col])
+    S = sp.csr_matrix((np.ones(off.sum()), (Ac.row[off], Ac.col[off])), shape=(n, n))
+    node = np.arange(n) // 3
+    cf = np.where(node % 3 == 0, 1, -1).astype(np.int8)
+    P = oracle.interp(A, S, cf, comp=comp, pmax=pmax)
+    Pone = P @ np.ones(P.shape[1])
+    beta_rows = lump_rows = 0
+    for i in np.nonzero(cf == -1)[0]:
+        cols = A.indices[A.indptr[i]:A.indptr[i + 1]]
+        vals = A.data[A.indptr[i]:A.indptr[i + 1]]
+        strongC = [(j, v) for j, v in zip(cols, vals)
+                   if j != i and comp[j] == comp[i] and cf[j] == 1]
+        if not any(v < 0 for _, v in strongC):
+            continue
+        pos_same = any(v > 0 for j, v in zip(cols, vals) if j != i and comp[j] == comp[i])
+        if any(v > 0 for _, v in strongC):
+            beta_rows += 1
+        elif pos_same:
+            lump_rows += 1
+        assert abs(Pone[i] - 1.0) <= 1e-13, (i, Pone[i])
+    assert beta_rows > 0 and lump_rows > 0, (beta_rows, lump_rows)
+    if pmax:
+        assert np.diff(P.indptr).max() <= pmax
+
+
+def test_pmis_weight_counts_the_points_a_point_influences():
+    """PMIS weights w_i = |S^T_i| + u_i (the number of points that depend
+    strongly on i).  On directed stars -- every leaf depends on its centre,
+    the centre on nothing -- the centre has the largest weight, becomes C, and
+    every leaf then has a C point in S_i and becomes F: C = the centres.  (A
+    weight |S_i| would instead make every leaf C first.)"""
+    stars = [7, 4, 1]
+    rows, cols, centres = [], [], []
+    base = 0
+    for k in stars:
+        centres.append(base)
+        for leaf in range(base + 1, base + 1 + k):
+            rows.append(leaf)
+            cols.append(base)
+        base += k + 1
+    S = sp.csr_matrix((np.ones(len(rows)), (rows, cols)), shape=(base, base))
+    for seed in (0, 1, 12345):
+        cf = oracle.pmis(S, seed=seed)
+        want = -np.ones(base, dtype=np.int8)
+        want[centres] = 1
+        assert np.array_equal(cf, want), (seed, cf)
+
+
+def directed_star_matrix(leaves=7):
+    """Scalar matrix whose strength graph is a directed star: each leaf row has
+    -1 to the centre (its only negative coupling), the centre row has only
+    positive couplings (so S_centre is empty)."""
+    n = leaves + 1
+    A = sp.lil_matrix((n, n))
+    A[0, 0] = 4.0
+    for i in range(1, n):
+        A[i, i] = 2.0
+        A[i, 0] = -1.0
+        A[0, i] = 0.25
+    return sp.csr_matrix(A)
+
+
+def test_pmis_through_the_amg_setup_on_a_directed_star():
+    """The same closed form through the AMG setup: strength from the matrix,
+    PMIS, direct interpolation (each leaf interpolates from the centre with
+    weight -a_i0 / a_ii = 1/2)."""
+    A = directed_star_matrix()
+    o = _amg_only(A, amg_max_coarse=1)
+    cf = o.cf(0, 0)
+    assert cf[0] == 1 and np.all(cf[1:] == -1)
+    P = o.scipy(Q_AMG_P, 0, 0).toarray()
+    assert np.array_equal(P[:, 0], np.r_[1.0, np.full(7, 0.5)])
+
+
 def test_interpolation_without_truncation_keeps_all_strong_c():
     A = poisson3d(7, 7, 7)
     o = _amg_only(A, amg_max_coarse=10, amg_pmax=0)

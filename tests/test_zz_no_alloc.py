@@ -3,11 +3,11 @@
 Callers that cannot allocate device memory where they run (all device memory
 handed to their own pool up front, or no allocation allowed after start-up)
 use this entry point; it takes its workspace from a fixed buffer compiled into
-the library.  Its result must equal that of mgr_vcycle (the same V-cycle with
-the handle's workspace) within the V-cycle tolerance of the parity tests
-(1e-10 relative), on two calls in a row, which also shows that what one call
-leaves in the shared buffer does not leak into the next.  This file is named
-to be collected last.
+the library.  Its result must equal that of mgr_vcycle (the same kernels with
+the handle's workspace) bit for bit, on two calls in a row, which also shows
+that what one call leaves in the shared buffer does not leak into the next;
+and neither the library's memory pool nor the device's free memory may change
+across the calls.  This file is named to be collected last.
 """
 import numpy as np
 import pytest
@@ -18,9 +18,6 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 from paper_1904_05960_gb300 import mgr  # noqa: E402
-
-TOL = 1e-10
-
 
 @pytest.fixture(scope="module", autouse=True)
 def _built():
@@ -46,10 +43,15 @@ def test_noalloc_vcycle_matches_vcycle_on_two_calls(precision):
             ref = torch.empty_like(b)
             mgr.mgr_vcycle(s.h, slot, b, ref)
             out = torch.full_like(b, float("nan"))
+            torch.cuda.synchronize()
+            pool_before = mgr.mgr_memory_usage()
+            free_before = torch.cuda.mem_get_info()[0]
             mgr.mgr_vcycle_noalloc(s.h, slot, b, out)
             torch.cuda.synchronize()
+            assert mgr.mgr_memory_usage() == pool_before
+            assert torch.cuda.mem_get_info()[0] == free_before
             assert torch.isfinite(out).all()
-            assert _rel(out, ref) <= TOL, (slot, call)
+            assert torch.equal(out, ref), (slot, call, _rel(out, ref))
     s.close()
 
 
@@ -72,5 +74,5 @@ def test_noalloc_rejects_workspace_beyond_the_fixed_buffer():
     mgr.mgr_vcycle(s.h, 2, b2, ref)
     mgr.mgr_vcycle_noalloc(s.h, 2, b2, out)
     torch.cuda.synchronize()
-    assert _rel(out, ref) <= TOL
+    assert torch.equal(out, ref)
     s.close()
