@@ -143,6 +143,13 @@ typedef struct {
   /* Jacobi iterations per triangular solve of the ILU(1) global smoother
    * (0..1000; default 3). */
   int32_t ilu_solve_sweeps;
+  /* MGR_MIXED only (INVALID_ARG with MGR_FP64): 1 stores the smoother
+   * diagonals the FP32 application reads -- the l1-Jacobi inverse diagonals
+   * of every AMG level, D_FF^-1 of the Jacobi F-relaxations and the
+   * point-block inverses of the global smoother -- in BF16 (each value
+   * rounded once from FP64), halving their bytes; every other operator stays
+   * FP32.  0 in the defaults. */
+  int32_t diag_bf16;
 } mgr_options_t;
 
 typedef struct {
@@ -248,6 +255,13 @@ int64_t mgr_get_cf(mgr_handle_t h, int slot, int lvl, int8_t* out);
  * arrays of that AMG's size).  Asynchronous on `stream`. */
 int mgr_vcycle(mgr_handle_t h, int slot, const double* b, double* x, void* stream);
 
+/* y = A x with the FP64 sparse product that fgmres_solve applies to the
+ * Jacobian at every iteration (the "w = A z_j" step of right-preconditioned
+ * GMRES, Sec. 4).  A's arrays, x and y are DEVICE arrays (n doubles each; y
+ * must not overlap x); the grouping arrays of A are not read.  Asynchronous
+ * on `stream`.  INVALID_ARG for a NULL or negative-size argument. */
+int mgr_spmv(const mgr_matrix_t* A, const double* x, double* y, void* stream);
+
 /* Splitmix64 (Steele, Lea, Flood 2014) as evaluated on the device, for tests
  * of the PMIS weight hash: out[i] = splitmix64(in[i]) for n values (device). */
 int mgr_splitmix64_device(const uint64_t* in, uint64_t* out, int64_t n, void* stream);
@@ -261,6 +275,11 @@ int mgr_splitmix64_device(const uint64_t* in, uint64_t* out, int64_t n, void* st
  *   b, x: DEVICE FP64 arrays of that AMG's size, supplied by the caller.
  *   Workspace: one fixed 8 MiB buffer compiled into the library
  *   (static __device__, held by every GPU that loads the library until exit).
+ *   The CUDA runtime maps it when it loads this part of the library on a
+ *   device; under lazy module loading (the CUDA default) that is the first
+ *   call of this entry point on the device, which therefore can take device
+ *   memory and should be made at start-up, before any stream capture; later
+ *   calls take none.
  *   A V-cycle whose level vectors need more than 8 MiB is rejected with
  *   MGR_ERR_INVALID_ARG and a message on stderr; nothing is launched then.
  *   Every call made outside stream capture looks up the buffer's device

@@ -115,6 +115,8 @@ def lib():
                                      C.POINTER(C.POINTER(C.c_int32)),
                                      C.POINTER(C.POINTER(C.c_double))]
             L.orc_free_buffer.argtypes = [P]
+            L.orc_matvec.argtypes = [P, P, P]
+            L.orc_csr_spmv.argtypes = [C.c_int64, P, P, P, P, P]
             L.orc_splitmix64.restype = C.c_uint64
             L.orc_splitmix64.argtypes = [C.c_uint64]
             _lib = L
@@ -214,6 +216,13 @@ class Oracle:
         lib().orc_apply(self.h, _p(v), _p(z))
         return z
 
+    def matvec(self, x):
+        """y = A x with the input matrix."""
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        y = np.zeros(self.n)
+        lib().orc_matvec(self.h, _p(x), _p(y))
+        return y
+
     def vcycle(self, slot, b):
         b = np.ascontiguousarray(b, dtype=np.float64)
         x = np.zeros_like(b)
@@ -286,6 +295,16 @@ class Oracle:
         out = np.zeros(n)
         lib().orc_get_l1(self.h, slot, lvl, _p(out))
         return out
+
+
+def csr_spmv(row_ptr, col, val, x):
+    """y = A x for a CSR matrix given by its arrays (any size)."""
+    n = len(row_ptr) - 1
+    arrs = [np.ascontiguousarray(row_ptr, dtype=np.int64), np.ascontiguousarray(col, dtype=np.int32),
+            np.ascontiguousarray(val, dtype=np.float64), np.ascontiguousarray(x, dtype=np.float64)]
+    y = np.zeros(n)
+    lib().orc_csr_spmv(n, *[_p(a) for a in arrs], _p(y))
+    return y
 
 
 def pmis(S, seed=0, slot=0, level=0):

@@ -1453,3 +1453,22 @@ int orc_interp(int64_t n, const int64_t *rp, const int32_t *ci, const double *v,
 }
 
 void orc_free_buffer(void *q) { free(q); }
+
+/* y = A x with the input matrix (the Jacobian product of the Arnoldi step). */
+int orc_matvec(void *hv, const double *x, double *y) {
+  oracle_t *h = hv;
+  spmv(&h->Afull, x, y);
+  return ORC_OK;
+}
+
+/* y = A x for a caller-given CSR matrix (same row sums as above: ascending
+ * column order from 0.0); usable at any size without a hierarchy. */
+int orc_csr_spmv(int64_t n, const int64_t *rp, const int32_t *ci, const double *v,
+                 const double *x, double *y) {
+  if (n < 0) return ORC_ERR_ARG;
+  ocsr a;
+  a.nr = n; a.nc = n; a.nnz = n ? rp[n] : 0;
+  a.rp = (int64_t *)rp; a.ci = (int32_t *)ci; a.v = (double *)v;
+  spmv(&a, x, y);
+  return ORC_OK;
+}

@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdio>
+#include <type_traits>
 #include <vector>
 
 #include "mgr_internal.cuh"
@@ -21,6 +22,11 @@ template <class T>
 __device__ __forceinline__ T ldg(const T* p) {
   return __ldg(p);
 }
+
+// Smoother diagonals may be stored in BF16 (diag_bf16): widened on load.
+__device__ __forceinline__ float dval(float x) { return x; }
+__device__ __forceinline__ double dval(double x) { return x; }
+__device__ __forceinline__ float dval(__nv_bfloat16 x) { return __bfloat162float(x); }
 
 // ----------------------------------------------------------------------------
 // CSR sparse products, G lanes per row (G in 2..32), fused epilogues.
@@ -53,11 +59,11 @@ __device__ __forceinline__ unsigned group_mask() {
 // lanes.  One accumulator rather than two: on GB300 the FP64 products share a
 // narrow pipe, and every extra add (merging accumulators) costs a warp
 // instruction (measured on the A_uu levels: 7-17% faster).
-template <class T, class X, class Y, class I, int G, int MODE>
+template <class T, class X, class Y, class I, int G, int MODE, class D>
 __global__ void __launch_bounds__(256)
 k_spmv(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci, const T* __restrict__ val,
        I nr, const X* __restrict__ x, Y* __restrict__ y, const Y* __restrict__ b,
-       const T* __restrict__ dinv, const int64_t* __restrict__ rows) {
+       const D* __restrict__ dinv, const int64_t* __restrict__ rows) {
   const I gid = (I)blockIdx.x * blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & (G - 1);
   const I stride = ((I)gridDim.x * blockDim.x) / G;
@@ -70,7 +76,7 @@ k_spmv(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci, const T* 
 #pragma unroll 4
       for (; k < e1; k += G) {
         const int32_t c0 = ci[k];
-        acc += (Y)val[k] * ((Y)ldg(dinv + c0) * (Y)ldg(x + c0));
+        acc += (Y)val[k] * ((Y)dval(ldg(dinv + c0)) * (Y)ldg(x + c0));
       }
     } else {
 #pragma unroll 4
@@ -81,13 +87,13 @@ k_spmv(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci, const T* 
     if (lane == 0) {
       if (MODE == MODE_AX) y[i] = acc;
       else if (MODE == MODE_RES) y[i] = b[i] - acc;
-      else if (MODE == MODE_SMOOTH) y[i] = (Y)x[i] + (Y)dinv[i] * (b[i] - acc);
+      else if (MODE == MODE_SMOOTH) y[i] = (Y)x[i] + (Y)dval(dinv[i]) * (b[i] - acc);
       else if (MODE == MODE_ADD) y[i] += acc;
       else if (MODE == MODE_GRES) y[i] = b[rows[i]] - acc;
       else if (MODE == MODE_RROWS) y[i] = b[row] - acc;
       else if (MODE == MODE_RES0) y[i] = b[i] - acc;
-      else if (MODE == MODE_PROL0) y[i] = (Y)dinv[i] * b[i] + acc;
-      else if (MODE == MODE_DRES || MODE == MODE_DRES0) y[i] = (Y)dinv[i] * (b[i] - acc);
+      else if (MODE == MODE_PROL0) y[i] = (Y)dval(dinv[i]) * b[i] + acc;
+      else if (MODE == MODE_DRES || MODE == MODE_DRES0) y[i] = (Y)dval(dinv[i]) * (b[i] - acc);
     }
   }
 }
@@ -109,9 +115,9 @@ static int pick_group(int64_t nnz, int64_t nr) {
   return g;
 }
 
-template <class T, class X, class Y, class I, int MODE>
+template <class T, class X, class Y, class I, int MODE, class D>
 static void spmv_launch_i(const int64_t* rp, const int32_t* ci, const T* val, int64_t nr,
-                          int64_t nnz, const X* x, Y* y, const Y* b, const T* dinv,
+                          int64_t nnz, const X* x, Y* y, const Y* b, const D* dinv,
                           const int64_t* rows, cudaStream_t s) {
   const int G = pick_group(nnz, nr);
   const int tpb = 256;
@@ -119,7 +125,7 @@ static void spmv_launch_i(const int64_t* rp, const int32_t* ci, const T* val, in
   const unsigned grid = (unsigned)std::min<int64_t>((threads + tpb - 1) / tpb, 152LL * 64);
 #define MGR_SPMV_CASE(g)                                                                    \
   case g:                                                                                   \
-    MGR_LAUNCH k_spmv<T, X, Y, I, g, MODE><<<grid, tpb, 0, s>>>(rp, ci, val, (I)nr, x, y, b, \
+    MGR_LAUNCH k_spmv<T, X, Y, I, g, MODE, D><<<grid, tpb, 0, s>>>(rp, ci, val, (I)nr, x, y, b, \
                                                                 dinv, rows);                \
     break;
   switch (G) {
@@ -133,16 +139,22 @@ static void spmv_launch_i(const int64_t* rp, const int32_t* ci, const T* val, in
 #undef MGR_SPMV_CASE
 }
 
-template <class T, class X, class Y, int MODE>
+// D (the storage of dinv) is never deduced: it is T unless given
+template <class U>
+struct ident {
+  using type = U;
+};
+
+template <class T, class X, class Y, int MODE, class D = T>
 static void spmv_launch(const int64_t* rp, const int32_t* ci, const T* val, int64_t nr, int64_t nnz,
-                        const X* x, Y* y, const Y* b, const T* dinv, const int64_t* rows,
-                        cudaStream_t s) {
+                        const X* x, Y* y, const Y* b, const typename ident<D>::type* dinv,
+                        const int64_t* rows, cudaStream_t s) {
   if (nr <= 0) return;
   // 32-bit offsets when every index (rows x lanes, nnz + 2 x lanes) fits
   if (nnz + 64 < INT32_MAX && nr * 16 + 152LL * 64 * 256 < INT32_MAX)
-    spmv_launch_i<T, X, Y, int, MODE>(rp, ci, val, nr, nnz, x, y, b, dinv, rows, s);
+    spmv_launch_i<T, X, Y, int, MODE, D>(rp, ci, val, nr, nnz, x, y, b, dinv, rows, s);
   else
-    spmv_launch_i<T, X, Y, int64_t, MODE>(rp, ci, val, nr, nnz, x, y, b, dinv, rows, s);
+    spmv_launch_i<T, X, Y, int64_t, MODE, D>(rp, ci, val, nr, nnz, x, y, b, dinv, rows, s);
 }
 
 template <class T>
@@ -159,10 +171,22 @@ inline const double* pick<double>(const double* d, const float*) { return d; }
 template <>
 inline const float* pick<float>(const double*, const float* f) { return f; }
 
-template <class T, int MODE>
-static void spmv(const Csr& A, const T* x, T* y, const T* b, const T* dinv, const int64_t* rows,
-                 cudaStream_t s) {
-  spmv_launch<T, T, T, MODE>(A.rp, A.ci, vals<T>(A), A.nr, A.nnz, x, y, b, dinv, rows, s);
+// a smoother diagonal in its storage type D (FP64, FP32 or BF16)
+template <class D>
+static inline const D* pickd(const double* d, const float* f, const __nv_bfloat16* h);
+template <>
+inline const double* pickd<double>(const double* d, const float*, const __nv_bfloat16*) { return d; }
+template <>
+inline const float* pickd<float>(const double*, const float* f, const __nv_bfloat16*) { return f; }
+template <>
+inline const __nv_bfloat16* pickd<__nv_bfloat16>(const double*, const float*, const __nv_bfloat16* h) {
+  return h;
+}
+
+template <class T, int MODE, class D = T>
+static void spmv(const Csr& A, const T* x, T* y, const T* b, const typename ident<D>::type* dinv,
+                 const int64_t* rows, cudaStream_t s) {
+  spmv_launch<T, T, T, MODE, D>(A.rp, A.ci, vals<T>(A), A.nr, A.nnz, x, y, b, dinv, rows, s);
 }
 
 void spmv64(const int64_t* rp, const int32_t* ci, const double* v, int64_t nr, int64_t nnz,
@@ -183,10 +207,10 @@ void residual64(const int64_t* rp, const int32_t* ci, const double* v, int64_t n
 // ----------------------------------------------------------------------------
 // Vector kernels
 // ----------------------------------------------------------------------------
-template <class T>
-__global__ void k_scale(const T* __restrict__ d, const T* __restrict__ b, T* __restrict__ x, int64_t n) {
+template <class T, class D>
+__global__ void k_scale(const D* __restrict__ d, const T* __restrict__ b, T* __restrict__ x, int64_t n) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    x[i] = d[i] * b[i];
+    x[i] = (T)dval(d[i]) * b[i];
 }
 
 template <class T>
@@ -236,13 +260,13 @@ __global__ void k_cast(const A* __restrict__ a, B* __restrict__ b, int64_t n) {
 // Each CTA owns BJ_BLOCKS consecutive cell blocks (their rows are consecutive,
 // at most 4 per block).  Phase 1: G lanes per row form the residual of those
 // rows in shared memory; phase 2: one thread per cell block applies its
-// inverse.
+// inverse (bd x bd values per block, row-major).
 static constexpr int BJ_BLOCKS = 64;
-template <class T, int G, bool FIRST>
+template <class T, int G, bool FIRST, class D>
 __global__ void __launch_bounds__(256)
 k_block_jacobi(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
                const T* __restrict__ val, const int64_t* __restrict__ bstart,
-               const T* __restrict__ binv, int64_t nblk, const T* __restrict__ v,
+               const D* __restrict__ binv, int bd, int64_t nblk, const T* __restrict__ v,
                const T* __restrict__ zin, T* __restrict__ zout) {
   __shared__ T rs[4 * BJ_BLOCKS];
   const int64_t k0 = (int64_t)blockIdx.x * BJ_BLOCKS;
@@ -269,10 +293,10 @@ k_block_jacobi(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
     const int64_t s0 = bstart[k];
     const int b = (int)(bstart[k + 1] - s0);
     const int q0 = (int)(s0 - r0);
-    const T* M = binv + 16 * k;
+    const D* M = binv + (int64_t)bd * bd * k;
     for (int i = 0; i < b; i++) {
       T d = 0;
-      for (int j = 0; j < b; j++) d += M[i * 4 + j] * rs[q0 + j];
+      for (int j = 0; j < b; j++) d += (T)dval(M[i * bd + j]) * rs[q0 + j];
       zout[s0 + i] = FIRST ? d : zin[s0 + i] + d;
     }
   }
@@ -282,10 +306,10 @@ k_block_jacobi(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
 // z_b += B_b^-1 (v - A z)_b in place.  A warp per block, 8 lanes per row (at
 // most 4 rows); blocks of one colour are not adjacent in A + A^T, so a warp
 // reads no unknown that another warp of the launch writes.
-template <class T>
+template <class T, class D>
 __global__ void __launch_bounds__(256)
 k_block_gs(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci, const T* __restrict__ val,
-           const int64_t* __restrict__ bstart, const T* __restrict__ binv,
+           const int64_t* __restrict__ bstart, const D* __restrict__ binv, int bd,
            const int64_t* __restrict__ list, int64_t count, const T* __restrict__ v, T* z) {
   const int lane = threadIdx.x & 31, g = lane >> 3, sub = lane & 7;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -305,9 +329,9 @@ k_block_gs(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci, const
 #pragma unroll
     for (int j = 0; j < 4; j++) rr[j] = __shfl_sync(FULL, r, j * 8);
     if (lane < b) {
-      const T* M = binv + 16 * k;
+      const D* M = binv + (int64_t)bd * bd * k;
       T d = 0;
-      for (int j = 0; j < b; j++) d += M[lane * 4 + j] * rr[j];
+      for (int j = 0; j < b; j++) d += (T)dval(M[lane * bd + j]) * rr[j];
       z[s0 + lane] += d;
     }
   }
@@ -411,8 +435,9 @@ struct WsLevel {
 };
 
 // One V-cycle on levels k.. of g; W[k'] holds the level vectors (for k' > k:
-// b, x; for every non-coarsest level: t, r).
-template <class T>
+// b, x; for every non-coarsest level: t, r).  D: storage type of the l1
+// diagonals read (T, or BF16 under diag_bf16).
+template <class T, class D>
 static void vcycle_on(Amg* g, int k, const T* b, T* x, const WsLevel<T>* W, cudaStream_t s) {
   AmgLevel& L = g->lev[k];
   const int64_t n = L.A.nr;
@@ -421,25 +446,38 @@ static void vcycle_on(Amg* g, int k, const T* b, T* x, const WsLevel<T>* W, cuda
     MGR_LAUNCH k_dense_gemv<T><<<grid_for(n * 32, 256), 256, 0, s>>>(inv, n, b, x);
     return;
   }
-  const T* dinv = pick<T>(L.dinv, L.dinvf);
+  const D* dinv = pickd<D>(L.dinv, L.dinvf, L.dinvh);
   T* t = W[k].t;
   T* r = W[k].r;
   T* cb = W[k + 1].b;
   T* cx = W[k + 1].x;
   if (L.A.nnz < FUSE_SCALE_NNZ) {
     // small level: fold t = dinv .* b into the residual and the prolongation
-    spmv<T, MODE_RES0>(L.A, b, r, b, dinv, nullptr, s);
+    spmv<T, MODE_RES0, D>(L.A, b, r, b, dinv, nullptr, s);
     spmv<T, MODE_AX>(L.R, r, cb, nullptr, nullptr, nullptr, s);
-    vcycle_on<T>(g, k + 1, cb, cx, W, s);
-    spmv<T, MODE_PROL0>(L.P, cx, t, b, dinv, nullptr, s);
+    vcycle_on<T, D>(g, k + 1, cb, cx, W, s);
+    spmv<T, MODE_PROL0, D>(L.P, cx, t, b, dinv, nullptr, s);
   } else {
-    MGR_LAUNCH k_scale<T><<<vgrid(n), 256, 0, s>>>(dinv, b, t, n);
+    MGR_LAUNCH k_scale<T, D><<<vgrid(n), 256, 0, s>>>(dinv, b, t, n);
     spmv<T, MODE_RES>(L.A, t, r, b, nullptr, nullptr, s);
     spmv<T, MODE_AX>(L.R, r, cb, nullptr, nullptr, nullptr, s);
-    vcycle_on<T>(g, k + 1, cb, cx, W, s);
+    vcycle_on<T, D>(g, k + 1, cb, cx, W, s);
     spmv<T, MODE_ADD>(L.P, cx, t, nullptr, nullptr, nullptr, s);
   }
-  spmv<T, MODE_SMOOTH>(L.A, t, x, b, dinv, nullptr, s);
+  spmv<T, MODE_SMOOTH, D>(L.A, t, x, b, dinv, nullptr, s);
+}
+
+// V-cycle on the level vectors W, with the diagonals in the storage the
+// hierarchy was set up with
+template <class T>
+static void vcycle_ws(Amg* g, int k, const T* b, T* x, const WsLevel<T>* W, cudaStream_t s) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (g->bf16) {
+      vcycle_on<float, __nv_bfloat16>(g, k, b, x, W, s);
+      return;
+    }
+  }
+  vcycle_on<T, T>(g, k, b, x, W, s);
 }
 
 // V-cycle with the handle's level workspace
@@ -448,7 +486,56 @@ static void vcycle(Amg* g, int k, const T* b, T* x, cudaStream_t s) {
   WsLevel<T> W[32];
   for (size_t q = 0; q < g->lev.size() && q < 32; q++)
     W[q] = WsLevel<T>{(T*)g->lev[q].b, (T*)g->lev[q].x, (T*)g->lev[q].t, (T*)g->lev[q].r};
-  vcycle_on<T>(g, k, b, x, W, s);
+  vcycle_ws<T>(g, k, b, x, W, s);
+}
+
+// Global relaxation by point-block Jacobi or multicolour point-block
+// Gauss-Seidel sweeps from zero (z = M_glo^-1 v), block inverses in storage D.
+template <class T, class D>
+static void block_sweeps(MgrLevel& L, const D* binv, const T* v, T* z, cudaStream_t s) {
+  const int64_t n = L.n;
+  const T* Av = vals<T>(L.A);
+  const int bd = L.bdim;
+  if (L.gs) {
+    // multicolour Gauss-Seidel sweeps from zero, in place on z
+    cudaMemsetAsync(z, 0, sizeof(T) * n, s);
+    for (int sw = 0; sw < L.global_sweeps; sw++)
+      for (int c = 0; c < L.ncolor; c++) {
+        const int64_t cnt = L.coff[c + 1] - L.coff[c];
+        if (cnt == 0) continue;
+        const unsigned gg = (unsigned)std::min<int64_t>((cnt + 7) / 8, 152LL * 16);
+        MGR_LAUNCH k_block_gs<T, D><<<gg, 256, 0, s>>>(L.A.rp, L.A.ci, Av, L.bstart, binv, bd,
+                                                       L.border + L.coff[c], cnt, v, z);
+      }
+    return;
+  }
+  T* buf[2] = {((L.global_sweeps - 1) % 2 == 0) ? z : (T*)L.z2,
+               ((L.global_sweeps - 1) % 2 == 0) ? (T*)L.z2 : z};
+  const unsigned bgrid = (unsigned)((L.nblk + BJ_BLOCKS - 1) / BJ_BLOCKS);
+  const int G = pick_group(L.A.nnz, L.A.nr);
+  bool first = true;
+  for (int sw = 0; sw < L.global_sweeps; sw++, first = false) {
+    const T* zi = first ? nullptr : buf[(sw - 1) % 2];
+    T* zo = buf[sw % 2];
+#define MGR_BJ_CASE(g)                                                                             \
+  case g:                                                                                          \
+    if (first)                                                                                     \
+      MGR_LAUNCH k_block_jacobi<T, g, true, D><<<bgrid, 256, 0, s>>>(L.A.rp, L.A.ci, Av, L.bstart, \
+                 binv, bd, L.nblk, v, zi, zo);                                                     \
+    else                                                                                           \
+      MGR_LAUNCH k_block_jacobi<T, g, false, D><<<bgrid, 256, 0, s>>>(L.A.rp, L.A.ci, Av,          \
+                 L.bstart, binv, bd, L.nblk, v, zi, zo);                                           \
+    break;
+    switch (G) {
+      MGR_BJ_CASE(1)
+      MGR_BJ_CASE(2)
+      MGR_BJ_CASE(4)
+      MGR_BJ_CASE(8)
+      MGR_BJ_CASE(16)
+      default: MGR_BJ_CASE(32)
+    }
+#undef MGR_BJ_CASE
+  }
 }
 
 // ----------------------------------------------------------------------------
@@ -469,12 +556,6 @@ static void mgr_level(Handle* h, int l, const T* v, T* z, cudaStream_t s) {
   // global relaxation z = M_glo^-1 v: sweeps from zero of point-block Jacobi
   // or of multicolour point-block Gauss-Seidel
   if (L.global_sweeps > 0 && L.nblk > 0) {
-    const T* binv = pick<T>(L.binv, L.binvf);
-    T* buf[2] = {((L.global_sweeps - 1) % 2 == 0) ? z : (T*)L.z2,
-                 ((L.global_sweeps - 1) % 2 == 0) ? (T*)L.z2 : z};
-    const unsigned bgrid = (unsigned)((L.nblk + BJ_BLOCKS - 1) / BJ_BLOCKS);
-    const int G = pick_group(L.A.nnz, L.A.nr);
-    bool first = true;
     if (L.ilu1) {
       // ILU(1) sweeps from zero: r = v - A z; y = L^-1 r and w = U^-1 y by
       // Jacobi iterations; z += w.  The last iteration writes z itself in
@@ -499,7 +580,7 @@ static void mgr_level(Handle* h, int l, const T* v, T* z, cudaStream_t s) {
         }
         T* last = (sw == 0) ? z : (it == 0 ? z2 : wb);   // never the buffer y is in
         if (it == 0) {
-          MGR_LAUNCH k_scale<T><<<vgrid(n), 256, 0, s>>>(di, y, last, n);
+          MGR_LAUNCH k_scale<T, T><<<vgrid(n), 256, 0, s>>>(di, y, last, n);
         }
         const T* w = nullptr;
         for (int t = 1; t <= it; t++) {
@@ -510,40 +591,16 @@ static void mgr_level(Handle* h, int l, const T* v, T* z, cudaStream_t s) {
         }
         if (sw > 0) MGR_LAUNCH k_add<T><<<vgrid(n), 256, 0, s>>>(z, last, n);
       }
-    } else if (L.gs) {
-      // multicolour Gauss-Seidel sweeps from zero, in place on z
-      cudaMemsetAsync(z, 0, sizeof(T) * n, s);
-      for (int sw = 0; sw < L.global_sweeps; sw++)
-        for (int c = 0; c < L.ncolor; c++) {
-          const int64_t cnt = L.coff[c + 1] - L.coff[c];
-          if (cnt == 0) continue;
-          const unsigned gg = (unsigned)std::min<int64_t>((cnt + 7) / 8, 152LL * 16);
-          MGR_LAUNCH k_block_gs<T><<<gg, 256, 0, s>>>(L.A.rp, L.A.ci, Av, L.bstart, binv,
-                                                      L.border + L.coff[c], cnt, v, z);
+    } else {
+      bool done = false;
+      if constexpr (std::is_same<T, float>::value) {
+        if (L.bf16) {
+          block_sweeps<float, __nv_bfloat16>(L, L.binvch, v, z, s);
+          done = true;
         }
-    }
-    for (int sw = 0; sw < ((L.gs || L.ilu1) ? 0 : L.global_sweeps); sw++, first = false) {
-      const T* zi = first ? nullptr : buf[(sw - 1) % 2];
-      T* zo = buf[sw % 2];
-#define MGR_BJ_CASE(g)                                                                           \
-  case g:                                                                                        \
-    if (first)                                                                                   \
-      MGR_LAUNCH k_block_jacobi<T, g, true><<<bgrid, 256, 0, s>>>(L.A.rp, L.A.ci, Av, L.bstart, binv, \
-                 L.nblk, v, zi, zo);                                                             \
-    else                                                                                         \
-      MGR_LAUNCH k_block_jacobi<T, g, false><<<bgrid, 256, 0, s>>>(L.A.rp, L.A.ci, Av, L.bstart,     \
-                 binv, L.nblk, v, zi, zo);                                                       \
-    break;
-      switch (G) {
-        MGR_BJ_CASE(1)
-        MGR_BJ_CASE(2)
-        MGR_BJ_CASE(4)
-        MGR_BJ_CASE(8)
-        MGR_BJ_CASE(16)
-        default: MGR_BJ_CASE(32)
       }
-#undef MGR_BJ_CASE
-        }
+      if (!done) block_sweeps<T, T>(L, pick<T>(L.binvc, L.binvcf), v, z, s);
+    }
     zero = false;
   }
   T* rF = (T*)L.rF;
@@ -575,7 +632,9 @@ static void mgr_level(Handle* h, int l, const T* v, T* z, cudaStream_t s) {
       }
       if (L.frelax == MGR_FRELAX_AMG_VCYCLE) vcycle<T>(L.famg, 0, rhs, eF, s);
       else if (L.dff_block) spmv<T, MODE_AX>(L.Bd, rhs, eF, nullptr, nullptr, nullptr, s);
-      else MGR_LAUNCH k_scale<T><<<vgrid(nF), 256, 0, s>>>(pick<T>(L.dFinv, L.dFinvf), rhs, eF, nF);
+      else if (std::is_same<T, float>::value && L.bf16)
+        MGR_LAUNCH k_scale<T, __nv_bfloat16><<<vgrid(nF), 256, 0, s>>>(L.dFinvh, rhs, eF, nF);
+      else MGR_LAUNCH k_scale<T, T><<<vgrid(nF), 256, 0, s>>>(pick<T>(L.dFinv, L.dFinvf), rhs, eF, nF);
       if (zero) zF_only = eF;
       else MGR_LAUNCH k_scatter_add<T><<<vgrid(nF), 256, 0, s>>>(z, L.Fidx, eF, nullptr, nF);
     }
@@ -786,12 +845,12 @@ int apply_vcycle64_ws(Handle* h, Amg* g, const double* b, double* x, void* ws, c
     float* b32 = (float*)p; p += ws_align((size_t)n * sizeof(float));
     float* x32 = (float*)p; p += ws_align((size_t)n * sizeof(float));
     MGR_LAUNCH k_cast<double, float><<<vgrid(n), 256, 0, s>>>(b, b32, n);
-    vcycle_on<float>(g, 0, b32, x32, W.data(), s);
+    vcycle_ws<float>(g, 0, b32, x32, W.data(), s);
     MGR_LAUNCH k_cast<float, double><<<vgrid(n), 256, 0, s>>>(x32, x, n);
   } else {
     std::vector<WsLevel<double>> W;
     carve<double>(g, p, W);
-    vcycle_on<double>(g, 0, b, x, W.data(), s);
+    vcycle_ws<double>(g, 0, b, x, W.data(), s);
   }
   MGR_TRY_CUDA(cudaGetLastError());
   return MGR_SUCCESS;

@@ -173,6 +173,7 @@ int setup_one(const mgr_matrix_t* A, const mgr_options_t* o, cudaStream_t s, Han
   if (A->n > INT32_MAX) return MGR_ERR_INVALID_ARG;
   for (int l = 0; l < MGR_MAX_LEVELS; l++)
     if (o->global_smoother[l] < 0 || o->global_smoother[l] > 2) return MGR_ERR_INVALID_ARG;
+  if (o->diag_bf16 != 0 && (o->diag_bf16 != 1 || o->precision != MGR_MIXED)) return MGR_ERR_INVALID_ARG;
   if (o->ilu_solve_sweeps < 0 || o->ilu_solve_sweeps > 1000) return MGR_ERR_INVALID_ARG;
   Handle* h = new (std::nothrow) Handle();
   if (!h) return MGR_ERR_OOM;
@@ -347,6 +348,17 @@ int mgr_vcycle(mgr_handle_t hh, int slot, const double* b, double* x, void* stre
   Amg* g = find_amg(h, slot);
   if (!g) return MGR_ERR_INVALID_ARG;
   return apply_vcycle64(h, g, b, x, (cudaStream_t)stream);
+}
+
+int mgr_spmv(const mgr_matrix_t* A, const double* x, double* y, void* stream) {
+  (void)cudaGetLastError();  // errors of earlier calls are not this call's
+  if (!A || A->n < 0 || A->nnz < 0 || (A->n > 0 && (!A->row_ptr || !x || !y)) ||
+      (A->nnz > 0 && (!A->col_idx || !A->val)))
+    return MGR_ERR_INVALID_ARG;
+  if (A->n == 0) return MGR_SUCCESS;
+  spmv64(A->row_ptr, A->col_idx, A->val, A->n, A->nnz, x, y, (cudaStream_t)stream);
+  MGR_TRY_CUDA(cudaGetLastError());
+  return MGR_SUCCESS;
 }
 
 int mgr_splitmix64_device(const uint64_t* in, uint64_t* out, int64_t n, void* stream) {

@@ -1,6 +1,7 @@
 // Internal declarations of the GB300 MGR library (not part of the C ABI).
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <atomic>
@@ -111,6 +112,7 @@ struct AmgLevel {
   int32_t* comp = nullptr;
   double* dinv = nullptr;    // 1 / l1-diagonal
   float* dinvf = nullptr;
+  __nv_bfloat16* dinvh = nullptr;   // BF16 copy (MGR_MIXED with diag_bf16)
   // apply workspace (value type chosen by the handle precision)
   void* x = nullptr;
   void* b = nullptr;
@@ -120,6 +122,7 @@ struct AmgLevel {
 
 struct Amg {
   std::vector<AmgLevel> lev;
+  bool bf16 = false;         // the FP32 V-cycle reads the BF16 smoother diagonals
   int64_t ncoarse = 0;
   double* inv = nullptr;     // dense inverse of the coarsest operator (row-major)
   float* invf = nullptr;
@@ -133,6 +136,7 @@ struct MgrLevel {
   bool F_is_prefix = false;                  // F = [0, nF), C = [nF, n)
   double* dFinv = nullptr;       // 1 / diag(A_FF)
   float* dFinvf = nullptr;
+  __nv_bfloat16* dFinvh = nullptr;   // BF16 copy (diag_bf16)
   Csr W;                         // W_p = -D_FF^-1 A_FC (nF x nC)
   Csr Wr;                        // W_r = -A_CF D_FF^-1 (nC x nF; Jacobi restriction)
   Csr Bd;                        // point-block D_FF^-1 (nF x nF; dff_block)
@@ -149,8 +153,14 @@ struct MgrLevel {
   int ncolor = 0;
   int64_t* border = nullptr;     // blocks grouped by colour
   std::vector<int64_t> coff;     // colour c's blocks: border[coff[c] .. coff[c+1])
-  double* binv = nullptr;        // 16 values per block, row-major b x b
-  float* binvf = nullptr;
+  double* binv = nullptr;        // setup layout: 16 values per block, row-major 4 x 4
+  // apply layout: bdim x bdim values per block (bdim = the level's largest
+  // block), row-major, so a 2x2 cell block reads 4 values instead of 16
+  int bdim = 0;
+  double* binvc = nullptr;
+  float* binvcf = nullptr;
+  __nv_bfloat16* binvch = nullptr;   // BF16 copy (diag_bf16)
+  bool bf16 = false;             // FP32 apply reads the BF16 diagonals
   // ILU(1) global smoother: the factors on one pattern (ilu: strict L with
   // unit diagonal implied, plus U), split for the triangular iterations
   bool ilu1 = false;

@@ -931,6 +931,25 @@ __global__ void k_block_inv(const int64_t* __restrict__ rp, const int32_t* __res
     for (int j = 0; j < 4; j++) binv[k * 16 + i * 4 + j] = (i < b && j < b) ? m[i][b + j] : 0.0;
 }
 
+// Largest point block of a level (atomic max over the blocks).
+__global__ void k_block_dim_max(const int64_t* __restrict__ bstart, int64_t nblk, int* __restrict__ out) {
+  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nblk) return;
+  atomicMax(out, (int)(bstart[k + 1] - bstart[k]));
+}
+
+// Apply layout of the block inverses: bd x bd values per block (row-major),
+// taken from the 4 x 4 setup layout.
+__global__ void k_compact_binv(const double* __restrict__ binv, int64_t nblk, int bd,
+                               double* __restrict__ out) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t per = (int64_t)bd * bd;
+  if (t >= nblk * per) return;
+  const int64_t k = t / per;
+  const int q = (int)(t - k * per);
+  out[t] = binv[k * 16 + (q / bd) * 4 + (q % bd)];
+}
+
 // ============================================================================
 // AMG setup (Sec. 6 solver settings)
 // ============================================================================
@@ -2608,6 +2627,18 @@ static int setup_level(Handle* h, int l, const int32_t* label, const int32_t* no
     MGR_LAUNCH k_block_inv<<<nblocks(L.nblk, 128), 128, 0, s>>>(L.A.rp, L.A.ci, L.A.v, L.bstart, L.nblk,
                                                       L.binv, h->derr);
     MGR_TRY(check_dev_err(h->derr, s));
+    {
+      int* dmax = tmp.get<int>(1);
+      if (tmp.err) return tmp.err;
+      MGR_TRY_CUDA(cudaMemsetAsync(dmax, 0, sizeof(int), s));
+      MGR_LAUNCH k_block_dim_max<<<nblocks(L.nblk, 256), 256, 0, s>>>(L.bstart, L.nblk, dmax);
+      MGR_TRY(read_back(&L.bdim, dmax, s));
+      if (L.bdim < 1 || L.bdim > 4) return MGR_ERR_INVALID_ARG;
+      L.binvc = P.get<double>((int64_t)L.bdim * L.bdim * L.nblk);
+      if (P.err) return P.err;
+      MGR_LAUNCH k_compact_binv<<<nblocks((int64_t)L.bdim * L.bdim * L.nblk, 256), 256, 0, s>>>(
+          L.binv, L.nblk, L.bdim, L.binvc);
+    }
     if (o.global_smoother[l] == 2) {
       L.ilu_solve_sweeps = o.ilu_solve_sweeps;
       MGR_TRY(ilu1_build(h, P, tmp, L, s));
@@ -2744,6 +2775,21 @@ static int f32(Pool& P, const double* a, float** b, int64_t n, cudaStream_t s) {
   return MGR_SUCCESS;
 }
 
+// BF16 storage of a smoother diagonal: each value rounded once, to nearest
+// even, from FP64.
+__global__ void k_d2bf(const double* __restrict__ a, __nv_bfloat16* __restrict__ b, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = __double2bfloat16(a[i]);
+}
+
+static int bf16(Pool& P, const double* a, __nv_bfloat16** b, int64_t n, cudaStream_t s) {
+  if (!a || n == 0) return MGR_SUCCESS;
+  *b = P.get<__nv_bfloat16>(n);
+  if (!*b) return P.err;
+  MGR_LAUNCH k_d2bf<<<grid_for(n, 256), 256, 0, s>>>(a, *b, n);
+  return MGR_SUCCESS;
+}
+
 static int amg_to_fp32(Handle* h, Amg* g, cudaStream_t s) {
   if (!g) return MGR_SUCCESS;
   Pool& P = h->pool;
@@ -2752,7 +2798,9 @@ static int amg_to_fp32(Handle* h, Amg* g, cudaStream_t s) {
     MGR_TRY(f32(P, L.P.v, &L.P.vf, L.P.nnz, s));
     MGR_TRY(f32(P, L.R.v, &L.R.vf, L.R.nnz, s));
     MGR_TRY(f32(P, L.dinv, &L.dinvf, L.A.nr, s));
+    if (h->opt.diag_bf16) MGR_TRY(bf16(P, L.dinv, &L.dinvh, L.A.nr, s));
   }
+  g->bf16 = h->opt.diag_bf16 != 0;
   MGR_TRY(f32(P, g->inv, &g->invf, g->ncoarse * g->ncoarse, s));
   return MGR_SUCCESS;
 }
@@ -2764,7 +2812,12 @@ int to_fp32(Handle* h, cudaStream_t s) {
     MGR_TRY(f32(P, L.W.v, &L.W.vf, L.W.nnz, s));
     MGR_TRY(f32(P, L.Acf.v, &L.Acf.vf, L.Acf.nnz, s));
     MGR_TRY(f32(P, L.dFinv, &L.dFinvf, L.nF, s));
-    MGR_TRY(f32(P, L.binv, &L.binvf, 16 * L.nblk, s));
+    MGR_TRY(f32(P, L.binvc, &L.binvcf, (int64_t)L.bdim * L.bdim * L.nblk, s));
+    if (h->opt.diag_bf16) {
+      MGR_TRY(bf16(P, L.dFinv, &L.dFinvh, L.nF, s));
+      MGR_TRY(bf16(P, L.binvc, &L.binvch, (int64_t)L.bdim * L.bdim * L.nblk, s));
+      L.bf16 = true;
+    }
     if (L.Wr.v) MGR_TRY(f32(P, L.Wr.v, &L.Wr.vf, L.Wr.nnz, s));
     if (L.Bd.v) MGR_TRY(f32(P, L.Bd.v, &L.Bd.vf, L.Bd.nnz, s));
     if (L.ilu1) {

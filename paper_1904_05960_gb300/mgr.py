@@ -29,7 +29,7 @@ EXPORTED = ["mgr_options_default", "fgmres_options_default", "mgr_setup", "mgr_a
             "mgr_amg_levels", "mgr_get_cf", "mgr_vcycle", "mgr_splitmix64_device",
             "mgr_launch_count", "mgr_trim_memory", "mgr_solve_host", "mgr_vcycle_noalloc", "mgr_setup_batched",
             "fgmres_solve_batched", "mgr_batch_info", "mgr_batch_handle", "mgr_destroy_batched",
-            "mgr_get_block_colors", "mgr_build_id", "mgr_memory_usage"]
+            "mgr_get_block_colors", "mgr_build_id", "mgr_memory_usage", "mgr_spmv"]
 
 
 class MgrMatrix(C.Structure):
@@ -53,7 +53,8 @@ class MgrOptions(C.Structure):
                 ("dff_block", C.c_int32 * MGR_MAX_LEVELS),
                 ("global_smoother", C.c_int32 * MGR_MAX_LEVELS),
                 ("agg_levels", C.c_int32 * MGR_MAX_LEVELS),
-                ("ilu_solve_sweeps", C.c_int32)]
+                ("ilu_solve_sweeps", C.c_int32),
+                ("diag_bf16", C.c_int32)]
 
 
 class FgmresOptions(C.Structure):
@@ -103,6 +104,7 @@ def lib():
             L.mgr_get_cf.restype = I64
             L.mgr_vcycle.argtypes = [P, C.c_int, P, P, P]
             L.mgr_splitmix64_device.argtypes = [P, P, I64, P]
+            L.mgr_spmv.argtypes = [C.POINTER(MgrMatrix), P, P, P]
             L.mgr_vcycle_noalloc.argtypes = [P, C.c_int, P, P, P]
             L.mgr_setup_batched.argtypes = [C.c_int, C.POINTER(MgrMatrix), C.POINTER(MgrOptions),
                                             C.c_int, P, C.POINTER(P)]
@@ -382,6 +384,11 @@ def mgr_vcycle_noalloc(h, slot, b, x, stream=None):
     cannot allocate device memory where they run)."""
     return _check(lib().mgr_vcycle_noalloc(h, slot, _ptr(b), _ptr(x), _stream_ptr(stream)),
                   "mgr_vcycle_noalloc")
+
+
+def mgr_spmv(A: DeviceMatrix, x, y, stream=None):
+    """y = A x (device FP64 tensors) with FGMRES's Jacobian product."""
+    return _check(lib().mgr_spmv(C.byref(A.c), _ptr(x), _ptr(y), _stream_ptr(stream)), "mgr_spmv")
 
 
 def mgr_splitmix64_device(inp, out, stream=None):

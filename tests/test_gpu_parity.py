@@ -80,6 +80,20 @@ def _rel(a, b):
     return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
 
 
+def _maxrel(a, b):
+    """Element-wise: the largest entry difference over the largest entry."""
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+def _spmv_bound_ok(p, x, y_gpu, y_orc, rtol=1e-12):
+    """Every entry of the FP64 product within rtol of its own scale
+    sum_j |a_ij x_j| (summation order is the only difference)."""
+    A = p.to_scipy()
+    scale = abs(A) @ np.abs(x)
+    bad = np.abs(y_gpu - y_orc) > rtol * scale
+    return not bad.any(), int(bad.sum())
+
+
 SMALL = [
     ("single_phase_8", lambda: synth.config(1)),
     ("two_phase_10x9x6", lambda: synth.two_phase(10, 9, 6)),
@@ -105,7 +119,8 @@ def test_apply_and_vcycles_match_oracle(name, make):
     rng = np.random.default_rng(7)
     v = rng.standard_normal(p.n)
     z = s.apply(torch.from_numpy(v).cuda()).cpu().numpy()
-    assert _rel(z, o.apply(v)) <= 1e-10
+    zo = o.apply(v)
+    assert _rel(z, zo) <= 1e-10 and _maxrel(z, zo) <= 1e-10
     for slot in range(o.num_levels + 1):
         if o.amg_levels(slot) == 0:
             continue
@@ -114,7 +129,93 @@ def test_apply_and_vcycles_match_oracle(name, make):
         x = torch.zeros(nA, dtype=torch.float64, device="cuda")
         mgr.mgr_vcycle(s.h, slot, torch.from_numpy(b).cuda(), x)
         torch.cuda.synchronize()
-        assert _rel(x.cpu().numpy(), o.vcycle(slot, b)) <= 1e-10
+        xg, xo = x.cpu().numpy(), o.vcycle(slot, b)
+        assert _rel(xg, xo) <= 1e-10 and _maxrel(xg, xo) <= 1e-10, (slot, _maxrel(xg, xo))
+    s.close()
+
+
+@pytest.mark.parametrize("name,make", SMALL + [
+    ("two_phase_4x4x3_tiny", lambda: synth.two_phase(4, 4, 3)),
+    ("channels_20x18x16", lambda: synth.channels(20, 18, 16, seed=2))],
+    ids=[s[0] for s in SMALL] + ["two_phase_4x4x3_tiny", "channels_20x18x16"])
+def test_jacobian_spmv_matches_oracle_elementwise(name, make):
+    """The FP64 Jacobian product of every FGMRES iteration (w = A z_j),
+    through the C ABI, against the oracle's row sums: every entry within
+    1e-12 of its own scale sum_j |a_ij x_j|."""
+    p = make()
+    A = mgr.DeviceMatrix(p)
+    rng = np.random.default_rng(3)
+    for x in (rng.standard_normal(p.n), np.abs(rng.standard_normal(p.n)) + 1.0):
+        y = torch.full((p.n,), float("nan"), dtype=torch.float64, device="cuda")
+        mgr.mgr_spmv(A, torch.from_numpy(x).cuda(), y)
+        torch.cuda.synchronize()
+        ok, nbad = _spmv_bound_ok(p, x, y.cpu().numpy(), oracle.csr_spmv(p.row_ptr, p.col, p.val, x))
+        assert ok, f"{nbad} entries outside the bound"
+
+
+@pytest.mark.parametrize("name,make", SMALL[1:], ids=[s[0] for s in SMALL[1:]])
+def test_mixed_precision_apply_within_fp32_bound(name, make):
+    """One application of the FP32 preconditioner (MGR_MIXED) and each of its
+    V-cycles against the oracle's FP64 ones, element-wise.  Bound 1e-4 of the
+    largest entry: every stored value and intermediate vector carries an FP32
+    rounding (unit roundoff 6e-8), and the smoothers' and coarse solves'
+    conditioning (below ~1e3 on these operators) amplifies it."""
+    p = make()
+    o = oracle.Oracle(p)
+    s = mgr.Solver(p, precision=mgr.MGR_MIXED)
+    rng = np.random.default_rng(17)
+    v = rng.standard_normal(p.n)
+    z = s.apply(torch.from_numpy(v).cuda()).cpu().numpy()
+    err = _maxrel(z, o.apply(v))
+    assert err <= 1e-4, err
+    assert err > 0.0          # it really ran in FP32
+    for slot in range(o.num_levels + 1):
+        if o.amg_levels(slot) == 0:
+            continue
+        nA = o.scipy(oracle.Q_AMG_A, slot, 0).shape[0]
+        b = rng.standard_normal(nA)
+        x = torch.zeros(nA, dtype=torch.float64, device="cuda")
+        mgr.mgr_vcycle(s.h, slot, torch.from_numpy(b).cuda(), x)
+        torch.cuda.synchronize()
+        assert _maxrel(x.cpu().numpy(), o.vcycle(slot, b)) <= 1e-4
+    s.close()
+
+
+@pytest.mark.parametrize("name,make", SMALL[1:] + [("config2_64x64x32", lambda: synth.config(2))],
+                         ids=[s[0] for s in SMALL[1:]] + ["config2_64x64x32"])
+def test_bf16_smoother_diagonals_solution_matches_oracle(name, make):
+    """diag_bf16 (MGR_MIXED): the l1-Jacobi diagonals, D_FF^-1 and the 2x2
+    block inverses read in BF16.  The preconditioner changes by the BF16
+    rounding of those values (unit roundoff 2^-9 ~ 2e-3), which flexible GMRES
+    absorbs: the solution stays within 1e-6 of the oracle's and the
+    iterations within +-2 of the oracle's.  One application differs from the
+    oracle's FP64 one by the diagonal rounding, below 5e-2 of its largest
+    entry (a few 2e-3 perturbations per level, damped by the smoothers)."""
+    p = make()
+    o = oracle.Oracle(p)
+    ref = o.fgmres(p.rhs)
+    s = mgr.Solver(p, precision=mgr.MGR_MIXED, diag_bf16=1)
+    v = np.random.default_rng(23).standard_normal(p.n)
+    z = s.apply(torch.from_numpy(v).cuda()).cpu().numpy()
+    err = _maxrel(z, o.apply(v))
+    assert 0.0 < err <= 5e-2, err
+    r = s.solve(torch.from_numpy(p.rhs).cuda())
+    assert r["converged"] and r["relres"] <= 1e-8
+    assert abs(r["iters"] - ref["iters"]) <= 2, (r["iters"], ref["iters"])
+    assert _rel(r["x"].cpu().numpy(), ref["x"]) <= 1e-6
+    s.close()
+
+
+def test_directed_star_hierarchy_matches_oracle():
+    """Scalar matrix whose strength graph is a directed star (the PMIS weight
+    pin): C/F marks, strength, P, R and the Galerkin operator bit-exact."""
+    from tests.test_oracle_pins import directed_star_matrix
+    from tests.helpers import scalar_problem
+    p = scalar_problem(directed_star_matrix())
+    o = oracle.Oracle(p, num_levels=0, amg_max_coarse=1)
+    s = mgr.Solver(p, num_levels=0, amg_max_coarse=1)
+    compare_hierarchy(o, s.h, 0)
+    assert mgr.mgr_get_cf(s.h, 0, 0).tolist() == [1] + [-1] * 7
     s.close()
 
 
@@ -189,7 +290,8 @@ def test_invalid_arguments_are_rejected():
     with pytest.raises(mgr.MgrError) as e:   # F = every label: empty C set
         mgr.mgr_setup(A, mgr.mgr_options_default(True, f_label_mask=[0b111, 0b10]))
     assert e.value.code == -1
-    for bad in (dict(global_smoother=[0, 3]), dict(ilu_solve_sweeps=-1)):
+    for bad in (dict(global_smoother=[0, 3]), dict(ilu_solve_sweeps=-1), dict(diag_bf16=1),
+                dict(diag_bf16=2, precision=mgr.MGR_MIXED)):
         with pytest.raises(mgr.MgrError) as e:
             mgr.mgr_setup(A, mgr.mgr_options_default(True, **bad))
         assert e.value.code == -1

@@ -447,6 +447,18 @@ def test_vcycle_symmetric_and_contracting_on_poisson():
     assert rho < 0.9
 
 
+def test_jacobian_product_equals_library_product():
+    """The Arnoldi step's y = A x (with and without a hierarchy) against
+    scipy's sparse product, to rounding: |dy_i| <= 1e-14 sum_j |a_ij x_j|."""
+    p = synth.two_phase(7, 6, 5, seed=2)
+    A = p.to_scipy()
+    x = np.random.default_rng(9).standard_normal(p.n)
+    ref = A @ x
+    bound = 1e-14 * (abs(A) @ np.abs(x))
+    for y in (oracle.Oracle(p).matvec(x), oracle.csr_spmv(p.row_ptr, p.col, p.val, x)):
+        assert np.all(np.abs(y - ref) <= bound)
+
+
 # --------------------------------------------------------------- full solves
 def test_single_phase_solve_matches_direct_solver():
     p = synth.config(1)
