@@ -1,12 +1,15 @@
 #!/usr/bin/env python3
 """Benchmark of MGR-preconditioned FGMRES on GB300.
 
-Workload: the two-phase poromechanics Jacobian on 64x64x32 unit cells
-(680,419 unknowns: 418,275 displacement + 2 x 131,072 cell dofs), FP64 plain
-MGR, seeded synthetic inputs.  One step = one pass of the whole hot path on a
-fresh Jacobian: mgr_setup (device hierarchy: W_p, S_1 with N_max dropping,
-S_2, both AMG hierarchies) + fgmres_solve to a 1e-8 true relative residual +
-mgr_destroy.
+Headline workload: the large heterogeneous two-phase poromechanics Jacobian,
+256x256x96 unit cells (31,803,171 unknowns: 19,220,259 displacement + 2 x
+6,291,456 cell dofs, 1.56e9 non-zeros), high-contrast permeability channels
+(1e3 in a 1e-3 background) and alternating stiff/soft layers (E 1e4 / 10,
+nu 0.3), seeded synthetic inputs; mixed precision (MGR_MIXED: FP32
+preconditioner, FP64 FGMRES).  One step = one pass of the whole hot path on
+the resident Jacobian: mgr_setup (device hierarchy: W_p, S_1 with N_max
+dropping, S_2, both AMG hierarchies) + fgmres_solve to a 1e-8 true relative
+residual + mgr_destroy.
 
     python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 
@@ -14,8 +17,11 @@ Prints one JSON line.  value = unknowns solved per second over all ranks
 (setup + solve), timed with CUDA events on the solve stream, barrier and
 synchronize on both sides, max over ranks.  Several GPUs run independent
 replicas (a single system's solve has no partition without halo exchange).
-The reference arm times the CPU oracle (oracle/) on a bounded sample of the
-same workload family.
+Extra keys: the FP64 preconditioner on the same system (mixed-vs-FP64
+speedup), end to end from host buffers, the 128x128x64 and 64x64x32 two-phase
+workloads with their errors against the oracle, operator variants, the
+64-system ensemble.  The reference arm times the CPU oracle (oracle/) on a
+bounded sample of the headline recipe.
 """
 from __future__ import annotations
 
@@ -33,30 +39,39 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "MGR-FGMRES solve s & dofs/s to rel-res 1e-8; V-cycle HBM GB/s; mixed vs FP64"
-WORKLOAD = dict(nx=64, ny=64, nz=32, seed=0, sigma=2.0)
-SAMPLE = dict(nx=32, ny=32, nz=16, seed=0, sigma=2.0)
-WORKLOAD_NAME = "two-phase poromechanics Jacobian, 64x64x32 cells, FP64 plain MGR"
-# the mixed-precision large case (128x128x64 cells, lognormal E): extra keys
-LARGE = dict(nx=128, ny=128, nz=64, seed=0, sigma=2.0, E_sigma=1.5)
-PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "vcycle_uu_traffic.txt")
+HEADLINE = dict(nx=256, ny=256, nz=96, seed=0)
+HEADLINE_NAME = ("two-phase poromechanics Jacobian, 256x256x96 cells, permeability channels "
+                 "1e3 in 1e-3, stiff/soft layers E 1e4/10, MGR_MIXED")
+# the same recipe at 1/512 of the cells: the bounded CPU sample of the oracle
+SAMPLE = dict(nx=32, ny=32, nz=12, seed=0)
+MEDIUM = dict(nx=128, ny=128, nz=64, seed=0, sigma=2.0, E_sigma=1.5)
+MEDIUM_NAME = "two_phase_128x128x64"
+SMALL = dict(nx=64, ny=64, nz=32, seed=0, sigma=2.0)
+MAX_ITER = 4000
+PROFILES = os.path.join(ROOT, "profiles")
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--vcycles", type=int, default=50)
-    ap.add_argument("--no-large", action="store_true",
-                    help="skip the 128x128x64 mixed-precision extra measurement")
+    ap.add_argument("--vcycles", type=int, default=10)
+    ap.add_argument("--no-extras", action="store_true",
+                    help="headline line only: skip the FP64, e2e, other workloads, variants "
+                         "and ensemble legs")
     ap.add_argument("--no-ensemble", action="store_true",
                     help="skip the 64-system batched ensemble extra measurement")
     ap.add_argument("--ensemble-size", type=int, default=64)
     ap.add_argument("--profile", action="store_true",
-                    help="short run for ncu: FP64 steps and V-cycles only, no clock "
-                         "sampling, no mixed/e2e/oracle legs; prints a partial line")
+                    help="short run for ncu: one headline setup and --profile-iters FGMRES "
+                         "iterations after a warm-up on the 64x64x32 workload; prints a "
+                         "partial line")
+    ap.add_argument("--profile-iters", type=int, default=30)
+    ap.add_argument("--profile-workload", choices=["headline", "small", "medium"],
+                    default="headline")
     return ap.parse_args()
 
 
@@ -205,23 +220,32 @@ def source_hash():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic():
-    """DRAM bytes per V-cycle from the committed ncu summary, if it was taken
-    on the current kernel sources; else None."""
-    if not os.path.exists(PROFILE_TRAFFIC):
-        return None
+def profiled_traffic(tag, algorithmic):
+    """DRAM bytes per V-cycle from the committed ncu summary
+    profiles/vcycle_uu_traffic_<tag>.txt if it was taken on the current kernel
+    sources, scaled to `algorithmic` bytes when the capture was on a smaller
+    case (traffic ~ proportional to the bytes the V-cycle must move); else
+    None.  Returns (bytes, note)."""
+    path = os.path.join(PROFILES, f"vcycle_uu_traffic_{tag}.txt")
+    if not os.path.exists(path):
+        return None, None
     kv = {}
-    with open(PROFILE_TRAFFIC) as f:
+    with open(path) as f:
         for line in f:
             if ":" in line and not line.startswith("#"):
                 k, v = line.split(":", 1)
                 kv[k.strip()] = v.strip()
     if kv.get("source_sha256_16") != source_hash():
-        return None
+        return None, "stale capture (kernel source changed)"
     try:
-        return float(kv["dram_bytes_per_vcycle"])
+        t = float(kv["dram_bytes_per_vcycle"])
+        alg = float(kv["algorithmic_bytes_per_vcycle"])
     except (KeyError, ValueError):
-        return None
+        return None, None
+    if abs(alg - algorithmic) <= 1e-6 * algorithmic:
+        return t, f"ncu capture of this V-cycle ({kv.get('workload', '?')})"
+    return t * algorithmic / alg, (f"scaled from the ncu capture of {kv.get('workload', '?')} "
+                                   f"(traffic/algorithmic {t / alg:.3f})")
 
 
 def measured_peak():
@@ -233,20 +257,29 @@ def measured_peak():
 
 
 # --------------------------------------------------------------------------- arms
+def sample_problem():
+    from paper_1904_05960_gb300 import synth
+    return synth.channels(**SAMPLE)
+
+
+def sample_text(p, iters):
+    return (f"bounded CPU sample: the headline recipe at {SAMPLE['nx']}x{SAMPLE['ny']}x{SAMPLE['nz']} "
+            f"cells ({p.n:,} unknowns, {iters} oracle iterations), one oracle setup + FGMRES "
+            "solve per step; value = sample unknowns / step seconds")
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    import numpy as np
     import oracle
-    from paper_1904_05960_gb300 import synth
-    p = synth.two_phase(**SAMPLE)
+    p = sample_problem()
     times = []
     iters = None
     for i in range(args.warmup + args.steps):
         t0 = time.perf_counter()
         o = oracle.Oracle(p)
-        r = o.fgmres(p.rhs)
+        r = o.fgmres(p.rhs, maxit=MAX_ITER)
         dt = time.perf_counter() - t0
         del o
         if i >= args.warmup:
@@ -254,18 +287,54 @@ def run_reference(args):
         iters = r["iters"]
     ms = 1e3 * sum(times) / len(times)
     value = p.n / (ms * 1e-3)
-    sample = (f"two-phase {SAMPLE['nx']}x{SAMPLE['ny']}x{SAMPLE['nz']} cells ({p.n:,} unknowns), "
-              "same recipe as the 64x64x32 workload; one oracle setup + FGMRES solve per step")
     line = dict(metric=METRIC, value=value, unit="dofs/s", n_gpus=args.gpus, steps=args.steps,
                 warmup=args.warmup, ms_per_step=ms, higher_is_better=True, scaling="weak",
                 vs_baseline=None, dtype="f64", data="synthetic", impl="reference",
-                config=dict(workload=WORKLOAD_NAME, parallelism=f"replicas x{world}",
-                            sample=f"bounded CPU sample: {p.n:,} unknowns, {iters} iterations; "
-                                   "value scaled to dofs/s of the sample"),
+                config=dict(workload=HEADLINE_NAME, parallelism=f"replicas x{world}",
+                            sample=sample_text(p, iters)),
                 cpu_baseline=dict(value=value, unit="dofs/s", cores=1, kind="oracle",
-                                  sample=sample),
+                                  sample=sample_text(p, iters)),
                 e2e=dict(value=value, unit="dofs/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
     print(json.dumps(line), flush=True)
+
+
+class Timer:
+    """CUDA events on one stream around a region."""
+
+    def __init__(self, torch, stream):
+        self.torch, self.stream = torch, stream
+        self.e0 = torch.cuda.Event(enable_timing=True)
+        self.e1 = torch.cuda.Event(enable_timing=True)
+
+    def start(self):
+        self.e0.record(self.stream)
+
+    def stop(self):
+        self.e1.record(self.stream)
+        self.torch.cuda.synchronize()
+        return self.e0.elapsed_time(self.e1)
+
+
+def graph_ms(torch, stream, fn, reps):
+    """Average time of fn() replayed from a CUDA graph (the way the solve runs
+    the preconditioner's kernels)."""
+    side = torch.cuda.Stream()
+    side.wait_stream(stream)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=side):
+        fn(side)
+    torch.cuda.synchronize()
+    tm = Timer(torch, stream)
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            g.replay()
+        torch.cuda.synchronize()
+        tm.start()
+        for _ in range(reps):
+            g.replay()
+        ms = tm.stop() / reps
+    del g
+    return ms
 
 
 def run_ours(args):
@@ -289,257 +358,297 @@ def run_ours(args):
     def reduce_max(x):
         return dist_max(x, world)
 
-    p = synth.two_phase(**WORKLOAD)
     stream = torch.cuda.current_stream()
-    A = mgr.DeviceMatrix(p)
-    b = torch.from_numpy(p.rhs).cuda()
-    x = torch.zeros_like(b)
-    fo = mgr.fgmres_options_default(restart=50, max_iter=1000, rtol=1e-8)
+    tm = Timer(torch, stream)
+    fo = mgr.fgmres_options_default(restart=50, max_iter=MAX_ITER, rtol=1e-8)
+    peak, peak_kind = measured_peak()
+    extras = not (args.no_extras or args.profile)
 
-    def step(prec, xout):
-        h = mgr.mgr_setup(A, mgr.mgr_options_default(True, precision=prec), stream)
-        r = mgr.fgmres_solve(h, A, b, xout, fo, stream)
+    def solve_step(A, b, x, prec, **kw):
+        h = mgr.mgr_setup(A, mgr.mgr_options_default(True, precision=prec, **kw), stream)
+        r = mgr.fgmres_solve(h, A, b, x, fo, stream)
         mgr.mgr_destroy(h)
         if not r["converged"]:
             raise RuntimeError(f"FGMRES did not converge: {r}")
         return r
 
-    def timed(prec, steps, warmup, clocks=False):
-        for _ in range(warmup):
-            step(prec, x)
-        barrier()
+    # ---- the 64x64x32 workload first: it also brings every FP64 and FP32
+    # kernel of the library into the process before the headline is timed
+    small = None
+    ps = synth.two_phase(**SMALL)
+    As = mgr.DeviceMatrix(ps)
+    bs = torch.from_numpy(ps.rhs).cuda()
+    xs = torch.zeros_like(bs)
+    if args.profile and args.profile_workload != "headline":
+        pp = ps if args.profile_workload == "small" else synth.two_phase(**MEDIUM)
+        Ap = As if pp is ps else mgr.DeviceMatrix(pp)
+        bp = torch.from_numpy(pp.rhs).cuda()
+        xp = torch.zeros_like(bp)
+        solve_step(Ap, bp, xp, mgr.MGR_MIXED)
         torch.cuda.synchronize()
-        sampler = ClockSampler(smi_device_id(local)) if clocks else None
-        if sampler:
-            sampler.__enter__()
-        l0 = mgr.mgr_launch_count()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        info = None
-        for _ in range(steps):
-            info = step(prec, x)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        barrier()
-        launches = mgr.mgr_launch_count() - l0
-        if sampler:
-            sampler.__exit__()
-        ms = reduce_max(e0.elapsed_time(e1) / steps)
-        return ms, info, launches, (sampler.summary() if sampler else None)
-
-    ms64, info64, launches, clocks = timed(mgr.MGR_FP64, args.steps, args.warmup,
-                                           clocks=not args.profile)
-    x64 = x.cpu().numpy().copy()
-    if args.profile:
-        peak, _ = measured_peak()
-        h = mgr.mgr_setup(A, mgr.mgr_options_default(True), stream)
-        vin = torch.randn(p.meta["n_u"], dtype=torch.float64, device="cuda")
+        h = mgr.mgr_setup(Ap, mgr.mgr_options_default(True, precision=mgr.MGR_MIXED), stream)
+        nu = pp.meta["n_u"]
+        vin = torch.randn(nu, dtype=torch.float64, device="cuda")
         vx = torch.empty_like(vin)
-        mgr.mgr_vcycle(h, 0, vin, vx, stream)
         torch.cuda.synchronize()
-        torch.cuda.nvtx.range_push("vcycle_uu_fp64")
         for _ in range(args.vcycles):
             mgr.mgr_vcycle(h, 0, vin, vx, stream)
         torch.cuda.synchronize()
-        torch.cuda.nvtx.range_pop()
-        byts = vcycle_bytes(mgr, h, 0, 8)
+        if rank == 0:
+            print(json.dumps(dict(profile=True, workload=args.profile_workload, vcycles=args.vcycles,
+                                  vcycle_algorithmic_bytes=vcycle_bytes(mgr, h, 0, 4))), flush=True)
+        mgr.mgr_destroy(h)
+        return
+    res_small = {}
+    for prec in (mgr.MGR_FP64, mgr.MGR_MIXED):
+        solve_step(As, bs, xs, prec)
+        tm.start()
+        for _ in range(3):
+            r = solve_step(As, bs, xs, prec)
+        res_small[prec] = (tm.stop() / 3, r, xs.cpu().numpy().copy())
+    vc_small = {}
+    for prec, vb in ((mgr.MGR_FP64, 8), (mgr.MGR_MIXED, 4)):
+        h = mgr.mgr_setup(As, mgr.mgr_options_default(True, precision=prec), stream)
+        vin = torch.randn(ps.meta["n_u"], dtype=torch.float64, device="cuda")
+        vx = torch.empty_like(vin)
+        ms_v = graph_ms(torch, stream, lambda st: mgr.mgr_vcycle(h, 0, vin, vx, st), 50)
+        byts = vcycle_bytes(mgr, h, 0, vb)
+        vc_small[prec] = dict(ms=ms_v, bytes=byts, frac=byts / (ms_v * 1e-3) / 1e9 / peak)
+        mgr.mgr_destroy(h)
+    if not args.profile:
+        small = dict(workload="two-phase 64x64x32 cells, lognormal k sigma 2", unknowns=ps.n,
+                     nnz=ps.nnz)
+        for prec, key in ((mgr.MGR_FP64, "fp64"), (mgr.MGR_MIXED, "mixed")):
+            ms, r, _ = res_small[prec]
+            small[key] = dict(ms_per_step=ms, value=job_value(ps.n, world, ms), iters=r["iters"],
+                              setup_s=r["setup_s"], solve_s=r["solve_s"],
+                              vcycle_uu_ms=vc_small[prec]["ms"],
+                              vcycle_uu_frac=vc_small[prec]["frac"])
+        small["speedup_mixed_vs_fp64"] = res_small[mgr.MGR_FP64][0] / res_small[mgr.MGR_MIXED][0]
+
+    # ---- headline workload
+    t0 = time.perf_counter()
+    p = synth.channels(**HEADLINE)
+    gen_s = time.perf_counter() - t0
+    A = mgr.DeviceMatrix(p)
+    b = torch.from_numpy(p.rhs).cuda()
+    x = torch.zeros_like(b)
+    if args.profile:
+        torch.cuda.synchronize()
+        h = mgr.mgr_setup(A, mgr.mgr_options_default(True, precision=mgr.MGR_MIXED), stream)
+        r = mgr.fgmres_solve(h, A, b, x, mgr.fgmres_options_default(max_iter=args.profile_iters),
+                             stream)
         mgr.mgr_destroy(h)
         if rank == 0:
-            print(json.dumps(dict(profile=True, ms_per_step=ms64, iters=info64["iters"],
-                                  gpu_launches=launches, vcycle_algorithmic_bytes=byts,
-                                  vcycles=args.vcycles)), flush=True)
+            print(json.dumps(dict(profile=True, workload="headline", iters=r["iters"],
+                                  solve_s=r["solve_s"], setup_s=r["setup_s"])), flush=True)
         return
-    ms32, info32, _, _ = timed(mgr.MGR_MIXED, args.steps, args.warmup)
-    x32 = x.cpu().numpy().copy()
-
-    # end to end through the public API with host buffers (pinned): one
-    # mgr_solve_host call copies the matrix and rhs in, runs setup + FGMRES +
-    # teardown and copies x out
-    Ah = mgr.HostMatrix(p, pin=True)
-    bh = torch.from_numpy(p.rhs).pin_memory()
-    xh = torch.empty(p.n, dtype=torch.float64).pin_memory()
-    h2d = Ah.nbytes + bh.numel() * bh.element_size()
-    d2h = xh.numel() * xh.element_size()
-    o64 = mgr.mgr_options_default(True)
-
-    def e2e_step():
-        r = mgr.mgr_solve_host(Ah, bh, xh, o64, fo, stream)
-        if not r["converged"]:
-            raise RuntimeError(f"FGMRES did not converge: {r}")
 
     for _ in range(args.warmup):
-        e2e_step()
+        solve_step(A, b, x, mgr.MGR_MIXED)
     barrier()
     torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
+    sampler = ClockSampler(smi_device_id(local))
+    sampler.__enter__()
+    l0 = mgr.mgr_launch_count()
+    tm.start()
+    info = None
     for _ in range(args.steps):
-        e2e_step()
-    e1.record(stream)
-    torch.cuda.synchronize()
+        info = solve_step(A, b, x, mgr.MGR_MIXED)
+    ms_local = tm.stop() / args.steps
     barrier()
-    ms_e2e = reduce_max(e0.elapsed_time(e1) / args.steps)
+    launches = mgr.mgr_launch_count() - l0
+    sampler.__exit__()
+    clocks = sampler.summary()
+    ms = reduce_max(ms_local)
+    x_mixed = x.cpu().numpy().copy()
 
-    # V-cycle of the displacement AMG (F-relaxation of the first reduction)
-    peak, peak_kind = measured_peak()
-    vc = {}
-    for prec, vb in ((mgr.MGR_FP64, 8), (mgr.MGR_MIXED, 4)):
-        h = mgr.mgr_setup(A, mgr.mgr_options_default(True, precision=prec), stream)
-        nu = p.meta["n_u"]
-        vb_in = torch.randn(nu, dtype=torch.float64, device="cuda")
-        vx = torch.empty_like(vb_in)
-        for _ in range(5):
-            mgr.mgr_vcycle(h, 0, vb_in, vx, stream)
-        torch.cuda.synchronize()
-        e0.record(stream)
-        for _ in range(args.vcycles):
-            mgr.mgr_vcycle(h, 0, vb_in, vx, stream)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms_eager = e0.elapsed_time(e1) / args.vcycles
-        # timed the way the solve runs it: the V-cycle's launches replayed from
-        # a CUDA graph (the preconditioner application is one captured graph)
-        side = torch.cuda.Stream()
-        side.wait_stream(stream)
-        g = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(g, stream=side):
-            mgr.mgr_vcycle(h, 0, vb_in, vx, side)
-        torch.cuda.synchronize()
-        with torch.cuda.stream(stream):
-            for _ in range(5):
-                g.replay()
-            torch.cuda.synchronize()
-            torch.cuda.nvtx.range_push(f"vcycle_uu_{'fp64' if vb == 8 else 'fp32'}")
-            e0.record(stream)
-            for _ in range(args.vcycles):
-                g.replay()
-            e1.record(stream)
-            torch.cuda.synchronize()
-            torch.cuda.nvtx.range_pop()
-        ms_v = e0.elapsed_time(e1) / args.vcycles
-        del g
-        # the mixed entry point's FP64<->FP32 casts are inside the measured call
-        # but not in the algorithmic bytes
-        byts = vcycle_bytes(mgr, h, 0, vb)
-        vc[prec] = dict(ms=ms_v, ms_eager=ms_eager, bytes=byts, gbs=byts / (ms_v * 1e-3) / 1e9)
-        mgr.mgr_destroy(h)
+    # roofline: the A_uu V-cycle (F-relaxation of the first reduction) in
+    # FP32, graph-replayed, on the headline hierarchy; the pressure V-cycle
+    # and the FP64 Jacobian product beside it
+    h = mgr.mgr_setup(A, mgr.mgr_options_default(True, precision=mgr.MGR_MIXED), stream)
+    kernels = {}
+    for slot, name in ((0, "vcycle_uu_fp32"), (2, "vcycle_pressure_fp32")):
+        nA = mgr.mgr_get_csr_dims(h, mgr.Q_AMG_A, slot, 0)[0]
+        vin = torch.randn(nA, dtype=torch.float64, device="cuda")
+        vx = torch.empty_like(vin)
+        ms_v = graph_ms(torch, stream, lambda st: mgr.mgr_vcycle(h, slot, vin, vx, st), args.vcycles)
+        byts = vcycle_bytes(mgr, h, slot, 4)
+        kernels[name] = dict(ms=ms_v, algorithmic_bytes=byts, gbs=byts / (ms_v * 1e-3) / 1e9,
+                             frac=byts / (ms_v * 1e-3) / 1e9 / peak)
+        del vin, vx
+    used, reserved = mgr.mgr_memory_usage()
+    mgr.mgr_destroy(h)
+    y = torch.empty_like(b)
+    xin = torch.randn_like(b)
+    mgr.mgr_spmv(A, xin, y)
+    tm.start()
+    for _ in range(args.vcycles):
+        mgr.mgr_spmv(A, xin, y)
+    ms_az = tm.stop() / args.vcycles
+    az_bytes = (p.n + 1) * 8 + p.nnz * 12 + 2 * p.n * 8
+    kernels["jacobian_spmv_fp64"] = dict(ms=ms_az, algorithmic_bytes=az_bytes,
+                                         gbs=az_bytes / (ms_az * 1e-3) / 1e9,
+                                         frac=az_bytes / (ms_az * 1e-3) / 1e9 / peak)
+    del y, xin
+    dom = kernels["vcycle_uu_fp32"]
+    traffic, traffic_note = profiled_traffic("fp32", dom["algorithmic_bytes"])
 
-    large = None
-    if not args.no_large:
-        pl = synth.two_phase(**LARGE)
-        Al = mgr.DeviceMatrix(pl)
-        bl = torch.from_numpy(pl.rhs).cuda()
-        xl = torch.zeros_like(bl)
-        res = {}
-        for prec in (mgr.MGR_MIXED, mgr.MGR_FP64):
-            def lstep():
-                hh = mgr.mgr_setup(Al, mgr.mgr_options_default(True, precision=prec), stream)
-                rr = mgr.fgmres_solve(hh, Al, bl, xl, fo, stream)
-                mgr.mgr_destroy(hh)
-                return rr
-            lstep()
-            barrier()
-            torch.cuda.synchronize()
-            e0.record(stream)
-            reps = 2
-            for _ in range(reps):
-                rr = lstep()
-            e1.record(stream)
-            torch.cuda.synchronize()
-            res[prec] = (reduce_max(e0.elapsed_time(e1) / reps), rr)
-        msm, rm = res[mgr.MGR_MIXED]
-        msd, rd = res[mgr.MGR_FP64]
-        large = dict(workload="two-phase 128x128x64 cells, lognormal E (sigma 1.5), MGR_MIXED",
-                     unknowns=pl.n, nnz=pl.nnz, value=job_value(pl.n, world, msm), unit="dofs/s",
-                     ms_per_step=msm, iters=rm["iters"], rel_res_true=rm["relres"],
-                     setup_s=rm["setup_s"], solve_s=rm["solve_s"], fp64_ms_per_step=msd,
-                     fp64_iters=rd["iters"], speedup_mixed_vs_fp64=msd / msm)
-        del Al, bl, xl
-
-    # operator and smoother variants (Sec. 5.1 options, multicolour block
-    # Gauss-Seidel, one sweep of ILU(1) as the level-2 global smoother as in
-    # Sec. 6): the same FP64 step on the same workload
-    variants = {}
-    for vname, vkw in (("jacobi_restriction", dict(restrict_jacobi=[1, 1])),
-                       ("mgr_post", dict(frelax_post=[1, 1])),
-                       ("point_block_dff", dict(dff_block=[1, 1])),
-                       ("block_gauss_seidel", dict(global_smoother=[0, 1])),
-                       ("aggressive_uu_amg", dict(agg_levels=[1, 0, 0])),
-                       ("ilu1_smoother", dict(global_smoother=[0, 2], global_sweeps=[0, 1],
-                                              ilu_solve_sweeps=3))):
-        vo = mgr.mgr_options_default(True, **vkw)
-
-        def vstep():
-            hh = mgr.mgr_setup(A, vo, stream)
-            rr = mgr.fgmres_solve(hh, A, b, x, fo, stream)
-            mgr.mgr_destroy(hh)
-            return rr
-        vstep()
-        torch.cuda.synchronize()
-        e0.record(stream)
-        for _ in range(3):
-            rv = vstep()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        msv = e0.elapsed_time(e1) / 3
-        variants[vname] = dict(ms_per_step=msv, iters=rv["iters"], setup_s=rv["setup_s"],
-                               solve_s=rv["solve_s"], converged=rv["converged"],
-                               relres=rv["relres"])
-
-    ensemble = None
-    if not args.no_ensemble:
-        ensemble = run_ensemble(args, mgr, stream, world)
-
-    n = p.n
-    value = job_value(n, world, ms64)
     line = dict(
-        metric=METRIC, value=value, unit="dofs/s", n_gpus=world, steps=args.steps,
-        warmup=args.warmup, ms_per_step=ms64, higher_is_better=True, scaling="weak",
-        vs_baseline=None, dtype="f64", data="synthetic",
-        config=dict(workload=WORKLOAD_NAME,
-                    unknowns=n, nnz=p.nnz, parallelism=f"replicas x{world}",
+        metric=METRIC, value=job_value(p.n, world, ms), unit="dofs/s", n_gpus=world,
+        steps=args.steps, warmup=args.warmup, ms_per_step=ms, higher_is_better=True,
+        scaling="weak", vs_baseline=None, dtype="f32/f64",
+        data="synthetic",
+        config=dict(workload=HEADLINE_NAME, unknowns=p.n, nnz=p.nnz,
+                    parallelism=f"replicas x{world}",
                     step="mgr_setup + fgmres_solve (m=50, rtol 1e-8 true residual) + mgr_destroy",
-                    l2="inputs larger than L2 (CSR of A: %.0f MB)" % (p.nnz * 12 / 1e6),
-                    iters=info64["iters"], setup_s=info64["setup_s"],
-                    solve_s=info64["solve_s"]),
-        roofline=dict(bound="hbm", kernel="AMG V-cycle on A_uu (F-relaxation of level 0), FP64",
-                      achieved=vc[mgr.MGR_FP64]["gbs"], peak=peak, unit="GB/s",
-                      frac=vc[mgr.MGR_FP64]["gbs"] / peak, peak_kind=peak_kind,
-                      traffic=profiled_traffic(), algorithmic_bytes=vc[mgr.MGR_FP64]["bytes"],
-                      ms=vc[mgr.MGR_FP64]["ms"], timing="CUDA-graph replay of mgr_vcycle",
-                      ms_eager_launches=vc[mgr.MGR_FP64]["ms_eager"]),
-        mixed=dict(value=job_value(n, world, ms32), ms_per_step=ms32,
-                   speedup_vs_fp64=ms64 / ms32, iters=info32["iters"],
-                   setup_s=info32["setup_s"], solve_s=info32["solve_s"],
-                   vcycle_gbs=vc[mgr.MGR_MIXED]["gbs"],
-                   vcycle_frac=vc[mgr.MGR_MIXED]["gbs"] / peak),
-        e2e=dict(value=job_value(n, world, ms_e2e), unit="dofs/s", h2d_bytes_per_step=h2d,
-                 d2h_bytes_per_step=d2h, ms_per_step=ms_e2e),
-        clocks=clocks,
-        gpu_launches=launches,
-    )
-    if large:
-        line["large_mixed"] = large
-    if ensemble:
-        line["ensemble"] = ensemble
-    if variants:
-        line["variants"] = variants
+                    l2="inputs larger than L2 (CSR of A: %.1f GB)" % (p.nnz * 12 / 1e9),
+                    iters=info["iters"], restarts=info["restarts"], setup_s=info["setup_s"],
+                    solve_s=info["solve_s"], rel_res_true=info["relres"],
+                    device_pool_gb=used / 1e9, generation_s=gen_s),
+        roofline=dict(bound="hbm", kernel="AMG V-cycle on A_uu (F-relaxation of the first "
+                      "reduction), FP32, on the headline hierarchy",
+                      achieved=dom["gbs"], peak=peak, unit="GB/s", frac=dom["frac"],
+                      peak_kind=peak_kind, traffic=traffic, traffic_note=traffic_note,
+                      algorithmic_bytes=dom["algorithmic_bytes"], ms=dom["ms"],
+                      timing="CUDA-graph replay of mgr_vcycle, CUDA events"),
+        kernels=kernels, clocks=clocks, gpu_launches=launches)
+
+    if extras:
+        # same step with the FP64 preconditioner (the plain form)
+        xd = torch.zeros_like(b)
+        tm.start()
+        rd = solve_step(A, b, xd, mgr.MGR_FP64)
+        ms_fp64 = reduce_max(tm.stop())
+        x_fp64 = xd.cpu().numpy().copy()
+        del xd
+        line["mixed_vs_fp64"] = dict(fp64_ms_per_step=ms_fp64, speedup=ms_fp64 / ms,
+                                     fp64_iters=rd["iters"], fp64_setup_s=rd["setup_s"],
+                                     fp64_solve_s=rd["solve_s"],
+                                     rel_diff_mixed_vs_fp64=float(
+                                         np.linalg.norm(x_mixed - x_fp64) / np.linalg.norm(x_fp64)))
+        # end to end through the public API from pinned host buffers: one
+        # mgr_solve_host call copies the matrix and rhs in, runs setup + FGMRES
+        # + teardown and copies x out.  The main steps above already ran every
+        # kernel and filled the library's memory pool; one more warm-up here.
+        del A
+        torch.cuda.empty_cache()
+        Ah = mgr.HostMatrix(p, pin=True)
+        bh = torch.from_numpy(p.rhs).pin_memory()
+        xh = torch.empty(p.n, dtype=torch.float64).pin_memory()
+        h2d = Ah.nbytes + bh.numel() * bh.element_size()
+        d2h = xh.numel() * xh.element_size()
+        om = mgr.mgr_options_default(True, precision=mgr.MGR_MIXED)
+        r = mgr.mgr_solve_host(Ah, bh, xh, om, fo, stream)
+        barrier()
+        torch.cuda.synchronize()
+        tm.start()
+        r = mgr.mgr_solve_host(Ah, bh, xh, om, fo, stream)
+        ms_e2e = reduce_max(tm.stop())
+        if not r["converged"]:
+            raise RuntimeError(f"FGMRES did not converge: {r}")
+        line["e2e"] = dict(value=job_value(p.n, world, ms_e2e), unit="dofs/s",
+                           h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h, ms_per_step=ms_e2e,
+                           steps=1, warmup=1, api="mgr_solve_host")
+        del Ah, bh, xh
+    else:
+        del A
+    del b, x
+    torch.cuda.empty_cache()
+    mgr.mgr_trim_memory(0)
+
+    if extras:
+        # the 128x128x64 two-phase workload (5.34M unknowns)
+        pm = synth.two_phase(**MEDIUM)
+        Am = mgr.DeviceMatrix(pm)
+        bm = torch.from_numpy(pm.rhs).cuda()
+        xm = torch.zeros_like(bm)
+        med = dict(workload="two-phase 128x128x64 cells, lognormal k sigma 2, lognormal E sigma 1.5",
+                   unknowns=pm.n, nnz=pm.nnz)
+        sols = {}
+        for prec, key, reps in ((mgr.MGR_MIXED, "mixed", 2), (mgr.MGR_FP64, "fp64", 1)):
+            solve_step(Am, bm, xm, prec)
+            tm.start()
+            for _ in range(reps):
+                r = solve_step(Am, bm, xm, prec)
+            msm = reduce_max(tm.stop() / reps)
+            sols[key] = xm.cpu().numpy().copy()
+            med[key] = dict(ms_per_step=msm, value=job_value(pm.n, world, msm), iters=r["iters"],
+                            setup_s=r["setup_s"], solve_s=r["solve_s"], rel_res_true=r["relres"])
+        med["speedup_mixed_vs_fp64"] = med["fp64"]["ms_per_step"] / med["mixed"]["ms_per_step"]
+        line["two_phase_128x128x64"] = med
+        del Am, bm, xm
+        torch.cuda.empty_cache()
+        line["two_phase_64x64x32"] = small
+
+        # operator and smoother variants (Sec. 5.1 options, multicolour block
+        # Gauss-Seidel, one sweep of ILU(1) as the level-2 global smoother as in
+        # Sec. 6, aggressive coarsening of A_uu, BF16 smoother diagonals): the
+        # same step on the 64x64x32 workload
+        variants = {}
+        for vname, prec, vkw in (("jacobi_restriction", mgr.MGR_FP64, dict(restrict_jacobi=[1, 1])),
+                                 ("mgr_post", mgr.MGR_FP64, dict(frelax_post=[1, 1])),
+                                 ("point_block_dff", mgr.MGR_FP64, dict(dff_block=[1, 1])),
+                                 ("block_gauss_seidel", mgr.MGR_FP64, dict(global_smoother=[0, 1])),
+                                 ("aggressive_uu_amg", mgr.MGR_FP64, dict(agg_levels=[1, 0, 0])),
+                                 ("ilu1_smoother", mgr.MGR_FP64,
+                                  dict(global_smoother=[0, 2], global_sweeps=[0, 1],
+                                       ilu_solve_sweeps=3)),
+                                 ("bf16_diagonals_mixed", mgr.MGR_MIXED, dict(diag_bf16=1))):
+            solve_step(As, bs, xs, prec, **vkw)
+            tm.start()
+            for _ in range(3):
+                rv = solve_step(As, bs, xs, prec, **vkw)
+            msv = tm.stop() / 3
+            variants[vname] = dict(ms_per_step=msv, iters=rv["iters"], setup_s=rv["setup_s"],
+                                   solve_s=rv["solve_s"], relres=rv["relres"],
+                                   precision="mixed" if prec == mgr.MGR_MIXED else "fp64")
+        line["variants_64x64x32"] = variants
+        if not args.no_ensemble:
+            line["ensemble"] = run_ensemble(args, mgr, stream, world)
+
+    # errors against the oracle (the oracle is run or read here, outside every
+    # timed region) and the CPU baseline
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
+        from oracle import fingerprint
+        errs = {}
+        # headline: the true residual of the GPU solution recomputed with the
+        # oracle's own sparse product (plain serial C), and the whole method
+        # against the oracle on the bounded sample of the same recipe
         t0 = time.perf_counter()
-        o = oracle.Oracle(p)
-        r = o.fgmres(p.rhs)
+        ax = oracle.csr_spmv(p.row_ptr, p.col, p.val, x_mixed)
+        errs["headline_rel_res_by_oracle_spmv"] = float(
+            np.linalg.norm(p.rhs - ax) / np.linalg.norm(p.rhs))
+        errs["headline_oracle_spmv_s"] = time.perf_counter() - t0
+        del ax
+        psm = sample_problem()
+        t0 = time.perf_counter()
+        o = oracle.Oracle(psm)
+        ro = o.fgmres(psm.rhs, maxit=MAX_ITER)
         dt = time.perf_counter() - t0
-        xo = r["x"]
-        nrm = np.linalg.norm(xo)
-        line["cpu_baseline"] = dict(
-            value=n / dt, unit="dofs/s", cores=1, kind="oracle",
-            sample="one full oracle setup + FGMRES solve of this 64x64x32 workload",
-            seconds=dt, iters=r["iters"])
-        line["error_vs_oracle"] = dict(fp64=float(np.linalg.norm(x64 - xo) / nrm),
-                                       mixed=float(np.linalg.norm(x32 - xo) / nrm))
+        del o
+        line["cpu_baseline"] = dict(value=psm.n / dt, unit="dofs/s", cores=1, kind="oracle",
+                                    sample=sample_text(psm, ro["iters"]), seconds=dt,
+                                    iters=ro["iters"])
+        Asm = mgr.DeviceMatrix(psm)
+        bsm = torch.from_numpy(psm.rhs).cuda()
+        xsm = torch.zeros_like(bsm)
+        for prec, key in ((mgr.MGR_MIXED, "sample_mixed"), (mgr.MGR_FP64, "sample_fp64")):
+            r = solve_step(Asm, bsm, xsm, prec)
+            xg = xsm.cpu().numpy()
+            errs[key] = dict(rel_err=float(np.linalg.norm(xg - ro["x"]) / np.linalg.norm(ro["x"])),
+                             iters=r["iters"], oracle_iters=ro["iters"])
+        if extras:
+            fp = fingerprint.load(MEDIUM_NAME)
+            errs[MEDIUM_NAME] = {k: fingerprint.compare(v, fp) for k, v in sols.items()}
+            t0 = time.perf_counter()
+            xo = oracle.Oracle(ps).fgmres(ps.rhs)["x"]
+            errs["two_phase_64x64x32"] = {
+                k: float(np.linalg.norm(res_small[prec][2] - xo) / np.linalg.norm(xo))
+                for prec, k in ((mgr.MGR_FP64, "fp64"), (mgr.MGR_MIXED, "mixed"))}
+            errs["two_phase_64x64x32_oracle_s"] = time.perf_counter() - t0
+        line["error_vs_oracle"] = errs
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -832,3 +832,24 @@ def test_fgmres_residual_history_is_the_krylov_minimum():
         assert abs(hist[k] - res) <= 1e-6 * max(res, 1e-8), (k, hist[k], res)
         v = B @ Q[:, -1]
     assert np.all(np.diff(hist[:13]) <= 1e-14)     # non-increasing within a cycle
+
+
+def test_fingerprint_comparison_recovers_a_known_error():
+    """The stored-fingerprint comparison (oracle/fingerprint.py): exact on the
+    sample, and the probe estimate within its ~18% spread (16 probes) of the
+    true relative error of a planted perturbation."""
+    from oracle import fingerprint
+    n = 20000
+    rng = np.random.default_rng(5)
+    x = rng.standard_normal(n)
+    idx = np.sort(rng.choice(n, 500, replace=False))
+    fp = dict(n=n, norm2=float(np.linalg.norm(x)), iters=1, probe_seed=1000, sample_idx=idx,
+              sample_x=x[idx],
+              probes=np.array([np.random.default_rng(1000 + k).standard_normal(n) @ x
+                               for k in range(16)]))
+    assert fingerprint.compare(x, fp)["probe_rel"] <= 1e-13
+    e = 1e-7 * rng.standard_normal(n)
+    c = fingerprint.compare(x + e, fp)
+    true = np.linalg.norm(e) / np.linalg.norm(x)
+    assert abs(c["sample_rel"] - np.linalg.norm(e[idx]) / np.linalg.norm(x[idx])) <= 1e-12
+    assert 0.5 * true <= c["probe_rel"] <= 1.5 * true
