@@ -388,9 +388,10 @@ def run_ours(args):
         Ap = As if pp is ps else mgr.DeviceMatrix(pp)
         bp = torch.from_numpy(pp.rhs).cuda()
         xp = torch.zeros_like(bp)
-        solve_step(Ap, bp, xp, mgr.MGR_MIXED)
+        solve_step(Ap, bp, xp, mgr.MGR_MIXED, **HEADLINE_OPTS)
         torch.cuda.synchronize()
-        h = mgr.mgr_setup(Ap, mgr.mgr_options_default(True, precision=mgr.MGR_MIXED), stream)
+        h = mgr.mgr_setup(Ap, mgr.mgr_options_default(True, precision=mgr.MGR_MIXED,
+                                                      **HEADLINE_OPTS), stream)
         nu = pp.meta["n_u"]
         vin = torch.randn(nu, dtype=torch.float64, device="cuda")
         vx = torch.empty_like(vin)
