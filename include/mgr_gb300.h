@@ -302,22 +302,35 @@ int mgr_vcycle_noalloc(mgr_handle_t h, int slot, const double* b, double* x, voi
  * FGMRES iteration and convergence test.  The paper solves one system per
  * run; these entries add nothing to its method (Sec. 5-6): system i's
  * hierarchy is exactly what mgr_setup builds for A[i] alone and its solution
- * exactly what fgmres_solve returns for it alone.  They run the systems
- * concurrently: host worker threads (native, one CUDA stream each) take the
- * systems largest first, so that the GPU executes several systems' captured
- * preconditioner graphs, Jacobian products and Gram-Schmidt kernels at once.
+ * exactly what fgmres_solve returns for it alone.  Two schedules:
+ *   workers: host worker threads (native, one CUDA stream each) take the
+ *     systems largest first, so that the GPU executes several systems'
+ *     captured preconditioner graphs, Jacobian products and Gram-Schmidt
+ *     kernels at once;
+ *   lockstep: every system advances one FGMRES iteration per round, each
+ *     phase of the round being one launch for all systems still iterating --
+ *     the preconditioner applications as ONE CUDA graph with a conditional
+ *     branch per system (its captured application; branches of finished
+ *     systems are switched off on the device), the Jacobian products as one
+ *     row-binned launch per lanes-per-row group, the Gram-Schmidt passes over
+ *     all systems' rows, and one readback of every Hessenberg column.  Each
+ *     system's arithmetic is its single-system arithmetic, so its iterations
+ *     and solution are bit for bit those of fgmres_solve.
  */
 typedef struct mgr_batch_s* mgr_batch_t;
 
 /* Set up nsys systems A[0..nsys) with the same options.  `workers` = number of
- * concurrent workers (1..16); 0 lets the library choose it by timing one
- * concurrent round of every system's preconditioner application with 1, 2, 4,
- * 8 and 16 workers (the fastest is kept; see mgr_batch_info).  The setups
+ * concurrent workers (1..16) of the worker schedule; -1 selects the lockstep
+ * schedule; 0 lets the library choose by timing one round of every system's
+ * preconditioner application with 1, 2, 4, 8 and 16 workers and with the
+ * lockstep graph (the fastest is kept; see mgr_batch_info).  The setups
  * themselves run on up to 16 workers.  Ordered after the caller's earlier work
  * on `stream`; synchronises `stream` before returning.  A[i] is owned by the
  * caller and may be freed afterwards.  Errors: INVALID_ARG (nsys <= 0, workers
- * > 16, or any system's mgr_setup argument error), and every error of
- * mgr_setup (the first one met; nothing is kept then). */
+ * > 16 or < -1, or any system's mgr_setup argument error), CUDA (workers = -1
+ * and the lockstep graph cannot be built; with workers = 0 the worker
+ * schedules remain), and every error of mgr_setup (the first one met;
+ * nothing is kept then). */
 int mgr_setup_batched(int nsys, const mgr_matrix_t* A, const mgr_options_t* o, int workers,
                       void* stream, mgr_batch_t* out);
 
@@ -332,11 +345,12 @@ int fgmres_solve_batched(mgr_batch_t bh, const mgr_matrix_t* A, const double* co
                          double* const* x, const fgmres_options_t* o, fgmres_info_t* info,
                          void* stream);
 
-/* Worker count in use, host wall time of the batched setup (s), and the
- * autotuner's record: tune_workers[5] = the worker counts it timed (1, 2, 4,
- * 8, 16, each capped at nsys, repeats dropped; 0 after the last) and
- * tune_ms[5] = their round times in ms (-1 after the last).  Nothing is timed
- * when workers were given to mgr_setup_batched.  Any pointer may be NULL. */
+/* Schedule in use (*workers: the worker count, or -1 for lockstep), host wall
+ * time of the batched setup (s), and the autotuner's record: tune_workers[6]
+ * = the schedules it timed (worker counts 1, 2, 4, 8, 16, each capped at nsys,
+ * repeats dropped, then -1 for lockstep; 0 after the last) and tune_ms[6] =
+ * their round times in ms (-1 after the last).  Nothing is timed when the
+ * schedule was given to mgr_setup_batched.  Any pointer may be NULL. */
 int mgr_batch_info(mgr_batch_t bh, int* workers, double* setup_s, int* tune_workers,
                    double* tune_ms);
 

@@ -489,6 +489,8 @@ static void vcycle(Amg* g, int k, const T* b, T* x, cudaStream_t s) {
   vcycle_ws<T>(g, k, b, x, W, s);
 }
 
+// ---- end of the AMG V-cycle: kernels and launch rules above this line ----
+
 // Global relaxation by point-block Jacobi or multicolour point-block
 // Gauss-Seidel sweeps from zero (z = M_glo^-1 v), block inverses in storage D.
 template <class T, class D>
@@ -740,6 +742,35 @@ int capture_apply_graph(Handle* h) {
   (void)cudaGetLastError();
   return MGR_SUCCESS;
 }
+
+// Capture one preconditioner application over the handle's fixed buffers
+// (FP64: gin -> gout; MGR_MIXED: vin32 -> zout32) into an existing graph (the
+// body of a conditional node of the lockstep batch graph).
+int capture_apply_into(Handle* h, cudaGraph_t body, long long* kernels) {
+  const bool mixed = h->opt.precision == MGR_MIXED;
+  if (!mixed && (!h->gin || !h->gout)) return MGR_ERR_INVALID_ARG;
+  cudaStream_t cs;
+  MGR_TRY_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  const long long before = g_launches.load();
+  cudaError_t e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0,
+                                                cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    if (mixed) mgr_level<float>(h, 0, h->vin32, h->zout32, cs);
+    else mgr_level<double>(h, 0, h->gin, h->gout, cs);
+    cudaGraph_t out = nullptr;
+    e = cudaStreamEndCapture(cs, &out);
+  }
+  if (kernels) *kernels = g_launches.load() - before;
+  g_launches.store(before);
+  cudaStreamDestroy(cs);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    return MGR_ERR_CUDA;
+  }
+  return MGR_SUCCESS;
+}
+
+int spmv_lanes(int64_t nnz, int64_t nr) { return pick_group(nnz, nr); }
 
 int apply_mgr(Handle* h, const double* v, double* z, cudaStream_t s) {
   if (h->opt.precision == MGR_MIXED) {

@@ -7,9 +7,19 @@
 // each with its own CUDA stream, takes systems largest first, so the GPU runs
 // several systems' captured preconditioner graphs, Jacobian products and
 // Gram-Schmidt kernels at once; small systems, whose kernels are too short
-// to fill the GPU, overlap with large ones.  The number of workers is chosen
-// at setup by timing one concurrent round of every system's preconditioner
-// graph with 1, 2, 4, 8 and 16 workers (the schedule autotuner).
+// to fill the GPU, overlap with large ones.
+//
+// The lockstep schedule instead advances every system one FGMRES iteration
+// per round with one launch per phase for all systems: the preconditioner
+// applications as one CUDA graph in which each system's captured application
+// is the body of a conditional node (a kernel at the graph's head switches the
+// branches of finished systems off), the Jacobian products as one row-binned
+// launch per lanes-per-row group, the Gram-Schmidt passes over all systems'
+// chunk blocks, and one readback of all Hessenberg columns (krylov.cu).
+//
+// The schedule autotuner times one round of every system's preconditioner
+// application with 1, 2, 4, 8 and 16 workers and with the lockstep graph,
+// and keeps the fastest.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -30,7 +40,8 @@ static constexpr uint32_t BATCH_MAGIC = 0x4d475242u;
 struct Batch {
   uint32_t magic = BATCH_MAGIC;
   int nsys = 0;
-  int workers = 1;                    // chosen worker count
+  int workers = 1;                    // chosen worker count (-1: lockstep)
+  Lockstep* ls = nullptr;             // lockstep plan (when built)
   std::vector<Handle*> sys;
   std::vector<int> order;             // systems by decreasing size
   std::vector<cudaStream_t> streams;  // one per worker (BATCH_MAX_WORKERS)
@@ -105,8 +116,86 @@ static int apply_fixed(Handle* h, cudaStream_t s) {
   return apply_mgr(h, h->gin, h->gout, s);
 }
 
+// The lockstep graph: a head kernel setting each system's branch condition
+// from its flag, then one conditional node per system whose body is that
+// system's captured preconditioner application.
+__global__ void k_set_branches(const unsigned long long* __restrict__ cond,
+                               const int* __restrict__ flag, int n) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) cudaGraphSetConditional(cond[i], flag[i] ? 1u : 0u);
+}
+
+static int build_lockstep(Batch* B, cudaStream_t s) {
+  const int ns = B->nsys;
+  for (Handle* h : B->sys)
+    if (h->opt.precision != B->sys[0]->opt.precision) return MGR_ERR_INVALID_ARG;
+  Lockstep* L = new (std::nothrow) Lockstep();
+  if (!L) return MGR_ERR_OOM;
+  B->ls = L;
+  L->nsys = ns;
+  L->mixed = B->sys[0]->opt.precision == MGR_MIXED;
+  L->pool.s = s;
+  L->flag = L->pool.get<int>(ns);
+  L->cond = L->pool.get<unsigned long long>(ns);
+  if (L->pool.err) return L->pool.err;
+  cudaGraph_t g = nullptr;
+  MGR_TRY_CUDA(cudaGraphCreate(&g, 0));
+  int rc = MGR_SUCCESS;
+  std::vector<cudaGraphConditionalHandle> hc(ns);
+  for (int i = 0; i < ns && !rc; i++)
+    if (cudaGraphConditionalHandleCreate(&hc[i], g, 0, cudaGraphCondAssignDefault) != cudaSuccess)
+      rc = MGR_ERR_CUDA;
+  cudaGraphNode_t head = nullptr;
+  if (!rc) {
+    if (cudaMemcpyAsync(L->cond, hc.data(), sizeof(unsigned long long) * ns, cudaMemcpyHostToDevice,
+                        s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess)
+      rc = MGR_ERR_CUDA;
+  }
+  if (!rc) {
+    cudaKernelNodeParams kp = {};
+    int n = ns;
+    void* args[] = {&L->cond, &L->flag, &n};
+    kp.func = (void*)k_set_branches;
+    kp.gridDim = dim3(1);
+    kp.blockDim = dim3(256);
+    kp.kernelParams = args;
+    if (cudaGraphAddKernelNode(&head, g, nullptr, 0, &kp) != cudaSuccess) rc = MGR_ERR_CUDA;
+  }
+  L->body_kernels.assign(ns, 0);
+  for (int i = 0; i < ns && !rc; i++) {
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = hc[i];
+    np.conditional.type = cudaGraphCondTypeIf;
+    np.conditional.size = 1;
+    cudaGraphNode_t cn = nullptr;
+    if (cudaGraphAddNode(&cn, g, &head, nullptr, 1, &np) != cudaSuccess) {
+      rc = MGR_ERR_CUDA;
+      break;
+    }
+    long long k = 0;
+    rc = capture_apply_into(B->sys[i], np.conditional.phGraph_out[0], &k);
+    L->body_kernels[i] = k;
+    L->graph_nodes += k;
+  }
+  if (!rc && cudaGraphInstantiate(&L->exec, g, 0) != cudaSuccess) rc = MGR_ERR_CUDA;
+  cudaGraphDestroy(g);
+  (void)cudaGetLastError();
+  return rc;
+}
+
+// One lockstep round: every system's preconditioner application through the
+// conditional graph.
+static int lockstep_round(Batch* B, cudaStream_t s) {
+  std::vector<int> ones(B->nsys, 1);
+  MGR_TRY_CUDA(cudaMemcpyAsync(B->ls->flag, ones.data(), sizeof(int) * B->nsys,
+                               cudaMemcpyHostToDevice, s));
+  MGR_TRY_CUDA(cudaGraphLaunch(B->ls->exec, s));
+  MGR_TRY_CUDA(cudaStreamSynchronize(s));
+  return MGR_SUCCESS;
+}
+
 // Schedule autotuner: time one round (one application per system) for each
-// worker count and keep the fastest.
+// worker count and for the lockstep graph, and keep the fastest.
 static int autotune_workers(Batch* B, cudaStream_t caller) {
   for (Handle* h : B->sys) {
     if (h->opt.precision == MGR_MIXED) {
@@ -144,6 +233,21 @@ static int autotune_workers(Batch* B, cudaStream_t caller) {
       B->workers = w;
     }
   }
+  if (B->ls && B->ls->exec) {
+    double t = 0.0;
+    for (int rep = 0; rep < 2; rep++) {
+      MGR_TRY_CUDA(cudaDeviceSynchronize());
+      const auto t0 = std::chrono::steady_clock::now();
+      MGR_TRY(lockstep_round(B, caller));
+      t = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    }
+    B->tune_workers.push_back(-1);
+    B->tune_ms.push_back(t);
+    if (t < best) {
+      best = t;
+      B->workers = -1;
+    }
+  }
   return MGR_SUCCESS;
 }
 
@@ -158,7 +262,7 @@ int mgr_setup_batched(int nsys, const mgr_matrix_t* A, const mgr_options_t* o, i
   (void)cudaGetLastError();  // errors of earlier calls are not this call's
   if (!out) return MGR_ERR_INVALID_ARG;
   *out = nullptr;
-  if (nsys <= 0 || !A || !o || workers > BATCH_MAX_WORKERS) return MGR_ERR_INVALID_ARG;
+  if (nsys <= 0 || !A || !o || workers > BATCH_MAX_WORKERS || workers < -1) return MGR_ERR_INVALID_ARG;
   Batch* B = new (std::nothrow) Batch();
   if (!B) return MGR_ERR_OOM;
   B->nsys = nsys;
@@ -183,12 +287,18 @@ int mgr_setup_batched(int nsys, const mgr_matrix_t* A, const mgr_options_t* o, i
   if (rc >= 0) rc = end_on(B, caller);
   if (rc >= 0 && cudaStreamSynchronize(caller) != cudaSuccess) rc = MGR_ERR_CUDA;
   B->setup_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-  if (rc >= 0) {
-    if (workers > 0) {
-      B->workers = std::min(workers, nsys);
-    } else {
-      rc = autotune_workers(B, caller);
+  if (rc >= 0 && workers <= 0) {
+    rc = build_lockstep(B, caller);
+    if (rc < 0 && workers == 0) {   // the worker schedules remain
+      delete B->ls;
+      B->ls = nullptr;
+      rc = MGR_SUCCESS;
     }
+  }
+  if (rc >= 0) {
+    if (workers > 0) B->workers = std::min(workers, nsys);
+    else if (workers < 0) B->workers = -1;
+    else rc = autotune_workers(B, caller);
   }
   if (rc < 0) {
     mgr_destroy_batched(reinterpret_cast<mgr_batch_t>(B));
@@ -207,6 +317,12 @@ int fgmres_solve_batched(mgr_batch_t bh, const mgr_matrix_t* A, const double* co
   for (int i = 0; i < B->nsys; i++)
     if (A[i].n != B->sys[i]->n || !b[i] || !x[i]) return MGR_ERR_INVALID_ARG;
   cudaStream_t caller = (cudaStream_t)stream;
+  if (B->workers < 0) {
+    for (Handle* h : B->sys) h->pool.s = caller;
+    int rc = fgmres_lockstep(B->ls, B->sys.data(), A, b, x, o, info, caller);
+    if (rc >= 0 && cudaStreamSynchronize(caller) != cudaSuccess) rc = MGR_ERR_CUDA;
+    return rc;
+  }
   MGR_TRY(begin_on(B, caller));
   int rc = run_workers(B, B->workers, [&](int i, cudaStream_t s) {
     (void)cudaGetLastError();
@@ -226,7 +342,7 @@ int mgr_batch_info(mgr_batch_t bh, int* workers, double* setup_s, int* tune_work
   if (!B || B->magic != BATCH_MAGIC) return MGR_ERR_INVALID_ARG;
   if (workers) *workers = B->workers;
   if (setup_s) *setup_s = B->setup_s;
-  for (int c = 0; c < 5; c++) {
+  for (int c = 0; c < 6; c++) {
     const bool have = c < (int)B->tune_ms.size();
     if (tune_workers) tune_workers[c] = have ? B->tune_workers[c] : 0;
     if (tune_ms) tune_ms[c] = have ? B->tune_ms[c] : -1.0;
@@ -246,6 +362,11 @@ int mgr_destroy_batched(mgr_batch_t bh) {
   if (!B || B->magic != BATCH_MAGIC) return MGR_ERR_INVALID_ARG;
   for (cudaStream_t ws : B->streams)
     if (ws) cudaStreamSynchronize(ws);
+  if (B->ls) {
+    cudaDeviceSynchronize();
+    delete B->ls;
+    B->ls = nullptr;
+  }
   for (Handle* h : B->sys)
     if (h) mgr_destroy(reinterpret_cast<mgr_handle_t>(h));
   for (cudaStream_t ws : B->streams)

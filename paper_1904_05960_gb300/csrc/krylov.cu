@@ -44,17 +44,21 @@ __device__ inline double block_sum(double v, double* sh) {
 // each warp then reduces whole vectors in a fixed order.  With UPDATE the block
 // first replaces its slice of w by w - sum_i h[i] V_i (classical Gram-Schmidt
 // update) and takes the dots with the updated w while V's slice is still in
-// cache, so the update and the next projection cost one pass.
+// cache, so the update and the next projection cost one pass.  Block `blk`
+// owns the chunk [blk * KB * MD_EPT, (blk + 1) * KB * MD_EPT); the body is
+// shared by the single-system kernel and the lockstep (many-system) kernel, so
+// both give the same bits.
 static constexpr int MD_EPT = 8;
+static constexpr int MD_CHUNK = KB * MD_EPT;
 template <bool UPDATE>
-__global__ void __launch_bounds__(KB) k_mdot(const double* __restrict__ V, int64_t ld, int nv,
-                                             double* __restrict__ w, int64_t n,
-                                             double* __restrict__ part,
-                                             const double* __restrict__ h) {
+__device__ __forceinline__ void mdot_body(const double* __restrict__ V, int64_t ld, int nv,
+                                          double* __restrict__ w, int64_t n,
+                                          double* __restrict__ part, const double* __restrict__ h,
+                                          int64_t blk) {
   __shared__ double sh[16][KB];
   __shared__ double hs[64];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int64_t base = (int64_t)blockIdx.x * (KB * MD_EPT) + threadIdx.x;
+  const int64_t base = blk * MD_CHUNK + threadIdx.x;
   double wr[MD_EPT];
 #pragma unroll
   for (int e = 0; e < MD_EPT; e++) {
@@ -100,24 +104,31 @@ __global__ void __launch_bounds__(KB) k_mdot(const double* __restrict__ V, int64
       for (int k = lane; k < KB; k += 32) s2 += sh[q][k];
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(FULL, s2, o);
-      if (lane == 0) part[(int64_t)blockIdx.x * nv + i0 + q] = s2;
+      if (lane == 0) part[blk * nv + i0 + q] = s2;
     }
     __syncthreads();
   }
 }
 
-static inline int mdot_blocks(int64_t n) { return (int)((n + KB * MD_EPT - 1) / (KB * MD_EPT)); }
+template <bool UPDATE>
+__global__ void __launch_bounds__(KB) k_mdot(const double* __restrict__ V, int64_t ld, int nv,
+                                             double* __restrict__ w, int64_t n,
+                                             double* __restrict__ part,
+                                             const double* __restrict__ h) {
+  mdot_body<UPDATE>(V, ld, nv, w, n, part, h, blockIdx.x);
+}
+
+static inline int mdot_blocks(int64_t n) { return (int)((n + MD_CHUNK - 1) / MD_CHUNK); }
 
 // h[i] (+)= sum_blk part[blk * nv + i]: one warp per vector, fixed order.
 // With SQRT the sum is replaced by its square root (a norm from partial sums
 // of squares) and rinv[0] receives 1/norm (1 if the norm is 0), so the
 // scaling kernels multiply instead of dividing per element.
 template <bool SQRT>
-__global__ void k_mdot_final(const double* __restrict__ part, int nblk, int nv,
-                             double* __restrict__ h, int accumulate, double* __restrict__ rinv) {
+__device__ __forceinline__ void mdot_final_warp(const double* __restrict__ part, int nblk, int nv,
+                                                int i, double* __restrict__ h, int accumulate,
+                                                double* __restrict__ rinv) {
   const int lane = threadIdx.x & 31;
-  const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (i >= nv) return;
   double acc = 0.0;
 #pragma unroll 4
   for (int b = lane; b < nblk; b += 32) acc += part[(int64_t)b * nv + i];
@@ -132,18 +143,30 @@ __global__ void k_mdot_final(const double* __restrict__ part, int nblk, int nv,
   }
 }
 
-// w -= sum_i h[i] V_i; with NORM, also part[blk] = sum over the block of the
-// updated w^2 (fixed order).
+template <bool SQRT>
+__global__ void k_mdot_final(const double* __restrict__ part, int nblk, int nv,
+                             double* __restrict__ h, int accumulate, double* __restrict__ rinv) {
+  const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (i >= nv) return;
+  mdot_final_warp<SQRT>(part, nblk, nv, i, h, accumulate, rinv);
+}
+
+// w -= sum_i h[i] V_i over block blk's chunk (the layout of mdot_body); with
+// NORM, also part[blk] = the chunk's sum of the updated w^2 in a fixed order.
 template <bool NORM>
-__global__ void __launch_bounds__(KB) k_mupdate(const double* __restrict__ V, int64_t ld, int nv,
-                                                const double* __restrict__ h, double* __restrict__ w,
-                                                int64_t n, double* __restrict__ part) {
+__device__ __forceinline__ void mupdate_body(const double* __restrict__ V, int64_t ld, int nv,
+                                             const double* __restrict__ h, double* __restrict__ w,
+                                             int64_t n, double* __restrict__ part, int64_t blk) {
   __shared__ double hs[64];
   __shared__ double red[KB / 32];
   for (int i = threadIdx.x; i < nv; i += blockDim.x) hs[i] = h[i];
   __syncthreads();
   double sq = 0.0;
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+  const int64_t base = blk * MD_CHUNK + threadIdx.x;
+#pragma unroll 1
+  for (int e = 0; e < MD_EPT; e++) {
+    const int64_t t = base + (int64_t)e * KB;
+    if (t >= n) break;
     double acc = w[t];
     int i = 0;
     // eight loads issued before their multiply-adds: memory-level parallelism
@@ -166,9 +189,16 @@ __global__ void __launch_bounds__(KB) k_mupdate(const double* __restrict__ V, in
     if (threadIdx.x == 0) {
       double s2 = 0.0;
       for (int q = 0; q < KB / 32; q++) s2 += red[q];
-      part[blockIdx.x] = s2;
+      part[blk] = s2;
     }
   }
+}
+
+template <bool NORM>
+__global__ void __launch_bounds__(KB) k_mupdate(const double* __restrict__ V, int64_t ld, int nv,
+                                                const double* __restrict__ h, double* __restrict__ w,
+                                                int64_t n, double* __restrict__ part) {
+  mupdate_body<NORM>(V, ld, nv, h, w, n, part, blockIdx.x);
 }
 
 // x += sum_i y[i] Z_i  (Z in FP64 or FP32)
@@ -368,9 +398,9 @@ int fgmres_run(Handle* h, const mgr_matrix_t* A, const double* b, double* x,
           MGR_LAUNCH k_mdot<true><<<nb, KB, 0, s>>>(h->V, n, j + 1, h->w, n, h->part, h->hcol);
           MGR_LAUNCH k_mdot_final<false><<<(j + 1 + 7) / 8, 256, 0, s>>>(h->part, nb, j + 1, h->yv, 0, nullptr);
         }
-        MGR_LAUNCH k_mupdate<true><<<KGRID, KB, 0, s>>>(h->V, n, j + 1, h->yv, h->w, n, h->part);   // w -= V h2
+        MGR_LAUNCH k_mupdate<true><<<mdot_blocks(n), KB, 0, s>>>(h->V, n, j + 1, h->yv, h->w, n, h->part);   // w -= V h2
         MGR_LAUNCH k_mdot_final<false><<<(j + 1 + 7) / 8, 256, 0, s>>>(h->yv, 1, j + 1, h->hcol, 1, nullptr);   // h += h2
-        MGR_LAUNCH k_mdot_final<true><<<1, 32, 0, s>>>(h->part, KGRID, 1, h->hcol + j + 1, 0, h->hred + 1);     // ||w||
+        MGR_LAUNCH k_mdot_final<true><<<1, 32, 0, s>>>(h->part, mdot_blocks(n), 1, h->hcol + j + 1, 0, h->hred + 1);     // ||w||
         MGR_LAUNCH k_scale_by<<<grid_for(n, KB), KB, 0, s>>>(h->w, h->hred + 1, vnext, n);
         if (tr) cudaEventRecord(tev[3], s);
         MGR_TRY_CUDA(cudaMemcpyAsync(hp, h->hcol, sizeof(double) * (j + 2), cudaMemcpyDeviceToHost, s));
@@ -464,6 +494,641 @@ int fgmres_run(Handle* h, const mgr_matrix_t* A, const double* b, double* x,
     info->solve_s = ms * 1e-3;
   }
   return status;
+}
+
+}  // namespace mgr
+
+// ===========================================================================
+// Lockstep batch: every system of an ensemble advances one FGMRES iteration
+// per round, and each phase of the round is one launch over all systems that
+// take part in it (a device flag per system): the preconditioner applications
+// as one CUDA graph with a conditional branch per system, the Jacobian
+// products as one row-binned launch per lanes-per-row group, the Gram-Schmidt
+// passes as launches over every system's chunk blocks, and one readback of
+// all Hessenberg columns.  Each system's arithmetic is that of fgmres_run
+// (same kernels' per-element and per-block bodies, same lanes per row, same
+// host Givens), so its iterations and solution equal its single-system solve.
+// ===========================================================================
+namespace mgr {
+namespace {
+
+enum { LS_VW = 0, LS_RR = 1, LS_BB = 2 };   // which vectors a dot pass reads
+
+__device__ __forceinline__ int ls_sys_of(const int64_t* __restrict__ off, int cnt, int64_t g) {
+  int lo = 0, hi = cnt;   // off[lo] <= g < off[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (off[mid] <= g) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// per row of every flagged system: x = 0 (what 0) or r = b (what 1)
+__global__ void k_ls_init(const LsSys* __restrict__ S, const int* __restrict__ flag,
+                          const int64_t* __restrict__ roff, int nsys, int64_t nrows, int what) {
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < nrows;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    const int s = ls_sys_of(roff, nsys, g);
+    if (!flag[s]) continue;
+    const int64_t i = g - roff[s];
+    if (what == 0) S[s].x[i] = 0.0;
+    else S[s].r[i] = S[s].b[i];
+  }
+}
+
+// v_j into the fixed input of the system's preconditioner graph
+__global__ void k_ls_gather(const LsSys* __restrict__ S, const int* __restrict__ flag,
+                            const int* __restrict__ jcur, const int64_t* __restrict__ roff,
+                            int nsys, int64_t nrows, int mixed) {
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < nrows;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    const int s = ls_sys_of(roff, nsys, g);
+    if (!flag[s]) continue;
+    const LsSys& d = S[s];
+    const int64_t i = g - roff[s];
+    const double v = d.V[(int64_t)jcur[s] * d.n + i];
+    if (mixed) d.vin32[i] = (float)v;
+    else d.gin[i] = v;
+  }
+}
+
+// z_j from the graph's fixed output: stored as Z_j; under MGR_MIXED also
+// widened once into r (the FP64 operand of the Jacobian product)
+__global__ void k_ls_scatter(const LsSys* __restrict__ S, const int* __restrict__ flag,
+                             const int* __restrict__ jcur, const int64_t* __restrict__ roff,
+                             int nsys, int64_t nrows, int mixed) {
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < nrows;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    const int s = ls_sys_of(roff, nsys, g);
+    if (!flag[s]) continue;
+    const LsSys& d = S[s];
+    const int64_t i = g - roff[s];
+    const int64_t at = (int64_t)jcur[s] * d.n + i;
+    if (mixed) {
+      const float v = d.zout32[i];
+      ((float*)d.Z)[at] = v;
+      d.r[i] = (double)v;
+    } else {
+      ((double*)d.Z)[at] = d.gout[i];
+    }
+  }
+}
+
+// FP64 CSR product over the rows of the group's systems, G lanes per row
+// (the single-system product's lanes for these matrices, so each row's sum
+// is formed in the same order).  RES: r = b - A x; else w = A z_j.
+template <int G, bool RES>
+__global__ void __launch_bounds__(256)
+k_ls_spmv(const LsSys* __restrict__ S, const int* __restrict__ flag, const int* __restrict__ jcur,
+          const int* __restrict__ gsys, const int64_t* __restrict__ goff, int cnt, int64_t nrows,
+          int mixed) {
+  const int lane = threadIdx.x & (G - 1);
+  const int64_t stride = ((int64_t)gridDim.x * blockDim.x) / G;
+  for (int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G; g < nrows; g += stride) {
+    const int q = ls_sys_of(goff, cnt, g);
+    const int s = gsys[q];
+    if (!flag[s]) continue;
+    const LsSys& d = S[s];
+    const int64_t i = g - goff[q];
+    const double* x = RES ? d.x : (mixed ? d.r : (const double*)d.Z + (int64_t)jcur[s] * d.n);
+    const int64_t e0 = d.rp[i], e1 = d.rp[i + 1];
+    double acc = 0.0;
+    int64_t k = e0 + lane;
+#pragma unroll 4
+    for (; k < e1; k += G) acc += d.val[k] * __ldg(x + d.ci[k]);
+    const unsigned mask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << ((threadIdx.x & 31) & ~(G - 1)));
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(mask, acc, o, G);
+    if (lane == 0) {
+      if (RES) d.r[i] = d.b[i] - acc;
+      else d.w[i] = acc;
+    }
+  }
+}
+
+// block -> (system, chunk) for the chunk-block passes
+__device__ __forceinline__ bool ls_block(const LsSys* __restrict__ S, const int* __restrict__ flag,
+                                         const int32_t* __restrict__ blk_sys, int* s_out,
+                                         int64_t* c_out) {
+  const int s = blk_sys[blockIdx.x];
+  if (!flag[s]) return false;
+  *s_out = s;
+  *c_out = (int64_t)blockIdx.x - S[s].blk0;
+  return true;
+}
+
+template <bool UPDATE>
+__global__ void __launch_bounds__(KB)
+k_ls_mdot(const LsSys* __restrict__ S, const int* __restrict__ flag, const int* __restrict__ jcur,
+          const int32_t* __restrict__ blk_sys, double* __restrict__ part,
+          const double* __restrict__ Hc, int which) {
+  int s;
+  int64_t c;
+  if (!ls_block(S, flag, blk_sys, &s, &c)) return;
+  const LsSys& d = S[s];
+  double* ps = part + d.blk0 * LS_H;
+  if (which == LS_VW)
+    mdot_body<UPDATE>(d.V, d.n, jcur[s] + 1, d.w, d.n, ps, Hc + (int64_t)s * LS_H, c);
+  else if (which == LS_RR)
+    mdot_body<false>(d.r, d.n, 1, d.r, d.n, ps, nullptr, c);
+  else
+    mdot_body<false>(d.b, d.n, 1, const_cast<double*>(d.b), d.n, ps, nullptr, c);
+}
+
+template <bool NORM>
+__global__ void __launch_bounds__(KB)
+k_ls_mupdate(const LsSys* __restrict__ S, const int* __restrict__ flag, const int* __restrict__ jcur,
+             const int32_t* __restrict__ blk_sys, double* __restrict__ part,
+             const double* __restrict__ Yv) {
+  int s;
+  int64_t c;
+  if (!ls_block(S, flag, blk_sys, &s, &c)) return;
+  const LsSys& d = S[s];
+  mupdate_body<NORM>(d.V, d.n, jcur[s] + 1, Yv + (int64_t)s * LS_H, d.w, d.n,
+                     part + d.blk0 * LS_H, c);
+}
+
+// per flagged system, warp per vector i < nv (nv = j + 1, or 1 when `one`):
+// dst[s * dstride + (off_j ? j + 1 : 0) + i] (+)= the sum of its partials in
+// the single-system order -- the system's chunk partials in `part`, or (rows)
+// the one partial row part[s * LS_H ..] -- and with SQRT red[s * 4 + 1] = 1/norm
+template <bool SQRT>
+__global__ void k_ls_final(const LsSys* __restrict__ S, const int* __restrict__ flag,
+                           const int* __restrict__ jcur, const double* __restrict__ part, int rows,
+                           double* __restrict__ dst, int dstride, int off_j, int one,
+                           int accumulate, double* __restrict__ red) {
+  const int s = blockIdx.y;
+  if (!flag[s]) return;
+  const int nv = one ? 1 : jcur[s] + 1;
+  const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (i >= nv) return;
+  const LsSys& d = S[s];
+  double* h = dst + (int64_t)s * dstride + (off_j ? jcur[s] + 1 : 0);
+  if (rows)
+    mdot_final_warp<SQRT>(part + (int64_t)s * LS_H, 1, nv, i, h, accumulate, red + (int64_t)s * 4 + 1);
+  else
+    mdot_final_warp<SQRT>(part + d.blk0 * LS_H, d.nb, nv, i, h, accumulate, red + (int64_t)s * 4 + 1);
+}
+
+// V_(j+1) = w * rinv (what 0), or V_0 = r * rinv (what 1)
+__global__ void k_ls_scale(const LsSys* __restrict__ S, const int* __restrict__ flag,
+                           const int* __restrict__ jcur, const int64_t* __restrict__ roff,
+                           int nsys, int64_t nrows, const double* __restrict__ red, int what) {
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < nrows;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    const int s = ls_sys_of(roff, nsys, g);
+    if (!flag[s]) continue;
+    const LsSys& d = S[s];
+    const int64_t i = g - roff[s];
+    const double f = red[(int64_t)s * 4 + 1];
+    if (what == 0) d.V[(int64_t)(jcur[s] + 1) * d.n + i] = d.w[i] * f;
+    else d.V[i] = d.r[i] * f;
+  }
+}
+
+// x += sum_{i < jcur+1} y_i Z_i (jcur holds jend - 1 here), as k_xupdate
+template <class Z>
+__global__ void __launch_bounds__(KB)
+k_ls_xupdate(const LsSys* __restrict__ S, const int* __restrict__ flag, const int* __restrict__ jcur,
+             const int64_t* __restrict__ roff, int nsys, int64_t nrows, const double* __restrict__ Yv) {
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < nrows;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    const int s = ls_sys_of(roff, nsys, g);
+    if (!flag[s]) continue;
+    const LsSys& d = S[s];
+    const int64_t t = g - roff[s];
+    const int nv = jcur[s] + 1;
+    const double* ys = Yv + (int64_t)s * LS_H;
+    const Z* Zb = (const Z*)d.Z;
+    const int64_t ld = d.n;
+    double acc = d.x[t];
+    int i = 0;
+    for (; i + 8 <= nv; i += 8) {
+      double z[8];
+#pragma unroll
+      for (int q = 0; q < 8; q++) z[q] = (double)Zb[(int64_t)(i + q) * ld + t];
+#pragma unroll
+      for (int q = 0; q < 8; q++) acc += ys[i + q] * z[q];
+    }
+    for (; i < nv; i++) acc += ys[i] * (double)Zb[(int64_t)i * ld + t];
+    d.x[t] = acc;
+  }
+}
+
+}  // namespace
+
+int ensure_krylov_ws(Handle* h, int m) { return ensure_krylov(h, m, h->pool.s); }
+
+// flag / jcur uploads between two host synchronisations each use their own
+// pinned slot: an asynchronous copy reads its host source when it runs
+static constexpr int LS_SLOTS = 4;
+
+Lockstep::~Lockstep() {
+  if (exec) cudaGraphExecDestroy(exec);
+  if (hpin) cudaFreeHost(hpin);
+  if (ipin) cudaFreeHost(ipin);
+  pool.free_all();
+}
+
+// Sizes the per-solve plan (descriptors, block map, SpMV groups, reduction
+// buffers) for restart m; built once and kept for later solves.
+static int lockstep_plan(Lockstep* L, Handle** hs, const mgr_matrix_t* A, const double* const* b,
+                         double* const* x, int m, cudaStream_t s) {
+  const int ns = L->nsys;
+  for (int q = 0; q < ns; q++) MGR_TRY(ensure_krylov_ws(hs[q], m));
+  Pool& P = L->pool;
+  P.s = s;
+  if (!L->dsys) {
+    L->dsys = P.get<LsSys>(ns);
+    L->jcur = P.get<int>(ns);
+    L->roff = P.get<int64_t>(ns + 1);
+    L->Hc = P.get<double>((int64_t)ns * LS_H);
+    L->Yv = P.get<double>((int64_t)ns * LS_H);
+    L->red = P.get<double>((int64_t)ns * 4);
+    if (P.err) return P.err;
+    MGR_TRY_CUDA(cudaMallocHost(&L->hpin, sizeof(double) * ((size_t)ns * LS_H + (size_t)ns * 4)));
+    MGR_TRY_CUDA(cudaMallocHost(&L->ipin, sizeof(int) * 2 * (size_t)ns * LS_SLOTS));
+    std::vector<int64_t> roff(ns + 1, 0);
+    std::vector<int32_t> bsys;
+    std::vector<int> lanes(ns);
+    for (int q = 0; q < ns; q++) {
+      roff[q + 1] = roff[q] + hs[q]->n;
+      const int nb = mdot_blocks(hs[q]->n);
+      for (int k = 0; k < nb; k++) bsys.push_back(q);
+      lanes[q] = spmv_lanes(A[q].nnz, A[q].n);
+    }
+    L->nrows = roff[ns];
+    L->nblk = (int64_t)bsys.size();
+    L->blk_sys = P.get<int32_t>(L->nblk);
+    L->part = P.get<double>(L->nblk * LS_H);
+    if (P.err) return P.err;
+    MGR_TRY_CUDA(cudaMemcpyAsync(L->roff, roff.data(), sizeof(int64_t) * (ns + 1),
+                                 cudaMemcpyHostToDevice, s));
+    MGR_TRY_CUDA(cudaMemcpyAsync(L->blk_sys, bsys.data(), sizeof(int32_t) * L->nblk,
+                                 cudaMemcpyHostToDevice, s));
+    // row bins: the systems grouped by their lanes per row
+    for (int q = 0; q < ns; q++) {
+      size_t gi = 0;
+      while (gi < L->gl.size() && L->gl[gi] != lanes[q]) gi++;
+      if (gi == L->gl.size()) L->gl.push_back(lanes[q]);
+    }
+    for (size_t gi = 0; gi < L->gl.size(); gi++) {
+      std::vector<int> sy;
+      std::vector<int64_t> off(1, 0);
+      for (int q = 0; q < ns; q++)
+        if (lanes[q] == L->gl[gi]) {
+          sy.push_back(q);
+          off.push_back(off.back() + hs[q]->n);
+        }
+      int* gs = P.get<int>(sy.size());
+      int64_t* go = P.get<int64_t>(off.size());
+      if (P.err) return P.err;
+      MGR_TRY_CUDA(cudaMemcpyAsync(gs, sy.data(), sizeof(int) * sy.size(), cudaMemcpyHostToDevice, s));
+      MGR_TRY_CUDA(cudaMemcpyAsync(go, off.data(), sizeof(int64_t) * off.size(),
+                                   cudaMemcpyHostToDevice, s));
+      L->gsys.push_back(gs);
+      L->groff.push_back(go);
+      L->grows.push_back(off.back());
+      L->gcnt.push_back((int)sy.size());
+    }
+    MGR_TRY_CUDA(cudaStreamSynchronize(s));   // host vectors above go out of scope
+  }
+  std::vector<LsSys> d(ns);
+  int64_t blk0 = 0;
+  for (int q = 0; q < ns; q++) {
+    Handle* h = hs[q];
+    d[q].n = h->n;
+    d[q].rp = A[q].row_ptr;
+    d[q].ci = A[q].col_idx;
+    d[q].val = A[q].val;
+    d[q].b = b[q];
+    d[q].x = x[q];
+    d[q].V = h->V;
+    d[q].w = h->w;
+    d[q].r = h->r;
+    d[q].Z = h->Z;
+    d[q].vin32 = h->vin32;
+    d[q].zout32 = h->zout32;
+    d[q].gin = h->gin;
+    d[q].gout = h->gout;
+    d[q].blk0 = blk0;
+    d[q].nb = mdot_blocks(h->n);
+    blk0 += d[q].nb;
+  }
+  MGR_TRY_CUDA(cudaMemcpyAsync(L->dsys, d.data(), sizeof(LsSys) * ns, cudaMemcpyHostToDevice, s));
+  MGR_TRY_CUDA(cudaStreamSynchronize(s));
+  L->m = m;
+  return MGR_SUCCESS;
+}
+
+int fgmres_lockstep(Lockstep* L, Handle** hs, const mgr_matrix_t* A, const double* const* b,
+                    double* const* x, const fgmres_options_t* o, fgmres_info_t* info,
+                    cudaStream_t s) {
+  const int ns = L->nsys;
+  const int m = o->restart > 0 ? o->restart : 50;
+  if (m > 60) return MGR_ERR_INVALID_ARG;
+  const int maxit = o->max_iter > 0 ? o->max_iter : 1000;
+  const double rtol = o->rtol > 0 ? o->rtol : 1e-8;
+  MGR_TRY(lockstep_plan(L, hs, A, b, x, m, s));
+  const bool mixed = L->mixed;
+  struct Events {
+    cudaEvent_t e[2] = {};
+    ~Events() {
+      for (auto& q : e)
+        if (q) cudaEventDestroy(q);
+    }
+  } ev;
+  MGR_TRY_CUDA(cudaEventCreate(&ev.e[0]));
+  MGR_TRY_CUDA(cudaEventCreate(&ev.e[1]));
+  MGR_TRY_CUDA(cudaEventRecord(ev.e[0], s));
+
+  // host state per system, as in fgmres_run
+  struct St {
+    std::vector<double> H, cs, sn, g, y;
+    double bnorm = 0.0, beta = 0.0, relres = 1.0;
+    int iters = 0, restarts = 0, status = MGR_NOT_CONVERGED, j = 0, jend = 0;
+    bool done = false, cycle_end = false, restart = false;
+  };
+  std::vector<St> st(ns);
+  for (auto& t : st) {
+    t.H.assign((size_t)(m + 1) * m, 0.0);
+    t.cs.assign(m, 0.0);
+    t.sn.assign(m, 0.0);
+    t.g.assign(m + 1, 0.0);
+    t.y.assign(m, 0.0);
+  }
+  int slot = 0;
+  int* hflag = L->ipin;
+  int* hj = L->ipin + ns;
+  double* hH = L->hpin;
+  double* hred = L->hpin + (size_t)ns * LS_H;
+  const unsigned vg = grid_for(L->nrows, KB, 152 * 16);
+  const int nbk = (int)L->nblk;
+  // the flags / columns written since the last upload go out from the
+  // current slot; the host then writes the next slot
+  auto upload = [&]() -> int {
+    MGR_TRY_CUDA(cudaMemcpyAsync(L->flag, hflag, sizeof(int) * ns, cudaMemcpyHostToDevice, s));
+    MGR_TRY_CUDA(cudaMemcpyAsync(L->jcur, hj, sizeof(int) * ns, cudaMemcpyHostToDevice, s));
+    if (++slot >= LS_SLOTS) return MGR_ERR_INVALID_ARG;   // more uploads than slots between syncs
+    int* nf = L->ipin + (size_t)slot * 2 * ns;
+    std::copy(hflag, hflag + ns, nf);
+    std::copy(hj, hj + ns, nf + ns);
+    hflag = nf;
+    hj = nf + ns;
+    return MGR_SUCCESS;
+  };
+  // after a host synchronisation every slot is free again
+  auto synced = [&]() {
+    if (slot == 0) return;
+    int* f0 = L->ipin;
+    std::copy(hflag, hflag + ns, f0);
+    std::copy(hj, hj + ns, f0 + ns);
+    hflag = f0;
+    hj = f0 + ns;
+    slot = 0;
+  };
+  auto spmv_all = [&](bool res) {
+    for (size_t gi = 0; gi < L->gl.size(); gi++) {
+      const int G = L->gl[gi];
+      const unsigned grid = (unsigned)std::min<int64_t>((L->grows[gi] * G + 255) / 256, 152LL * 64);
+#define MGR_LS_CASE(gg)                                                                             \
+  case gg:                                                                                          \
+    if (res)                                                                                        \
+      MGR_LAUNCH k_ls_spmv<gg, true><<<grid, 256, 0, s>>>(L->dsys, L->flag, L->jcur, L->gsys[gi],  \
+                                                          L->groff[gi], L->gcnt[gi], L->grows[gi], \
+                                                          mixed);                                   \
+    else                                                                                            \
+      MGR_LAUNCH k_ls_spmv<gg, false><<<grid, 256, 0, s>>>(L->dsys, L->flag, L->jcur, L->gsys[gi], \
+                                                           L->groff[gi], L->gcnt[gi], L->grows[gi],\
+                                                           mixed);                                  \
+    break;
+      switch (G) {
+        MGR_LS_CASE(1)
+        MGR_LS_CASE(2)
+        MGR_LS_CASE(4)
+        MGR_LS_CASE(8)
+        MGR_LS_CASE(16)
+        default: MGR_LS_CASE(32)
+      }
+#undef MGR_LS_CASE
+    }
+  };
+  const dim3 fin1(1, ns), finv(8, ns);   // one warp / up to 64 warps per system
+
+  // x = 0, ||b||, r = b for every system
+  for (int q = 0; q < ns; q++) {
+    hflag[q] = 1;
+    hj[q] = 0;
+  }
+  MGR_TRY(upload());
+  MGR_LAUNCH k_ls_init<<<vg, KB, 0, s>>>(L->dsys, L->flag, L->roff, ns, L->nrows, 0);
+  MGR_LAUNCH k_ls_mdot<false><<<nbk, KB, 0, s>>>(L->dsys, L->flag, L->jcur, L->blk_sys, L->part,
+                                                  nullptr, LS_BB);
+  MGR_LAUNCH k_ls_final<false><<<fin1, 32, 0, s>>>(L->dsys, L->flag, L->jcur, L->part, 0, L->red, 4,
+                                                   0, 1, 0, L->red);
+  MGR_TRY_CUDA(cudaMemcpyAsync(hred, L->red, sizeof(double) * 4 * ns, cudaMemcpyDeviceToHost, s));
+  MGR_TRY_CUDA(cudaStreamSynchronize(s));
+  synced();
+  bool any_restart = false;
+  for (int q = 0; q < ns; q++) {
+    St& t = st[q];
+    t.bnorm = std::sqrt(hred[(size_t)q * 4]);
+    if (info && info[q].res_hist && info[q].res_hist_cap > 0) info[q].res_hist[0] = 1.0;
+    if (t.bnorm == 0.0) {
+      t.status = MGR_SUCCESS;
+      t.relres = 0.0;
+      t.done = true;
+    } else if (maxit > 0) {
+      t.beta = t.bnorm;
+      t.restart = true;
+      any_restart = true;
+    } else {
+      t.done = true;
+    }
+    hflag[q] = t.restart ? 1 : 0;
+  }
+  if (any_restart) {
+    MGR_TRY(upload());
+    MGR_LAUNCH k_ls_init<<<vg, KB, 0, s>>>(L->dsys, L->flag, L->roff, ns, L->nrows, 1);
+  }
+  std::vector<int> ends;
+  for (;;) {
+    // cycle starts: v_0 = r / ||r||
+    any_restart = false;
+    for (int q = 0; q < ns; q++) {
+      hflag[q] = st[q].restart ? 1 : 0;
+      any_restart |= st[q].restart;
+    }
+    if (any_restart) {
+      MGR_TRY(upload());
+      MGR_LAUNCH k_ls_mdot<false><<<nbk, KB, 0, s>>>(L->dsys, L->flag, L->jcur, L->blk_sys, L->part,
+                                                      nullptr, LS_RR);
+      MGR_LAUNCH k_ls_final<true><<<fin1, 32, 0, s>>>(L->dsys, L->flag, L->jcur, L->part, 0, L->red, 4,
+                                                      0, 1, 0, L->red);
+      MGR_LAUNCH k_ls_scale<<<vg, KB, 0, s>>>(L->dsys, L->flag, L->jcur, L->roff, ns, L->nrows, L->red, 1);
+      for (int q = 0; q < ns; q++)
+        if (st[q].restart) {
+          St& t = st[q];
+          std::fill(t.g.begin(), t.g.end(), 0.0);
+          t.g[0] = t.beta;
+          t.j = 0;
+          t.jend = 0;
+          t.restart = false;
+        }
+    }
+    // one iteration of every system in a cycle
+    int active = 0;
+    long long graph_kernels = 1;
+    for (int q = 0; q < ns; q++) {
+      const bool a = !st[q].done && !st[q].cycle_end;
+      hflag[q] = a ? 1 : 0;
+      hj[q] = st[q].j;
+      if (a) {
+        active++;
+        graph_kernels += L->body_kernels[q];
+      }
+    }
+    if (active > 0) {
+      MGR_TRY(upload());
+      MGR_LAUNCH k_ls_gather<<<vg, KB, 0, s>>>(L->dsys, L->flag, L->jcur, L->roff, ns, L->nrows, mixed);
+      MGR_TRY_CUDA(cudaGraphLaunch(L->exec, s));
+      g_launches += graph_kernels;
+      MGR_LAUNCH k_ls_scatter<<<vg, KB, 0, s>>>(L->dsys, L->flag, L->jcur, L->roff, ns, L->nrows, mixed);
+      spmv_all(false);
+      // classical Gram-Schmidt, twice (the passes of fgmres_run)
+      MGR_LAUNCH k_ls_mdot<false><<<nbk, KB, 0, s>>>(L->dsys, L->flag, L->jcur, L->blk_sys, L->part,
+                                                      nullptr, LS_VW);
+      MGR_LAUNCH k_ls_final<false><<<finv, 256, 0, s>>>(L->dsys, L->flag, L->jcur, L->part, 0, L->Hc,
+                                                        LS_H, 0, 0, 0, L->red);   // h1
+      MGR_LAUNCH k_ls_mdot<true><<<nbk, KB, 0, s>>>(L->dsys, L->flag, L->jcur, L->blk_sys, L->part,
+                                                     L->Hc, LS_VW);
+      MGR_LAUNCH k_ls_final<false><<<finv, 256, 0, s>>>(L->dsys, L->flag, L->jcur, L->part, 0, L->Yv,
+                                                        LS_H, 0, 0, 0, L->red);   // h2
+      MGR_LAUNCH k_ls_mupdate<true><<<nbk, KB, 0, s>>>(L->dsys, L->flag, L->jcur, L->blk_sys, L->part,
+                                                        L->Yv);
+      MGR_LAUNCH k_ls_final<false><<<finv, 256, 0, s>>>(L->dsys, L->flag, L->jcur, L->Yv, 1, L->Hc,
+                                                        LS_H, 0, 0, 1, L->red);   // h += h2
+      MGR_LAUNCH k_ls_final<true><<<fin1, 32, 0, s>>>(L->dsys, L->flag, L->jcur, L->part, 0, L->Hc,
+                                                      LS_H, 1, 1, 0, L->red);   // ||w||
+      MGR_LAUNCH k_ls_scale<<<vg, KB, 0, s>>>(L->dsys, L->flag, L->jcur, L->roff, ns, L->nrows, L->red, 0);
+      MGR_TRY_CUDA(cudaMemcpyAsync(hH, L->Hc, sizeof(double) * LS_H * ns, cudaMemcpyDeviceToHost, s));
+      MGR_TRY_CUDA(cudaStreamSynchronize(s));
+      synced();
+      MGR_TRY_CUDA(cudaGetLastError());
+      for (int q = 0; q < ns; q++) {
+        if (!hflag[q]) continue;
+        St& t = st[q];
+        const int j = t.j;
+        const double* hp = hH + (size_t)q * LS_H;
+        for (int i = 0; i <= j + 1; i++) t.H[(size_t)i * m + j] = hp[i];
+        const double hn = hp[j + 1];
+        if (!std::isfinite(hn)) {
+          t.status = MGR_ERR_BREAKDOWN;
+          t.done = true;
+          continue;
+        }
+        for (int i = 0; i < j; i++) {
+          double a = t.H[(size_t)i * m + j], c = t.H[(size_t)(i + 1) * m + j];
+          t.H[(size_t)i * m + j] = t.cs[i] * a + t.sn[i] * c;
+          t.H[(size_t)(i + 1) * m + j] = -t.sn[i] * a + t.cs[i] * c;
+        }
+        double a = t.H[(size_t)j * m + j], c = t.H[(size_t)(j + 1) * m + j];
+        double den = std::sqrt(a * a + c * c);
+        t.cs[j] = den == 0.0 ? 1.0 : a / den;
+        t.sn[j] = den == 0.0 ? 0.0 : c / den;
+        t.H[(size_t)j * m + j] = t.cs[j] * a + t.sn[j] * c;
+        t.H[(size_t)(j + 1) * m + j] = 0.0;
+        t.g[j + 1] = -t.sn[j] * t.g[j];
+        t.g[j] = t.cs[j] * t.g[j];
+        t.iters++;
+        t.jend = j + 1;
+        if (info && info[q].res_hist && t.iters < info[q].res_hist_cap)
+          info[q].res_hist[t.iters] = std::fabs(t.g[j + 1]) / t.bnorm;
+        if (std::fabs(t.g[j + 1]) <= rtol * t.bnorm || hn == 0.0 || j + 1 >= m || t.iters >= maxit)
+          t.cycle_end = true;
+        else
+          t.j = j + 1;
+      }
+    }
+    // cycle ends: y = H^-1 g, x += Z y, true residual
+    ends.clear();
+    for (int q = 0; q < ns; q++)
+      if (!st[q].done && st[q].cycle_end) ends.push_back(q);
+    if (ends.empty()) {
+      bool running = false;
+      for (int q = 0; q < ns; q++) running |= !st[q].done;
+      if (!running) break;
+      continue;
+    }
+    for (int q = 0; q < ns; q++) {
+      hflag[q] = 0;
+      hj[q] = 0;
+    }
+    for (int q : ends) {
+      St& t = st[q];
+      for (int i = t.jend - 1; i >= 0; i--) {
+        double v = t.g[i];
+        for (int k = i + 1; k < t.jend; k++) v -= t.H[(size_t)i * m + k] * t.y[k];
+        t.y[i] = v / t.H[(size_t)i * m + i];
+      }
+      std::copy(t.y.begin(), t.y.begin() + t.jend, hH + (size_t)q * LS_H);
+      hflag[q] = 1;
+      hj[q] = t.jend - 1;
+    }
+    MGR_TRY_CUDA(cudaMemcpyAsync(L->Yv, hH, sizeof(double) * LS_H * ns, cudaMemcpyHostToDevice, s));
+    MGR_TRY(upload());
+    if (mixed)
+      MGR_LAUNCH k_ls_xupdate<float><<<vg, KB, 0, s>>>(L->dsys, L->flag, L->jcur, L->roff, ns, L->nrows,
+                                                       L->Yv);
+    else
+      MGR_LAUNCH k_ls_xupdate<double><<<vg, KB, 0, s>>>(L->dsys, L->flag, L->jcur, L->roff, ns,
+                                                        L->nrows, L->Yv);
+    spmv_all(true);
+    MGR_LAUNCH k_ls_mdot<false><<<nbk, KB, 0, s>>>(L->dsys, L->flag, L->jcur, L->blk_sys, L->part,
+                                                    nullptr, LS_RR);
+    MGR_LAUNCH k_ls_final<false><<<fin1, 32, 0, s>>>(L->dsys, L->flag, L->jcur, L->part, 0, L->red, 4,
+                                                     0, 1, 0, L->red);
+    MGR_TRY_CUDA(cudaMemcpyAsync(hred, L->red, sizeof(double) * 4 * ns, cudaMemcpyDeviceToHost, s));
+    MGR_TRY_CUDA(cudaStreamSynchronize(s));
+    synced();
+    for (int q : ends) {
+      St& t = st[q];
+      t.cycle_end = false;
+      t.beta = std::sqrt(hred[(size_t)q * 4]);
+      t.relres = t.beta / t.bnorm;
+      if (!std::isfinite(t.beta)) {
+        t.status = MGR_ERR_BREAKDOWN;
+        t.done = true;
+      } else if (t.relres <= rtol || t.beta == 0.0) {
+        t.status = MGR_SUCCESS;
+        t.done = true;
+      } else {
+        t.restarts++;
+        if (t.iters >= maxit) t.done = true;
+        else t.restart = true;
+      }
+    }
+  }
+  MGR_TRY_CUDA(cudaEventRecord(ev.e[1], s));
+  MGR_TRY_CUDA(cudaEventSynchronize(ev.e[1]));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, ev.e[0], ev.e[1]);
+  int first_err = 0, worst = 0;
+  for (int q = 0; q < ns; q++) {
+    const St& t = st[q];
+    if (info) {
+      info[q].iters = t.iters;
+      info[q].restarts = t.restarts;
+      info[q].converged = t.status == MGR_SUCCESS;
+      info[q].rel_res_true = t.relres;
+      info[q].setup_s = hs[q]->setup_s;
+      info[q].solve_s = ms * 1e-3;
+    }
+    if (t.status < 0 && !first_err) first_err = t.status;
+    if (t.status > worst) worst = t.status;
+  }
+  return first_err ? first_err : worst;
 }
 
 }  // namespace mgr

@@ -227,6 +227,8 @@ int apply_mgr(Handle* h, const double* v, double* z, cudaStream_t s);
 int apply_mgr32(Handle* h, const float* v, float* z, cudaStream_t s);
 int apply_mgr_mixed_into(Handle* h, const double* v, float* z, cudaStream_t s);
 int capture_apply_graph(Handle* h);
+int capture_apply_into(Handle* h, cudaGraph_t body, long long* kernels);
+int spmv_lanes(int64_t nnz, int64_t nr);   // lanes per row of the CSR product
 int setup_one(const mgr_matrix_t* A, const mgr_options_t* o, cudaStream_t s, Handle** out);
 int fgmres_run(Handle* h, const mgr_matrix_t* A, const double* b, double* x,
                const fgmres_options_t* o, fgmres_info_t* info, cudaStream_t s);
@@ -241,6 +243,58 @@ void spmv64_x32(const int64_t* rp, const int32_t* ci, const double* v, int64_t n
                 int64_t nnz, const float* x, double* y, cudaStream_t s);
 void residual64(const int64_t* rp, const int32_t* ci, const double* v, int64_t nr,
                 int64_t nnz, const double* b, const double* x, double* r, cudaStream_t s);
+
+// ----------------------------------------------------------------------------
+// Lockstep batch (many systems, one launch per phase; krylov.cu, batched.cu)
+// ----------------------------------------------------------------------------
+static constexpr int LS_H = 64;   // Hessenberg column stride per system (m <= 60)
+
+struct LsSys {                     // device descriptor of one system
+  int64_t n = 0;
+  const int64_t* rp = nullptr;
+  const int32_t* ci = nullptr;
+  const double* val = nullptr;
+  const double* b = nullptr;
+  double *x = nullptr, *V = nullptr, *w = nullptr, *r = nullptr;
+  void* Z = nullptr;
+  float *vin32 = nullptr, *zout32 = nullptr;
+  double *gin = nullptr, *gout = nullptr;
+  int64_t blk0 = 0;                // first chunk block of this system
+  int32_t nb = 0;                  // its chunk blocks
+  int32_t pad = 0;
+};
+
+struct Lockstep {
+  int nsys = 0;
+  bool mixed = false;
+  cudaGraphExec_t exec = nullptr;   // one conditional branch per system
+  long long graph_nodes = 0;
+  std::vector<long long> body_kernels;
+  int* flag = nullptr;              // device [nsys]: branch / phase participation
+  unsigned long long* cond = nullptr;
+  Pool pool;                        // the plan's own device memory
+  // per-solve plan (sized at the first solve)
+  int m = 0;
+  LsSys* dsys = nullptr;            // device [nsys]
+  int* jcur = nullptr;              // device [nsys]
+  int32_t* blk_sys = nullptr;       // device [total chunk blocks]
+  int64_t nblk = 0;
+  int64_t* roff = nullptr;          // device [nsys + 1] row offsets of all systems
+  int64_t nrows = 0;
+  std::vector<int> gl;              // lanes per row of each SpMV group
+  std::vector<int*> gsys;           // device: the systems of each group
+  std::vector<int64_t*> groff;      // device: row offsets within each group
+  std::vector<int64_t> grows;
+  std::vector<int> gcnt;
+  double *Hc = nullptr, *Yv = nullptr, *red = nullptr, *part = nullptr;
+  double* hpin = nullptr;           // pinned host: Hc, red mirrors
+  int* ipin = nullptr;              // pinned host: flag, jcur
+  ~Lockstep();
+};
+int fgmres_lockstep(Lockstep* L, Handle** hs, const mgr_matrix_t* A, const double* const* b,
+                    double* const* x, const fgmres_options_t* o, fgmres_info_t* info,
+                    cudaStream_t s);
+int ensure_krylov_ws(Handle* h, int m);
 
 // ----------------------------------------------------------------------------
 // Small device helpers

@@ -312,11 +312,11 @@ def fgmres_solve_batched(bh, As, bs, xs, opts: FgmresOptions | None = None, stre
 def mgr_batch_info(bh):
     w = C.c_int(0)
     s = C.c_double(0.0)
-    tw = (C.c_int * 5)()
-    t = (C.c_double * 5)()
+    tw = (C.c_int * 6)()
+    t = (C.c_double * 6)()
     _check(lib().mgr_batch_info(bh, C.byref(w), C.byref(s), tw, t), "mgr_batch_info")
     return dict(workers=w.value, setup_s=s.value,
-                tune_ms={k: v for k, v in zip(list(tw), list(t)) if k > 0})
+                tune_ms={k: v for k, v in zip(list(tw), list(t)) if k != 0})
 
 
 def mgr_batch_handle(bh, i):

@@ -44,17 +44,18 @@ def _solve_single(p, A, precision):
 
 
 @pytest.mark.parametrize("precision", [mgr.MGR_MIXED, mgr.MGR_FP64])
-@pytest.mark.parametrize("workers", [0, 3])
+@pytest.mark.parametrize("workers", [0, 3, -1], ids=["autotuned", "3-workers", "lockstep"])
 def test_batched_equals_single_solves(members, precision, workers):
     As = [mgr.DeviceMatrix(p) for p in members]
     bh = mgr.mgr_setup_batched(As, mgr.mgr_options_default(True, precision=precision),
                                workers=workers)
     info = mgr.mgr_batch_info(bh)
-    assert 1 <= info["workers"] <= min(16, NSYS)
+    assert info["workers"] == -1 or 1 <= info["workers"] <= min(16, NSYS)
     if workers:
         assert info["workers"] == workers and not info["tune_ms"]
     else:
-        assert info["tune_ms"] and info["workers"] in info["tune_ms"]
+        # every worker count and the lockstep graph were timed
+        assert info["tune_ms"] and info["workers"] in info["tune_ms"] and -1 in info["tune_ms"]
     bs = [torch.from_numpy(p.rhs).cuda() for p in members]
     xs = [torch.full_like(b, float("nan")) for b in bs]
     st, infos = mgr.fgmres_solve_batched(bh, As, bs, xs)
@@ -71,6 +72,38 @@ def test_batched_equals_single_solves(members, precision, workers):
     for i in range(NSYS):
         assert torch.equal(xs2[i], xs[i])
     mgr.mgr_destroy_batched(bh)
+
+
+def test_lockstep_launches_per_round(members):
+    """Lockstep: each FGMRES round is one launch per phase for all systems
+    (plus the kernels inside the one preconditioner graph), so the library's
+    launches per round stay far below what the systems would launch one by
+    one."""
+    As = [mgr.DeviceMatrix(p) for p in members]
+    opts = mgr.mgr_options_default(True, precision=mgr.MGR_MIXED)
+    bs = [torch.from_numpy(p.rhs).cuda() for p in members]
+    xs = [torch.zeros_like(b) for b in bs]
+    bh = mgr.mgr_setup_batched(As, opts, workers=-1)
+    l0 = mgr.mgr_launch_count()
+    st, infos = mgr.fgmres_solve_batched(bh, As, bs, xs)
+    lock_launches = mgr.mgr_launch_count() - l0
+    mgr.mgr_destroy_batched(bh)
+    assert st == mgr.MGR_SUCCESS
+    rounds = max(i["iters"] for i in infos)
+    total = sum(i["iters"] for i in infos)
+    # the same systems one after another (their setups launch the same
+    # kernels in both cases, so compare the solves only)
+    hs = [mgr.mgr_setup(A, opts) for A in As]
+    l0 = mgr.mgr_launch_count()
+    for h, A, b in zip(hs, As, bs):
+        mgr.fgmres_solve(h, A, b, torch.zeros_like(b))
+    single_launches = mgr.mgr_launch_count() - l0
+    for h in hs:
+        mgr.mgr_destroy(h)
+    # both count every kernel of every preconditioner graph; outside the graph
+    # a single solve launches a dozen Krylov kernels per iteration, the
+    # lockstep solve a dozen per round for all systems together
+    assert lock_launches <= single_launches - 10 * (total - rounds), (lock_launches, single_launches)
 
 
 def test_batched_member_matches_oracle(members):
@@ -112,9 +145,10 @@ def test_batched_argument_errors(members):
     with pytest.raises(mgr.MgrError) as e:
         mgr.mgr_setup_batched([], mgr.mgr_options_default(True))
     assert e.value.code == -1
-    with pytest.raises(mgr.MgrError) as e:
-        mgr.mgr_setup_batched(As, mgr.mgr_options_default(True), workers=17)
-    assert e.value.code == -1
+    for bad in (17, -2):
+        with pytest.raises(mgr.MgrError) as e:
+            mgr.mgr_setup_batched(As, mgr.mgr_options_default(True), workers=bad)
+        assert e.value.code == -1
     bh = mgr.mgr_setup_batched(As, mgr.mgr_options_default(True), workers=1)
     bs = [torch.from_numpy(p.rhs).cuda() for p in members[:2]]
     xs = [torch.zeros_like(b) for b in bs]
