@@ -222,7 +222,152 @@ static int copy_csr(Pool& P, const Csr& a, Csr& b, cudaStream_t s) {
 static constexpr int SPG_WARPS = 8;
 static constexpr int SPG_WORDS = 1024;                 // 32768 columns per window
 static constexpr int64_t SPG_WBITS = 32LL * SPG_WORDS;
+static constexpr int SPG_HASH = 2048;                  // hash slots per warp (8 KB)
+static constexpr int SPG_HASH_UB = SPG_HASH / 2;       // rows with at most this many products
 
+// Row i of the pattern by bitmap windows: the candidate columns are marked in
+// a shared-memory bitmap window of SPG_WBITS columns and extracted in
+// ascending order, window by window over the row's column span.
+template <bool FILL>
+__device__ __forceinline__ int64_t sym_row_bitmap(uint32_t* bm, const int32_t* __restrict__ aci,
+                                                  int64_t a0, int64_t a1,
+                                                  const int64_t* __restrict__ brp,
+                                                  const int32_t* __restrict__ bci,
+                                                  int32_t* __restrict__ cci, int64_t out0) {
+  const int lane = threadIdx.x & 31;
+  int32_t lo = INT32_MAX, hi = -1;
+  for (int64_t t = a0 + lane; t < a1; t += 32) {
+    int32_t k = (int32_t)aci[t];
+    int64_t b0 = brp[k], b1 = brp[k + 1];
+    if (b1 > b0) {
+      lo = min(lo, bci[b0]);
+      hi = max(hi, bci[b1 - 1]);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    lo = min(lo, __shfl_xor_sync(FULL, lo, o));
+    hi = max(hi, __shfl_xor_sync(FULL, hi, o));
+  }
+  int64_t running = 0;
+  for (int64_t w0 = lo; hi >= 0 && w0 <= hi; w0 += SPG_WBITS) {
+    int64_t wend = (hi - w0) / 32 + 1;           // words that can hold bits
+    if (wend > SPG_WORDS) wend = SPG_WORDS;
+    for (int q = lane; q < wend; q += 32) bm[q] = 0u;
+    __syncwarp();
+    const int64_t w1 = w0 + SPG_WBITS;
+    for (int64_t t = a0 + lane; t < a1; t += 32) {
+      int32_t k = (int32_t)aci[t];
+      for (int64_t e = brp[k]; e < brp[k + 1]; e++) {
+        int64_t j = bci[e];
+        if (j >= w0 && j < w1) {
+          int64_t off = j - w0;
+          atomicOr(&bm[off >> 5], 1u << (off & 31));
+        }
+      }
+    }
+    __syncwarp();
+    for (int64_t q0 = 0; q0 < wend; q0 += 32) {
+      int64_t q = q0 + lane;
+      uint32_t word = (q < wend) ? bm[q] : 0u;
+      int c = __popc(word);
+      int x = c;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(FULL, x, o);
+        if (lane >= o) x += y;
+      }
+      int tot = __shfl_sync(FULL, x, 31);
+      if (FILL) {
+        int64_t pos = out0 + running + (x - c);
+        while (word) {
+          int b = __ffs(word) - 1;
+          word &= word - 1;
+          cci[pos++] = (int32_t)(w0 + 32 * q + b);
+        }
+      }
+      running += tot;
+    }
+    __syncwarp();
+  }
+  return running;
+}
+
+// Row i of the pattern by a shared-memory hash set (rows with at most
+// SPG_HASH_UB products, whose columns may span the whole matrix): insert
+// every product's column into an open-addressing table of 2^lg >= 2 ub
+// slots, compact the distinct columns to the front and sort them ascending
+// (bitonic, in the warp).  The set of columns, hence the pattern, is the one
+// the bitmap path finds.
+template <bool FILL>
+__device__ __forceinline__ int64_t sym_row_hash(int32_t* ht, int lg, const int32_t* __restrict__ aci,
+                                                int64_t a0, int64_t a1,
+                                                const int64_t* __restrict__ brp,
+                                                const int32_t* __restrict__ bci,
+                                                int32_t* __restrict__ cci, int64_t out0) {
+  const int lane = threadIdx.x & 31;
+  const int size = 1 << lg;
+  const uint32_t mask = (uint32_t)size - 1u;
+  for (int q = lane; q < size; q += 32) ht[q] = -1;
+  __syncwarp();
+  for (int64_t t = a0 + lane; t < a1; t += 32) {
+    const int32_t k = (int32_t)aci[t];
+    for (int64_t e = brp[k]; e < brp[k + 1]; e++) {
+      const int32_t j = bci[e];
+      uint32_t h = ((uint32_t)j * 0x9E3779B1u) >> (32 - lg);
+      for (;;) {
+        const int32_t old = atomicCAS(&ht[h], -1, j);
+        if (old == -1 || old == j) break;
+        h = (h + 1u) & mask;
+      }
+    }
+  }
+  __syncwarp();
+  // compact the occupied slots to the front (in place: every lane reads its
+  // slot of a 32-slot chunk before any lane writes, and writes land below)
+  int d = 0;
+  for (int q0 = 0; q0 < size; q0 += 32) {
+    const int32_t v = ht[q0 + lane];
+    const unsigned bal = __ballot_sync(FULL, v != -1);
+    __syncwarp();
+    if (v != -1) ht[d + __popc(bal & ((1u << lane) - 1u))] = v;
+    d += __popc(bal);
+    __syncwarp();
+  }
+  if (FILL && d > 0) {
+    int P = 1;
+    while (P < d) P <<= 1;
+    for (int q = d + lane; q < P; q += 32) ht[q] = INT32_MAX;
+    __syncwarp();
+    for (int k = 2; k <= P; k <<= 1)
+      for (int jj = k >> 1; jj > 0; jj >>= 1) {
+        for (int i = lane; i < P; i += 32) {
+          const int partner = i ^ jj;
+          if (partner > i) {
+            const int32_t a = ht[i], b = ht[partner];
+            const bool up = (i & k) == 0;
+            if ((a > b) == up) {
+              ht[i] = b;
+              ht[partner] = a;
+            }
+          }
+        }
+        __syncwarp();
+      }
+    for (int q = lane; q < d; q += 32) cci[out0 + q] = ht[q];
+    __syncwarp();
+  }
+  return d;
+}
+
+// Deterministic sparse matrix product C = A * B, symbolic part: one warp per
+// output row, by hash set for rows with few products and by bitmap windows
+// otherwise; FILL writes the row's columns at cnt_or_rp[i] (and its length to
+// cnt_out[i] if given), else cnt_or_rp[i] = the row's length.
+//   numeric : one warp per output row; the A entries are taken one at a time in
+//   ascending order and the lanes add a_ik * b_kj into distinct output slots,
+//   so every entry is summed over ascending k from 0.0 exactly as a sequential
+//   Gustavson product would.
 template <bool FILL>
 __global__ void __launch_bounds__(SPG_WARPS * 32)
 k_spgemm_symbolic(const int64_t* __restrict__ arp, const int32_t* __restrict__ aci, int64_t nr,
@@ -231,67 +376,27 @@ k_spgemm_symbolic(const int64_t* __restrict__ arp, const int32_t* __restrict__ a
                   int64_t* __restrict__ cnt_out) {
   extern __shared__ uint32_t smem[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  uint32_t* bm = smem + wid * SPG_WORDS;
+  uint32_t* bm = smem + wid * SPG_HASH;
   for (int64_t i = (int64_t)blockIdx.x * SPG_WARPS + wid; i < nr; i += (int64_t)gridDim.x * SPG_WARPS) {
     const int64_t a0 = arp[i], a1 = arp[i + 1];
-    int32_t lo = INT32_MAX, hi = -1;
+    int64_t ub = 0;
     for (int64_t t = a0 + lane; t < a1; t += 32) {
-      int32_t k = aci[t];
-      int64_t b0 = brp[k], b1 = brp[k + 1];
-      if (b1 > b0) {
-        lo = min(lo, bci[b0]);
-        hi = max(hi, bci[b1 - 1]);
-      }
+      const int32_t k = aci[t];
+      ub += brp[k + 1] - brp[k];
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      lo = min(lo, __shfl_xor_sync(FULL, lo, o));
-      hi = max(hi, __shfl_xor_sync(FULL, hi, o));
-    }
-    int64_t running = 0;
+    for (int o = 16; o > 0; o >>= 1) ub += __shfl_xor_sync(FULL, ub, o);
     const int64_t out0 = FILL ? cnt_or_rp[i] : 0;
-    for (int64_t w0 = lo; hi >= 0 && w0 <= hi; w0 += SPG_WBITS) {
-      int64_t wend = (hi - w0) / 32 + 1;           // words that can hold bits
-      if (wend > SPG_WORDS) wend = SPG_WORDS;
-      for (int q = lane; q < wend; q += 32) bm[q] = 0u;
-      __syncwarp();
-      const int64_t w1 = w0 + SPG_WBITS;
-      for (int64_t t = a0 + lane; t < a1; t += 32) {
-        int32_t k = aci[t];
-        for (int64_t e = brp[k]; e < brp[k + 1]; e++) {
-          int64_t j = bci[e];
-          if (j >= w0 && j < w1) {
-            int64_t off = j - w0;
-            atomicOr(&bm[off >> 5], 1u << (off & 31));
-          }
-        }
-      }
-      __syncwarp();
-      for (int64_t q0 = 0; q0 < wend; q0 += 32) {
-        int64_t q = q0 + lane;
-        uint32_t word = (q < wend) ? bm[q] : 0u;
-        int c = __popc(word);
-        int x = c;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          int y = __shfl_up_sync(FULL, x, o);
-          if (lane >= o) x += y;
-        }
-        int tot = __shfl_sync(FULL, x, 31);
-        if (FILL) {
-          int64_t pos = out0 + running + (x - c);
-          while (word) {
-            int b = __ffs(word) - 1;
-            word &= word - 1;
-            cci[pos++] = (int32_t)(w0 + 32 * q + b);
-          }
-        }
-        running += tot;
-      }
-      __syncwarp();
+    int64_t len;
+    if (ub <= SPG_HASH_UB) {
+      int lg = 6;
+      while ((1LL << lg) < 2 * ub) lg++;
+      len = sym_row_hash<FILL>((int32_t*)bm, lg, aci, a0, a1, brp, bci, cci, out0);
+    } else {
+      len = sym_row_bitmap<FILL>(bm, aci, a0, a1, brp, bci, cci, out0);
     }
-    if (!FILL && lane == 0) cnt_or_rp[i] = running;
-    if (FILL && cnt_out && lane == 0) cnt_out[i] = running;
+    if (!FILL && lane == 0) cnt_or_rp[i] = len;
+    if (FILL && cnt_out && lane == 0) cnt_out[i] = len;
   }
 }
 
@@ -485,7 +590,7 @@ static int spgemm_pattern(Pool& P, Pool& tmp, const Csr& A, const Csr& B, Csr& C
   C.rp = P.get<int64_t>(A.nr + 1);
   int64_t* cnt = tmp.get<int64_t>(A.nr + 1);
   if (P.err || tmp.err) return P.err ? P.err : tmp.err;
-  const size_t sm = sizeof(uint32_t) * SPG_WORDS * SPG_WARPS;
+  const size_t sm = sizeof(uint32_t) * SPG_HASH * SPG_WARPS;
   // once per process (setups may run concurrently on several host threads)
   static std::once_flag attr_once;
   static cudaError_t attr_err = cudaSuccess;
