@@ -389,7 +389,7 @@ def run_ours(args):
     As = mgr.DeviceMatrix(ps)
     bs = torch.from_numpy(ps.rhs).cuda()
     xs = torch.zeros_like(bs)
-    if args.profile and args.profile_workload != "headline":
+    if args.profile and args.profile_workload in ("small", "medium"):
         pp = ps if args.profile_workload == "small" else synth.two_phase(**MEDIUM)
         Ap = As if pp is ps else mgr.DeviceMatrix(pp)
         bp = torch.from_numpy(pp.rhs).cuda()

@@ -710,15 +710,15 @@ int capture_apply_graph(Handle* h) {
   }
   cudaStream_t cs;
   MGR_TRY_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-  const long long before = g_launches.load();
   cudaGraph_t graph = nullptr;
   cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
+    t_capturing++;
     if (mixed) mgr_level<float>(h, 0, h->vin32, h->zout32, cs);
     else mgr_level<double>(h, 0, h->gin, h->gout, cs);
+    t_capturing--;
     e = cudaStreamEndCapture(cs, &graph);
   }
-  g_launches.store(before);
   if (e == cudaSuccess && graph) {
     size_t nn = 0;
     cudaGraphGetNodes(graph, nullptr, &nn);
@@ -746,27 +746,14 @@ int capture_apply_graph(Handle* h) {
 // Capture one preconditioner application over the handle's fixed buffers
 // (FP64: gin -> gout; MGR_MIXED: vin32 -> zout32) into an existing graph (the
 // body of a conditional node of the lockstep batch graph).
-int capture_apply_into(Handle* h, cudaGraph_t body, long long* kernels) {
+// One preconditioner application over the handle's fixed buffers (FP64: gin
+// -> gout; MGR_MIXED: vin32 -> zout32) launched on `s` -- used inside a
+// stream capture (the lockstep batch graph's per-system branches).
+int launch_apply_fixed(Handle* h, cudaStream_t s) {
   const bool mixed = h->opt.precision == MGR_MIXED;
   if (!mixed && (!h->gin || !h->gout)) return MGR_ERR_INVALID_ARG;
-  cudaStream_t cs;
-  MGR_TRY_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-  const long long before = g_launches.load();
-  cudaError_t e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0,
-                                                cudaStreamCaptureModeThreadLocal);
-  if (e == cudaSuccess) {
-    if (mixed) mgr_level<float>(h, 0, h->vin32, h->zout32, cs);
-    else mgr_level<double>(h, 0, h->gin, h->gout, cs);
-    cudaGraph_t out = nullptr;
-    e = cudaStreamEndCapture(cs, &out);
-  }
-  if (kernels) *kernels = g_launches.load() - before;
-  g_launches.store(before);
-  cudaStreamDestroy(cs);
-  if (e != cudaSuccess) {
-    (void)cudaGetLastError();
-    return MGR_ERR_CUDA;
-  }
+  if (mixed) mgr_level<float>(h, 0, h->vin32, h->zout32, s);
+  else mgr_level<double>(h, 0, h->gin, h->gout, s);
   return MGR_SUCCESS;
 }
 
@@ -777,7 +764,7 @@ int apply_mgr(Handle* h, const double* v, double* z, cudaStream_t s) {
     MGR_LAUNCH k_cast<double, float><<<vgrid(h->n), 256, 0, s>>>(v, h->vin32, h->n);
     if (h->apply_exec) {
       MGR_TRY_CUDA(cudaGraphLaunch(h->apply_exec, s));
-      g_launches += h->apply_nodes;
+      count_graph_launch(h->apply_nodes);
     } else {
       mgr_level<float>(h, 0, h->vin32, h->zout32, s);
     }
@@ -785,7 +772,7 @@ int apply_mgr(Handle* h, const double* v, double* z, cudaStream_t s) {
   } else if (h->apply_exec) {
     MGR_TRY_CUDA(cudaMemcpyAsync(h->gin, v, sizeof(double) * h->n, cudaMemcpyDeviceToDevice, s));
     MGR_TRY_CUDA(cudaGraphLaunch(h->apply_exec, s));
-    g_launches += h->apply_nodes;
+    count_graph_launch(h->apply_nodes);
     MGR_TRY_CUDA(cudaMemcpyAsync(z, h->gout, sizeof(double) * h->n, cudaMemcpyDeviceToDevice, s));
   } else {
     mgr_level<double>(h, 0, v, z, s);
@@ -804,7 +791,7 @@ int apply_mgr_mixed_into(Handle* h, const double* v, float* z, cudaStream_t s) {
   MGR_LAUNCH k_cast<double, float><<<vgrid(h->n), 256, 0, s>>>(v, h->vin32, h->n);
   if (h->apply_exec) {
     MGR_TRY_CUDA(cudaGraphLaunch(h->apply_exec, s));
-    g_launches += h->apply_nodes;
+    count_graph_launch(h->apply_nodes);
     if (z != h->zout32)
       MGR_TRY_CUDA(cudaMemcpyAsync(z, h->zout32, sizeof(float) * h->n, cudaMemcpyDeviceToDevice, s));
   } else {

@@ -117,14 +117,15 @@ static int apply_fixed(Handle* h, cudaStream_t s) {
 }
 
 // The lockstep graph: a head kernel setting each system's branch condition
-// from its flag, then one conditional node per system whose body is that
-// system's captured preconditioner application.
+// from its flag, then one conditional node per system whose body is one whole
+// FGMRES iteration of that system (its captured preconditioner application
+// between the Krylov kernels, with the column j read from the device).
 __global__ void k_set_branches(const unsigned long long* __restrict__ cond,
                                const int* __restrict__ flag, int n) {
   for (int i = threadIdx.x; i < n; i += blockDim.x) cudaGraphSetConditional(cond[i], flag[i] ? 1u : 0u);
 }
 
-static int build_lockstep(Batch* B, cudaStream_t s) {
+static int build_lockstep(Batch* B, const mgr_matrix_t* A, cudaStream_t s) {
   const int ns = B->nsys;
   for (Handle* h : B->sys)
     if (h->opt.precision != B->sys[0]->opt.precision) return MGR_ERR_INVALID_ARG;
@@ -137,6 +138,7 @@ static int build_lockstep(Batch* B, cudaStream_t s) {
   L->flag = L->pool.get<int>(ns);
   L->cond = L->pool.get<unsigned long long>(ns);
   if (L->pool.err) return L->pool.err;
+  MGR_TRY(lockstep_alloc(L, B->sys.data(), A, s));
   cudaGraph_t g = nullptr;
   MGR_TRY_CUDA(cudaGraphCreate(&g, 0));
   int rc = MGR_SUCCESS;
@@ -161,6 +163,8 @@ static int build_lockstep(Batch* B, cudaStream_t s) {
     if (cudaGraphAddKernelNode(&head, g, nullptr, 0, &kp) != cudaSuccess) rc = MGR_ERR_CUDA;
   }
   L->body_kernels.assign(ns, 0);
+  cudaStream_t cs = nullptr;
+  if (!rc && cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) rc = MGR_ERR_CUDA;
   for (int i = 0; i < ns && !rc; i++) {
     cudaGraphNodeParams np = {};
     np.type = cudaGraphNodeTypeConditional;
@@ -172,19 +176,29 @@ static int build_lockstep(Batch* B, cudaStream_t s) {
       rc = MGR_ERR_CUDA;
       break;
     }
-    long long k = 0;
-    rc = capture_apply_into(B->sys[i], np.conditional.phGraph_out[0], &k);
-    L->body_kernels[i] = k;
-    L->graph_nodes += k;
+    if (cudaStreamBeginCaptureToGraph(cs, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      rc = MGR_ERR_CUDA;
+      break;
+    }
+    const long long before = t_captured;
+    t_capturing++;
+    const int rb = lockstep_iteration(L, B->sys[i], i, cs);
+    t_capturing--;
+    L->body_kernels[i] = t_captured - before;
+    cudaGraph_t out = nullptr;
+    if (cudaStreamEndCapture(cs, &out) != cudaSuccess || rb != MGR_SUCCESS) rc = MGR_ERR_CUDA;
+    L->graph_nodes += L->body_kernels[i];
   }
+  if (cs) cudaStreamDestroy(cs);
   if (!rc && cudaGraphInstantiate(&L->exec, g, 0) != cudaSuccess) rc = MGR_ERR_CUDA;
   cudaGraphDestroy(g);
   (void)cudaGetLastError();
   return rc;
 }
 
-// One lockstep round: every system's preconditioner application through the
-// conditional graph.
+// One lockstep round: one FGMRES iteration of every system through the
+// lockstep graph (on buffers made valid by lockstep_tune_prepare).
 static int lockstep_round(Batch* B, cudaStream_t s) {
   std::vector<int> ones(B->nsys, 1);
   MGR_TRY_CUDA(cudaMemcpyAsync(B->ls->flag, ones.data(), sizeof(int) * B->nsys,
@@ -194,18 +208,11 @@ static int lockstep_round(Batch* B, cudaStream_t s) {
   return MGR_SUCCESS;
 }
 
-// Schedule autotuner: time one round (one application per system) for each
+// Schedule autotuner: time one round -- one FGMRES iteration (preconditioner
+// application, Jacobian product, Gram-Schmidt) of every system -- for each
 // worker count and for the lockstep graph, and keep the fastest.
-static int autotune_workers(Batch* B, cudaStream_t caller) {
-  for (Handle* h : B->sys) {
-    if (h->opt.precision == MGR_MIXED) {
-      MGR_TRY_CUDA(cudaMemsetAsync(h->vin32, 0, sizeof(float) * h->n, caller));
-    } else if (h->gin) {
-      MGR_TRY_CUDA(cudaMemsetAsync(h->gin, 0, sizeof(double) * h->n, caller));
-    } else {
-      return MGR_SUCCESS;   // no fixed buffers: keep the default
-    }
-  }
+static constexpr int TUNE_M = 50;
+static int autotune_workers(Batch* B, const mgr_matrix_t* A, cudaStream_t caller) {
   MGR_TRY_CUDA(cudaStreamSynchronize(caller));
   const int counts[5] = {1, 2, 4, 8, 16};
   double best = 1e300;
@@ -219,7 +226,7 @@ static int autotune_workers(Batch* B, cudaStream_t caller) {
       MGR_TRY_CUDA(cudaDeviceSynchronize());
       const auto t0 = std::chrono::steady_clock::now();
       const int rc = run_workers(B, w, [&](int i, cudaStream_t s) {
-        MGR_TRY(apply_fixed(B->sys[i], s));
+        MGR_TRY(krylov_tune_iteration(B->sys[i], &A[i], TUNE_M, s));
         MGR_TRY_CUDA(cudaStreamSynchronize(s));
         return MGR_SUCCESS;
       });
@@ -234,6 +241,7 @@ static int autotune_workers(Batch* B, cudaStream_t caller) {
     }
   }
   if (B->ls && B->ls->exec) {
+    MGR_TRY(lockstep_tune_prepare(B->ls, B->sys.data(), A, TUNE_M, caller));
     double t = 0.0;
     for (int rep = 0; rep < 2; rep++) {
       MGR_TRY_CUDA(cudaDeviceSynchronize());
@@ -288,7 +296,7 @@ int mgr_setup_batched(int nsys, const mgr_matrix_t* A, const mgr_options_t* o, i
   if (rc >= 0 && cudaStreamSynchronize(caller) != cudaSuccess) rc = MGR_ERR_CUDA;
   B->setup_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   if (rc >= 0 && workers <= 0) {
-    rc = build_lockstep(B, caller);
+    rc = build_lockstep(B, A, caller);
     if (rc < 0 && workers == 0) {   // the worker schedules remain
       delete B->ls;
       B->ls = nullptr;
@@ -298,7 +306,7 @@ int mgr_setup_batched(int nsys, const mgr_matrix_t* A, const mgr_options_t* o, i
   if (rc >= 0) {
     if (workers > 0) B->workers = std::min(workers, nsys);
     else if (workers < 0) B->workers = -1;
-    else rc = autotune_workers(B, caller);
+    else rc = autotune_workers(B, A, caller);
   }
   if (rc < 0) {
     mgr_destroy_batched(reinterpret_cast<mgr_batch_t>(B));

@@ -11,6 +11,9 @@
 
 namespace mgr {
 std::atomic<long long> g_launches{0};
+std::atomic<long long> g_host_launches{0};
+thread_local int t_capturing = 0;
+thread_local long long t_captured = 0;
 thread_local Trace g_trace;
 
 static double now_ms() {
@@ -371,6 +374,8 @@ int mgr_splitmix64_device(const uint64_t* in, uint64_t* out, int64_t n, void* st
 }
 
 int64_t mgr_launch_count(void) { return (int64_t)g_launches.load(); }
+
+int64_t mgr_host_launch_count(void) { return (int64_t)g_host_launches.load(); }
 
 #ifndef MGR_BUILD_ID
 #define MGR_BUILD_ID "unversioned"

@@ -524,6 +524,23 @@ __device__ __forceinline__ int ls_sys_of(const int64_t* __restrict__ off, int cn
   return lo;
 }
 
+// Row g of a launch over every system's rows (single < 0: the systems' rows
+// concatenated, the system found from the row offsets) or over the rows of
+// system `single` alone (a branch of the lockstep graph).
+__device__ __forceinline__ int64_t ls_rows(const LsSys* __restrict__ S, int single, int64_t nrows) {
+  return single >= 0 ? S[single].n : nrows;
+}
+__device__ __forceinline__ int ls_row(const int64_t* __restrict__ roff, int nsys, int single,
+                                      int64_t g, int64_t* i) {
+  if (single >= 0) {
+    *i = g;
+    return single;
+  }
+  const int s = ls_sys_of(roff, nsys, g);
+  *i = g - roff[s];
+  return s;
+}
+
 // per row of every flagged system: x = 0 (what 0) or r = b (what 1)
 __global__ void k_ls_init(const LsSys* __restrict__ S, const int* __restrict__ flag,
                           const int64_t* __restrict__ roff, int nsys, int64_t nrows, int what) {
@@ -540,13 +557,14 @@ __global__ void k_ls_init(const LsSys* __restrict__ S, const int* __restrict__ f
 // v_j into the fixed input of the system's preconditioner graph
 __global__ void k_ls_gather(const LsSys* __restrict__ S, const int* __restrict__ flag,
                             const int* __restrict__ jcur, const int64_t* __restrict__ roff,
-                            int nsys, int64_t nrows, int mixed) {
-  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < nrows;
+                            int nsys, int64_t nrows, int mixed, int single) {
+  const int64_t tot = ls_rows(S, single, nrows);
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < tot;
        g += (int64_t)gridDim.x * blockDim.x) {
-    const int s = ls_sys_of(roff, nsys, g);
+    int64_t i;
+    const int s = ls_row(roff, nsys, single, g, &i);
     if (!flag[s]) continue;
     const LsSys& d = S[s];
-    const int64_t i = g - roff[s];
     const double v = d.V[(int64_t)jcur[s] * d.n + i];
     if (mixed) d.vin32[i] = (float)v;
     else d.gin[i] = v;
@@ -557,13 +575,14 @@ __global__ void k_ls_gather(const LsSys* __restrict__ S, const int* __restrict__
 // widened once into r (the FP64 operand of the Jacobian product)
 __global__ void k_ls_scatter(const LsSys* __restrict__ S, const int* __restrict__ flag,
                              const int* __restrict__ jcur, const int64_t* __restrict__ roff,
-                             int nsys, int64_t nrows, int mixed) {
-  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < nrows;
+                             int nsys, int64_t nrows, int mixed, int single) {
+  const int64_t tot = ls_rows(S, single, nrows);
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < tot;
        g += (int64_t)gridDim.x * blockDim.x) {
-    const int s = ls_sys_of(roff, nsys, g);
+    int64_t i;
+    const int s = ls_row(roff, nsys, single, g, &i);
     if (!flag[s]) continue;
     const LsSys& d = S[s];
-    const int64_t i = g - roff[s];
     const int64_t at = (int64_t)jcur[s] * d.n + i;
     if (mixed) {
       const float v = d.zout32[i];
@@ -582,15 +601,23 @@ template <int G, bool RES>
 __global__ void __launch_bounds__(256)
 k_ls_spmv(const LsSys* __restrict__ S, const int* __restrict__ flag, const int* __restrict__ jcur,
           const int* __restrict__ gsys, const int64_t* __restrict__ goff, int cnt, int64_t nrows,
-          int mixed) {
+          int mixed, int single) {
   const int lane = threadIdx.x & (G - 1);
   const int64_t stride = ((int64_t)gridDim.x * blockDim.x) / G;
-  for (int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G; g < nrows; g += stride) {
-    const int q = ls_sys_of(goff, cnt, g);
-    const int s = gsys[q];
+  const int64_t tot = ls_rows(S, single, nrows);
+  for (int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G; g < tot; g += stride) {
+    int s;
+    int64_t i;
+    if (single >= 0) {
+      s = single;
+      i = g;
+    } else {
+      const int q = ls_sys_of(goff, cnt, g);
+      s = gsys[q];
+      i = g - goff[q];
+    }
     if (!flag[s]) continue;
     const LsSys& d = S[s];
-    const int64_t i = g - goff[q];
     const double* x = RES ? d.x : (mixed ? d.r : (const double*)d.Z + (int64_t)jcur[s] * d.n);
     const int64_t e0 = d.rp[i], e1 = d.rp[i + 1];
     double acc = 0.0;
@@ -607,14 +634,15 @@ k_ls_spmv(const LsSys* __restrict__ S, const int* __restrict__ flag, const int* 
   }
 }
 
-// block -> (system, chunk) for the chunk-block passes
+// block -> (system, chunk) for the chunk-block passes (single >= 0: the
+// launch covers that system's chunks alone)
 __device__ __forceinline__ bool ls_block(const LsSys* __restrict__ S, const int* __restrict__ flag,
-                                         const int32_t* __restrict__ blk_sys, int* s_out,
-                                         int64_t* c_out) {
-  const int s = blk_sys[blockIdx.x];
+                                         const int32_t* __restrict__ blk_sys, int single,
+                                         int* s_out, int64_t* c_out) {
+  const int s = single >= 0 ? single : blk_sys[blockIdx.x];
   if (!flag[s]) return false;
   *s_out = s;
-  *c_out = (int64_t)blockIdx.x - S[s].blk0;
+  *c_out = single >= 0 ? (int64_t)blockIdx.x : (int64_t)blockIdx.x - S[s].blk0;
   return true;
 }
 
@@ -622,10 +650,10 @@ template <bool UPDATE>
 __global__ void __launch_bounds__(KB)
 k_ls_mdot(const LsSys* __restrict__ S, const int* __restrict__ flag, const int* __restrict__ jcur,
           const int32_t* __restrict__ blk_sys, double* __restrict__ part,
-          const double* __restrict__ Hc, int which) {
+          const double* __restrict__ Hc, int which, int single) {
   int s;
   int64_t c;
-  if (!ls_block(S, flag, blk_sys, &s, &c)) return;
+  if (!ls_block(S, flag, blk_sys, single, &s, &c)) return;
   const LsSys& d = S[s];
   double* ps = part + d.blk0 * LS_H;
   if (which == LS_VW)
@@ -640,10 +668,10 @@ template <bool NORM>
 __global__ void __launch_bounds__(KB)
 k_ls_mupdate(const LsSys* __restrict__ S, const int* __restrict__ flag, const int* __restrict__ jcur,
              const int32_t* __restrict__ blk_sys, double* __restrict__ part,
-             const double* __restrict__ Yv) {
+             const double* __restrict__ Yv, int single) {
   int s;
   int64_t c;
-  if (!ls_block(S, flag, blk_sys, &s, &c)) return;
+  if (!ls_block(S, flag, blk_sys, single, &s, &c)) return;
   const LsSys& d = S[s];
   mupdate_body<NORM>(d.V, d.n, jcur[s] + 1, Yv + (int64_t)s * LS_H, d.w, d.n,
                      part + d.blk0 * LS_H, c);
@@ -657,8 +685,8 @@ template <bool SQRT>
 __global__ void k_ls_final(const LsSys* __restrict__ S, const int* __restrict__ flag,
                            const int* __restrict__ jcur, const double* __restrict__ part, int rows,
                            double* __restrict__ dst, int dstride, int off_j, int one,
-                           int accumulate, double* __restrict__ red) {
-  const int s = blockIdx.y;
+                           int accumulate, double* __restrict__ red, int single) {
+  const int s = single >= 0 ? single : blockIdx.y;
   if (!flag[s]) return;
   const int nv = one ? 1 : jcur[s] + 1;
   const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -674,13 +702,15 @@ __global__ void k_ls_final(const LsSys* __restrict__ S, const int* __restrict__ 
 // V_(j+1) = w * rinv (what 0), or V_0 = r * rinv (what 1)
 __global__ void k_ls_scale(const LsSys* __restrict__ S, const int* __restrict__ flag,
                            const int* __restrict__ jcur, const int64_t* __restrict__ roff,
-                           int nsys, int64_t nrows, const double* __restrict__ red, int what) {
-  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < nrows;
+                           int nsys, int64_t nrows, const double* __restrict__ red, int what,
+                           int single) {
+  const int64_t tot = ls_rows(S, single, nrows);
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < tot;
        g += (int64_t)gridDim.x * blockDim.x) {
-    const int s = ls_sys_of(roff, nsys, g);
+    int64_t i;
+    const int s = ls_row(roff, nsys, single, g, &i);
     if (!flag[s]) continue;
     const LsSys& d = S[s];
-    const int64_t i = g - roff[s];
     const double f = red[(int64_t)s * 4 + 1];
     if (what == 0) d.V[(int64_t)(jcur[s] + 1) * d.n + i] = d.w[i] * f;
     else d.V[i] = d.r[i] * f;
@@ -733,67 +763,172 @@ Lockstep::~Lockstep() {
 
 // Sizes the per-solve plan (descriptors, block map, SpMV groups, reduction
 // buffers) for restart m; built once and kept for later solves.
+// The plan's device buffers (descriptors, row offsets, chunk-block map, SpMV
+// groups, Hessenberg / reduction buffers), sized from the systems alone so
+// that the lockstep graph, built at setup, can name them.
+int lockstep_alloc(Lockstep* L, Handle** hs, const mgr_matrix_t* A, cudaStream_t s) {
+  const int ns = L->nsys;
+  Pool& P = L->pool;
+  P.s = s;
+  L->dsys = P.get<LsSys>(ns);
+  L->jcur = P.get<int>(ns);
+  L->roff = P.get<int64_t>(ns + 1);
+  L->Hc = P.get<double>((int64_t)ns * LS_H);
+  L->Yv = P.get<double>((int64_t)ns * LS_H);
+  L->red = P.get<double>((int64_t)ns * 4);
+  if (P.err) return P.err;
+  MGR_TRY_CUDA(cudaMallocHost(&L->hpin, sizeof(double) * ((size_t)ns * LS_H + (size_t)ns * 4)));
+  MGR_TRY_CUDA(cudaMallocHost(&L->ipin, sizeof(int) * 2 * (size_t)ns * LS_SLOTS));
+  std::vector<int64_t> roff(ns + 1, 0);
+  std::vector<int32_t> bsys;
+  L->lanes.assign(ns, 1);
+  L->nb.assign(ns, 0);
+  for (int q = 0; q < ns; q++) {
+    roff[q + 1] = roff[q] + hs[q]->n;
+    L->nb[q] = mdot_blocks(hs[q]->n);
+    for (int k = 0; k < L->nb[q]; k++) bsys.push_back(q);
+    L->lanes[q] = spmv_lanes(A[q].nnz, A[q].n);
+  }
+  L->nrows = roff[ns];
+  L->nblk = (int64_t)bsys.size();
+  L->blk_sys = P.get<int32_t>(L->nblk);
+  L->part = P.get<double>(L->nblk * LS_H);
+  if (P.err) return P.err;
+  MGR_TRY_CUDA(cudaMemcpyAsync(L->roff, roff.data(), sizeof(int64_t) * (ns + 1),
+                               cudaMemcpyHostToDevice, s));
+  MGR_TRY_CUDA(cudaMemcpyAsync(L->blk_sys, bsys.data(), sizeof(int32_t) * L->nblk,
+                               cudaMemcpyHostToDevice, s));
+  // row bins: the systems grouped by their lanes per row
+  for (int q = 0; q < ns; q++) {
+    size_t gi = 0;
+    while (gi < L->gl.size() && L->gl[gi] != L->lanes[q]) gi++;
+    if (gi == L->gl.size()) L->gl.push_back(L->lanes[q]);
+  }
+  for (size_t gi = 0; gi < L->gl.size(); gi++) {
+    std::vector<int> sy;
+    std::vector<int64_t> off(1, 0);
+    for (int q = 0; q < ns; q++)
+      if (L->lanes[q] == L->gl[gi]) {
+        sy.push_back(q);
+        off.push_back(off.back() + hs[q]->n);
+      }
+    int* gs = P.get<int>(sy.size());
+    int64_t* go = P.get<int64_t>(off.size());
+    if (P.err) return P.err;
+    MGR_TRY_CUDA(cudaMemcpyAsync(gs, sy.data(), sizeof(int) * sy.size(), cudaMemcpyHostToDevice, s));
+    MGR_TRY_CUDA(cudaMemcpyAsync(go, off.data(), sizeof(int64_t) * off.size(), cudaMemcpyHostToDevice, s));
+    MGR_TRY_CUDA(cudaStreamSynchronize(s));   // the host vectors go out of scope
+    L->gsys.push_back(gs);
+    L->groff.push_back(go);
+    L->grows.push_back(off.back());
+    L->gcnt.push_back((int)sy.size());
+  }
+  MGR_TRY_CUDA(cudaStreamSynchronize(s));
+  return MGR_SUCCESS;
+}
+
+// One FGMRES iteration of system q, launched on `s` (recorded by stream
+// capture as the body of the system's branch in the lockstep graph): z_j =
+// M^-1 v_j, w = A z_j, classical Gram-Schmidt twice, v_(j+1) = w / ||w||,
+// with j read from the device (jcur[q]) when the graph runs.  The same
+// per-row, per-chunk and per-element bodies as fgmres_run's kernels, so the
+// same bits.
+int lockstep_iteration(Lockstep* L, Handle* h, int q, cudaStream_t s) {
+  const int ns = L->nsys;
+  const int mixed = L->mixed;
+  const int64_t n = h->n;
+  const unsigned vg = grid_for(n, KB, 152 * 16);
+  const int nb = L->nb[q];
+  MGR_LAUNCH k_ls_gather<<<vg, KB, 0, s>>>(L->dsys, L->flag, L->jcur, L->roff, ns, L->nrows, mixed, q);
+  MGR_TRY(launch_apply_fixed(h, s));
+  MGR_LAUNCH k_ls_scatter<<<vg, KB, 0, s>>>(L->dsys, L->flag, L->jcur, L->roff, ns, L->nrows, mixed, q);
+  const int G = L->lanes[q];
+  const unsigned sg = (unsigned)std::min<int64_t>((n * G + 255) / 256, 152LL * 64);
+#define MGR_LSQ_CASE(gg)                                                                          \
+  case gg:                                                                                        \
+    MGR_LAUNCH k_ls_spmv<gg, false><<<sg, 256, 0, s>>>(L->dsys, L->flag, L->jcur, nullptr,       \
+                                                       nullptr, 0, 0, mixed, q);                  \
+    break;
+  switch (G) {
+    MGR_LSQ_CASE(1)
+    MGR_LSQ_CASE(2)
+    MGR_LSQ_CASE(4)
+    MGR_LSQ_CASE(8)
+    MGR_LSQ_CASE(16)
+    default: MGR_LSQ_CASE(32)
+  }
+#undef MGR_LSQ_CASE
+  const dim3 f1(1, 1), fv(8, 1);
+  MGR_LAUNCH k_ls_mdot<false><<<nb, KB, 0, s>>>(L->dsys, L->flag, L->jcur, L->blk_sys, L->part,
+                                                 nullptr, LS_VW, q);
+  MGR_LAUNCH k_ls_final<false><<<fv, 256, 0, s>>>(L->dsys, L->flag, L->jcur, L->part, 0, L->Hc, LS_H,
+                                                  0, 0, 0, L->red, q);   // h1
+  MGR_LAUNCH k_ls_mdot<true><<<nb, KB, 0, s>>>(L->dsys, L->flag, L->jcur, L->blk_sys, L->part, L->Hc,
+                                                LS_VW, q);
+  MGR_LAUNCH k_ls_final<false><<<fv, 256, 0, s>>>(L->dsys, L->flag, L->jcur, L->part, 0, L->Yv, LS_H,
+                                                  0, 0, 0, L->red, q);   // h2
+  MGR_LAUNCH k_ls_mupdate<true><<<nb, KB, 0, s>>>(L->dsys, L->flag, L->jcur, L->blk_sys, L->part,
+                                                   L->Yv, q);
+  MGR_LAUNCH k_ls_final<false><<<fv, 256, 0, s>>>(L->dsys, L->flag, L->jcur, L->Yv, 1, L->Hc, LS_H,
+                                                  0, 0, 1, L->red, q);   // h += h2
+  MGR_LAUNCH k_ls_final<true><<<f1, 32, 0, s>>>(L->dsys, L->flag, L->jcur, L->part, 0, L->Hc, LS_H,
+                                                1, 1, 0, L->red, q);     // ||w||
+  MGR_LAUNCH k_ls_scale<<<vg, KB, 0, s>>>(L->dsys, L->flag, L->jcur, L->roff, ns, L->nrows, L->red, 0, q);
+  return MGR_SUCCESS;
+}
+
+// One FGMRES iteration (j = 0, from a zero v_0) of a single system with
+// fgmres_run's kernels and no readback: the unit the batch schedule
+// autotuner times for the worker schedules.  Allocates the Krylov workspace
+// for restart m on `s` if it is not there yet.
+int krylov_tune_iteration(Handle* h, const mgr_matrix_t* A, int m, cudaStream_t s) {
+  h->pool.s = s;
+  MGR_TRY(ensure_krylov(h, m, s));
+  const int64_t n = h->n;
+  MGR_TRY_CUDA(cudaMemsetAsync(h->V, 0, sizeof(double) * n, s));
+  if (h->opt.precision == MGR_MIXED) {
+    MGR_TRY(apply_mgr_mixed_into(h, h->V, h->zout32, s));
+    MGR_LAUNCH k_widen<<<grid_for(n, KB), KB, 0, s>>>(h->zout32, (float*)h->Z, h->r, n);
+    spmv64(A->row_ptr, A->col_idx, A->val, n, A->nnz, h->r, h->w, s);
+  } else {
+    MGR_TRY(apply_mgr(h, h->V, (double*)h->Z, s));
+    spmv64(A->row_ptr, A->col_idx, A->val, n, A->nnz, (double*)h->Z, h->w, s);
+  }
+  const int nb = mdot_blocks(n);
+  mdot(h, h->V, n, 1, h->w, n, h->hcol, 0, s);
+  MGR_LAUNCH k_mdot<true><<<nb, KB, 0, s>>>(h->V, n, 1, h->w, n, h->part, h->hcol);
+  MGR_LAUNCH k_mdot_final<false><<<1, 256, 0, s>>>(h->part, nb, 1, h->yv, 0, nullptr);
+  MGR_LAUNCH k_mupdate<true><<<nb, KB, 0, s>>>(h->V, n, 1, h->yv, h->w, n, h->part);
+  MGR_LAUNCH k_mdot_final<false><<<1, 256, 0, s>>>(h->yv, 1, 1, h->hcol, 1, nullptr);
+  MGR_LAUNCH k_mdot_final<true><<<1, 32, 0, s>>>(h->part, nb, 1, h->hcol + 1, 0, h->hred + 1);
+  MGR_LAUNCH k_scale_by<<<grid_for(n, KB), KB, 0, s>>>(h->w, h->hred + 1, h->V + n, n);
+  MGR_TRY_CUDA(cudaGetLastError());
+  return MGR_SUCCESS;
+}
+
+static int lockstep_plan(Lockstep* L, Handle** hs, const mgr_matrix_t* A, const double* const* b,
+                         double* const* x, int m, cudaStream_t s);
+
+// The lockstep graph's round over valid buffers for the autotuner: every
+// system's Krylov workspace for restart m, descriptors, j = 0 and v_0 = 0.
+int lockstep_tune_prepare(Lockstep* L, Handle** hs, const mgr_matrix_t* A, int m, cudaStream_t s) {
+  std::vector<const double*> nb(L->nsys, nullptr);
+  std::vector<double*> nx(L->nsys, nullptr);
+  for (int q = 0; q < L->nsys; q++) hs[q]->pool.s = s;
+  MGR_TRY(lockstep_plan(L, hs, A, nb.data(), nx.data(), m, s));
+  for (int q = 0; q < L->nsys; q++)
+    MGR_TRY_CUDA(cudaMemsetAsync(hs[q]->V, 0, sizeof(double) * hs[q]->n, s));
+  MGR_TRY_CUDA(cudaMemsetAsync(L->jcur, 0, sizeof(int) * L->nsys, s));
+  MGR_TRY_CUDA(cudaStreamSynchronize(s));
+  return MGR_SUCCESS;
+}
+
+// Per solve: every system's Krylov workspace for restart m and the
+// descriptors that point at it.
 static int lockstep_plan(Lockstep* L, Handle** hs, const mgr_matrix_t* A, const double* const* b,
                          double* const* x, int m, cudaStream_t s) {
   const int ns = L->nsys;
   for (int q = 0; q < ns; q++) MGR_TRY(ensure_krylov_ws(hs[q], m));
-  Pool& P = L->pool;
-  P.s = s;
-  if (!L->dsys) {
-    L->dsys = P.get<LsSys>(ns);
-    L->jcur = P.get<int>(ns);
-    L->roff = P.get<int64_t>(ns + 1);
-    L->Hc = P.get<double>((int64_t)ns * LS_H);
-    L->Yv = P.get<double>((int64_t)ns * LS_H);
-    L->red = P.get<double>((int64_t)ns * 4);
-    if (P.err) return P.err;
-    MGR_TRY_CUDA(cudaMallocHost(&L->hpin, sizeof(double) * ((size_t)ns * LS_H + (size_t)ns * 4)));
-    MGR_TRY_CUDA(cudaMallocHost(&L->ipin, sizeof(int) * 2 * (size_t)ns * LS_SLOTS));
-    std::vector<int64_t> roff(ns + 1, 0);
-    std::vector<int32_t> bsys;
-    std::vector<int> lanes(ns);
-    for (int q = 0; q < ns; q++) {
-      roff[q + 1] = roff[q] + hs[q]->n;
-      const int nb = mdot_blocks(hs[q]->n);
-      for (int k = 0; k < nb; k++) bsys.push_back(q);
-      lanes[q] = spmv_lanes(A[q].nnz, A[q].n);
-    }
-    L->nrows = roff[ns];
-    L->nblk = (int64_t)bsys.size();
-    L->blk_sys = P.get<int32_t>(L->nblk);
-    L->part = P.get<double>(L->nblk * LS_H);
-    if (P.err) return P.err;
-    MGR_TRY_CUDA(cudaMemcpyAsync(L->roff, roff.data(), sizeof(int64_t) * (ns + 1),
-                                 cudaMemcpyHostToDevice, s));
-    MGR_TRY_CUDA(cudaMemcpyAsync(L->blk_sys, bsys.data(), sizeof(int32_t) * L->nblk,
-                                 cudaMemcpyHostToDevice, s));
-    // row bins: the systems grouped by their lanes per row
-    for (int q = 0; q < ns; q++) {
-      size_t gi = 0;
-      while (gi < L->gl.size() && L->gl[gi] != lanes[q]) gi++;
-      if (gi == L->gl.size()) L->gl.push_back(lanes[q]);
-    }
-    for (size_t gi = 0; gi < L->gl.size(); gi++) {
-      std::vector<int> sy;
-      std::vector<int64_t> off(1, 0);
-      for (int q = 0; q < ns; q++)
-        if (lanes[q] == L->gl[gi]) {
-          sy.push_back(q);
-          off.push_back(off.back() + hs[q]->n);
-        }
-      int* gs = P.get<int>(sy.size());
-      int64_t* go = P.get<int64_t>(off.size());
-      if (P.err) return P.err;
-      MGR_TRY_CUDA(cudaMemcpyAsync(gs, sy.data(), sizeof(int) * sy.size(), cudaMemcpyHostToDevice, s));
-      MGR_TRY_CUDA(cudaMemcpyAsync(go, off.data(), sizeof(int64_t) * off.size(),
-                                   cudaMemcpyHostToDevice, s));
-      L->gsys.push_back(gs);
-      L->groff.push_back(go);
-      L->grows.push_back(off.back());
-      L->gcnt.push_back((int)sy.size());
-    }
-    MGR_TRY_CUDA(cudaStreamSynchronize(s));   // host vectors above go out of scope
-  }
   std::vector<LsSys> d(ns);
   int64_t blk0 = 0;
   for (int q = 0; q < ns; q++) {
@@ -813,7 +948,7 @@ static int lockstep_plan(Lockstep* L, Handle** hs, const mgr_matrix_t* A, const 
     d[q].gin = h->gin;
     d[q].gout = h->gout;
     d[q].blk0 = blk0;
-    d[q].nb = mdot_blocks(h->n);
+    d[q].nb = L->nb[q];
     blk0 += d[q].nb;
   }
   MGR_TRY_CUDA(cudaMemcpyAsync(L->dsys, d.data(), sizeof(LsSys) * ns, cudaMemcpyHostToDevice, s));
@@ -897,11 +1032,11 @@ int fgmres_lockstep(Lockstep* L, Handle** hs, const mgr_matrix_t* A, const doubl
     if (res)                                                                                        \
       MGR_LAUNCH k_ls_spmv<gg, true><<<grid, 256, 0, s>>>(L->dsys, L->flag, L->jcur, L->gsys[gi],  \
                                                           L->groff[gi], L->gcnt[gi], L->grows[gi], \
-                                                          mixed);                                   \
+                                                          mixed, -1);                               \
     else                                                                                            \
       MGR_LAUNCH k_ls_spmv<gg, false><<<grid, 256, 0, s>>>(L->dsys, L->flag, L->jcur, L->gsys[gi], \
                                                            L->groff[gi], L->gcnt[gi], L->grows[gi],\
-                                                           mixed);                                  \
+                                                           mixed, -1);                              \
     break;
       switch (G) {
         MGR_LS_CASE(1)
@@ -924,9 +1059,9 @@ int fgmres_lockstep(Lockstep* L, Handle** hs, const mgr_matrix_t* A, const doubl
   MGR_TRY(upload());
   MGR_LAUNCH k_ls_init<<<vg, KB, 0, s>>>(L->dsys, L->flag, L->roff, ns, L->nrows, 0);
   MGR_LAUNCH k_ls_mdot<false><<<nbk, KB, 0, s>>>(L->dsys, L->flag, L->jcur, L->blk_sys, L->part,
-                                                  nullptr, LS_BB);
+                                                  nullptr, LS_BB, -1);
   MGR_LAUNCH k_ls_final<false><<<fin1, 32, 0, s>>>(L->dsys, L->flag, L->jcur, L->part, 0, L->red, 4,
-                                                   0, 1, 0, L->red);
+                                                   0, 1, 0, L->red, -1);
   MGR_TRY_CUDA(cudaMemcpyAsync(hred, L->red, sizeof(double) * 4 * ns, cudaMemcpyDeviceToHost, s));
   MGR_TRY_CUDA(cudaStreamSynchronize(s));
   synced();
@@ -963,10 +1098,11 @@ int fgmres_lockstep(Lockstep* L, Handle** hs, const mgr_matrix_t* A, const doubl
     if (any_restart) {
       MGR_TRY(upload());
       MGR_LAUNCH k_ls_mdot<false><<<nbk, KB, 0, s>>>(L->dsys, L->flag, L->jcur, L->blk_sys, L->part,
-                                                      nullptr, LS_RR);
+                                                      nullptr, LS_RR, -1);
       MGR_LAUNCH k_ls_final<true><<<fin1, 32, 0, s>>>(L->dsys, L->flag, L->jcur, L->part, 0, L->red, 4,
-                                                      0, 1, 0, L->red);
-      MGR_LAUNCH k_ls_scale<<<vg, KB, 0, s>>>(L->dsys, L->flag, L->jcur, L->roff, ns, L->nrows, L->red, 1);
+                                                      0, 1, 0, L->red, -1);
+      MGR_LAUNCH k_ls_scale<<<vg, KB, 0, s>>>(L->dsys, L->flag, L->jcur, L->roff, ns, L->nrows, L->red, 1,
+                                              -1);
       for (int q = 0; q < ns; q++)
         if (st[q].restart) {
           St& t = st[q];
@@ -990,28 +1126,11 @@ int fgmres_lockstep(Lockstep* L, Handle** hs, const mgr_matrix_t* A, const doubl
       }
     }
     if (active > 0) {
+      // one launch: each active system's whole iteration is a branch of the
+      // lockstep graph, the branches of the others are switched off
       MGR_TRY(upload());
-      MGR_LAUNCH k_ls_gather<<<vg, KB, 0, s>>>(L->dsys, L->flag, L->jcur, L->roff, ns, L->nrows, mixed);
       MGR_TRY_CUDA(cudaGraphLaunch(L->exec, s));
-      g_launches += graph_kernels;
-      MGR_LAUNCH k_ls_scatter<<<vg, KB, 0, s>>>(L->dsys, L->flag, L->jcur, L->roff, ns, L->nrows, mixed);
-      spmv_all(false);
-      // classical Gram-Schmidt, twice (the passes of fgmres_run)
-      MGR_LAUNCH k_ls_mdot<false><<<nbk, KB, 0, s>>>(L->dsys, L->flag, L->jcur, L->blk_sys, L->part,
-                                                      nullptr, LS_VW);
-      MGR_LAUNCH k_ls_final<false><<<finv, 256, 0, s>>>(L->dsys, L->flag, L->jcur, L->part, 0, L->Hc,
-                                                        LS_H, 0, 0, 0, L->red);   // h1
-      MGR_LAUNCH k_ls_mdot<true><<<nbk, KB, 0, s>>>(L->dsys, L->flag, L->jcur, L->blk_sys, L->part,
-                                                     L->Hc, LS_VW);
-      MGR_LAUNCH k_ls_final<false><<<finv, 256, 0, s>>>(L->dsys, L->flag, L->jcur, L->part, 0, L->Yv,
-                                                        LS_H, 0, 0, 0, L->red);   // h2
-      MGR_LAUNCH k_ls_mupdate<true><<<nbk, KB, 0, s>>>(L->dsys, L->flag, L->jcur, L->blk_sys, L->part,
-                                                        L->Yv);
-      MGR_LAUNCH k_ls_final<false><<<finv, 256, 0, s>>>(L->dsys, L->flag, L->jcur, L->Yv, 1, L->Hc,
-                                                        LS_H, 0, 0, 1, L->red);   // h += h2
-      MGR_LAUNCH k_ls_final<true><<<fin1, 32, 0, s>>>(L->dsys, L->flag, L->jcur, L->part, 0, L->Hc,
-                                                      LS_H, 1, 1, 0, L->red);   // ||w||
-      MGR_LAUNCH k_ls_scale<<<vg, KB, 0, s>>>(L->dsys, L->flag, L->jcur, L->roff, ns, L->nrows, L->red, 0);
+      count_graph_launch(graph_kernels);
       MGR_TRY_CUDA(cudaMemcpyAsync(hH, L->Hc, sizeof(double) * LS_H * ns, cudaMemcpyDeviceToHost, s));
       MGR_TRY_CUDA(cudaStreamSynchronize(s));
       synced();
@@ -1086,9 +1205,9 @@ int fgmres_lockstep(Lockstep* L, Handle** hs, const mgr_matrix_t* A, const doubl
                                                         L->nrows, L->Yv);
     spmv_all(true);
     MGR_LAUNCH k_ls_mdot<false><<<nbk, KB, 0, s>>>(L->dsys, L->flag, L->jcur, L->blk_sys, L->part,
-                                                    nullptr, LS_RR);
+                                                    nullptr, LS_RR, -1);
     MGR_LAUNCH k_ls_final<false><<<fin1, 32, 0, s>>>(L->dsys, L->flag, L->jcur, L->part, 0, L->red, 4,
-                                                     0, 1, 0, L->red);
+                                                     0, 1, 0, L->red, -1);
     MGR_TRY_CUDA(cudaMemcpyAsync(hred, L->red, sizeof(double) * 4 * ns, cudaMemcpyDeviceToHost, s));
     MGR_TRY_CUDA(cudaStreamSynchronize(s));
     synced();

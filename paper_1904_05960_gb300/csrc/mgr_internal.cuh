@@ -36,10 +36,30 @@ struct Status {
     if (_s != MGR_SUCCESS) return _s; \
   } while (0)
 
-// Host-side count of kernel launches made by this library (every launch site
-// is written `MGR_LAUNCH kernel<<<...>>>(...)`, a comma expression).
+// Host-side counts of this library's work: g_launches = kernels executed
+// (a graph launch adds its kernel nodes), g_host_launches = launch calls the
+// host issued (a graph launch counts once).  Every launch site is written
+// `MGR_LAUNCH kernel<<<...>>>(...)`, a comma expression; launches recorded
+// into a graph by stream capture on this thread are counted in t_captured
+// instead (they run when the graph is launched).
 extern std::atomic<long long> g_launches;
-#define MGR_LAUNCH ++mgr::g_launches,
+extern std::atomic<long long> g_host_launches;
+extern thread_local int t_capturing;
+extern thread_local long long t_captured;
+inline int count_launch() {
+  if (t_capturing) {
+    ++t_captured;
+  } else {
+    ++g_launches;
+    ++g_host_launches;
+  }
+  return 0;
+}
+inline void count_graph_launch(long long kernels) {
+  g_launches += kernels;
+  ++g_host_launches;
+}
+#define MGR_LAUNCH (void)mgr::count_launch(),
 
 // device-side error word values (first error wins)
 enum DevErr : int { DEV_OK = 0, DEV_ZERO_DIAG = 1, DEV_BAD_ARG = 2, DEV_OVERFLOW = 3 };
@@ -227,7 +247,7 @@ int apply_mgr(Handle* h, const double* v, double* z, cudaStream_t s);
 int apply_mgr32(Handle* h, const float* v, float* z, cudaStream_t s);
 int apply_mgr_mixed_into(Handle* h, const double* v, float* z, cudaStream_t s);
 int capture_apply_graph(Handle* h);
-int capture_apply_into(Handle* h, cudaGraph_t body, long long* kernels);
+int launch_apply_fixed(Handle* h, cudaStream_t s);
 int spmv_lanes(int64_t nnz, int64_t nr);   // lanes per row of the CSR product
 int setup_one(const mgr_matrix_t* A, const mgr_options_t* o, cudaStream_t s, Handle** out);
 int fgmres_run(Handle* h, const mgr_matrix_t* A, const double* b, double* x,
@@ -286,11 +306,16 @@ struct Lockstep {
   std::vector<int64_t*> groff;      // device: row offsets within each group
   std::vector<int64_t> grows;
   std::vector<int> gcnt;
+  std::vector<int> lanes, nb;       // per system: lanes per row, chunk blocks
   double *Hc = nullptr, *Yv = nullptr, *red = nullptr, *part = nullptr;
   double* hpin = nullptr;           // pinned host: Hc, red mirrors
   int* ipin = nullptr;              // pinned host: flag, jcur
   ~Lockstep();
 };
+int lockstep_alloc(Lockstep* L, Handle** hs, const mgr_matrix_t* A, cudaStream_t s);
+int lockstep_iteration(Lockstep* L, Handle* h, int q, cudaStream_t s);
+int lockstep_tune_prepare(Lockstep* L, Handle** hs, const mgr_matrix_t* A, int m, cudaStream_t s);
+int krylov_tune_iteration(Handle* h, const mgr_matrix_t* A, int m, cudaStream_t s);
 int fgmres_lockstep(Lockstep* L, Handle** hs, const mgr_matrix_t* A, const double* const* b,
                     double* const* x, const fgmres_options_t* o, fgmres_info_t* info,
                     cudaStream_t s);
