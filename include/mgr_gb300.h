@@ -368,9 +368,16 @@ int mgr_destroy_batched(mgr_batch_t bh);
  * Synchronises the device. */
 int64_t mgr_get_block_colors(mgr_handle_t h, int level, int32_t* out, int32_t* ncolor);
 
-/* Number of CUDA kernel launches this library has issued in this process
- * (all handles, all threads).  Lets a caller count the kernels of a region. */
+/* Number of CUDA kernels this library has run in this process (all handles,
+ * all threads; a graph launch adds the kernels of the graph, those of a
+ * lockstep batch graph's active branches).  Lets a caller count the kernels
+ * of a region. */
 int64_t mgr_launch_count(void);
+
+/* Number of launch calls this library's host code has issued in this process:
+ * one per kernel launched directly and one per CUDA graph launched, however
+ * many kernels the graph holds. */
+int64_t mgr_host_launch_count(void);
 
 /* Identifier of the sources this library was compiled from: the first 16 hex
  * digits of a SHA-256 over the CUDA sources, this header and the compiler

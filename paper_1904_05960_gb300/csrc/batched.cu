@@ -105,21 +105,9 @@ static int end_on(Batch* B, cudaStream_t caller) {
   return MGR_SUCCESS;
 }
 
-// One preconditioner application of system h on stream s, from the handle's
-// fixed buffers (the captured graph, or the same launches if capture failed).
-static int apply_fixed(Handle* h, cudaStream_t s) {
-  if (h->apply_exec) {
-    MGR_TRY_CUDA(cudaGraphLaunch(h->apply_exec, s));
-    return MGR_SUCCESS;
-  }
-  if (h->opt.precision == MGR_MIXED) return apply_mgr32(h, h->vin32, h->zout32, s);
-  return apply_mgr(h, h->gin, h->gout, s);
-}
-
 // The lockstep graph: a head kernel setting each system's branch condition
-// from its flag, then one conditional node per system whose body is one whole
-// FGMRES iteration of that system (its captured preconditioner application
-// between the Krylov kernels, with the column j read from the device).
+// from its flag, then one conditional node per system whose body is that
+// system's captured preconditioner application (over its fixed buffers).
 __global__ void k_set_branches(const unsigned long long* __restrict__ cond,
                                const int* __restrict__ flag, int n) {
   for (int i = threadIdx.x; i < n; i += blockDim.x) cudaGraphSetConditional(cond[i], flag[i] ? 1u : 0u);
@@ -183,7 +171,7 @@ static int build_lockstep(Batch* B, const mgr_matrix_t* A, cudaStream_t s) {
     }
     const long long before = t_captured;
     t_capturing++;
-    const int rb = lockstep_iteration(L, B->sys[i], i, cs);
+    const int rb = launch_apply_fixed(B->sys[i], cs);
     t_capturing--;
     L->body_kernels[i] = t_captured - before;
     cudaGraph_t out = nullptr;
@@ -195,17 +183,6 @@ static int build_lockstep(Batch* B, const mgr_matrix_t* A, cudaStream_t s) {
   cudaGraphDestroy(g);
   (void)cudaGetLastError();
   return rc;
-}
-
-// One lockstep round: one FGMRES iteration of every system through the
-// lockstep graph (on buffers made valid by lockstep_tune_prepare).
-static int lockstep_round(Batch* B, cudaStream_t s) {
-  std::vector<int> ones(B->nsys, 1);
-  MGR_TRY_CUDA(cudaMemcpyAsync(B->ls->flag, ones.data(), sizeof(int) * B->nsys,
-                               cudaMemcpyHostToDevice, s));
-  MGR_TRY_CUDA(cudaGraphLaunch(B->ls->exec, s));
-  MGR_TRY_CUDA(cudaStreamSynchronize(s));
-  return MGR_SUCCESS;
 }
 
 // Schedule autotuner: time one round -- one FGMRES iteration (preconditioner
@@ -246,7 +223,7 @@ static int autotune_workers(Batch* B, const mgr_matrix_t* A, cudaStream_t caller
     for (int rep = 0; rep < 2; rep++) {
       MGR_TRY_CUDA(cudaDeviceSynchronize());
       const auto t0 = std::chrono::steady_clock::now();
-      MGR_TRY(lockstep_round(B, caller));
+      MGR_TRY(lockstep_tune_round(B->ls, caller));
       t = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     }
     B->tune_workers.push_back(-1);

@@ -827,53 +827,81 @@ int lockstep_alloc(Lockstep* L, Handle** hs, const mgr_matrix_t* A, cudaStream_t
   return MGR_SUCCESS;
 }
 
-// One FGMRES iteration of system q, launched on `s` (recorded by stream
-// capture as the body of the system's branch in the lockstep graph): z_j =
-// M^-1 v_j, w = A z_j, classical Gram-Schmidt twice, v_(j+1) = w / ||w||,
-// with j read from the device (jcur[q]) when the graph runs.  The same
-// per-row, per-chunk and per-element bodies as fgmres_run's kernels, so the
-// same bits.
-int lockstep_iteration(Lockstep* L, Handle* h, int q, cudaStream_t s) {
+// The row-binned Jacobian products of every flagged system: one launch per
+// lanes-per-row group.  RES: r = b - A x; else w = A z_j.
+static void ls_spmv_all(Lockstep* L, bool res, cudaStream_t s) {
+  const int mixed = L->mixed;
+  for (size_t gi = 0; gi < L->gl.size(); gi++) {
+    const int G = L->gl[gi];
+    const unsigned grid = (unsigned)std::min<int64_t>((L->grows[gi] * G + 255) / 256, 152LL * 64);
+#define MGR_LS_CASE(gg)                                                                             \
+  case gg:                                                                                          \
+    if (res)                                                                                        \
+      MGR_LAUNCH k_ls_spmv<gg, true><<<grid, 256, 0, s>>>(L->dsys, L->flag, L->jcur, L->gsys[gi],  \
+                                                          L->groff[gi], L->gcnt[gi], L->grows[gi], \
+                                                          mixed, -1);                               \
+    else                                                                                            \
+      MGR_LAUNCH k_ls_spmv<gg, false><<<grid, 256, 0, s>>>(L->dsys, L->flag, L->jcur, L->gsys[gi], \
+                                                           L->groff[gi], L->gcnt[gi], L->grows[gi],\
+                                                           mixed, -1);                              \
+    break;
+    switch (G) {
+      MGR_LS_CASE(1)
+      MGR_LS_CASE(2)
+      MGR_LS_CASE(4)
+      MGR_LS_CASE(8)
+      MGR_LS_CASE(16)
+      default: MGR_LS_CASE(32)
+    }
+#undef MGR_LS_CASE
+  }
+}
+
+// One FGMRES iteration of every flagged system (flag and jcur already on the
+// device), each phase one launch for all of them: v_j into the graph inputs;
+// the lockstep graph (the preconditioner application of every flagged system
+// as a conditional branch); z_j out; w = A z_j; classical Gram-Schmidt twice;
+// v_(j+1) = w / ||w||.  Every per-row, per-chunk and per-element body is the
+// one fgmres_run's kernels use, so each system gets the same bits.
+static int ls_iterate(Lockstep* L, long long graph_kernels, cudaStream_t s) {
   const int ns = L->nsys;
   const int mixed = L->mixed;
-  const int64_t n = h->n;
-  const unsigned vg = grid_for(n, KB, 152 * 16);
-  const int nb = L->nb[q];
-  MGR_LAUNCH k_ls_gather<<<vg, KB, 0, s>>>(L->dsys, L->flag, L->jcur, L->roff, ns, L->nrows, mixed, q);
-  MGR_TRY(launch_apply_fixed(h, s));
-  MGR_LAUNCH k_ls_scatter<<<vg, KB, 0, s>>>(L->dsys, L->flag, L->jcur, L->roff, ns, L->nrows, mixed, q);
-  const int G = L->lanes[q];
-  const unsigned sg = (unsigned)std::min<int64_t>((n * G + 255) / 256, 152LL * 64);
-#define MGR_LSQ_CASE(gg)                                                                          \
-  case gg:                                                                                        \
-    MGR_LAUNCH k_ls_spmv<gg, false><<<sg, 256, 0, s>>>(L->dsys, L->flag, L->jcur, nullptr,       \
-                                                       nullptr, 0, 0, mixed, q);                  \
-    break;
-  switch (G) {
-    MGR_LSQ_CASE(1)
-    MGR_LSQ_CASE(2)
-    MGR_LSQ_CASE(4)
-    MGR_LSQ_CASE(8)
-    MGR_LSQ_CASE(16)
-    default: MGR_LSQ_CASE(32)
-  }
-#undef MGR_LSQ_CASE
-  const dim3 f1(1, 1), fv(8, 1);
-  MGR_LAUNCH k_ls_mdot<false><<<nb, KB, 0, s>>>(L->dsys, L->flag, L->jcur, L->blk_sys, L->part,
-                                                 nullptr, LS_VW, q);
-  MGR_LAUNCH k_ls_final<false><<<fv, 256, 0, s>>>(L->dsys, L->flag, L->jcur, L->part, 0, L->Hc, LS_H,
-                                                  0, 0, 0, L->red, q);   // h1
-  MGR_LAUNCH k_ls_mdot<true><<<nb, KB, 0, s>>>(L->dsys, L->flag, L->jcur, L->blk_sys, L->part, L->Hc,
-                                                LS_VW, q);
-  MGR_LAUNCH k_ls_final<false><<<fv, 256, 0, s>>>(L->dsys, L->flag, L->jcur, L->part, 0, L->Yv, LS_H,
-                                                  0, 0, 0, L->red, q);   // h2
-  MGR_LAUNCH k_ls_mupdate<true><<<nb, KB, 0, s>>>(L->dsys, L->flag, L->jcur, L->blk_sys, L->part,
-                                                   L->Yv, q);
-  MGR_LAUNCH k_ls_final<false><<<fv, 256, 0, s>>>(L->dsys, L->flag, L->jcur, L->Yv, 1, L->Hc, LS_H,
-                                                  0, 0, 1, L->red, q);   // h += h2
-  MGR_LAUNCH k_ls_final<true><<<f1, 32, 0, s>>>(L->dsys, L->flag, L->jcur, L->part, 0, L->Hc, LS_H,
-                                                1, 1, 0, L->red, q);     // ||w||
-  MGR_LAUNCH k_ls_scale<<<vg, KB, 0, s>>>(L->dsys, L->flag, L->jcur, L->roff, ns, L->nrows, L->red, 0, q);
+  const unsigned vg = grid_for(L->nrows, KB, 152 * 16);
+  const int nbk = (int)L->nblk;
+  const dim3 fin1(1, ns), finv(8, ns);   // one warp / up to 64 warps per system
+  MGR_LAUNCH k_ls_gather<<<vg, KB, 0, s>>>(L->dsys, L->flag, L->jcur, L->roff, ns, L->nrows, mixed, -1);
+  MGR_TRY_CUDA(cudaGraphLaunch(L->exec, s));
+  count_graph_launch(graph_kernels);
+  MGR_LAUNCH k_ls_scatter<<<vg, KB, 0, s>>>(L->dsys, L->flag, L->jcur, L->roff, ns, L->nrows, mixed, -1);
+  ls_spmv_all(L, false, s);
+  MGR_LAUNCH k_ls_mdot<false><<<nbk, KB, 0, s>>>(L->dsys, L->flag, L->jcur, L->blk_sys, L->part,
+                                                  nullptr, LS_VW, -1);
+  MGR_LAUNCH k_ls_final<false><<<finv, 256, 0, s>>>(L->dsys, L->flag, L->jcur, L->part, 0, L->Hc, LS_H,
+                                                    0, 0, 0, L->red, -1);   // h1
+  MGR_LAUNCH k_ls_mdot<true><<<nbk, KB, 0, s>>>(L->dsys, L->flag, L->jcur, L->blk_sys, L->part, L->Hc,
+                                                 LS_VW, -1);
+  MGR_LAUNCH k_ls_final<false><<<finv, 256, 0, s>>>(L->dsys, L->flag, L->jcur, L->part, 0, L->Yv, LS_H,
+                                                    0, 0, 0, L->red, -1);   // h2
+  MGR_LAUNCH k_ls_mupdate<true><<<nbk, KB, 0, s>>>(L->dsys, L->flag, L->jcur, L->blk_sys, L->part,
+                                                    L->Yv, -1);
+  MGR_LAUNCH k_ls_final<false><<<finv, 256, 0, s>>>(L->dsys, L->flag, L->jcur, L->Yv, 1, L->Hc, LS_H,
+                                                    0, 0, 1, L->red, -1);   // h += h2
+  MGR_LAUNCH k_ls_final<true><<<fin1, 32, 0, s>>>(L->dsys, L->flag, L->jcur, L->part, 0, L->Hc, LS_H,
+                                                  1, 1, 0, L->red, -1);     // ||w||
+  MGR_LAUNCH k_ls_scale<<<vg, KB, 0, s>>>(L->dsys, L->flag, L->jcur, L->roff, ns, L->nrows, L->red, 0,
+                                          -1);
+  return MGR_SUCCESS;
+}
+
+// One lockstep round for the autotuner: every system at j = 0 (buffers made
+// valid by lockstep_tune_prepare), synchronised.
+int lockstep_tune_round(Lockstep* L, cudaStream_t s) {
+  std::vector<int> ones(L->nsys, 1);
+  MGR_TRY_CUDA(cudaMemcpyAsync(L->flag, ones.data(), sizeof(int) * L->nsys, cudaMemcpyHostToDevice, s));
+  long long k = 1;
+  for (long long q : L->body_kernels) k += q;
+  MGR_TRY(ls_iterate(L, k, s));
+  MGR_TRY_CUDA(cudaStreamSynchronize(s));
   return MGR_SUCCESS;
 }
 
@@ -1023,32 +1051,6 @@ int fgmres_lockstep(Lockstep* L, Handle** hs, const mgr_matrix_t* A, const doubl
     hj = f0 + ns;
     slot = 0;
   };
-  auto spmv_all = [&](bool res) {
-    for (size_t gi = 0; gi < L->gl.size(); gi++) {
-      const int G = L->gl[gi];
-      const unsigned grid = (unsigned)std::min<int64_t>((L->grows[gi] * G + 255) / 256, 152LL * 64);
-#define MGR_LS_CASE(gg)                                                                             \
-  case gg:                                                                                          \
-    if (res)                                                                                        \
-      MGR_LAUNCH k_ls_spmv<gg, true><<<grid, 256, 0, s>>>(L->dsys, L->flag, L->jcur, L->gsys[gi],  \
-                                                          L->groff[gi], L->gcnt[gi], L->grows[gi], \
-                                                          mixed, -1);                               \
-    else                                                                                            \
-      MGR_LAUNCH k_ls_spmv<gg, false><<<grid, 256, 0, s>>>(L->dsys, L->flag, L->jcur, L->gsys[gi], \
-                                                           L->groff[gi], L->gcnt[gi], L->grows[gi],\
-                                                           mixed, -1);                              \
-    break;
-      switch (G) {
-        MGR_LS_CASE(1)
-        MGR_LS_CASE(2)
-        MGR_LS_CASE(4)
-        MGR_LS_CASE(8)
-        MGR_LS_CASE(16)
-        default: MGR_LS_CASE(32)
-      }
-#undef MGR_LS_CASE
-    }
-  };
   const dim3 fin1(1, ns), finv(8, ns);   // one warp / up to 64 warps per system
 
   // x = 0, ||b||, r = b for every system
@@ -1126,11 +1128,8 @@ int fgmres_lockstep(Lockstep* L, Handle** hs, const mgr_matrix_t* A, const doubl
       }
     }
     if (active > 0) {
-      // one launch: each active system's whole iteration is a branch of the
-      // lockstep graph, the branches of the others are switched off
       MGR_TRY(upload());
-      MGR_TRY_CUDA(cudaGraphLaunch(L->exec, s));
-      count_graph_launch(graph_kernels);
+      MGR_TRY(ls_iterate(L, graph_kernels, s));
       MGR_TRY_CUDA(cudaMemcpyAsync(hH, L->Hc, sizeof(double) * LS_H * ns, cudaMemcpyDeviceToHost, s));
       MGR_TRY_CUDA(cudaStreamSynchronize(s));
       synced();
@@ -1203,7 +1202,7 @@ int fgmres_lockstep(Lockstep* L, Handle** hs, const mgr_matrix_t* A, const doubl
     else
       MGR_LAUNCH k_ls_xupdate<double><<<vg, KB, 0, s>>>(L->dsys, L->flag, L->jcur, L->roff, ns,
                                                         L->nrows, L->Yv);
-    spmv_all(true);
+    ls_spmv_all(L, true, s);
     MGR_LAUNCH k_ls_mdot<false><<<nbk, KB, 0, s>>>(L->dsys, L->flag, L->jcur, L->blk_sys, L->part,
                                                     nullptr, LS_RR, -1);
     MGR_LAUNCH k_ls_final<false><<<fin1, 32, 0, s>>>(L->dsys, L->flag, L->jcur, L->part, 0, L->red, 4,

@@ -313,7 +313,7 @@ struct Lockstep {
   ~Lockstep();
 };
 int lockstep_alloc(Lockstep* L, Handle** hs, const mgr_matrix_t* A, cudaStream_t s);
-int lockstep_iteration(Lockstep* L, Handle* h, int q, cudaStream_t s);
+int lockstep_tune_round(Lockstep* L, cudaStream_t s);
 int lockstep_tune_prepare(Lockstep* L, Handle** hs, const mgr_matrix_t* A, int m, cudaStream_t s);
 int krylov_tune_iteration(Handle* h, const mgr_matrix_t* A, int m, cudaStream_t s);
 int fgmres_lockstep(Lockstep* L, Handle** hs, const mgr_matrix_t* A, const double* const* b,

@@ -29,7 +29,7 @@ EXPORTED = ["mgr_options_default", "fgmres_options_default", "mgr_setup", "mgr_a
             "mgr_amg_levels", "mgr_get_cf", "mgr_vcycle", "mgr_splitmix64_device",
             "mgr_launch_count", "mgr_trim_memory", "mgr_solve_host", "mgr_vcycle_noalloc", "mgr_setup_batched",
             "fgmres_solve_batched", "mgr_batch_info", "mgr_batch_handle", "mgr_destroy_batched",
-            "mgr_get_block_colors", "mgr_build_id", "mgr_memory_usage", "mgr_spmv"]
+            "mgr_get_block_colors", "mgr_build_id", "mgr_memory_usage", "mgr_spmv", "mgr_host_launch_count"]
 
 
 class MgrMatrix(C.Structure):
@@ -118,6 +118,8 @@ def lib():
             L.mgr_get_block_colors.restype = I64
             L.mgr_launch_count.argtypes = []
             L.mgr_launch_count.restype = I64
+            L.mgr_host_launch_count.argtypes = []
+            L.mgr_host_launch_count.restype = I64
             L.mgr_trim_memory.argtypes = [C.c_size_t]
             L.mgr_build_id.argtypes = []
             L.mgr_build_id.restype = C.c_char_p
@@ -423,6 +425,11 @@ def mgr_memory_usage():
     u, r = C.c_size_t(0), C.c_size_t(0)
     _check(lib().mgr_memory_usage(C.byref(u), C.byref(r)), "mgr_memory_usage")
     return u.value, r.value
+
+
+def mgr_host_launch_count():
+    """Launch calls issued by the library's host code (a graph launch counts once)."""
+    return int(lib().mgr_host_launch_count())
 
 
 def mgr_trim_memory(keep_bytes=0):
