@@ -189,8 +189,9 @@ class ClockSampler:
 # --------------------------------------------------------------------------- roofline
 def vcycle_bytes(mgr, h, slot, value_bytes):
     """Algorithmic DRAM bytes of one V-cycle of AMG slot `slot`: every matrix
-    read once per use (row pointers 8 B, column index 4 B, value), every
-    vector read or written once per kernel (see the design notes)."""
+    read once per use (row pointers 8 B, column index 4 B -- or a 2-byte
+    pattern id per row where the operator has shared row patterns -- value),
+    every vector read or written once per kernel (see the design notes)."""
     vb = value_bytes
     nlev = mgr.mgr_amg_levels(h, slot)
     total = 0
@@ -203,7 +204,12 @@ def vcycle_bytes(mgr, h, slot, value_bytes):
         nc = dims[k + 1][0]
         _, _, nnzP = mgr.mgr_get_csr_dims(h, mgr.Q_AMG_P, slot, k)
         _, _, nnzR = mgr.mgr_get_csr_dims(h, mgr.Q_AMG_R, slot, k)
-        A = (n + 1) * 8 + nnzA * (4 + vb)
+        if mgr.mgr_row_patterns(h, slot, k) > 0:
+            # shared row patterns: a 2-byte pattern id per row instead of a
+            # column index per non-zero (the pattern table stays in cache)
+            A = (n + 1) * 8 + 2 * n + nnzA * vb
+        else:
+            A = (n + 1) * 8 + nnzA * (4 + vb)
         total += 3 * n * vb                                   # t = dinv .* b
         total += A + 3 * n * vb                               # r = b - A t
         total += (nc + 1) * 8 + nnzR * (4 + vb) + n * vb + nc * vb   # b_c = R r

@@ -247,6 +247,16 @@ int mgr_get_csr(mgr_handle_t h, int kind, int slot, int lvl, int64_t* dims,
 /* Number of AMG levels in slot `slot` (0 if that slot has no AMG). */
 int mgr_amg_levels(mgr_handle_t h, int slot);
 
+/* Number of shared row patterns of the operator of AMG slot `slot`, level
+ * `lvl` (0: the operator is applied as plain CSR).  The finest operator of
+ * each AMG with at least 2^20 non-zeros is checked at setup: when its rows
+ * share at most 4096 patterns of columns relative to the row -- the stencil
+ * rows of a structured mesh -- the application reads a 2-byte pattern id per
+ * row and the values, instead of a 4-byte column index per non-zero; the
+ * products are the same, summed in the same order.  INVALID_ARG for a bad
+ * handle, slot or level.  Host-side query. */
+int mgr_row_patterns(mgr_handle_t h, int slot, int lvl);
+
 /* C/F marks (+1 C, -1 F, int8, HOST buffer of length n or NULL) of AMG slot
  * `slot`, level `lvl`; returns n, or a negative error. */
 int64_t mgr_get_cf(mgr_handle_t h, int slot, int lvl, int8_t* out);

@@ -98,6 +98,48 @@ k_spmv(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci, const T* 
   }
 }
 
+// The same product over an operator with shared row patterns: row i's
+// columns are i + poff[pstart[pid[i]] + k], so per non-zero only the value is
+// streamed (plus a 2-byte pattern id per row); the pattern table is a few KB
+// and stays in cache.  Every row's sum is formed in the order of k_spmv.
+template <class T, class X, class Y, class I, int G, int MODE, class D>
+__global__ void __launch_bounds__(256)
+k_spmv_pat(const int64_t* __restrict__ rp, const uint16_t* __restrict__ pid,
+           const int32_t* __restrict__ pstart, const int32_t* __restrict__ poff,
+           const T* __restrict__ val, I nr, const X* __restrict__ x, Y* __restrict__ y,
+           const Y* __restrict__ b, const D* __restrict__ dinv) {
+  const I gid = (I)blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & (G - 1);
+  const I stride = ((I)gridDim.x * blockDim.x) / G;
+  for (I i = gid / G; i < nr; i += stride) {
+    const I e0 = (I)rp[i], e1 = (I)rp[i + 1];
+    const int32_t* po = poff + pstart[pid[i]];
+    Y acc = 0;
+    I k = e0 + lane;
+    if (MODE == MODE_RES0 || MODE == MODE_DRES0) {
+#pragma unroll 4
+      for (; k < e1; k += G) {
+        const I c0 = i + (I)__ldg(po + (k - e0));
+        acc += (Y)val[k] * ((Y)dval(ldg(dinv + c0)) * (Y)ldg(x + c0));
+      }
+    } else {
+#pragma unroll 4
+      for (; k < e1; k += G) acc += (Y)val[k] * (Y)ldg(x + (i + (I)__ldg(po + (k - e0))));
+    }
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(group_mask<G>(), acc, o, G);
+    if (lane == 0) {
+      if (MODE == MODE_AX) y[i] = acc;
+      else if (MODE == MODE_RES) y[i] = b[i] - acc;
+      else if (MODE == MODE_SMOOTH) y[i] = (Y)x[i] + (Y)dval(dinv[i]) * (b[i] - acc);
+      else if (MODE == MODE_ADD) y[i] += acc;
+      else if (MODE == MODE_RES0) y[i] = b[i] - acc;
+      else if (MODE == MODE_PROL0) y[i] = (Y)dval(dinv[i]) * b[i] + acc;
+      else if (MODE == MODE_DRES || MODE == MODE_DRES0) y[i] = (Y)dval(dinv[i]) * (b[i] - acc);
+    }
+  }
+}
+
 // Lanes per row from the mean row length (measured on GB300 for FP64 CSR:
 // ~19 non-zeros per row run best with 2 lanes, ~34-46 with 4, ~150-210 with
 // 8).
@@ -186,7 +228,28 @@ inline const __nv_bfloat16* pickd<__nv_bfloat16>(const double*, const float*, co
 template <class T, int MODE, class D = T>
 static void spmv(const Csr& A, const T* x, T* y, const T* b, const typename ident<D>::type* dinv,
                  const int64_t* rows, cudaStream_t s) {
-  spmv_launch<T, T, T, MODE, D>(A.rp, A.ci, vals<T>(A), A.nr, A.nnz, x, y, b, dinv, rows, s);
+  const bool pat = A.pid && MODE != MODE_GRES && MODE != MODE_RROWS && A.nr > 0 &&
+                   A.nnz + 64 < INT32_MAX && A.nr * 16 + 152LL * 64 * 256 < INT32_MAX;
+  if (!pat) {
+    spmv_launch<T, T, T, MODE, D>(A.rp, A.ci, vals<T>(A), A.nr, A.nnz, x, y, b, dinv, rows, s);
+    return;
+  }
+  const int G = pick_group(A.nnz, A.nr);
+  const unsigned grid = (unsigned)std::min<int64_t>((A.nr * G + 255) / 256, 152LL * 64);
+#define MGR_SPMV_PAT_CASE(g)                                                                      \
+  case g:                                                                                         \
+    MGR_LAUNCH k_spmv_pat<T, T, T, int, g, MODE, D><<<grid, 256, 0, s>>>(                         \
+        A.rp, A.pid, A.pstart, A.poff, vals<T>(A), (int)A.nr, x, y, b, dinv);                     \
+    break;
+  switch (G) {
+    MGR_SPMV_PAT_CASE(1)
+    MGR_SPMV_PAT_CASE(2)
+    MGR_SPMV_PAT_CASE(4)
+    MGR_SPMV_PAT_CASE(8)
+    MGR_SPMV_PAT_CASE(16)
+    MGR_SPMV_PAT_CASE(32)
+  }
+#undef MGR_SPMV_PAT_CASE
 }
 
 void spmv64(const int64_t* rp, const int32_t* ci, const double* v, int64_t nr, int64_t nnz,

@@ -331,6 +331,14 @@ int mgr_amg_levels(mgr_handle_t hh, int slot) {
   return g ? (int)g->lev.size() : 0;
 }
 
+int mgr_row_patterns(mgr_handle_t hh, int slot, int lvl) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (!h) return MGR_ERR_INVALID_ARG;
+  Amg* g = find_amg(h, slot);
+  if (!g || lvl < 0 || lvl >= (int)g->lev.size()) return MGR_ERR_INVALID_ARG;
+  return g->lev[lvl].A.pid ? g->lev[lvl].A.npat : 0;
+}
+
 int64_t mgr_get_cf(mgr_handle_t hh, int slot, int lvl, int8_t* out) {
   Handle* h = reinterpret_cast<Handle*>(hh);
   if (!h) return MGR_ERR_INVALID_ARG;

@@ -121,6 +121,14 @@ struct Csr {
   int32_t* ci = nullptr;
   double* v = nullptr;   // FP64 values (setup, FP64 apply)
   float* vf = nullptr;   // FP32 copy (mixed-precision apply), may be null
+  // Shared row patterns (square operators of a structured mesh): row i's
+  // columns are i + poff[pstart[pid[i]] + k], k < row length, so the apply
+  // reads a 2-byte pattern id per row instead of a 4-byte column per
+  // non-zero.  Null when the rows do not share few enough patterns.
+  uint16_t* pid = nullptr;
+  int32_t* pstart = nullptr;
+  int32_t* poff = nullptr;
+  int32_t npat = 0;
 };
 
 // ----------------------------------------------------------------------------
@@ -238,6 +246,7 @@ int build_mgr_hierarchy(Handle* h, const mgr_matrix_t* A, cudaStream_t s);
 int build_amg(Handle* h, Pool& P, int* derr, const Csr& A, bool own_input, const int32_t* comp,
               int slot, Amg** out, cudaStream_t s);
 int to_fp32(Handle* h, cudaStream_t s);
+int build_row_patterns(Pool& P, Csr& A, cudaStream_t s);
 
 // ----------------------------------------------------------------------------
 // Apply entry points (apply.cu)

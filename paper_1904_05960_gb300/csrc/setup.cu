@@ -2069,6 +2069,210 @@ static int coarsen_step(const mgr_options_t& o, Pool& Ps, Pool& Pi, Pool& tmp, c
   return MGR_SUCCESS;
 }
 
+// ============================================================================
+// Shared row patterns of a square operator
+// ============================================================================
+// On a structured mesh most rows of an operator such as A_uu have the same
+// columns relative to the row (the interior rows of one displacement
+// component), so the columns can be stored once per distinct pattern:
+//   1. hash each row's (column - row) sequence;
+//   2. insert the hashes into an open-addressing table of PAT_SLOTS slots
+//      (the row that claims a slot represents its pattern);
+//   3. number the occupied slots, copy each representative's offsets;
+//   4. check every row against its pattern (a hash collision or an
+//      overfull table leaves the operator without patterns).
+static constexpr int PAT_SLOTS = 8192;   // power of two
+static constexpr int PAT_MAX = 4096;     // at most this many distinct patterns
+static constexpr int64_t PAT_MIN_NNZ = 1 << 20;   // smaller operators keep plain CSR
+
+__device__ __forceinline__ uint64_t pat_mix(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__global__ void k_pat_hash(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci, int64_t n,
+                           unsigned long long* __restrict__ hash) {
+  const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+  for (int64_t i = (int64_t)blockIdx.x * wpb + (threadIdx.x >> 5); i < n; i += (int64_t)gridDim.x * wpb) {
+    const int64_t e0 = rp[i], e1 = rp[i + 1];
+    uint64_t acc = 0;
+    for (int64_t k = e0 + lane; k < e1; k += 32) {
+      const uint32_t off = (uint32_t)((int64_t)ci[k] - i);
+      acc ^= pat_mix(((uint64_t)off) | ((uint64_t)(k - e0) << 32));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc ^= __shfl_xor_sync(FULL, acc, o);
+    if (lane == 0) {
+      uint64_t h = pat_mix(acc + (uint64_t)(e1 - e0) * 0x9E3779B97F4A7C15ull);
+      hash[i] = h ? h : 1ull;   // 0 marks an empty slot
+    }
+  }
+}
+
+__global__ void k_pat_insert(const unsigned long long* __restrict__ hash, int64_t n,
+                             unsigned long long* keys, int64_t* __restrict__ rep,
+                             int32_t* __restrict__ slot_of, int* __restrict__ overflow) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const unsigned long long h = hash[i];
+    uint32_t sl = (uint32_t)(h & (PAT_SLOTS - 1));
+    int found = -1;
+    for (int probe = 0; probe < PAT_SLOTS; probe++) {
+      const unsigned long long k = ((volatile unsigned long long*)keys)[sl];
+      if (k == h) {
+        found = (int)sl;
+        break;
+      }
+      if (k == 0ull) {
+        const unsigned long long old = atomicCAS(&keys[sl], 0ull, h);
+        if (old == 0ull) {
+          rep[sl] = i;
+          found = (int)sl;
+          break;
+        }
+        if (old == h) {
+          found = (int)sl;
+          break;
+        }
+      }
+      sl = (sl + 1) & (PAT_SLOTS - 1);
+    }
+    slot_of[i] = found;
+    if (found < 0) atomicExch(overflow, 1);
+  }
+}
+
+// one block: number the occupied slots (ascending slot order) and take each
+// pattern's length from its representative row
+__global__ void __launch_bounds__(1024)
+k_pat_number(const unsigned long long* __restrict__ keys, const int64_t* __restrict__ rep,
+             const int64_t* __restrict__ rp, int32_t* __restrict__ slot2pid,
+             int32_t* __restrict__ plen, int* __restrict__ npat) {
+  __shared__ int wsum[32];
+  __shared__ int base;
+  if (threadIdx.x == 0) base = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int s0 = 0; s0 < PAT_SLOTS; s0 += blockDim.x) {
+    const int sl = s0 + threadIdx.x;
+    const int occ = (sl < PAT_SLOTS && keys[sl] != 0ull) ? 1 : 0;
+    const unsigned bal = __ballot_sync(FULL, occ);
+    const int before_in_warp = __popc(bal & ((1u << lane) - 1u));
+    if (lane == 0) wsum[wid] = __popc(bal);
+    __syncthreads();
+    int before = 0;
+    for (int w = 0; w < wid; w++) before += wsum[w];
+    if (occ) {
+      const int id = base + before + before_in_warp;
+      slot2pid[sl] = id;
+      if (id < PAT_MAX) plen[id] = (int32_t)(rp[rep[sl] + 1] - rp[rep[sl]]);
+    } else if (sl < PAT_SLOTS) {
+      slot2pid[sl] = -1;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int t = 0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += wsum[w];
+      base += t;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *npat = base;
+}
+
+// warp per occupied slot: its representative's column offsets
+__global__ void k_pat_fill(const unsigned long long* __restrict__ keys, const int64_t* __restrict__ rep,
+                           const int32_t* __restrict__ slot2pid, const int64_t* __restrict__ rp,
+                           const int32_t* __restrict__ ci, const int32_t* __restrict__ pstart,
+                           int32_t* __restrict__ poff) {
+  const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+  for (int sl = blockIdx.x * wpb + (threadIdx.x >> 5); sl < PAT_SLOTS; sl += gridDim.x * wpb) {
+    if (keys[sl] == 0ull) continue;
+    const int p = slot2pid[sl];
+    const int64_t r = rep[sl], e0 = rp[r], e1 = rp[r + 1];
+    for (int64_t k = e0 + lane; k < e1; k += 32) poff[pstart[p] + (k - e0)] = (int32_t)((int64_t)ci[k] - r);
+  }
+}
+
+// warp per row: the row against its pattern; pid[i] = the pattern's number
+__global__ void k_pat_verify(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci, int64_t n,
+                             const int32_t* __restrict__ slot_of, const int32_t* __restrict__ slot2pid,
+                             const int32_t* __restrict__ pstart, const int32_t* __restrict__ poff,
+                             uint16_t* __restrict__ pid, int* __restrict__ bad) {
+  const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+  for (int64_t i = (int64_t)blockIdx.x * wpb + (threadIdx.x >> 5); i < n; i += (int64_t)gridDim.x * wpb) {
+    const int p = slot2pid[slot_of[i]];
+    const int64_t e0 = rp[i], e1 = rp[i + 1];
+    bool ok = (int64_t)(pstart[p + 1] - pstart[p]) == e1 - e0;
+    if (ok)
+      for (int64_t k = e0 + lane; k < e1; k += 32)
+        if ((int64_t)ci[k] - i != (int64_t)poff[pstart[p] + (k - e0)]) ok = false;
+    if (__any_sync(FULL, !ok) && lane == 0) atomicExch(bad, 1);
+    if (lane == 0) pid[i] = (uint16_t)p;
+  }
+}
+
+int build_row_patterns(Pool& P, Csr& A, cudaStream_t s) {
+  const int64_t n = A.nr;
+  if (n <= 0 || A.nr != A.nc) return MGR_SUCCESS;
+  Pool tmp;
+  tmp.s = s;
+  unsigned long long* hash = tmp.get<unsigned long long>(n);
+  unsigned long long* keys = tmp.get<unsigned long long>(PAT_SLOTS);
+  int64_t* rep = tmp.get<int64_t>(PAT_SLOTS);
+  int32_t* slot_of = tmp.get<int32_t>(n);
+  int32_t* slot2pid = tmp.get<int32_t>(PAT_SLOTS);
+  int32_t* plen = tmp.get<int32_t>(PAT_MAX);
+  int* flags = tmp.get<int>(3);   // overflow, npat, bad
+  if (tmp.err) {
+    tmp.free_all_async(s);
+    return tmp.err;
+  }
+  MGR_TRY_CUDA(cudaMemsetAsync(keys, 0, sizeof(unsigned long long) * PAT_SLOTS, s));
+  MGR_TRY_CUDA(cudaMemsetAsync(flags, 0, sizeof(int) * 3, s));
+  MGR_LAUNCH k_pat_hash<<<grid_for(n, 8, 152 * 16), 256, 0, s>>>(A.rp, A.ci, n, hash);
+  MGR_LAUNCH k_pat_insert<<<grid_for(n, 256, 152 * 16), 256, 0, s>>>(hash, n, keys, rep, slot_of, flags);
+  MGR_LAUNCH k_pat_number<<<1, 1024, 0, s>>>(keys, rep, A.rp, slot2pid, plen, flags + 1);
+  int hf[3] = {0, 0, 0};
+  MGR_TRY_CUDA(cudaMemcpyAsync(hf, flags, sizeof(int) * 2, cudaMemcpyDeviceToHost, s));
+  MGR_TRY_CUDA(cudaStreamSynchronize(s));
+  const int npat = hf[1];
+  if (hf[0] || npat <= 0 || npat > PAT_MAX) {   // too many patterns: plain CSR
+    tmp.free_all_async(s);
+    return MGR_SUCCESS;
+  }
+  std::vector<int32_t> len(npat), start(npat + 1, 0);
+  MGR_TRY_CUDA(cudaMemcpyAsync(len.data(), plen, sizeof(int32_t) * npat, cudaMemcpyDeviceToHost, s));
+  MGR_TRY_CUDA(cudaStreamSynchronize(s));
+  for (int p = 0; p < npat; p++) start[p + 1] = start[p] + len[p];
+  A.pstart = P.get<int32_t>(npat + 1);
+  A.poff = P.get<int32_t>(start[npat] > 0 ? start[npat] : 1);
+  A.pid = P.get<uint16_t>(n);
+  if (P.err) {
+    tmp.free_all_async(s);
+    return P.err;
+  }
+  MGR_TRY_CUDA(cudaMemcpyAsync(A.pstart, start.data(), sizeof(int32_t) * (npat + 1),
+                               cudaMemcpyHostToDevice, s));
+  MGR_LAUNCH k_pat_fill<<<grid_for((int64_t)PAT_SLOTS * 32, 256, 152 * 16), 256, 0, s>>>(
+      keys, rep, slot2pid, A.rp, A.ci, A.pstart, A.poff);
+  MGR_LAUNCH k_pat_verify<<<grid_for(n, 8, 152 * 16), 256, 0, s>>>(A.rp, A.ci, n, slot_of, slot2pid,
+                                                                    A.pstart, A.poff, A.pid, flags + 2);
+  MGR_TRY_CUDA(cudaMemcpyAsync(hf + 2, flags + 2, sizeof(int), cudaMemcpyDeviceToHost, s));
+  MGR_TRY_CUDA(cudaStreamSynchronize(s));   // `start` outlives its copy
+  tmp.free_all_async(s);
+  if (hf[2]) {   // a hash collision: keep plain CSR
+    P.release(A.pstart, s);
+    P.release(A.poff, s);
+    P.release(A.pid, s);
+    A.pstart = A.poff = nullptr;
+    A.pid = nullptr;
+    return MGR_SUCCESS;
+  }
+  A.npat = npat;
+  return MGR_SUCCESS;
+}
+
 int build_amg(Handle* h, Pool& P, int* derr, const Csr& A0, bool own_input,
               const int32_t* comp0, int slot, Amg** out, cudaStream_t s) {
   Pool tmp;
@@ -2174,6 +2378,8 @@ int build_amg(Handle* h, Pool& P, int* derr, const Csr& A0, bool own_input,
   }
   if (rc == MGR_SUCCESS) rc = check_dev_err(derr, s);
   if (rc == MGR_SUCCESS) rc = dense_coarsest(P, derr, g, tmp, s);
+  // shared row patterns of the finest operator (the mesh's own stencil)
+  if (rc == MGR_SUCCESS && g->lev[0].A.nnz >= PAT_MIN_NNZ) rc = build_row_patterns(P, g->lev[0].A, s);
   g_trace.mark("amg coarsest inverse", slot, (int)g->lev.size() - 1);
   tmp.free_all_async(s);
   return rc;

@@ -29,7 +29,7 @@ EXPORTED = ["mgr_options_default", "fgmres_options_default", "mgr_setup", "mgr_a
             "mgr_amg_levels", "mgr_get_cf", "mgr_vcycle", "mgr_splitmix64_device",
             "mgr_launch_count", "mgr_trim_memory", "mgr_solve_host", "mgr_vcycle_noalloc", "mgr_setup_batched",
             "fgmres_solve_batched", "mgr_batch_info", "mgr_batch_handle", "mgr_destroy_batched",
-            "mgr_get_block_colors", "mgr_build_id", "mgr_memory_usage", "mgr_spmv", "mgr_host_launch_count"]
+            "mgr_get_block_colors", "mgr_build_id", "mgr_memory_usage", "mgr_spmv", "mgr_host_launch_count", "mgr_row_patterns"]
 
 
 class MgrMatrix(C.Structure):
@@ -101,6 +101,7 @@ def lib():
             L.mgr_get_csr.argtypes = [P, C.c_int, C.c_int, C.c_int, P, P, P, P]
             L.mgr_amg_levels.argtypes = [P, C.c_int]
             L.mgr_get_cf.argtypes = [P, C.c_int, C.c_int, P]
+            L.mgr_row_patterns.argtypes = [P, C.c_int, C.c_int]
             L.mgr_get_cf.restype = I64
             L.mgr_vcycle.argtypes = [P, C.c_int, P, P, P]
             L.mgr_splitmix64_device.argtypes = [P, P, I64, P]
@@ -365,6 +366,11 @@ def mgr_get_scipy(h, kind, slot=0, lvl=0):
 
 def mgr_amg_levels(h, slot):
     return int(lib().mgr_amg_levels(h, slot))
+
+
+def mgr_row_patterns(h, slot, lvl):
+    """Shared row patterns of an AMG operator (0: applied as plain CSR)."""
+    return _check(lib().mgr_row_patterns(h, slot, lvl), "mgr_row_patterns")
 
 
 def mgr_get_cf(h, slot, lvl):

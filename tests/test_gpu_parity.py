@@ -333,6 +333,16 @@ def test_full_size_workload_hierarchy_and_solve():
     o = oracle.Oracle(p)
     s = mgr.Solver(p)
     compare_hierarchy(o, s.h, 2)
+    # the displacement operator is applied through shared row patterns (the
+    # mesh stencil: a few hundred distinct column-offset rows), with the
+    # V-cycle still the oracle's to the apply bar, element-wise
+    npat = mgr.mgr_row_patterns(s.h, 0, 0)
+    assert 0 < npat <= 4096, npat
+    b = np.random.default_rng(31).standard_normal(p.meta["n_u"])
+    x = torch.zeros(p.meta["n_u"], dtype=torch.float64, device="cuda")
+    mgr.mgr_vcycle(s.h, 0, torch.from_numpy(b).cuda(), x)
+    torch.cuda.synchronize()
+    assert _maxrel(x.cpu().numpy(), o.vcycle(0, b)) <= 1e-10
     ref = o.fgmres(p.rhs)
     r = s.solve(torch.from_numpy(p.rhs).cuda())
     assert r["converged"] and abs(r["iters"] - ref["iters"]) <= 2
