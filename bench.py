@@ -526,18 +526,29 @@ def run_ours(args):
                              frac=byts / (ms_v * 1e-3) / 1e9 / peak)
         del vin, vx
     used, reserved = mgr.mgr_memory_usage()
-    mgr.mgr_destroy(h)
+    # the FP64 Jacobian product as the solve forms it (through the setup's
+    # segmented row patterns: a value per non-zero, a pattern id and S segment
+    # starts per row), and the plain CSR product beside it
     y = torch.empty_like(b)
     xin = torch.randn_like(b)
-    mgr.mgr_spmv(A, xin, y)
-    tm.start()
-    for _ in range(args.vcycles):
-        mgr.mgr_spmv(A, xin, y)
-    ms_az = tm.stop() / args.vcycles
-    az_bytes = (p.n + 1) * 8 + p.nnz * 12 + 2 * p.n * 8
-    kernels["jacobian_spmv_fp64"] = dict(ms=ms_az, algorithmic_bytes=az_bytes,
-                                         gbs=az_bytes / (ms_az * 1e-3) / 1e9,
-                                         frac=az_bytes / (ms_az * 1e-3) / 1e9 / peak)
+    npat, nseg = mgr.mgr_jacobian_patterns(h)
+    via_pat = mgr.mgr_jacobian_product(h, A, xin, y, check=True)
+    csr_bytes = (p.n + 1) * 8 + p.nnz * 12 + 2 * p.n * 8
+    pat_bytes = (p.n + 1) * 8 + p.nnz * 8 + p.n * (2 + 4 * nseg) + 2 * p.n * 8
+    for name, fn, byts in (
+            ("jacobian_spmv_fp64", lambda: mgr.mgr_jacobian_product(h, A, xin, y, check=False),
+             pat_bytes if via_pat else csr_bytes),
+            ("jacobian_spmv_fp64_csr", lambda: mgr.mgr_spmv(A, xin, y), csr_bytes)):
+        fn()
+        tm.start()
+        for _ in range(args.vcycles):
+            fn()
+        ms_az = tm.stop() / args.vcycles
+        kernels[name] = dict(ms=ms_az, algorithmic_bytes=byts, gbs=byts / (ms_az * 1e-3) / 1e9,
+                             frac=byts / (ms_az * 1e-3) / 1e9 / peak)
+    kernels["jacobian_spmv_fp64"].update(row_patterns=npat, segments_per_row=nseg,
+                                         through_patterns=bool(via_pat))
+    mgr.mgr_destroy(h)
     del y, xin
     dom = kernels["vcycle_uu_fp32"]
     traffic, traffic_note = profiled_traffic("fp32", dom["algorithmic_bytes"])

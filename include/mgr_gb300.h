@@ -156,7 +156,23 @@ typedef struct {
   int32_t restart;   /* Krylov subspace size m (default 50) */
   int32_t max_iter;  /* total preconditioner applications (default 1000) */
   double rtol;       /* stop when ||b - A x||_2 <= rtol ||b||_2 (default 1e-8) */
+  /* Arnoldi orthogonalisation of iteration j, in FP64 (the paper names GMRES
+   * without fixing it):
+   *   MGR_ORTHO_MGS  -- modified Gram-Schmidt: j + 2 dependent launches, each
+   *                     one projection (2 FMAs per basis entry, memory-bound);
+   *   MGR_ORTHO_CGS2 -- classical Gram-Schmidt applied twice: three passes
+   *                     over the basis, 4 FMAs per basis entry (FP64-bound on
+   *                     GB300, but a fixed handful of launches);
+   *   MGR_ORTHO_AUTO -- (default) MGS for systems of at least 2^21 unknowns,
+   *                     CGS2 below, where MGS's per-launch latency dominates.
+   * Every batch schedule follows the same per-system choice, so batched
+   * solutions stay bitwise those of fgmres_solve.  Other values: INVALID_ARG. */
+  int32_t ortho;
 } fgmres_options_t;
+
+#define MGR_ORTHO_CGS2 0
+#define MGR_ORTHO_MGS 1
+#define MGR_ORTHO_AUTO 2
 
 typedef struct {
   int32_t iters;         /* preconditioner applications performed */
@@ -265,12 +281,37 @@ int64_t mgr_get_cf(mgr_handle_t h, int slot, int lvl, int8_t* out);
  * arrays of that AMG's size).  Asynchronous on `stream`. */
 int mgr_vcycle(mgr_handle_t h, int slot, const double* b, double* x, void* stream);
 
-/* y = A x with the FP64 sparse product that fgmres_solve applies to the
- * Jacobian at every iteration (the "w = A z_j" step of right-preconditioned
- * GMRES, Sec. 4).  A's arrays, x and y are DEVICE arrays (n doubles each; y
+/* y = A x with the FP64 CSR product that fgmres_solve applies to the Jacobian
+ * at every iteration (the "w = A z_j" step of right-preconditioned GMRES,
+ * Sec. 4; mgr_jacobian_product gives the pattern form of the same sums).
+ * A's arrays, x and y are DEVICE arrays (n doubles each; y
  * must not overlap x); the grouping arrays of A are not read.  Asynchronous
  * on `stream`.  INVALID_ARG for a NULL or negative-size argument. */
 int mgr_spmv(const mgr_matrix_t* A, const double* x, double* y, void* stream);
+
+/* Segmented row patterns of the Jacobian, analysed by mgr_setup when A has
+ * at least 2^24 non-zeros: each row's sorted columns are cut into segments
+ * wherever a column lies more than 2^15 past the one before it; rows whose
+ * segments hold the same offsets from their first columns share a pattern
+ * (at most 4096), and a row then keeps a 2-byte pattern id and the first
+ * column of each segment.  Returns the number of patterns (0: none -- the
+ * solve's products read the CSR); *segments (may be NULL) = the segment starts
+ * kept per row.  INVALID_ARG for a NULL handle.  Host-side query. */
+int mgr_jacobian_patterns(mgr_handle_t h, int* segments);
+
+/* y = A x as fgmres_solve(h, A, ...) forms it: through h's Jacobian patterns
+ * when they describe A -- the same row_ptr / col_idx device arrays, n and nnz
+ * as at mgr_setup, and every row matching its pattern -- else the CSR product
+ * of mgr_spmv.  Both form every row's sum in the same order, so y is bitwise
+ * mgr_spmv's.  check = 1: every row is checked first (one pass over the index
+ * arrays, synchronising `stream`; fgmres_solve does the same at its start);
+ * check = 0: the outcome of the last check of those arrays (at mgr_setup, by
+ * a solve or by a check = 1 call) is reused and the call is asynchronous --
+ * only for a caller that has not rewritten the index arrays since.  Device
+ * arrays as for mgr_spmv.  Returns 1 (patterns used), 0 (CSR) or a negative
+ * error (INVALID_ARG also for check other than 0 or 1). */
+int mgr_jacobian_product(mgr_handle_t h, const mgr_matrix_t* A, const double* x, double* y,
+                         int check, void* stream);
 
 /* Splitmix64 (Steele, Lea, Flood 2014) as evaluated on the device, for tests
  * of the PMIS weight hash: out[i] = splitmix64(in[i]) for n values (device). */
@@ -322,8 +363,9 @@ int mgr_vcycle_noalloc(mgr_handle_t h, int slot, const double* b, double* x, voi
  *     the preconditioner applications as ONE CUDA graph with a conditional
  *     branch per system (its captured application; branches of finished
  *     systems are switched off on the device), the Jacobian products as one
- *     row-binned launch per lanes-per-row group, the Gram-Schmidt passes over
- *     all systems' rows, and one readback of every Hessenberg column.  Each
+ *     row-binned launch per lanes-per-row group, each Gram-Schmidt launch (a
+ *     modified Gram-Schmidt projection, or a classical pass) over all systems'
+ *     rows, and one readback of every Hessenberg column.  Each
  *     system's arithmetic is its single-system arithmetic, so its iterations
  *     and solution are bit for bit those of fgmres_solve.
  */
@@ -331,9 +373,10 @@ typedef struct mgr_batch_s* mgr_batch_t;
 
 /* Set up nsys systems A[0..nsys) with the same options.  `workers` = number of
  * concurrent workers (1..16) of the worker schedule; -1 selects the lockstep
- * schedule; 0 lets the library choose by timing one round of every system's
- * preconditioner application with 1, 2, 4, 8 and 16 workers and with the
- * lockstep graph (the fastest is kept; see mgr_batch_info).  The setups
+ * schedule; 0 lets the library choose by timing one round -- one FGMRES
+ * iteration of every system: preconditioner application, Jacobian product and
+ * the default Gram-Schmidt -- with 1, 2, 4, 8 and 16 workers and with the
+ * lockstep schedule (the fastest is kept; see mgr_batch_info).  The setups
  * themselves run on up to 16 workers.  Ordered after the caller's earlier work
  * on `stream`; synchronises `stream` before returning.  A[i] is owned by the
  * caller and may be freed afterwards.  Errors: INVALID_ARG (nsys <= 0, workers

@@ -38,8 +38,12 @@ def nvcc():
 
 
 def _flags(verbose=False):
+    # host code: no contracted multiply-adds either (GCC contracts them by
+    # default on Arm, and where it does depends on the surrounding code), so
+    # the host Givens rotations and triangular solves of the single-system and
+    # the batched FGMRES round identically on every machine
     common = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
-                     "-I", os.path.join(ROOT, "include")]
+                     "-Xcompiler", "-ffp-contract=off", "-I", os.path.join(ROOT, "include")]
     if verbose:
         common += ["-Xptxas", "-v"]
     return common

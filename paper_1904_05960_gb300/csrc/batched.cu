@@ -186,8 +186,8 @@ static int build_lockstep(Batch* B, const mgr_matrix_t* A, cudaStream_t s) {
 }
 
 // Schedule autotuner: time one round -- one FGMRES iteration (preconditioner
-// application, Jacobian product, Gram-Schmidt) of every system -- for each
-// worker count and for the lockstep graph, and keep the fastest.
+// application, Jacobian product, the default Gram-Schmidt) of every system --
+// for each worker count and for the lockstep graph, and keep the fastest.
 static constexpr int TUNE_M = 50;
 static int autotune_workers(Batch* B, const mgr_matrix_t* A, cudaStream_t caller) {
   MGR_TRY_CUDA(cudaStreamSynchronize(caller));
@@ -203,7 +203,7 @@ static int autotune_workers(Batch* B, const mgr_matrix_t* A, cudaStream_t caller
       MGR_TRY_CUDA(cudaDeviceSynchronize());
       const auto t0 = std::chrono::steady_clock::now();
       const int rc = run_workers(B, w, [&](int i, cudaStream_t s) {
-        MGR_TRY(krylov_tune_iteration(B->sys[i], &A[i], TUNE_M, s));
+        MGR_TRY(krylov_tune_iteration(B->sys[i], &A[i], TUNE_M, MGR_ORTHO_AUTO, s));
         MGR_TRY_CUDA(cudaStreamSynchronize(s));
         return MGR_SUCCESS;
       });
@@ -218,7 +218,7 @@ static int autotune_workers(Batch* B, const mgr_matrix_t* A, cudaStream_t caller
     }
   }
   if (B->ls && B->ls->exec) {
-    MGR_TRY(lockstep_tune_prepare(B->ls, B->sys.data(), A, TUNE_M, caller));
+    MGR_TRY(lockstep_tune_prepare(B->ls, B->sys.data(), A, TUNE_M, MGR_ORTHO_AUTO, caller));
     double t = 0.0;
     for (int rep = 0; rep < 2; rep++) {
       MGR_TRY_CUDA(cudaDeviceSynchronize());

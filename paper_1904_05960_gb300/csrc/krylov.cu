@@ -120,35 +120,43 @@ __global__ void __launch_bounds__(KB) k_mdot(const double* __restrict__ V, int64
 
 static inline int mdot_blocks(int64_t n) { return (int)((n + MD_CHUNK - 1) / MD_CHUNK); }
 
-// h[i] (+)= sum_blk part[blk * nv + i]: one warp per vector, fixed order.
-// With SQRT the sum is replaced by its square root (a norm from partial sums
-// of squares) and rinv[0] receives 1/norm (1 if the norm is 0), so the
-// scaling kernels multiply instead of dividing per element.
+// h[i] (+)= sum_blk part[blk * nv + i]: one block of FIN_T threads per vector,
+// each thread adding a strided share of the partials (several loads in
+// flight), then a fixed reduction tree.  With SQRT the sum is replaced by its
+// square root (a norm from partial sums of squares) and rinv[0] receives
+// 1/norm (1 if the norm is 0), so the scaling kernels multiply instead of
+// dividing per element.
+static constexpr int FIN_T = 256;
 template <bool SQRT>
-__device__ __forceinline__ void mdot_final_warp(const double* __restrict__ part, int nblk, int nv,
-                                                int i, double* __restrict__ h, int accumulate,
-                                                double* __restrict__ rinv) {
-  const int lane = threadIdx.x & 31;
+__device__ __forceinline__ void mdot_final_block(const double* __restrict__ part, int nblk, int nv,
+                                                 int i, double* __restrict__ h, int accumulate,
+                                                 double* __restrict__ rinv) {
+  __shared__ double red[FIN_T / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   double acc = 0.0;
 #pragma unroll 4
-  for (int b = lane; b < nblk; b += 32) acc += part[(int64_t)b * nv + i];
+  for (int b = threadIdx.x; b < nblk; b += FIN_T) acc += part[(int64_t)b * nv + i];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
-  if (lane == 0) {
+  if (lane == 0) red[wid] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tot = 0.0;
+    for (int q = 0; q < FIN_T / 32; q++) tot += red[q];
     if (SQRT) {
-      acc = sqrt(acc);
-      rinv[0] = acc > 0.0 ? 1.0 / acc : 1.0;
+      tot = sqrt(tot);
+      rinv[0] = tot > 0.0 ? 1.0 / tot : 1.0;
     }
-    h[i] = accumulate ? h[i] + acc : acc;
+    h[i] = accumulate ? h[i] + tot : tot;
   }
 }
 
+// launched with nv blocks of FIN_T threads
 template <bool SQRT>
-__global__ void k_mdot_final(const double* __restrict__ part, int nblk, int nv,
-                             double* __restrict__ h, int accumulate, double* __restrict__ rinv) {
-  const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (i >= nv) return;
-  mdot_final_warp<SQRT>(part, nblk, nv, i, h, accumulate, rinv);
+__global__ void __launch_bounds__(FIN_T) k_mdot_final(const double* __restrict__ part, int nblk,
+                                                      int nv, double* __restrict__ h,
+                                                      int accumulate, double* __restrict__ rinv) {
+  mdot_final_block<SQRT>(part, nblk, nv, blockIdx.x, h, accumulate, rinv);
 }
 
 // w -= sum_i h[i] V_i over block blk's chunk (the layout of mdot_body); with
@@ -199,6 +207,90 @@ __global__ void __launch_bounds__(KB) k_mupdate(const double* __restrict__ V, in
                                                 const double* __restrict__ h, double* __restrict__ w,
                                                 int64_t n, double* __restrict__ part) {
   mupdate_body<NORM>(V, ld, nv, h, w, n, part, blockIdx.x);
+}
+
+// Modified Gram-Schmidt, step i of iteration j, in one launch:
+//   w -= h[i-1] V_(i-1)                          (i >= 1)
+//   h[i] = V_i . w                                (i <= j)
+//   h[j+1] = ||w||, rinv[0] = 1 / ||w||           (i = j + 1; 1 if ||w|| = 0)
+// G = mgs_grid(n) blocks stride over KB-entry tiles, ascending for even i and
+// descending for odd i, so that every step starts where the one before it
+// ended, while that end of w and V_(i-1) is still in L2.  Each block stores
+// its partial sum; the last block to arrive (a ticket counter that it resets)
+// adds the partials in block order, so the sum does not depend on which block
+// arrives last.  No block waits for another.  The body is shared by the
+// single-system kernel and the lockstep (many-system) kernel.
+static constexpr int MGS_GRID = 152 * 8;
+__host__ __device__ inline int mgs_grid(int64_t n) {
+  const int64_t t = (n + KB - 1) / KB;
+  return (int)(t < 1 ? 1 : (t < MGS_GRID ? t : MGS_GRID));
+}
+__device__ __forceinline__ void mgs_body(const double* __restrict__ V, int64_t ld, int i, int j,
+                                         double* __restrict__ w, int64_t n,
+                                         double* __restrict__ part, double* __restrict__ h,
+                                         double* __restrict__ rinv, unsigned* __restrict__ ticket,
+                                         int G, int blk) {
+  __shared__ double red[KB / 32];
+  __shared__ bool last;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const double hp = i > 0 ? h[i - 1] : 0.0;
+  const double* vp = V + (int64_t)(i > 0 ? i - 1 : 0) * ld;
+  const double* vi = V + (int64_t)(i <= j ? i : 0) * ld;
+  const int64_t ntile = (n + KB - 1) / KB;
+  const int64_t nk = blk < ntile ? (ntile - blk + G - 1) / G : 0;
+  double acc = 0.0;
+#pragma unroll 4
+  for (int64_t kk = 0; kk < nk; kk++) {
+    const int64_t k = (i & 1) ? nk - 1 - kk : kk;
+    const int64_t t = (blk + k * G) * KB + threadIdx.x;
+    if (t < n) {
+      double x = w[t];
+      if (i > 0) {
+        x -= hp * vp[t];
+        w[t] = x;
+      }
+      acc += (i <= j ? vi[t] : x) * x;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
+  if (lane == 0) red[wid] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s2 = 0.0;
+    for (int q = 0; q < KB / 32; q++) s2 += red[q];
+    part[blk] = s2;
+    __threadfence();
+    last = atomicAdd(ticket, 1u) == (unsigned)(G - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  double s2 = 0.0;
+  for (int b = threadIdx.x; b < G; b += KB) s2 += __ldcg(part + b);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(FULL, s2, o);
+  if (lane == 0) red[wid] = s2;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tot = 0.0;
+    for (int q = 0; q < KB / 32; q++) tot += red[q];
+    if (i <= j) {
+      h[i] = tot;
+    } else {
+      const double nrm = sqrt(tot);
+      h[i] = nrm;
+      rinv[0] = nrm > 0.0 ? 1.0 / nrm : 1.0;
+    }
+    *ticket = 0u;
+  }
+}
+
+__global__ void __launch_bounds__(KB) k_mgs_step(const double* __restrict__ V, int64_t ld, int i,
+                                                 int j, double* __restrict__ w, int64_t n,
+                                                 double* __restrict__ part, double* __restrict__ h,
+                                                 double* __restrict__ rinv,
+                                                 unsigned* __restrict__ ticket) {
+  mgs_body(V, ld, i, j, w, n, part, h, rinv, ticket, gridDim.x, blockIdx.x);
 }
 
 // x += sum_i y[i] Z_i  (Z in FP64 or FP32)
@@ -264,8 +356,9 @@ static int ensure_krylov(Handle* h, int m, cudaStream_t s) {
   h->hcol = P.get<double>(m + 2);
   h->hred = P.get<double>(4);
   h->yv = P.get<double>(m + 2);
+  h->ticket = P.get<unsigned>(1);
   if (P.err) return P.err;
-  (void)s;
+  MGR_TRY_CUDA(cudaMemsetAsync(h->ticket, 0, sizeof(unsigned), s));
   return MGR_SUCCESS;
 }
 
@@ -274,7 +367,94 @@ static void mdot(Handle* h, const double* V, int64_t ld, int nv, const double* w
                  double* dst, int accumulate, cudaStream_t s) {
   const int nb = mdot_blocks(n);
   MGR_LAUNCH k_mdot<false><<<nb, KB, 0, s>>>(V, ld, nv, const_cast<double*>(w), n, h->part, nullptr);
-  MGR_LAUNCH k_mdot_final<false><<<(nv + 7) / 8, 256, 0, s>>>(h->part, nb, nv, dst, accumulate, nullptr);
+  MGR_LAUNCH k_mdot_final<false><<<nv, FIN_T, 0, s>>>(h->part, nb, nv, dst, accumulate, nullptr);
+}
+
+// ---------------------------------------------------------------------------
+// Jacobian product through segmented row patterns
+// ---------------------------------------------------------------------------
+// Row i's k-th column is base[i * S + (e >> 28)] + (e & 0x0FFFFFFF), e = its
+// pattern's k-th encoding: per non-zero only the value is streamed (the
+// pattern table is small and stays in cache; a 2-byte id and S segment starts
+// per row).  G lanes per row, one accumulator per lane, loads unrolled by
+// four: the CSR product's loop, so every row's sum is formed in the same order
+// and the results are bitwise those of the CSR product.
+template <class I, int G, bool RES>
+__global__ void __launch_bounds__(256)
+k_spmv_seg(const int64_t* __restrict__ rp, const uint16_t* __restrict__ pid,
+           const int32_t* __restrict__ pstart, const uint32_t* __restrict__ penc,
+           const int32_t* __restrict__ base, int S, const double* __restrict__ val, I nr,
+           const double* __restrict__ x, double* __restrict__ y, const double* __restrict__ b) {
+  const I gid = (I)blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & (G - 1);
+  const I stride = ((I)gridDim.x * blockDim.x) / G;
+  const unsigned gmask = (G == 32) ? FULL : (((1u << G) - 1u) << ((threadIdx.x & 31) & ~(G - 1)));
+  for (I i = gid / G; i < nr; i += stride) {
+    const I e0 = (I)rp[i], e1 = (I)rp[i + 1];
+    const uint32_t* pe = penc + pstart[pid[i]];
+    const int32_t* bi = base + (int64_t)i * S;
+    double acc = 0;
+    I k = e0 + lane;
+#pragma unroll 4
+    for (; k < e1; k += G) {
+      const uint32_t e = __ldg(pe + (k - e0));
+      acc += val[k] * __ldg(x + (__ldg(bi + (e >> 28)) + (int32_t)(e & 0x0FFFFFFFu)));
+    }
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(gmask, acc, o, G);
+    if (lane == 0) y[i] = RES ? b[i] - acc : acc;
+  }
+}
+
+template <class I, bool RES>
+static void spmv_seg_launch(const SegPatterns& P, const int64_t* rp, const double* val, int64_t nr,
+                            int64_t nnz, const double* x, double* y, const double* b,
+                            cudaStream_t s) {
+  const int G = spmv_lanes(nnz, nr);
+  const unsigned grid = (unsigned)std::min<int64_t>((nr * G + 255) / 256, 152LL * 64);
+#define MGR_SEG_CASE(g)                                                                          \
+  case g:                                                                                        \
+    MGR_LAUNCH k_spmv_seg<I, g, RES><<<grid, 256, 0, s>>>(rp, P.pid, P.pstart, P.penc, P.base,   \
+                                                          P.S, val, (I)nr, x, y, b);             \
+    break;
+  switch (G) {
+    MGR_SEG_CASE(1)
+    MGR_SEG_CASE(2)
+    MGR_SEG_CASE(4)
+    MGR_SEG_CASE(8)
+    MGR_SEG_CASE(16)
+    default: MGR_SEG_CASE(32)
+  }
+#undef MGR_SEG_CASE
+}
+
+void jacobian_product(Handle* h, const mgr_matrix_t* A, bool pat, const double* x, double* y,
+                      const double* b, bool res, cudaStream_t s) {
+  const int64_t n = A->n, nnz = A->nnz;
+  if (!pat || n <= 0) {
+    if (res) residual64(A->row_ptr, A->col_idx, A->val, n, nnz, b, x, y, s);
+    else spmv64(A->row_ptr, A->col_idx, A->val, n, nnz, x, y, s);
+    return;
+  }
+  const SegPatterns& P = h->jpat.ps;
+  // 32-bit offsets on the same condition as the CSR product
+  if (nnz + 64 < INT32_MAX && n * 16 + 152LL * 64 * 256 < INT32_MAX) {
+    if (res) spmv_seg_launch<int, true>(P, A->row_ptr, A->val, n, nnz, x, y, b, s);
+    else spmv_seg_launch<int, false>(P, A->row_ptr, A->val, n, nnz, x, y, b, s);
+  } else {
+    if (res) spmv_seg_launch<int64_t, true>(P, A->row_ptr, A->val, n, nnz, x, y, b, s);
+    else spmv_seg_launch<int64_t, false>(P, A->row_ptr, A->val, n, nnz, x, y, b, s);
+  }
+}
+
+// Modified Gram-Schmidt of w against V_0..V_j: hcol[0..j] = the projections,
+// hcol[j+1] = ||w||, vnext = w / ||w||
+static void mgs(Handle* h, int j, double* vnext, cudaStream_t s) {
+  const int64_t n = h->n;
+  for (int i = 0; i <= j + 1; i++)
+    MGR_LAUNCH k_mgs_step<<<mgs_grid(n), KB, 0, s>>>(h->V, n, i, j, h->w, n, h->part, h->hcol,
+                                                     h->hred + 1, h->ticket);
+  MGR_LAUNCH k_scale_by<<<grid_for(n, KB), KB, 0, s>>>(h->w, h->hred + 1, vnext, n);
 }
 
 // Pinned host buffers of 72 doubles (m <= 60) for the Hessenberg readbacks.
@@ -318,10 +498,16 @@ int fgmres_run(Handle* h, const mgr_matrix_t* A, const double* b, double* x,
                const fgmres_options_t* o, fgmres_info_t* info, cudaStream_t s) {
   const int64_t n = h->n;
   const int m = o->restart > 0 ? o->restart : 50;
-  if (m > 60) return MGR_ERR_INVALID_ARG;
+  const int ortho = resolve_ortho(o->ortho, n);
+  if (m > 60 || ortho < 0) return MGR_ERR_INVALID_ARG;
   const int maxit = o->max_iter > 0 ? o->max_iter : 1000;
   const double rtol = o->rtol > 0 ? o->rtol : 1e-8;
   MGR_TRY(ensure_krylov(h, m, s));
+  // the Jacobian products go through the setup's row patterns when they still
+  // describe A (checked here, once per solve), else through the CSR
+  const int pv = jacobian_patterns_valid(h, A, s);
+  if (pv < 0) return pv;
+  const bool pat = pv == 1;
   const bool mixed = h->opt.precision == MGR_MIXED;
   // pinned host mirror for the per-iteration readbacks, leased per host thread
   double* hp = nullptr;
@@ -366,7 +552,7 @@ int fgmres_run(Handle* h, const mgr_matrix_t* A, const double* b, double* x,
       {
         const int nb = mdot_blocks(n);
         MGR_LAUNCH k_mdot<false><<<nb, KB, 0, s>>>(h->r, n, 1, h->r, n, h->part, nullptr);
-        MGR_LAUNCH k_mdot_final<true><<<1, 32, 0, s>>>(h->part, nb, 1, h->hred, 0, h->hred + 1);
+        MGR_LAUNCH k_mdot_final<true><<<1, FIN_T, 0, s>>>(h->part, nb, 1, h->hred, 0, h->hred + 1);
         MGR_LAUNCH k_scale_by<<<grid_for(n, KB), KB, 0, s>>>(h->r, h->hred + 1, h->V, n);
       }
       std::fill(g.begin(), g.end(), 0.0);
@@ -383,25 +569,27 @@ int fgmres_run(Handle* h, const mgr_matrix_t* A, const double* b, double* x,
           MGR_TRY(apply_mgr_mixed_into(h, vj, h->zout32, s));
           MGR_LAUNCH k_widen<<<grid_for(n, KB), KB, 0, s>>>(h->zout32, zj, h->r, n);
           if (tr) cudaEventRecord(tev[1], s);
-          spmv64(A->row_ptr, A->col_idx, A->val, n, A->nnz, h->r, h->w, s);
+          jacobian_product(h, A, pat, h->r, h->w, nullptr, false, s);
         } else {
           double* zj = (double*)h->Z + (int64_t)j * n;
           MGR_TRY(apply_mgr(h, vj, zj, s));
           if (tr) cudaEventRecord(tev[1], s);
-          spmv64(A->row_ptr, A->col_idx, A->val, n, A->nnz, zj, h->w, s);
+          jacobian_product(h, A, pat, zj, h->w, nullptr, false, s);
         }
         if (tr) cudaEventRecord(tev[2], s);
-        // classical Gram-Schmidt, twice; the second update also forms ||w||^2
-        mdot(h, h->V, n, j + 1, h->w, n, h->hcol, 0, s);                       // h1 = V^T w
-        {
-          const int nb = mdot_blocks(n);                                        // w -= V h1; h2 = V^T w
+        if (ortho == MGR_ORTHO_MGS) {
+          mgs(h, j, vnext, s);   // j + 1 dependent projections, then ||w||
+        } else {
+          // classical Gram-Schmidt, twice; the second update also forms ||w||^2
+          mdot(h, h->V, n, j + 1, h->w, n, h->hcol, 0, s);                     // h1 = V^T w
+          const int nb = mdot_blocks(n);                                      // w -= V h1; h2 = V^T w
           MGR_LAUNCH k_mdot<true><<<nb, KB, 0, s>>>(h->V, n, j + 1, h->w, n, h->part, h->hcol);
-          MGR_LAUNCH k_mdot_final<false><<<(j + 1 + 7) / 8, 256, 0, s>>>(h->part, nb, j + 1, h->yv, 0, nullptr);
+          MGR_LAUNCH k_mdot_final<false><<<j + 1, FIN_T, 0, s>>>(h->part, nb, j + 1, h->yv, 0, nullptr);
+          MGR_LAUNCH k_mupdate<true><<<nb, KB, 0, s>>>(h->V, n, j + 1, h->yv, h->w, n, h->part);   // w -= V h2
+          MGR_LAUNCH k_mdot_final<false><<<j + 1, FIN_T, 0, s>>>(h->yv, 1, j + 1, h->hcol, 1, nullptr);   // h += h2
+          MGR_LAUNCH k_mdot_final<true><<<1, FIN_T, 0, s>>>(h->part, nb, 1, h->hcol + j + 1, 0, h->hred + 1);   // ||w||
+          MGR_LAUNCH k_scale_by<<<grid_for(n, KB), KB, 0, s>>>(h->w, h->hred + 1, vnext, n);
         }
-        MGR_LAUNCH k_mupdate<true><<<mdot_blocks(n), KB, 0, s>>>(h->V, n, j + 1, h->yv, h->w, n, h->part);   // w -= V h2
-        MGR_LAUNCH k_mdot_final<false><<<(j + 1 + 7) / 8, 256, 0, s>>>(h->yv, 1, j + 1, h->hcol, 1, nullptr);   // h += h2
-        MGR_LAUNCH k_mdot_final<true><<<1, 32, 0, s>>>(h->part, mdot_blocks(n), 1, h->hcol + j + 1, 0, h->hred + 1);     // ||w||
-        MGR_LAUNCH k_scale_by<<<grid_for(n, KB), KB, 0, s>>>(h->w, h->hred + 1, vnext, n);
         if (tr) cudaEventRecord(tev[3], s);
         MGR_TRY_CUDA(cudaMemcpyAsync(hp, h->hcol, sizeof(double) * (j + 2), cudaMemcpyDeviceToHost, s));
         MGR_TRY_CUDA(cudaStreamSynchronize(s));
@@ -460,7 +648,7 @@ int fgmres_run(Handle* h, const mgr_matrix_t* A, const double* b, double* x,
       else
         MGR_LAUNCH k_xupdate<double><<<KGRID, KB, 0, s>>>((const double*)h->Z, n, jend, h->yv, x, n);
       // true residual in FP64
-      residual64(A->row_ptr, A->col_idx, A->val, n, A->nnz, b, x, h->r, s);
+      jacobian_product(h, A, pat, x, h->r, b, true, s);
       mdot(h, h->r, n, 1, h->r, n, h->hred, 0, s);   // ||r||^2
       MGR_TRY(read_back(hp, h->hred, s));
       beta = std::sqrt(hp[0]);
@@ -655,6 +843,7 @@ k_ls_mdot(const LsSys* __restrict__ S, const int* __restrict__ flag, const int* 
   int64_t c;
   if (!ls_block(S, flag, blk_sys, single, &s, &c)) return;
   const LsSys& d = S[s];
+  if (which == LS_VW && d.ortho != MGR_ORTHO_CGS2) return;   // a classical Gram-Schmidt pass
   double* ps = part + d.blk0 * LS_H;
   if (which == LS_VW)
     mdot_body<UPDATE>(d.V, d.n, jcur[s] + 1, d.w, d.n, ps, Hc + (int64_t)s * LS_H, c);
@@ -673,30 +862,34 @@ k_ls_mupdate(const LsSys* __restrict__ S, const int* __restrict__ flag, const in
   int64_t c;
   if (!ls_block(S, flag, blk_sys, single, &s, &c)) return;
   const LsSys& d = S[s];
+  if (d.ortho != MGR_ORTHO_CGS2) return;   // classical Gram-Schmidt only
   mupdate_body<NORM>(d.V, d.n, jcur[s] + 1, Yv + (int64_t)s * LS_H, d.w, d.n,
                      part + d.blk0 * LS_H, c);
 }
 
-// per flagged system, warp per vector i < nv (nv = j + 1, or 1 when `one`):
-// dst[s * dstride + (off_j ? j + 1 : 0) + i] (+)= the sum of its partials in
-// the single-system order -- the system's chunk partials in `part`, or (rows)
-// the one partial row part[s * LS_H ..] -- and with SQRT red[s * 4 + 1] = 1/norm
+// per flagged system, block (blockIdx.x) per vector i < nv (nv = j + 1, or 1
+// when `one`), FIN_T threads: dst[s * dstride + (off_j ? j + 1 : 0) + i] (+)=
+// the sum of its partials in the single-system order -- the system's chunk
+// partials in `part`, or (rows) the one partial row part[s * LS_H ..] -- and
+// with SQRT red[s * 4 + 1] = 1/norm.  gs: a classical Gram-Schmidt step,
+// skipped by systems that orthogonalise by modified Gram-Schmidt.
 template <bool SQRT>
-__global__ void k_ls_final(const LsSys* __restrict__ S, const int* __restrict__ flag,
-                           const int* __restrict__ jcur, const double* __restrict__ part, int rows,
-                           double* __restrict__ dst, int dstride, int off_j, int one,
-                           int accumulate, double* __restrict__ red, int single) {
+__global__ void __launch_bounds__(FIN_T)
+k_ls_final(const LsSys* __restrict__ S, const int* __restrict__ flag, const int* __restrict__ jcur,
+           const double* __restrict__ part, int rows, double* __restrict__ dst, int dstride,
+           int off_j, int one, int accumulate, double* __restrict__ red, int gs, int single) {
   const int s = single >= 0 ? single : blockIdx.y;
   if (!flag[s]) return;
   const int nv = one ? 1 : jcur[s] + 1;
-  const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int i = blockIdx.x;
   if (i >= nv) return;
   const LsSys& d = S[s];
+  if (gs && d.ortho != MGR_ORTHO_CGS2) return;
   double* h = dst + (int64_t)s * dstride + (off_j ? jcur[s] + 1 : 0);
   if (rows)
-    mdot_final_warp<SQRT>(part + (int64_t)s * LS_H, 1, nv, i, h, accumulate, red + (int64_t)s * 4 + 1);
+    mdot_final_block<SQRT>(part + (int64_t)s * LS_H, 1, nv, i, h, accumulate, red + (int64_t)s * 4 + 1);
   else
-    mdot_final_warp<SQRT>(part + d.blk0 * LS_H, d.nb, nv, i, h, accumulate, red + (int64_t)s * 4 + 1);
+    mdot_final_block<SQRT>(part + d.blk0 * LS_H, d.nb, nv, i, h, accumulate, red + (int64_t)s * 4 + 1);
 }
 
 // V_(j+1) = w * rinv (what 0), or V_0 = r * rinv (what 1)
@@ -715,6 +908,28 @@ __global__ void k_ls_scale(const LsSys* __restrict__ S, const int* __restrict__ 
     if (what == 0) d.V[(int64_t)(jcur[s] + 1) * d.n + i] = d.w[i] * f;
     else d.V[i] = d.r[i] * f;
   }
+}
+
+// Modified Gram-Schmidt step i for every flagged system that orthogonalises
+// that way and whose iteration j has i <= j + 1: grid (the largest system's
+// mgs_grid, systems); the blocks beyond a system's own mgs_grid return, the
+// rest run the single-system body with that system's grid, partial buffer,
+// counter and Hessenberg column.
+__global__ void __launch_bounds__(KB) k_ls_mgs(const LsSys* __restrict__ S, const int* __restrict__ flag,
+                                               const int* __restrict__ jcur, int i,
+                                               double* __restrict__ part, double* __restrict__ Hc,
+                                               double* __restrict__ red,
+                                               unsigned* __restrict__ tickets) {
+  const int s = blockIdx.y;
+  if (!flag[s]) return;
+  const LsSys& d = S[s];
+  if (d.ortho != MGR_ORTHO_MGS) return;
+  const int j = jcur[s];
+  if (i > j + 1) return;
+  const int G = mgs_grid(d.n);
+  if ((int)blockIdx.x >= G) return;
+  mgs_body(d.V, d.n, i, j, d.w, d.n, part + d.blk0 * LS_H, Hc + (int64_t)s * LS_H,
+           red + (int64_t)s * 4 + 1, tickets + s, G, blockIdx.x);
 }
 
 // x += sum_{i < jcur+1} y_i Z_i (jcur holds jend - 1 here), as k_xupdate
@@ -748,7 +963,11 @@ k_ls_xupdate(const LsSys* __restrict__ S, const int* __restrict__ flag, const in
 
 }  // namespace
 
-int ensure_krylov_ws(Handle* h, int m) { return ensure_krylov(h, m, h->pool.s); }
+int ensure_krylov_ws(Handle* h, int m) {
+  MGR_TRY(ensure_krylov(h, m, h->pool.s));
+  MGR_TRY_CUDA(cudaStreamSynchronize(h->pool.s));   // the counter reset, before other streams
+  return MGR_SUCCESS;
+}
 
 // flag / jcur uploads between two host synchronisations each use their own
 // pinned slot: an asynchronous copy reads its host source when it runs
@@ -776,7 +995,9 @@ int lockstep_alloc(Lockstep* L, Handle** hs, const mgr_matrix_t* A, cudaStream_t
   L->Hc = P.get<double>((int64_t)ns * LS_H);
   L->Yv = P.get<double>((int64_t)ns * LS_H);
   L->red = P.get<double>((int64_t)ns * 4);
+  L->tickets = P.get<unsigned>(ns);
   if (P.err) return P.err;
+  MGR_TRY_CUDA(cudaMemsetAsync(L->tickets, 0, sizeof(unsigned) * ns, s));
   MGR_TRY_CUDA(cudaMallocHost(&L->hpin, sizeof(double) * ((size_t)ns * LS_H + (size_t)ns * 4)));
   MGR_TRY_CUDA(cudaMallocHost(&L->ipin, sizeof(int) * 2 * (size_t)ns * LS_SLOTS));
   std::vector<int64_t> roff(ns + 1, 0);
@@ -786,6 +1007,7 @@ int lockstep_alloc(Lockstep* L, Handle** hs, const mgr_matrix_t* A, cudaStream_t
   for (int q = 0; q < ns; q++) {
     roff[q + 1] = roff[q] + hs[q]->n;
     L->nb[q] = mdot_blocks(hs[q]->n);
+    L->mgs_gmax = std::max(L->mgs_gmax, mgs_grid(hs[q]->n));
     for (int k = 0; k < L->nb[q]; k++) bsys.push_back(q);
     L->lanes[q] = spmv_lanes(A[q].nnz, A[q].n);
   }
@@ -860,34 +1082,42 @@ static void ls_spmv_all(Lockstep* L, bool res, cudaStream_t s) {
 // One FGMRES iteration of every flagged system (flag and jcur already on the
 // device), each phase one launch for all of them: v_j into the graph inputs;
 // the lockstep graph (the preconditioner application of every flagged system
-// as a conditional branch); z_j out; w = A z_j; classical Gram-Schmidt twice;
-// v_(j+1) = w / ||w||.  Every per-row, per-chunk and per-element body is the
-// one fgmres_run's kernels use, so each system gets the same bits.
-static int ls_iterate(Lockstep* L, long long graph_kernels, cudaStream_t s) {
+// as a conditional branch); z_j out; w = A z_j; Gram-Schmidt -- modified
+// (one launch per projection up to jmax + 1, jmax = the largest j of the
+// flagged systems that use it, -1 for none) and classical twice (seven
+// launches, when any flagged system uses it); v_(j+1) = w / ||w||.  Every
+// per-row, per-chunk and per-element body is the one fgmres_run's kernels
+// use, so each system gets the same bits.
+static int ls_iterate(Lockstep* L, long long graph_kernels, int jmax, bool cgs, cudaStream_t s) {
   const int ns = L->nsys;
   const int mixed = L->mixed;
   const unsigned vg = grid_for(L->nrows, KB, 152 * 16);
   const int nbk = (int)L->nblk;
-  const dim3 fin1(1, ns), finv(8, ns);   // one warp / up to 64 warps per system
+  const dim3 fin1(1, ns), finv(LS_H, ns);   // one block per vector and system
   MGR_LAUNCH k_ls_gather<<<vg, KB, 0, s>>>(L->dsys, L->flag, L->jcur, L->roff, ns, L->nrows, mixed, -1);
   MGR_TRY_CUDA(cudaGraphLaunch(L->exec, s));
   count_graph_launch(graph_kernels);
   MGR_LAUNCH k_ls_scatter<<<vg, KB, 0, s>>>(L->dsys, L->flag, L->jcur, L->roff, ns, L->nrows, mixed, -1);
   ls_spmv_all(L, false, s);
-  MGR_LAUNCH k_ls_mdot<false><<<nbk, KB, 0, s>>>(L->dsys, L->flag, L->jcur, L->blk_sys, L->part,
-                                                  nullptr, LS_VW, -1);
-  MGR_LAUNCH k_ls_final<false><<<finv, 256, 0, s>>>(L->dsys, L->flag, L->jcur, L->part, 0, L->Hc, LS_H,
-                                                    0, 0, 0, L->red, -1);   // h1
-  MGR_LAUNCH k_ls_mdot<true><<<nbk, KB, 0, s>>>(L->dsys, L->flag, L->jcur, L->blk_sys, L->part, L->Hc,
-                                                 LS_VW, -1);
-  MGR_LAUNCH k_ls_final<false><<<finv, 256, 0, s>>>(L->dsys, L->flag, L->jcur, L->part, 0, L->Yv, LS_H,
-                                                    0, 0, 0, L->red, -1);   // h2
-  MGR_LAUNCH k_ls_mupdate<true><<<nbk, KB, 0, s>>>(L->dsys, L->flag, L->jcur, L->blk_sys, L->part,
-                                                    L->Yv, -1);
-  MGR_LAUNCH k_ls_final<false><<<finv, 256, 0, s>>>(L->dsys, L->flag, L->jcur, L->Yv, 1, L->Hc, LS_H,
-                                                    0, 0, 1, L->red, -1);   // h += h2
-  MGR_LAUNCH k_ls_final<true><<<fin1, 32, 0, s>>>(L->dsys, L->flag, L->jcur, L->part, 0, L->Hc, LS_H,
-                                                  1, 1, 0, L->red, -1);     // ||w||
+  for (int i = 0; i <= jmax + 1 && jmax >= 0; i++)
+    MGR_LAUNCH k_ls_mgs<<<dim3(L->mgs_gmax, ns), KB, 0, s>>>(L->dsys, L->flag, L->jcur, i, L->part,
+                                                             L->Hc, L->red, L->tickets);
+  if (cgs) {
+    MGR_LAUNCH k_ls_mdot<false><<<nbk, KB, 0, s>>>(L->dsys, L->flag, L->jcur, L->blk_sys, L->part,
+                                                    nullptr, LS_VW, -1);
+    MGR_LAUNCH k_ls_final<false><<<finv, FIN_T, 0, s>>>(L->dsys, L->flag, L->jcur, L->part, 0, L->Hc,
+                                                        LS_H, 0, 0, 0, L->red, 1, -1);   // h1
+    MGR_LAUNCH k_ls_mdot<true><<<nbk, KB, 0, s>>>(L->dsys, L->flag, L->jcur, L->blk_sys, L->part,
+                                                   L->Hc, LS_VW, -1);
+    MGR_LAUNCH k_ls_final<false><<<finv, FIN_T, 0, s>>>(L->dsys, L->flag, L->jcur, L->part, 0, L->Yv,
+                                                        LS_H, 0, 0, 0, L->red, 1, -1);   // h2
+    MGR_LAUNCH k_ls_mupdate<true><<<nbk, KB, 0, s>>>(L->dsys, L->flag, L->jcur, L->blk_sys, L->part,
+                                                      L->Yv, -1);
+    MGR_LAUNCH k_ls_final<false><<<finv, FIN_T, 0, s>>>(L->dsys, L->flag, L->jcur, L->Yv, 1, L->Hc,
+                                                        LS_H, 0, 0, 1, L->red, 1, -1);   // h += h2
+    MGR_LAUNCH k_ls_final<true><<<fin1, FIN_T, 0, s>>>(L->dsys, L->flag, L->jcur, L->part, 0, L->Hc,
+                                                       LS_H, 1, 1, 0, L->red, 1, -1);    // ||w||
+  }
   MGR_LAUNCH k_ls_scale<<<vg, KB, 0, s>>>(L->dsys, L->flag, L->jcur, L->roff, ns, L->nrows, L->red, 0,
                                           -1);
   return MGR_SUCCESS;
@@ -900,7 +1130,9 @@ int lockstep_tune_round(Lockstep* L, cudaStream_t s) {
   MGR_TRY_CUDA(cudaMemcpyAsync(L->flag, ones.data(), sizeof(int) * L->nsys, cudaMemcpyHostToDevice, s));
   long long k = 1;
   for (long long q : L->body_kernels) k += q;
-  MGR_TRY(ls_iterate(L, k, s));
+  bool mgs_any = false, cgs_any = false;
+  for (int o : L->ortho) (o == MGR_ORTHO_MGS ? mgs_any : cgs_any) = true;
+  MGR_TRY(ls_iterate(L, k, mgs_any ? 0 : -1, cgs_any, s));
   MGR_TRY_CUDA(cudaStreamSynchronize(s));
   return MGR_SUCCESS;
 }
@@ -909,41 +1141,50 @@ int lockstep_tune_round(Lockstep* L, cudaStream_t s) {
 // fgmres_run's kernels and no readback: the unit the batch schedule
 // autotuner times for the worker schedules.  Allocates the Krylov workspace
 // for restart m on `s` if it is not there yet.
-int krylov_tune_iteration(Handle* h, const mgr_matrix_t* A, int m, cudaStream_t s) {
+int krylov_tune_iteration(Handle* h, const mgr_matrix_t* A, int m, int ortho, cudaStream_t s) {
   h->pool.s = s;
   MGR_TRY(ensure_krylov(h, m, s));
+  const int pv = jacobian_patterns_valid(h, A, s);
+  if (pv < 0) return pv;
+  const bool pat = pv == 1;
   const int64_t n = h->n;
   MGR_TRY_CUDA(cudaMemsetAsync(h->V, 0, sizeof(double) * n, s));
   if (h->opt.precision == MGR_MIXED) {
     MGR_TRY(apply_mgr_mixed_into(h, h->V, h->zout32, s));
     MGR_LAUNCH k_widen<<<grid_for(n, KB), KB, 0, s>>>(h->zout32, (float*)h->Z, h->r, n);
-    spmv64(A->row_ptr, A->col_idx, A->val, n, A->nnz, h->r, h->w, s);
+    jacobian_product(h, A, pat, h->r, h->w, nullptr, false, s);
   } else {
     MGR_TRY(apply_mgr(h, h->V, (double*)h->Z, s));
-    spmv64(A->row_ptr, A->col_idx, A->val, n, A->nnz, (double*)h->Z, h->w, s);
+    jacobian_product(h, A, pat, (double*)h->Z, h->w, nullptr, false, s);
+  }
+  if (resolve_ortho(ortho, n) == MGR_ORTHO_MGS) {
+    mgs(h, 0, h->V + n, s);
+    MGR_TRY_CUDA(cudaGetLastError());
+    return MGR_SUCCESS;
   }
   const int nb = mdot_blocks(n);
   mdot(h, h->V, n, 1, h->w, n, h->hcol, 0, s);
   MGR_LAUNCH k_mdot<true><<<nb, KB, 0, s>>>(h->V, n, 1, h->w, n, h->part, h->hcol);
-  MGR_LAUNCH k_mdot_final<false><<<1, 256, 0, s>>>(h->part, nb, 1, h->yv, 0, nullptr);
+  MGR_LAUNCH k_mdot_final<false><<<1, FIN_T, 0, s>>>(h->part, nb, 1, h->yv, 0, nullptr);
   MGR_LAUNCH k_mupdate<true><<<nb, KB, 0, s>>>(h->V, n, 1, h->yv, h->w, n, h->part);
-  MGR_LAUNCH k_mdot_final<false><<<1, 256, 0, s>>>(h->yv, 1, 1, h->hcol, 1, nullptr);
-  MGR_LAUNCH k_mdot_final<true><<<1, 32, 0, s>>>(h->part, nb, 1, h->hcol + 1, 0, h->hred + 1);
+  MGR_LAUNCH k_mdot_final<false><<<1, FIN_T, 0, s>>>(h->yv, 1, 1, h->hcol, 1, nullptr);
+  MGR_LAUNCH k_mdot_final<true><<<1, FIN_T, 0, s>>>(h->part, nb, 1, h->hcol + 1, 0, h->hred + 1);
   MGR_LAUNCH k_scale_by<<<grid_for(n, KB), KB, 0, s>>>(h->w, h->hred + 1, h->V + n, n);
   MGR_TRY_CUDA(cudaGetLastError());
   return MGR_SUCCESS;
 }
 
 static int lockstep_plan(Lockstep* L, Handle** hs, const mgr_matrix_t* A, const double* const* b,
-                         double* const* x, int m, cudaStream_t s);
+                         double* const* x, int m, int ortho, cudaStream_t s);
 
 // The lockstep graph's round over valid buffers for the autotuner: every
 // system's Krylov workspace for restart m, descriptors, j = 0 and v_0 = 0.
-int lockstep_tune_prepare(Lockstep* L, Handle** hs, const mgr_matrix_t* A, int m, cudaStream_t s) {
+int lockstep_tune_prepare(Lockstep* L, Handle** hs, const mgr_matrix_t* A, int m, int ortho,
+                          cudaStream_t s) {
   std::vector<const double*> nb(L->nsys, nullptr);
   std::vector<double*> nx(L->nsys, nullptr);
   for (int q = 0; q < L->nsys; q++) hs[q]->pool.s = s;
-  MGR_TRY(lockstep_plan(L, hs, A, nb.data(), nx.data(), m, s));
+  MGR_TRY(lockstep_plan(L, hs, A, nb.data(), nx.data(), m, ortho, s));
   for (int q = 0; q < L->nsys; q++)
     MGR_TRY_CUDA(cudaMemsetAsync(hs[q]->V, 0, sizeof(double) * hs[q]->n, s));
   MGR_TRY_CUDA(cudaMemsetAsync(L->jcur, 0, sizeof(int) * L->nsys, s));
@@ -951,13 +1192,14 @@ int lockstep_tune_prepare(Lockstep* L, Handle** hs, const mgr_matrix_t* A, int m
   return MGR_SUCCESS;
 }
 
-// Per solve: every system's Krylov workspace for restart m and the
-// descriptors that point at it.
+// Per solve: every system's Krylov workspace for restart m, its resolved
+// orthogonalisation, and the descriptors that point at them.
 static int lockstep_plan(Lockstep* L, Handle** hs, const mgr_matrix_t* A, const double* const* b,
-                         double* const* x, int m, cudaStream_t s) {
+                         double* const* x, int m, int ortho, cudaStream_t s) {
   const int ns = L->nsys;
   for (int q = 0; q < ns; q++) MGR_TRY(ensure_krylov_ws(hs[q], m));
   std::vector<LsSys> d(ns);
+  L->ortho.assign(ns, MGR_ORTHO_CGS2);
   int64_t blk0 = 0;
   for (int q = 0; q < ns; q++) {
     Handle* h = hs[q];
@@ -977,6 +1219,8 @@ static int lockstep_plan(Lockstep* L, Handle** hs, const mgr_matrix_t* A, const 
     d[q].gout = h->gout;
     d[q].blk0 = blk0;
     d[q].nb = L->nb[q];
+    d[q].ortho = L->ortho[q] = resolve_ortho(ortho, h->n);
+    if (d[q].ortho < 0) return MGR_ERR_INVALID_ARG;
     blk0 += d[q].nb;
   }
   MGR_TRY_CUDA(cudaMemcpyAsync(L->dsys, d.data(), sizeof(LsSys) * ns, cudaMemcpyHostToDevice, s));
@@ -993,7 +1237,7 @@ int fgmres_lockstep(Lockstep* L, Handle** hs, const mgr_matrix_t* A, const doubl
   if (m > 60) return MGR_ERR_INVALID_ARG;
   const int maxit = o->max_iter > 0 ? o->max_iter : 1000;
   const double rtol = o->rtol > 0 ? o->rtol : 1e-8;
-  MGR_TRY(lockstep_plan(L, hs, A, b, x, m, s));
+  MGR_TRY(lockstep_plan(L, hs, A, b, x, m, o->ortho, s));
   const bool mixed = L->mixed;
   struct Events {
     cudaEvent_t e[2] = {};
@@ -1062,8 +1306,8 @@ int fgmres_lockstep(Lockstep* L, Handle** hs, const mgr_matrix_t* A, const doubl
   MGR_LAUNCH k_ls_init<<<vg, KB, 0, s>>>(L->dsys, L->flag, L->roff, ns, L->nrows, 0);
   MGR_LAUNCH k_ls_mdot<false><<<nbk, KB, 0, s>>>(L->dsys, L->flag, L->jcur, L->blk_sys, L->part,
                                                   nullptr, LS_BB, -1);
-  MGR_LAUNCH k_ls_final<false><<<fin1, 32, 0, s>>>(L->dsys, L->flag, L->jcur, L->part, 0, L->red, 4,
-                                                   0, 1, 0, L->red, -1);
+  MGR_LAUNCH k_ls_final<false><<<fin1, FIN_T, 0, s>>>(L->dsys, L->flag, L->jcur, L->part, 0, L->red, 4,
+                                                   0, 1, 0, L->red, 0, -1);
   MGR_TRY_CUDA(cudaMemcpyAsync(hred, L->red, sizeof(double) * 4 * ns, cudaMemcpyDeviceToHost, s));
   MGR_TRY_CUDA(cudaStreamSynchronize(s));
   synced();
@@ -1101,8 +1345,8 @@ int fgmres_lockstep(Lockstep* L, Handle** hs, const mgr_matrix_t* A, const doubl
       MGR_TRY(upload());
       MGR_LAUNCH k_ls_mdot<false><<<nbk, KB, 0, s>>>(L->dsys, L->flag, L->jcur, L->blk_sys, L->part,
                                                       nullptr, LS_RR, -1);
-      MGR_LAUNCH k_ls_final<true><<<fin1, 32, 0, s>>>(L->dsys, L->flag, L->jcur, L->part, 0, L->red, 4,
-                                                      0, 1, 0, L->red, -1);
+      MGR_LAUNCH k_ls_final<true><<<fin1, FIN_T, 0, s>>>(L->dsys, L->flag, L->jcur, L->part, 0, L->red, 4,
+                                                      0, 1, 0, L->red, 0, -1);
       MGR_LAUNCH k_ls_scale<<<vg, KB, 0, s>>>(L->dsys, L->flag, L->jcur, L->roff, ns, L->nrows, L->red, 1,
                                               -1);
       for (int q = 0; q < ns; q++)
@@ -1116,7 +1360,8 @@ int fgmres_lockstep(Lockstep* L, Handle** hs, const mgr_matrix_t* A, const doubl
         }
     }
     // one iteration of every system in a cycle
-    int active = 0;
+    int active = 0, jmax = -1;
+    bool cgs = false;
     long long graph_kernels = 1;
     for (int q = 0; q < ns; q++) {
       const bool a = !st[q].done && !st[q].cycle_end;
@@ -1125,11 +1370,13 @@ int fgmres_lockstep(Lockstep* L, Handle** hs, const mgr_matrix_t* A, const doubl
       if (a) {
         active++;
         graph_kernels += L->body_kernels[q];
+        if (L->ortho[q] == MGR_ORTHO_MGS) jmax = std::max(jmax, st[q].j);
+        else cgs = true;
       }
     }
     if (active > 0) {
       MGR_TRY(upload());
-      MGR_TRY(ls_iterate(L, graph_kernels, s));
+      MGR_TRY(ls_iterate(L, graph_kernels, jmax, cgs, s));
       MGR_TRY_CUDA(cudaMemcpyAsync(hH, L->Hc, sizeof(double) * LS_H * ns, cudaMemcpyDeviceToHost, s));
       MGR_TRY_CUDA(cudaStreamSynchronize(s));
       synced();
@@ -1205,8 +1452,8 @@ int fgmres_lockstep(Lockstep* L, Handle** hs, const mgr_matrix_t* A, const doubl
     ls_spmv_all(L, true, s);
     MGR_LAUNCH k_ls_mdot<false><<<nbk, KB, 0, s>>>(L->dsys, L->flag, L->jcur, L->blk_sys, L->part,
                                                     nullptr, LS_RR, -1);
-    MGR_LAUNCH k_ls_final<false><<<fin1, 32, 0, s>>>(L->dsys, L->flag, L->jcur, L->part, 0, L->red, 4,
-                                                     0, 1, 0, L->red, -1);
+    MGR_LAUNCH k_ls_final<false><<<fin1, FIN_T, 0, s>>>(L->dsys, L->flag, L->jcur, L->part, 0, L->red, 4,
+                                                     0, 1, 0, L->red, 0, -1);
     MGR_TRY_CUDA(cudaMemcpyAsync(hred, L->red, sizeof(double) * 4 * ns, cudaMemcpyDeviceToHost, s));
     MGR_TRY_CUDA(cudaStreamSynchronize(s));
     synced();

@@ -93,6 +93,7 @@ struct Pool {
   }
   // stream-ordered release of one allocation after the work queued on fs
   void release(void* p, cudaStream_t fs) {
+    if (!p) return;
     for (auto& q : ptrs)
       if (q == p) {
         cudaFreeAsync(q, fs);
@@ -202,6 +203,28 @@ struct MgrLevel {
        *rC = nullptr, *eC = nullptr;
 };
 
+// Segmented row patterns of a CSR (the Jacobian): row i's k-th column is
+// base[i * S + (e >> 28)] + (e & 0x0FFFFFFF), e = penc[pstart[pid[i]] + k].
+struct SegPatterns {
+  uint16_t* pid = nullptr;
+  int32_t* pstart = nullptr;
+  uint32_t* penc = nullptr;
+  int32_t* base = nullptr;
+  int32_t npat = 0;
+  int32_t S = 0;
+  void release(Pool& P, cudaStream_t s);
+};
+
+// The Jacobian's patterns with the arrays they were taken from
+static constexpr int64_t JPAT_MIN_NNZ = int64_t(1) << 24;
+struct JacobianPatterns {
+  const int64_t* rp = nullptr;
+  const int32_t* ci = nullptr;
+  int64_t n = 0, nnz = 0;
+  SegPatterns ps;
+  bool checked = false;   // the last check against those arrays passed
+};
+
 struct Handle {
   mgr_options_t opt;
   int L = 0;
@@ -231,6 +254,11 @@ struct Handle {
   double* hcol = nullptr;        // device Hessenberg column scratch
   double* hred = nullptr;
   double* yv = nullptr;
+  unsigned* ticket = nullptr;    // arrival counter of the Gram-Schmidt steps (0 between launches)
+  // segmented row patterns of the Jacobian mgr_setup saw, for fgmres_solve's
+  // products (used while the solve's matrix has the same index arrays and
+  // every row still matches: checked at the start of every solve)
+  JacobianPatterns jpat;
   int* derr = nullptr;           // device error word
   // the F-relaxation AMG built concurrently with the rest of the setup owns
   // its allocations here (second stream) and reports through derr2
@@ -247,6 +275,14 @@ int build_amg(Handle* h, Pool& P, int* derr, const Csr& A, bool own_input, const
               int slot, Amg** out, cudaStream_t s);
 int to_fp32(Handle* h, cudaStream_t s);
 int build_row_patterns(Pool& P, Csr& A, cudaStream_t s);
+int build_jacobian_patterns(Handle* h, const mgr_matrix_t* A, cudaStream_t s);
+// 1 when h's segmented patterns still describe A's index arrays (one pass
+// over them; synchronises s), else 0; < 0 on a CUDA error
+int jacobian_patterns_valid(Handle* h, const mgr_matrix_t* A, cudaStream_t s);
+// y = A x (res: y = b - A x), through the patterns when `pat`, else CSR: the
+// same sums in the same order either way
+void jacobian_product(Handle* h, const mgr_matrix_t* A, bool pat, const double* x, double* y,
+                      const double* b, bool res, cudaStream_t s);
 
 // ----------------------------------------------------------------------------
 // Apply entry points (apply.cu)
@@ -290,7 +326,7 @@ struct LsSys {                     // device descriptor of one system
   double *gin = nullptr, *gout = nullptr;
   int64_t blk0 = 0;                // first chunk block of this system
   int32_t nb = 0;                  // its chunk blocks
-  int32_t pad = 0;
+  int32_t ortho = 0;               // this solve's orthogonalisation (MGR_ORTHO_MGS or _CGS2)
 };
 
 struct Lockstep {
@@ -317,14 +353,26 @@ struct Lockstep {
   std::vector<int> gcnt;
   std::vector<int> lanes, nb;       // per system: lanes per row, chunk blocks
   double *Hc = nullptr, *Yv = nullptr, *red = nullptr, *part = nullptr;
+  unsigned* tickets = nullptr;      // device [nsys]: modified Gram-Schmidt arrival counters
+  int mgs_gmax = 1;                 // the largest system's modified Gram-Schmidt grid
+  std::vector<int> ortho;           // this solve's resolved orthogonalisation per system
   double* hpin = nullptr;           // pinned host: Hc, red mirrors
   int* ipin = nullptr;              // pinned host: flag, jcur
   ~Lockstep();
 };
 int lockstep_alloc(Lockstep* L, Handle** hs, const mgr_matrix_t* A, cudaStream_t s);
+// The orthogonalisation a solve of n unknowns uses for the option value o
+// (MGR_ORTHO_AUTO: modified Gram-Schmidt from 2^21 unknowns), or -1 for an
+// unknown value.
+static constexpr int64_t MGS_AUTO_MIN_N = int64_t(1) << 21;
+inline int resolve_ortho(int o, int64_t n) {
+  if (o == MGR_ORTHO_AUTO) return n >= MGS_AUTO_MIN_N ? MGR_ORTHO_MGS : MGR_ORTHO_CGS2;
+  return (o == MGR_ORTHO_MGS || o == MGR_ORTHO_CGS2) ? o : -1;
+}
 int lockstep_tune_round(Lockstep* L, cudaStream_t s);
-int lockstep_tune_prepare(Lockstep* L, Handle** hs, const mgr_matrix_t* A, int m, cudaStream_t s);
-int krylov_tune_iteration(Handle* h, const mgr_matrix_t* A, int m, cudaStream_t s);
+int lockstep_tune_prepare(Lockstep* L, Handle** hs, const mgr_matrix_t* A, int m, int ortho,
+                          cudaStream_t s);
+int krylov_tune_iteration(Handle* h, const mgr_matrix_t* A, int m, int ortho, cudaStream_t s);
 int fgmres_lockstep(Lockstep* L, Handle** hs, const mgr_matrix_t* A, const double* const* b,
                     double* const* x, const fgmres_options_t* o, fgmres_info_t* info,
                     cudaStream_t s);

@@ -19,6 +19,7 @@ MGR_MAX_LEVELS = 8
 MGR_SUCCESS, MGR_NOT_CONVERGED = 0, 1
 MGR_FRELAX_AMG_VCYCLE, MGR_FRELAX_JACOBI = 0, 1
 MGR_FP64, MGR_MIXED = 0, 1
+MGR_ORTHO_CGS2, MGR_ORTHO_MGS, MGR_ORTHO_AUTO = 0, 1, 2
 
 # hierarchy inspection kinds (mgr_get_csr)
 Q_MGR_A, Q_MGR_W, Q_MGR_COR, Q_MGR_CORKEPT, Q_MGR_S, Q_MGR_WR, Q_MGR_BD, Q_MGR_ILU = 0, 1, 2, 3, 4, 5, 6, 7
@@ -29,7 +30,8 @@ EXPORTED = ["mgr_options_default", "fgmres_options_default", "mgr_setup", "mgr_a
             "mgr_amg_levels", "mgr_get_cf", "mgr_vcycle", "mgr_splitmix64_device",
             "mgr_launch_count", "mgr_trim_memory", "mgr_solve_host", "mgr_vcycle_noalloc", "mgr_setup_batched",
             "fgmres_solve_batched", "mgr_batch_info", "mgr_batch_handle", "mgr_destroy_batched",
-            "mgr_get_block_colors", "mgr_build_id", "mgr_memory_usage", "mgr_spmv", "mgr_host_launch_count", "mgr_row_patterns"]
+            "mgr_get_block_colors", "mgr_build_id", "mgr_memory_usage", "mgr_spmv", "mgr_host_launch_count", "mgr_row_patterns",
+            "mgr_jacobian_patterns", "mgr_jacobian_product"]
 
 
 class MgrMatrix(C.Structure):
@@ -58,7 +60,8 @@ class MgrOptions(C.Structure):
 
 
 class FgmresOptions(C.Structure):
-    _fields_ = [("restart", C.c_int32), ("max_iter", C.c_int32), ("rtol", C.c_double)]
+    _fields_ = [("restart", C.c_int32), ("max_iter", C.c_int32), ("rtol", C.c_double),
+                ("ortho", C.c_int32)]
 
 
 class FgmresInfo(C.Structure):
@@ -106,6 +109,8 @@ def lib():
             L.mgr_vcycle.argtypes = [P, C.c_int, P, P, P]
             L.mgr_splitmix64_device.argtypes = [P, P, I64, P]
             L.mgr_spmv.argtypes = [C.POINTER(MgrMatrix), P, P, P]
+            L.mgr_jacobian_patterns.argtypes = [P, C.POINTER(C.c_int)]
+            L.mgr_jacobian_product.argtypes = [P, C.POINTER(MgrMatrix), P, P, C.c_int, P]
             L.mgr_vcycle_noalloc.argtypes = [P, C.c_int, P, P, P]
             L.mgr_setup_batched.argtypes = [C.c_int, C.POINTER(MgrMatrix), C.POINTER(MgrOptions),
                                             C.c_int, P, C.POINTER(P)]
@@ -399,6 +404,21 @@ def mgr_spmv(A: DeviceMatrix, x, y, stream=None):
     return _check(lib().mgr_spmv(C.byref(A.c), _ptr(x), _ptr(y), _stream_ptr(stream)), "mgr_spmv")
 
 
+def mgr_jacobian_patterns(h):
+    """(patterns, segment starts per row) of the setup's Jacobian analysis
+    ((0, 0): the solve's products read the CSR)."""
+    seg = C.c_int(0)
+    n = _check(lib().mgr_jacobian_patterns(h, C.byref(seg)), "mgr_jacobian_patterns")
+    return n, seg.value
+
+
+def mgr_jacobian_product(h, A: DeviceMatrix, x, y, check=True, stream=None):
+    """y = A x as fgmres_solve forms it; True when the patterns were used.
+    check=False reuses the last check of A's index arrays (asynchronous)."""
+    return _check(lib().mgr_jacobian_product(h, C.byref(A.c), _ptr(x), _ptr(y), int(bool(check)),
+                                             _stream_ptr(stream)), "mgr_jacobian_product") == 1
+
+
 def mgr_splitmix64_device(inp, out, stream=None):
     return _check(lib().mgr_splitmix64_device(_ptr(inp), _ptr(out), inp.numel(),
                                               _stream_ptr(stream)), "mgr_splitmix64_device")
@@ -453,11 +473,12 @@ class Solver:
         self.stream = stream
         self.h = mgr_setup(self.A, self.opts, stream)
 
-    def solve(self, b, restart=50, max_iter=1000, rtol=1e-8, hist_cap=0):
+    def solve(self, b, restart=50, max_iter=1000, rtol=1e-8, hist_cap=0, ortho=MGR_ORTHO_AUTO):
         import torch
         x = torch.zeros_like(b)
         r = fgmres_solve(self.h, self.A, b, x,
-                         fgmres_options_default(restart=restart, max_iter=max_iter, rtol=rtol),
+                         fgmres_options_default(restart=restart, max_iter=max_iter, rtol=rtol,
+                                                ortho=ortho),
                          self.stream, hist_cap=hist_cap)
         r["x"] = x
         return r

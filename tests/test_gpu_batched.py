@@ -34,18 +34,19 @@ def members():
     return [synth.ensemble_member(i, SIDES) for i in range(NSYS)]
 
 
-def _solve_single(p, A, precision):
+def _solve_single(p, A, precision, ortho=mgr.MGR_ORTHO_AUTO):
     h = mgr.mgr_setup(A, mgr.mgr_options_default(True, precision=precision))
     b = torch.from_numpy(p.rhs).cuda()
     x = torch.zeros_like(b)
-    r = mgr.fgmres_solve(h, A, b, x)
+    r = mgr.fgmres_solve(h, A, b, x, mgr.fgmres_options_default(ortho=ortho))
     mgr.mgr_destroy(h)
     return x, r
 
 
 @pytest.mark.parametrize("precision", [mgr.MGR_MIXED, mgr.MGR_FP64])
 @pytest.mark.parametrize("workers", [0, 3, -1], ids=["autotuned", "3-workers", "lockstep"])
-def test_batched_equals_single_solves(members, precision, workers):
+@pytest.mark.parametrize("ortho", [mgr.MGR_ORTHO_MGS, mgr.MGR_ORTHO_CGS2], ids=["mgs", "cgs2"])
+def test_batched_equals_single_solves(members, precision, workers, ortho):
     As = [mgr.DeviceMatrix(p) for p in members]
     bh = mgr.mgr_setup_batched(As, mgr.mgr_options_default(True, precision=precision),
                                workers=workers)
@@ -58,17 +59,18 @@ def test_batched_equals_single_solves(members, precision, workers):
         assert info["tune_ms"] and info["workers"] in info["tune_ms"] and -1 in info["tune_ms"]
     bs = [torch.from_numpy(p.rhs).cuda() for p in members]
     xs = [torch.full_like(b, float("nan")) for b in bs]
-    st, infos = mgr.fgmres_solve_batched(bh, As, bs, xs)
+    fo = mgr.fgmres_options_default(ortho=ortho)
+    st, infos = mgr.fgmres_solve_batched(bh, As, bs, xs, fo)
     assert st == mgr.MGR_SUCCESS
     torch.cuda.synchronize()
     for i, (p, A) in enumerate(zip(members, As)):
         assert infos[i]["converged"] and infos[i]["relres"] <= 1e-8
-        x1, r1 = _solve_single(p, A, precision)
+        x1, r1 = _solve_single(p, A, precision, ortho)
         assert infos[i]["iters"] == r1["iters"], i
         assert torch.equal(xs[i], x1), i
     # a second solve on the same batch gives the same answer
     xs2 = [torch.zeros_like(b) for b in bs]
-    mgr.fgmres_solve_batched(bh, As, bs, xs2)
+    mgr.fgmres_solve_batched(bh, As, bs, xs2, fo)
     for i in range(NSYS):
         assert torch.equal(xs2[i], xs[i])
     mgr.mgr_destroy_batched(bh)
@@ -79,14 +81,16 @@ def test_lockstep_launches_per_round(members):
     (the preconditioner applications of all of them in one graph launch), so
     the host issues the same dozen-odd launches per round whatever the number
     of systems, where the systems solved one by one issue a dozen or more per
-    iteration each."""
+    iteration each (classical Gram-Schmidt, whose launches per iteration are
+    fixed)."""
     As = [mgr.DeviceMatrix(p) for p in members]
     opts = mgr.mgr_options_default(True, precision=mgr.MGR_MIXED)
+    fo = mgr.fgmres_options_default(ortho=mgr.MGR_ORTHO_CGS2)
     bs = [torch.from_numpy(p.rhs).cuda() for p in members]
     xs = [torch.zeros_like(b) for b in bs]
     bh = mgr.mgr_setup_batched(As, opts, workers=-1)
     h0, k0 = mgr.mgr_host_launch_count(), mgr.mgr_launch_count()
-    st, infos = mgr.fgmres_solve_batched(bh, As, bs, xs)
+    st, infos = mgr.fgmres_solve_batched(bh, As, bs, xs, fo)
     lock_host = mgr.mgr_host_launch_count() - h0
     lock_kernels = mgr.mgr_launch_count() - k0
     mgr.mgr_destroy_batched(bh)
@@ -96,7 +100,7 @@ def test_lockstep_launches_per_round(members):
     hs = [mgr.mgr_setup(A, opts) for A in As]
     h0, k0 = mgr.mgr_host_launch_count(), mgr.mgr_launch_count()
     for h, A, b in zip(hs, As, bs):
-        mgr.fgmres_solve(h, A, b, torch.zeros_like(b))
+        mgr.fgmres_solve(h, A, b, torch.zeros_like(b), fo)
     single_host = mgr.mgr_host_launch_count() - h0
     single_kernels = mgr.mgr_launch_count() - k0
     for h in hs:
@@ -160,3 +164,9 @@ def test_batched_argument_errors(members):
         mgr.fgmres_solve_batched(bh, As[::-1], bs[::-1], xs[::-1])
     assert e.value.code == -1
     mgr.mgr_destroy_batched(bh)
+    for workers in (1, -1):                         # an unknown orthogonalisation
+        bh = mgr.mgr_setup_batched(As, mgr.mgr_options_default(True), workers=workers)
+        with pytest.raises(mgr.MgrError) as e:
+            mgr.fgmres_solve_batched(bh, As, bs, xs, mgr.fgmres_options_default(ortho=3))
+        assert e.value.code == -1
+        mgr.mgr_destroy_batched(bh)

@@ -219,12 +219,15 @@ def test_directed_star_hierarchy_matches_oracle():
     s.close()
 
 
+@pytest.mark.parametrize("ortho", [mgr.MGR_ORTHO_MGS, mgr.MGR_ORTHO_CGS2], ids=["mgs", "cgs2"])
 @pytest.mark.parametrize("name,make", SMALL, ids=[s[0] for s in SMALL])
-def test_fgmres_matches_oracle(name, make):
+def test_fgmres_matches_oracle(name, make, ortho):
+    """Either orthogonalisation reaches the oracle's (modified Gram-Schmidt)
+    iteration count to +-2 and its solution to 1e-6."""
     p = make()
     ref = oracle.Oracle(p).fgmres(p.rhs)
     s = mgr.Solver(p)
-    r = s.solve(torch.from_numpy(p.rhs).cuda())
+    r = s.solve(torch.from_numpy(p.rhs).cuda(), ortho=ortho)
     assert r["converged"] and r["relres"] <= 1e-8
     assert abs(r["iters"] - ref["iters"]) <= 2, (r["iters"], ref["iters"])
     assert _rel(r["x"].cpu().numpy(), ref["x"]) <= 1e-6
@@ -238,6 +241,36 @@ def test_restart_path_matches_oracle():
     r = s.solve(torch.from_numpy(p.rhs).cuda(), restart=5)
     assert r["converged"] and r["restarts"] >= 1
     assert abs(r["iters"] - ref["iters"]) <= 2
+    assert _rel(r["x"].cpu().numpy(), ref["x"]) <= 1e-6
+    s.close()
+
+
+MGS_CASES = SMALL + [
+    # 3 * 49 * 49 * 33 + 2 * 48 * 48 * 32 = 385,161 unknowns: more KB-entry
+    # tiles than Gram-Schmidt blocks, so the blocks sweep several tiles in both
+    # directions and the last tile is ragged
+    ("two_phase_48x48x32", lambda: synth.two_phase(48, 48, 32, seed=6)),
+]
+
+
+@pytest.mark.parametrize("name,make", MGS_CASES, ids=[s[0] for s in MGS_CASES])
+def test_modified_gram_schmidt_matches_oracle(name, make):
+    """FGMRES with modified Gram-Schmidt (the oracle's orthogonalisation):
+    the residual history agrees step by step -- to 1e-6 of each estimate plus
+    1e-12 of ||b||, the rounding the Arnoldi recurrence accumulates relative to
+    the starting residual -- and the solution to 1e-6; a short restart takes
+    the restart path too."""
+    p = make()
+    restart = 12 if p.n < 100000 else 50
+    ref = oracle.Oracle(p).fgmres(p.rhs, restart=restart, hist_cap=1001)
+    s = mgr.Solver(p)
+    r = s.solve(torch.from_numpy(p.rhs).cuda(), restart=restart, hist_cap=1001,
+                ortho=mgr.MGR_ORTHO_MGS)
+    assert r["converged"] and r["relres"] <= 1e-8
+    assert abs(r["iters"] - ref["iters"]) <= 1, (r["iters"], ref["iters"])
+    k = min(len(r["hist"]), len(ref["hist"])) - 1
+    h_gpu, h_orc = np.asarray(r["hist"][:k]), ref["hist"][:k]
+    assert np.all(np.abs(h_gpu - h_orc) <= 1e-6 * h_orc + 1e-12), name
     assert _rel(r["x"].cpu().numpy(), ref["x"]) <= 1e-6
     s.close()
 
@@ -295,6 +328,11 @@ def test_invalid_arguments_are_rejected():
         with pytest.raises(mgr.MgrError) as e:
             mgr.mgr_setup(A, mgr.mgr_options_default(True, **bad))
         assert e.value.code == -1
+    s = mgr.Solver(p)
+    with pytest.raises(mgr.MgrError) as e:
+        s.solve(torch.zeros(p.n, dtype=torch.float64, device="cuda"), ortho=3)
+    assert e.value.code == -1
+    s.close()
 
 
 def test_memory_pool_trim_keeps_handles_valid():
@@ -348,6 +386,61 @@ def test_full_size_workload_hierarchy_and_solve():
     assert r["converged"] and abs(r["iters"] - ref["iters"]) <= 2
     assert _rel(r["x"].cpu().numpy(), ref["x"]) <= 1e-6
     s.close()
+
+
+def _mid_column(row_ptr, col, start_row):
+    """(entry, new column) of the first row from start_row with two columns at
+    least 2 apart: moving that entry's column half-way keeps the row sorted
+    and unique, a valid CSR with another structure."""
+    for r in range(start_row, len(row_ptr) - 1):
+        for k in range(int(row_ptr[r]) + 1, int(row_ptr[r + 1])):
+            if int(col[k]) - int(col[k - 1]) >= 2:
+                return k, (int(col[k]) + int(col[k - 1])) // 2
+    raise AssertionError("no row with a gap")
+
+
+def test_jacobian_patterns_product_and_solve():
+    """The 64x64x32 two-phase Jacobian (31.35M non-zeros) is analysed into
+    segmented row patterns at setup; the solve's product through them is
+    bitwise the CSR product.  When the index arrays are rewritten in place
+    after the setup (one entry moved to another column), the per-call check
+    sees it and the product reads the CSR: still bitwise the CSR product of
+    the new matrix; restoring the arrays brings the patterns back."""
+    p = synth.config(2)
+    A = mgr.DeviceMatrix(p)
+    h = mgr.mgr_setup(A, mgr.mgr_options_default(True))
+    npat, seg = mgr.mgr_jacobian_patterns(h)
+    assert 0 < npat <= 4096 and 1 <= seg <= 8, (npat, seg)
+    x = torch.from_numpy(np.random.default_rng(41).standard_normal(p.n)).cuda()
+    y_pat = torch.empty_like(x)
+    y_csr = torch.empty_like(x)
+    assert mgr.mgr_jacobian_product(h, A, x, y_pat)
+    mgr.mgr_spmv(A, x, y_csr)
+    torch.cuda.synchronize()
+    assert torch.equal(y_pat, y_csr)
+    ref = oracle.csr_spmv(p.row_ptr, p.col, p.val, x.cpu().numpy())
+    ok, nbad = _spmv_bound_ok(p, x.cpu().numpy(), y_pat.cpu().numpy(), ref)
+    assert ok, nbad
+    # the structure changed in place: one entry of a row in the middle
+    k, c = _mid_column(p.row_ptr, p.col, p.n // 2)
+    old = int(A.col_idx[k].item())
+    A.col_idx[k] = c
+    assert not mgr.mgr_jacobian_product(h, A, x, y_pat)
+    mgr.mgr_spmv(A, x, y_csr)
+    torch.cuda.synchronize()
+    assert torch.equal(y_pat, y_csr)
+    assert not mgr.mgr_jacobian_product(h, A, x, y_pat, check=False)   # the failed check holds
+    A.col_idx[k] = old
+    assert mgr.mgr_jacobian_product(h, A, x, y_pat)
+    assert mgr.mgr_jacobian_product(h, A, x, y_pat, check=False)
+    # the solve through the patterns: the oracle's iterations and solution
+    ref = oracle.Oracle(p).fgmres(p.rhs)
+    b = torch.from_numpy(p.rhs).cuda()
+    xs = torch.zeros_like(b)
+    r = mgr.fgmres_solve(h, A, b, xs)
+    assert r["converged"] and abs(r["iters"] - ref["iters"]) <= 2
+    assert _rel(xs.cpu().numpy(), ref["x"]) <= 1e-6
+    mgr.mgr_destroy(h)
 
 
 def test_large_workload_against_oracle_fingerprint():
