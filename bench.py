@@ -190,7 +190,8 @@ class ClockSampler:
 def vcycle_bytes(mgr, h, slot, value_bytes):
     """Algorithmic DRAM bytes of one V-cycle of AMG slot `slot`: every matrix
     read once per use (row pointers 8 B, column index 4 B -- or a 2-byte
-    pattern id per row where the operator has shared row patterns -- value),
+    pattern id per row where the operator has shared row patterns, and in
+    FP32 a slice offset per 32 rows instead of row pointers -- value),
     every vector read or written once per kernel (see the design notes)."""
     vb = value_bytes
     nlev = mgr.mgr_amg_levels(h, slot)
@@ -206,8 +207,12 @@ def vcycle_bytes(mgr, h, slot, value_bytes):
         _, _, nnzR = mgr.mgr_get_csr_dims(h, mgr.Q_AMG_R, slot, k)
         if mgr.mgr_row_patterns(h, slot, k) > 0:
             # shared row patterns: a 2-byte pattern id per row instead of a
-            # column index per non-zero (the pattern table stays in cache)
-            A = (n + 1) * 8 + 2 * n + nnzA * vb
+            # column index per non-zero (the pattern table stays in cache);
+            # the FP32 values sliced by 32 rows: a slice offset per 32 rows
+            # instead of a row pointer per row (the zero padding, < 1% here,
+            # is not counted)
+            rows = (n // 32 + 1) * 8 if vb == 4 else (n + 1) * 8
+            A = rows + 2 * n + nnzA * vb
         else:
             A = (n + 1) * 8 + nnzA * (4 + vb)
         total += 3 * n * vb                                   # t = dinv .* b

@@ -130,6 +130,10 @@ struct Csr {
   int32_t* pstart = nullptr;
   int32_t* poff = nullptr;
   int32_t npat = 0;
+  // FP32 values of a patterned operator sliced for the apply (SELL-32): the
+  // value k of row r at vsell[soff[r / 32] + 32 k + r % 32]; null otherwise
+  float* vsell = nullptr;
+  int64_t* soff = nullptr;
 };
 
 // ----------------------------------------------------------------------------

@@ -3349,11 +3349,60 @@ static int bf16(Pool& P, const double* a, __nv_bfloat16** b, int64_t n, cudaStre
   return MGR_SUCCESS;
 }
 
+// SELL-32 FP32 copy of a patterned operator's values (see Csr::vsell):
+// slice lengths (32 x the slice's longest row), their exclusive scan into
+// soff, then every value rounded once from FP64 into its slot, zero padding.
+__global__ void k_sell_len(const int64_t* __restrict__ rp, int64_t n, int64_t ns,
+                           int64_t* __restrict__ cnt) {
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < ns; q += (int64_t)gridDim.x * blockDim.x) {
+    int64_t m = 0;
+    for (int64_t r = q * 32; r < q * 32 + 32 && r < n; r++) m = max(m, rp[r + 1] - rp[r]);
+    cnt[q] = 32 * m;
+  }
+}
+
+__global__ void k_sell_fill(const int64_t* __restrict__ rp, const double* __restrict__ v, int64_t n,
+                            const int64_t* __restrict__ soff, float* __restrict__ vs) {
+  const int64_t npad = (n + 31) & ~int64_t(31);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < npad; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t sl = i >> 5;
+    const int64_t L = (soff[sl + 1] - soff[sl]) >> 5;
+    const int64_t len = i < n ? rp[i + 1] - rp[i] : 0;
+    const int64_t e0 = i < n ? rp[i] : 0;
+    float* o = vs + soff[sl] + (i & 31);
+    for (int64_t k = 0; k < L; k++) o[k * 32] = k < len ? (float)v[e0 + k] : 0.0f;
+  }
+}
+
+static int sell_fp32(Pool& P, Csr& A, cudaStream_t s) {
+  const int64_t n = A.nr, ns = (n + 31) / 32;
+  if (!A.pid || n <= 0) return MGR_SUCCESS;
+  Pool tmp;
+  tmp.s = s;
+  int64_t* cnt = tmp.get<int64_t>(ns);
+  A.soff = P.get<int64_t>(ns + 1);
+  if (tmp.err || P.err) {
+    tmp.free_all_async(s);
+    return tmp.err ? tmp.err : P.err;
+  }
+  MGR_LAUNCH k_sell_len<<<grid_for(ns, 256), 256, 0, s>>>(A.rp, n, ns, cnt);
+  int64_t total = 0;
+  int rc = rowptr_from_counts(cnt, A.soff, ns, &total, s, tmp);
+  tmp.free_all_async(s);
+  MGR_TRY(rc);
+  A.vsell = P.get<float>(total > 0 ? total : 1);
+  if (!A.vsell) return P.err;
+  MGR_LAUNCH k_sell_fill<<<grid_for((n + 31) & ~int64_t(31), 256), 256, 0, s>>>(A.rp, A.v, n, A.soff,
+                                                                               A.vsell);
+  return MGR_SUCCESS;
+}
+
 static int amg_to_fp32(Handle* h, Amg* g, cudaStream_t s) {
   if (!g) return MGR_SUCCESS;
   Pool& P = h->pool;
   for (auto& L : g->lev) {
     MGR_TRY(f32(P, L.A.v, &L.A.vf, L.A.nnz, s));
+    MGR_TRY(sell_fp32(P, L.A, s));
     MGR_TRY(f32(P, L.P.v, &L.P.vf, L.P.nnz, s));
     MGR_TRY(f32(P, L.R.v, &L.R.vf, L.R.nnz, s));
     MGR_TRY(f32(P, L.dinv, &L.dinvf, L.A.nr, s));
