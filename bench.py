@@ -531,18 +531,19 @@ def run_ours(args):
                              frac=byts / (ms_v * 1e-3) / 1e9 / peak)
         del vin, vx
     used, reserved = mgr.mgr_memory_usage()
-    # the FP64 Jacobian product as the solve forms it (through the setup's
-    # segmented row patterns: a value per non-zero, a pattern id and S segment
-    # starts per row), and the plain CSR product beside it
+    # the FP64 Jacobian product as the solve forms it (over the sliced copy
+    # of A the solve makes: one thread per row, one multiply-add per
+    # non-zero), the plain CSR product beside it, and the per-solve copy
     y = torch.empty_like(b)
     xin = torch.randn_like(b)
-    npat, nseg = mgr.mgr_jacobian_patterns(h)
-    via_pat = mgr.mgr_jacobian_product(h, A, xin, y, check=True)
+    tm.start()
+    sliced = mgr.mgr_jacobian_product(h, A, xin, y, refresh=True)
+    ms_copy = tm.stop()
     csr_bytes = (p.n + 1) * 8 + p.nnz * 12 + 2 * p.n * 8
-    pat_bytes = (p.n + 1) * 8 + p.nnz * 8 + p.n * (2 + 4 * nseg) + 2 * p.n * 8
+    sell_bytes = (p.n // 32 + 1) * 8 + (p.n + 1) * 8 + p.nnz * 12 + 2 * p.n * 8
     for name, fn, byts in (
-            ("jacobian_spmv_fp64", lambda: mgr.mgr_jacobian_product(h, A, xin, y, check=False),
-             pat_bytes if via_pat else csr_bytes),
+            ("jacobian_spmv_fp64", lambda: mgr.mgr_jacobian_product(h, A, xin, y, refresh=False),
+             sell_bytes if sliced else csr_bytes),
             ("jacobian_spmv_fp64_csr", lambda: mgr.mgr_spmv(A, xin, y), csr_bytes)):
         fn()
         tm.start()
@@ -550,9 +551,11 @@ def run_ours(args):
             fn()
         ms_az = tm.stop() / args.vcycles
         kernels[name] = dict(ms=ms_az, algorithmic_bytes=byts, gbs=byts / (ms_az * 1e-3) / 1e9,
-                             frac=byts / (ms_az * 1e-3) / 1e9 / peak)
-    kernels["jacobian_spmv_fp64"].update(row_patterns=npat, segments_per_row=nseg,
-                                         through_patterns=bool(via_pat))
+                             frac=byts / (ms_az * 1e-3) / 1e9 / peak,
+                             fp64_fma_floor_ms=p.nnz / 0.625e12 * 1e3)
+    kernels["jacobian_spmv_fp64"].update(sliced_copy=bool(sliced), copy_ms_per_solve=ms_copy,
+                                         fp64_floor_note="nnz multiply-adds at GB300's nominal "
+                                                         "1.25 TFLOP/s FP64")
     mgr.mgr_destroy(h)
     del y, xin
     dom = kernels["vcycle_uu_fp32"]

@@ -283,35 +283,27 @@ int mgr_vcycle(mgr_handle_t h, int slot, const double* b, double* x, void* strea
 
 /* y = A x with the FP64 CSR product that fgmres_solve applies to the Jacobian
  * at every iteration (the "w = A z_j" step of right-preconditioned GMRES,
- * Sec. 4; mgr_jacobian_product gives the pattern form of the same sums).
+ * Sec. 4; large systems use the sliced form of mgr_jacobian_product).
  * A's arrays, x and y are DEVICE arrays (n doubles each; y
  * must not overlap x); the grouping arrays of A are not read.  Asynchronous
  * on `stream`.  INVALID_ARG for a NULL or negative-size argument. */
 int mgr_spmv(const mgr_matrix_t* A, const double* x, double* y, void* stream);
 
-/* Segmented row patterns of the Jacobian, analysed by mgr_setup when A has
- * at least 2^24 non-zeros: each row's sorted columns are cut into segments
- * wherever a column lies more than 2^15 past the one before it; rows whose
- * segments hold the same offsets from their first columns share a pattern
- * (at most 4096), and a row then keeps a 2-byte pattern id and the first
- * column of each segment.  Returns the number of patterns (0: none -- the
- * solve's products read the CSR); *segments (may be NULL) = the segment starts
- * kept per row.  INVALID_ARG for a NULL handle.  Host-side query. */
-int mgr_jacobian_patterns(mgr_handle_t h, int* segments);
-
-/* y = A x as fgmres_solve(h, A, ...) forms it: through h's Jacobian patterns
- * when they describe A -- the same row_ptr / col_idx device arrays, n and nnz
- * as at mgr_setup, and every row matching its pattern -- else the CSR product
- * of mgr_spmv.  Both form every row's sum in the same order, so y is bitwise
- * mgr_spmv's.  check = 1: every row is checked first (one pass over the index
- * arrays, synchronising `stream`; fgmres_solve does the same at its start);
- * check = 0: the outcome of the last check of those arrays (at mgr_setup, by
- * a solve or by a check = 1 call) is reused and the call is asynchronous --
- * only for a caller that has not rewritten the index arrays since.  Device
- * arrays as for mgr_spmv.  Returns 1 (patterns used), 0 (CSR) or a negative
- * error (INVALID_ARG also for check other than 0 or 1). */
+/* y = A x as fgmres_solve(h, A, ...) forms it.  From 2^24 non-zeros the
+ * solve's FP64 products read a sliced (SELL-32) copy of A, rebuilt from A at
+ * the start of every solve: rows in slices of 32, a slice's entries stored
+ * entry-major, one GPU thread per row (GB300's FP64 pipe is narrow, and this
+ * form issues one multiply-add per non-zero with no cross-lane reduction).
+ * Each row's sum then runs over its entries in order, so y agrees with
+ * mgr_spmv to rounding, not bitwise.  refresh = 1 rebuilds the copy from A
+ * first (one pass over A; synchronises `stream`); refresh = 0 reuses the copy
+ * of the last solve or refresh of these same arrays -- only for a caller that
+ * has not changed A since -- and is asynchronous.  Below 2^24 non-zeros this
+ * is mgr_spmv.  Device arrays as for mgr_spmv.  Returns 1 (sliced copy read),
+ * 0 (CSR) or a negative error (INVALID_ARG also for refresh other than 0 or
+ * 1). */
 int mgr_jacobian_product(mgr_handle_t h, const mgr_matrix_t* A, const double* x, double* y,
-                         int check, void* stream);
+                         int refresh, void* stream);
 
 /* Splitmix64 (Steele, Lea, Flood 2014) as evaluated on the device, for tests
  * of the PMIS weight hash: out[i] = splitmix64(in[i]) for n values (device). */

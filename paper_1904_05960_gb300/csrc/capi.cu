@@ -199,7 +199,6 @@ int setup_one(const mgr_matrix_t* A, const mgr_options_t* o, cudaStream_t s, Han
   g_trace.mark("hierarchy");
   if (!rc && o->precision == MGR_MIXED) rc = to_fp32(h, s);
   if (!rc) rc = alloc_apply_workspace(h, s);
-  if (!rc) rc = build_jacobian_patterns(h, A, s);
   if (!rc && cudaStreamSynchronize(s) != cudaSuccess) rc = MGR_ERR_CUDA;
   g_trace.mark("fp32 copies + workspace");
   if (!rc) rc = capture_apply_graph(h);
@@ -341,30 +340,23 @@ int mgr_row_patterns(mgr_handle_t hh, int slot, int lvl) {
   return g->lev[lvl].A.pid ? g->lev[lvl].A.npat : 0;
 }
 
-int mgr_jacobian_patterns(mgr_handle_t hh, int* segments) {
-  Handle* h = reinterpret_cast<Handle*>(hh);
-  if (!h) return MGR_ERR_INVALID_ARG;
-  if (segments) *segments = h->jpat.ps.S;
-  return h->jpat.ps.npat;
-}
-
 int mgr_jacobian_product(mgr_handle_t hh, const mgr_matrix_t* A, const double* x, double* y,
-                         int check, void* stream) {
+                         int refresh, void* stream) {
   (void)cudaGetLastError();  // errors of earlier calls are not this call's
   Handle* h = reinterpret_cast<Handle*>(hh);
   if (!h || !A || A->n != h->n || A->nnz < 0 || (A->n > 0 && (!A->row_ptr || !x || !y)) ||
-      (A->nnz > 0 && (!A->col_idx || !A->val)) || (check != 0 && check != 1))
+      (A->nnz > 0 && (!A->col_idx || !A->val)) || (refresh != 0 && refresh != 1))
     return MGR_ERR_INVALID_ARG;
   const cudaStream_t s = (cudaStream_t)stream;
-  const JacobianPatterns& J = h->jpat;
-  int pv = 0;
-  if (check) pv = jacobian_patterns_valid(h, A, s);
-  else pv = J.checked && J.ps.npat > 0 && J.rp == A->row_ptr && J.ci == A->col_idx &&
+  const JacobianSell& J = h->jsell;
+  int sv = 0;
+  if (refresh) sv = jacobian_sell_refresh(h, A, s);
+  else sv = J.valid && J.rp == A->row_ptr && J.ci == A->col_idx && J.val == A->val &&
             J.n == A->n && J.nnz == A->nnz;
-  if (pv < 0) return pv;
-  jacobian_product(h, A, pv == 1, x, y, nullptr, false, s);
+  if (sv < 0) return sv;
+  jacobian_product(h, A, sv == 1, x, y, nullptr, false, s);
   MGR_TRY_CUDA(cudaGetLastError());
-  return pv;
+  return sv;
 }
 
 int64_t mgr_get_cf(mgr_handle_t hh, int slot, int lvl, int8_t* out) {

@@ -371,80 +371,41 @@ static void mdot(Handle* h, const double* V, int64_t ld, int nv, const double* w
 }
 
 // ---------------------------------------------------------------------------
-// Jacobian product through segmented row patterns
+// Jacobian product over the sliced copy
 // ---------------------------------------------------------------------------
-// Row i's k-th column is base[i * S + (e >> 28)] + (e & 0x0FFFFFFF), e = its
-// pattern's k-th encoding: per non-zero only the value is streamed (the
-// pattern table is small and stays in cache; a 2-byte id and S segment starts
-// per row).  G lanes per row, one accumulator per lane, loads unrolled by
-// four: the CSR product's loop, so every row's sum is formed in the same order
-// and the results are bitwise those of the CSR product.
-template <class I, int G, bool RES>
+// One thread per row, entry k of row i at soff[i / 32] + 32 k + i % 32: one
+// multiply-add per non-zero, summed over k in order (row lengths from the CSR
+// row pointers).  RES: y = b - A x.
+template <bool RES>
 __global__ void __launch_bounds__(256)
-k_spmv_seg(const int64_t* __restrict__ rp, const uint16_t* __restrict__ pid,
-           const int32_t* __restrict__ pstart, const uint32_t* __restrict__ penc,
-           const int32_t* __restrict__ base, int S, const double* __restrict__ val, I nr,
-           const double* __restrict__ x, double* __restrict__ y, const double* __restrict__ b) {
-  const I gid = (I)blockIdx.x * blockDim.x + threadIdx.x;
-  const int lane = threadIdx.x & (G - 1);
-  const I stride = ((I)gridDim.x * blockDim.x) / G;
-  const unsigned gmask = (G == 32) ? FULL : (((1u << G) - 1u) << ((threadIdx.x & 31) & ~(G - 1)));
-  for (I i = gid / G; i < nr; i += stride) {
-    const I e0 = (I)rp[i], e1 = (I)rp[i + 1];
-    const uint32_t* pe = penc + pstart[pid[i]];
-    const int32_t* bi = base + (int64_t)i * S;
-    double acc = 0;
-    I k = e0 + lane;
+k_spmv_sell64(const int64_t* __restrict__ soff, const int64_t* __restrict__ rp,
+              const int32_t* __restrict__ sci, const double* __restrict__ sval, int64_t n,
+              const double* __restrict__ x, double* __restrict__ y, const double* __restrict__ b) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t o = soff[i >> 5] + (i & 31);
+    const int len = (int)(rp[i + 1] - rp[i]);
+    double acc = 0.0;
 #pragma unroll 4
-    for (; k < e1; k += G) {
-      const uint32_t e = __ldg(pe + (k - e0));
-      acc += val[k] * __ldg(x + (__ldg(bi + (e >> 28)) + (int32_t)(e & 0x0FFFFFFFu)));
-    }
-#pragma unroll
-    for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(gmask, acc, o, G);
-    if (lane == 0) y[i] = RES ? b[i] - acc : acc;
+    for (int k = 0; k < len; k++) acc += sval[o + (int64_t)k * 32] * __ldg(x + sci[o + (int64_t)k * 32]);
+    y[i] = RES ? b[i] - acc : acc;
   }
 }
 
-template <class I, bool RES>
-static void spmv_seg_launch(const SegPatterns& P, const int64_t* rp, const double* val, int64_t nr,
-                            int64_t nnz, const double* x, double* y, const double* b,
-                            cudaStream_t s) {
-  const int G = spmv_lanes(nnz, nr);
-  const unsigned grid = (unsigned)std::min<int64_t>((nr * G + 255) / 256, 152LL * 64);
-#define MGR_SEG_CASE(g)                                                                          \
-  case g:                                                                                        \
-    MGR_LAUNCH k_spmv_seg<I, g, RES><<<grid, 256, 0, s>>>(rp, P.pid, P.pstart, P.penc, P.base,   \
-                                                          P.S, val, (I)nr, x, y, b);             \
-    break;
-  switch (G) {
-    MGR_SEG_CASE(1)
-    MGR_SEG_CASE(2)
-    MGR_SEG_CASE(4)
-    MGR_SEG_CASE(8)
-    MGR_SEG_CASE(16)
-    default: MGR_SEG_CASE(32)
-  }
-#undef MGR_SEG_CASE
-}
-
-void jacobian_product(Handle* h, const mgr_matrix_t* A, bool pat, const double* x, double* y,
+void jacobian_product(Handle* h, const mgr_matrix_t* A, bool sell, const double* x, double* y,
                       const double* b, bool res, cudaStream_t s) {
   const int64_t n = A->n, nnz = A->nnz;
-  if (!pat || n <= 0) {
+  if (!sell || n <= 0) {
     if (res) residual64(A->row_ptr, A->col_idx, A->val, n, nnz, b, x, y, s);
     else spmv64(A->row_ptr, A->col_idx, A->val, n, nnz, x, y, s);
     return;
   }
-  const SegPatterns& P = h->jpat.ps;
-  // 32-bit offsets on the same condition as the CSR product
-  if (nnz + 64 < INT32_MAX && n * 16 + 152LL * 64 * 256 < INT32_MAX) {
-    if (res) spmv_seg_launch<int, true>(P, A->row_ptr, A->val, n, nnz, x, y, b, s);
-    else spmv_seg_launch<int, false>(P, A->row_ptr, A->val, n, nnz, x, y, b, s);
-  } else {
-    if (res) spmv_seg_launch<int64_t, true>(P, A->row_ptr, A->val, n, nnz, x, y, b, s);
-    else spmv_seg_launch<int64_t, false>(P, A->row_ptr, A->val, n, nnz, x, y, b, s);
-  }
+  const JacobianSell& J = h->jsell;
+  const unsigned grid = (unsigned)std::min<int64_t>((n + 255) / 256, 152LL * 64);
+  if (res)
+    MGR_LAUNCH k_spmv_sell64<true><<<grid, 256, 0, s>>>(J.soff, A->row_ptr, J.sci, J.sval, n, x, y, b);
+  else
+    MGR_LAUNCH k_spmv_sell64<false><<<grid, 256, 0, s>>>(J.soff, A->row_ptr, J.sci, J.sval, n, x, y, b);
 }
 
 // Modified Gram-Schmidt of w against V_0..V_j: hcol[0..j] = the projections,
@@ -503,11 +464,10 @@ int fgmres_run(Handle* h, const mgr_matrix_t* A, const double* b, double* x,
   const int maxit = o->max_iter > 0 ? o->max_iter : 1000;
   const double rtol = o->rtol > 0 ? o->rtol : 1e-8;
   MGR_TRY(ensure_krylov(h, m, s));
-  // the Jacobian products go through the setup's row patterns when they still
-  // describe A (checked here, once per solve), else through the CSR
-  const int pv = jacobian_patterns_valid(h, A, s);
-  if (pv < 0) return pv;
-  const bool pat = pv == 1;
+  // large Jacobians: the products read a sliced copy of A made here
+  const int sv = jacobian_sell_refresh(h, A, s);
+  if (sv < 0) return sv;
+  const bool pat = sv == 1;
   const bool mixed = h->opt.precision == MGR_MIXED;
   // pinned host mirror for the per-iteration readbacks, leased per host thread
   double* hp = nullptr;
@@ -806,6 +766,7 @@ k_ls_spmv(const LsSys* __restrict__ S, const int* __restrict__ flag, const int* 
     }
     if (!flag[s]) continue;
     const LsSys& d = S[s];
+    if (d.sval) continue;   // its product reads the sliced copy (k_ls_spmv_sell)
     const double* x = RES ? d.x : (mixed ? d.r : (const double*)d.Z + (int64_t)jcur[s] * d.n);
     const int64_t e0 = d.rp[i], e1 = d.rp[i + 1];
     double acc = 0.0;
@@ -819,6 +780,30 @@ k_ls_spmv(const LsSys* __restrict__ S, const int* __restrict__ flag, const int* 
       if (RES) d.r[i] = d.b[i] - acc;
       else d.w[i] = acc;
     }
+  }
+}
+
+// The product of every flagged system with a sliced copy, one thread per row
+// over all systems' rows: k_spmv_sell64's per-row loop.
+template <bool RES>
+__global__ void __launch_bounds__(256)
+k_ls_spmv_sell(const LsSys* __restrict__ S, const int* __restrict__ flag, const int* __restrict__ jcur,
+               const int64_t* __restrict__ roff, int nsys, int64_t nrows, int mixed) {
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < nrows;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    const int s = ls_sys_of(roff, nsys, g);
+    if (!flag[s]) continue;
+    const LsSys& d = S[s];
+    if (!d.sval) continue;
+    const int64_t i = g - roff[s];
+    const double* x = RES ? d.x : (mixed ? d.r : (const double*)d.Z + (int64_t)jcur[s] * d.n);
+    const int64_t o = d.soff[i >> 5] + (i & 31);
+    const int len = (int)(d.rp[i + 1] - d.rp[i]);
+    double acc = 0.0;
+#pragma unroll 4
+    for (int k = 0; k < len; k++) acc += d.sval[o + (int64_t)k * 32] * __ldg(x + d.sci[o + (int64_t)k * 32]);
+    if (RES) d.r[i] = d.b[i] - acc;
+    else d.w[i] = acc;
   }
 }
 
@@ -1053,6 +1038,15 @@ int lockstep_alloc(Lockstep* L, Handle** hs, const mgr_matrix_t* A, cudaStream_t
 // lanes-per-row group.  RES: r = b - A x; else w = A z_j.
 static void ls_spmv_all(Lockstep* L, bool res, cudaStream_t s) {
   const int mixed = L->mixed;
+  if (L->any_sell) {
+    const unsigned vg = grid_for(L->nrows, 256, 152 * 64);
+    if (res)
+      MGR_LAUNCH k_ls_spmv_sell<true><<<vg, 256, 0, s>>>(L->dsys, L->flag, L->jcur, L->roff, L->nsys,
+                                                         L->nrows, mixed);
+    else
+      MGR_LAUNCH k_ls_spmv_sell<false><<<vg, 256, 0, s>>>(L->dsys, L->flag, L->jcur, L->roff, L->nsys,
+                                                          L->nrows, mixed);
+  }
   for (size_t gi = 0; gi < L->gl.size(); gi++) {
     const int G = L->gl[gi];
     const unsigned grid = (unsigned)std::min<int64_t>((L->grows[gi] * G + 255) / 256, 152LL * 64);
@@ -1144,9 +1138,9 @@ int lockstep_tune_round(Lockstep* L, cudaStream_t s) {
 int krylov_tune_iteration(Handle* h, const mgr_matrix_t* A, int m, int ortho, cudaStream_t s) {
   h->pool.s = s;
   MGR_TRY(ensure_krylov(h, m, s));
-  const int pv = jacobian_patterns_valid(h, A, s);
-  if (pv < 0) return pv;
-  const bool pat = pv == 1;
+  const int sv = jacobian_sell_refresh(h, A, s);
+  if (sv < 0) return sv;
+  const bool pat = sv == 1;
   const int64_t n = h->n;
   MGR_TRY_CUDA(cudaMemsetAsync(h->V, 0, sizeof(double) * n, s));
   if (h->opt.precision == MGR_MIXED) {
@@ -1200,6 +1194,7 @@ static int lockstep_plan(Lockstep* L, Handle** hs, const mgr_matrix_t* A, const 
   for (int q = 0; q < ns; q++) MGR_TRY(ensure_krylov_ws(hs[q], m));
   std::vector<LsSys> d(ns);
   L->ortho.assign(ns, MGR_ORTHO_CGS2);
+  L->any_sell = false;
   int64_t blk0 = 0;
   for (int q = 0; q < ns; q++) {
     Handle* h = hs[q];
@@ -1221,6 +1216,16 @@ static int lockstep_plan(Lockstep* L, Handle** hs, const mgr_matrix_t* A, const 
     d[q].nb = L->nb[q];
     d[q].ortho = L->ortho[q] = resolve_ortho(ortho, h->n);
     if (d[q].ortho < 0) return MGR_ERR_INVALID_ARG;
+    // large systems: the products read a sliced copy, as in fgmres_run (the
+    // autotuner's plan has no right-hand sides and needs none)
+    const int sv = jacobian_sell_refresh(h, &A[q], s);
+    if (sv < 0) return sv;
+    if (sv == 1) {
+      d[q].soff = h->jsell.soff;
+      d[q].sci = h->jsell.sci;
+      d[q].sval = h->jsell.sval;
+      L->any_sell = true;
+    }
     blk0 += d[q].nb;
   }
   MGR_TRY_CUDA(cudaMemcpyAsync(L->dsys, d.data(), sizeof(LsSys) * ns, cudaMemcpyHostToDevice, s));

@@ -207,26 +207,21 @@ struct MgrLevel {
        *rC = nullptr, *eC = nullptr;
 };
 
-// Segmented row patterns of a CSR (the Jacobian): row i's k-th column is
-// base[i * S + (e >> 28)] + (e & 0x0FFFFFFF), e = penc[pstart[pid[i]] + k].
-struct SegPatterns {
-  uint16_t* pid = nullptr;
-  int32_t* pstart = nullptr;
-  uint32_t* penc = nullptr;
-  int32_t* base = nullptr;
-  int32_t npat = 0;
-  int32_t S = 0;
-  void release(Pool& P, cudaStream_t s);
-};
-
-// The Jacobian's patterns with the arrays they were taken from
-static constexpr int64_t JPAT_MIN_NNZ = int64_t(1) << 24;
-struct JacobianPatterns {
+// Sliced (SELL-32) copy of the Jacobian for the FP64 products of FGMRES:
+// entry k of row r at soff[r / 32] + 32 k + r % 32 of sci / sval (padded with
+// column r and value 0); row lengths from the CSR row pointers.
+static constexpr int64_t JSELL_MIN_NNZ = int64_t(1) << 24;
+struct JacobianSell {
+  int64_t* soff = nullptr;
+  int32_t* sci = nullptr;
+  double* sval = nullptr;
+  int64_t ns_cap = 0, cap = 0;
+  // the matrix the copy was made from, and whether it is current
   const int64_t* rp = nullptr;
   const int32_t* ci = nullptr;
+  const double* val = nullptr;
   int64_t n = 0, nnz = 0;
-  SegPatterns ps;
-  bool checked = false;   // the last check against those arrays passed
+  bool valid = false;
 };
 
 struct Handle {
@@ -259,10 +254,9 @@ struct Handle {
   double* hred = nullptr;
   double* yv = nullptr;
   unsigned* ticket = nullptr;    // arrival counter of the Gram-Schmidt steps (0 between launches)
-  // segmented row patterns of the Jacobian mgr_setup saw, for fgmres_solve's
-  // products (used while the solve's matrix has the same index arrays and
-  // every row still matches: checked at the start of every solve)
-  JacobianPatterns jpat;
+  // sliced copy of the Jacobian for fgmres_solve's products (from 2^24
+  // non-zeros), rebuilt from the solve's matrix at the start of every solve
+  JacobianSell jsell;
   int* derr = nullptr;           // device error word
   // the F-relaxation AMG built concurrently with the rest of the setup owns
   // its allocations here (second stream) and reports through derr2
@@ -279,13 +273,11 @@ int build_amg(Handle* h, Pool& P, int* derr, const Csr& A, bool own_input, const
               int slot, Amg** out, cudaStream_t s);
 int to_fp32(Handle* h, cudaStream_t s);
 int build_row_patterns(Pool& P, Csr& A, cudaStream_t s);
-int build_jacobian_patterns(Handle* h, const mgr_matrix_t* A, cudaStream_t s);
-// 1 when h's segmented patterns still describe A's index arrays (one pass
-// over them; synchronises s), else 0; < 0 on a CUDA error
-int jacobian_patterns_valid(Handle* h, const mgr_matrix_t* A, cudaStream_t s);
-// y = A x (res: y = b - A x), through the patterns when `pat`, else CSR: the
-// same sums in the same order either way
-void jacobian_product(Handle* h, const mgr_matrix_t* A, bool pat, const double* x, double* y,
+// (Re)build h's sliced copy of A (nnz >= JSELL_MIN_NNZ; synchronises s):
+// 1 when built, 0 when A is below the size, < 0 on an error
+int jacobian_sell_refresh(Handle* h, const mgr_matrix_t* A, cudaStream_t s);
+// y = A x (res: y = b - A x), over h's sliced copy when `sell`, else the CSR
+void jacobian_product(Handle* h, const mgr_matrix_t* A, bool sell, const double* x, double* y,
                       const double* b, bool res, cudaStream_t s);
 
 // ----------------------------------------------------------------------------
@@ -331,6 +323,9 @@ struct LsSys {                     // device descriptor of one system
   int64_t blk0 = 0;                // first chunk block of this system
   int32_t nb = 0;                  // its chunk blocks
   int32_t ortho = 0;               // this solve's orthogonalisation (MGR_ORTHO_MGS or _CGS2)
+  const int64_t* soff = nullptr;   // sliced copy of A (null: the products read the CSR)
+  const int32_t* sci = nullptr;
+  const double* sval = nullptr;
 };
 
 struct Lockstep {
@@ -360,6 +355,7 @@ struct Lockstep {
   unsigned* tickets = nullptr;      // device [nsys]: modified Gram-Schmidt arrival counters
   int mgs_gmax = 1;                 // the largest system's modified Gram-Schmidt grid
   std::vector<int> ortho;           // this solve's resolved orthogonalisation per system
+  bool any_sell = false;            // some system's products read its sliced copy
   double* hpin = nullptr;           // pinned host: Hc, red mirrors
   int* ipin = nullptr;              // pinned host: flag, jcur
   ~Lockstep();

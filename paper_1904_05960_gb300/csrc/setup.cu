@@ -2274,253 +2274,6 @@ int build_row_patterns(Pool& P, Csr& A, cudaStream_t s) {
   return MGR_SUCCESS;
 }
 
-// ============================================================================
-// Segmented row patterns (the Jacobian)
-// ============================================================================
-// The Jacobian's rows mix displacement and cell columns whose offsets from the
-// row change from row to row, so the row-relative patterns above do not
-// repeat.  Instead each row's sorted columns are cut into segments wherever a
-// column lies more than SEG_GAP past the one before it; an entry is encoded as
-// (segment << 28) | (column - the segment's first column), and a row keeps
-// the first column of each of its segments (S per row, S = the largest
-// segment count).  On a structured mesh the segments are the stencil's mesh
-// planes of each unknown block, and a few hundred encoding sequences cover all
-// rows.  Same detection as above (hash, insert, number, fill, verify), with
-// the segment starts written by the verify pass.
-static constexpr int SEG_MAX = 8;
-static constexpr int64_t SEG_GAP = 1 << 15;
-static constexpr uint32_t SEG_OFF_MASK = (1u << 28) - 1u;
-
-// Running state of one row's segmentation across its 32-entry chunks.
-struct SegRun {
-  int nseg = 0;       // segments started in the chunks before
-  int32_t base = 0;   // first column of the last of them
-};
-
-// Encoding of entry k0 + lane of a row with entries [e0, e1); every lane of
-// the warp calls it with the same k0.  Sets `col`, the entry's segment and
-// whether it starts one; clears `ok` when the entry does not fit the encoding.
-__device__ __forceinline__ uint32_t seg_enc(const int32_t* __restrict__ ci, int64_t e0, int64_t e1,
-                                            int64_t k0, int lane, SegRun& run, bool& ok,
-                                            bool& starts, int32_t& col, int& seg) {
-  const int64_t k = k0 + lane;
-  const bool valid = k < e1;
-  col = valid ? ci[k] : 0;
-  const int32_t prev = (valid && k > e0) ? ci[k - 1] : 0;
-  starts = valid && (k == e0 || (int64_t)col - prev > SEG_GAP);
-  const unsigned mask = __ballot_sync(FULL, starts);
-  const unsigned upto = mask & (0xFFFFFFFFu >> (31 - lane));   // lanes 0..lane
-  const int32_t own = __shfl_sync(FULL, col, upto ? 31 - __clz(upto) : 0);
-  const int32_t last = __shfl_sync(FULL, col, mask ? 31 - __clz(mask) : 0);
-  const int32_t base = upto ? own : run.base;
-  seg = run.nseg + __popc(upto) - 1;
-  run.base = mask ? last : run.base;
-  run.nseg += __popc(mask);
-  const int64_t off = (int64_t)col - base;
-  if (valid && (off > (int64_t)SEG_OFF_MASK || seg >= SEG_MAX)) ok = false;
-  return ((uint32_t)seg << 28) | (uint32_t)(off & SEG_OFF_MASK);
-}
-
-// warp per row: hash[i] of its encodings; flags[0] = 1 if a row does not fit
-// the encoding, flags[3] = the largest segment count
-__global__ void k_seg_hash(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci, int64_t n,
-                           unsigned long long* __restrict__ hash, int* __restrict__ flags) {
-  const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
-  for (int64_t i = (int64_t)blockIdx.x * wpb + (threadIdx.x >> 5); i < n; i += (int64_t)gridDim.x * wpb) {
-    const int64_t e0 = rp[i], e1 = rp[i + 1];
-    uint64_t acc = 0;
-    SegRun run;
-    bool ok = true;
-    for (int64_t k0 = e0; k0 < e1; k0 += 32) {
-      bool starts;
-      int32_t col;
-      int seg;
-      const uint32_t e = seg_enc(ci, e0, e1, k0, lane, run, ok, starts, col, seg);
-      if (k0 + lane < e1) acc ^= pat_mix((uint64_t)e | ((uint64_t)(k0 + lane - e0) << 32));
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc ^= __shfl_xor_sync(FULL, acc, o);
-    const bool bad = __any_sync(FULL, !ok);
-    if (lane == 0) {
-      const uint64_t h = pat_mix(acc + (uint64_t)(e1 - e0) * 0x9E3779B97F4A7C15ull);
-      hash[i] = h ? h : 1ull;   // 0 marks an empty slot
-      if (bad) atomicExch(flags, 1);
-      if (run.nseg > 0) atomicMax(flags + 3, run.nseg);
-    }
-  }
-}
-
-// warp per occupied slot: its representative's encodings
-__global__ void k_seg_fill(const unsigned long long* __restrict__ keys, const int64_t* __restrict__ rep,
-                           const int32_t* __restrict__ slot2pid, const int64_t* __restrict__ rp,
-                           const int32_t* __restrict__ ci, const int32_t* __restrict__ pstart,
-                           uint32_t* __restrict__ penc) {
-  const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
-  for (int sl = blockIdx.x * wpb + (threadIdx.x >> 5); sl < PAT_SLOTS; sl += gridDim.x * wpb) {
-    if (keys[sl] == 0ull) continue;
-    const int p = slot2pid[sl];
-    const int64_t r = rep[sl], e0 = rp[r], e1 = rp[r + 1];
-    SegRun run;
-    bool ok = true;
-    for (int64_t k0 = e0; k0 < e1; k0 += 32) {
-      bool starts;
-      int32_t col;
-      int seg;
-      const uint32_t e = seg_enc(ci, e0, e1, k0, lane, run, ok, starts, col, seg);
-      if (k0 + lane < e1) penc[pstart[p] + (k0 + lane - e0)] = e;
-    }
-  }
-}
-
-// warp per row: the row against its pattern (from the hash table: slot_of,
-// or stored: pid with slot_of null); write pid[i] and the segment starts when
-// `write`, else compare the stored ones too.  bad[0] = 1 on any mismatch.
-__global__ void k_seg_verify(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci, int64_t n,
-                             const int32_t* __restrict__ slot_of, const int32_t* __restrict__ slot2pid,
-                             const int32_t* __restrict__ pstart, const uint32_t* __restrict__ penc,
-                             int npat, uint16_t* __restrict__ pid, int32_t* __restrict__ base,
-                             int S, int write, int* __restrict__ bad) {
-  const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
-  for (int64_t i = (int64_t)blockIdx.x * wpb + (threadIdx.x >> 5); i < n; i += (int64_t)gridDim.x * wpb) {
-    const int p = write ? slot2pid[slot_of[i]] : (int)pid[i];
-    const int64_t e0 = rp[i], e1 = rp[i + 1];
-    bool ok = p >= 0 && p < npat && e1 >= e0 && (int64_t)(pstart[p + 1] - pstart[p]) == e1 - e0;
-    SegRun run;
-    if (ok)
-      for (int64_t k0 = e0; k0 < e1; k0 += 32) {
-        bool starts;
-        int32_t col;
-        int seg;
-        const uint32_t e = seg_enc(ci, e0, e1, k0, lane, run, ok, starts, col, seg);
-        if (k0 + lane < e1) {
-          if (e != penc[pstart[p] + (k0 + lane - e0)]) ok = false;
-          if (starts) {
-            if (seg >= S) ok = false;
-            else if (write) base[i * S + seg] = col;
-            else if (base[i * S + seg] != col) ok = false;
-          }
-        }
-      }
-    if (__any_sync(FULL, !ok) && lane == 0) atomicExch(bad, 1);
-    if (write && lane == 0) pid[i] = (uint16_t)(p >= 0 ? p : 0);
-  }
-}
-
-void SegPatterns::release(Pool& P, cudaStream_t s) {
-  P.release(pid, s);
-  P.release(pstart, s);
-  P.release(penc, s);
-  P.release(base, s);
-  *this = SegPatterns();
-}
-
-// The segmented patterns of the n-row CSR (rp, ci) into out (from P), or none
-// (out.npat = 0) when the rows do not share few enough of them.
-static int build_seg_patterns(Pool& P, const int64_t* rp, const int32_t* ci, int64_t n,
-                              SegPatterns& out, cudaStream_t s) {
-  out = SegPatterns();
-  if (n <= 0) return MGR_SUCCESS;
-  Pool tmp;
-  tmp.s = s;
-  unsigned long long* hash = tmp.get<unsigned long long>(n);
-  unsigned long long* keys = tmp.get<unsigned long long>(PAT_SLOTS);
-  int64_t* rep = tmp.get<int64_t>(PAT_SLOTS);
-  int32_t* slot_of = tmp.get<int32_t>(n);
-  int32_t* slot2pid = tmp.get<int32_t>(PAT_SLOTS);
-  int32_t* plen = tmp.get<int32_t>(PAT_MAX);
-  int* flags = tmp.get<int>(4);   // misfit or overflow, npat, bad, segments
-  if (tmp.err) {
-    tmp.free_all_async(s);
-    return tmp.err;
-  }
-  MGR_TRY_CUDA(cudaMemsetAsync(keys, 0, sizeof(unsigned long long) * PAT_SLOTS, s));
-  MGR_TRY_CUDA(cudaMemsetAsync(flags, 0, sizeof(int) * 4, s));
-  MGR_LAUNCH k_seg_hash<<<grid_for(n, 8, 152 * 16), 256, 0, s>>>(rp, ci, n, hash, flags);
-  MGR_LAUNCH k_pat_insert<<<grid_for(n, 256, 152 * 16), 256, 0, s>>>(hash, n, keys, rep, slot_of, flags);
-  MGR_LAUNCH k_pat_number<<<1, 1024, 0, s>>>(keys, rep, rp, slot2pid, plen, flags + 1);
-  int hf[4] = {0, 0, 0, 0};
-  MGR_TRY_CUDA(cudaMemcpyAsync(hf, flags, sizeof(int) * 4, cudaMemcpyDeviceToHost, s));
-  MGR_TRY_CUDA(cudaStreamSynchronize(s));
-  const int npat = hf[1], S = hf[3];
-  if (g_trace.on)
-    fprintf(stderr, "mgr_trace segmented patterns: rows %lld, %d patterns, %d segments, misfit %d\n",
-            (long long)n, npat, S, hf[0]);
-  if (hf[0] || npat <= 0 || npat > PAT_MAX || S <= 0 || S > SEG_MAX) {   // plain CSR
-    tmp.free_all_async(s);
-    return MGR_SUCCESS;
-  }
-  std::vector<int32_t> len(npat), start(npat + 1, 0);
-  MGR_TRY_CUDA(cudaMemcpyAsync(len.data(), plen, sizeof(int32_t) * npat, cudaMemcpyDeviceToHost, s));
-  MGR_TRY_CUDA(cudaStreamSynchronize(s));
-  for (int q = 0; q < npat; q++) start[q + 1] = start[q] + len[q];
-  SegPatterns ps;
-  ps.pstart = P.get<int32_t>(npat + 1);
-  ps.penc = P.get<uint32_t>(start[npat] > 0 ? start[npat] : 1);
-  ps.pid = P.get<uint16_t>(n);
-  ps.base = P.get<int32_t>(n * S);
-  if (P.err) {
-    tmp.free_all_async(s);
-    ps.release(P, s);
-    return P.err;
-  }
-  MGR_TRY_CUDA(cudaMemcpyAsync(ps.pstart, start.data(), sizeof(int32_t) * (npat + 1),
-                               cudaMemcpyHostToDevice, s));
-  MGR_LAUNCH k_seg_fill<<<grid_for((int64_t)PAT_SLOTS * 32, 256, 152 * 16), 256, 0, s>>>(
-      keys, rep, slot2pid, rp, ci, ps.pstart, ps.penc);
-  MGR_LAUNCH k_seg_verify<<<grid_for(n, 8, 152 * 16), 256, 0, s>>>(
-      rp, ci, n, slot_of, slot2pid, ps.pstart, ps.penc, npat, ps.pid, ps.base, S, 1, flags + 2);
-  MGR_TRY_CUDA(cudaMemcpyAsync(hf + 2, flags + 2, sizeof(int), cudaMemcpyDeviceToHost, s));
-  MGR_TRY_CUDA(cudaStreamSynchronize(s));   // `start` outlives its copy
-  tmp.free_all_async(s);
-  if (hf[2]) {   // a hash collision: keep plain CSR
-    ps.release(P, s);
-    return MGR_SUCCESS;
-  }
-  ps.npat = npat;
-  ps.S = S;
-  out = ps;
-  return MGR_SUCCESS;
-}
-
-// The Jacobian's segmented patterns, kept with the (row_ptr, col_idx, n, nnz)
-// they describe; nothing for small matrices (the one-off analysis would cost
-// more than the products it shortens) or 64-bit offsets.
-int build_jacobian_patterns(Handle* h, const mgr_matrix_t* A, cudaStream_t s) {
-  h->jpat = JacobianPatterns();
-  if (A->nnz < JPAT_MIN_NNZ || A->nnz + 64 >= INT32_MAX) return MGR_SUCCESS;
-  MGR_TRY(build_seg_patterns(h->pool, A->row_ptr, A->col_idx, A->n, h->jpat.ps, s));
-  if (h->jpat.ps.npat == 0) return MGR_SUCCESS;
-  h->jpat.rp = A->row_ptr;
-  h->jpat.ci = A->col_idx;
-  h->jpat.n = A->n;
-  h->jpat.nnz = A->nnz;
-  h->jpat.checked = true;   // every row was just verified against its pattern
-  return MGR_SUCCESS;
-}
-
-int jacobian_patterns_valid(Handle* h, const mgr_matrix_t* A, cudaStream_t s) {
-  JacobianPatterns& J = h->jpat;
-  if (J.ps.npat == 0 || J.rp != A->row_ptr || J.ci != A->col_idx || J.n != A->n || J.nnz != A->nnz)
-    return 0;
-  int* bad = h->pool.get<int>(1);
-  if (!bad) return h->pool.err;
-  int hb = 1;
-  int rc = MGR_SUCCESS;
-  if (cudaMemsetAsync(bad, 0, sizeof(int), s) != cudaSuccess) rc = MGR_ERR_CUDA;
-  if (!rc) {
-    MGR_LAUNCH k_seg_verify<<<grid_for(J.n, 8, 152 * 16), 256, 0, s>>>(
-        J.rp, J.ci, J.n, nullptr, nullptr, J.ps.pstart, J.ps.penc, J.ps.npat, J.ps.pid, J.ps.base,
-        J.ps.S, 0, bad);
-    if (cudaMemcpyAsync(&hb, bad, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaStreamSynchronize(s) != cudaSuccess)
-      rc = MGR_ERR_CUDA;
-  }
-  h->pool.release(bad, s);
-  if (rc) return rc;
-  J.checked = hb == 0;
-  return J.checked ? 1 : 0;
-}
-
 int build_amg(Handle* h, Pool& P, int* derr, const Csr& A0, bool own_input,
               const int32_t* comp0, int slot, Amg** out, cudaStream_t s) {
   Pool tmp;
@@ -3395,6 +3148,81 @@ static int sell_fp32(Pool& P, Csr& A, cudaStream_t s) {
   MGR_LAUNCH k_sell_fill<<<grid_for((n + 31) & ~int64_t(31), 256), 256, 0, s>>>(A.rp, A.v, n, A.soff,
                                                                                A.vsell);
   return MGR_SUCCESS;
+}
+
+// ----------------------------------------------------------------------------
+// Sliced (SELL-32) copy of the Jacobian for the FP64 products of FGMRES
+// ----------------------------------------------------------------------------
+// On GB300 the FP64 product is bound by the narrow FP64 pipe as much as by
+// HBM: with G lanes per row every row adds log2(G) shuffle-adds and a ragged
+// last round of multiply-adds.  One thread per row over a sliced copy (rows
+// in slices of 32, a slice's entries k-major: entry k of row r at
+// soff[r / 32] + 32 k + r % 32, padded with column r and value 0) issues one
+// multiply-add per non-zero and loads 256 contiguous bytes of values per warp
+// instruction.  A belongs to the caller and its values may change between
+// solves, so the copy is rebuilt from A at the start of every solve.
+__global__ void k_jsell_fill(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                             const double* __restrict__ v, int64_t n,
+                             const int64_t* __restrict__ soff, int32_t* __restrict__ sci,
+                             double* __restrict__ sval) {
+  const int64_t npad = (n + 31) & ~int64_t(31);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < npad; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t sl = i >> 5;
+    const int64_t L = (soff[sl + 1] - soff[sl]) >> 5;
+    const int64_t len = i < n ? rp[i + 1] - rp[i] : 0;
+    const int64_t e0 = i < n ? rp[i] : 0;
+    const int32_t self = (int32_t)(i < n ? i : 0);
+    const int64_t o = soff[sl] + (i & 31);
+    for (int64_t k = 0; k < L; k++) {
+      const bool in = k < len;
+      sci[o + k * 32] = in ? ci[e0 + k] : self;
+      sval[o + k * 32] = in ? v[e0 + k] : 0.0;
+    }
+  }
+}
+
+int jacobian_sell_refresh(Handle* h, const mgr_matrix_t* A, cudaStream_t s) {
+  JacobianSell& J = h->jsell;
+  J.valid = false;
+  if (A->nnz < JSELL_MIN_NNZ || A->n <= 0 || A->n != h->n) return 0;
+  const int64_t n = A->n, ns = (n + 31) / 32;
+  Pool& P = h->pool;
+  if (J.ns_cap < ns + 1) {
+    P.release(J.soff, s);
+    J.soff = P.get<int64_t>(ns + 1);
+    if (!J.soff) return P.err;
+    J.ns_cap = ns + 1;
+  }
+  Pool tmp;
+  tmp.s = s;
+  int64_t* cnt = tmp.get<int64_t>(ns);
+  if (!cnt) {
+    tmp.free_all_async(s);
+    return tmp.err;
+  }
+  MGR_LAUNCH k_sell_len<<<grid_for(ns, 256), 256, 0, s>>>(A->row_ptr, n, ns, cnt);
+  int64_t total = 0;
+  const int rc = rowptr_from_counts(cnt, J.soff, ns, &total, s, tmp);
+  tmp.free_all_async(s);
+  MGR_TRY(rc);
+  if (J.cap < total) {
+    P.release(J.sci, s);
+    P.release(J.sval, s);
+    J.sci = P.get<int32_t>(total);
+    J.sval = P.get<double>(total);
+    if (!J.sci || !J.sval) return P.err;
+    J.cap = total;
+  }
+  MGR_LAUNCH k_jsell_fill<<<grid_for((n + 31) & ~int64_t(31), 256), 256, 0, s>>>(
+      A->row_ptr, A->col_idx, A->val, n, J.soff, J.sci, J.sval);
+  MGR_TRY_CUDA(cudaGetLastError());
+  J.rp = A->row_ptr;
+  J.ci = A->col_idx;
+  J.val = A->val;
+  J.n = n;
+  J.nnz = A->nnz;
+  J.valid = true;
+  return 1;
 }
 
 static int amg_to_fp32(Handle* h, Amg* g, cudaStream_t s) {

@@ -31,7 +31,7 @@ EXPORTED = ["mgr_options_default", "fgmres_options_default", "mgr_setup", "mgr_a
             "mgr_launch_count", "mgr_trim_memory", "mgr_solve_host", "mgr_vcycle_noalloc", "mgr_setup_batched",
             "fgmres_solve_batched", "mgr_batch_info", "mgr_batch_handle", "mgr_destroy_batched",
             "mgr_get_block_colors", "mgr_build_id", "mgr_memory_usage", "mgr_spmv", "mgr_host_launch_count", "mgr_row_patterns",
-            "mgr_jacobian_patterns", "mgr_jacobian_product"]
+            "mgr_jacobian_product"]
 
 
 class MgrMatrix(C.Structure):
@@ -109,7 +109,6 @@ def lib():
             L.mgr_vcycle.argtypes = [P, C.c_int, P, P, P]
             L.mgr_splitmix64_device.argtypes = [P, P, I64, P]
             L.mgr_spmv.argtypes = [C.POINTER(MgrMatrix), P, P, P]
-            L.mgr_jacobian_patterns.argtypes = [P, C.POINTER(C.c_int)]
             L.mgr_jacobian_product.argtypes = [P, C.POINTER(MgrMatrix), P, P, C.c_int, P]
             L.mgr_vcycle_noalloc.argtypes = [P, C.c_int, P, P, P]
             L.mgr_setup_batched.argtypes = [C.c_int, C.POINTER(MgrMatrix), C.POINTER(MgrOptions),
@@ -404,19 +403,12 @@ def mgr_spmv(A: DeviceMatrix, x, y, stream=None):
     return _check(lib().mgr_spmv(C.byref(A.c), _ptr(x), _ptr(y), _stream_ptr(stream)), "mgr_spmv")
 
 
-def mgr_jacobian_patterns(h):
-    """(patterns, segment starts per row) of the setup's Jacobian analysis
-    ((0, 0): the solve's products read the CSR)."""
-    seg = C.c_int(0)
-    n = _check(lib().mgr_jacobian_patterns(h, C.byref(seg)), "mgr_jacobian_patterns")
-    return n, seg.value
-
-
-def mgr_jacobian_product(h, A: DeviceMatrix, x, y, check=True, stream=None):
-    """y = A x as fgmres_solve forms it; True when the patterns were used.
-    check=False reuses the last check of A's index arrays (asynchronous)."""
-    return _check(lib().mgr_jacobian_product(h, C.byref(A.c), _ptr(x), _ptr(y), int(bool(check)),
-                                             _stream_ptr(stream)), "mgr_jacobian_product") == 1
+def mgr_jacobian_product(h, A: DeviceMatrix, x, y, refresh=True, stream=None):
+    """y = A x as fgmres_solve forms it; True when a sliced copy of A was read.
+    refresh=False reuses the last copy (asynchronous; A must be unchanged)."""
+    return _check(lib().mgr_jacobian_product(h, C.byref(A.c), _ptr(x), _ptr(y),
+                                             int(bool(refresh)), _stream_ptr(stream)),
+                  "mgr_jacobian_product") == 1
 
 
 def mgr_splitmix64_device(inp, out, stream=None):

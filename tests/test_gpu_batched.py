@@ -76,6 +76,28 @@ def test_batched_equals_single_solves(members, precision, workers, ortho):
     mgr.mgr_destroy_batched(bh)
 
 
+def test_lockstep_with_sliced_jacobians_equals_single_solves():
+    """Two systems large enough (31M non-zeros each) for the solves to read
+    sliced copies of their Jacobians: the lockstep schedule's row-parallel
+    product over those copies gives every system its single-system bits."""
+    probs = [synth.two_phase(64, 64, 32, seed=q, sigma=2.0) for q in (0, 1)]
+    As = [mgr.DeviceMatrix(p) for p in probs]
+    bs = [torch.from_numpy(p.rhs).cuda() for p in probs]
+    opts = mgr.mgr_options_default(True, precision=mgr.MGR_MIXED)
+    bh = mgr.mgr_setup_batched(As, opts, workers=-1)
+    xs = [torch.zeros_like(b) for b in bs]
+    st, infos = mgr.fgmres_solve_batched(bh, As, bs, xs)
+    assert st == mgr.MGR_SUCCESS
+    mgr.mgr_destroy_batched(bh)
+    for p, A, b, x, inf in zip(probs, As, bs, xs, infos):
+        h = mgr.mgr_setup(A, opts)
+        x1 = torch.zeros_like(b)
+        r = mgr.fgmres_solve(h, A, b, x1)
+        assert mgr.mgr_jacobian_product(h, A, b, torch.empty_like(b), refresh=False)
+        mgr.mgr_destroy(h)
+        assert r["iters"] == inf["iters"] and torch.equal(x1, x)
+
+
 def test_lockstep_launches_per_round(members):
     """Lockstep: each FGMRES round is one launch per phase for all systems
     (the preconditioner applications of all of them in one graph launch), so
