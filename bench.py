@@ -662,7 +662,8 @@ def run_ours(args):
                                  ("ilu1_smoother", mgr.MGR_FP64,
                                   dict(global_smoother=[0, 2], global_sweeps=[0, 1],
                                        ilu_solve_sweeps=3)),
-                                 ("bf16_diagonals_mixed", mgr.MGR_MIXED, dict(diag_bf16=1))):
+                                 ("bf16_diagonals_mixed", mgr.MGR_MIXED, dict(diag_bf16=1)),
+                                 ("f16_values_mixed", mgr.MGR_MIXED, dict(values_f16=1))):
             solve_step(As, bs, xs, prec, **vkw)
             tm.start()
             for _ in range(3):

@@ -150,6 +150,12 @@ typedef struct {
    * rounded once from FP64), halving their bytes; every other operator stays
    * FP32.  0 in the defaults. */
   int32_t diag_bf16;
+  /* MGR_MIXED only (INVALID_ARG with MGR_FP64): 1 stores the values of the
+   * AMG operators that have shared row patterns (the finest operator of each
+   * AMG with at least 2^20 non-zeros) in FP16, each row scaled by its largest
+   * magnitude (kept in FP32), halving the bytes of the V-cycles' largest
+   * products; the products still add in FP32.  0 in the defaults. */
+  int32_t values_f16;
 } mgr_options_t;
 
 typedef struct {

@@ -147,12 +147,17 @@ k_spmv_pat(const int64_t* __restrict__ rp, const uint16_t* __restrict__ pid,
 // value loads are 128 contiguous bytes, its gathers of x follow the rows,
 // and each thread has its whole row's loads to issue -- no row-pointer reads
 // and no cross-lane reduction.  Each row's sum runs over k in order.
-template <class T, class X, class Y, int MODE, class D>
+// With FP16 values (VT = __half) each row's sum is multiplied by its scale.
+__device__ __forceinline__ float vload(float v) { return v; }
+__device__ __forceinline__ double vload(double v) { return v; }
+__device__ __forceinline__ float vload(__half v) { return __half2float(v); }
+template <class T, class X, class Y, int MODE, class D, class VT = T>
 __global__ void __launch_bounds__(256)
 k_spmv_sell(const int64_t* __restrict__ soff, const uint16_t* __restrict__ pid,
             const int32_t* __restrict__ pstart, const int32_t* __restrict__ poff,
-            const T* __restrict__ vsell, int64_t nr, const X* __restrict__ x, Y* __restrict__ y,
-            const Y* __restrict__ b, const D* __restrict__ dinv) {
+            const VT* __restrict__ vsell, const float* __restrict__ rscale, int64_t nr,
+            const X* __restrict__ x, Y* __restrict__ y, const Y* __restrict__ b,
+            const D* __restrict__ dinv) {
   const int64_t npad = (nr + 31) & ~int64_t(31);
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < npad;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -161,18 +166,20 @@ k_spmv_sell(const int64_t* __restrict__ soff, const uint16_t* __restrict__ pid,
     const int p = pid[i];
     const int32_t* po = poff + pstart[p];
     const int len = pstart[p + 1] - pstart[p];
-    const T* v = vsell + soff[sl] + (i & 31);
+    const VT* v = vsell + soff[sl] + (i & 31);
     Y acc = 0;
     if (MODE == MODE_RES0 || MODE == MODE_DRES0) {
 #pragma unroll 4
       for (int k = 0; k < len; k++) {
         const int64_t c = i + __ldg(po + k);
-        acc += (Y)v[(int64_t)k * 32] * ((Y)dval(ldg(dinv + c)) * (Y)ldg(x + c));
+        acc += (Y)vload(v[(int64_t)k * 32]) * ((Y)dval(ldg(dinv + c)) * (Y)ldg(x + c));
       }
     } else {
 #pragma unroll 4
-      for (int k = 0; k < len; k++) acc += (Y)v[(int64_t)k * 32] * (Y)ldg(x + (i + __ldg(po + k)));
+      for (int k = 0; k < len; k++)
+        acc += (Y)vload(v[(int64_t)k * 32]) * (Y)ldg(x + (i + __ldg(po + k)));
     }
+    if (std::is_same<VT, __half>::value) acc *= (Y)rscale[i];
     if (MODE == MODE_AX) y[i] = acc;
     else if (MODE == MODE_RES) y[i] = b[i] - acc;
     else if (MODE == MODE_SMOOTH) y[i] = (Y)x[i] + (Y)dval(dinv[i]) * (b[i] - acc);
@@ -272,10 +279,14 @@ template <class T, int MODE, class D = T>
 static void spmv(const Csr& A, const T* x, T* y, const T* b, const typename ident<D>::type* dinv,
                  const int64_t* rows, cudaStream_t s) {
   if constexpr (std::is_same<T, float>::value) {
-    if (A.vsell && MODE != MODE_GRES && MODE != MODE_RROWS && A.nr > 0) {
+    if ((A.vsell || A.vsellh) && MODE != MODE_GRES && MODE != MODE_RROWS && A.nr > 0) {
       const unsigned grid = (unsigned)std::min<int64_t>((A.nr + 255) / 256, 152LL * 64);
-      MGR_LAUNCH k_spmv_sell<T, T, T, MODE, D><<<grid, 256, 0, s>>>(A.soff, A.pid, A.pstart, A.poff,
-                                                                   A.vsell, A.nr, x, y, b, dinv);
+      if (A.vsellh)
+        MGR_LAUNCH k_spmv_sell<T, T, T, MODE, D, __half><<<grid, 256, 0, s>>>(
+            A.soff, A.pid, A.pstart, A.poff, A.vsellh, A.rscale, A.nr, x, y, b, dinv);
+      else
+        MGR_LAUNCH k_spmv_sell<T, T, T, MODE, D><<<grid, 256, 0, s>>>(
+            A.soff, A.pid, A.pstart, A.poff, A.vsell, nullptr, A.nr, x, y, b, dinv);
       return;
     }
   }

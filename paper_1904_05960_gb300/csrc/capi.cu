@@ -178,6 +178,7 @@ int setup_one(const mgr_matrix_t* A, const mgr_options_t* o, cudaStream_t s, Han
   for (int l = 0; l < MGR_MAX_LEVELS; l++)
     if (o->global_smoother[l] < 0 || o->global_smoother[l] > 2) return MGR_ERR_INVALID_ARG;
   if (o->diag_bf16 != 0 && (o->diag_bf16 != 1 || o->precision != MGR_MIXED)) return MGR_ERR_INVALID_ARG;
+  if (o->values_f16 != 0 && (o->values_f16 != 1 || o->precision != MGR_MIXED)) return MGR_ERR_INVALID_ARG;
   if (o->ilu_solve_sweeps < 0 || o->ilu_solve_sweeps > 1000) return MGR_ERR_INVALID_ARG;
   Handle* h = new (std::nothrow) Handle();
   if (!h) return MGR_ERR_OOM;

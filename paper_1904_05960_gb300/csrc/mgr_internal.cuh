@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <atomic>
@@ -134,6 +135,10 @@ struct Csr {
   // value k of row r at vsell[soff[r / 32] + 32 k + r % 32]; null otherwise
   float* vsell = nullptr;
   int64_t* soff = nullptr;
+  // values_f16: the sliced values in FP16 instead (vsell null), row r's
+  // values divided by rscale[r] (its largest magnitude)
+  __half* vsellh = nullptr;
+  float* rscale = nullptr;
 };
 
 // ----------------------------------------------------------------------------

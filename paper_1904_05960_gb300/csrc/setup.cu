@@ -3127,7 +3127,28 @@ __global__ void k_sell_fill(const int64_t* __restrict__ rp, const double* __rest
   }
 }
 
-static int sell_fp32(Pool& P, Csr& A, cudaStream_t s) {
+// FP16 variant (values_f16): rscale[r] = the row's largest magnitude (1 for
+// a zero row), every value divided by it in FP64 and rounded once to FP16.
+__global__ void k_sell_fill_h(const int64_t* __restrict__ rp, const double* __restrict__ v, int64_t n,
+                              const int64_t* __restrict__ soff, __half* __restrict__ vs,
+                              float* __restrict__ rscale) {
+  const int64_t npad = (n + 31) & ~int64_t(31);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < npad; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t sl = i >> 5;
+    const int64_t L = (soff[sl + 1] - soff[sl]) >> 5;
+    const int64_t len = i < n ? rp[i + 1] - rp[i] : 0;
+    const int64_t e0 = i < n ? rp[i] : 0;
+    double m = 0.0;
+    for (int64_t k = 0; k < len; k++) m = fmax(m, fabs(v[e0 + k]));
+    const float sc = m > 0.0 ? (float)m : 1.0f;
+    if (i < n) rscale[i] = sc;
+    __half* o = vs + soff[sl] + (i & 31);
+    for (int64_t k = 0; k < L; k++)
+      o[k * 32] = k < len ? __double2half(v[e0 + k] / (double)sc) : __double2half(0.0);
+  }
+}
+
+static int sell_fp32(Pool& P, Csr& A, cudaStream_t s, bool f16 = false) {
   const int64_t n = A.nr, ns = (n + 31) / 32;
   if (!A.pid || n <= 0) return MGR_SUCCESS;
   Pool tmp;
@@ -3143,6 +3164,14 @@ static int sell_fp32(Pool& P, Csr& A, cudaStream_t s) {
   int rc = rowptr_from_counts(cnt, A.soff, ns, &total, s, tmp);
   tmp.free_all_async(s);
   MGR_TRY(rc);
+  if (f16) {
+    A.vsellh = P.get<__half>(total > 0 ? total : 1);
+    A.rscale = P.get<float>(n);
+    if (!A.vsellh || !A.rscale) return P.err;
+    MGR_LAUNCH k_sell_fill_h<<<grid_for((n + 31) & ~int64_t(31), 256), 256, 0, s>>>(
+        A.rp, A.v, n, A.soff, A.vsellh, A.rscale);
+    return MGR_SUCCESS;
+  }
   A.vsell = P.get<float>(total > 0 ? total : 1);
   if (!A.vsell) return P.err;
   MGR_LAUNCH k_sell_fill<<<grid_for((n + 31) & ~int64_t(31), 256), 256, 0, s>>>(A.rp, A.v, n, A.soff,
@@ -3230,7 +3259,7 @@ static int amg_to_fp32(Handle* h, Amg* g, cudaStream_t s) {
   Pool& P = h->pool;
   for (auto& L : g->lev) {
     MGR_TRY(f32(P, L.A.v, &L.A.vf, L.A.nnz, s));
-    MGR_TRY(sell_fp32(P, L.A, s));
+    MGR_TRY(sell_fp32(P, L.A, s, h->opt.values_f16 != 0));
     MGR_TRY(f32(P, L.P.v, &L.P.vf, L.P.nnz, s));
     MGR_TRY(f32(P, L.R.v, &L.R.vf, L.R.nnz, s));
     MGR_TRY(f32(P, L.dinv, &L.dinvf, L.A.nr, s));

@@ -56,7 +56,7 @@ class MgrOptions(C.Structure):
                 ("global_smoother", C.c_int32 * MGR_MAX_LEVELS),
                 ("agg_levels", C.c_int32 * MGR_MAX_LEVELS),
                 ("ilu_solve_sweeps", C.c_int32),
-                ("diag_bf16", C.c_int32)]
+                ("diag_bf16", C.c_int32), ("values_f16", C.c_int32)]
 
 
 class FgmresOptions(C.Structure):

@@ -211,6 +211,29 @@ def test_bf16_smoother_diagonals_solution_matches_oracle(name, make):
     s.close()
 
 
+def test_f16_values_solution_matches_oracle():
+    """values_f16 (MGR_MIXED) on the 64x64x32 workload: the patterned
+    operators (A_uu and the pressure operator) read FP16 values scaled per
+    row.  Each value carries a relative rounding of 2^-11 ~ 5e-4 of its row's
+    largest magnitude; one application stays within 5e-2 of the oracle's FP64
+    one (as for the BF16 diagonals), and flexible GMRES absorbs the change:
+    iterations within +-2 of the oracle's, solution within 1e-6."""
+    p = synth.config(2)
+    o = oracle.Oracle(p)
+    ref = o.fgmres(p.rhs)
+    s = mgr.Solver(p, precision=mgr.MGR_MIXED, values_f16=1)
+    assert mgr.mgr_row_patterns(s.h, 0, 0) > 0
+    v = np.random.default_rng(29).standard_normal(p.n)
+    z = s.apply(torch.from_numpy(v).cuda()).cpu().numpy()
+    err = _maxrel(z, o.apply(v))
+    assert 0.0 < err <= 5e-2, err
+    r = s.solve(torch.from_numpy(p.rhs).cuda())
+    assert r["converged"] and r["relres"] <= 1e-8
+    assert abs(r["iters"] - ref["iters"]) <= 2, (r["iters"], ref["iters"])
+    assert _rel(r["x"].cpu().numpy(), ref["x"]) <= 1e-6
+    s.close()
+
+
 def test_directed_star_hierarchy_matches_oracle():
     """Scalar matrix whose strength graph is a directed star (the PMIS weight
     pin): C/F marks, strength, P, R and the Galerkin operator bit-exact."""
@@ -329,7 +352,8 @@ def test_invalid_arguments_are_rejected():
         mgr.mgr_setup(A, mgr.mgr_options_default(True, f_label_mask=[0b111, 0b10]))
     assert e.value.code == -1
     for bad in (dict(global_smoother=[0, 3]), dict(ilu_solve_sweeps=-1), dict(diag_bf16=1),
-                dict(diag_bf16=2, precision=mgr.MGR_MIXED)):
+                dict(diag_bf16=2, precision=mgr.MGR_MIXED), dict(values_f16=1),
+                dict(values_f16=2, precision=mgr.MGR_MIXED)):
         with pytest.raises(mgr.MgrError) as e:
             mgr.mgr_setup(A, mgr.mgr_options_default(True, **bad))
         assert e.value.code == -1
