@@ -190,6 +190,42 @@ k_spmv_sell(const int64_t* __restrict__ soff, const uint16_t* __restrict__ pid,
   }
 }
 
+// The same over a sliced operator without row patterns: the column of each
+// entry is stored beside its value (sci).  Row lengths from the row pointers.
+// MODE_GRES: y[t] = b[rows[t]] - (A x)[t] (A has one row per t).
+template <class T, class X, class Y, int MODE, class D>
+__global__ void __launch_bounds__(256)
+k_spmv_sellc(const int64_t* __restrict__ soff, const int64_t* __restrict__ rp,
+             const int32_t* __restrict__ sci, const T* __restrict__ vsell, int64_t nr,
+             const X* __restrict__ x, Y* __restrict__ y, const Y* __restrict__ b,
+             const D* __restrict__ dinv, const int64_t* __restrict__ rows) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nr;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t o = soff[i >> 5] + (i & 31);
+    const int len = (int)(rp[i + 1] - rp[i]);
+    Y acc = 0;
+    if (MODE == MODE_RES0 || MODE == MODE_DRES0) {
+#pragma unroll 4
+      for (int k = 0; k < len; k++) {
+        const int32_t c = sci[o + (int64_t)k * 32];
+        acc += (Y)vsell[o + (int64_t)k * 32] * ((Y)dval(ldg(dinv + c)) * (Y)ldg(x + c));
+      }
+    } else {
+#pragma unroll 4
+      for (int k = 0; k < len; k++)
+        acc += (Y)vsell[o + (int64_t)k * 32] * (Y)ldg(x + sci[o + (int64_t)k * 32]);
+    }
+    if (MODE == MODE_AX) y[i] = acc;
+    else if (MODE == MODE_RES) y[i] = b[i] - acc;
+    else if (MODE == MODE_SMOOTH) y[i] = (Y)x[i] + (Y)dval(dinv[i]) * (b[i] - acc);
+    else if (MODE == MODE_ADD) y[i] += acc;
+    else if (MODE == MODE_GRES) y[i] = b[rows[i]] - acc;
+    else if (MODE == MODE_RES0) y[i] = b[i] - acc;
+    else if (MODE == MODE_PROL0) y[i] = (Y)dval(dinv[i]) * b[i] + acc;
+    else if (MODE == MODE_DRES || MODE == MODE_DRES0) y[i] = (Y)dval(dinv[i]) * (b[i] - acc);
+  }
+}
+
 // Lanes per row from the mean row length (measured on GB300 for FP64 CSR:
 // ~19 non-zeros per row run best with 2 lanes, ~34-46 with 4, ~150-210 with
 // 8).
@@ -279,6 +315,12 @@ template <class T, int MODE, class D = T>
 static void spmv(const Csr& A, const T* x, T* y, const T* b, const typename ident<D>::type* dinv,
                  const int64_t* rows, cudaStream_t s) {
   if constexpr (std::is_same<T, float>::value) {
+    if (A.vsell && A.sci && MODE != MODE_RROWS && A.nr > 0) {
+      const unsigned grid = (unsigned)std::min<int64_t>((A.nr + 255) / 256, 152LL * 64);
+      MGR_LAUNCH k_spmv_sellc<T, T, T, MODE, D><<<grid, 256, 0, s>>>(A.soff, A.rp, A.sci, A.vsell,
+                                                                    A.nr, x, y, b, dinv, rows);
+      return;
+    }
     if ((A.vsell || A.vsellh) && MODE != MODE_GRES && MODE != MODE_RROWS && A.nr > 0) {
       const unsigned grid = (unsigned)std::min<int64_t>((A.nr + 255) / 256, 152LL * 64);
       if (A.vsellh)
@@ -793,8 +835,7 @@ static void mgr_level(Handle* h, int l, const T* v, T* z, cudaStream_t s) {
     spmv<T, MODE_ADD>(L.Wr, rFsrc, rC, nullptr, nullptr, nullptr, s);
   } else if (zF_only) {
     // z is zero outside F, so (A z)_C = A_CF z_F
-    spmv_launch<T, T, T, MODE_GRES>(L.Acf.rp, L.Acf.ci, vals<T>(L.Acf), nC, L.Acf.nnz, zF_only,
-                                    rC, v, nullptr, L.Cidx, s);
+    spmv<T, MODE_GRES>(L.Acf, zF_only, rC, v, nullptr, L.Cidx, s);
   } else if (zero) {
     MGR_LAUNCH k_gather<T><<<vgrid(nC), 256, 0, s>>>(v, L.Cidx, nC, rC);
     cudaMemsetAsync(z, 0, sizeof(T) * n, s);

@@ -139,6 +139,7 @@ struct Csr {
   // values divided by rscale[r] (its largest magnitude)
   __half* vsellh = nullptr;
   float* rscale = nullptr;
+  int32_t* sci = nullptr;   // sliced column indices of an operator without row patterns
 };
 
 // ----------------------------------------------------------------------------

@@ -3114,16 +3114,21 @@ __global__ void k_sell_len(const int64_t* __restrict__ rp, int64_t n, int64_t ns
   }
 }
 
-__global__ void k_sell_fill(const int64_t* __restrict__ rp, const double* __restrict__ v, int64_t n,
-                            const int64_t* __restrict__ soff, float* __restrict__ vs) {
+__global__ void k_sell_fill(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                            const double* __restrict__ v, int64_t n,
+                            const int64_t* __restrict__ soff, float* __restrict__ vs,
+                            int32_t* __restrict__ sc) {
   const int64_t npad = (n + 31) & ~int64_t(31);
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < npad; i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t sl = i >> 5;
     const int64_t L = (soff[sl + 1] - soff[sl]) >> 5;
     const int64_t len = i < n ? rp[i + 1] - rp[i] : 0;
     const int64_t e0 = i < n ? rp[i] : 0;
-    float* o = vs + soff[sl] + (i & 31);
-    for (int64_t k = 0; k < L; k++) o[k * 32] = k < len ? (float)v[e0 + k] : 0.0f;
+    const int64_t o = soff[sl] + (i & 31);
+    for (int64_t k = 0; k < L; k++) {
+      vs[o + k * 32] = k < len ? (float)v[e0 + k] : 0.0f;
+      if (sc) sc[o + k * 32] = k < len ? ci[e0 + k] : 0;
+    }
   }
 }
 
@@ -3148,9 +3153,18 @@ __global__ void k_sell_fill_h(const int64_t* __restrict__ rp, const double* __re
   }
 }
 
-static int sell_fp32(Pool& P, Csr& A, cudaStream_t s, bool f16 = false) {
+// Sliced FP32 copy of an operator: of a patterned operator (values only,
+// FP32 or, with f16, FP16), or with `columns` of an unpatterned operator with
+// at least SELL_MIN_ROWS rows (one thread per row needs that many rows).  Of
+// the unpatterned operators only A_CF of the restriction gains (measured at
+// the headline: the apply 6.82 -> 6.73 ms); the coarse AMG levels, with
+// longer and irregular rows, lose (A_uu V-cycle 2.93 -> 3.10 ms).
+static constexpr int64_t SELL_MIN_ROWS = int64_t(1) << 18;
+static int sell_fp32(Pool& P, Csr& A, cudaStream_t s, bool f16 = false, bool columns = false) {
   const int64_t n = A.nr, ns = (n + 31) / 32;
-  if (!A.pid || n <= 0) return MGR_SUCCESS;
+  if (n <= 0 || !A.v) return MGR_SUCCESS;
+  if (!A.pid && !(columns && n >= SELL_MIN_ROWS && A.nnz + 64 < INT32_MAX)) return MGR_SUCCESS;
+  if (!A.pid) f16 = false;
   Pool tmp;
   tmp.s = s;
   int64_t* cnt = tmp.get<int64_t>(ns);
@@ -3174,8 +3188,12 @@ static int sell_fp32(Pool& P, Csr& A, cudaStream_t s, bool f16 = false) {
   }
   A.vsell = P.get<float>(total > 0 ? total : 1);
   if (!A.vsell) return P.err;
-  MGR_LAUNCH k_sell_fill<<<grid_for((n + 31) & ~int64_t(31), 256), 256, 0, s>>>(A.rp, A.v, n, A.soff,
-                                                                               A.vsell);
+  if (!A.pid) {
+    A.sci = P.get<int32_t>(total > 0 ? total : 1);
+    if (!A.sci) return P.err;
+  }
+  MGR_LAUNCH k_sell_fill<<<grid_for((n + 31) & ~int64_t(31), 256), 256, 0, s>>>(A.rp, A.ci, A.v, n,
+                                                                               A.soff, A.vsell, A.sci);
   return MGR_SUCCESS;
 }
 
@@ -3276,6 +3294,7 @@ int to_fp32(Handle* h, cudaStream_t s) {
     MGR_TRY(f32(P, L.A.v, &L.A.vf, L.A.nnz, s));
     MGR_TRY(f32(P, L.W.v, &L.W.vf, L.W.nnz, s));
     MGR_TRY(f32(P, L.Acf.v, &L.Acf.vf, L.Acf.nnz, s));
+    MGR_TRY(sell_fp32(P, L.Acf, s, false, true));
     MGR_TRY(f32(P, L.dFinv, &L.dFinvf, L.nF, s));
     MGR_TRY(f32(P, L.binvc, &L.binvcf, (int64_t)L.bdim * L.bdim * L.nblk, s));
     if (h->opt.diag_bf16) {
