@@ -91,7 +91,7 @@ typedef struct {
  * first and no dropping at the second, one AMG V-cycle as the first
  * F-relaxation, one Jacobi sweep as the second, three cell-block Jacobi sweeps
  * as the second-level global smoother, AMG (theta 0.25, P_max 4, coarsest
- * <= 64 rows, <= 25 levels) on the final pressure system.
+ * <= 160 rows, <= 25 levels) on the final pressure system.
  */
 typedef struct {
   int32_t num_levels;                       /* number of reductions (0..8) */

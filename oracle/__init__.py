@@ -143,7 +143,7 @@ def default_options(two_phase=True, **kw):
              frelax_sweeps=[1, 1] if two_phase else [1],
              nmax_drop=[4, -1] if two_phase else [4],
              global_sweeps=[0, 3] if two_phase else [0],
-             amg_theta=0.25, amg_pmax=4, amg_max_coarse=64, amg_max_levels=25, seed=0,
+             amg_theta=0.25, amg_pmax=4, amg_max_coarse=160, amg_max_levels=25, seed=0,
              restrict_jacobi=[0] * MAXL, frelax_post=[0] * MAXL, dff_block=[0] * MAXL,
              global_smoother=[0] * MAXL, agg_levels=[0] * MAXL,
              ilu_solve_sweeps=3)

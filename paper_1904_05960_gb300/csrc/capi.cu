@@ -98,7 +98,7 @@ void mgr_options_default(mgr_options_t* o, int two_phase) {
   o->global_sweeps[1] = two_phase ? 3 : 0;
   o->amg_theta = 0.25;
   o->amg_pmax = 4;
-  o->amg_max_coarse = 64;
+  o->amg_max_coarse = 160;
   o->amg_max_levels = 25;
   o->precision = MGR_FP64;
   o->seed = 0;
