@@ -56,3 +56,36 @@ def test_error_strings_without_gpu():
     o = mgr.mgr_options_default(True)
     assert o.num_levels == 2 and o.nmax_drop[0] == 4 and o.nmax_drop[1] == -1
     assert o.global_sweeps[1] == 3 and abs(o.amg_theta - 0.25) < 1e-15
+
+
+def _header_src():
+    with open(os.path.join(ROOT, "include", "mgr_gb300.h")) as f:
+        return re.sub(r"/\*.*?\*/", "", f.read(), flags=re.S)
+
+
+def _struct_fields(src, name):
+    """Field names of `typedef struct { ... } name;` in declaration order."""
+    m = re.search(r"typedef struct\s*\{((?:(?!typedef struct).)*?)\}\s*" + name + r"\s*;", src,
+                  flags=re.S)
+    assert m, name
+    return re.findall(r"([A-Za-z_][A-Za-z0-9_]*)\s*(?:\[[^\]]*\])?\s*;", m.group(1))
+
+
+def test_binding_structs_and_constants_match_the_header():
+    """The ctypes mirrors of the option and info structs list the header's
+    fields in the header's order, and every MGR_* constant the binding
+    defines has the header's value (a field added on one side only would
+    shift every later field of the other)."""
+    from paper_1904_05960_gb300 import mgr
+    src = _header_src()
+    for cname, pyname in (("mgr_options_t", "MgrOptions"), ("fgmres_options_t", "FgmresOptions"),
+                          ("fgmres_info_t", "FgmresInfo"), ("mgr_matrix_t", "MgrMatrix")):
+        fields = [f[0] for f in getattr(mgr, pyname)._fields_]
+        assert fields == _struct_fields(src, cname), cname
+    defines = {k: int(v) for k, v in re.findall(r"#define\s+(MGR_[A-Z0-9_]+)\s+\(?(-?\d+)\)?", src)}
+    shared = [k for k in defines if hasattr(mgr, k)]
+    assert len(shared) >= 10
+    for k in shared:
+        assert getattr(mgr, k) == defines[k], k
+    fo = mgr.fgmres_options_default()
+    assert fo.ortho == mgr.MGR_ORTHO_AUTO and fo.restart == 50
