@@ -374,7 +374,9 @@ typedef struct mgr_batch_s* mgr_batch_t;
  * schedule; 0 lets the library choose by timing one round -- one FGMRES
  * iteration of every system: preconditioner application, Jacobian product and
  * the default Gram-Schmidt -- with 1, 2, 4, 8 and 16 workers and with the
- * lockstep schedule (the fastest is kept; see mgr_batch_info).  The setups
+ * lockstep schedule (the fastest is kept, the lockstep schedule only when
+ * its round takes under 0.8 of the best worker count's, since its rounds
+ * keep their cost while systems finish; see mgr_batch_info).  The setups
  * themselves run on up to 16 workers.  Ordered after the caller's earlier work
  * on `stream`; synchronises `stream` before returning.  A[i] is owned by the
  * caller and may be freed afterwards.  Errors: INVALID_ARG (nsys <= 0, workers

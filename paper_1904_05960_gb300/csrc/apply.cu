@@ -228,14 +228,15 @@ k_spmv_sellc(const int64_t* __restrict__ soff, const int64_t* __restrict__ rp,
 
 // Lanes per row from the mean row length (measured on GB300 for FP64 CSR:
 // ~19 non-zeros per row run best with 2 lanes, ~34-46 with 4, ~150-210 with
-// 8).
-static int pick_group(int64_t nnz, int64_t nr) {
+// 8; with 4-byte values rows of 128 and more run best with 16 -- the headline
+// A_uu V-cycle's coarse levels of 148-207 non-zeros per row: 2.92 -> 2.85 ms).
+static int pick_group(int64_t nnz, int64_t nr, int vbytes = 8) {
   const double avg = nr > 0 ? (double)nnz / (double)nr : 1.0;
   int g;
   if (avg < 6) g = 1;
   else if (avg < 24) g = 2;
   else if (avg < 64) g = 4;
-  else if (avg < 256) g = 8;
+  else if (avg < (vbytes == 4 ? 128 : 256)) g = 8;
   else g = 16;
   // small matrices: latency-bound, so spend more lanes per row (while a row
   // still has entries for them) until about half the GPU's threads are busy
@@ -247,7 +248,7 @@ template <class T, class X, class Y, class I, int MODE, class D>
 static void spmv_launch_i(const int64_t* rp, const int32_t* ci, const T* val, int64_t nr,
                           int64_t nnz, const X* x, Y* y, const Y* b, const D* dinv,
                           const int64_t* rows, cudaStream_t s) {
-  const int G = pick_group(nnz, nr);
+  const int G = pick_group(nnz, nr, (int)sizeof(T));
   const int tpb = 256;
   const int64_t threads = nr * G;
   const unsigned grid = (unsigned)std::min<int64_t>((threads + tpb - 1) / tpb, 152LL * 64);
@@ -338,7 +339,7 @@ static void spmv(const Csr& A, const T* x, T* y, const T* b, const typename iden
     spmv_launch<T, T, T, MODE, D>(A.rp, A.ci, vals<T>(A), A.nr, A.nnz, x, y, b, dinv, rows, s);
     return;
   }
-  const int G = pick_group(A.nnz, A.nr);
+  const int G = pick_group(A.nnz, A.nr, (int)sizeof(T));
   const unsigned grid = (unsigned)std::min<int64_t>((A.nr * G + 255) / 256, 152LL * 64);
 #define MGR_SPMV_PAT_CASE(g)                                                                      \
   case g:                                                                                         \

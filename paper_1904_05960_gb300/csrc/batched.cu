@@ -186,9 +186,14 @@ static int build_lockstep(Batch* B, const mgr_matrix_t* A, cudaStream_t s) {
 }
 
 // Schedule autotuner: time one round -- one FGMRES iteration (preconditioner
-// application, Jacobian product, the default Gram-Schmidt) of every system --
-// for each worker count and for the lockstep graph, and keep the fastest.
+// application, Jacobian product, the default Gram-Schmidt at iteration TUNE_J
+// of a cycle) of every system -- for each worker count and for the lockstep
+// graph, and keep the fastest.
 static constexpr int TUNE_M = 50;
+// the round timed is iteration TUNE_J of a cycle (half the default restart),
+// so that the Gram-Schmidt work of an average iteration is in it
+static constexpr int TUNE_J = 24;
+static constexpr double LOCKSTEP_MARGIN = 0.8;
 static int autotune_workers(Batch* B, const mgr_matrix_t* A, cudaStream_t caller) {
   MGR_TRY_CUDA(cudaStreamSynchronize(caller));
   const int counts[5] = {1, 2, 4, 8, 16};
@@ -203,7 +208,7 @@ static int autotune_workers(Batch* B, const mgr_matrix_t* A, cudaStream_t caller
       MGR_TRY_CUDA(cudaDeviceSynchronize());
       const auto t0 = std::chrono::steady_clock::now();
       const int rc = run_workers(B, w, [&](int i, cudaStream_t s) {
-        MGR_TRY(krylov_tune_iteration(B->sys[i], &A[i], TUNE_M, MGR_ORTHO_AUTO, s));
+        MGR_TRY(krylov_tune_iteration(B->sys[i], &A[i], TUNE_M, MGR_ORTHO_AUTO, TUNE_J, s));
         MGR_TRY_CUDA(cudaStreamSynchronize(s));
         return MGR_SUCCESS;
       });
@@ -218,7 +223,7 @@ static int autotune_workers(Batch* B, const mgr_matrix_t* A, cudaStream_t caller
     }
   }
   if (B->ls && B->ls->exec) {
-    MGR_TRY(lockstep_tune_prepare(B->ls, B->sys.data(), A, TUNE_M, MGR_ORTHO_AUTO, caller));
+    MGR_TRY(lockstep_tune_prepare(B->ls, B->sys.data(), A, TUNE_M, MGR_ORTHO_AUTO, TUNE_J, caller));
     double t = 0.0;
     for (int rep = 0; rep < 2; rep++) {
       MGR_TRY_CUDA(cudaDeviceSynchronize());
@@ -228,7 +233,12 @@ static int autotune_workers(Batch* B, const mgr_matrix_t* A, cudaStream_t caller
     }
     B->tune_workers.push_back(-1);
     B->tune_ms.push_back(t);
-    if (t < best) {
+    // a round with every system active flatters the lockstep schedule: its
+    // rounds keep their phase structure while the systems finish one by one,
+    // where the workers move on to the next system (measured on the
+    // 64-system ensemble: the lockstep round 10% faster than 8 workers', the
+    // whole solve 8% slower), so it must win the round by more than that
+    if (t < LOCKSTEP_MARGIN * best) {
       best = t;
       B->workers = -1;
     }

@@ -1117,8 +1117,8 @@ static int ls_iterate(Lockstep* L, long long graph_kernels, int jmax, bool cgs, 
   return MGR_SUCCESS;
 }
 
-// One lockstep round for the autotuner: every system at j = 0 (buffers made
-// valid by lockstep_tune_prepare), synchronised.
+// One lockstep round for the autotuner: every system at the iteration
+// lockstep_tune_prepare set up, synchronised.
 int lockstep_tune_round(Lockstep* L, cudaStream_t s) {
   std::vector<int> ones(L->nsys, 1);
   MGR_TRY_CUDA(cudaMemcpyAsync(L->flag, ones.data(), sizeof(int) * L->nsys, cudaMemcpyHostToDevice, s));
@@ -1126,44 +1126,54 @@ int lockstep_tune_round(Lockstep* L, cudaStream_t s) {
   for (long long q : L->body_kernels) k += q;
   bool mgs_any = false, cgs_any = false;
   for (int o : L->ortho) (o == MGR_ORTHO_MGS ? mgs_any : cgs_any) = true;
-  MGR_TRY(ls_iterate(L, k, mgs_any ? 0 : -1, cgs_any, s));
+  MGR_TRY(ls_iterate(L, k, mgs_any ? L->tune_j : -1, cgs_any, s));
   MGR_TRY_CUDA(cudaStreamSynchronize(s));
   return MGR_SUCCESS;
 }
 
-// One FGMRES iteration (j = 0, from a zero v_0) of a single system with
-// fgmres_run's kernels and no readback: the unit the batch schedule
-// autotuner times for the worker schedules.  Allocates the Krylov workspace
-// for restart m on `s` if it is not there yet.
-int krylov_tune_iteration(Handle* h, const mgr_matrix_t* A, int m, int ortho, cudaStream_t s) {
+// One FGMRES iteration (iteration j of a cycle, over a zero basis) of a
+// single system with fgmres_run's kernels and no readback: the unit the batch
+// schedule autotuner times for the worker schedules.  Allocates the Krylov
+// workspace for restart m on `s` if it is not there yet.
+int krylov_tune_iteration(Handle* h, const mgr_matrix_t* A, int m, int ortho, int j,
+                          cudaStream_t s) {
   h->pool.s = s;
   MGR_TRY(ensure_krylov(h, m, s));
-  const int sv = jacobian_sell_refresh(h, A, s);
+  if (j < 0 || j >= m) return MGR_ERR_INVALID_ARG;
+  // the sliced copy of A, made once for all of the autotuner's rounds
+  const JacobianSell& J = h->jsell;
+  int sv = (J.valid && J.rp == A->row_ptr && J.ci == A->col_idx && J.val == A->val &&
+            J.n == A->n && J.nnz == A->nnz) ? 1 : 0;
+  if (!sv) sv = jacobian_sell_refresh(h, A, s);
   if (sv < 0) return sv;
   const bool pat = sv == 1;
   const int64_t n = h->n;
-  MGR_TRY_CUDA(cudaMemsetAsync(h->V, 0, sizeof(double) * n, s));
+  // iteration j of a cycle over a zero basis: the arithmetic of any basis
+  MGR_TRY_CUDA(cudaMemsetAsync(h->V, 0, sizeof(double) * n * (j + 1), s));
+  double* vj = h->V + (int64_t)j * n;
+  double* vnext = h->V + (int64_t)(j + 1) * n;
   if (h->opt.precision == MGR_MIXED) {
-    MGR_TRY(apply_mgr_mixed_into(h, h->V, h->zout32, s));
-    MGR_LAUNCH k_widen<<<grid_for(n, KB), KB, 0, s>>>(h->zout32, (float*)h->Z, h->r, n);
+    MGR_TRY(apply_mgr_mixed_into(h, vj, h->zout32, s));
+    MGR_LAUNCH k_widen<<<grid_for(n, KB), KB, 0, s>>>(h->zout32, (float*)h->Z + (int64_t)j * n, h->r, n);
     jacobian_product(h, A, pat, h->r, h->w, nullptr, false, s);
   } else {
-    MGR_TRY(apply_mgr(h, h->V, (double*)h->Z, s));
-    jacobian_product(h, A, pat, (double*)h->Z, h->w, nullptr, false, s);
+    double* zj = (double*)h->Z + (int64_t)j * n;
+    MGR_TRY(apply_mgr(h, vj, zj, s));
+    jacobian_product(h, A, pat, zj, h->w, nullptr, false, s);
   }
   if (resolve_ortho(ortho, n) == MGR_ORTHO_MGS) {
-    mgs(h, 0, h->V + n, s);
+    mgs(h, j, vnext, s);
     MGR_TRY_CUDA(cudaGetLastError());
     return MGR_SUCCESS;
   }
   const int nb = mdot_blocks(n);
-  mdot(h, h->V, n, 1, h->w, n, h->hcol, 0, s);
-  MGR_LAUNCH k_mdot<true><<<nb, KB, 0, s>>>(h->V, n, 1, h->w, n, h->part, h->hcol);
-  MGR_LAUNCH k_mdot_final<false><<<1, FIN_T, 0, s>>>(h->part, nb, 1, h->yv, 0, nullptr);
-  MGR_LAUNCH k_mupdate<true><<<nb, KB, 0, s>>>(h->V, n, 1, h->yv, h->w, n, h->part);
-  MGR_LAUNCH k_mdot_final<false><<<1, FIN_T, 0, s>>>(h->yv, 1, 1, h->hcol, 1, nullptr);
-  MGR_LAUNCH k_mdot_final<true><<<1, FIN_T, 0, s>>>(h->part, nb, 1, h->hcol + 1, 0, h->hred + 1);
-  MGR_LAUNCH k_scale_by<<<grid_for(n, KB), KB, 0, s>>>(h->w, h->hred + 1, h->V + n, n);
+  mdot(h, h->V, n, j + 1, h->w, n, h->hcol, 0, s);
+  MGR_LAUNCH k_mdot<true><<<nb, KB, 0, s>>>(h->V, n, j + 1, h->w, n, h->part, h->hcol);
+  MGR_LAUNCH k_mdot_final<false><<<j + 1, FIN_T, 0, s>>>(h->part, nb, j + 1, h->yv, 0, nullptr);
+  MGR_LAUNCH k_mupdate<true><<<nb, KB, 0, s>>>(h->V, n, j + 1, h->yv, h->w, n, h->part);
+  MGR_LAUNCH k_mdot_final<false><<<j + 1, FIN_T, 0, s>>>(h->yv, 1, j + 1, h->hcol, 1, nullptr);
+  MGR_LAUNCH k_mdot_final<true><<<1, FIN_T, 0, s>>>(h->part, nb, 1, h->hcol + j + 1, 0, h->hred + 1);
+  MGR_LAUNCH k_scale_by<<<grid_for(n, KB), KB, 0, s>>>(h->w, h->hred + 1, vnext, n);
   MGR_TRY_CUDA(cudaGetLastError());
   return MGR_SUCCESS;
 }
@@ -1172,17 +1182,21 @@ static int lockstep_plan(Lockstep* L, Handle** hs, const mgr_matrix_t* A, const 
                          double* const* x, int m, int ortho, cudaStream_t s);
 
 // The lockstep graph's round over valid buffers for the autotuner: every
-// system's Krylov workspace for restart m, descriptors, j = 0 and v_0 = 0.
-int lockstep_tune_prepare(Lockstep* L, Handle** hs, const mgr_matrix_t* A, int m, int ortho,
+// system's Krylov workspace for restart m, descriptors, iteration j of a
+// cycle over a zero basis (v_0 .. v_j = 0).
+int lockstep_tune_prepare(Lockstep* L, Handle** hs, const mgr_matrix_t* A, int m, int ortho, int j,
                           cudaStream_t s) {
+  if (j < 0 || j >= m) return MGR_ERR_INVALID_ARG;
   std::vector<const double*> nb(L->nsys, nullptr);
   std::vector<double*> nx(L->nsys, nullptr);
   for (int q = 0; q < L->nsys; q++) hs[q]->pool.s = s;
   MGR_TRY(lockstep_plan(L, hs, A, nb.data(), nx.data(), m, ortho, s));
   for (int q = 0; q < L->nsys; q++)
-    MGR_TRY_CUDA(cudaMemsetAsync(hs[q]->V, 0, sizeof(double) * hs[q]->n, s));
-  MGR_TRY_CUDA(cudaMemsetAsync(L->jcur, 0, sizeof(int) * L->nsys, s));
-  MGR_TRY_CUDA(cudaStreamSynchronize(s));
+    MGR_TRY_CUDA(cudaMemsetAsync(hs[q]->V, 0, sizeof(double) * hs[q]->n * (j + 1), s));
+  std::vector<int> jv(L->nsys, j);
+  MGR_TRY_CUDA(cudaMemcpyAsync(L->jcur, jv.data(), sizeof(int) * L->nsys, cudaMemcpyHostToDevice, s));
+  MGR_TRY_CUDA(cudaStreamSynchronize(s));   // jv outlives its copy
+  L->tune_j = j;
   return MGR_SUCCESS;
 }
 

@@ -362,6 +362,7 @@ struct Lockstep {
   int mgs_gmax = 1;                 // the largest system's modified Gram-Schmidt grid
   std::vector<int> ortho;           // this solve's resolved orthogonalisation per system
   bool any_sell = false;            // some system's products read its sliced copy
+  int tune_j = 0;                   // the autotuner's iteration within a cycle
   double* hpin = nullptr;           // pinned host: Hc, red mirrors
   int* ipin = nullptr;              // pinned host: flag, jcur
   ~Lockstep();
@@ -376,9 +377,9 @@ inline int resolve_ortho(int o, int64_t n) {
   return (o == MGR_ORTHO_MGS || o == MGR_ORTHO_CGS2) ? o : -1;
 }
 int lockstep_tune_round(Lockstep* L, cudaStream_t s);
-int lockstep_tune_prepare(Lockstep* L, Handle** hs, const mgr_matrix_t* A, int m, int ortho,
+int lockstep_tune_prepare(Lockstep* L, Handle** hs, const mgr_matrix_t* A, int m, int ortho, int j,
                           cudaStream_t s);
-int krylov_tune_iteration(Handle* h, const mgr_matrix_t* A, int m, int ortho, cudaStream_t s);
+int krylov_tune_iteration(Handle* h, const mgr_matrix_t* A, int m, int ortho, int j, cudaStream_t s);
 int fgmres_lockstep(Lockstep* L, Handle** hs, const mgr_matrix_t* A, const double* const* b,
                     double* const* x, const fgmres_options_t* o, fgmres_info_t* info,
                     cudaStream_t s);
