@@ -708,6 +708,35 @@ static void block_sweeps(MgrLevel& L, const D* binv, const T* v, T* z, cudaStrea
   }
 }
 
+// k_interp_correct over a sliced W (FP32, one thread per F row; the C rows
+// copied as there): z_F (+)= base + W e_C, z_C (+)= e_C.
+template <class T>
+__global__ void __launch_bounds__(256)
+k_interp_correct_sell(const int64_t* __restrict__ soff, const int64_t* __restrict__ wrp,
+                      const int32_t* __restrict__ sci, const T* __restrict__ sv,
+                      const int64_t* __restrict__ Fidx, const int64_t* __restrict__ Cidx,
+                      int64_t nF, int64_t nC, const T* __restrict__ eC, const T* __restrict__ base,
+                      T* __restrict__ z) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nF + nC;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    if (t < nF) {
+      const int64_t o = soff[t >> 5] + (t & 31);
+      const int len = (int)(wrp[t + 1] - wrp[t]);
+      T acc = 0;
+#pragma unroll 4
+      for (int k = 0; k < len; k++) acc += sv[o + (int64_t)k * 32] * ldg(eC + sci[o + (int64_t)k * 32]);
+      const int64_t d = Fidx ? Fidx[t] : t;
+      if (base) z[d] = base[t] + acc;
+      else z[d] += acc;
+    } else {
+      const int64_t c = t - nF;
+      const int64_t d = Cidx ? Cidx[c] : nF + c;
+      if (base) z[d] = eC[c];
+      else z[d] += eC[c];
+    }
+  }
+}
+
 // ----------------------------------------------------------------------------
 // Algorithm 2 at level l
 // ----------------------------------------------------------------------------
@@ -847,10 +876,20 @@ static void mgr_level(Handle* h, int l, const T* v, T* z, cudaStream_t s) {
   // coarse-grid correction by recursion
   mgr_level<T>(h, l + 1, rC, eC, s);
   // interpolate e = P~ e_C = [W_p e_C; e_C] and correct
-  const int G = pick_group(L.W.nnz, nF);
+  bool sliced = false;
+  if constexpr (std::is_same<T, float>::value) {
+    if (L.W.vsell && L.W.sci && L.W.nr == nF) {
+      const unsigned g1 = (unsigned)std::min<int64_t>((nF + nC + 255) / 256, 152LL * 64);
+      MGR_LAUNCH k_interp_correct_sell<T><<<g1, 256, 0, s>>>(L.W.soff, L.W.rp, L.W.sci, L.W.vsell, Fi,
+                                                            Ci, nF, nC, eC, zF_only, z);
+      sliced = true;
+    }
+  }
+  const int G = sliced ? 0 : pick_group(L.W.nnz, nF);
   unsigned grid = (unsigned)std::min<int64_t>(((nF + nC) * G + 255) / 256, 152LL * 64);
   const T* wv = vals<T>(L.W);
   switch (G) {
+    case 0: break;   // done over the sliced W
     case 1: MGR_LAUNCH k_interp_correct<T, 1><<<grid, 256, 0, s>>>(L.W.rp, L.W.ci, wv, Fi, Ci, nF, nC, eC, zF_only, z); break;
     case 2: MGR_LAUNCH k_interp_correct<T, 2><<<grid, 256, 0, s>>>(L.W.rp, L.W.ci, wv, Fi, Ci, nF, nC, eC, zF_only, z); break;
     case 4: MGR_LAUNCH k_interp_correct<T, 4><<<grid, 256, 0, s>>>(L.W.rp, L.W.ci, wv, Fi, Ci, nF, nC, eC, zF_only, z); break;

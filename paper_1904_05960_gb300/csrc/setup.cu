@@ -3156,9 +3156,10 @@ __global__ void k_sell_fill_h(const int64_t* __restrict__ rp, const double* __re
 // Sliced FP32 copy of an operator: of a patterned operator (values only,
 // FP32 or, with f16, FP16), or with `columns` of an unpatterned operator with
 // at least SELL_MIN_ROWS rows (one thread per row needs that many rows).  Of
-// the unpatterned operators only A_CF of the restriction gains (measured at
-// the headline: the apply 6.82 -> 6.73 ms); the coarse AMG levels, with
-// longer and irregular rows, lose (A_uu V-cycle 2.93 -> 3.10 ms).
+// the unpatterned operators A_CF of the restriction and W of the
+// interpolation gain (measured at the headline: the apply 6.82 -> 6.73 ms,
+// then 6.66 -> 6.53 ms); the coarse AMG levels, with longer and irregular
+// rows, lose (A_uu V-cycle 2.93 -> 3.10 ms).
 static constexpr int64_t SELL_MIN_ROWS = int64_t(1) << 18;
 static int sell_fp32(Pool& P, Csr& A, cudaStream_t s, bool f16 = false, bool columns = false) {
   const int64_t n = A.nr, ns = (n + 31) / 32;
@@ -3295,6 +3296,7 @@ int to_fp32(Handle* h, cudaStream_t s) {
     MGR_TRY(f32(P, L.W.v, &L.W.vf, L.W.nnz, s));
     MGR_TRY(f32(P, L.Acf.v, &L.Acf.vf, L.Acf.nnz, s));
     MGR_TRY(sell_fp32(P, L.Acf, s, false, true));
+    MGR_TRY(sell_fp32(P, L.W, s, false, true));
     MGR_TRY(f32(P, L.dFinv, &L.dFinvf, L.nF, s));
     MGR_TRY(f32(P, L.binvc, &L.binvcf, (int64_t)L.bdim * L.bdim * L.nblk, s));
     if (h->opt.diag_bf16) {
