@@ -74,7 +74,8 @@ def parse():
                          "iterations after a warm-up on the 64x64x32 workload; prints a "
                          "partial line")
     ap.add_argument("--profile-iters", type=int, default=30)
-    ap.add_argument("--profile-workload", choices=["headline", "headline_vcycle", "small", "medium"],
+    ap.add_argument("--profile-workload", choices=["headline", "headline_vcycle", "small", "medium",
+                                                   "krylov"],
                     default="headline")
     return ap.parse_args()
 
@@ -400,6 +401,30 @@ def run_ours(args):
     As = mgr.DeviceMatrix(ps)
     bs = torch.from_numpy(ps.rhs).cuda()
     xs = torch.zeros_like(bs)
+    if args.profile and args.profile_workload == "krylov":
+        # FGMRES iterations inside an NVTX range "solve" on the 96x96x48
+        # two-phase workload (2.27M unknowns: modified Gram-Schmidt; 115M
+        # non-zeros: the sliced Jacobian copy), small enough for full ncu
+        # captures of the Krylov kernels
+        pk = synth.two_phase(96, 96, 48, seed=0, sigma=2.0)
+        Ak = mgr.DeviceMatrix(pk)
+        bk = torch.from_numpy(pk.rhs).cuda()
+        xk = torch.zeros_like(bk)
+        solve_step(Ak, bk, xk, mgr.MGR_MIXED, **HEADLINE_OPTS)
+        hk = mgr.mgr_setup(Ak, mgr.mgr_options_default(True, precision=mgr.MGR_MIXED,
+                                                       **HEADLINE_OPTS), stream)
+        xk.zero_()
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("solve")
+        rk = mgr.fgmres_solve(hk, Ak, bk, xk, mgr.fgmres_options_default(max_iter=args.profile_iters),
+                              stream)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        mgr.mgr_destroy(hk)
+        if rank == 0:
+            print(json.dumps(dict(profile=True, workload="krylov", unknowns=pk.n, nnz=pk.nnz,
+                                  iters=rk["iters"])), flush=True)
+        return
     if args.profile and args.profile_workload in ("small", "medium"):
         pp = ps if args.profile_workload == "small" else synth.two_phase(**MEDIUM)
         Ap = As if pp is ps else mgr.DeviceMatrix(pp)
