@@ -209,88 +209,139 @@ __global__ void __launch_bounds__(KB) k_mupdate(const double* __restrict__ V, in
   mupdate_body<NORM>(V, ld, nv, h, w, n, part, blockIdx.x);
 }
 
-// Modified Gram-Schmidt, step i of iteration j, in one launch:
-//   w -= h[i-1] V_(i-1)                          (i >= 1)
-//   h[i] = V_i . w                                (i <= j)
-//   h[j+1] = ||w||, rinv[0] = 1 / ||w||           (i = j + 1; 1 if ||w|| = 0)
-// G = mgs_grid(n) blocks stride over KB-entry tiles, ascending for even i and
-// descending for odd i, so that every step starts where the one before it
-// ended, while that end of w and V_(i-1) is still in L2.  Each block stores
-// its partial sum; the last block to arrive (a ticket counter that it resets)
-// adds the partials in block order, so the sum does not depend on which block
-// arrives last.  No block waits for another.  The body is shared by the
-// single-system kernel and the lockstep (many-system) kernel.
+// Modified Gram-Schmidt of iteration j, two projections per launch.  Pass p
+// (p = 0 .. j/2 + 1) of iteration j:
+//   w -= h[2p-2] V_(2p-2) + h[2p-1] V_(2p-1)      (p >= 1; the second term when 2p-1 <= j)
+//   h[2p]   = V_2p . w                             (2p <= j)
+//   h[2p+1] = V_(2p+1) . w - h[2p] g[p]            (2p+1 <= j)
+//   h[j+1] = ||w||, rinv[0] = 1 / ||w|| (1 if ||w|| = 0), and for even j
+//   g[j/2] = V_j . w / ||w||                       (the last pass, p = j/2 + 1)
+// g[k] = V_2k . V_(2k+1) is the basis's own (rounding-level) inner product,
+// formed when V_(2k+1) is: V_(2k+1) . (w - h[2k] V_2k) = V_(2k+1) . w -
+// h[2k] g[k], so each projection is the one the one-at-a-time recurrence
+// takes, and w is read and written once per two projections (48 bytes per
+// entry instead of 64).  G = mgs_grid(n) blocks stride over KB-entry tiles,
+// ascending for even p and descending for odd p, so that every pass starts
+// where the one before it ended, while that end of w and the last basis
+// vectors are still in L2.  Each block stores its two partial sums; the last
+// block to arrive (a ticket counter that it resets) adds the partials in block
+// order, so the sums do not depend on which block arrives last.  No block
+// waits for another.  The body is shared by the single-system kernel and the
+// lockstep (many-system) kernel.
 static constexpr int MGS_GRID = 152 * 8;
 __host__ __device__ inline int mgs_grid(int64_t n) {
   const int64_t t = (n + KB - 1) / KB;
   return (int)(t < 1 ? 1 : (t < MGS_GRID ? t : MGS_GRID));
 }
-__device__ __forceinline__ void mgs_body(const double* __restrict__ V, int64_t ld, int i, int j,
-                                         double* __restrict__ w, int64_t n,
-                                         double* __restrict__ part, double* __restrict__ h,
-                                         double* __restrict__ rinv, unsigned* __restrict__ ticket,
-                                         int G, int blk) {
-  __shared__ double red[KB / 32];
+// part holds 2 G partials: [0, G) the first sum, [G, 2G) the second
+__device__ __forceinline__ void mgs_pair_body(const double* __restrict__ V, int64_t ld, int p,
+                                              int j, double* __restrict__ w, int64_t n,
+                                              double* __restrict__ part, double* __restrict__ h,
+                                              double* __restrict__ g, double* __restrict__ rinv,
+                                              unsigned* __restrict__ ticket, int G, int blk) {
+  __shared__ double red[2][KB / 32];
   __shared__ bool last;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const double hp = i > 0 ? h[i - 1] : 0.0;
-  const double* vp = V + (int64_t)(i > 0 ? i - 1 : 0) * ld;
-  const double* vi = V + (int64_t)(i <= j ? i : 0) * ld;
+  const bool fin = 2 * p > j;                   // the last pass: ||w||
+  const bool upd = p > 0;
+  const bool upd2 = upd && 2 * p - 1 <= j;
+  // the second sum: V_(2p+1) . w, or at the last pass of an even j, V_j . w
+  // (V_j = V_(2p-2), the vector the update reads)
+  const bool two = fin ? (j % 2 == 0) : (2 * p + 1 <= j);
+  const double ha = upd ? h[2 * p - 2] : 0.0;
+  const double hb = upd2 ? h[2 * p - 1] : 0.0;
+  const double* va = V + (int64_t)(upd ? 2 * p - 2 : 0) * ld;
+  const double* vb = V + (int64_t)(upd2 ? 2 * p - 1 : 0) * ld;
+  const double* da = V + (int64_t)(fin ? 0 : 2 * p) * ld;
+  const double* db = V + (int64_t)(!fin && two ? 2 * p + 1 : 0) * ld;
   const int64_t ntile = (n + KB - 1) / KB;
   const int64_t nk = blk < ntile ? (ntile - blk + G - 1) / G : 0;
-  double acc = 0.0;
+  double acc0 = 0.0, acc1 = 0.0;
 #pragma unroll 4
   for (int64_t kk = 0; kk < nk; kk++) {
-    const int64_t k = (i & 1) ? nk - 1 - kk : kk;
+    const int64_t k = (p & 1) ? nk - 1 - kk : kk;
     const int64_t t = (blk + k * G) * KB + threadIdx.x;
     if (t < n) {
       double x = w[t];
-      if (i > 0) {
-        x -= hp * vp[t];
+      double a = 0.0;
+      if (upd) {
+        a = va[t];
+        x -= ha * a;
+        if (upd2) x -= hb * vb[t];
         w[t] = x;
       }
-      acc += (i <= j ? vi[t] : x) * x;
+      if (fin) {
+        acc0 += x * x;
+        if (two) acc1 += a * x;
+      } else {
+        acc0 += da[t] * x;
+        if (two) acc1 += db[t] * x;
+      }
     }
   }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
-  if (lane == 0) red[wid] = acc;
+  for (int o = 16; o > 0; o >>= 1) {
+    acc0 += __shfl_xor_sync(FULL, acc0, o);
+    acc1 += __shfl_xor_sync(FULL, acc1, o);
+  }
+  if (lane == 0) {
+    red[0][wid] = acc0;
+    red[1][wid] = acc1;
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double s2 = 0.0;
-    for (int q = 0; q < KB / 32; q++) s2 += red[q];
-    part[blk] = s2;
+    double s0 = 0.0, s1 = 0.0;
+    for (int q = 0; q < KB / 32; q++) {
+      s0 += red[0][q];
+      s1 += red[1][q];
+    }
+    part[blk] = s0;
+    part[G + blk] = s1;
     __threadfence();
     last = atomicAdd(ticket, 1u) == (unsigned)(G - 1);
   }
   __syncthreads();
   if (!last) return;
-  double s2 = 0.0;
-  for (int b = threadIdx.x; b < G; b += KB) s2 += __ldcg(part + b);
+  double s0 = 0.0, s1 = 0.0;
+  for (int b = threadIdx.x; b < G; b += KB) {
+    s0 += __ldcg(part + b);
+    s1 += __ldcg(part + G + b);
+  }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(FULL, s2, o);
-  if (lane == 0) red[wid] = s2;
+  for (int o = 16; o > 0; o >>= 1) {
+    s0 += __shfl_xor_sync(FULL, s0, o);
+    s1 += __shfl_xor_sync(FULL, s1, o);
+  }
+  if (lane == 0) {
+    red[0][wid] = s0;
+    red[1][wid] = s1;
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double tot = 0.0;
-    for (int q = 0; q < KB / 32; q++) tot += red[q];
-    if (i <= j) {
-      h[i] = tot;
+    double t0 = 0.0, t1 = 0.0;
+    for (int q = 0; q < KB / 32; q++) {
+      t0 += red[0][q];
+      t1 += red[1][q];
+    }
+    if (!fin) {
+      h[2 * p] = t0;
+      if (two) h[2 * p + 1] = t1 - t0 * g[p];
     } else {
-      const double nrm = sqrt(tot);
-      h[i] = nrm;
+      const double nrm = sqrt(t0);
+      h[j + 1] = nrm;
       rinv[0] = nrm > 0.0 ? 1.0 / nrm : 1.0;
+      if (two) g[j / 2] = nrm > 0.0 ? t1 / nrm : 0.0;
     }
     *ticket = 0u;
   }
 }
 
-__global__ void __launch_bounds__(KB) k_mgs_step(const double* __restrict__ V, int64_t ld, int i,
+__global__ void __launch_bounds__(KB) k_mgs_pair(const double* __restrict__ V, int64_t ld, int p,
                                                  int j, double* __restrict__ w, int64_t n,
                                                  double* __restrict__ part, double* __restrict__ h,
-                                                 double* __restrict__ rinv,
+                                                 double* __restrict__ g, double* __restrict__ rinv,
                                                  unsigned* __restrict__ ticket) {
-  mgs_body(V, ld, i, j, w, n, part, h, rinv, ticket, gridDim.x, blockIdx.x);
+  mgs_pair_body(V, ld, p, j, w, n, part, h, g, rinv, ticket, gridDim.x, blockIdx.x);
 }
 
 // x += sum_i y[i] Z_i  (Z in FP64 or FP32)
@@ -357,8 +408,12 @@ static int ensure_krylov(Handle* h, int m, cudaStream_t s) {
   h->hred = P.get<double>(4);
   h->yv = P.get<double>(m + 2);
   h->ticket = P.get<unsigned>(1);
+  h->gram = P.get<double>(m / 2 + 2);
   if (P.err) return P.err;
   MGR_TRY_CUDA(cudaMemsetAsync(h->ticket, 0, sizeof(unsigned), s));
+  // written by the solve before it is read; zeros for the autotuner's
+  // iteration over a zero basis
+  MGR_TRY_CUDA(cudaMemsetAsync(h->gram, 0, sizeof(double) * (m / 2 + 2), s));
   return MGR_SUCCESS;
 }
 
@@ -408,13 +463,14 @@ void jacobian_product(Handle* h, const mgr_matrix_t* A, bool sell, const double*
     MGR_LAUNCH k_spmv_sell64<false><<<grid, 256, 0, s>>>(J.soff, A->row_ptr, J.sci, J.sval, n, x, y, b);
 }
 
-// Modified Gram-Schmidt of w against V_0..V_j: hcol[0..j] = the projections,
-// hcol[j+1] = ||w||, vnext = w / ||w||
+// Modified Gram-Schmidt of w against V_0..V_j, two projections per launch
+// (j/2 + 2 launches): hcol[0..j] = the projections, hcol[j+1] = ||w||,
+// vnext = w / ||w||
 static void mgs(Handle* h, int j, double* vnext, cudaStream_t s) {
   const int64_t n = h->n;
-  for (int i = 0; i <= j + 1; i++)
-    MGR_LAUNCH k_mgs_step<<<mgs_grid(n), KB, 0, s>>>(h->V, n, i, j, h->w, n, h->part, h->hcol,
-                                                     h->hred + 1, h->ticket);
+  for (int p = 0; p <= j / 2 + 1; p++)
+    MGR_LAUNCH k_mgs_pair<<<mgs_grid(n), KB, 0, s>>>(h->V, n, p, j, h->w, n, h->part, h->hcol,
+                                                     h->gram, h->hred + 1, h->ticket);
   MGR_LAUNCH k_scale_by<<<grid_for(n, KB), KB, 0, s>>>(h->w, h->hred + 1, vnext, n);
 }
 
@@ -895,26 +951,26 @@ __global__ void k_ls_scale(const LsSys* __restrict__ S, const int* __restrict__ 
   }
 }
 
-// Modified Gram-Schmidt step i for every flagged system that orthogonalises
-// that way and whose iteration j has i <= j + 1: grid (the largest system's
+// Modified Gram-Schmidt pass p for every flagged system that orthogonalises
+// that way and whose iteration j has p <= j/2 + 1: grid (the largest system's
 // mgs_grid, systems); the blocks beyond a system's own mgs_grid return, the
 // rest run the single-system body with that system's grid, partial buffer,
-// counter and Hessenberg column.
+// counter, Gram entries and Hessenberg column.
 __global__ void __launch_bounds__(KB) k_ls_mgs(const LsSys* __restrict__ S, const int* __restrict__ flag,
-                                               const int* __restrict__ jcur, int i,
+                                               const int* __restrict__ jcur, int p,
                                                double* __restrict__ part, double* __restrict__ Hc,
-                                               double* __restrict__ red,
+                                               double* __restrict__ gram, double* __restrict__ red,
                                                unsigned* __restrict__ tickets) {
   const int s = blockIdx.y;
   if (!flag[s]) return;
   const LsSys& d = S[s];
   if (d.ortho != MGR_ORTHO_MGS) return;
   const int j = jcur[s];
-  if (i > j + 1) return;
+  if (p > j / 2 + 1) return;
   const int G = mgs_grid(d.n);
   if ((int)blockIdx.x >= G) return;
-  mgs_body(d.V, d.n, i, j, d.w, d.n, part + d.blk0 * LS_H, Hc + (int64_t)s * LS_H,
-           red + (int64_t)s * 4 + 1, tickets + s, G, blockIdx.x);
+  mgs_pair_body(d.V, d.n, p, j, d.w, d.n, part + d.blk0 * LS_H, Hc + (int64_t)s * LS_H,
+                gram + (int64_t)s * LS_H, red + (int64_t)s * 4 + 1, tickets + s, G, blockIdx.x);
 }
 
 // x += sum_{i < jcur+1} y_i Z_i (jcur holds jend - 1 here), as k_xupdate
@@ -981,8 +1037,10 @@ int lockstep_alloc(Lockstep* L, Handle** hs, const mgr_matrix_t* A, cudaStream_t
   L->Yv = P.get<double>((int64_t)ns * LS_H);
   L->red = P.get<double>((int64_t)ns * 4);
   L->tickets = P.get<unsigned>(ns);
+  L->gram = P.get<double>((int64_t)ns * LS_H);
   if (P.err) return P.err;
   MGR_TRY_CUDA(cudaMemsetAsync(L->tickets, 0, sizeof(unsigned) * ns, s));
+  MGR_TRY_CUDA(cudaMemsetAsync(L->gram, 0, sizeof(double) * ns * LS_H, s));
   MGR_TRY_CUDA(cudaMallocHost(&L->hpin, sizeof(double) * ((size_t)ns * LS_H + (size_t)ns * 4)));
   MGR_TRY_CUDA(cudaMallocHost(&L->ipin, sizeof(int) * 2 * (size_t)ns * LS_SLOTS));
   std::vector<int64_t> roff(ns + 1, 0);
@@ -1077,8 +1135,8 @@ static void ls_spmv_all(Lockstep* L, bool res, cudaStream_t s) {
 // device), each phase one launch for all of them: v_j into the graph inputs;
 // the lockstep graph (the preconditioner application of every flagged system
 // as a conditional branch); z_j out; w = A z_j; Gram-Schmidt -- modified
-// (one launch per projection up to jmax + 1, jmax = the largest j of the
-// flagged systems that use it, -1 for none) and classical twice (seven
+// (one launch per pair of projections up to pass jmax/2 + 1, jmax = the
+// largest j of the flagged systems that use it, -1 for none) and classical twice (seven
 // launches, when any flagged system uses it); v_(j+1) = w / ||w||.  Every
 // per-row, per-chunk and per-element body is the one fgmres_run's kernels
 // use, so each system gets the same bits.
@@ -1093,9 +1151,9 @@ static int ls_iterate(Lockstep* L, long long graph_kernels, int jmax, bool cgs, 
   count_graph_launch(graph_kernels);
   MGR_LAUNCH k_ls_scatter<<<vg, KB, 0, s>>>(L->dsys, L->flag, L->jcur, L->roff, ns, L->nrows, mixed, -1);
   ls_spmv_all(L, false, s);
-  for (int i = 0; i <= jmax + 1 && jmax >= 0; i++)
-    MGR_LAUNCH k_ls_mgs<<<dim3(L->mgs_gmax, ns), KB, 0, s>>>(L->dsys, L->flag, L->jcur, i, L->part,
-                                                             L->Hc, L->red, L->tickets);
+  for (int p = 0; p <= jmax / 2 + 1 && jmax >= 0; p++)
+    MGR_LAUNCH k_ls_mgs<<<dim3(L->mgs_gmax, ns), KB, 0, s>>>(L->dsys, L->flag, L->jcur, p, L->part,
+                                                             L->Hc, L->gram, L->red, L->tickets);
   if (cgs) {
     MGR_LAUNCH k_ls_mdot<false><<<nbk, KB, 0, s>>>(L->dsys, L->flag, L->jcur, L->blk_sys, L->part,
                                                     nullptr, LS_VW, -1);

@@ -260,6 +260,7 @@ struct Handle {
   double* hred = nullptr;
   double* yv = nullptr;
   unsigned* ticket = nullptr;    // arrival counter of the Gram-Schmidt steps (0 between launches)
+  double* gram = nullptr;        // device [m/2 + 2]: V_2k . V_(2k+1) of the current cycle
   // sliced copy of the Jacobian for fgmres_solve's products (from 2^24
   // non-zeros), rebuilt from the solve's matrix at the start of every solve
   JacobianSell jsell;
@@ -359,6 +360,7 @@ struct Lockstep {
   std::vector<int> lanes, nb;       // per system: lanes per row, chunk blocks
   double *Hc = nullptr, *Yv = nullptr, *red = nullptr, *part = nullptr;
   unsigned* tickets = nullptr;      // device [nsys]: modified Gram-Schmidt arrival counters
+  double* gram = nullptr;           // device [nsys * LS_H]: each system's V_2k . V_(2k+1)
   int mgs_gmax = 1;                 // the largest system's modified Gram-Schmidt grid
   std::vector<int> ortho;           // this solve's resolved orthogonalisation per system
   bool any_sell = false;            // some system's products read its sliced copy
@@ -369,9 +371,9 @@ struct Lockstep {
 };
 int lockstep_alloc(Lockstep* L, Handle** hs, const mgr_matrix_t* A, cudaStream_t s);
 // The orthogonalisation a solve of n unknowns uses for the option value o
-// (MGR_ORTHO_AUTO: modified Gram-Schmidt from 2^21 unknowns), or -1 for an
+// (MGR_ORTHO_AUTO: modified Gram-Schmidt from 2^20 unknowns), or -1 for an
 // unknown value.
-static constexpr int64_t MGS_AUTO_MIN_N = int64_t(1) << 21;
+static constexpr int64_t MGS_AUTO_MIN_N = int64_t(1) << 20;
 inline int resolve_ortho(int o, int64_t n) {
   if (o == MGR_ORTHO_AUTO) return n >= MGS_AUTO_MIN_N ? MGR_ORTHO_MGS : MGR_ORTHO_CGS2;
   return (o == MGR_ORTHO_MGS || o == MGR_ORTHO_CGS2) ? o : -1;
