@@ -164,12 +164,12 @@ typedef struct {
   double rtol;       /* stop when ||b - A x||_2 <= rtol ||b||_2 (default 1e-8) */
   /* Arnoldi orthogonalisation of iteration j, in FP64 (the paper names GMRES
    * without fixing it):
-   *   MGR_ORTHO_MGS  -- modified Gram-Schmidt, four projections per launch
-   *                     (j/4 + 2 dependent launches; each projection of a
-   *                     block of four basis vectors is corrected by the
-   *                     block's own basis inner products, so every projection
-   *                     is the one-at-a-time recurrence's; 2 FMAs and 20
-   *                     bytes per basis entry, FP64- and memory-bound);
+   *   MGR_ORTHO_MGS  -- modified Gram-Schmidt, two projections per launch
+   *                     (j/2 + 2 dependent launches; the second projection of
+   *                     a pair is corrected by the pair's own basis inner
+   *                     product, so every projection is the one-at-a-time
+   *                     recurrence's; 2 FMAs and 24 bytes per basis entry,
+   *                     memory-bound);
    *   MGR_ORTHO_CGS2 -- classical Gram-Schmidt applied twice: three passes
    *                     over the basis, 4 FMAs per basis entry (FP64-bound on
    *                     GB300, but a fixed handful of launches);
@@ -366,7 +366,7 @@ int mgr_vcycle_noalloc(mgr_handle_t h, int slot, const double* b, double* x, voi
  *     branch per system (its captured application; branches of finished
  *     systems are switched off on the device), the Jacobian products as one
  *     row-binned launch per lanes-per-row group, each Gram-Schmidt launch (a
- *     modified Gram-Schmidt block of projections, or a classical pass) over all systems'
+ *     modified Gram-Schmidt pair of projections, or a classical pass) over all systems'
  *     rows, and one readback of every Hessenberg column.  Each
  *     system's arithmetic is its single-system arithmetic, so its iterations
  *     and solution are bit for bit those of fgmres_solve.

@@ -209,150 +209,139 @@ __global__ void __launch_bounds__(KB) k_mupdate(const double* __restrict__ V, in
   mupdate_body<NORM>(V, ld, nv, h, w, n, part, blockIdx.x);
 }
 
-// Modified Gram-Schmidt of iteration j, MGS_B projections per launch.  The
-// basis is taken in blocks of B = MGS_B vectors (block k = V_kB .. V_(kB+B-1));
-// pass p (p = 0 .. j/B + 1) of iteration j:
-//   w -= sum_l h[(p-1)B + l] V_((p-1)B + l)        (p >= 1: block p - 1, the
-//                                                    vectors up to V_j)
-//   h[pB + l] = V_(pB+l) . w - sum_(a<l) h[pB + a] g_p(a, l)   (pB + l <= j)
-//   h[j+1] = ||w||, rinv[0] = 1 / ||w|| (1 if ||w|| = 0), and, when V_(j+1)
-//   falls in the block of V_j, g(a, .) = V_a . w / ||w|| for the block's
-//   earlier vectors V_a                              (the last pass, p = j/B + 1)
-// g_k(a, l) = V_(kB+a) . V_(kB+l) is the basis's own (rounding-level) inner
-// product, formed when V_(kB+l) is: V_(pB+l) . (w - sum_(a<l) h[pB+a] V_(pB+a))
-// is V_(pB+l) . w - sum_(a<l) h[pB+a] g_p(a, l), so each projection is the one
-// the one-at-a-time recurrence takes, and w is read and written once per B
-// projections (16 + 16 / B bytes per entry and projection instead of 32).
-// G = mgs_grid(n) blocks stride over KB-entry tiles, ascending for even p and
-// descending for odd p, so that every pass starts where the one before it
-// ended, while that end of w and the last basis vectors are still in L2.  Each
-// block stores its B partial sums; the last block to arrive (a ticket counter
-// that it resets) adds the partials in block order, so the sums do not depend
-// on which block arrives last.  No block waits for another.  The body is
-// shared by the single-system kernel and the lockstep (many-system) kernel.
-static constexpr int MGS_GRID = 152 * MGS_BLOCKS_PER_SM;
+// Modified Gram-Schmidt of iteration j, two projections per launch.  Pass p
+// (p = 0 .. j/2 + 1) of iteration j:
+//   w -= h[2p-2] V_(2p-2) + h[2p-1] V_(2p-1)      (p >= 1; the second term when 2p-1 <= j)
+//   h[2p]   = V_2p . w                             (2p <= j)
+//   h[2p+1] = V_(2p+1) . w - h[2p] g[p]            (2p+1 <= j)
+//   h[j+1] = ||w||, rinv[0] = 1 / ||w|| (1 if ||w|| = 0), and for even j
+//   g[j/2] = V_j . w / ||w||                       (the last pass, p = j/2 + 1)
+// g[k] = V_2k . V_(2k+1) is the basis's own (rounding-level) inner product,
+// formed when V_(2k+1) is: V_(2k+1) . (w - h[2k] V_2k) = V_(2k+1) . w -
+// h[2k] g[k], so each projection is the one the one-at-a-time recurrence
+// takes, and w is read and written once per two projections (48 bytes per
+// entry instead of 64).  G = mgs_grid(n) blocks stride over KB-entry tiles,
+// ascending for even p and descending for odd p, so that every pass starts
+// where the one before it ended, while that end of w and the last basis
+// vectors are still in L2.  Each block stores its two partial sums; the last
+// block to arrive (a ticket counter that it resets) adds the partials in block
+// order, so the sums do not depend on which block arrives last.  No block
+// waits for another.  The body is shared by the single-system kernel and the
+// lockstep (many-system) kernel.
+static constexpr int MGS_GRID = 152 * 8;
 __host__ __device__ inline int mgs_grid(int64_t n) {
   const int64_t t = (n + KB - 1) / KB;
   return (int)(t < 1 ? 1 : (t < MGS_GRID ? t : MGS_GRID));
 }
-// part holds B G partials: [l G, (l + 1) G) the l-th sum; g holds block k's
-// entries at g[(k B + l) B + a], a < l
-template <int B>
-__device__ __forceinline__ void mgs_block_body(const double* __restrict__ V, int64_t ld, int p,
-                                               int j, double* __restrict__ w, int64_t n,
-                                               double* __restrict__ part, double* __restrict__ h,
-                                               double* __restrict__ g, double* __restrict__ rinv,
-                                               unsigned* __restrict__ ticket, int G, int blk) {
-  __shared__ double red[B][KB / 32];
+// part holds 2 G partials: [0, G) the first sum, [G, 2G) the second
+__device__ __forceinline__ void mgs_pair_body(const double* __restrict__ V, int64_t ld, int p,
+                                              int j, double* __restrict__ w, int64_t n,
+                                              double* __restrict__ part, double* __restrict__ h,
+                                              double* __restrict__ g, double* __restrict__ rinv,
+                                              unsigned* __restrict__ ticket, int G, int blk) {
+  __shared__ double red[2][KB / 32];
   __shared__ bool last;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const bool fin = p > j / B;                                  // the last pass: ||w||
-  const int nu = p == 0 ? 0 : (fin ? j % B + 1 : B);           // vectors of the update
-  const int nd = fin ? 0 : min(B, j - p * B + 1);              // vectors of the products
-  const int ng = (fin && j % B != B - 1) ? nu : 0;             // Gram products, last pass
-  double hu[B];
-#pragma unroll
-  for (int l = 0; l < B; l++) hu[l] = l < nu ? h[(p - 1) * B + l] : 0.0;
-  const double* Vu = V + (int64_t)(p > 0 ? (p - 1) * B : 0) * ld;
-  const double* Vd = V + (int64_t)(fin ? 0 : p * B) * ld;
+  const bool fin = 2 * p > j;                   // the last pass: ||w||
+  const bool upd = p > 0;
+  const bool upd2 = upd && 2 * p - 1 <= j;
+  // the second sum: V_(2p+1) . w, or at the last pass of an even j, V_j . w
+  // (V_j = V_(2p-2), the vector the update reads)
+  const bool two = fin ? (j % 2 == 0) : (2 * p + 1 <= j);
+  const double ha = upd ? h[2 * p - 2] : 0.0;
+  const double hb = upd2 ? h[2 * p - 1] : 0.0;
+  const double* va = V + (int64_t)(upd ? 2 * p - 2 : 0) * ld;
+  const double* vb = V + (int64_t)(upd2 ? 2 * p - 1 : 0) * ld;
+  const double* da = V + (int64_t)(fin ? 0 : 2 * p) * ld;
+  const double* db = V + (int64_t)(!fin && two ? 2 * p + 1 : 0) * ld;
   const int64_t ntile = (n + KB - 1) / KB;
   const int64_t nk = blk < ntile ? (ntile - blk + G - 1) / G : 0;
-  double acc[B];
-#pragma unroll
-  for (int l = 0; l < B; l++) acc[l] = 0.0;
-#pragma unroll 2
+  double acc0 = 0.0, acc1 = 0.0;
+#pragma unroll 4
   for (int64_t kk = 0; kk < nk; kk++) {
     const int64_t k = (p & 1) ? nk - 1 - kk : kk;
     const int64_t t = (blk + k * G) * KB + threadIdx.x;
     if (t < n) {
       double x = w[t];
-      double u[B];
-#pragma unroll
-      for (int l = 0; l < B; l++) u[l] = l < nu ? Vu[(int64_t)l * ld + t] : 0.0;
-#pragma unroll
-      for (int l = 0; l < B; l++)
-        if (l < nu) x -= hu[l] * u[l];
-      if (nu > 0) w[t] = x;
+      double a = 0.0;
+      if (upd) {
+        a = va[t];
+        x -= ha * a;
+        if (upd2) x -= hb * vb[t];
+        w[t] = x;
+      }
       if (fin) {
-        acc[0] += x * x;
-#pragma unroll
-        for (int l = 0; l + 1 < B; l++)
-          if (l < ng) acc[l + 1] += u[l] * x;
+        acc0 += x * x;
+        if (two) acc1 += a * x;
       } else {
-#pragma unroll
-        for (int l = 0; l < B; l++)
-          if (l < nd) acc[l] += Vd[(int64_t)l * ld + t] * x;
+        acc0 += da[t] * x;
+        if (two) acc1 += db[t] * x;
       }
     }
   }
 #pragma unroll
-  for (int l = 0; l < B; l++) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc[l] += __shfl_xor_sync(FULL, acc[l], o);
+  for (int o = 16; o > 0; o >>= 1) {
+    acc0 += __shfl_xor_sync(FULL, acc0, o);
+    acc1 += __shfl_xor_sync(FULL, acc1, o);
   }
   if (lane == 0) {
-#pragma unroll
-    for (int l = 0; l < B; l++) red[l][wid] = acc[l];
+    red[0][wid] = acc0;
+    red[1][wid] = acc1;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-#pragma unroll
-    for (int l = 0; l < B; l++) {
-      double s2 = 0.0;
-      for (int q = 0; q < KB / 32; q++) s2 += red[l][q];
-      part[(int64_t)l * G + blk] = s2;
+    double s0 = 0.0, s1 = 0.0;
+    for (int q = 0; q < KB / 32; q++) {
+      s0 += red[0][q];
+      s1 += red[1][q];
     }
+    part[blk] = s0;
+    part[G + blk] = s1;
     __threadfence();
     last = atomicAdd(ticket, 1u) == (unsigned)(G - 1);
   }
   __syncthreads();
   if (!last) return;
-#pragma unroll
-  for (int l = 0; l < B; l++) acc[l] = 0.0;
+  double s0 = 0.0, s1 = 0.0;
   for (int b = threadIdx.x; b < G; b += KB) {
-#pragma unroll
-    for (int l = 0; l < B; l++) acc[l] += __ldcg(part + (int64_t)l * G + b);
+    s0 += __ldcg(part + b);
+    s1 += __ldcg(part + G + b);
   }
 #pragma unroll
-  for (int l = 0; l < B; l++) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc[l] += __shfl_xor_sync(FULL, acc[l], o);
+  for (int o = 16; o > 0; o >>= 1) {
+    s0 += __shfl_xor_sync(FULL, s0, o);
+    s1 += __shfl_xor_sync(FULL, s1, o);
   }
   if (lane == 0) {
-#pragma unroll
-    for (int l = 0; l < B; l++) red[l][wid] = acc[l];
+    red[0][wid] = s0;
+    red[1][wid] = s1;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double tot[B];
-#pragma unroll
-    for (int l = 0; l < B; l++) {
-      tot[l] = 0.0;
-      for (int q = 0; q < KB / 32; q++) tot[l] += red[l][q];
+    double t0 = 0.0, t1 = 0.0;
+    for (int q = 0; q < KB / 32; q++) {
+      t0 += red[0][q];
+      t1 += red[1][q];
     }
     if (!fin) {
-      const double* gp = g + (int64_t)p * B * B;
-      for (int l = 0; l < nd; l++) {
-        double v = tot[l];
-        for (int a = 0; a < l; a++) v -= h[p * B + a] * gp[l * B + a];
-        h[p * B + l] = v;
-      }
+      h[2 * p] = t0;
+      if (two) h[2 * p + 1] = t1 - t0 * g[p];
     } else {
-      const double nrm = sqrt(tot[0]);
+      const double nrm = sqrt(t0);
       h[j + 1] = nrm;
       rinv[0] = nrm > 0.0 ? 1.0 / nrm : 1.0;
-      double* gk = g + ((int64_t)((j + 1) / B) * B + (j + 1) % B) * B;
-      for (int a = 0; a < ng; a++) gk[a] = nrm > 0.0 ? tot[1 + a] / nrm : 0.0;
+      if (two) g[j / 2] = nrm > 0.0 ? t1 / nrm : 0.0;
     }
     *ticket = 0u;
   }
 }
 
-__global__ void __launch_bounds__(KB, MGS_BLOCKS_PER_SM)
-k_mgs_block(const double* __restrict__ V, int64_t ld, int p, int j, double* __restrict__ w,
-            int64_t n, double* __restrict__ part, double* __restrict__ h, double* __restrict__ g,
-            double* __restrict__ rinv, unsigned* __restrict__ ticket) {
-  mgs_block_body<MGS_B>(V, ld, p, j, w, n, part, h, g, rinv, ticket, gridDim.x, blockIdx.x);
+__global__ void __launch_bounds__(KB) k_mgs_pair(const double* __restrict__ V, int64_t ld, int p,
+                                                 int j, double* __restrict__ w, int64_t n,
+                                                 double* __restrict__ part, double* __restrict__ h,
+                                                 double* __restrict__ g, double* __restrict__ rinv,
+                                                 unsigned* __restrict__ ticket) {
+  mgs_pair_body(V, ld, p, j, w, n, part, h, g, rinv, ticket, gridDim.x, blockIdx.x);
 }
 
 // x += sum_i y[i] Z_i  (Z in FP64 or FP32)
@@ -414,18 +403,17 @@ static int ensure_krylov(Handle* h, int m, cudaStream_t s) {
   else h->Z = P.get<double>((int64_t)m * n);
   h->w = P.get<double>(n);
   h->r = P.get<double>(n);
-  h->part = P.get<double>(std::max<int64_t>((int64_t)std::max<int64_t>(KGRID, mdot_blocks(n)) * (m + 2),
-                                             (int64_t)MGS_B * MGS_GRID));
+  h->part = P.get<double>((int64_t)std::max<int64_t>(KGRID, mdot_blocks(n)) * (m + 2));
   h->hcol = P.get<double>(m + 2);
   h->hred = P.get<double>(4);
   h->yv = P.get<double>(m + 2);
   h->ticket = P.get<unsigned>(1);
-  h->gram = P.get<double>(mgs_gram_size(m));
+  h->gram = P.get<double>(m / 2 + 2);
   if (P.err) return P.err;
   MGR_TRY_CUDA(cudaMemsetAsync(h->ticket, 0, sizeof(unsigned), s));
   // written by the solve before it is read; zeros for the autotuner's
   // iteration over a zero basis
-  MGR_TRY_CUDA(cudaMemsetAsync(h->gram, 0, sizeof(double) * mgs_gram_size(m), s));
+  MGR_TRY_CUDA(cudaMemsetAsync(h->gram, 0, sizeof(double) * (m / 2 + 2), s));
   return MGR_SUCCESS;
 }
 
@@ -475,14 +463,14 @@ void jacobian_product(Handle* h, const mgr_matrix_t* A, bool sell, const double*
     MGR_LAUNCH k_spmv_sell64<false><<<grid, 256, 0, s>>>(J.soff, A->row_ptr, J.sci, J.sval, n, x, y, b);
 }
 
-// Modified Gram-Schmidt of w against V_0..V_j, MGS_B projections per launch
-// (j/MGS_B + 2 launches): hcol[0..j] = the projections, hcol[j+1] = ||w||,
+// Modified Gram-Schmidt of w against V_0..V_j, two projections per launch
+// (j/2 + 2 launches): hcol[0..j] = the projections, hcol[j+1] = ||w||,
 // vnext = w / ||w||
 static void mgs(Handle* h, int j, double* vnext, cudaStream_t s) {
   const int64_t n = h->n;
-  for (int p = 0; p <= j / MGS_B + 1; p++)
-    MGR_LAUNCH k_mgs_block<<<mgs_grid(n), KB, 0, s>>>(h->V, n, p, j, h->w, n, h->part, h->hcol,
-                                                      h->gram, h->hred + 1, h->ticket);
+  for (int p = 0; p <= j / 2 + 1; p++)
+    MGR_LAUNCH k_mgs_pair<<<mgs_grid(n), KB, 0, s>>>(h->V, n, p, j, h->w, n, h->part, h->hcol,
+                                                     h->gram, h->hred + 1, h->ticket);
   MGR_LAUNCH k_scale_by<<<grid_for(n, KB), KB, 0, s>>>(h->w, h->hred + 1, vnext, n);
 }
 
@@ -968,7 +956,7 @@ __global__ void k_ls_scale(const LsSys* __restrict__ S, const int* __restrict__ 
 // mgs_grid, systems); the blocks beyond a system's own mgs_grid return, the
 // rest run the single-system body with that system's grid, partial buffer,
 // counter, Gram entries and Hessenberg column.
-__global__ void __launch_bounds__(KB, MGS_BLOCKS_PER_SM) k_ls_mgs(const LsSys* __restrict__ S, const int* __restrict__ flag,
+__global__ void __launch_bounds__(KB) k_ls_mgs(const LsSys* __restrict__ S, const int* __restrict__ flag,
                                                const int* __restrict__ jcur, int p,
                                                double* __restrict__ part, double* __restrict__ Hc,
                                                double* __restrict__ gram, double* __restrict__ red,
@@ -978,12 +966,11 @@ __global__ void __launch_bounds__(KB, MGS_BLOCKS_PER_SM) k_ls_mgs(const LsSys* _
   const LsSys& d = S[s];
   if (d.ortho != MGR_ORTHO_MGS) return;
   const int j = jcur[s];
-  if (p > j / MGS_B + 1) return;
+  if (p > j / 2 + 1) return;
   const int G = mgs_grid(d.n);
   if ((int)blockIdx.x >= G) return;
-  mgs_block_body<MGS_B>(d.V, d.n, p, j, d.w, d.n, part + d.blk0 * LS_H, Hc + (int64_t)s * LS_H,
-                        gram + (int64_t)s * LS_G, red + (int64_t)s * 4 + 1, tickets + s, G,
-                        blockIdx.x);
+  mgs_pair_body(d.V, d.n, p, j, d.w, d.n, part + d.blk0 * LS_H, Hc + (int64_t)s * LS_H,
+                gram + (int64_t)s * LS_H, red + (int64_t)s * 4 + 1, tickets + s, G, blockIdx.x);
 }
 
 // x += sum_{i < jcur+1} y_i Z_i (jcur holds jend - 1 here), as k_xupdate
@@ -1050,10 +1037,10 @@ int lockstep_alloc(Lockstep* L, Handle** hs, const mgr_matrix_t* A, cudaStream_t
   L->Yv = P.get<double>((int64_t)ns * LS_H);
   L->red = P.get<double>((int64_t)ns * 4);
   L->tickets = P.get<unsigned>(ns);
-  L->gram = P.get<double>((int64_t)ns * LS_G);
+  L->gram = P.get<double>((int64_t)ns * LS_H);
   if (P.err) return P.err;
   MGR_TRY_CUDA(cudaMemsetAsync(L->tickets, 0, sizeof(unsigned) * ns, s));
-  MGR_TRY_CUDA(cudaMemsetAsync(L->gram, 0, sizeof(double) * ns * LS_G, s));
+  MGR_TRY_CUDA(cudaMemsetAsync(L->gram, 0, sizeof(double) * ns * LS_H, s));
   MGR_TRY_CUDA(cudaMallocHost(&L->hpin, sizeof(double) * ((size_t)ns * LS_H + (size_t)ns * 4)));
   MGR_TRY_CUDA(cudaMallocHost(&L->ipin, sizeof(int) * 2 * (size_t)ns * LS_SLOTS));
   std::vector<int64_t> roff(ns + 1, 0);
@@ -1148,7 +1135,7 @@ static void ls_spmv_all(Lockstep* L, bool res, cudaStream_t s) {
 // device), each phase one launch for all of them: v_j into the graph inputs;
 // the lockstep graph (the preconditioner application of every flagged system
 // as a conditional branch); z_j out; w = A z_j; Gram-Schmidt -- modified
-// (one launch per MGS_B projections up to pass jmax/MGS_B + 1, jmax = the
+// (one launch per pair of projections up to pass jmax/2 + 1, jmax = the
 // largest j of the flagged systems that use it, -1 for none) and classical twice (seven
 // launches, when any flagged system uses it); v_(j+1) = w / ||w||.  Every
 // per-row, per-chunk and per-element body is the one fgmres_run's kernels
@@ -1164,7 +1151,7 @@ static int ls_iterate(Lockstep* L, long long graph_kernels, int jmax, bool cgs, 
   count_graph_launch(graph_kernels);
   MGR_LAUNCH k_ls_scatter<<<vg, KB, 0, s>>>(L->dsys, L->flag, L->jcur, L->roff, ns, L->nrows, mixed, -1);
   ls_spmv_all(L, false, s);
-  for (int p = 0; p <= jmax / MGS_B + 1 && jmax >= 0; p++)
+  for (int p = 0; p <= jmax / 2 + 1 && jmax >= 0; p++)
     MGR_LAUNCH k_ls_mgs<<<dim3(L->mgs_gmax, ns), KB, 0, s>>>(L->dsys, L->flag, L->jcur, p, L->part,
                                                              L->Hc, L->gram, L->red, L->tickets);
   if (cgs) {

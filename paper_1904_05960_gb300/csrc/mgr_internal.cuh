@@ -260,7 +260,7 @@ struct Handle {
   double* hred = nullptr;
   double* yv = nullptr;
   unsigned* ticket = nullptr;    // arrival counter of the Gram-Schmidt steps (0 between launches)
-  double* gram = nullptr;        // device [mgs_gram_size(m)]: the current cycle's block Gram entries
+  double* gram = nullptr;        // device [m/2 + 2]: V_2k . V_(2k+1) of the current cycle
   // sliced copy of the Jacobian for fgmres_solve's products (from 2^24
   // non-zeros), rebuilt from the solve's matrix at the start of every solve
   JacobianSell jsell;
@@ -316,13 +316,6 @@ void residual64(const int64_t* rp, const int32_t* ci, const double* v, int64_t n
 // Lockstep batch (many systems, one launch per phase; krylov.cu, batched.cu)
 // ----------------------------------------------------------------------------
 static constexpr int LS_H = 64;   // Hessenberg column stride per system (m <= 60)
-// modified Gram-Schmidt: projections per launch, resident blocks per SM of
-// its kernels (their grid), and the size of a restart-m basis's block Gram
-// entries (blocks 0 .. m/MGS_B, MGS_B x MGS_B each)
-static constexpr int MGS_B = 4;
-static constexpr int MGS_BLOCKS_PER_SM = 8;
-__host__ __device__ constexpr int mgs_gram_size(int m) { return (m / MGS_B + 2) * MGS_B * MGS_B; }
-static constexpr int LS_G = mgs_gram_size(60);   // per-system Gram stride in a lockstep plan
 
 struct LsSys {                     // device descriptor of one system
   int64_t n = 0;
@@ -367,7 +360,7 @@ struct Lockstep {
   std::vector<int> lanes, nb;       // per system: lanes per row, chunk blocks
   double *Hc = nullptr, *Yv = nullptr, *red = nullptr, *part = nullptr;
   unsigned* tickets = nullptr;      // device [nsys]: modified Gram-Schmidt arrival counters
-  double* gram = nullptr;           // device [nsys * LS_G]: each system's block Gram entries
+  double* gram = nullptr;           // device [nsys * LS_H]: each system's V_2k . V_(2k+1)
   int mgs_gmax = 1;                 // the largest system's modified Gram-Schmidt grid
   std::vector<int> ortho;           // this solve's resolved orthogonalisation per system
   bool any_sell = false;            // some system's products read its sliced copy
