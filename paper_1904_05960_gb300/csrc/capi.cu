@@ -40,8 +40,6 @@ __global__ void k_splitmix(const uint64_t* __restrict__ in, uint64_t* __restrict
     out[i] = splitmix64(in[i]);
 }
 
-static void destroy_amg(Amg* g) { delete g; }
-
 static const Csr* find_csr(Handle* h, int kind, int slot, int lvl) {
   if (kind < 10) {
     if (slot < 0 || slot >= h->L) return nullptr;

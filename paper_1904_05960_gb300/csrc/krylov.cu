@@ -574,7 +574,6 @@ int fgmres_run(Handle* h, const mgr_matrix_t* A, const double* b, double* x,
       std::fill(g.begin(), g.end(), 0.0);
       g[0] = beta;
       int jend = 0;
-      bool stop = false;
       for (int j = 0; j < m && iters < maxit; j++) {
         double* vj = h->V + (int64_t)j * n;
         double* vnext = h->V + (int64_t)(j + 1) * n;
@@ -629,7 +628,6 @@ int fgmres_run(Handle* h, const mgr_matrix_t* A, const double* b, double* x,
         const double hn = hp[j + 1];
         if (!std::isfinite(hn)) {
           status = MGR_ERR_BREAKDOWN;
-          stop = true;
           break;
         }
         for (int i = 0; i < j; i++) {
@@ -677,7 +675,6 @@ int fgmres_run(Handle* h, const mgr_matrix_t* A, const double* b, double* x,
         status = MGR_SUCCESS;
         break;
       }
-      (void)stop;
       restarts++;
     }
   }
